@@ -1,0 +1,318 @@
+"""FP64 CPU oracle of the boosted-frame PIC step (test infrastructure only).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline / reference
+arm of ``bench.py`` may import this package. The product path (the CUDA
+library behind ``include/pic.h`` and its Python binding) never imports it, and
+this package imports nothing from the product.
+
+``pic_oracle.c`` restates the method of Vay et al., "Modeling laser wakefield
+accelerators in a Lorentz boosted frame" (arXiv:1009.2727) in plain double
+precision loops; this module builds it with gcc and exposes it through ctypes.
+``boost.py`` holds the paper's analytic frame/speed-up formulas (Sec. 2).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_SRC = os.path.join(_HERE, "pic_oracle.c")
+_lock = threading.Lock()
+_lib = None
+
+# component ids used by the oracle: E, B, J
+EX, EY, EZ, BX, BY, BZ, JX, JY, JZ = range(9)
+COMPONENTS = ("Ex", "Ey", "Ez", "Bx", "By", "Bz", "Jx", "Jy", "Jz")
+
+
+def build(force: bool = False) -> str:
+    """Compile pic_oracle.c into oracle/_build/liboracle.so (plain gcc, no FMA contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(_SRC):
+        return _SO
+    tmp = _SO + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-std=c99", "-O2", "-fPIC", "-shared", "-ffp-contract=off",
+           "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+class _Config(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("nz", ctypes.c_int),
+        ("dz_lab", ctypes.c_double), ("dx", ctypes.c_double), ("gamma_boost", ctypes.c_double),
+        ("courant", ctypes.c_double), ("dt_override", ctypes.c_double),
+        ("ck_alpha", ctypes.c_double), ("ck_beta", ctypes.c_double), ("ck_gamma", ctypes.c_double),
+        ("theta", ctypes.c_double),
+        ("pml_cells", ctypes.c_int), ("pml_sigma_max", ctypes.c_double), ("pml_delta", ctypes.c_double),
+        ("pml_power", ctypes.c_double), ("pml_xi_exp", ctypes.c_int),
+        ("filter_passes", ctypes.c_int), ("filter_stride", ctypes.c_int), ("filter_compensate", ctypes.c_int),
+        ("filter_J", ctypes.c_int), ("filter_gather", ctypes.c_int),
+        ("order", ctypes.c_int), ("particle_guard", ctypes.c_int),
+        ("periodic_x", ctypes.c_int), ("periodic_z", ctypes.c_int),
+        ("moving_window", ctypes.c_int), ("window_beta", ctypes.c_double),
+    ]
+
+
+class _Plasma(ctypes.Structure):
+    _fields_ = [("n0", ctypes.c_double), ("z_start_lab", ctypes.c_double), ("ramp_lab", ctypes.c_double),
+                ("length_lab", ctypes.c_double), ("ppc_x", ctypes.c_int), ("ppc_z", ctypes.c_int),
+                ("ions", ctypes.c_int)]
+
+
+class _Laser(ctypes.Structure):
+    _fields_ = [("lambda0", ctypes.c_double), ("a0", ctypes.c_double), ("w0", ctypes.c_double),
+                ("tau_fwhm", ctypes.c_double), ("t_peak", ctypes.c_double), ("x_center", ctypes.c_double),
+                ("phase", ctypes.c_double), ("z_antenna", ctypes.c_double), ("beta_s", ctypes.c_double)]
+
+
+_D = ctypes.POINTER(ctypes.c_double)
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(_D)
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            L.orc_create.restype = ctypes.c_void_p
+            L.orc_create.argtypes = [ctypes.POINTER(_Config)]
+            L.orc_destroy.argtypes = [ctypes.c_void_p]
+            L.orc_step.argtypes = [ctypes.c_void_p, ctypes.c_int]
+            L.orc_load_plasma.argtypes = [ctypes.c_void_p, ctypes.POINTER(_Plasma)]
+            L.orc_set_laser.argtypes = [ctypes.c_void_p, ctypes.POINTER(_Laser)]
+            L.orc_set_beam.argtypes = [ctypes.c_void_p, ctypes.c_long, _D, _D, _D, _D, _D,
+                                       ctypes.c_double, ctypes.c_double]
+            L.orc_info.argtypes = [ctypes.c_void_p, _D]
+            for f in ("orc_get_field", "orc_set_field", "orc_get_gather_field"):
+                getattr(L, f).argtypes = [ctypes.c_void_p, ctypes.c_int, _D]
+            L.orc_get_history.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _D]
+            L.orc_set_history.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _D]
+            L.orc_set_ext_current.argtypes = [ctypes.c_void_p, ctypes.c_int, _D, ctypes.c_int]
+            L.orc_set_ext_profile.argtypes = [ctypes.c_void_p, ctypes.c_long, _D]
+            L.orc_num_particles.restype = ctypes.c_long
+            L.orc_num_particles.argtypes = [ctypes.c_void_p, ctypes.c_int]
+            L.orc_get_particles.argtypes = [ctypes.c_void_p, ctypes.c_int, _D, _D, _D, _D, _D, _D,
+                                            ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_int)]
+            L.orc_set_particles.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_long, _D, _D, _D, _D, _D, _D]
+            L.orc_rho.argtypes = [ctypes.c_void_p, _D]
+            L.orc_diag.argtypes = [ctypes.c_void_p, _D]
+            L.orc_btd_set.argtypes = [ctypes.c_void_p, ctypes.c_int, _D, _D]
+            L.orc_btd_get.argtypes = [ctypes.c_void_p, _D, ctypes.POINTER(ctypes.c_int)]
+            L.orc_filter_field.argtypes = [ctypes.c_void_p, ctypes.c_int, _D]
+            L.orc_deposit_one.argtypes = [ctypes.c_void_p, _D, _D, _D] + [ctypes.c_double] * 6
+            L.orc_rho_one.argtypes = [ctypes.c_void_p, _D] + [ctypes.c_double] * 3
+            L.orc_shape.restype = ctypes.c_double
+            L.orc_shape.argtypes = [ctypes.c_int, ctypes.c_double]
+            L.orc_cfl_2d.restype = ctypes.c_double
+            L.orc_cfl_2d.argtypes = [ctypes.c_double] * 6
+            L.orc_cfl_3d.restype = ctypes.c_double
+            L.orc_cfl_3d.argtypes = [ctypes.c_double] * 7
+            L.orc_filter_line.argtypes = [_D, _D, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int]
+            L.orc_boris.argtypes = [_D, _D, _D, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+            _lib = L
+    return _lib
+
+
+# ----------------------------------------------------------------------------
+# single functions
+def shape(order: int, s: float) -> float:
+    return lib().orc_shape(order, s)
+
+
+def cfl_2d(a, b, g, dx, dz, theta=0.0) -> float:
+    """dt limit of the 2D tunable solver (Eq. cfl restricted to d/dy = 0), with Friedman factor."""
+    return lib().orc_cfl_2d(a, b, g, dx, dz, theta)
+
+
+def cfl_3d(a, b, g, dx, dy, dz, theta=0.0) -> float:
+    return lib().orc_cfl_3d(a, b, g, dx, dy, dz, theta)
+
+
+def filter_line(x: np.ndarray, stride: int, alpha: float, periodic: bool) -> np.ndarray:
+    a = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.empty_like(a)
+    lib().orc_filter_line(_p(a), _p(out), a.size, stride, alpha, int(periodic))
+    return out
+
+
+def boris(u, E, B, q, m, dt) -> np.ndarray:
+    uu = np.array(u, dtype=np.float64)
+    e = np.array(E, dtype=np.float64)
+    b = np.array(B, dtype=np.float64)
+    lib().orc_boris(_p(uu), _p(e), _p(b), q, m, dt)
+    return uu
+
+
+# ----------------------------------------------------------------------------
+def _mk_config(w: dict) -> _Config:
+    c = _Config()
+    c.nx, c.nz = int(w["nx"]), int(w["nz"])
+    c.dz_lab, c.dx = float(w["dz_lab"]), float(w["dx"])
+    c.gamma_boost = float(w.get("gamma_boost", 1.0))
+    c.courant = float(w.get("courant", 0.9))
+    c.dt_override = float(w.get("dt", 0.0) or 0.0)
+    a, b, g = w.get("solver", (1.0, 0.0, 0.0))
+    c.ck_alpha, c.ck_beta, c.ck_gamma = float(a), float(b), float(g)
+    c.theta = float(w.get("theta", 0.0))
+    c.pml_cells = int(w.get("pml_cells", 0))
+    c.pml_sigma_max = float(w.get("pml_sigma_max", 4.0))
+    c.pml_delta = float(w.get("pml_delta", 5.0))
+    c.pml_power = float(w.get("pml_power", 2.0))
+    c.pml_xi_exp = int(w.get("pml_xi_exp", 1))
+    c.filter_passes = int(w.get("filter_passes", 0))
+    c.filter_stride = int(w.get("filter_stride", 1))
+    c.filter_compensate = int(w.get("filter_compensate", 0))
+    c.filter_J = int(w.get("filter_J", 0))
+    c.filter_gather = int(w.get("filter_gather", 0))
+    c.order = int(w.get("order", 3))
+    c.particle_guard = int(w.get("particle_guard", -1))
+    c.periodic_x = int(w.get("periodic_x", 0))
+    c.periodic_z = int(w.get("periodic_z", 0))
+    c.moving_window = int(w.get("moving_window", 0))
+    c.window_beta = float(w.get("window_beta", 0.0))
+    return c
+
+
+class Sim:
+    """One oracle simulation built from a workload dict (see paper_1009_2727_gb300.workloads)."""
+
+    def __init__(self, w: dict):
+        self.L = lib()
+        self.w = dict(w)
+        self._cfg = _mk_config(w)
+        self.h = self.L.orc_create(ctypes.byref(self._cfg))
+        info = self.info()
+        self.nx, self.nz = int(w["nx"]), int(w["nz"])
+        self.dx, self.dz, self.dt = info["dx"], info["dz"], info["dt"]
+        if w.get("plasma"):
+            p = w["plasma"]
+            pl = _Plasma(float(p["n0"]), float(p.get("z_start_lab", 0.0)), float(p.get("ramp_lab", 0.0)),
+                         float(p.get("length_lab", 0.0)), int(p["ppc_x"]), int(p["ppc_z"]), int(p.get("ions", 1)))
+            self.L.orc_load_plasma(self.h, ctypes.byref(pl))
+        if w.get("laser"):
+            l = w["laser"]
+            la = _Laser(float(l["lambda0"]), float(l["a0"]), float(l["w0"]), float(l["tau_fwhm"]),
+                        float(l.get("t_peak", 0.0)), float(l.get("x_center", 0.5 * self.nx * self.dx)),
+                        float(l.get("phase", 0.0)), float(l["z_antenna"]), float(l.get("beta_s", 0.0)))
+            self.L.orc_set_laser(self.h, ctypes.byref(la))
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            self.L.orc_destroy(h)
+            self.h = None
+
+    # -- state ------------------------------------------------------------
+    def info(self) -> dict:
+        o = np.zeros(13)
+        self.L.orc_info(self.h, _p(o))
+        keys = ("dx", "dz", "dt", "gamma", "beta", "z0", "step", "t", "guard", "gx_lo", "gx_hi", "gz_lo", "gz_hi")
+        return dict(zip(keys, o.tolist()))
+
+    def step(self, n: int = 1):
+        self.L.orc_step(self.h, int(n))
+
+    def field(self, comp: int) -> np.ndarray:
+        out = np.zeros((self.nx + 1) * (self.nz + 1))
+        self.L.orc_get_field(self.h, comp, _p(out))
+        return out.reshape(self.nx + 1, self.nz + 1)
+
+    def set_field(self, comp: int, a: np.ndarray):
+        a = np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+        self.L.orc_set_field(self.h, comp, _p(a))
+
+    def gather_field(self, comp: int) -> np.ndarray:
+        out = np.zeros((self.nx + 1) * (self.nz + 1))
+        self.L.orc_get_gather_field(self.h, comp, _p(out))
+        return out.reshape(self.nx + 1, self.nz + 1)
+
+    def history(self, which: int, comp: int) -> np.ndarray:
+        out = np.zeros((self.nx + 1) * (self.nz + 1))
+        self.L.orc_get_history(self.h, which, comp, _p(out))
+        return out.reshape(self.nx + 1, self.nz + 1)
+
+    def set_history(self, which: int, comp: int, a: np.ndarray):
+        a = np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+        self.L.orc_set_history(self.h, which, comp, _p(a))
+
+    def set_ext_current(self, comp: int, a: np.ndarray, alternate: bool = False):
+        """comp 0..2 = Jx, Jy, Jz; added every step before the current filter."""
+        self._ext = getattr(self, "_ext", {})
+        a = np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+        self._ext[comp] = a
+        self.L.orc_set_ext_current(self.h, comp, _p(a), int(alternate))
+
+    def set_ext_profile(self, prof: np.ndarray):
+        """per-step multiplier of the external current (zero after the table ends)"""
+        self._prof = np.ascontiguousarray(prof, dtype=np.float64)
+        self.L.orc_set_ext_profile(self.h, self._prof.size, _p(self._prof))
+
+    def filter_field(self, comp: int, a: np.ndarray) -> np.ndarray:
+        b = np.ascontiguousarray(a, dtype=np.float64).reshape(-1).copy()
+        self.L.orc_filter_field(self.h, comp, _p(b))
+        return b.reshape(self.nx + 1, self.nz + 1)
+
+    def rho(self) -> np.ndarray:
+        out = np.zeros((self.nx + 1) * (self.nz + 1))
+        self.L.orc_rho(self.h, _p(out))
+        return out.reshape(self.nx + 1, self.nz + 1)
+
+    def particles(self, species: int = 0) -> dict:
+        n = self.L.orc_num_particles(self.h, species)
+        arrs = {k: np.zeros(n) for k in ("x", "z", "ux", "uy", "uz", "w")}
+        ids = np.zeros(n, dtype=np.uint32)
+        flag = np.zeros(n, dtype=np.int32)
+        self.L.orc_get_particles(self.h, species, *(_p(arrs[k]) for k in ("x", "z", "ux", "uy", "uz", "w")),
+                                 ids.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                                 flag.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+        arrs["id"] = ids
+        arrs["alive"] = (flag & 1) != 0
+        arrs["active"] = (flag & 2) != 0
+        return arrs
+
+    def set_particles(self, species: int, x, z, ux, uy, uz, w):
+        a = [np.ascontiguousarray(v, dtype=np.float64) for v in (x, z, ux, uy, uz, w)]
+        self.L.orc_set_particles(self.h, species, a[0].size, *(_p(v) for v in a))
+
+    def set_beam(self, x, z, ux, uy, uz, t_lab: float, z_plane: float):
+        a = [np.ascontiguousarray(v, dtype=np.float64) for v in (x, z, ux, uy, uz)]
+        self.L.orc_set_beam(self.h, a[0].size, *(_p(v) for v in a), float(t_lab), float(z_plane))
+
+    def diag(self) -> dict:
+        o = np.zeros(5)
+        self.L.orc_diag(self.h, _p(o))
+        return dict(zip(("n_e", "n_beam", "gamma_lab", "spread", "field_energy"), o.tolist()))
+
+    def btd_set(self, zL: np.ndarray, tL: np.ndarray):
+        zL = np.ascontiguousarray(zL, dtype=np.float64)
+        tL = np.ascontiguousarray(tL, dtype=np.float64)
+        self._nrows = zL.size
+        self.L.orc_btd_set(self.h, zL.size, _p(zL), _p(tL))
+
+    def btd_get(self):
+        out = np.zeros(self._nrows * 6 * (self.nx + 1))
+        done = np.zeros(self._nrows * 2, dtype=np.int32)
+        self.L.orc_btd_get(self.h, _p(out), done.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+        return out.reshape(self._nrows, 6, self.nx + 1), done.reshape(self._nrows, 2)
+
+    def deposit_one(self, x0, z0, x1, z1, vy, qw):
+        shp = (self.nx + 1) * (self.nz + 1)
+        J = [np.zeros(shp) for _ in range(3)]
+        self.L.orc_deposit_one(self.h, _p(J[0]), _p(J[1]), _p(J[2]), x0, z0, x1, z1, vy, qw)
+        return [j.reshape(self.nx + 1, self.nz + 1) for j in J]
+
+    def rho_one(self, x, z, qw):
+        r = np.zeros((self.nx + 1) * (self.nz + 1))
+        self.L.orc_rho_one(self.h, _p(r), x, z, qw)
+        return r.reshape(self.nx + 1, self.nz + 1)

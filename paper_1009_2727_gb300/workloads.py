@@ -1,0 +1,119 @@
+"""Seeded, synthetic workload definitions shared by the tests, the oracle and the bench.
+
+Pure data: every entry is a plain number (SI units). This module holds none of
+the method's arithmetic; each consumer (the CUDA library through
+``pic_init``/``pic_load_plasma``/``pic_inject_laser``, the CPU oracle)
+derives its own numerical parameters (boosted cell, time step, weights) from
+these inputs.
+
+Shapes and parameter values follow the paper's workloads: the scaled 0.1 GeV
+stage of Table Tablephyspar2d (n_e = 1e19 cm^-3, lambda = 0.8 um, dx = 0.65 um,
+lambda/dz resolution, boosted frame gamma = 13) and the tunable-solver table
+(Table CKcoefs). No public dataset is involved; every input is synthetic.
+"""
+from __future__ import annotations
+
+import copy
+
+import numpy as np
+
+# Table CKcoefs: (alpha, beta, gamma) of the tunable solver, cubic-cell sets
+SOLVERS = {
+    "yee": (1.0, 0.0, 0.0),
+    "ck": (7.0 / 12.0, 1.0 / 12.0, 1.0 / 48.0),
+    "ck2": (19.0 / 24.0, 1.0 / 24.0, 1.0 / 96.0),
+    "ck3": (11.0 / 12.0, 1.0 / 24.0, -1.0 / 48.0),
+    "ck4": (3.0 / 4.0, 1.0 / 16.0, 0.0),
+    "ck5": (5.0 / 8.0, 3.0 / 40.0, 3.0 / 160.0),
+}
+
+LAMBDA0 = 0.8e-6
+
+
+def parity_2d() -> dict:
+    """Plain FP64 parity workload: 2D 256 (z) x 64 (x) cells, gamma_boost = 5.
+
+    dz = lambda0/16 in the lab (boosted dz* = (1+beta) gamma dz = 0.4949 um),
+    dx = 1.98 um (four boosted cells), Courant 0.9, Yee coefficients, 8-cell
+    PML, one bilinear pass (no compensation) on J and on the gathered fields,
+    cubic shapes, n0 = 1e18 cm^-3 with a 10-cell linear entrance ramp, 2x2
+    particles per cell, ions fixed in the lab; Gaussian laser a0 = 1,
+    w0 = 8 um, tau = 30 fs (intensity FWHM), y-polarised.
+    """
+    return {
+        "name": "parity_2d_256x64_g5",
+        "nx": 64, "nz": 256,
+        "dz_lab": LAMBDA0 / 16.0, "dx": 1.98e-6,
+        "gamma_boost": 5.0, "courant": 0.9, "dt": 0.0,
+        "solver": SOLVERS["yee"], "theta": 0.0,
+        "pml_cells": 8, "pml_sigma_max": 4.0, "pml_delta": 5.0, "pml_power": 2.0, "pml_xi_exp": 1,
+        "filter_passes": 1, "filter_stride": 1, "filter_compensate": 0, "filter_J": 1, "filter_gather": 1,
+        "order": 3, "particle_guard": -1,
+        "moving_window": 0, "window_beta": 0.0,
+        "precision": "fp64",
+        "plasma": {"n0": 1e24, "z_start_lab": 5.0 * 30.0e-6, "ramp_lab": 5.0 * 10 * 0.4949e-6,
+                   "length_lab": 0.0, "ppc_x": 2, "ppc_z": 2, "ions": 1},
+        "laser": {"lambda0": LAMBDA0, "a0": 1.0, "w0": 8e-6, "tau_fwhm": 30e-15, "t_peak": 27e-15,
+                  "x_center": 32 * 1.98e-6, "phase": 0.0, "z_antenna": 18 * 0.4949e-6, "beta_s": 0.0},
+        "steps": 500, "parity_steps": 100,
+    }
+
+
+def stage_2d(gamma_boost: float = 13.0) -> dict:
+    """Mixed-precision 2D boosted-frame 0.1 GeV-class stage: 4096 (z) x 256 (x) cells.
+
+    n0 = 1e19 cm^-3, 4x4 particles per cell, a0 = 2, w0 = 12 um, tau = 30 fs,
+    gamma_boost = 13, lambda/dz = 64 in the lab, dx = 0.65 um, Cole-Karkkainen
+    coefficients at Courant 0.99, 16-cell PML, Friedman theta = 0.1, four
+    bilinear passes plus compensation, cubic shapes. The plasma fills the box
+    and keeps entering through the +z plane (steady streaming state).
+    """
+    g = float(gamma_boost)
+    dz_b = (1.0 + np.sqrt(1.0 - 1.0 / g ** 2)) * g * LAMBDA0 / 64.0 if g > 1 else LAMBDA0 / 64.0
+    return {
+        "name": f"stage_2d_4096x256_g{g:g}",
+        "nx": 256, "nz": 4096,
+        "dz_lab": LAMBDA0 / 64.0, "dx": 0.65e-6,
+        "gamma_boost": g, "courant": 0.99, "dt": 0.0,
+        "solver": SOLVERS["ck"], "theta": 0.1,
+        "pml_cells": 16, "pml_sigma_max": 4.0, "pml_delta": 5.0, "pml_power": 2.0, "pml_xi_exp": 1,
+        "filter_passes": 4, "filter_stride": 1, "filter_compensate": 1, "filter_J": 1, "filter_gather": 1,
+        "order": 3, "particle_guard": -1,
+        "moving_window": 0, "window_beta": 0.0,
+        "precision": "mixed",
+        "plasma": {"n0": 1e25, "z_start_lab": g * 40 * dz_b, "ramp_lab": 4e-6,
+                   "length_lab": 0.0, "ppc_x": 4, "ppc_z": 4, "ions": 1},
+        "laser": {"lambda0": LAMBDA0, "a0": 2.0, "w0": 12e-6, "tau_fwhm": 30e-15, "t_peak": 45e-15,
+                  "x_center": 128 * 0.65e-6, "phase": 0.0, "z_antenna": 34 * dz_b, "beta_s": 0.0},
+    }
+
+
+def shrink(w: dict, nx: int, nz: int, **over) -> dict:
+    """Same physics on a smaller box (parity cases the oracle finishes in seconds)."""
+    v = copy.deepcopy(w)
+    v["nx"], v["nz"] = nx, nz
+    if v.get("laser"):
+        v["laser"]["x_center"] = 0.5 * nx * v["dx"]
+    v["name"] = f"{w['name']}_shrunk_{nz}x{nx}"
+    for k, val in over.items():
+        if isinstance(val, dict) and isinstance(v.get(k), dict):
+            v[k].update(val)
+        else:
+            v[k] = val
+    return v
+
+
+def lab_beam(n: int, seed: int, gamma_b: float, R_b: float, L_b: float, z_c: float, x_c: float,
+             spread: float = 0.0):
+    """Seeded lab-frame test beam (Table Tablephyspar2d profiles): transverse exp(-r^2/(8 R_b^2)),
+    longitudinal exp(-z^2/(2 L_b^2)), momentum along z with an optional relative spread.
+
+    Returns (x, z, ux, uy, uz) with u = gamma v in m/s.
+    """
+    rng = np.random.default_rng(seed)
+    c = 299792458.0
+    x = x_c + rng.normal(0.0, 2.0 * R_b, n)
+    z = z_c + rng.normal(0.0, L_b, n)
+    g = gamma_b * (1.0 + spread * rng.normal(0.0, 1.0, n))
+    uz = np.sqrt(g * g - 1.0) * c
+    return x, z, np.zeros(n), np.zeros(n), uz

@@ -1,0 +1,564 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: printed
+values of the paper (tests/golden/), closed forms (numerical dispersion,
+filter gain, Boris rotation, Lorentz transforms), invariants (discrete charge
+conservation, Gauss's law) or special cases with a known answer.
+"""
+import json
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from paper_1009_2727_gb300 import workloads as W
+
+C = 299792458.0
+QE = 1.602176634e-19
+ME = 9.1093837015e-31
+EPS0 = 8.8541878128e-12
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _frac(s):
+    s = s.strip()
+    if "sqrt" in s:
+        return eval(s, {"sqrt": math.sqrt})
+    return float(Fraction(s))
+
+
+def vacuum(nx, nz, solver="yee", dx=1e-6, dz=1e-6, courant=0.95, theta=0.0, periodic=True, **kw):
+    w = {"nx": nx, "nz": nz, "dz_lab": dz, "dx": dx, "gamma_boost": 1.0, "courant": courant,
+         "solver": W.SOLVERS[solver] if isinstance(solver, str) else solver, "theta": theta,
+         "pml_cells": 0, "order": 3, "periodic_x": int(periodic), "periodic_z": int(periodic)}
+    w.update(kw)
+    return w
+
+
+# ---------------------------------------------------------------------------
+# shapes (Sec. 4: cubic splines)
+def test_shape_partition_of_unity_and_moments(orc):
+    for order in (1, 3):
+        for x in np.linspace(0.0, 1.0, 23):
+            tot = sum(orc.shape(order, x - i) for i in range(-4, 6))
+            first = sum((x - i) * orc.shape(order, x - i) for i in range(-4, 6))
+            assert abs(tot - 1.0) < 1e-15
+            assert abs(first) < 1e-15
+    # the cubic B-spline reproduces quadratics: sum (x-i)^2 B3(x-i) = 1/3 (variance of 4 unit boxes)
+    for x in np.linspace(0.0, 1.0, 23):
+        m2 = sum((x - i) ** 2 * orc.shape(3, x - i) for i in range(-4, 6))
+        assert abs(m2 - 1.0 / 3.0) < 1e-14
+    assert orc.shape(3, 0.0) == pytest.approx(2.0 / 3.0, abs=1e-16)
+    assert orc.shape(3, 1.0) == pytest.approx(1.0 / 6.0, abs=1e-16)
+    assert orc.shape(3, 2.0) == 0.0 and orc.shape(1, 1.0) == 0.0
+
+
+# ---------------------------------------------------------------------------
+# Table CKcoefs and Eq. cfl
+def test_ck_table_normalisation_primes_and_cfl(orc):
+    tab = json.load(open(os.path.join(GOLD, "ck_coefficients.json")))
+    for name, bp, gp, a, b, g, cfl in tab["rows"]:
+        A, B, G = Fraction(a), Fraction(b), Fraction(g)
+        assert A + 4 * B + 4 * G == 1, name
+        assert Fraction(bp) == -8 * B - 16 * G, name           # beta' = -8 beta - 16 gamma
+        assert Fraction(gp) == 48 * G, name                     # gamma' = 48 gamma
+        lim = orc.cfl_3d(float(A), float(B), float(G), 1.0, 1.0, 1.0, 0.0) * C
+        assert lim == pytest.approx(_frac(cfl), rel=1e-12), name
+        assert W.SOLVERS[name] == pytest.approx((float(A), float(B), float(G)), abs=1e-16)
+
+
+def _disp_rhs(a, b, g, kx, kz, dx, dz, ky=0.0, dy=1.0):
+    """right-hand side of Eq. num_disp with the C_x, C_y, C_z of Eq. coef_num_disp1"""
+    cx, cy, cz = np.cos(kx * dx), np.cos(ky * dy), np.cos(kz * dz)
+    Cx = a + 2 * b * (cy + cz) + 4 * g * cy * cz
+    Cz = a + 2 * b * (cx + cy) + 4 * g * cx * cy
+    Cy = a + 2 * b * (cz + cx) + 4 * g * cz * cx
+    return (Cx * (np.sin(kx * dx / 2) / dx) ** 2 + Cz * (np.sin(kz * dz / 2) / dz) ** 2
+            + Cy * (np.sin(ky * dy / 2) / dy) ** 2)
+
+
+@pytest.mark.parametrize("name", list(W.SOLVERS))
+@pytest.mark.parametrize("dx,dz", [(1.0, 1.0), (2.0, 1.0), (1.0, 3.0), (0.65, 0.3245)])
+def test_cfl_2d_is_max_of_dispersion(orc, name, dx, dz):
+    a, b, g = W.SOLVERS[name]
+    kx = np.linspace(0, np.pi / dx, 201)[:, None]
+    kz = np.linspace(0, np.pi / dz, 201)[None, :]
+    rhs = _disp_rhs(a, b, g, kx, kz, dx, dz)
+    dt_brute = 1.0 / (C * math.sqrt(rhs.max()))
+    assert orc.cfl_2d(a, b, g, dx, dz, 0.0) == pytest.approx(dt_brute, rel=1e-12)
+    for th in (0.1, 0.5, 1.0):   # Friedman limit, Sec. 4.3
+        assert orc.cfl_2d(a, b, g, dx, dz, th) == pytest.approx(
+            dt_brute * math.sqrt((2 + th) / (2 + 3 * th)), rel=1e-12)
+
+
+@pytest.mark.parametrize("name", ["yee", "ck", "ck2"])
+def test_stability_boundary(orc, name):
+    """a noisy periodic vacuum field grows just above the limit and stays bounded just below it"""
+    rng = np.random.default_rng(7)
+    out = {}
+    for cour in (0.999, 1.001):
+        s = orc.Sim(vacuum(16, 16, name, courant=cour, dz=0.7e-6))
+        for comp in range(6):
+            f = rng.standard_normal((17, 17)) * (1.0 if comp < 3 else 1.0 / C)
+            s.set_field(comp, f)
+        e0 = sum(np.sum(s.field(c) ** 2) for c in range(3))
+        s.step(600)
+        out[cour] = sum(np.sum(s.field(c) ** 2) for c in range(3)) / e0
+    assert out[0.999] < 10.0
+    assert out[1.001] > 1e6
+
+
+# ---------------------------------------------------------------------------
+# Eq. num_disp: a vacuum Fourier mode advances by exactly the root of the dispersion relation
+def _mode_fields(w, s, mx, mz, n, pol):
+    a, b, g = w["solver"]
+    nx, nz, dx, dz, dt = w["nx"], w["nz"], s.dx, s.dz, s.dt
+    kx, kz = 2 * np.pi * mx / (nx * dx), 2 * np.pi * mz / (nz * dz)
+    sx, sz = np.sin(kx * dx / 2), np.sin(kz * dz / 2)
+    cx, cz = np.cos(kx * dx), np.cos(kz * dz)
+    Cx = a + 2 * b * (1 + cz) + 4 * g * cz       # c_y = 1 (d/dy = 0)
+    Cz = a + 2 * b * (cx + 1) + 4 * g * cx
+    St = C * dt * math.sqrt(Cx * sx ** 2 / dx ** 2 + Cz * sz ** 2 / dz ** 2)
+    om = 2 * math.asin(St) / dt
+    i = np.arange(nx + 1)[:, None]
+    k = np.arange(nz + 1)[None, :]
+
+    def wave(xs, zs, t):
+        return np.cos(kx * (i + xs) * dx + kz * (k + zs) * dz - om * t)
+
+    tE, tB = n * dt, (n - 0.5) * dt
+    if pol == "TE":
+        return {1: wave(0, 0, tE), 3: -(dt / dz) * sz * Cz / St * wave(0, 0.5, tB),
+                5: (dt / dx) * sx * Cx / St * wave(0.5, 0, tB)}
+    return {4: wave(0.5, 0.5, tB), 0: C * C * dt * sz / (dz * St) * wave(0.5, 0, tE),
+            2: -C * C * dt * sx / (dx * St) * wave(0, 0.5, tE)}
+
+
+@pytest.mark.parametrize("name", list(W.SOLVERS))
+@pytest.mark.parametrize("pol", ["TE", "TM"])
+@pytest.mark.parametrize("dx,dz", [(1e-6, 1e-6), (1.3e-6, 0.5e-6)])
+def test_vacuum_mode_follows_dispersion(orc, name, pol, dx, dz):
+    w = vacuum(24, 20, name, dx=dx, dz=dz, courant=0.97)
+    s = orc.Sim(w)
+    w["solver"] = W.SOLVERS[name]
+    for (mx, mz) in ((1, 0), (0, 3), (2, 5), (7, 9)):
+        s = orc.Sim(w)
+        f0 = _mode_fields(w, s, mx, mz, 0, pol)
+        for comp in range(6):
+            s.set_field(comp, f0.get(comp, np.zeros((25, 21))))
+        N = 40
+        s.step(N)
+        fN = _mode_fields(w, s, mx, mz, N, pol)
+        for comp, ref in fN.items():
+            got = s.field(comp)[:24, :20]
+            scale = np.abs(ref).max()
+            assert np.abs(got - ref[:24, :20]).max() <= 1e-10 * scale, (name, pol, mx, mz, comp)
+
+
+# ---------------------------------------------------------------------------
+# Sec. 4.3: Friedman damping, Eq. num_disp_Friedman
+@pytest.mark.parametrize("theta", [0.1, 0.5, 1.0])
+@pytest.mark.parametrize("name", ["yee", "ck"])
+def test_friedman_amplification_roots(orc, theta, name):
+    nx, nz, dx, dz = 16, 12, 1e-6, 1e-6
+    w = vacuum(nx, nz, name, dx=dx, dz=dz, courant=0.9, theta=theta)
+    a, b, g = W.SOLVERS[name]
+    s0 = orc.Sim(w)
+    dt = s0.dt
+    for (mx, mz) in ((1, 1), (3, 2), (5, 4)):
+        kx, kz = 2 * np.pi * mx / (nx * dx), 2 * np.pi * mz / (nz * dz)
+        i = np.arange(nx + 1)[:, None]
+        k = np.arange(nz + 1)[None, :]
+
+        def phase(xs, zs):
+            return np.exp(1j * (kx * (i + xs) * dx + kz * (k + zs) * dz))
+
+        # TE state: Ey (0,0), Bx (0,1/2), Bz (1/2,0), E^{n-1}_y, E-bar_y
+        ph = [phase(0, 0), phase(0, 0.5), phase(0.5, 0), phase(0, 0), phase(0, 0)]
+        M = np.zeros((5, 5), complex)
+        for col in range(5):
+            # a real unit-amplitude mode in one slot; the scheme is real and shift-invariant, so the
+            # projection of the result onto each slot's exp(i phase) is one column of the mode matrix
+            s = orc.Sim(w)
+            fields = [np.real(ph[j]) if j == col else np.zeros_like(np.real(ph[j])) for j in range(5)]
+            s.set_field(1, fields[0]); s.set_field(3, fields[1]); s.set_field(5, fields[2])
+            s.set_history(0, 1, fields[3]); s.set_history(1, 1, fields[4])
+            s.step(1)
+            res = [s.field(1), s.field(3), s.field(5), s.history(0, 1), s.history(1, 1)]
+            M[:, col] = [2.0 / (nx * nz) * np.sum(res[j][:nx, :nz] * np.conj(ph[j][:nx, :nz])) for j in range(5)]
+        lam = np.linalg.eigvals(M)
+        cx, cz = np.cos(kx * dx), np.cos(kz * dz)
+        Cx = a + 2 * b * (1 + cz) + 4 * g * cz
+        Cz = a + 2 * b * (cx + 1) + 4 * g * cx
+        wsq = (C * dt) ** 2 * (Cx * (np.sin(kx * dx / 2) / dx) ** 2 + Cz * (np.sin(kz * dz / 2) / dz) ** 2)
+        # (sin(w dt/2)/(c dt))^2 = F Omega^2 with lambda = exp(-i w dt):
+        # (l-1)^2 (2l - th) + 4 w l (2l - th) + 2 w th (l-1)^2 = 0
+        wsq = float(wsq)
+        sq = np.polymul([1.0, -1.0], [1.0, -1.0])
+        P = np.polyadd(np.polyadd(np.polymul(sq, [2.0, -theta]), np.polymul([4.0 * wsq, 0.0], [2.0, -theta])),
+                       np.multiply(2.0 * wsq * theta, sq))
+        roots = np.roots(P)
+        for r in roots:
+            assert np.min(np.abs(lam - r)) < 1e-9, (theta, name, mx, mz, r, lam)
+        # damping: every physical root inside the unit circle for theta > 0
+        assert np.all(np.abs(roots) < 1.0)
+
+
+# ---------------------------------------------------------------------------
+# Sec. 4.1: filter
+@pytest.mark.parametrize("n", [1, 2, 4, 7])
+def test_filter_impulse_is_binomial(orc, n):
+    N = 64
+    x = np.zeros(N)
+    x[N // 2] = 1.0
+    for _ in range(n):
+        x = orc.filter_line(x, 1, 0.5, False)
+    for j in range(-n, n + 1):
+        assert x[N // 2 + j] == pytest.approx(math.comb(2 * n, n + j) / 4 ** n, abs=1e-16)
+    assert np.abs(np.delete(x, range(N // 2 - n, N // 2 + n + 1))).max() == 0.0
+
+
+@pytest.mark.parametrize("n,stride,comp", [(1, 1, False), (4, 1, True), (4, 2, True), (3, 3, True)])
+def test_filter_gain_single_mode(orc, n, stride, comp):
+    N = 96
+    j = np.arange(N)
+    for m in (1, 5, 12, 24, 31, 48):
+        k = 2 * np.pi * m / N
+        x = np.cos(k * j + 0.3)
+        y = x.copy()
+        for _ in range(n):
+            y = orc.filter_line(y, stride, 0.5, True)
+        G = (0.5 + 0.5 * np.cos(stride * k)) ** n
+        if comp:
+            ac = n / 2 + 1
+            y = orc.filter_line(y, stride, ac, True)
+            G *= ac + (1 - ac) * np.cos(stride * k)
+        assert np.abs(y - G * x).max() < 1e-13
+
+
+def test_filter_compensation_is_fourth_order(orc):
+    """with alpha_c = n/2 + 1 the gain is 1 + O(k^4) (Sec. 4.1)"""
+    n = 4
+    ks = np.array([1e-2, 2e-2])
+    G = (0.5 + 0.5 * np.cos(ks)) ** n * ((n / 2 + 1) + (1 - (n / 2 + 1)) * np.cos(ks))
+    r = np.log(np.abs(G[1] - 1) / np.abs(G[0] - 1)) / np.log(2)
+    assert r == pytest.approx(4.0, abs=0.05)
+    # and the oracle's 2D filter applies that gain along each axis of a periodic 2D mode
+    w = vacuum(32, 24, "yee", filter_passes=4, filter_compensate=1, filter_stride=1)
+    s = orc.Sim(w)
+    i = np.arange(33)[:, None]
+    k = np.arange(25)[None, :]
+    kx, kz = 2 * np.pi * 3 / 32, 2 * np.pi * 5 / 24
+    f = np.cos(kx * i + kz * k + 0.2)
+    got = s.filter_field(1, f)[:32, :24]
+
+    def Gk(kk):
+        return (0.5 + 0.5 * np.cos(kk)) ** 4 * (3 - 2 * np.cos(kk))
+    assert np.abs(got - Gk(kx) * Gk(kz) * f[:32, :24]).max() < 1e-13
+
+
+# ---------------------------------------------------------------------------
+# Boris push (textbook)
+def test_boris_gyration_rotation_angle(orc):
+    B = np.array([0.0, 2.0, 0.0])
+    u = np.array([0.6 * C, 0.0, 0.3 * C])
+    g = math.sqrt(1 + (u @ u) / C ** 2)
+    dt = 2e-13
+    t = QE * 2.0 * dt / (2 * g * ME)
+    ang0 = math.atan2(u[2], u[0])
+    uu = u.copy()
+    N = 777
+    for _ in range(N):
+        uu = orc.boris(uu, [0, 0, 0], B, -QE, ME, dt)
+    assert np.linalg.norm(uu) == pytest.approx(np.linalg.norm(u), rel=1e-13)
+    ang = math.atan2(uu[2], uu[0])
+    expect = (ang0 - N * 2 * math.atan(t))   # electron: rotation sense for q < 0 about +y is negative in (x,z)
+    d = (ang - expect + math.pi) % (2 * math.pi) - math.pi
+    assert abs(d) < 1e-9
+
+
+def test_boris_exb_drift_exact(orc):
+    Ex, By = 3e8, 2.0          # v_d = Ex/By = 0.5 c along +z (E x B)
+    vd = Ex / By
+    gd = 1 / math.sqrt(1 - (vd / C) ** 2)
+    u = np.array([0.0, 0.0, gd * vd])
+    for _ in range(300):
+        u = orc.boris(u, [Ex, 0, 0], [0, By, 0], -QE, ME, 1e-15)
+    # relativistic Boris keeps the E x B drift state up to O((q E dt/(2 m u))^2)
+    assert abs(u[0]) < 1e-6 * gd * vd
+    assert u[2] == pytest.approx(gd * vd, rel=1e-6)
+
+
+# ---------------------------------------------------------------------------
+# Esirkepov deposition: exact discrete continuity, Sec. 4.2.2
+@pytest.mark.parametrize("order", [1, 3])
+def test_esirkepov_continuity_and_total_current(orc, order):
+    w = vacuum(20, 20, "yee", dx=1.1e-6, dz=0.7e-6, periodic=False, order=order)
+    s = orc.Sim(w)
+    rng = np.random.default_rng(11 + order)
+    for _ in range(40):
+        x0, z0 = rng.uniform(8, 12) * s.dx, rng.uniform(8, 12) * s.dz
+        x1, z1 = x0 + rng.uniform(-0.95, 0.95) * s.dx, z0 + rng.uniform(-0.95, 0.95) * s.dz
+        vy, qw = rng.uniform(-1, 1) * 1e8, -QE * 3.7e10
+        Jx, Jy, Jz = s.deposit_one(x0, z0, x1, z1, vy, qw)
+        r0, r1 = s.rho_one(x0, z0, qw), s.rho_one(x1, z1, qw)
+        div = np.zeros_like(r0)
+        div[1:, :] += (Jx[1:, :] - Jx[:-1, :]) / s.dx
+        div[0, :] += Jx[0, :] / s.dx
+        div[:, 1:] += (Jz[:, 1:] - Jz[:, :-1]) / s.dz
+        div[:, 0] += Jz[:, 0] / s.dz
+        res = (r1 - r0) / s.dt + div
+        scale = np.abs(r1 - r0).max() / s.dt
+        assert np.abs(res).max() <= 1e-12 * scale
+        area = s.dx * s.dz
+        assert Jx.sum() * area == pytest.approx(qw * (x1 - x0) / s.dt, rel=1e-12)
+        assert Jz.sum() * area == pytest.approx(qw * (z1 - z0) / s.dt, rel=1e-12)
+        assert Jy.sum() * area == pytest.approx(qw * vy, rel=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Gauss's law kept by the full step (Sec. 4.2.2 with PR-8): div E - F(rho)/eps0 constant
+def test_gauss_law_invariant_full_step(orc):
+    w = W.shrink(W.parity_2d(), 48, 160)
+    s = orc.Sim(w)
+    info = s.info()
+    s.step(30)
+    Ex, Ez = s.field(0), s.field(2)
+    div = np.zeros_like(Ex)
+    div[1:, :] += (Ex[1:, :] - Ex[:-1, :]) / s.dx
+    div[:, 1:] += (Ez[:, 1:] - Ez[:, :-1]) / s.dz
+    rho = s.rho()
+    frho = s.filter_field(1, rho)
+    G = div - frho / EPS0
+    i0, i1 = int(info["gx_lo"]) + 8, int(info["gx_hi"]) - 8
+    k0, k1 = int(info["gz_lo"]) + 8, int(info["gz_hi"]) - 8
+    p = s.particles(0)
+    n_e = np.abs(p["w"]).max() * 4 / (s.dx * s.dz)
+    scale = QE * n_e / EPS0
+    assert np.abs(div[i0:i1, k0:k1]).max() > 1e-6 * scale     # the laser did separate charge
+    assert np.abs(G[i0:i1, k0:k1]).max() < 1e-11 * scale
+
+
+# ---------------------------------------------------------------------------
+# App. I: odd-even mode at c dt = dz, removed by one bilinear pass
+def _app1(orc, filt, alternate, nsteps):
+    nz = 64
+    w = vacuum(4, nz, "ck", dx=1e-6, dz=1e-6, dt=1e-6 / C, filter_J=filt, filter_passes=1, order=1)
+    s = orc.Sim(w)
+    src = np.zeros((5, nz + 1))
+    src[:, nz // 2] = 1.0
+    s.set_ext_current(0, src, alternate=alternate)
+    s.step(nsteps)
+    ex = s.field(0)[0, :nz]
+    nyq = abs(np.sum(ex * (-1.0) ** np.arange(nz))) / nz
+    return nyq, np.abs(ex).max()
+
+
+def test_app1_odd_even_mode(orc):
+    """At c dt = dz the grid Nyquist mode has the double amplification root lambda = -1 (Eq. 1db-1de):
+    a Heaviside source leaves it growing like n, a source modulated at the Nyquist frequency drives it
+    resonantly (like n^2); one bilinear pass on the source removes it exactly (App. I)."""
+    nyq_u, mx_u = _app1(orc, 0, False, 10)
+    nyq_f, mx_f = _app1(orc, 1, False, 10)
+    assert nyq_u > 0.05 * mx_u                 # the Heaviside source excites the odd-even mode
+    assert nyq_f < 1e-14 * mx_f                # one 1-2-1 pass removes it
+    h20, _ = _app1(orc, 0, False, 20)
+    assert h20 / nyq_u == pytest.approx(2.0, rel=1e-6)
+    a10, _ = _app1(orc, 0, True, 10)
+    a20, _ = _app1(orc, 0, True, 20)
+    assert a20 / a10 == pytest.approx(4.0, rel=1e-6)
+    f20, m20 = _app1(orc, 1, True, 20)
+    assert f20 < 1e-14 * m20
+
+
+# ---------------------------------------------------------------------------
+# Sec. 3.1.2: laser through a plane in the boosted frame, E'0/E0 = omega'/omega = 1/((1+beta) gamma)
+@pytest.mark.slow
+@pytest.mark.parametrize("beta_s", [0.0, -0.3])
+def test_boosted_antenna_amplitude_and_frequency(orc, beta_s):
+    from oracle import boost
+    g = 4.0
+    lam = 0.8e-6
+    nz, nx = 640, 64
+    dzb = boost.boosted_dz(g, lam / 16)
+    w = {"nx": nx, "nz": nz, "dz_lab": lam / 16, "dx": 4e-6, "gamma_boost": g, "courant": 0.9,
+         "solver": W.SOLVERS["yee"], "theta": 0.0, "pml_cells": 8, "order": 3, "filter_J": 0,
+         "laser": {"lambda0": lam, "a0": 0.01, "w0": 1.0, "tau_fwhm": 10e-15, "t_peak": 20e-15,
+                   "x_center": 0.5 * nx * 4e-6, "z_antenna": 420 * dzb, "beta_s": beta_s}}
+    s = orc.Sim(w)
+    kp = 470
+    series = []
+    for _ in range(500):
+        s.step(1)
+        series.append(s.field(1)[nx // 2, kp])
+    series = np.array(series)
+    E0 = 0.01 * ME * C * (2 * np.pi * C / lam) / QE
+    Ep = E0 * boost.laser_amplitude_ratio(g)
+    assert np.abs(series).max() == pytest.approx(Ep, rel=0.04)
+    crossings = []
+    for j in range(5, len(series) - 6):
+        if np.abs(series[j - 5:j + 6]).max() > 0.3 * Ep and series[j] * series[j + 1] < 0:
+            crossings.append(j + series[j] / (series[j] - series[j + 1]))
+    assert len(crossings) > 6
+    period = 2 * np.mean(np.diff(crossings)) * s.dt
+    beta = math.sqrt(1 - 1 / g ** 2)
+    assert period == pytest.approx((1 + beta) * g * lam / C, rel=0.02)
+
+
+# ---------------------------------------------------------------------------
+# Sec. 2: printed stage estimates
+def test_stage_estimates_printed_values():
+    from oracle import boost
+    gold = json.load(open(os.path.join(GOLD, "stage_estimates.json")))
+    lam, xi, eta = gold["lambda_m"], gold["xi"], gold["eta"]
+    for st in gold["stages"]:
+        n = st["n_e_cm3"] * 1e6
+        assert boost.lambda_p(n) * 1e6 == pytest.approx(st["lambda_p_um"], rel=6e-3)
+        assert boost.gamma_wake(n, lam) == pytest.approx(st["gamma_w"], rel=5e-3)
+        assert xi * boost.dephasing_length(n, lam) == pytest.approx(st["L_m"], rel=1e-2)
+    gw = boost.gamma_wake(1e16 * 1e6, lam)
+    smax = boost.speedup_gamma_inf(gw, xi, eta)
+    assert 2.9e5 < smax < 3.3e5                         # "as large as 300,000"
+    # limits of Eq. Eq_scaling1d
+    gw = 132.0
+    assert boost.speedup_approx(2.0, gw, xi, eta) == pytest.approx((1 + math.sqrt(0.75)) ** 2 * 4, rel=2e-3)
+    assert boost.speedup_approx(1e7, gw, xi, eta) == pytest.approx(boost.speedup_gamma_inf(gw, xi, eta), rel=1e-3)
+    assert boost.speedup_approx(gw, gw, xi, eta) == pytest.approx(boost.speedup_wake_frame(gw, xi, eta), rel=0.05)
+    # the exact and approximate forms agree for L = xi L_d >> eta lambda_p
+    n = 1e17 * 1e6
+    L = xi * boost.dephasing_length(n, lam)
+    gw = boost.gamma_wake(n, lam)
+    for g in (5.0, 30.0, 100.0):
+        assert boost.speedup_exact(g, n, lam, L, eta) == pytest.approx(boost.speedup_approx(g, gw, xi, eta), rel=0.02)
+    # R_lab / R*_t reproduces S (Sec. 2)
+    b = boost.boosted(30.0, n, lam, L, eta)
+    assert boost.r_lab(n, lam, L, eta) / b["R"] == pytest.approx(boost.speedup_exact(30.0, n, lam, L, eta), rel=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# App. II: split-field PML with the enlarged stencil
+def _harris_run(orc, n, steps, solver, xi_exp, pml):
+    w = vacuum(n, n, solver, periodic=False, pml_cells=pml, pml_xi_exp=xi_exp, courant=0.99)
+    s = orc.Sim(w)
+    # Harris pulse (10 - 15 cos(2 pi c t/L) + 6 cos(4 pi c t/L) - cos(6 pi c t/L))/32, L = 50 dx (App. II)
+    ph = 2 * np.pi * C * s.dt * np.arange(steps) / (50 * s.dx)
+    prof = (10 - 15 * np.cos(ph) + 6 * np.cos(2 * ph) - np.cos(3 * ph)) / 32
+    prof[ph >= 2 * np.pi] = 0.0
+    src = np.zeros((n + 1, n + 1))
+    src[n // 2, n // 2] = 1.0
+    s.set_ext_current(1, src)
+    s.set_ext_profile(prof)
+    s.step(steps)
+    return s
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("solver", ["yee", "ck"])
+def test_pml_reflection_small(orc, solver):
+    n, big, steps, pml = 96, 288, 170, 8
+    ref = _harris_run(orc, big, steps, solver, 1, 0)
+    off = (big - n) // 2
+    er = ref.field(1)[off:off + n + 1, off:off + n + 1]
+    scale = np.abs(er).max()
+    refl = {}
+    for xe in (1, 0):
+        s = _harris_run(orc, n, steps, solver, xe, pml)
+        e = s.field(1)
+        inner = slice(pml + 4, n - pml - 4)
+        refl[xe] = np.abs(e[inner, inner] - er[inner, inner]).max() / scale
+    assert refl[1] < 0.03 and refl[0] < 0.03
+    assert refl[0] == pytest.approx(refl[1], rel=0.5)     # "both implementations gave nearly identical results"
+
+
+# ---------------------------------------------------------------------------
+# Sec. 3.1.1: beam through a plane reproduces the Lorentz transform of the worldlines
+def test_beam_plane_injection_matches_lorentz(orc):
+    g = 5.0
+    beta = math.sqrt(1 - 1 / g ** 2)
+    w = vacuum(16, 64, "yee", periodic=False, gamma_boost=g, dz_lab=0.05e-6, dx=1e-6)
+    s = orc.Sim(w)
+    gb = 20.0
+    vb = C * math.sqrt(1 - 1 / gb ** 2)
+    zl = np.array([0.0, 1e-6, 2.5e-6, 4e-6])
+    n = zl.size
+    ub = gb * vb
+    # the beam trails a lab plane at 100 um by ~100 um: it crosses it at boosted times t' > 0
+    s.set_beam(np.full(n, 8e-6), zl, np.zeros(n), np.zeros(n), np.full(n, ub), 0.0, 100e-6)
+    p = s.particles(2)
+    dzp = np.diff(p["z"])
+    assert dzp == pytest.approx(np.diff(zl) / (g * (1 - beta * vb / C)), rel=1e-12)
+    vzp = (vb - beta * C) / (1 - beta * vb / C)
+    s.step(60)
+    p = s.particles(2)
+    act = p["active"] & p["alive"]
+    assert act.any()
+    gp = np.sqrt(1 + (p["ux"] ** 2 + p["uy"] ** 2 + p["uz"] ** 2) / C ** 2)
+    assert (p["uz"] / gp)[act] == pytest.approx(vzp, rel=1e-12)
+    d = s.diag()
+    assert d["gamma_lab"] == pytest.approx(gb, rel=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Sec. 3.2: lab-frame stations
+def test_btd_lab_frame_identity(orc):
+    w = W.shrink(W.parity_2d(), 32, 96, gamma_boost=1.0, plasma=None)
+    w["plasma"] = None
+    w["laser"]["z_antenna"] = 30 * w["dz_lab"]
+    s = orc.Sim(w)
+    dz, dt = s.dz, s.dt
+    ks = np.arange(20, 60)
+    s.btd_set(ks * dz, np.full(ks.size, 37 * dt))
+    s.step(37)
+    ey37 = s.field(1).copy()
+    bx36 = s.field(3).copy()      # B^{36.5}
+    s.step(1)
+    bx37 = s.field(3).copy()      # B^{37.5}
+    out, done = s.btd_get()
+    assert done.all()
+    assert out[:, 1, :].T == pytest.approx(ey37[:, ks], abs=1e-9 * np.abs(ey37).max())
+    # B part at t = 37 dt = midpoint of B^{36.5}, B^{37.5}; Bx interpolated to z = k dz from (k +- 1/2)
+    bmid = 0.5 * (bx36 + bx37)
+    bz = 0.5 * (bmid[:, ks] + bmid[:, ks - 1])
+    assert out[:, 3, :].T == pytest.approx(bz, abs=1e-9 * np.abs(bmid).max())
+
+
+@pytest.mark.slow
+def test_btd_boosted_laser_seen_in_lab(orc):
+    """a boosted-frame laser recorded at a lab station has the lab amplitude E0 and the lab period"""
+    from oracle import boost
+    g = 3.0
+    beta = math.sqrt(1 - 1 / g ** 2)
+    lam = 0.8e-6
+    nz, nx = 560, 48
+    dzb = boost.boosted_dz(g, lam / 20)
+    w = {"nx": nx, "nz": nz, "dz_lab": lam / 20, "dx": 4e-6, "gamma_boost": g, "courant": 0.9,
+         "solver": W.SOLVERS["yee"], "theta": 0.0, "pml_cells": 8, "order": 3,
+         "laser": {"lambda0": lam, "a0": 0.01, "w0": 1.0, "tau_fwhm": 12e-15, "t_peak": 24e-15,
+                   "x_center": 0.5 * nx * 4e-6, "z_antenna": 60 * dzb, "beta_s": 0.0}}
+    s = orc.Sim(w)
+    # the pulse peak leaves the antenna at t'_pk and meets the lab station 150 cells further on
+    tpk = 24e-15 * (1 + beta) * g
+    zmeet = 60 * dzb + 150 * dzb
+    tmeet = tpk + 150 * dzb / C
+    zL = g * (zmeet + beta * C * tmeet)
+    tl0 = g * (tmeet + beta * zmeet / C)
+    T = lam / C
+    tL = tl0 + np.linspace(-10 * T, 10 * T, 801)
+    s.btd_set(np.full(tL.size, zL), tL)
+    tp_max = (g * (tL - beta * zL / C)).max()
+    s.step(int(tp_max / s.dt) + 3)
+    out, done = s.btd_get()
+    ok = done.all(axis=1)
+    assert ok.sum() > 700
+    ey = out[ok, 1, nx // 2]
+    E0 = 0.01 * ME * C * (2 * np.pi * C / lam) / QE
+    assert np.abs(ey).max() == pytest.approx(E0, rel=0.04)
+    t = tL[ok]
+    cr = []
+    for j in range(20, len(ey) - 21):
+        if np.abs(ey[j - 20:j + 21]).max() > 0.3 * E0 and ey[j] * ey[j + 1] < 0:
+            cr.append(t[j] + (t[j + 1] - t[j]) * ey[j] / (ey[j] - ey[j + 1]))
+    assert len(cr) > 6
+    assert 2 * np.mean(np.diff(cr)) == pytest.approx(T, rel=0.02)
