@@ -1,0 +1,304 @@
+"""Benchmark of the boosted-frame PIC step (one JSON line on rank 0).
+
+Workload: the 2D boosted-frame 0.1 GeV-class stage, 4096 (z) x 256 (x) cells,
+n0 = 1e19 cm^-3, 16 particles per cell, gamma_boost = 13, CK solver, 16-cell
+PML, Friedman theta = 0.1, 4 bilinear passes + compensation, cubic shapes,
+FP32 fields/momenta with FP64 positions (mixed precision). The box is full of
+plasma that keeps streaming in through the +z plane. A step is one full PIC
+step (Faraday/Friedman/PML, gather-field filter, gather/push/deposit,
+antenna, ion current, current filter + Ampere/PML, inflow, periodic sort).
+
+value: electron particle-steps per second of the whole job (all ranks),
+device-timed with CUDA events over exactly K steps after W warm-up steps.
+e2e: the same metric through the public API with host-side wall clock, each
+step followed by a device->host read of the step's diagnostics (pic_get_stats),
+including context creation and plasma loading.
+The particle arrays (~0.9 GB) exceed the 129 MB L2, so no L2 flush is needed.
+
+--impl reference times the FP64 CPU oracle (the plain restatement of the
+method used by the tests) on the host cores, on a bounded sample of the same
+workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+# algorithmic bytes per electron particle-step of the push kernel (mixed): read x,z (2x8),
+# u (3x4), w (4); write x,z (2x8), u (3x4)
+BYTES_PER_PARTICLE = {"mixed": 60, "fp64": 88}
+# algorithmic bytes per cell-step of the field kernels (mixed, with Friedman): see the design notes
+BYTES_PER_CELL = {"mixed": 168, "fp64": 336}
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(p))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def max_over_ranks(v: float, ws: int) -> float:
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(v: float, ws: int) -> float:
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier(ws: int):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ----------------------------------------------------------------------------
+def cpu_oracle_sample(w: dict, seconds: float = 15.0, max_steps: int = 40) -> dict:
+    """Time the FP64 oracle, as it stands, on a bounded sample of the workload: the same numerics on a
+    box of 512 (z) x 256 (x) cells (one eighth of the particles), a few steps."""
+    import oracle
+    from paper_1009_2727_gb300 import workloads as W
+    ws = W.shrink(w, w["nx"], 512)
+    ws["precision"] = "fp64"
+    t0 = time.perf_counter()
+    s = oracle.Sim(ws)
+    setup = time.perf_counter() - t0
+    n = len(s.particles(0)["x"])
+    steps = 0
+    t0 = time.perf_counter()
+    while steps < max_steps and (time.perf_counter() - t0) < seconds:
+        s.step(1)
+        steps += 1
+    dt = time.perf_counter() - t0
+    return {"value": n * steps / dt, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"{ws['name']}: {n} electrons (+ as many ions), {steps} steps, {dt:.1f} s "
+                      f"(setup {setup:.1f} s), single thread"}
+
+
+def run_reference(args, w):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1009_2727_gb300 import workloads as W
+    wsmp = W.shrink(w, w["nx"], 256)
+    wsmp["precision"] = "fp64"
+    s = oracle.Sim(wsmp)
+    n = len(s.particles(0)["x"])
+    for _ in range(args.warmup):
+        s.step(1)
+    t0 = time.perf_counter()
+    s.step(args.steps)
+    dt = time.perf_counter() - t0
+    v = n * args.steps / dt
+    line = {"metric": "particle-steps/s", "value": v, "unit": "particle-steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": w["name"] + " (bounded sample: 256 x 256 cells)", "grid": [w["nz"], w["nx"]],
+                       "ppc": 16, "precision": "fp64 oracle"},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": v, "unit": "particle-steps/s",
+                             "sample": f"{wsmp['name']}: {n} electrons, {args.steps} steps, {dt:.1f} s"},
+            "e2e": {"value": v, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=8)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--order", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+
+    from paper_1009_2727_gb300 import workloads as W
+    w = W.stage_2d()
+    w["order"] = args.order
+    w["precision"] = args.precision
+    if args.impl == "reference":
+        return run_reference(args, w)
+
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://")
+    else:
+        torch.cuda.set_device(0)
+    from paper_1009_2727_gb300.pic import Simulation
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_sample(w)
+
+    sim = Simulation(w, precision=args.precision)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 3)):
+        sim.step(1)
+    sim.sync()
+    n_e = sim.stats()["n_electrons"]
+    # per-kernel timing of the push kernel over the timed steps (events on the library's stream)
+    sim.timing(True, 0)
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    barrier(ws)
+    torch.cuda.synchronize()
+    l0 = sim.launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    sim.step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clocks = sampler.stop()
+    launches = sim.launches() - l0
+    ms = ev0.elapsed_time(ev1)
+    push_ms, push_n = sim.timing(False)
+    sim.sync()
+    n_e1 = sim.stats()["n_electrons"]
+    n_avg = 0.5 * (n_e + n_e1)
+    ms_max = max_over_ranks(ms, ws)
+    total_ps = sum_over_ranks(n_avg * args.steps, ws)
+    value = total_ps / (ms_max * 1e-3)
+    # roofline of the dominant kernel
+    peaks = measured_peaks()
+    peak = peaks.get("hbm_gbs", 6800.0)
+    bpp = BYTES_PER_PARTICLE[args.precision]
+    push_avg_ms = push_ms / max(push_n, 1)
+    achieved = n_avg * bpp / (push_avg_ms * 1e-3) / 1e9
+    roof = {"kernel": "k_push (gather + Boris + Esirkepov)", "bound": "hbm", "achieved": achieved, "peak": peak,
+            "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback",
+            "algorithmic_bytes_per_particle": bpp, "push_ms_per_step": push_avg_ms,
+            "share_of_step": push_avg_ms / (ms / args.steps)}
+    sim.close()
+    del sim
+
+    e2e = None
+    if not args.no_e2e:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s2 = Simulation(w, precision=args.precision)
+        k2 = max(args.steps // 2, 10)
+        for _ in range(k2):
+            s2.step(1)
+            st = s2.stats()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        n2 = st["n_electrons"]
+        import ctypes
+        from paper_1009_2727_gb300 import capi
+        h2d = (ctypes.sizeof(capi.PicConfig) + ctypes.sizeof(capi.PicPlasma) + ctypes.sizeof(capi.PicLaser)) / k2
+        e2e_v = sum_over_ranks(n2 * k2, ws) / max_over_ranks(wall, ws)
+        e2e = {"value": e2e_v, "unit": "particle-steps/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": ctypes.sizeof(capi.PicStats),
+               "note": f"wall clock of pic_init + pic_load_plasma + {k2} x (pic_step + pic_get_stats)"}
+        s2.close()
+
+    if rank == 0:
+        line = {
+            "metric": "particle-steps/s", "value": value, "unit": "particle-steps/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64pos" if args.precision == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": w["name"], "grid": [w["nz"], w["nx"]], "ppc": 16, "gamma_boost": w["gamma_boost"],
+                       "solver": "CK", "theta": w["theta"], "filter": "4 passes + compensation",
+                       "shape_order": args.order, "precision": args.precision, "electrons": int(n_avg),
+                       "cell_steps_per_s": w["nx"] * w["nz"] * args.steps * ws / (ms_max * 1e-3),
+                       "l2": "inputs larger than L2 (particle arrays ~0.9 GB)",
+                       "parallelism": f"{ws} independent replicas" if ws > 1 else "1 GPU"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,217 @@
+/*
+ * pic.h — C ABI of the GB300-native boosted-frame electromagnetic PIC step.
+ *
+ * The library advances a 2-1/2D (x,z; all six field components, three momentum
+ * components, fields independent of y) laser-wakefield simulation in a Lorentz
+ * boosted frame, following J.-L. Vay, C.G.R. Geddes, E. Cormier-Michel,
+ * D.P. Grote, "Modeling laser wakefield accelerators in a Lorentz boosted
+ * frame" (arXiv:1009.2727). Every step runs in the library's CUDA kernels
+ * (sm_103a) on one GPU and one caller-supplied CUDA stream.
+ *
+ * Conventions
+ *  - SI units. Lab-frame physical inputs (densities, laser, beam, stations) are
+ *    transformed by the library.
+ *  - Every function returns a pic_status (0 = PIC_OK, negative = error). Errors
+ *    are sticky per context; pic_last_error() returns a text description.
+ *  - Device memory is owned by the library and obtained only through the
+ *    allocator callback given to pic_init (or cudaMalloc when it is NULL); it is
+ *    released by pic_free. Caller buffers are never retained after a call.
+ *  - A context is used from one host thread at a time; all device work is
+ *    enqueued on the context's stream. pic_step is asynchronous.
+ *  - Grid arrays are (nx+1) x (nz+1), row-major with z fastest: element (i,k)
+ *    is at i*(nz+1)+k in every buffer this ABI copies out. Each component sits
+ *    at its own Yee position: Ex (i+1/2,k), Ey (i,k), Ez (i,k+1/2),
+ *    Bx (i,k+1/2), By (i+1/2,k+1/2), Bz (i+1/2,k); J like E.
+ */
+#ifndef PIC_H
+#define PIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PIC_API_VERSION 1
+
+typedef enum {
+  PIC_OK = 0,
+  PIC_EINVAL = -1,     /* bad argument or configuration */
+  PIC_ENOMEM = -2,     /* the allocator returned NULL */
+  PIC_ECFL = -3,       /* dt above the stability limit (Eq. cfl with the Friedman factor) */
+  PIC_EOVERFLOW = -4,  /* particle or lab-sample capacity exceeded */
+  PIC_ECUDA = -5,      /* a CUDA runtime call failed */
+  PIC_ETIMEOUT = -6,   /* a bounded device wait gave up */
+  PIC_ENAN = -7,       /* a non-finite value was detected */
+  PIC_ESTATE = -8      /* call out of order (e.g. pic_step before pic_load_plasma when required) */
+} pic_status;
+
+enum { PIC_FP64 = 0, PIC_MIXED = 1 };              /* pic_config.precision */
+enum { PIC_EX = 0, PIC_EY, PIC_EZ, PIC_BX, PIC_BY, PIC_BZ, PIC_JX, PIC_JY, PIC_JZ, PIC_RHO };
+enum { PIC_ELECTRONS = 0, PIC_BEAM = 2 };            /* pic_get_particles species */
+
+typedef struct pic_ctx pic_ctx;                      /* opaque, owned by the library */
+
+/* Device allocator: returns a device pointer of at least `bytes` usable on
+ * `stream`, or NULL. Called only inside pic_init/pic_load_plasma/
+ * pic_boosted_to_lab_diag (never inside pic_step unless particle capacity must
+ * grow). `user` is passed through. */
+typedef void* (*pic_alloc_fn)(size_t bytes, void* stream, void* user);
+typedef void (*pic_free_fn)(void* ptr, size_t bytes, void* stream, void* user);
+
+/* Numerical configuration. struct_size must be sizeof(pic_config) and version
+ * PIC_API_VERSION. */
+typedef struct {
+  uint32_t struct_size, version;
+  int32_t dim;            /* 2 (x,z). 3 is reserved. */
+  int32_t nx, nz;         /* cells along x and z; the PML occupies pml_cells on each side */
+  double dz_lab;          /* lab longitudinal cell [m]; the computational cell is (1+beta) gamma dz_lab (Sec. 5.1.1) */
+  double dx;              /* transverse cell [m] */
+  double gamma_boost;     /* Lorentz factor of the computational frame (1 = lab) */
+  double courant;         /* dt = courant * dt_CFL when dt <= 0 */
+  double dt;              /* explicit time step [s], or <= 0 */
+  double ck_alpha, ck_beta, ck_gamma; /* tunable-solver coefficients (Table CKcoefs), alpha+4beta+4gamma = 1 */
+  double theta;           /* Friedman damping 0..1 (Eq. Faraday_Friedman) */
+  int32_t pml_cells;      /* split-field PML thickness (App. II); 0 = PEC walls */
+  double pml_sigma_max;   /* sigma_m in units of c/delta (paper: 4) */
+  double pml_delta;       /* Delta in cells (paper: 5) */
+  double pml_power;       /* profile exponent n (paper: 2) */
+  int32_t pml_xi_exp;     /* 1: xi = exp(-sigma dt); 0: (1 - sigma dt/2)/(1 + sigma dt/2) */
+  int32_t filter_passes;  /* bilinear passes per axis (Eq. 3ptfilter, alpha = 1/2) */
+  int32_t filter_stride;  /* stride s (Eq. 3ptfilter_stride) */
+  int32_t filter_compensate; /* 1: one extra pass with alpha_c = n/2 + 1 */
+  int32_t filter_J;       /* filter the deposited current */
+  int32_t filter_gather;  /* filter the fields used by the gather */
+  int32_t shape_order;    /* 1 or 3 */
+  int32_t particle_guard; /* cells between the PML and the particle domain; < 0 = default */
+  int32_t precision;      /* PIC_FP64 or PIC_MIXED (FP32 fields/momenta, FP64 positions and PML coefficients) */
+  int32_t moving_window;  /* 1: the grid follows the wake at window_beta c */
+  double window_beta;
+  int32_t tile_x, tile_z; /* particle tile in cells; 0 = default */
+  int32_t sort_every;     /* steps between particle sorts; 0 = default */
+  int32_t reserved[8];
+} pic_config;
+
+/* Cold plasma fixed in the lab (Sec. 3.1.1), on a regular lattice, entering the
+ * boosted box through the plane at the +z edge of the particle domain. */
+typedef struct {
+  uint32_t struct_size, version;
+  double n0;              /* lab electron density of the plateau [m^-3] */
+  double z_start_lab;     /* lab position where the linear entrance ramp starts [m] */
+  double ramp_lab;        /* lab length of the linear ramp [m] */
+  double length_lab;      /* lab length of the plateau [m]; <= 0 = unbounded */
+  int32_t ppc_x, ppc_z;   /* macro-particles per cell along x and z */
+  int32_t ions;           /* 1: neutralising ions fixed in the lab, same lattice */
+  /* optional test beam (Sec. 3.1.1): beam_n lab-frame particles given at lab
+   * time beam_t_lab, injected through the lab plane z = beam_z_plane_lab.
+   * Host pointers, read during the call only; u = gamma v [m/s]. */
+  int64_t beam_n;
+  const double *beam_x, *beam_z, *beam_ux, *beam_uy, *beam_uz;
+  double beam_t_lab, beam_z_plane_lab;
+  int32_t reserved[8];
+} pic_plasma;
+
+/* Gaussian laser injected through a plane (Sec. 3.1.2). The lab waveform at the
+ * antenna is E0 exp(-(x-x_center)^2/w0^2) exp(-(s-t_peak)^2/(2 sigma_t^2))
+ * sin(omega (s - t_peak) + phase), sigma_t = tau_fwhm/(2 sqrt(ln 2)), y-polarised. */
+typedef struct {
+  uint32_t struct_size, version;
+  double lambda0, a0, w0, tau_fwhm, t_peak, x_center, phase;
+  double z_antenna;       /* antenna position in the computational frame at t' = 0 [m] */
+  double beta_s;          /* antenna-plane velocity / c in the computational frame */
+  int32_t reserved[8];
+} pic_laser;
+
+/* Back-transformed diagnostics (Sec. 3.2): n_rows lab samples (z_lab[r], t_lab[r])
+ * each covering all nx+1 transverse positions and the six lab-frame components. */
+typedef struct {
+  uint32_t struct_size, version;
+  int64_t n_rows;
+  const double* z_lab;    /* host pointers, copied during the call */
+  const double* t_lab;
+} pic_btd_req;
+
+typedef struct {
+  uint32_t struct_size, version;
+  void* data;             /* n_rows * 6 * (nx+1) values of the context precision's real type
+                             (double for PIC_FP64, float for PIC_MIXED), layout [row][component][i] */
+  int32_t* done;          /* n_rows * 2 flags: E part complete, B part complete (may be NULL) */
+  int32_t on_device;      /* 1: data/done are device pointers, 0: host pointers */
+  int64_t n_rows_filled;  /* out: rows with both parts complete */
+} pic_btd_out;
+
+typedef struct {
+  uint32_t struct_size, version;
+  int64_t step;
+  double t;               /* computational-frame time [s] */
+  double dt, dx, dz, gamma, beta;
+  int64_t n_electrons;    /* live plasma electrons */
+  int64_t n_beam_active;
+  double beam_gamma_lab;  /* mean lab-frame Lorentz factor of the active test beam */
+  double beam_spread;     /* rms(gamma_lab)/mean */
+  double field_energy;    /* per unit length along y [J/m] */
+  int32_t gx_lo, gx_hi, gz_lo, gz_hi; /* particle domain in cells */
+  int64_t sorts, overflow_chunks;     /* runtime counters */
+  double z0;              /* grid origin (moving window) [m] */
+} pic_stats;
+
+/* Create a context: validates cfg (coefficient normalisation, shape order,
+ * dt against the stability limit -> PIC_ECFL), derives the boosted cell and
+ * time step, allocates and zeroes the fields. cuda_stream is a cudaStream_t
+ * (NULL = the legacy default stream). On error *out is NULL. */
+int pic_init(const pic_config* cfg, pic_alloc_fn alloc, pic_free_fn free_fn, void* alloc_user,
+             void* cuda_stream, pic_ctx** out);
+
+/* Load the plasma (rows inside the particle domain at t' = 0) and, optionally,
+ * the test beam. May be called once, before the first pic_step. */
+int pic_load_plasma(pic_ctx* ctx, const pic_plasma* plasma);
+
+/* Register the laser antenna; its current is deposited inside every pic_step. */
+int pic_inject_laser(pic_ctx* ctx, const pic_laser* laser);
+
+/* Advance nsteps steps (asynchronous on the context stream). Returns a host-side
+ * status; device-side errors are reported by pic_sync. */
+int pic_step(pic_ctx* ctx, int nsteps);
+
+/* Wait for the stream and return the sticky device status. */
+int pic_sync(pic_ctx* ctx);
+
+/* Lab-frame stations/snapshots. With req != NULL and out == NULL: register the
+ * sample rows (replacing any previous request) and zero their buffers; they are
+ * filled while stepping. With req == NULL and out != NULL: copy the rows out
+ * (synchronises the stream). */
+int pic_boosted_to_lab_diag(pic_ctx* ctx, const pic_btd_req* req, pic_btd_out* out);
+
+/* Release all device memory and the context. NULL is accepted. */
+int pic_free(pic_ctx* ctx);
+
+/* Accessors (synchronise the stream). */
+/* Copy one grid component (PIC_EX..PIC_JZ, or PIC_RHO = charge density of
+ * electrons and ions at the current positions) into dst: (nx+1)*(nz+1) values
+ * of type double (always converted to double). on_device selects dst memory. */
+int pic_get_field(pic_ctx* ctx, int comp, double* dst, int on_device);
+/* Overwrite one of the six E/B components from a host array of doubles (tests). */
+int pic_set_field(pic_ctx* ctx, int comp, const double* src);
+/* Copy the live particles of one species to host arrays of capacity *count
+ * (doubles; id as uint32). On return *count is the number of live particles.
+ * flags (may be NULL): bit0 alive, bit1 active (test beam). Pass x == NULL to
+ * query the count only. */
+int pic_get_particles(pic_ctx* ctx, int species, double* x, double* z, double* ux, double* uy,
+                      double* uz, double* w, uint32_t* id, int32_t* flags, int64_t* count);
+int pic_get_stats(pic_ctx* ctx, pic_stats* out);
+const char* pic_last_error(pic_ctx* ctx);
+
+/* Number of kernel launches enqueued so far by this context (bench accounting). */
+int64_t pic_kernel_launches(pic_ctx* ctx);
+
+/* Record CUDA events around the launches of the named kernel class in the next
+ * pic_step calls and return their summed duration in ms (0 = particle kernel,
+ * 1 = field kernels). Used by the benchmark for the per-kernel roofline. */
+int pic_kernel_timing(pic_ctx* ctx, int enable, int which, double* ms_total, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PIC_H */

@@ -1,0 +1,489 @@
+// Auxiliary kernels of the boosted-frame PIC step:
+//  - the current of the ions fixed in the lab (PR-9): they move rigidly at
+//    -beta c on the electrons' lattice, so the sum of their Esirkepov currents
+//    factorises into a transverse lattice profile times a per-column prefix
+//    sum of the change of the deposited row density (exact, no particles);
+//  - the laser antenna current (Sec. 3.1.2, PR-13/14);
+//  - the test beam through a plane (Sec. 3.1.1): Lorentz transform and push;
+//  - back-transformed lab-frame samples (Sec. 3.2, PR-16);
+//  - charge density, reductions, moving-window shift, copies.
+#include "pic_common.cuh"
+
+namespace picgb {
+
+namespace {
+
+__device__ __forceinline__ double shape_val(int order, double s) {
+  double a = fabs(s);
+  if (order == 1) return a < 1.0 ? 1.0 - a : 0.0;
+  if (a < 1.0) return 2.0 / 3.0 - a * a + 0.5 * a * a * a;
+  if (a < 2.0) { double t = 2.0 - a; return t * t * t / 6.0; }
+  return 0.0;
+}
+
+__device__ double lab_density_d(const InjectP& ip, double zl) {
+  if (zl < ip.z_start_lab) return 0.0;
+  double r = zl - ip.z_start_lab;
+  if (ip.ramp_lab > 0.0 && r < ip.ramp_lab) return ip.n0 * r / ip.ramp_lab;
+  double pe = ip.ramp_lab + ip.length_lab;
+  if (ip.length_lab > 0.0 && r >= pe) return 0.0;
+  return ip.n0;
+}
+
+// R(k) = sum over live rows of w_m S(Z_m(t) - k) at two times; dR prefix-summed into C
+__global__ void k_ion_rows(GridP g, long long mlo, long long mhi, double t0, double t1, InjectP ip, int order,
+                           double* R0, double* R1) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k > g.nz) return;
+  const double reach = order == 3 ? 2.0 : 1.0;
+  const double wfac = g.dx * g.dz / (double)(ip.ppc_x * ip.ppc_z);
+  double acc[2] = {0.0, 0.0};
+  const double ts[2] = {t0, t1};
+  for (int q = 0; q < 2; q++) {
+    const double shift = ip.beta * kC * ts[q];
+    long long ma = (long long)floor(((k - reach) * g.dz + g.z0 + shift) / ip.h - 0.5) - 1;
+    long long mb = (long long)ceil(((k + reach) * g.dz + g.z0 + shift) / ip.h - 0.5) + 1;
+    if (ma < mlo) ma = mlo;
+    if (mb > mhi - 1) mb = mhi - 1;
+    for (long long m = ma; m <= mb; m++) {
+      const double zlat = (m + 0.5) * ip.h;
+      const double Zm = (zlat - shift - g.z0) / g.dz;
+      const double sv = shape_val(order, Zm - k);
+      if (sv == 0.0) continue;
+      const double w = ip.gamma * lab_density_d(ip, ip.gamma * zlat) * wfac;
+      acc[q] += w * sv;
+    }
+  }
+  R0[k] = acc[0];
+  R1[k] = acc[1];
+}
+
+__global__ void k_ion_prefix(int n, const double* R0, const double* R1, double* C) {
+  // single block: running prefix sum of R1 - R0 in chunks of blockDim
+  __shared__ double sh[1024];
+  __shared__ double carry;
+  if (threadIdx.x == 0) carry = 0.0;
+  __syncthreads();
+  for (int base = 0; base < n; base += blockDim.x) {
+    const int k = base + threadIdx.x;
+    double v = k < n ? R1[k] - R0[k] : 0.0;
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+      double y = threadIdx.x >= (unsigned)o ? sh[threadIdx.x - o] : 0.0;
+      __syncthreads();
+      sh[threadIdx.x] += y;
+      __syncthreads();
+    }
+    if (k < n) C[k] = carry + sh[threadIdx.x];
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry += sh[threadIdx.x];
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// antenna: J_y of one +/- pair per transverse node (Sec. 3.1.2)
+__device__ double emit_field(const LaserP& l, double x, double tp) {
+  const double om = 2.0 * kPi * kC / l.lambda0;
+  const double E0 = l.a0 * kMe * kC * om / kQe;
+  const double dop = (1.0 + l.beta) * l.gamma;
+  const double sl = (1.0 - l.beta_s) * tp / dop;
+  const double sig = l.tau / (2.0 * sqrt(log(2.0)));
+  const double dxr = x - l.x_center;
+  const double gv = E0 * exp(-dxr * dxr / (l.w0 * l.w0)) * exp(-(sl - l.t_peak) * (sl - l.t_peak) / (2.0 * sig * sig)) *
+                    sin(om * (sl - l.t_peak) + l.phase);
+  return (1.0 - l.beta_s) / dop * gv;
+}
+
+template <class T>
+__global__ void k_antenna(GridP g, T* Jy, LaserP l, int order, double t0, double t1) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > g.nx) return;
+  const double th = 0.5 * (t0 + t1);
+  const double za0 = l.z_antenna + l.beta_s * kC * t0;
+  const double za1 = l.z_antenna + l.beta_s * kC * t1;
+  const double zlo = g.z0 + g.gz_lo * g.dz, zhi = g.z0 + g.gz_hi * g.dz;
+  if (za0 < zlo || za0 >= zhi || za1 < zlo || za1 >= zhi) return;
+  const double Z0 = (za0 - g.z0) / g.dz, Z1 = (za1 - g.z0) / g.dz;
+  const int fz = (int)floor(Z0 < Z1 ? Z0 : Z1);
+  double kx = 0.0;
+  for (int ia = max(g.gx_lo, i - 2); ia <= min(g.gx_hi, i + 2); ia++) {
+    const double wx = shape_val(order, (double)(ia - i));
+    if (wx == 0.0) continue;
+    kx += -2.0 * kEps0 * kC * emit_field(l, ia * g.dx, th) * wx;
+  }
+  if (kx == 0.0) return;
+  for (int k = fz - 3; k <= fz + 4; k++) {
+    if (k < 0 || k > g.nz) continue;
+    const double wz = 0.5 * (shape_val(order, Z0 - k) + shape_val(order, Z1 - k));
+    if (wz == 0.0) continue;
+    Jy[(long)i * g.ld + k] += T(kx * wz / g.dz);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// test beam through a plane (Sec. 3.1.1, Eq. t*..Eq. zp)
+__global__ void k_beam_sum_vz(int n, const double* ux, const double* uy, const double* uz, double* acc) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const double gj = sqrt(1.0 + (ux[j] * ux[j] + uy[j] * uy[j] + uz[j] * uz[j]) / (kC * kC));
+  atomicAdd(&acc[0], uz[j] / gj);
+}
+
+template <class T>
+__global__ void k_beam_transform(Beam<T> b, const double* lx, const double* lz, const double* lux, const double* luy,
+                                 const double* luz, double t_lab, double z_plane, double gam, double be, double* acc) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= b.n) return;
+  const double betab = acc[0] / b.n / kC;
+  const double gj = sqrt(1.0 + (lux[j] * lux[j] + luy[j] * luy[j] + luz[j] * luz[j]) / (kC * kC));
+  const double vx = lux[j] / gj, vy = luy[j] / gj, vz = luz[j] / gj;
+  const double tcross = t_lab + (z_plane - lz[j]) / vz;
+  const double xs = lx[j] + vx * (tcross - t_lab);
+  const double tpc = gam * (tcross - be * z_plane / kC);
+  const double zpc = gam * (z_plane - be * kC * tcross);
+  const double den = 1.0 - be * betab;
+  const double vxp = vx / (gam * den), vyp = vy / (gam * den), vzp = (vz - be * kC) / den;
+  const double v2 = (vxp * vxp + vyp * vyp + vzp * vzp) / (kC * kC);
+  const double gp = 1.0 / sqrt(1.0 - v2);
+  b.x[j] = xs;
+  b.uxb[j] = T(gp * vxp); b.uyb[j] = T(gp * vyp); b.uzb[j] = T(gp * vzp);
+  b.ux[j] = b.uxb[j]; b.uy[j] = b.uyb[j]; b.uz[j] = b.uzb[j];
+  b.tc[j] = tpc;
+  b.zf0[j] = zpc;   // completed by k_beam_finish
+  b.flag[j] = 1;    // alive, frozen
+  atomicAdd(&acc[1], vzp);
+}
+
+template <class T>
+__global__ void k_beam_finish(Beam<T> b, double t_now, double* acc) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= b.n) return;
+  const double vbar = acc[1] / b.n;
+  const double zf = b.zf0[j] - vbar * b.tc[j];
+  b.zf0[j] = zf;
+  b.z[j] = zf + vbar * t_now;
+  if (j == 0) acc[2] = vbar;
+}
+
+template <class T>
+__device__ T gather_global(const T* F, const GridP& g, int order, double X, double Z, double sx, double sz) {
+  const int fx = (int)floor(X), fz = (int)floor(Z);
+  double acc = 0.0;
+  for (int i = fx - 3; i <= fx + 3; i++) {
+    const double wx = shape_val(order, X - (i + sx));
+    if (wx == 0.0 || i < 0 || i > g.nx) continue;
+    for (int k = fz - 3; k <= fz + 3; k++) {
+      const double wz = shape_val(order, Z - (k + sz));
+      if (wz == 0.0 || k < 0 || k > g.nz) continue;
+      acc += (double)F[(long)i * g.ld + k] * wx * wz;
+    }
+  }
+  return T(acc);
+}
+
+template <class T>
+__global__ void k_beam_push(GridP g, FieldPtrs<T> f, Beam<T> b, int order, double tn, double tn1, const double* acc) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= b.n) return;
+  int fl = b.flag[j];
+  if (!(fl & 1)) return;
+  if (!(fl & 2)) {
+    if (tn >= b.tc[j]) {
+      fl |= 2;
+      b.flag[j] = fl;
+      b.ux[j] = b.uxb[j]; b.uy[j] = b.uyb[j]; b.uz[j] = b.uzb[j];
+    } else {
+      b.z[j] = b.zf0[j] + acc[2] * tn1;
+      return;
+    }
+  }
+  const double x = b.x[j], z = b.z[j];
+  const double X = x / g.dx, Z = (z - g.z0) / g.dz;
+  const double E[3] = {(double)gather_global<T>(f.fE[0], g, order, X, Z, 0.5, 0.0),
+                       (double)gather_global<T>(f.fE[1], g, order, X, Z, 0.0, 0.0),
+                       (double)gather_global<T>(f.fE[2], g, order, X, Z, 0.0, 0.5)};
+  const double B[3] = {(double)gather_global<T>(f.fB[0], g, order, X, Z, 0.0, 0.5),
+                       (double)gather_global<T>(f.fB[1], g, order, X, Z, 0.5, 0.5),
+                       (double)gather_global<T>(f.fB[2], g, order, X, Z, 0.5, 0.0)};
+  const T k = T(-kQe * g.dt / (2.0 * kMe));
+  const T ic2 = T(1.0 / (kC * kC));
+  T ux = b.ux[j], uy = b.uy[j], uz = b.uz[j];
+  T umx = ux + k * T(E[0]), umy = uy + k * T(E[1]), umz = uz + k * T(E[2]);
+  T gm = sqrt(T(1) + (umx * umx + umy * umy + umz * umz) * ic2);
+  T tbx = k * T(B[0]) / gm, tby = k * T(B[1]) / gm, tbz = k * T(B[2]) / gm;
+  T t2 = tbx * tbx + tby * tby + tbz * tbz;
+  T sf = T(2) / (T(1) + t2);
+  T upx = umx + (umy * tbz - umz * tby), upy = umy + (umz * tbx - umx * tbz), upz = umz + (umx * tby - umy * tbx);
+  T plx = umx + sf * (upy * tbz - upz * tby), ply = umy + sf * (upz * tbx - upx * tbz),
+    plz = umz + sf * (upx * tby - upy * tbx);
+  ux = plx + k * T(E[0]); uy = ply + k * T(E[1]); uz = plz + k * T(E[2]);
+  const T g1 = sqrt(T(1) + (ux * ux + uy * uy + uz * uz) * ic2);
+  const double xn = x + g.dt * (double)(ux / g1);
+  const double zn = z + g.dt * (double)(uz / g1);
+  b.x[j] = xn; b.z[j] = zn; b.ux[j] = ux; b.uy[j] = uy; b.uz[j] = uz;
+  const double xlo = g.gx_lo * g.dx, xhi = g.gx_hi * g.dx;
+  const double zlo = g.z0 + g.gz_lo * g.dz, zhi = g.z0 + g.gz_hi * g.dz + g.dz;
+  if (xn < xlo || xn >= xhi || zn < zlo || zn >= zhi) b.flag[j] = fl & ~1;
+}
+
+// ---------------------------------------------------------------------------
+// back-transformed samples: rows [r0, r1) of the t'-sorted list
+template <class T>
+__device__ double interp_z(const T* F, const GridP& g, int i, double zp, double stz) {
+  const double Z = (zp - g.z0) / g.dz - stz;
+  const int k = (int)floor(Z);
+  const double fr = Z - k;
+  double a = 0.0, b = 0.0;
+  if (k >= 0 && k <= g.nz) a = (double)F[(long)i * g.ld + k];
+  if (k + 1 >= 0 && k + 1 <= g.nz) b = (double)F[(long)i * g.ld + k + 1];
+  return (1.0 - fr) * a + fr * b;
+}
+
+template <class T>
+__global__ void k_btd(GridP g, FieldPtrs<T> f, int which, int post, int r0, int r1, const int* order_idx,
+                      const double* tp, const double* zp, double ta, double gam, double be, T* out, int* done) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int rr = r0 + blockIdx.y;
+  if (rr >= r1 || i > g.nx) return;
+  const int row = order_idx[rr];
+  const double fr = (tp[rr] - ta) / g.dt;
+  const double wgt = post ? fr : 1.0 - fr;
+  const double z = zp[rr];
+  const int nxp = g.nx + 1;
+  T* o = out + (size_t)row * 6 * nxp;
+  if (which == 0) {
+    const double ex = interp_z<T>(f.E[0], g, i, z, 0.0);
+    const double ey = interp_z<T>(f.E[1], g, i, z, 0.0);
+    const double ez = interp_z<T>(f.E[2], g, i, z, 0.5);
+    o[0 * nxp + i] += T(wgt * gam * ex);
+    o[1 * nxp + i] += T(wgt * gam * ey);
+    o[2 * nxp + i] += T(wgt * ez);
+    o[3 * nxp + i] += T(wgt * (-gam * be * ey / kC));
+    o[4 * nxp + i] += T(wgt * (gam * be * ex / kC));
+  } else {
+    const double bx = interp_z<T>(f.B[0], g, i, z, 0.5);
+    const double by = interp_z<T>(f.B[1], g, i, z, 0.5);
+    const double bz = interp_z<T>(f.B[2], g, i, z, 0.0);
+    o[0 * nxp + i] += T(wgt * gam * be * kC * by);
+    o[1 * nxp + i] += T(wgt * (-gam * be * kC * bx));
+    o[3 * nxp + i] += T(wgt * gam * bx);
+    o[4 * nxp + i] += T(wgt * gam * by);
+    o[5 * nxp + i] += T(wgt * bz);
+  }
+  if (post && i == 0) done[2 * row + which] = 1;
+}
+
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void k_rho(GridP g, Particles<T> p, const Ctrl* ctrl, int order, double q, double* rho) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= ctrl->count) return;
+  const double w = (double)p.w[j];
+  if (w == 0.0) return;
+  const double X = p.x[j] / g.dx, Z = (p.z[j] - g.z0) / g.dz;
+  const int fx = (int)floor(X), fz = (int)floor(Z);
+  for (int i = fx - 2; i <= fx + 3; i++)
+    for (int k = fz - 2; k <= fz + 3; k++) {
+      const double s = shape_val(order, X - i) * shape_val(order, Z - k);
+      if (s != 0.0 && i >= 0 && i <= g.nx && k >= 0 && k <= g.nz)
+        atomicAdd(&rho[(long)i * (g.nz + 1) + k], q * w * s / (g.dx * g.dz));
+    }
+}
+
+__global__ void k_ion_rho(GridP g, const double* ion_x, const double* R, double coef, double* rho) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y;
+  if (k > g.nz) return;
+  rho[(long)i * (g.nz + 1) + k] += coef * ion_x[i] * R[k];
+}
+
+template <class T>
+__global__ void k_stats(GridP g, FieldPtrs<T> f, Particles<T> p, const Ctrl* ctrl, Beam<T> b, double gam, double be,
+                        double* out) {
+  // out: [0] n_e, [1] n_beam_active, [2] sum gamma_lab, [3] sum gamma_lab^2, [4] field energy
+  const long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long nthr = (long)gridDim.x * blockDim.x;
+  double ne = 0, na = 0, sg = 0, sg2 = 0, en = 0;
+  for (long j = tid; j < ctrl->count; j += nthr) ne += p.w[j] != T(0) ? 1.0 : 0.0;
+  for (long j = tid; j < b.n; j += nthr) {
+    if ((b.flag[j] & 3) != 3) continue;
+    const double ux = b.ux[j], uy = b.uy[j], uz = b.uz[j];
+    const double gp = sqrt(1.0 + (ux * ux + uy * uy + uz * uz) / (kC * kC));
+    const double gl = gam * (gp + be * uz / kC);
+    na += 1; sg += gl; sg2 += gl * gl;
+  }
+  const long ncell = (long)(g.nx + 1) * (g.nz + 1);
+  const double mu0 = 1.0 / (kEps0 * kC * kC);
+  for (long e = tid; e < ncell; e += nthr) {
+    const long i = e / (g.nz + 1), k = e - i * (g.nz + 1);
+    const long q = i * g.ld + k;
+    double e2 = 0, b2 = 0;
+    for (int c = 0; c < 3; c++) {
+      const double ev = f.E[c][q], bv = f.B[c][q];
+      e2 += ev * ev; b2 += bv * bv;
+    }
+    en += 0.5 * (kEps0 * e2 + b2 / mu0) * g.dx * g.dz;
+  }
+  atomicAdd(&out[0], ne); atomicAdd(&out[1], na); atomicAdd(&out[2], sg); atomicAdd(&out[3], sg2);
+  atomicAdd(&out[4], en);
+}
+
+template <class T>
+__global__ void k_shift_copy(GridP g, const T* src, T* dst, int sh) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y;
+  if (k > g.nz) return;
+  dst[(long)i * g.ld + k] = k + sh <= g.nz ? src[(long)i * g.ld + k + sh] : T(0);
+}
+
+__global__ void k_shift_chunks(Chunk* c, const Ctrl* ctrl, int sh) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= ctrl->nchunks) return;
+  if (c[j].ix0 <= c[j].ix1) { c[j].iz0 -= sh; c[j].iz1 -= sh; }
+}
+
+template <class T>
+__global__ void k_convert(const T* src, double* dst, GridP g) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y;
+  if (k > g.nz) return;
+  dst[(long)i * (g.nz + 1) + k] = (double)src[(long)i * g.ld + k];
+}
+
+template <class T>
+__global__ void k_convert_back(const double* src, T* dst, GridP g) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y;
+  if (k > g.nz) return;
+  dst[(long)i * g.ld + k] = T(src[(long)i * (g.nz + 1) + k]);
+}
+
+template <class T>
+__global__ void k_compact(Particles<T> p, const Ctrl* ctrl, double* out6, uint32_t* ido, int* nout, int cap_out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= ctrl->count) return;
+  if (p.w[j] == T(0)) return;
+  const int o = atomicAdd(nout, 1);
+  if (o >= cap_out) return;
+  out6[0 * (size_t)cap_out + o] = p.x[j];
+  out6[1 * (size_t)cap_out + o] = p.z[j];
+  out6[2 * (size_t)cap_out + o] = p.ux[j];
+  out6[3 * (size_t)cap_out + o] = p.uy[j];
+  out6[4 * (size_t)cap_out + o] = p.uz[j];
+  out6[5 * (size_t)cap_out + o] = p.w[j];
+  ido[o] = p.id[j];
+}
+
+}  // namespace
+
+void launch_ion_column(const GridP& g, long long mlo, long long mhi, double t0, double t1, const InjectP& ip,
+                       int order, double* R0, double* R1, double* C, cudaStream_t s) {
+  k_ion_rows<<<(g.nz + 1 + 255) / 256, 256, 0, s>>>(g, mlo, mhi, t0, t1, ip, order, R0, R1);
+  k_ion_prefix<<<1, 1024, 0, s>>>(g.nz + 1, R0, R1, C);
+}
+
+template <class T>
+void launch_antenna(const GridP& g, T* Jy, const LaserP& lp, int order, double t0, double t1, cudaStream_t s) {
+  k_antenna<T><<<(g.nx + 1 + 127) / 128, 128, 0, s>>>(g, Jy, lp, order, t0, t1);
+}
+
+template <class T>
+void launch_beam_init(Beam<T> b, const double* lx, const double* lz, const double* lux, const double* luy,
+                      const double* luz, double t_lab, double z_plane, double gamma, double beta, double t_now,
+                      double* scratch, cudaStream_t s) {
+  cudaMemsetAsync(scratch, 0, 4 * sizeof(double), s);
+  const int nb = (b.n + 255) / 256;
+  k_beam_sum_vz<<<nb, 256, 0, s>>>(b.n, lux, luy, luz, scratch);
+  k_beam_transform<T><<<nb, 256, 0, s>>>(b, lx, lz, lux, luy, luz, t_lab, z_plane, gamma, beta, scratch);
+  k_beam_finish<T><<<nb, 256, 0, s>>>(b, t_now, scratch);
+}
+
+template <class T>
+void launch_beam_push(const GridP& g, const FieldPtrs<T>& f, Beam<T> b, int order, double tn, double tn1, double,
+                      const double* scratch, cudaStream_t s) {
+  if (b.n <= 0) return;
+  k_beam_push<T><<<(b.n + 127) / 128, 128, 0, s>>>(g, f, b, order, tn, tn1, scratch);
+}
+
+template <class T>
+void launch_btd(const GridP& g, const FieldPtrs<T>& f, int which, int post, int r0, int r1, const int* order_idx,
+                const double* tp, const double* zp, double ta, double gamma, double beta, T* out, int* done,
+                cudaStream_t s) {
+  if (r1 <= r0) return;
+  dim3 grd((g.nx + 1 + 127) / 128, r1 - r0);
+  k_btd<T><<<grd, 128, 0, s>>>(g, f, which, post, r0, r1, order_idx, tp, zp, ta, gamma, beta, out, done);
+}
+
+template <class T>
+void launch_rho(const GridP& g, Particles<T> p, const Ctrl* ctrl, int cap, int order, double q, double* rho,
+                cudaStream_t s) {
+  if (cap <= 0) return;
+  k_rho<T><<<(cap + 255) / 256, 256, 0, s>>>(g, p, ctrl, order, q, rho);
+}
+
+void launch_ion_rho(const GridP& g, const double* ion_x, const double* R, double coef, double* rho, cudaStream_t s) {
+  dim3 grd((g.nz + 1 + 255) / 256, g.nx + 1);
+  k_ion_rho<<<grd, 256, 0, s>>>(g, ion_x, R, coef, rho);
+}
+
+template <class T>
+void launch_stats(const GridP& g, const FieldPtrs<T>& f, Particles<T> p, const Ctrl* ctrl, int cap, Beam<T> b,
+                  double gamma, double beta, double* out, cudaStream_t s) {
+  (void)cap;
+  cudaMemsetAsync(out, 0, 8 * sizeof(double), s);
+  k_stats<T><<<304, 256, 0, s>>>(g, f, p, ctrl, b, gamma, beta, out);
+}
+
+template <class T>
+void launch_shift(const GridP& g, T* arr, T* tmp, int sh, cudaStream_t s) {
+  dim3 grd((g.nz + 1 + 255) / 256, g.nx + 1);
+  k_shift_copy<T><<<grd, 256, 0, s>>>(g, arr, tmp, sh);
+  cudaMemcpyAsync(arr, tmp, sizeof(T) * (size_t)(g.nx + 1) * g.ld, cudaMemcpyDeviceToDevice, s);
+}
+
+void launch_shift_chunks(Chunk* chunks, Ctrl* ctrl, int sh, int chunk_cap, cudaStream_t s) {
+  k_shift_chunks<<<(chunk_cap + 255) / 256, 256, 0, s>>>(chunks, ctrl, sh);
+}
+
+template <class T>
+void launch_convert(const T* src, double* dst, const GridP& g, cudaStream_t s) {
+  dim3 grd((g.nz + 1 + 255) / 256, g.nx + 1);
+  k_convert<T><<<grd, 256, 0, s>>>(src, dst, g);
+}
+
+template <class T>
+void launch_convert_back(const double* src, T* dst, const GridP& g, cudaStream_t s) {
+  dim3 grd((g.nz + 1 + 255) / 256, g.nx + 1);
+  k_convert_back<T><<<grd, 256, 0, s>>>(src, dst, g);
+}
+
+template <class T>
+void launch_compact_copy(Particles<T> p, const Ctrl* ctrl, int cap, double* out6, uint32_t* id_out, int* nout,
+                         cudaStream_t s) {
+  cudaMemsetAsync(nout, 0, sizeof(int), s);
+  if (cap <= 0) return;
+  k_compact<T><<<(cap + 255) / 256, 256, 0, s>>>(p, ctrl, out6, id_out, nout, cap);
+}
+
+#define INST(T)                                                                                                   \
+  template void launch_antenna<T>(const GridP&, T*, const LaserP&, int, double, double, cudaStream_t);           \
+  template void launch_beam_init<T>(Beam<T>, const double*, const double*, const double*, const double*,          \
+                                    const double*, double, double, double, double, double, double*, cudaStream_t); \
+  template void launch_beam_push<T>(const GridP&, const FieldPtrs<T>&, Beam<T>, int, double, double, double,      \
+                                    const double*, cudaStream_t);                                                 \
+  template void launch_btd<T>(const GridP&, const FieldPtrs<T>&, int, int, int, int, const int*, const double*,   \
+                              const double*, double, double, double, T*, int*, cudaStream_t);                     \
+  template void launch_rho<T>(const GridP&, Particles<T>, const Ctrl*, int, int, double, double*, cudaStream_t);  \
+  template void launch_stats<T>(const GridP&, const FieldPtrs<T>&, Particles<T>, const Ctrl*, int, Beam<T>,       \
+                                double, double, double*, cudaStream_t);                                           \
+  template void launch_shift<T>(const GridP&, T*, T*, int, cudaStream_t);                                        \
+  template void launch_convert<T>(const T*, double*, const GridP&, cudaStream_t);                                \
+  template void launch_convert_back<T>(const double*, T*, const GridP&, cudaStream_t);                           \
+  template void launch_compact_copy<T>(Particles<T>, const Ctrl*, int, double*, uint32_t*, int*, cudaStream_t);
+INST(float)
+INST(double)
+#undef INST
+
+}  // namespace picgb

@@ -1,0 +1,889 @@
+// C ABI of the GB300 boosted-frame PIC library (include/pic.h): context,
+// device memory through the caller's allocator, host-side scheduling of the
+// per-step launches (all arithmetic of the step runs in the kernels of
+// pic_fields.cu, pic_particles.cu and pic_aux.cu).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/pic.h"
+#include "pic_common.cuh"
+
+namespace picgb {
+int push_occupancy(int order, bool dbl, int smem_nodes);
+}
+
+using namespace picgb;
+
+namespace {
+
+struct HostGeom {
+  double dx, dz, dt, gamma, beta, a2, b2, dt_cfl;
+  int guard, gx_lo, gx_hi, gz_lo, gz_hi, ld;
+};
+
+double lab_density_h(const pic_plasma& p, double zl) {
+  if (zl < p.z_start_lab) return 0.0;
+  double r = zl - p.z_start_lab;
+  if (p.ramp_lab > 0.0 && r < p.ramp_lab) return p.n0 * r / p.ramp_lab;
+  double pe = p.ramp_lab + p.length_lab;
+  if (p.length_lab > 0.0 && r >= pe) return 0.0;
+  return p.n0;
+}
+
+// 2D stability limit of the tunable solver restricted to d/dy = 0 (Eq. cfl), Friedman factor (Sec. 4.3)
+double cfl_2d(double a, double g, double dx, double dz, double theta) {
+  double kx = 1.0 / (dx * dx), kz = 1.0 / (dz * dz);
+  double mx = kx > kz ? kx : kz;
+  double t = (a - 4.0 * g) * (kx + kz);
+  if (t > mx) mx = t;
+  return 1.0 / std::sqrt(mx) / kC * std::sqrt((2.0 + theta) / (2.0 + 3.0 * theta));
+}
+
+}  // namespace
+
+struct SimBase {
+  virtual ~SimBase() {}
+};
+
+struct pic_ctx {
+  pic_config cfg;
+  HostGeom hg;
+  cudaStream_t stream = nullptr;
+  pic_alloc_fn alloc = nullptr;
+  pic_free_fn freef = nullptr;
+  void* user = nullptr;
+  struct A { void* p; size_t n; };
+  std::vector<A> allocs;
+  std::string err;
+  int status = PIC_OK;
+  int64_t launches = 0;
+  std::unique_ptr<SimBase> sim;
+
+  void* dalloc(size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~size_t(255);
+    void* p = nullptr;
+    if (alloc) p = alloc(bytes, (void*)stream, user);
+    else if (cudaMalloc(&p, bytes) != cudaSuccess) p = nullptr;
+    if (!p) return nullptr;
+    allocs.push_back({p, bytes});
+    cudaMemsetAsync(p, 0, bytes, stream);
+    return p;
+  }
+  void release_all() {
+    for (auto& a : allocs) {
+      if (freef) freef(a.p, a.n, (void*)stream, user);
+      else cudaFree(a.p);
+    }
+    allocs.clear();
+  }
+  int fail(int code, const std::string& m) {
+    if (status == PIC_OK) { status = code; err = m; }
+    return code;
+  }
+};
+
+namespace {
+
+template <class T>
+struct Sim : SimBase {
+  pic_ctx* c;
+  GridP g;
+  FieldPtrs<T> f{};
+  PmlTabs pt{};
+  FilterSpec fs{};
+  bool friedman = false, filt_gather = false, filt_J = false;
+  T* tmp = nullptr;
+  Ctrl* ctrl = nullptr;
+  Ctrl* hmirror = nullptr;     // pinned
+  // particles
+  Particles<T> P{}, P2{};
+  Chunk* chunks = nullptr;
+  int cap = 0, chunk_cap = 0, chunk_max = 4096, smem_nodes = 0, push_grid = 0;
+  SortBufs sb{};
+  int sort_every = 8;
+  long long count_ub = 0;
+  bool loaded = false;
+  pic_plasma pl{};
+  InjectP ip{};
+  long long row_next = 0, row_first = 0;
+  double zlo_prev = 0.0;
+  // ions
+  bool ions = false;
+  double *ion_x = nullptr, *ion_R0 = nullptr, *ion_R1 = nullptr, *ion_C = nullptr;
+  // laser
+  bool has_laser = false;
+  LaserP lp{};
+  // beam
+  Beam<T> beam{};
+  double* beam_scratch = nullptr;
+  // btd
+  int nrows = 0;
+  int* btd_idx = nullptr;
+  double *btd_tp = nullptr, *btd_zp = nullptr;
+  std::vector<double> h_tp;
+  T* btd_out = nullptr;
+  int* btd_done = nullptr;
+  // bookkeeping
+  long long step = 0;
+  long long shifts = 0;
+  int64_t sorts = 0;
+  double* stats_buf = nullptr;
+  double* stage = nullptr;    // (nx+1)*(nz+1) doubles
+  size_t stage_n = 0;
+  // timing
+  bool timing = false;
+  int timing_which = 0;
+  std::vector<cudaEvent_t> ev;
+  int64_t timed_launches = 0;
+
+  explicit Sim(pic_ctx* ctx) : c(ctx) {}
+  ~Sim() override {
+    for (auto e : ev) cudaEventDestroy(e);
+    if (hmirror) cudaFreeHost(hmirror);
+  }
+
+  template <class U>
+  U* al(size_t n) { return (U*)c->dalloc(n * sizeof(U)); }
+
+  int init() {
+    const pic_config& cf = c->cfg;
+    const HostGeom& h = c->hg;
+    g.nx = cf.nx; g.nz = cf.nz; g.ld = h.ld;
+    g.dx = h.dx; g.dz = h.dz; g.dt = h.dt; g.z0 = 0.0;
+    g.gx_lo = h.gx_lo; g.gx_hi = h.gx_hi; g.gz_lo = h.gz_lo; g.gz_hi = h.gz_hi;
+    g.pml = cf.pml_cells;
+    friedman = cf.theta != 0.0;
+    filt_gather = cf.filter_gather && cf.filter_passes + cf.filter_compensate > 0;
+    filt_J = cf.filter_J && cf.filter_passes + cf.filter_compensate > 0;
+    fs.passes = cf.filter_passes; fs.stride = cf.filter_stride; fs.compensate = cf.filter_compensate;
+    const size_t N = (size_t)(cf.nx + 1) * g.ld;
+    auto grid = [&]() { return al<T>(N); };
+    for (int q = 0; q < 3; q++) {
+      f.E[q] = grid(); f.Eo[q] = grid(); f.B[q] = grid(); f.J[q] = grid(); f.Jn[q] = grid();
+      f.Bavg[q] = grid();
+      if (friedman) { f.Eb[q] = grid(); f.Ebn[q] = grid(); }
+      if (filt_gather) { f.fE[q] = grid(); f.fB[q] = grid(); }
+      if (!f.E[q] || !f.Eo[q] || !f.B[q] || !f.J[q] || !f.Jn[q] || !f.Bavg[q]) return c->fail(PIC_ENOMEM, "field allocation failed");
+      if (friedman && (!f.Eb[q] || !f.Ebn[q])) return c->fail(PIC_ENOMEM, "field allocation failed");
+      if (filt_gather && (!f.fE[q] || !f.fB[q])) return c->fail(PIC_ENOMEM, "field allocation failed");
+    }
+    if (cf.pml_cells > 0) {
+      f.Byx = grid(); f.Byz = grid(); f.Eyx = grid(); f.Eyz = grid();
+      if (!f.Byx || !f.Byz || !f.Eyx || !f.Eyz) return c->fail(PIC_ENOMEM, "PML allocation failed");
+    }
+    tmp = grid();
+    if (!tmp) return c->fail(PIC_ENOMEM, "allocation failed");
+    // PML tables (App. II, PR-18)
+    std::vector<double> hx(6 * (cf.nx + 1)), hz(6 * (cf.nz + 1));
+    auto sigma = [&](double pos, int n, double dcell) {
+      int L = cf.pml_cells;
+      if (L <= 0) return 0.0;
+      double d = 0.0;
+      if (pos < L) d = L - pos;
+      if (pos > n - L) d = pos - (n - L);
+      if (d <= 0.0) return 0.0;
+      return cf.pml_sigma_max * kC / dcell * std::pow(d / cf.pml_delta, cf.pml_power);
+    };
+    auto xi = [&](double s) {
+      if (cf.pml_xi_exp) return std::exp(-s * h.dt);
+      return (1.0 - 0.5 * s * h.dt) / (1.0 + 0.5 * s * h.dt);
+    };
+    auto coef = [&](double s) { return s <= 0.0 ? h.dt : (1.0 - xi(s)) / s; };
+    auto fill = [&](std::vector<double>& v, int n, double dcell) {
+      for (int i = 0; i <= n; i++) {
+        double si = sigma(i, n, dcell), sh = sigma(i + 0.5, n, dcell);
+        v[0 * (n + 1) + i] = si; v[1 * (n + 1) + i] = sh;
+        v[2 * (n + 1) + i] = xi(si); v[3 * (n + 1) + i] = xi(sh);
+        v[4 * (n + 1) + i] = coef(si); v[5 * (n + 1) + i] = coef(sh);
+      }
+    };
+    fill(hx, cf.nx, h.dx);
+    fill(hz, cf.nz, h.dz);
+    double* dx_t = al<double>(hx.size());
+    double* dz_t = al<double>(hz.size());
+    if (!dx_t || !dz_t) return c->fail(PIC_ENOMEM, "allocation failed");
+    cudaMemcpyAsync(dx_t, hx.data(), hx.size() * 8, cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(dz_t, hz.data(), hz.size() * 8, cudaMemcpyHostToDevice, c->stream);
+    const int nx1 = cf.nx + 1, nz1 = cf.nz + 1;
+    pt.sx_i = dx_t; pt.sx_h = dx_t + nx1; pt.xx_i = dx_t + 2 * nx1; pt.xx_h = dx_t + 3 * nx1;
+    pt.cx_i = dx_t + 4 * nx1; pt.cx_h = dx_t + 5 * nx1;
+    pt.sz_i = dz_t; pt.sz_h = dz_t + nz1; pt.xz_i = dz_t + 2 * nz1; pt.xz_h = dz_t + 3 * nz1;
+    pt.cz_i = dz_t + 4 * nz1; pt.cz_h = dz_t + 5 * nz1;
+    ctrl = al<Ctrl>(1);
+    stats_buf = al<double>(8);
+    stage_n = (size_t)nx1 * nz1;
+    stage = al<double>(stage_n);
+    if (!ctrl || !stats_buf || !stage) return c->fail(PIC_ENOMEM, "allocation failed");
+    if (cudaMallocHost(&hmirror, sizeof(Ctrl)) != cudaSuccess) hmirror = nullptr;
+    // particle tiles
+    int tx = cf.tile_x > 0 ? cf.tile_x : 16, tz = cf.tile_z > 0 ? cf.tile_z : 16;
+    sb.tx = tx; sb.tz = tz;
+    sb.ntx = (cf.nx + tx - 1) / tx; sb.ntz = (cf.nz + tz - 1) / tz;
+    sb.R = 32;
+    sort_every = cf.sort_every > 0 ? cf.sort_every : 8;
+    const int margin = 10;
+    smem_nodes = (tx + 6 + margin) * (tz + 6 + margin);
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    push_grid = nsm * push_occupancy(cf.shape_order, sizeof(T) == 8, smem_nodes);
+    return cudaGetLastError() == cudaSuccess ? PIC_OK : c->fail(PIC_ECUDA, "CUDA error during init");
+  }
+
+  void set_ptrs_for_step() {
+    if (!filt_gather) {
+      for (int q = 0; q < 3; q++) { f.fE[q] = f.E[q]; f.fB[q] = f.Bavg[q]; }
+    }
+  }
+
+  double time_of(long long n) const { return (double)n * g.dt; }
+  double zlo() const { return g.z0 + g.gz_lo * g.dz; }
+  double zhi() const { return g.z0 + g.gz_hi * g.dz; }
+
+  long long rows_inside(double t) const {
+    double y = (zhi() + c->hg.beta * kC * t) / ip.h - 0.5;
+    return (long long)std::ceil(y);
+  }
+  long long rows_from(double t) const {
+    return (long long)std::ceil((zlo() + c->hg.beta * kC * t) / ip.h - 0.5);
+  }
+  bool row_has_density(long long m) const {
+    double zlat = (m + 0.5) * ip.h;
+    return c->hg.gamma * lab_density_h(pl, c->hg.gamma * zlat) > 0.0;
+  }
+
+  int load_plasma(const pic_plasma* p) {
+    if (loaded) return c->fail(PIC_ESTATE, "plasma already loaded");
+    pl = *p;
+    const pic_config& cf = c->cfg;
+    const HostGeom& h = c->hg;
+    if (pl.ppc_x < 1 || pl.ppc_z < 1) return c->fail(PIC_EINVAL, "ppc must be >= 1");
+    ip.h = h.dz / pl.ppc_z;
+    ip.gamma = h.gamma; ip.beta = h.beta;
+    ip.n0 = pl.n0; ip.z_start_lab = pl.z_start_lab; ip.ramp_lab = pl.ramp_lab; ip.length_lab = pl.length_lab;
+    ip.ppc_x = pl.ppc_x; ip.ppc_z = pl.ppc_z;
+    ip.nxl = (g.gx_hi - g.gx_lo) * pl.ppc_x;
+    ip.xblock = 32;
+    ions = pl.ions != 0 && pl.n0 > 0.0;
+    // capacity: the particle domain full of plasma plus injection headroom
+    const double rows_per_step = h.beta * kC * h.dt / ip.h + 2.0;
+    const long long full = (long long)(g.gz_hi - g.gz_lo + 2) * pl.ppc_z * (long long)ip.nxl;
+    const long long head = (long long)(rows_per_step + 2) * ip.nxl * (sort_every + 4);
+    long long want = (long long)(full * 1.05) + head + 4096;
+    if (cf.moving_window) want += (long long)((cf.window_beta * kC * h.dt / ip.h + 2) * ip.nxl * (sort_every + 4));
+    if (pl.n0 <= 0.0) want = 4096;
+    if (want > 2000000000LL) return c->fail(PIC_EOVERFLOW, "particle capacity above 2^31");
+    cap = (int)want;
+    Particles<T>* both[2] = {&P, &P2};
+    for (Particles<T>* q : both) {
+      q->x = al<double>(cap); q->z = al<double>(cap);
+      q->ux = al<T>(cap); q->uy = al<T>(cap); q->uz = al<T>(cap); q->w = al<T>(cap);
+      q->id = al<uint32_t>(cap);
+      if (!q->x || !q->z || !q->ux || !q->uy || !q->uz || !q->w || !q->id) return c->fail(PIC_ENOMEM, "particle allocation failed");
+    }
+    const int ntiles = sb.ntx * sb.ntz;
+    const int inj_chunks = ((g.gx_hi - g.gx_lo + ip.xblock - 1) / ip.xblock) * 4;
+    chunk_cap = 2 * ntiles + cap / chunk_max + inj_chunks * (sort_every + 4) + 4096;
+    chunks = al<Chunk>(chunk_cap);
+    const int nbins = ntiles * sb.R;
+    sb.cell_cnt = al<int>((size_t)cf.nx * cf.nz);
+    sb.bin_cnt = al<int>(nbins + 1);
+    sb.bin_start = al<int>(nbins + 1);
+    sb.key = al<int>(cap);
+    sb.slot = al<int>(cap);
+    sb.scan_tmp = al<int>(1024 + (nbins + 1023) / 1024);
+    if (!chunks || !sb.cell_cnt || !sb.bin_cnt || !sb.bin_start || !sb.key || !sb.slot || !sb.scan_tmp)
+      return c->fail(PIC_ENOMEM, "sort allocation failed");
+    if (nbins > 1024 * 1024) return c->fail(PIC_EINVAL, "too many sort bins; enlarge tile_x/tile_z");
+    if (ions) {
+      ion_x = al<double>(cf.nx + 1);
+      ion_R0 = al<double>(cf.nz + 1); ion_R1 = al<double>(cf.nz + 1); ion_C = al<double>(cf.nz + 1);
+      if (!ion_x || !ion_R0 || !ion_R1 || !ion_C) return c->fail(PIC_ENOMEM, "allocation failed");
+      // transverse lattice profile sum_a S(X_a - i)
+      std::vector<double> xp(cf.nx + 1, 0.0);
+      for (int a = 0; a < ip.nxl; a++) {
+        double X = ((g.gx_lo + (a + 0.5) / pl.ppc_x) * g.dx) / g.dx;
+        int fx = (int)std::floor(X);
+        for (int i = fx - 2; i <= fx + 3; i++) {
+          if (i < 0 || i > cf.nx) continue;
+          double s = std::fabs(X - i), v;
+          if (cf.shape_order == 1) v = s < 1.0 ? 1.0 - s : 0.0;
+          else if (s < 1.0) v = 2.0 / 3.0 - s * s + 0.5 * s * s * s;
+          else if (s < 2.0) { double t = 2.0 - s; v = t * t * t / 6.0; }
+          else v = 0.0;
+          xp[i] += v;
+        }
+      }
+      cudaMemcpyAsync(ion_x, xp.data(), xp.size() * 8, cudaMemcpyHostToDevice, c->stream);
+    }
+    // initial rows (PR-12)
+    const double t = time_of(step);
+    long long m_end = rows_inside(t);
+    long long m_beg = rows_from(t);
+    row_first = m_beg;
+    row_next = m_end;
+    zlo_prev = zlo();
+    if (pl.n0 > 0.0) {
+      long long a = m_beg, b = m_end;
+      while (a < b && !row_has_density(a)) a++;
+      while (b > a && !row_has_density(b - 1)) b--;
+      if (b > a) {
+        ip.m_beg = a; ip.m_end = b; ip.t = t; ip.rblock = 8;
+        if ((b - a) * (long long)ip.nxl > cap) return c->fail(PIC_EOVERFLOW, "initial plasma exceeds capacity");
+        launch_inject<T>(g, P, chunks, ctrl, ip, cap, chunk_cap, c->stream);
+        c->launches += 2;
+        count_ub = (b - a) * (long long)ip.nxl;
+        do_sort();
+      }
+    }
+    // test beam
+    if (p->beam_n > 0) {
+      if (!p->beam_x || !p->beam_z || !p->beam_ux || !p->beam_uy || !p->beam_uz) return c->fail(PIC_EINVAL, "beam arrays missing");
+      const int n = (int)p->beam_n;
+      beam.n = n;
+      beam.x = al<double>(n); beam.z = al<double>(n); beam.ux = al<T>(n); beam.uy = al<T>(n); beam.uz = al<T>(n);
+      beam.tc = al<double>(n); beam.zf0 = al<double>(n); beam.uxb = al<T>(n); beam.uyb = al<T>(n); beam.uzb = al<T>(n);
+      beam.flag = al<int>(n);
+      beam_scratch = al<double>(4);
+      double* lab = al<double>(5 * (size_t)n);
+      if (!beam.x || !beam.flag || !lab || !beam_scratch) return c->fail(PIC_ENOMEM, "beam allocation failed");
+      const double* srcs[5] = {p->beam_x, p->beam_z, p->beam_ux, p->beam_uy, p->beam_uz};
+      for (int q = 0; q < 5; q++) cudaMemcpyAsync(lab + (size_t)q * n, srcs[q], 8 * (size_t)n, cudaMemcpyHostToDevice, c->stream);
+      cudaStreamSynchronize(c->stream);   // host arrays are only valid during the call
+      launch_beam_init<T>(beam, lab, lab + n, lab + 2 * (size_t)n, lab + 3 * (size_t)n, lab + 4 * (size_t)n, p->beam_t_lab,
+                          p->beam_z_plane_lab, h.gamma, h.beta, time_of(step), beam_scratch, c->stream);
+      c->launches += 3;
+    }
+    loaded = true;
+    return cudaGetLastError() == cudaSuccess ? PIC_OK : c->fail(PIC_ECUDA, "CUDA error in load_plasma");
+  }
+
+  void do_sort() {
+    launch_sort<T>(g, P, P2, sb, chunks, ctrl, cap, chunk_max, chunk_cap, c->stream);
+    c->launches += 8;
+    std::swap(P, P2);
+    sorts++;
+    if (hmirror) cudaMemcpyAsync(&hmirror->count, &ctrl->count, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  }
+
+  int set_laser(const pic_laser* l) {
+    lp.lambda0 = l->lambda0; lp.a0 = l->a0; lp.w0 = l->w0; lp.tau = l->tau_fwhm; lp.t_peak = l->t_peak;
+    lp.x_center = l->x_center; lp.phase = l->phase; lp.z_antenna = l->z_antenna; lp.beta_s = l->beta_s;
+    lp.gamma = c->hg.gamma; lp.beta = c->hg.beta;
+    if (!(l->lambda0 > 0) || !(l->w0 > 0) || !(l->tau_fwhm > 0)) return c->fail(PIC_EINVAL, "laser lambda0, w0, tau must be > 0");
+    has_laser = true;
+    return PIC_OK;
+  }
+
+  void btd_range(double ta, double tb, int& r0, int& r1) const {
+    r0 = (int)(std::lower_bound(h_tp.begin(), h_tp.end(), ta) - h_tp.begin());
+    r1 = (int)(std::lower_bound(h_tp.begin(), h_tp.end(), tb) - h_tp.begin());
+  }
+
+  void btd(int post) {
+    if (nrows == 0) return;
+    const double tn = time_of(step);
+    int r0, r1;
+    btd_range(tn, time_of(step + 1), r0, r1);
+    if (r1 > r0) {
+      launch_btd<T>(g, f, 0, post, r0, r1, btd_idx, btd_tp, btd_zp, tn, c->hg.gamma, c->hg.beta, btd_out, btd_done, c->stream);
+      c->launches++;
+    }
+    const double ta = tn - 0.5 * g.dt;
+    btd_range(ta, ta + g.dt, r0, r1);
+    if (r1 > r0) {
+      launch_btd<T>(g, f, 1, post, r0, r1, btd_idx, btd_tp, btd_zp, ta, c->hg.gamma, c->hg.beta, btd_out, btd_done, c->stream);
+      c->launches++;
+    }
+  }
+
+  void window_shift() {
+    const pic_config& cf = c->cfg;
+    if (!cf.moving_window) return;
+    const double t = time_of(step);
+    long long want = (long long)std::floor(cf.window_beta * kC * t / g.dz);
+    long long sh = want - shifts;
+    if (sh <= 0) return;
+    for (int q = 0; q < 3; q++) {
+      launch_shift<T>(g, f.E[q], tmp, (int)sh, c->stream);
+      launch_shift<T>(g, f.Eo[q], tmp, (int)sh, c->stream);
+      launch_shift<T>(g, f.B[q], tmp, (int)sh, c->stream);
+      if (friedman) launch_shift<T>(g, f.Eb[q], tmp, (int)sh, c->stream);
+      c->launches += friedman ? 4 : 3;
+    }
+    if (cf.pml_cells > 0) {
+      T* arrs[4] = {f.Byx, f.Byz, f.Eyx, f.Eyz};
+      for (int q = 0; q < 4; q++) { launch_shift<T>(g, arrs[q], tmp, (int)sh, c->stream); c->launches++; }
+    }
+    if (loaded && chunks) { launch_shift_chunks(chunks, ctrl, (int)sh, chunk_cap, c->stream); c->launches++; }
+    shifts = want;
+    g.z0 = (double)want * g.dz;
+  }
+
+  void refresh_count_bound(long long add) {
+    if (count_ub + add <= cap) return;
+    // read the device count after a synchronisation; compact if needed
+    cudaStreamSynchronize(c->stream);
+    Ctrl hc;
+    cudaMemcpy(&hc, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost);
+    count_ub = hc.count;
+    if (count_ub + add > cap) {
+      do_sort();
+      cudaStreamSynchronize(c->stream);
+      cudaMemcpy(&hc, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost);
+      count_ub = hc.count;
+    }
+  }
+
+  int one_step() {
+    const pic_config& cf = c->cfg;
+    const HostGeom& h = c->hg;
+    const double tn = time_of(step), tn1 = time_of(step + 1);
+    window_shift();
+    set_ptrs_for_step();
+    btd(0);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto tstart = [&](int which) {
+      if (timing && timing_which == which) {
+        cudaEventCreate(&e0); cudaEventCreate(&e1);
+        cudaEventRecord(e0, c->stream);
+      }
+    };
+    auto tstop = [&](int which) {
+      if (timing && timing_which == which && e0) {
+        cudaEventRecord(e1, c->stream);
+        ev.push_back(e0); ev.push_back(e1);
+        e0 = e1 = nullptr;
+        timed_launches++;
+      }
+    };
+    // 1. Faraday + Friedman + PML-B (B^{n-1/2} -> B^{n+1/2}, Bavg)
+    tstart(1);
+    launch_faraday<T>(g, f, pt, h.a2, h.b2, cf.theta, friedman, c->stream);
+    // 2. gather copies
+    launch_filter_fields<T>(g, f, fs, filt_gather, c->stream);
+    tstop(1);
+    c->launches += 1 + (filt_gather ? 1 : 0);
+    // 3. particles
+    if (loaded && cap > 0) {
+      tstart(0);
+      launch_push<T>(g, f, P, chunks, ctrl, cf.shape_order, push_grid, smem_nodes, -kQe, kMe, c->stream);
+      tstop(0);
+      c->launches++;
+    }
+    if (beam.n > 0) {
+      launch_beam_push<T>(g, f, beam, cf.shape_order, tn, tn1, 0.0, beam_scratch, c->stream);
+      c->launches++;
+    }
+    // 4. antenna
+    if (has_laser) {
+      launch_antenna<T>(g, f.J[1], lp, cf.shape_order, tn, tn1, c->stream);
+      c->launches++;
+    }
+    // 5. ion column current
+    double ion_coef = 0.0;
+    if (ions && loaded) {
+      long long mlo = std::max(row_first, (long long)std::ceil((zlo_prev + h.beta * kC * tn) / ip.h - 0.5));
+      if (step == 0) mlo = row_first;
+      launch_ion_column(g, mlo, row_next, tn, tn1, ip, cf.shape_order, ion_R0, ion_R1, ion_C, c->stream);
+      c->launches += 2;
+      ion_coef = -kQe / (g.dx * g.dt);
+    }
+    // 6-7. current filter + Ampere + PML-E
+    tstart(1);
+    launch_ampere<T>(g, f, pt, fs, filt_J, (ions && loaded) ? ion_x : nullptr, ion_C, ion_coef, c->stream);
+    tstop(1);
+    c->launches++;
+    for (int q = 0; q < 3; q++) {
+      std::swap(f.E[q], f.Eo[q]);
+      std::swap(f.J[q], f.Jn[q]);
+      if (friedman) std::swap(f.Eb[q], f.Ebn[q]);
+    }
+    set_ptrs_for_step();
+    btd(1);
+    zlo_prev = zlo();
+    // 8. plasma rows entering through z_hi
+    if (loaded && pl.n0 > 0.0) {
+      long long m_end = rows_inside(tn1);
+      long long a = row_next, b = m_end;
+      if (b > row_next) row_next = b;
+      while (a < b && !row_has_density(a)) a++;
+      while (b > a && !row_has_density(b - 1)) b--;
+      if (b > a) {
+        long long add = (b - a) * (long long)ip.nxl;
+        refresh_count_bound(add);
+        if (count_ub + add > cap) return c->fail(PIC_EOVERFLOW, "particle capacity exceeded");
+        ip.m_beg = a; ip.m_end = b; ip.t = tn1; ip.rblock = 4;
+        launch_inject<T>(g, P, chunks, ctrl, ip, cap, chunk_cap, c->stream);
+        c->launches += 2;
+        count_ub += add;
+      }
+    }
+    step++;
+    if (loaded && cap > 0 && step % sort_every == 0) do_sort();
+    return PIC_OK;
+  }
+
+  int run(int n) {
+    for (int i = 0; i < n; i++) {
+      int r = one_step();
+      if (r != PIC_OK) return r;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return c->fail(PIC_ECUDA, std::string("CUDA error in pic_step: ") + cudaGetErrorString(e));
+    return PIC_OK;
+  }
+
+  int btd_set(const pic_btd_req* r) {
+    const int n = (int)r->n_rows;
+    if (n <= 0 || !r->z_lab || !r->t_lab) return c->fail(PIC_EINVAL, "empty lab-sample request");
+    const double ga = c->hg.gamma, be = c->hg.beta;
+    std::vector<double> tp(n), zp(n);
+    std::vector<int> idx(n);
+    for (int i = 0; i < n; i++) {
+      tp[i] = ga * (r->t_lab[i] - be * r->z_lab[i] / kC);
+      zp[i] = ga * (r->z_lab[i] - be * kC * r->t_lab[i]);
+      idx[i] = i;
+    }
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return tp[a] < tp[b]; });
+    std::vector<double> stp(n), szp(n);
+    for (int i = 0; i < n; i++) { stp[i] = tp[idx[i]]; szp[i] = zp[idx[i]]; }
+    nrows = n;
+    h_tp = stp;
+    btd_idx = al<int>(n); btd_tp = al<double>(n); btd_zp = al<double>(n);
+    btd_out = al<T>((size_t)n * 6 * (g.nx + 1));
+    btd_done = al<int>(2 * (size_t)n);
+    if (!btd_idx || !btd_tp || !btd_zp || !btd_out || !btd_done) return c->fail(PIC_ENOMEM, "lab-sample allocation failed");
+    cudaMemcpyAsync(btd_idx, idx.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(btd_tp, stp.data(), 8 * (size_t)n, cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(btd_zp, szp.data(), 8 * (size_t)n, cudaMemcpyHostToDevice, c->stream);
+    cudaStreamSynchronize(c->stream);
+    return PIC_OK;
+  }
+
+  int btd_get(pic_btd_out* o) {
+    if (nrows == 0) return c->fail(PIC_ESTATE, "no lab-sample request registered");
+    const size_t n = (size_t)nrows * 6 * (g.nx + 1);
+    cudaStreamSynchronize(c->stream);
+    cudaMemcpyKind k = o->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (o->data) cudaMemcpy(o->data, btd_out, n * sizeof(T), k);
+    std::vector<int> d(2 * (size_t)nrows);
+    cudaMemcpy(d.data(), btd_done, d.size() * 4, cudaMemcpyDeviceToHost);
+    if (o->done) cudaMemcpy(o->done, btd_done, d.size() * 4, k);
+    int64_t full = 0;
+    for (int i = 0; i < nrows; i++) full += (d[2 * i] && d[2 * i + 1]) ? 1 : 0;
+    o->n_rows_filled = full;
+    return cudaGetLastError() == cudaSuccess ? PIC_OK : c->fail(PIC_ECUDA, "CUDA error in lab-sample copy");
+  }
+
+  int get_field(int comp, double* dst, int on_device) {
+    set_ptrs_for_step();
+    const size_t n = stage_n;
+    if (comp >= PIC_EX && comp <= PIC_JZ) {
+      const T* src = comp < 3 ? f.E[comp] : comp < 6 ? f.B[comp - 3] : f.Jn[comp - 6];
+      launch_convert<T>(src, stage, g, c->stream);
+    } else if (comp == PIC_RHO) {
+      cudaMemsetAsync(stage, 0, n * 8, c->stream);
+      if (loaded) launch_rho<T>(g, P, ctrl, cap, c->cfg.shape_order, -kQe, stage, c->stream);
+      if (ions && loaded) {
+        const double t = time_of(step);
+        long long mlo = std::max(row_first, (long long)std::ceil((zlo_prev + c->hg.beta * kC * t) / ip.h - 0.5));
+        if (step == 0) mlo = row_first;
+        launch_ion_column(g, mlo, row_next, t, t, ip, c->cfg.shape_order, ion_R0, ion_R1, ion_C, c->stream);
+        launch_ion_rho(g, ion_x, ion_R0, kQe / (g.dx * g.dz), stage, c->stream);
+      }
+    } else {
+      return c->fail(PIC_EINVAL, "unknown component");
+    }
+    cudaStreamSynchronize(c->stream);
+    cudaMemcpy(dst, stage, n * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost);
+    return cudaGetLastError() == cudaSuccess ? PIC_OK : c->fail(PIC_ECUDA, "CUDA error in get_field");
+  }
+
+  int set_field(int comp, const double* src) {
+    if (comp < PIC_EX || comp > PIC_BZ) return c->fail(PIC_EINVAL, "only E and B can be set");
+    cudaMemcpyAsync(stage, src, stage_n * 8, cudaMemcpyHostToDevice, c->stream);
+    launch_convert_back<T>(stage, comp < 3 ? f.E[comp] : f.B[comp - 3], g, c->stream);
+    cudaStreamSynchronize(c->stream);
+    return cudaGetLastError() == cudaSuccess ? PIC_OK : c->fail(PIC_ECUDA, "CUDA error in set_field");
+  }
+
+  int get_particles(int species, double* x, double* z, double* ux, double* uy, double* uz, double* w, uint32_t* id,
+                    int32_t* flags, int64_t* count) {
+    cudaStreamSynchronize(c->stream);
+    if (species == PIC_BEAM) {
+      const int n = beam.n;
+      if (!x) { *count = n; return PIC_OK; }
+      if (*count < n) return c->fail(PIC_EINVAL, "output capacity too small");
+      std::vector<T> tu(n);
+      std::vector<int> fl(n);
+      if (n > 0) {
+        cudaMemcpy(x, beam.x, 8 * (size_t)n, cudaMemcpyDeviceToHost);
+        cudaMemcpy(z, beam.z, 8 * (size_t)n, cudaMemcpyDeviceToHost);
+        T* srcs[3] = {beam.ux, beam.uy, beam.uz};
+        double* dsts[3] = {ux, uy, uz};
+        for (int q = 0; q < 3; q++) {
+          cudaMemcpy(tu.data(), srcs[q], sizeof(T) * n, cudaMemcpyDeviceToHost);
+          for (int j = 0; j < n; j++) dsts[q][j] = (double)tu[j];
+        }
+        cudaMemcpy(fl.data(), beam.flag, 4 * (size_t)n, cudaMemcpyDeviceToHost);
+      }
+      for (int j = 0; j < n; j++) {
+        if (w) w[j] = 1.0;
+        if (id) id[j] = (uint32_t)j;
+        if (flags) flags[j] = fl[j];
+      }
+      *count = n;
+      return PIC_OK;
+    }
+    if (species != PIC_ELECTRONS) return c->fail(PIC_EINVAL, "unknown species");
+    if (!loaded || cap == 0) { *count = 0; return PIC_OK; }
+    double* out6 = al<double>(6 * (size_t)cap);
+    uint32_t* ido = al<uint32_t>(cap);
+    int* nout = al<int>(1);
+    if (!out6 || !ido || !nout) return c->fail(PIC_ENOMEM, "staging allocation failed");
+    launch_compact_copy<T>(P, ctrl, cap, out6, ido, nout, c->stream);
+    int hn = 0;
+    cudaStreamSynchronize(c->stream);
+    cudaMemcpy(&hn, nout, 4, cudaMemcpyDeviceToHost);
+    if (!x) { *count = hn; free_last(3); return PIC_OK; }
+    if (*count < hn) { free_last(3); return c->fail(PIC_EINVAL, "output capacity too small"); }
+    double* dsts[6] = {x, z, ux, uy, uz, w};
+    for (int q = 0; q < 6; q++)
+      if (dsts[q]) cudaMemcpy(dsts[q], out6 + (size_t)q * cap, 8 * (size_t)hn, cudaMemcpyDeviceToHost);
+    if (id) cudaMemcpy(id, ido, 4 * (size_t)hn, cudaMemcpyDeviceToHost);
+    if (flags) for (int j = 0; j < hn; j++) flags[j] = 1;
+    *count = hn;
+    free_last(3);
+    return cudaGetLastError() == cudaSuccess ? PIC_OK : c->fail(PIC_ECUDA, "CUDA error in get_particles");
+  }
+
+  void free_last(int n) {
+    for (int i = 0; i < n && !c->allocs.empty(); i++) {
+      auto a = c->allocs.back();
+      c->allocs.pop_back();
+      cudaStreamSynchronize(c->stream);
+      if (c->freef) c->freef(a.p, a.n, (void*)c->stream, c->user);
+      else cudaFree(a.p);
+    }
+  }
+
+  int stats(pic_stats* o) {
+    set_ptrs_for_step();
+    launch_stats<T>(g, f, P, ctrl, cap, beam, c->hg.gamma, c->hg.beta, stats_buf, c->stream);
+    double h[8];
+    Ctrl hc;
+    cudaStreamSynchronize(c->stream);
+    cudaMemcpy(h, stats_buf, sizeof(h), cudaMemcpyDeviceToHost);
+    cudaMemcpy(&hc, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost);
+    o->step = step; o->t = time_of(step);
+    o->dt = g.dt; o->dx = g.dx; o->dz = g.dz; o->gamma = c->hg.gamma; o->beta = c->hg.beta;
+    o->n_electrons = (int64_t)h[0];
+    o->n_beam_active = (int64_t)h[1];
+    o->beam_gamma_lab = h[1] > 0 ? h[2] / h[1] : 0.0;
+    double var = h[1] > 0 ? h[3] / h[1] - o->beam_gamma_lab * o->beam_gamma_lab : 0.0;
+    o->beam_spread = o->beam_gamma_lab > 0 ? std::sqrt(var > 0 ? var : 0) / o->beam_gamma_lab : 0.0;
+    o->field_energy = h[4];
+    o->gx_lo = g.gx_lo; o->gx_hi = g.gx_hi; o->gz_lo = g.gz_lo; o->gz_hi = g.gz_hi;
+    o->sorts = sorts; o->overflow_chunks = hc.overflow_chunks;
+    o->z0 = g.z0;
+    return cudaGetLastError() == cudaSuccess ? PIC_OK : c->fail(PIC_ECUDA, "CUDA error in stats");
+  }
+
+  int sync() {
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return c->fail(PIC_ECUDA, std::string("CUDA error: ") + cudaGetErrorString(e));
+    Ctrl hc;
+    cudaMemcpy(&hc, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost);
+    if (hc.status & ST_OVERFLOW) return c->fail(PIC_EOVERFLOW, "device capacity exceeded");
+    if (hc.status & ST_NAN) return c->fail(PIC_ENAN, "non-finite particle state");
+    if (hc.status & ST_OUTSIDE) return c->fail(PIC_EINVAL, "particle outside the grid");
+    if (hc.status & ST_TIMEOUT) return c->fail(PIC_ETIMEOUT, "device wait timed out");
+    return PIC_OK;
+  }
+
+  int kernel_timing(int enable, int which, double* ms, int64_t* nl) {
+    if (enable) {
+      for (auto e : ev) cudaEventDestroy(e);
+      ev.clear();
+      timing = true; timing_which = which; timed_launches = 0;
+      return PIC_OK;
+    }
+    cudaStreamSynchronize(c->stream);
+    double tot = 0.0;
+    for (size_t i = 0; i + 1 < ev.size(); i += 2) {
+      float m = 0.f;
+      cudaEventElapsedTime(&m, ev[i], ev[i + 1]);
+      tot += m;
+    }
+    if (ms) *ms = tot;
+    if (nl) *nl = timed_launches;
+    for (auto e : ev) cudaEventDestroy(e);
+    ev.clear();
+    timing = false;
+    return PIC_OK;
+  }
+};
+
+template <class T>
+Sim<T>* S(pic_ctx* c) { return static_cast<Sim<T>*>(c->sim.get()); }
+
+#define DISPATCH(ctx, expr)                                                  \
+  ((ctx)->cfg.precision == PIC_FP64 ? S<double>(ctx)->expr : S<float>(ctx)->expr)
+
+}  // namespace
+
+extern "C" {
+
+int pic_init(const pic_config* cfg, pic_alloc_fn alloc, pic_free_fn free_fn, void* alloc_user, void* cuda_stream,
+             pic_ctx** out) {
+  if (!out) return PIC_EINVAL;
+  *out = nullptr;
+  if (!cfg || cfg->struct_size != sizeof(pic_config) || cfg->version != PIC_API_VERSION) return PIC_EINVAL;
+  if (cfg->dim != 2) return PIC_EINVAL;
+  if (cfg->nx < 8 || cfg->nz < 8 || !(cfg->dx > 0) || !(cfg->dz_lab > 0)) return PIC_EINVAL;
+  if (cfg->shape_order != 1 && cfg->shape_order != 3) return PIC_EINVAL;
+  if (cfg->precision != PIC_FP64 && cfg->precision != PIC_MIXED) return PIC_EINVAL;
+  if (std::fabs(cfg->ck_alpha + 4 * cfg->ck_beta + 4 * cfg->ck_gamma - 1.0) > 1e-12) return PIC_EINVAL;
+  if (cfg->theta < 0 || cfg->theta > 1) return PIC_EINVAL;
+  if (cfg->filter_passes < 0 || cfg->filter_stride < 1 || cfg->pml_cells < 0) return PIC_EINVAL;
+  std::unique_ptr<pic_ctx> c(new pic_ctx());
+  c->cfg = *cfg;
+  c->stream = (cudaStream_t)cuda_stream;
+  c->alloc = alloc; c->freef = free_fn; c->user = alloc_user;
+  HostGeom& h = c->hg;
+  h.gamma = cfg->gamma_boost < 1.0 ? 1.0 : cfg->gamma_boost;
+  h.beta = std::sqrt(1.0 - 1.0 / (h.gamma * h.gamma));
+  h.dz = (1.0 + h.beta) * h.gamma * cfg->dz_lab;     // Sec. 5.1.1
+  h.dx = cfg->dx;
+  h.a2 = cfg->ck_alpha + 2.0 * cfg->ck_beta;         // PR-3
+  h.b2 = cfg->ck_beta + 2.0 * cfg->ck_gamma;
+  h.dt_cfl = cfl_2d(cfg->ck_alpha, cfg->ck_gamma, h.dx, h.dz, cfg->theta);
+  h.dt = cfg->dt > 0.0 ? cfg->dt : cfg->courant * h.dt_cfl;
+  if (!(h.dt > 0.0)) return PIC_EINVAL;
+  if (h.dt > h.dt_cfl * (1.0 + 1e-12)) return PIC_ECFL;
+  const int P = cfg->filter_passes + (cfg->filter_compensate ? 1 : 0);
+  h.guard = cfg->particle_guard >= 0 ? cfg->particle_guard : (cfg->shape_order == 3 ? 3 : 2) + P * cfg->filter_stride + 2;
+  const int L = cfg->pml_cells;
+  h.gx_lo = L + h.guard; h.gx_hi = cfg->nx - L - h.guard;
+  h.gz_lo = L + h.guard; h.gz_hi = cfg->nz - L - h.guard;
+  if (h.gx_hi - h.gx_lo < 2 || h.gz_hi - h.gz_lo < 2) return PIC_EINVAL;
+  if (h.gx_lo < 4 || h.gz_lo < 4) return PIC_EINVAL;
+  const int elem = cfg->precision == PIC_FP64 ? 8 : 4;
+  const int align = 128 / elem;
+  h.ld = ((cfg->nz + 1 + align - 1) / align) * align;
+  int r;
+  if (cfg->precision == PIC_FP64) {
+    auto* s = new Sim<double>(c.get());
+    c->sim.reset(s);
+    r = s->init();
+  } else {
+    auto* s = new Sim<float>(c.get());
+    c->sim.reset(s);
+    r = s->init();
+  }
+  if (r != PIC_OK) {
+    c->sim.reset();
+    c->release_all();
+    return r;
+  }
+  cudaStreamSynchronize(c->stream);
+  *out = c.release();
+  return PIC_OK;
+}
+
+int pic_load_plasma(pic_ctx* c, const pic_plasma* p) {
+  if (!c) return PIC_EINVAL;
+  if (!p || p->struct_size != sizeof(pic_plasma) || p->version != PIC_API_VERSION) return c->fail(PIC_EINVAL, "bad pic_plasma");
+  if (c->status != PIC_OK) return c->status;
+  return DISPATCH(c, load_plasma(p));
+}
+
+int pic_inject_laser(pic_ctx* c, const pic_laser* l) {
+  if (!c) return PIC_EINVAL;
+  if (!l || l->struct_size != sizeof(pic_laser) || l->version != PIC_API_VERSION) return c->fail(PIC_EINVAL, "bad pic_laser");
+  if (c->status != PIC_OK) return c->status;
+  return DISPATCH(c, set_laser(l));
+}
+
+int pic_step(pic_ctx* c, int nsteps) {
+  if (!c) return PIC_EINVAL;
+  if (nsteps < 0) return c->fail(PIC_EINVAL, "nsteps < 0");
+  if (c->status != PIC_OK) return c->status;
+  return DISPATCH(c, run(nsteps));
+}
+
+int pic_sync(pic_ctx* c) {
+  if (!c) return PIC_EINVAL;
+  int r = DISPATCH(c, sync());
+  return c->status != PIC_OK ? c->status : r;
+}
+
+int pic_boosted_to_lab_diag(pic_ctx* c, const pic_btd_req* req, pic_btd_out* out) {
+  if (!c) return PIC_EINVAL;
+  if (c->status != PIC_OK) return c->status;
+  if (req && !out) {
+    if (req->struct_size != sizeof(pic_btd_req) || req->version != PIC_API_VERSION) return c->fail(PIC_EINVAL, "bad pic_btd_req");
+    return DISPATCH(c, btd_set(req));
+  }
+  if (!req && out) {
+    if (out->struct_size != sizeof(pic_btd_out) || out->version != PIC_API_VERSION) return c->fail(PIC_EINVAL, "bad pic_btd_out");
+    return DISPATCH(c, btd_get(out));
+  }
+  return c->fail(PIC_EINVAL, "pass exactly one of req and out");
+}
+
+int pic_free(pic_ctx* c) {
+  if (!c) return PIC_OK;
+  cudaStreamSynchronize(c->stream);
+  c->sim.reset();
+  c->release_all();
+  delete c;
+  return PIC_OK;
+}
+
+int pic_get_field(pic_ctx* c, int comp, double* dst, int on_device) {
+  if (!c || !dst) return PIC_EINVAL;
+  if (c->status != PIC_OK) return c->status;
+  return DISPATCH(c, get_field(comp, dst, on_device));
+}
+
+int pic_set_field(pic_ctx* c, int comp, const double* src) {
+  if (!c || !src) return PIC_EINVAL;
+  if (c->status != PIC_OK) return c->status;
+  return DISPATCH(c, set_field(comp, src));
+}
+
+int pic_get_particles(pic_ctx* c, int species, double* x, double* z, double* ux, double* uy, double* uz, double* w,
+                      uint32_t* id, int32_t* flags, int64_t* count) {
+  if (!c || !count) return PIC_EINVAL;
+  if (c->status != PIC_OK) return c->status;
+  return DISPATCH(c, get_particles(species, x, z, ux, uy, uz, w, id, flags, count));
+}
+
+int pic_get_stats(pic_ctx* c, pic_stats* out) {
+  if (!c || !out) return PIC_EINVAL;
+  if (out->struct_size != sizeof(pic_stats) || out->version != PIC_API_VERSION) return c->fail(PIC_EINVAL, "bad pic_stats");
+  if (c->status != PIC_OK) return c->status;
+  return DISPATCH(c, stats(out));
+}
+
+const char* pic_last_error(pic_ctx* c) {
+  if (!c) return "null context";
+  return c->err.empty() ? "" : c->err.c_str();
+}
+
+int64_t pic_kernel_launches(pic_ctx* c) { return c ? c->launches : 0; }
+
+int pic_kernel_timing(pic_ctx* c, int enable, int which, double* ms_total, int64_t* launches) {
+  if (!c) return PIC_EINVAL;
+  return DISPATCH(c, kernel_timing(enable, which, ms_total, launches));
+}
+
+}  // extern "C"

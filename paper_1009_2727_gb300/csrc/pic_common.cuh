@@ -1,0 +1,201 @@
+// Internal declarations of the GB300 PIC library (device types, shape
+// functions, kernel launchers). Not part of the public ABI (include/pic.h).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace picgb {
+
+// CODATA 2018
+constexpr double kC = 299792458.0;
+constexpr double kQe = 1.602176634e-19;
+constexpr double kMe = 9.1093837015e-31;
+constexpr double kEps0 = 8.8541878128e-12;
+constexpr double kPi = 3.14159265358979323846;
+
+enum Comp { EX = 0, EY, EZ, BX, BY, BZ };
+
+// Device status bits (sticky, read by pic_sync)
+enum StatusBits : int { ST_OVERFLOW = 1, ST_NAN = 2, ST_OUTSIDE = 4, ST_TIMEOUT = 8 };
+
+// Geometry passed by value to every kernel.
+struct GridP {
+  int nx, nz, ld;            // cells; row stride (elements) of every grid array
+  double dx, dz, dt;
+  double z0;                 // grid origin along z (moving window)
+  int gx_lo, gx_hi, gz_lo, gz_hi;  // particle domain (cells)
+  int pml;                   // PML cells (0 = none)
+};
+
+// Valid index range of each E/B component (PEC walls); J uses the E ranges.
+__host__ __device__ inline void valid_range(int comp, int nx, int nz, int& i0, int& i1, int& k0, int& k1) {
+  switch (comp) {
+    case EX: i0 = 0; i1 = nx - 1; k0 = 1; k1 = nz - 1; break;
+    case EY: i0 = 1; i1 = nx - 1; k0 = 1; k1 = nz - 1; break;
+    case EZ: i0 = 1; i1 = nx - 1; k0 = 0; k1 = nz - 1; break;
+    case BX: i0 = 0; i1 = nx;     k0 = 0; k1 = nz - 1; break;
+    case BY: i0 = 0; i1 = nx - 1; k0 = 0; k1 = nz - 1; break;
+    default: i0 = 0; i1 = nx - 1; k0 = 0; k1 = nz;     break;
+  }
+}
+
+// PML coefficient tables (always FP64): sigma, xi and (1-xi)/sigma at integer
+// and half positions along x (size nx+1) and z (size nz+1).
+struct PmlTabs {
+  const double *sx_i, *sx_h, *xx_i, *xx_h, *cx_i, *cx_h;
+  const double *sz_i, *sz_h, *xz_i, *xz_h, *cz_i, *cz_h;
+};
+
+template <class T>
+struct FieldPtrs {
+  T* E[3];      // E^n
+  T* Eo[3];     // other E buffer: E^{n-1} on entry to Faraday, receives E^{n+1} in Ampere
+  T* B[3];
+  T* J[3];      // current being deposited this step
+  T* Jn[3];     // other current buffer (zeroed by Ampere for the next step)
+  T* Eb[3];     // Friedman E-bar (read)
+  T* Ebn[3];    // Friedman E-bar (write)
+  T* Bavg[3];   // (B^{n-1/2} + B^{n+1/2})/2
+  T* fE[3];     // gather copies
+  T* fB[3];
+  T* Byx; T* Byz; T* Eyx; T* Eyz;  // split PML parts (full-size, used in the PML only)
+};
+
+struct FilterSpec {
+  int passes, stride, compensate;
+};
+
+// Particle chunk: a contiguous particle range and the bounding box of the
+// cells its particles occupy (inclusive, grid-relative cells).
+struct Chunk {
+  int p0, p1;
+  int ix0, ix1, iz0, iz1;
+};
+
+template <class T>
+struct Particles {
+  double* x; double* z;
+  T* ux; T* uy; T* uz; T* w;
+  uint32_t* id;
+};
+
+// Control block in device memory.
+struct Ctrl {
+  int count;          // particle slots in use (electrons)
+  int nchunks;
+  int next_chunk;     // work counter of the persistent particle kernel
+  int status;
+  int overflow_chunks;
+  int pad[3];
+  double red[8];      // reduction scratch
+};
+
+// ---------------------------------------------------------------------------
+// B-spline weights from the fractional offset t in [0,1) of a position above
+// node f: order 3 -> nodes f-1..f+2, order 1 -> nodes f, f+1.
+template <class R>
+__device__ __forceinline__ void weights3(R t, R* w) {
+  R t2 = t * t, t3 = t2 * t, s = R(1) - t;
+  w[0] = s * s * s * R(1.0 / 6.0);
+  w[1] = R(2.0 / 3.0) - t2 + R(0.5) * t3;
+  w[2] = R(1.0 / 6.0) + R(0.5) * (t + t2 - t3);
+  w[3] = t3 * R(1.0 / 6.0);
+}
+template <class R>
+__device__ __forceinline__ void weights1(R t, R* w) {
+  w[0] = R(1) - t;
+  w[1] = t;
+}
+
+// ---------------------------------------------------------------------------
+// Launchers (defined in the .cu files, instantiated for float and double).
+template <class T>
+void launch_faraday(const GridP& g, const FieldPtrs<T>& f, const PmlTabs& pt, double a2, double b2,
+                    double theta, bool friedman, cudaStream_t s);
+template <class T>
+void launch_filter_fields(const GridP& g, const FieldPtrs<T>& f, const FilterSpec& fs, bool enabled, cudaStream_t s);
+template <class T>
+void launch_ampere(const GridP& g, const FieldPtrs<T>& f, const PmlTabs& pt, const FilterSpec& fs, bool filter_on,
+                   const double* ion_x, const double* ion_c, double ion_coef, cudaStream_t s);
+
+template <class T>
+void launch_push(const GridP& g, const FieldPtrs<T>& f, Particles<T> p, Chunk* chunks, Ctrl* ctrl, int order,
+                 int grid_blocks, int smem_nodes, double q, double m, cudaStream_t s);
+
+struct SortBufs {
+  int* cell_cnt;       // nx*nz
+  int* bin_cnt;        // ntiles*R (+1)
+  int* bin_start;      // ntiles*R + 1
+  int* key;            // per particle
+  int* slot;
+  int* scan_tmp;
+  int ntx, ntz, tx, tz, R;
+};
+template <class T>
+void launch_sort(const GridP& g, Particles<T> src, Particles<T> dst, SortBufs sb, Chunk* chunks, Ctrl* ctrl,
+                 int cap, int chunk_max, int chunk_cap, cudaStream_t s);
+
+struct InjectP {
+  long long m_beg, m_end;       // lattice rows to create
+  double t;                     // time of the positions
+  double h;                     // row spacing
+  double gamma, beta;
+  double n0, z_start_lab, ramp_lab, length_lab;
+  int ppc_x, ppc_z, nxl;
+  int xblock;                   // cells per chunk along x
+  int rblock;                   // rows per chunk
+};
+template <class T>
+void launch_inject(const GridP& g, Particles<T> p, Chunk* chunks, Ctrl* ctrl, const InjectP& ip, int cap,
+                   int chunk_cap, cudaStream_t s);
+void launch_add_counts(Ctrl* ctrl, int dcount, int dchunks, cudaStream_t s);
+
+void launch_ion_column(const GridP& g, long long mlo, long long mhi, double t0, double t1, const InjectP& ip,
+                       int order, double* R0, double* R1, double* C, cudaStream_t s);
+
+struct LaserP {
+  double lambda0, a0, w0, tau, t_peak, x_center, phase, z_antenna, beta_s;
+  double gamma, beta;
+};
+template <class T>
+void launch_antenna(const GridP& g, T* Jy, const LaserP& lp, int order, double t0, double t1, cudaStream_t s);
+
+template <class T>
+struct Beam {
+  double* x; double* z; T* ux; T* uy; T* uz;
+  double* tc; double* zf0; T* uxb; T* uyb; T* uzb; int* flag;  // bit0 alive, bit1 active
+  int n;
+};
+template <class T>
+void launch_beam_init(Beam<T> b, const double* lx, const double* lz, const double* lux, const double* luy,
+                      const double* luz, double t_lab, double z_plane, double gamma, double beta, double t_now,
+                      double* scratch, cudaStream_t s);
+template <class T>
+void launch_beam_push(const GridP& g, const FieldPtrs<T>& f, Beam<T> b, int order, double tn, double tn1,
+                      double vbar_dev_unused, const double* scratch, cudaStream_t s);
+
+template <class T>
+void launch_btd(const GridP& g, const FieldPtrs<T>& f, int which, int post, int r0, int r1, const int* order_idx,
+                const double* tp, const double* zp, double ta, double gamma, double beta, T* out, int* done,
+                cudaStream_t s);
+
+template <class T>
+void launch_rho(const GridP& g, Particles<T> p, const Ctrl* ctrl, int cap, int order, double q, double* rho,
+                cudaStream_t s);
+void launch_ion_rho(const GridP& g, const double* ion_x, const double* R, double coef, double* rho, cudaStream_t s);
+template <class T>
+void launch_stats(const GridP& g, const FieldPtrs<T>& f, Particles<T> p, const Ctrl* ctrl, int cap, Beam<T> b,
+                  double gamma, double beta, double* out, cudaStream_t s);
+template <class T>
+void launch_shift(const GridP& g, T* arr, T* tmp, int sh, cudaStream_t s);
+void launch_shift_chunks(Chunk* chunks, Ctrl* ctrl, int sh, int chunk_cap, cudaStream_t s);
+template <class T>
+void launch_convert(const T* src, double* dst, const GridP& g, cudaStream_t s);
+template <class T>
+void launch_convert_back(const double* src, T* dst, const GridP& g, cudaStream_t s);
+template <class T>
+void launch_compact_copy(Particles<T> p, const Ctrl* ctrl, int cap, double* out6, uint32_t* id_out, int* nout,
+                         cudaStream_t s);
+
+}  // namespace picgb

@@ -1,0 +1,571 @@
+// Particle kernels of the boosted-frame PIC step:
+//  - k_push: persistent gather -> Boris -> move -> Esirkepov kernel. One CTA
+//    takes one chunk (a contiguous run of particles whose cells lie in a known
+//    bounding box), stages the six gather fields of the box in shared memory,
+//    deposits J into a shared-memory copy of the box with shared atomics and
+//    adds the box to the global current once. A chunk whose box exceeds the
+//    shared-memory capacity runs the same arithmetic on global memory.
+//  - tile sort (counting sort into tiles; within a tile, particles are grouped
+//    by their rank inside their cell so that the lanes of a warp usually hold
+//    particles of different cells and their shared atomics do not collide);
+//  - plasma rows entering through the +z plane (Sec. 3.1.1, PR-12).
+#include <climits>
+
+#include "pic_common.cuh"
+
+namespace picgb {
+
+namespace {
+
+constexpr int PB_THREADS = 256;
+
+template <int ORDER>
+struct St;
+template <>
+struct St<3> { static constexpr int NG = 4, ND = 5, LO = 2, HI = 3; };
+template <>
+struct St<1> { static constexpr int NG = 2, ND = 3, LO = 1, HI = 2; };
+
+template <class T, int ORDER>
+__device__ __forceinline__ void wts(T t, T* w) {
+  if (ORDER == 3) weights3<T>(t, w);
+  else weights1<T>(t, w);
+}
+
+// place NG weights of a particle whose first node is at offset o (0 or 1) into an ND window
+template <class T, int ORDER>
+__device__ __forceinline__ void place(const T* w, int o, T* S) {
+  constexpr int NG = St<ORDER>::NG, ND = St<ORDER>::ND;
+#pragma unroll
+  for (int j = 0; j < ND; j++) {
+    T a = (j < NG) ? w[j] : T(0);
+    T b = (j >= 1) ? w[j - 1] : T(0);
+    S[j] = o ? b : a;
+  }
+}
+
+template <class T>
+struct View {
+  const T* fe[6];   // gather fields
+  T* j[3];          // current
+  int ld, ox, oz;   // index = (i - ox)*ld + (k - oz)
+};
+
+template <class T, int ORDER>
+__device__ __forceinline__ T interp(const T* F, const View<T>& v, int fi, int fk, const T* wx, const T* wz) {
+  constexpr int NG = St<ORDER>::NG;
+  const int off = ORDER == 3 ? 1 : 0;
+  T acc = T(0);
+#pragma unroll
+  for (int a = 0; a < NG; a++) {
+    const T* row = F + (long)(fi - off + a - v.ox) * v.ld + (fk - off - v.oz);
+    T r = T(0);
+#pragma unroll
+    for (int b = 0; b < NG; b++) r += row[b] * wz[b];
+    acc += r * wx[a];
+  }
+  return acc;
+}
+
+template <class T, bool SMEM>
+__device__ __forceinline__ void jadd(T* p, T v) {
+  atomicAdd(p, v);
+}
+
+struct PushConst {
+  double dx, dz, dt, z0;
+  double xlo, xhi, zlo, zhi;
+  double qm_half;   // q dt/(2m)
+  double q;
+};
+
+template <class T, int ORDER, bool SMEM>
+__device__ __forceinline__ void push_one(const View<T>& v, Particles<T>& p, int pi, const PushConst& pc,
+                                         int& bx0, int& bx1, int& bz0, int& bz1) {
+  constexpr int NG = St<ORDER>::NG, ND = St<ORDER>::ND;
+  const T w = p.w[pi];
+  if (w == T(0)) return;
+  const double x = p.x[pi], z = p.z[pi];
+  T ux = p.ux[pi], uy = p.uy[pi], uz = p.uz[pi];
+  const double X = x / pc.dx, Z = (z - pc.z0) / pc.dz;
+  const int fx = (int)floor(X), fz = (int)floor(Z);
+  const T tx = T(X - fx), tz = T(Z - fz);
+  const double Xh = X - 0.5, Zh = Z - 0.5;
+  const int fxh = (int)floor(Xh), fzh = (int)floor(Zh);
+  const T txh = T(Xh - fxh), tzh = T(Zh - fzh);
+  T wxi[NG], wzi[NG], wxh[NG], wzh[NG];
+  wts<T, ORDER>(tx, wxi); wts<T, ORDER>(tz, wzi);
+  wts<T, ORDER>(txh, wxh); wts<T, ORDER>(tzh, wzh);
+  // energy-conserving gather from each component's Yee location
+  const T Ex = interp<T, ORDER>(v.fe[0], v, fxh, fz, wxh, wzi);
+  const T Ey = interp<T, ORDER>(v.fe[1], v, fx, fz, wxi, wzi);
+  const T Ez = interp<T, ORDER>(v.fe[2], v, fx, fzh, wxi, wzh);
+  const T Bx = interp<T, ORDER>(v.fe[3], v, fx, fzh, wxi, wzh);
+  const T By = interp<T, ORDER>(v.fe[4], v, fxh, fzh, wxh, wzh);
+  const T Bz = interp<T, ORDER>(v.fe[5], v, fxh, fz, wxh, wzi);
+  // relativistic Boris push
+  const T k = T(pc.qm_half);
+  const T ic2 = T(1.0 / (kC * kC));
+  T umx = ux + k * Ex, umy = uy + k * Ey, umz = uz + k * Ez;
+  T gm = sqrt(T(1) + (umx * umx + umy * umy + umz * umz) * ic2);
+  T tbx = k * Bx / gm, tby = k * By / gm, tbz = k * Bz / gm;
+  T t2 = tbx * tbx + tby * tby + tbz * tbz;
+  T sf = T(2) / (T(1) + t2);
+  T sbx = sf * tbx, sby = sf * tby, sbz = sf * tbz;
+  T upx = umx + (umy * tbz - umz * tby);
+  T upy = umy + (umz * tbx - umx * tbz);
+  T upz = umz + (umx * tby - umy * tbx);
+  T plx = umx + (upy * sbz - upz * sby);
+  T ply = umy + (upz * sbx - upx * sbz);
+  T plz = umz + (upx * sby - upy * sbx);
+  ux = plx + k * Ex; uy = ply + k * Ey; uz = plz + k * Ez;
+  const T g1 = sqrt(T(1) + (ux * ux + uy * uy + uz * uz) * ic2);
+  const T vx = ux / g1, vy = uy / g1, vz = uz / g1;
+  const double xn = x + pc.dt * (double)vx;
+  const double zn = z + pc.dt * (double)vz;
+  // Esirkepov deposition on an ND x ND window
+  const double Xn = xn / pc.dx, Zn = (zn - pc.z0) / pc.dz;
+  const int fxn = (int)floor(Xn), fzn = (int)floor(Zn);
+  const T txn = T(Xn - fxn), tzn = T(Zn - fzn);
+  const int off = ORDER == 3 ? 1 : 0;
+  const int bx = min(fx, fxn) - off, bz = min(fz, fzn) - off;
+  T S0x[ND], S1x[ND], S0z[ND], S1z[ND];
+  {
+    T w0[NG], w1[NG];
+    place<T, ORDER>(wxi, fx - off - bx, S0x);
+    wts<T, ORDER>(txn, w1); place<T, ORDER>(w1, fxn - off - bx, S1x);
+    place<T, ORDER>(wzi, fz - off - bz, S0z);
+    wts<T, ORDER>(tzn, w0); place<T, ORDER>(w0, fzn - off - bz, S1z);
+  }
+  T DSx[ND], DSz[ND];
+#pragma unroll
+  for (int a = 0; a < ND; a++) { DSx[a] = S1x[a] - S0x[a]; DSz[a] = S1z[a] - S0z[a]; }
+  const T qw = T(pc.q) * w;
+  const T cx = -qw / T(pc.dz * pc.dt);
+  const T cz = -qw / T(pc.dx * pc.dt);
+  const T cy = qw * vy / T(pc.dx * pc.dz);
+  T* Jx = v.j[0] + (long)(bx - v.ox) * v.ld + (bz - v.oz);
+  T* Jy = v.j[1] + (long)(bx - v.ox) * v.ld + (bz - v.oz);
+  T* Jz = v.j[2] + (long)(bx - v.ox) * v.ld + (bz - v.oz);
+#pragma unroll
+  for (int b = 0; b < ND; b++) {
+    const T fzb = S0z[b] + T(0.5) * DSz[b];
+    T acc = T(0);
+#pragma unroll
+    for (int a = 0; a < ND - 1; a++) {
+      acc += cx * DSx[a] * fzb;
+      if (acc != T(0)) jadd<T, SMEM>(Jx + (long)a * v.ld + b, acc);
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < ND; a++) {
+    const T fxa = S0x[a] + T(0.5) * DSx[a];
+    T acc = T(0);
+#pragma unroll
+    for (int b = 0; b < ND - 1; b++) {
+      acc += cz * DSz[b] * fxa;
+      if (acc != T(0)) jadd<T, SMEM>(Jz + (long)a * v.ld + b, acc);
+    }
+  }
+  if (cy != T(0)) {
+#pragma unroll
+    for (int a = 0; a < ND; a++) {
+#pragma unroll
+      for (int b = 0; b < ND; b++) {
+        T wy = S0x[a] * S0z[b] + T(0.5) * DSx[a] * S0z[b] + T(0.5) * S0x[a] * DSz[b] + DSx[a] * DSz[b] * T(1.0 / 3.0);
+        if (wy != T(0)) jadd<T, SMEM>(Jy + (long)a * v.ld + b, cy * wy);
+      }
+    }
+  }
+  p.x[pi] = xn; p.z[pi] = zn;
+  p.ux[pi] = ux; p.uy[pi] = uy; p.uz[pi] = uz;
+  if (xn < pc.xlo || xn >= pc.xhi || zn < pc.zlo || zn >= pc.zhi) {
+    p.w[pi] = T(0);
+  } else {
+    bx0 = min(bx0, fxn); bx1 = max(bx1, fxn);
+    bz0 = min(bz0, fzn); bz1 = max(bz1, fzn);
+  }
+}
+
+template <class T>
+__device__ __forceinline__ View<T> global_view(const FieldPtrs<T>& f, const GridP& g) {
+  View<T> v;
+  for (int q = 0; q < 3; q++) { v.fe[q] = f.fE[q]; v.fe[3 + q] = f.fB[q]; v.j[q] = f.J[q]; }
+  v.ld = g.ld; v.ox = 0; v.oz = 0;
+  return v;
+}
+
+// global-memory path with an index guard: a particle whose stencil would leave
+// the arrays (only possible for corrupted or non-finite state) is removed and
+// flagged instead of being pushed.
+template <class T, int ORDER>
+__device__ __noinline__ void push_global_guarded(const View<T>& vg, const GridP& g, Particles<T>& p, int pi,
+                                                 const PushConst& pc, Ctrl* ctrl, int& bx0, int& bx1, int& bz0,
+                                                 int& bz1) {
+  if (p.w[pi] == T(0)) return;
+  const double X = p.x[pi] / pc.dx, Z = (p.z[pi] - pc.z0) / pc.dz;
+  const bool ok = X >= St<ORDER>::LO + 1 && X < g.nx - St<ORDER>::HI - 1 && Z >= St<ORDER>::LO + 1 &&
+                  Z < g.nz - St<ORDER>::HI - 1;
+  if (!ok) {
+    p.w[pi] = T(0);
+    atomicOr(&ctrl->status, (X == X && Z == Z) ? ST_OUTSIDE : ST_NAN);
+    return;
+  }
+  push_one<T, ORDER, false>(vg, p, pi, pc, bx0, bx1, bz0, bz1);
+}
+
+template <class T, int ORDER>
+__global__ void __launch_bounds__(PB_THREADS) k_push(GridP g, FieldPtrs<T> f, Particles<T> p, Chunk* chunks,
+                                                     Ctrl* ctrl, int cap_nodes, PushConst pc) {
+  extern __shared__ unsigned char smraw[];
+  T* sm = reinterpret_cast<T*>(smraw);
+  __shared__ int s_chunk;
+  __shared__ int s_bb[4];
+  const int nchunks = ctrl->nchunks;
+  while (true) {
+    if (threadIdx.x == 0) {
+      s_chunk = atomicAdd(&ctrl->next_chunk, 1);
+      s_bb[0] = INT_MAX; s_bb[1] = INT_MIN; s_bb[2] = INT_MAX; s_bb[3] = INT_MIN;
+    }
+    __syncthreads();
+    const int c = s_chunk;
+    if (c >= nchunks) break;
+    const Chunk ch = chunks[c];
+    if (ch.ix0 > ch.ix1 || ch.p1 <= ch.p0) {   // empty chunk
+      __syncthreads();
+      continue;
+    }
+    const int wx0 = ch.ix0 - St<ORDER>::LO, wx1 = ch.ix1 + St<ORDER>::HI;
+    const int wz0 = ch.iz0 - St<ORDER>::LO, wz1 = ch.iz1 + St<ORDER>::HI;
+    const int wxn = wx1 - wx0 + 1, wzn = wz1 - wz0 + 1;
+    const int nn = wxn * wzn;
+    const bool use_smem = nn <= cap_nodes && wx0 >= 0 && wz0 >= 0 && wx1 <= g.nx && wz1 <= g.nz;
+    int bx0 = INT_MAX, bx1 = INT_MIN, bz0 = INT_MAX, bz1 = INT_MIN;
+    if (use_smem) {
+      for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+        const int li = e / wzn, lk = e - li * wzn;
+        const long gp = (long)(wx0 + li) * g.ld + (wz0 + lk);
+#pragma unroll
+        for (int q = 0; q < 3; q++) {
+          sm[q * cap_nodes + e] = f.fE[q][gp];
+          sm[(3 + q) * cap_nodes + e] = f.fB[q][gp];
+          sm[(6 + q) * cap_nodes + e] = T(0);
+        }
+      }
+      __syncthreads();
+      View<T> v;
+      for (int q = 0; q < 6; q++) v.fe[q] = sm + q * cap_nodes;
+      for (int q = 0; q < 3; q++) v.j[q] = sm + (6 + q) * cap_nodes;
+      v.ld = wzn; v.ox = wx0; v.oz = wz0;
+      View<T> vg = global_view<T>(f, g);
+      for (int pi = ch.p0 + threadIdx.x; pi < ch.p1; pi += blockDim.x) {
+        // a particle outside the chunk's box (should not happen) takes the global path
+        const double X = p.x[pi] / pc.dx, Z = (p.z[pi] - pc.z0) / pc.dz;
+        const int fx = (int)floor(X), fz = (int)floor(Z);
+        if (fx >= ch.ix0 && fx <= ch.ix1 && fz >= ch.iz0 && fz <= ch.iz1)
+          push_one<T, ORDER, true>(v, p, pi, pc, bx0, bx1, bz0, bz1);
+        else
+          push_global_guarded<T, ORDER>(vg, g, p, pi, pc, ctrl, bx0, bx1, bz0, bz1);
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+        const int li = e / wzn, lk = e - li * wzn;
+        const long gp = (long)(wx0 + li) * g.ld + (wz0 + lk);
+#pragma unroll
+        for (int q = 0; q < 3; q++) {
+          T val = sm[(6 + q) * cap_nodes + e];
+          if (val != T(0)) atomicAdd(f.J[q] + gp, val);
+        }
+      }
+    } else {
+      if (threadIdx.x == 0) atomicAdd(&ctrl->overflow_chunks, 1);
+      View<T> vg = global_view<T>(f, g);
+      for (int pi = ch.p0 + threadIdx.x; pi < ch.p1; pi += blockDim.x)
+        push_global_guarded<T, ORDER>(vg, g, p, pi, pc, ctrl, bx0, bx1, bz0, bz1);
+    }
+    // bounding box of the chunk's live particles for the next step
+    bx0 = __reduce_min_sync(0xffffffffu, bx0); bx1 = __reduce_max_sync(0xffffffffu, bx1);
+    bz0 = __reduce_min_sync(0xffffffffu, bz0); bz1 = __reduce_max_sync(0xffffffffu, bz1);
+    if ((threadIdx.x & 31) == 0) {
+      atomicMin(&s_bb[0], bx0); atomicMax(&s_bb[1], bx1);
+      atomicMin(&s_bb[2], bz0); atomicMax(&s_bb[3], bz1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      Chunk o = ch;
+      o.ix0 = s_bb[0]; o.ix1 = s_bb[1]; o.iz0 = s_bb[2]; o.iz1 = s_bb[3];
+      chunks[c] = o;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// sort
+template <class T>
+__global__ void k_sort_key(GridP g, Particles<T> p, SortBufs sb, const Ctrl* ctrl) {
+  const int n = ctrl->count;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (p.w[i] == T(0)) { sb.key[i] = -1; return; }
+  int cx = (int)floor(p.x[i] / g.dx);
+  int cz = (int)floor((p.z[i] - g.z0) / g.dz);
+  cx = min(max(cx, 0), g.nx - 1);
+  cz = min(max(cz, 0), g.nz - 1);
+  const int tile = (cx / sb.tx) * sb.ntz + (cz / sb.tz);
+  const int r = atomicAdd(&sb.cell_cnt[(long)cx * g.nz + cz], 1);
+  const int bin = tile * sb.R + min(r, sb.R - 1);
+  sb.key[i] = bin;
+  sb.slot[i] = atomicAdd(&sb.bin_cnt[bin], 1);
+}
+
+template <class T>
+__global__ void k_sort_scatter(Particles<T> s, Particles<T> d, SortBufs sb, const Ctrl* ctrl) {
+  const int n = ctrl->count;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int key = sb.key[i];
+  if (key < 0) return;
+  const int o = sb.bin_start[key] + sb.slot[i];
+  d.x[o] = s.x[i]; d.z[o] = s.z[i];
+  d.ux[o] = s.ux[i]; d.uy[o] = s.uy[i]; d.uz[o] = s.uz[i];
+  d.w[o] = s.w[i]; d.id[o] = s.id[i];
+}
+
+__global__ void k_build_chunks(SortBufs sb, Chunk* chunks, Ctrl* ctrl, int chunk_max, int chunk_cap, int nx, int nz) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int ntiles = sb.ntx * sb.ntz;
+  if (t >= ntiles) return;
+  const int p0 = sb.bin_start[t * sb.R], p1 = sb.bin_start[(t + 1) * sb.R];
+  const int n = p1 - p0;
+  if (n <= 0) return;
+  const int nch = (n + chunk_max - 1) / chunk_max;
+  const int base = atomicAdd(&ctrl->nchunks, nch);
+  const int tx = t / sb.ntz, tz = t - tx * sb.ntz;
+  for (int j = 0; j < nch; j++) {
+    if (base + j >= chunk_cap) { atomicOr(&ctrl->status, ST_OVERFLOW); return; }
+    Chunk c;
+    c.p0 = p0 + j * chunk_max;
+    c.p1 = min(p1, p0 + (j + 1) * chunk_max);
+    c.ix0 = tx * sb.tx; c.ix1 = min(nx - 1, (tx + 1) * sb.tx - 1);
+    c.iz0 = tz * sb.tz; c.iz1 = min(nz - 1, (tz + 1) * sb.tz - 1);
+    chunks[base + j] = c;
+  }
+}
+
+__global__ void k_sort_finish_pre(Ctrl* ctrl) { ctrl->nchunks = 0; }
+__global__ void k_sort_finish(Ctrl* ctrl, const int* bin_start, int nbins) { ctrl->count = bin_start[nbins]; }
+
+// exclusive scan of n ints (n <= 1024*1024): block sums, scan of sums, local scans
+__global__ void k_scan_sums(const int* in, int n, int* sums) {
+  __shared__ int ws[32];
+  const int i = blockIdx.x * 1024 + threadIdx.x;
+  int v = i < n ? in[i] : 0;
+  v = __reduce_add_sync(0xffffffffu, v);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    int s = ws[threadIdx.x];
+    s = __reduce_add_sync(0xffffffffu, s);
+    if (threadIdx.x == 0) sums[blockIdx.x] = s;
+  }
+}
+
+__device__ int block_excl_scan(int v, int* total) {
+  __shared__ int ws[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) ws[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int s = lane < (blockDim.x >> 5) ? ws[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    ws[lane] = s;
+  }
+  __syncthreads();
+  int pre = (wid > 0 ? ws[wid - 1] : 0) + x - v;
+  if (total) *total = ws[(blockDim.x >> 5) - 1];
+  __syncthreads();
+  return pre;
+}
+
+__global__ void k_scan_top(int* sums, int nb) {
+  // single block of 1024 threads; nb <= 1024
+  int v = threadIdx.x < nb ? sums[threadIdx.x] : 0;
+  int pre = block_excl_scan(v, nullptr);
+  if (threadIdx.x < nb) sums[threadIdx.x] = pre;
+}
+
+__global__ void k_scan_local(const int* in, int n, const int* sums, int* out) {
+  const int i = blockIdx.x * 1024 + threadIdx.x;
+  int v = i < n ? in[i] : 0;
+  int total;
+  int pre = block_excl_scan(v, &total);
+  const int off = sums[blockIdx.x];
+  if (i < n) out[i] = off + pre;
+  if (i == n - 1) out[n] = off + pre + v;
+}
+
+// ---------------------------------------------------------------------------
+// plasma rows entering through the plane z_hi (or the initial load)
+__device__ double lab_density(const InjectP& ip, double zl) {
+  if (zl < ip.z_start_lab) return 0.0;
+  double r = zl - ip.z_start_lab;
+  if (ip.ramp_lab > 0.0 && r < ip.ramp_lab) return ip.n0 * r / ip.ramp_lab;
+  double pe = ip.ramp_lab + ip.length_lab;
+  if (ip.length_lab > 0.0 && r >= pe) return 0.0;
+  return ip.n0;
+}
+
+template <class T>
+__global__ void k_inject(GridP g, Particles<T> p, Chunk* chunks, Ctrl* ctrl, InjectP ip, int cap, int chunk_cap) {
+  const int xb = blockIdx.x, rb = blockIdx.y;
+  const int nxb = gridDim.x;
+  const long long nrows = ip.m_end - ip.m_beg;
+  const long long r0 = (long long)rb * ip.rblock;
+  const int nr = (int)min((long long)ip.rblock, nrows - r0);
+  const int ncx_dom = g.gx_hi - g.gx_lo;
+  const int cx0 = xb * ip.xblock;
+  const int ncx = min(ip.xblock, ncx_dom - cx0);
+  const int per_row = ncx * ip.ppc_x;
+  const int cnt = nr * per_row;
+  const int base = ctrl->count;
+  const long long start = (long long)base + r0 * ip.nxl + (long long)nr * cx0 * ip.ppc_x;
+  const double gdz = g.dz;
+  for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+    const int r = j / per_row, al = j - r * per_row;
+    const long long m = ip.m_beg + r0 + r;
+    const long long a = (long long)cx0 * ip.ppc_x + al;
+    const long long o = start + j;
+    if (o >= cap) { atomicOr(&ctrl->status, ST_OVERFLOW); continue; }
+    const double zlat = (m + 0.5) * ip.h;
+    const double n = ip.gamma * lab_density(ip, ip.gamma * zlat);
+    p.x[o] = (g.gx_lo + (a + 0.5) / ip.ppc_x) * g.dx;
+    p.z[o] = zlat - ip.beta * kC * ip.t;
+    p.ux[o] = T(0); p.uy[o] = T(0);
+    p.uz[o] = T(-ip.gamma * ip.beta * kC);
+    p.w[o] = T(n * g.dx * gdz / (double)(ip.ppc_x * ip.ppc_z));
+    p.id[o] = (uint32_t)((unsigned long long)m * (unsigned long long)ip.nxl + (unsigned long long)a);
+  }
+  if (threadIdx.x == 0 && cnt > 0) {
+    const int ci = ctrl->nchunks + rb * nxb + xb;
+    if (ci >= chunk_cap || start + cnt > cap) { atomicOr(&ctrl->status, ST_OVERFLOW); return; }
+    Chunk c;
+    c.p0 = (int)start; c.p1 = (int)(start + cnt);
+    c.ix0 = g.gx_lo + cx0; c.ix1 = g.gx_lo + cx0 + ncx - 1;
+    const double za = ((ip.m_beg + r0 + 0.5) * ip.h - ip.beta * kC * ip.t - g.z0) / gdz;
+    const double zb = ((ip.m_beg + r0 + nr - 1 + 0.5) * ip.h - ip.beta * kC * ip.t - g.z0) / gdz;
+    c.iz0 = (int)floor(za); c.iz1 = (int)floor(zb);
+    chunks[ci] = c;
+  }
+}
+
+__global__ void k_add_counts(Ctrl* ctrl, int dcount, int dchunks) {
+  ctrl->count += dcount;
+  ctrl->nchunks += dchunks;
+}
+
+}  // namespace
+
+template <class T>
+void launch_push(const GridP& g, const FieldPtrs<T>& f, Particles<T> p, Chunk* chunks, Ctrl* ctrl, int order,
+                 int grid_blocks, int smem_nodes, double q, double m, cudaStream_t s) {
+  PushConst pc;
+  pc.dx = g.dx; pc.dz = g.dz; pc.dt = g.dt; pc.z0 = g.z0;
+  pc.xlo = g.gx_lo * g.dx; pc.xhi = g.gx_hi * g.dx;
+  pc.zlo = g.z0 + g.gz_lo * g.dz; pc.zhi = g.z0 + g.gz_hi * g.dz + g.dz;
+  pc.qm_half = q * g.dt / (2.0 * m);
+  pc.q = q;
+  const size_t sm = (size_t)9 * smem_nodes * sizeof(T);
+  cudaMemsetAsync(&ctrl->next_chunk, 0, sizeof(int), s);
+  if (order == 3) {
+    cudaFuncSetAttribute(k_push<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_push<T, 3><<<grid_blocks, PB_THREADS, sm, s>>>(g, f, p, chunks, ctrl, smem_nodes, pc);
+  } else {
+    cudaFuncSetAttribute(k_push<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_push<T, 1><<<grid_blocks, PB_THREADS, sm, s>>>(g, f, p, chunks, ctrl, smem_nodes, pc);
+  }
+}
+
+int push_occupancy(int order, bool dbl, int smem_nodes) {
+  int nb = 0;
+  if (dbl) {
+    size_t sm = (size_t)9 * smem_nodes * sizeof(double);
+    if (order == 3) {
+      cudaFuncSetAttribute(k_push<double, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_push<double, 3>, PB_THREADS, sm);
+    } else {
+      cudaFuncSetAttribute(k_push<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_push<double, 1>, PB_THREADS, sm);
+    }
+  } else {
+    size_t sm = (size_t)9 * smem_nodes * sizeof(float);
+    if (order == 3) {
+      cudaFuncSetAttribute(k_push<float, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_push<float, 3>, PB_THREADS, sm);
+    } else {
+      cudaFuncSetAttribute(k_push<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_push<float, 1>, PB_THREADS, sm);
+    }
+  }
+  return nb > 0 ? nb : 1;
+}
+
+static void exclusive_scan(const int* in, int n, int* out, int* tmp, cudaStream_t s) {
+  const int nb = (n + 1023) / 1024;
+  k_scan_sums<<<nb, 1024, 0, s>>>(in, n, tmp);
+  k_scan_top<<<1, 1024, 0, s>>>(tmp, nb);
+  k_scan_local<<<nb, 1024, 0, s>>>(in, n, tmp, out);
+}
+
+template <class T>
+void launch_sort(const GridP& g, Particles<T> src, Particles<T> dst, SortBufs sb, Chunk* chunks, Ctrl* ctrl, int cap,
+                 int chunk_max, int chunk_cap, cudaStream_t s) {
+  const int nbins = sb.ntx * sb.ntz * sb.R;
+  cudaMemsetAsync(sb.cell_cnt, 0, sizeof(int) * (size_t)g.nx * g.nz, s);
+  cudaMemsetAsync(sb.bin_cnt, 0, sizeof(int) * (size_t)(nbins + 1), s);
+  const int nb = (cap + 255) / 256;
+  k_sort_key<T><<<nb, 256, 0, s>>>(g, src, sb, ctrl);
+  exclusive_scan(sb.bin_cnt, nbins, sb.bin_start, sb.scan_tmp, s);
+  k_sort_scatter<T><<<nb, 256, 0, s>>>(src, dst, sb, ctrl);
+  k_sort_finish_pre<<<1, 1, 0, s>>>(ctrl);
+  const int ntiles = sb.ntx * sb.ntz;
+  k_build_chunks<<<(ntiles + 255) / 256, 256, 0, s>>>(sb, chunks, ctrl, chunk_max, chunk_cap, g.nx, g.nz);
+  k_sort_finish<<<1, 1, 0, s>>>(ctrl, sb.bin_start, nbins);
+}
+
+template <class T>
+void launch_inject(const GridP& g, Particles<T> p, Chunk* chunks, Ctrl* ctrl, const InjectP& ip, int cap,
+                   int chunk_cap, cudaStream_t s) {
+  const long long nrows = ip.m_end - ip.m_beg;
+  if (nrows <= 0) return;
+  const int ncx = g.gx_hi - g.gx_lo;
+  dim3 grd((ncx + ip.xblock - 1) / ip.xblock, (unsigned)((nrows + ip.rblock - 1) / ip.rblock));
+  k_inject<T><<<grd, 256, 0, s>>>(g, p, chunks, ctrl, ip, cap, chunk_cap);
+  launch_add_counts(ctrl, (int)(nrows * ip.nxl), (int)(grd.x * grd.y), s);
+}
+
+void launch_add_counts(Ctrl* ctrl, int dcount, int dchunks, cudaStream_t s) {
+  k_add_counts<<<1, 1, 0, s>>>(ctrl, dcount, dchunks);
+}
+
+#define INST(T)                                                                                                 \
+  template void launch_push<T>(const GridP&, const FieldPtrs<T>&, Particles<T>, Chunk*, Ctrl*, int, int, int,   \
+                               double, double, cudaStream_t);                                                   \
+  template void launch_sort<T>(const GridP&, Particles<T>, Particles<T>, SortBufs, Chunk*, Ctrl*, int, int, int,\
+                               cudaStream_t);                                                                   \
+  template void launch_inject<T>(const GridP&, Particles<T>, Chunk*, Ctrl*, const InjectP&, int, int, cudaStream_t);
+INST(float)
+INST(double)
+#undef INST
+
+}  // namespace picgb

@@ -1,0 +1,230 @@
+"""Python-side handle of one library context (marshalling through capi.py).
+
+``Simulation(workload)`` creates a context from a workload dict (see
+workloads.py): pic_init + pic_load_plasma + pic_inject_laser, with device
+memory from torch's caching allocator on torch's current CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import capi
+
+_D = ctypes.POINTER(ctypes.c_double)
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(_D)
+
+
+class PicError(RuntimeError):
+    pass
+
+
+class Simulation:
+    def __init__(self, w: dict, precision: str | None = None, stream=None, tile=None, sort_every: int = 0,
+                 use_torch_allocator: bool = True):
+        import torch
+        if not torch.cuda.is_available():
+            raise PicError("a CUDA device is required (the library has no CPU path)")
+        self.L = capi.load()
+        self.w = dict(w)
+        self.torch = torch
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        prec = precision or w.get("precision", "fp64")
+        self.precision = capi.PIC_FP64 if prec == "fp64" else capi.PIC_MIXED
+        self.nx, self.nz = int(w["nx"]), int(w["nz"])
+        c = capi.PicConfig()
+        c.struct_size = ctypes.sizeof(capi.PicConfig)
+        c.version = capi.API_VERSION
+        c.dim = 2
+        c.nx, c.nz = self.nx, self.nz
+        c.dz_lab, c.dx = float(w["dz_lab"]), float(w["dx"])
+        c.gamma_boost = float(w.get("gamma_boost", 1.0))
+        c.courant = float(w.get("courant", 0.9))
+        c.dt = float(w.get("dt", 0.0) or 0.0)
+        c.ck_alpha, c.ck_beta, c.ck_gamma = (float(v) for v in w.get("solver", (1.0, 0.0, 0.0)))
+        c.theta = float(w.get("theta", 0.0))
+        c.pml_cells = int(w.get("pml_cells", 0))
+        c.pml_sigma_max = float(w.get("pml_sigma_max", 4.0))
+        c.pml_delta = float(w.get("pml_delta", 5.0))
+        c.pml_power = float(w.get("pml_power", 2.0))
+        c.pml_xi_exp = int(w.get("pml_xi_exp", 1))
+        c.filter_passes = int(w.get("filter_passes", 0))
+        c.filter_stride = int(w.get("filter_stride", 1))
+        c.filter_compensate = int(w.get("filter_compensate", 0))
+        c.filter_J = int(w.get("filter_J", 0))
+        c.filter_gather = int(w.get("filter_gather", 0))
+        c.shape_order = int(w.get("order", 3))
+        c.particle_guard = int(w.get("particle_guard", -1))
+        c.precision = self.precision
+        c.moving_window = int(w.get("moving_window", 0))
+        c.window_beta = float(w.get("window_beta", 0.0))
+        if tile:
+            c.tile_x, c.tile_z = int(tile[0]), int(tile[1])
+        c.sort_every = int(sort_every)
+        self._cfg = c
+        self._keep = []
+        if use_torch_allocator:
+            dev = self.device.index
+
+            def _alloc(nbytes, stream, user):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(nbytes), dev, stream)
+                except Exception:
+                    return None
+
+            def _free(ptr, nbytes, stream, user):
+                torch.cuda.caching_allocator_delete(ptr)
+
+            self._alloc_cb = capi.ALLOC_FN(_alloc)
+            self._free_cb = capi.FREE_FN(_free)
+        else:
+            self._alloc_cb = capi.ALLOC_FN()
+            self._free_cb = capi.FREE_FN()
+        h = ctypes.c_void_p()
+        r = self.L.pic_init(ctypes.byref(c), self._alloc_cb, self._free_cb, None,
+                            ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        if r != 0:
+            raise PicError(f"pic_init failed: {capi.STATUS_NAMES.get(r, r)}")
+        self.h = h
+        if w.get("plasma") or w.get("beam"):
+            self.load_plasma(w.get("plasma"), w.get("beam"))
+        if w.get("laser"):
+            self.inject_laser(w["laser"])
+
+    # ------------------------------------------------------------------
+    def _check(self, r: int, what: str):
+        if r != 0:
+            msg = self.L.pic_last_error(self.h).decode()
+            raise PicError(f"{what} failed: {capi.STATUS_NAMES.get(r, r)} {msg}")
+
+    def load_plasma(self, p: dict | None, beam: dict | None = None):
+        pl = capi.PicPlasma()
+        pl.struct_size = ctypes.sizeof(capi.PicPlasma)
+        pl.version = capi.API_VERSION
+        if p:
+            pl.n0 = float(p["n0"])
+            pl.z_start_lab = float(p.get("z_start_lab", 0.0))
+            pl.ramp_lab = float(p.get("ramp_lab", 0.0))
+            pl.length_lab = float(p.get("length_lab", 0.0))
+            pl.ppc_x, pl.ppc_z = int(p["ppc_x"]), int(p["ppc_z"])
+            pl.ions = int(p.get("ions", 1))
+        else:
+            pl.ppc_x = pl.ppc_z = 1
+        if beam:
+            arrs = [np.ascontiguousarray(beam[k], dtype=np.float64) for k in ("x", "z", "ux", "uy", "uz")]
+            self._keep.append(arrs)
+            pl.beam_n = arrs[0].size
+            pl.beam_x, pl.beam_z, pl.beam_ux, pl.beam_uy, pl.beam_uz = (_p(a) for a in arrs)
+            pl.beam_t_lab = float(beam.get("t_lab", 0.0))
+            pl.beam_z_plane_lab = float(beam["z_plane_lab"])
+        self._check(self.L.pic_load_plasma(self.h, ctypes.byref(pl)), "pic_load_plasma")
+
+    def inject_laser(self, l: dict):
+        la = capi.PicLaser()
+        la.struct_size = ctypes.sizeof(capi.PicLaser)
+        la.version = capi.API_VERSION
+        la.lambda0, la.a0, la.w0 = float(l["lambda0"]), float(l["a0"]), float(l["w0"])
+        la.tau_fwhm, la.t_peak = float(l["tau_fwhm"]), float(l.get("t_peak", 0.0))
+        la.x_center = float(l.get("x_center", 0.5 * self.nx * float(self.w["dx"])))
+        la.phase, la.z_antenna, la.beta_s = float(l.get("phase", 0.0)), float(l["z_antenna"]), float(l.get("beta_s", 0.0))
+        self._check(self.L.pic_inject_laser(self.h, ctypes.byref(la)), "pic_inject_laser")
+
+    def step(self, n: int = 1):
+        self._check(self.L.pic_step(self.h, int(n)), "pic_step")
+
+    def sync(self):
+        self._check(self.L.pic_sync(self.h), "pic_sync")
+
+    def field(self, comp: int) -> np.ndarray:
+        out = np.zeros((self.nx + 1) * (self.nz + 1))
+        self._check(self.L.pic_get_field(self.h, comp, _p(out), 0), "pic_get_field")
+        return out.reshape(self.nx + 1, self.nz + 1)
+
+    def field_device(self, comp: int):
+        t = self.torch.empty((self.nx + 1, self.nz + 1), dtype=self.torch.float64, device=self.device)
+        ptr = ctypes.cast(ctypes.c_void_p(t.data_ptr()), _D)
+        self._check(self.L.pic_get_field(self.h, comp, ptr, 1), "pic_get_field")
+        return t
+
+    def set_field(self, comp: int, a: np.ndarray):
+        a = np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+        self._check(self.L.pic_set_field(self.h, comp, _p(a)), "pic_set_field")
+
+    def particles(self, species: int = capi.ELECTRONS) -> dict:
+        n = ctypes.c_int64(0)
+        self._check(self.L.pic_get_particles(self.h, species, None, None, None, None, None, None, None, None,
+                                             ctypes.byref(n)), "pic_get_particles")
+        cnt = max(int(n.value), 1)
+        a = {k: np.zeros(cnt) for k in ("x", "z", "ux", "uy", "uz", "w")}
+        ids = np.zeros(cnt, dtype=np.uint32)
+        fl = np.zeros(cnt, dtype=np.int32)
+        n = ctypes.c_int64(cnt)
+        self._check(self.L.pic_get_particles(self.h, species, *(_p(a[k]) for k in ("x", "z", "ux", "uy", "uz", "w")),
+                                             ids.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                                             fl.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ctypes.byref(n)),
+                    "pic_get_particles")
+        m = int(n.value)
+        out = {k: v[:m] for k, v in a.items()}
+        out["id"] = ids[:m]
+        out["alive"] = (fl[:m] & 1) != 0
+        out["active"] = (fl[:m] & 2) != 0
+        return out
+
+    def stats(self) -> dict:
+        s = capi.PicStats()
+        s.struct_size = ctypes.sizeof(capi.PicStats)
+        s.version = capi.API_VERSION
+        self._check(self.L.pic_get_stats(self.h, ctypes.byref(s)), "pic_get_stats")
+        return {k: getattr(s, k) for k, _ in capi.PicStats._fields_ if k not in ("struct_size", "version")}
+
+    def btd_set(self, z_lab: np.ndarray, t_lab: np.ndarray):
+        z = np.ascontiguousarray(z_lab, dtype=np.float64)
+        t = np.ascontiguousarray(t_lab, dtype=np.float64)
+        r = capi.PicBtdReq()
+        r.struct_size = ctypes.sizeof(capi.PicBtdReq)
+        r.version = capi.API_VERSION
+        r.n_rows = z.size
+        r.z_lab, r.t_lab = _p(z), _p(t)
+        self._btd_rows = z.size
+        self._check(self.L.pic_boosted_to_lab_diag(self.h, ctypes.byref(r), None), "pic_boosted_to_lab_diag")
+
+    def btd_get(self):
+        n = self._btd_rows
+        dt = np.float64 if self.precision == capi.PIC_FP64 else np.float32
+        data = np.zeros(n * 6 * (self.nx + 1), dtype=dt)
+        done = np.zeros(2 * n, dtype=np.int32)
+        o = capi.PicBtdOut()
+        o.struct_size = ctypes.sizeof(capi.PicBtdOut)
+        o.version = capi.API_VERSION
+        o.data = data.ctypes.data_as(ctypes.c_void_p)
+        o.done = done.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        o.on_device = 0
+        self._check(self.L.pic_boosted_to_lab_diag(self.h, None, ctypes.byref(o)), "pic_boosted_to_lab_diag")
+        return data.reshape(n, 6, self.nx + 1).astype(np.float64), done.reshape(n, 2)
+
+    def launches(self) -> int:
+        return int(self.L.pic_kernel_launches(self.h))
+
+    def timing(self, enable: bool, which: int = 0):
+        ms = ctypes.c_double(0.0)
+        nl = ctypes.c_int64(0)
+        self._check(self.L.pic_kernel_timing(self.h, int(enable), int(which), ctypes.byref(ms), ctypes.byref(nl)),
+                    "pic_kernel_timing")
+        return ms.value, nl.value
+
+    def close(self):
+        h = getattr(self, "h", None)
+        if h:
+            self.L.pic_free(h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

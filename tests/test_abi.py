@@ -1,0 +1,42 @@
+"""The C ABI library builds, loads on a CPU-only host and exports every symbol of include/pic.h."""
+import ctypes
+import os
+import re
+
+from paper_1009_2727_gb300 import capi
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "pic.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pic_[a-z_]+)\s*\(", src)) - {"pic_alloc_fn", "pic_free_fn"})
+
+
+def test_library_exports_every_declared_symbol():
+    L = capi.load()
+    names = declared_functions()
+    assert len(names) >= 14
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+    assert set(names) == set(capi.EXPORTS)
+
+
+def test_struct_layouts_match_header_sizes():
+    # field counts of the ctypes mirrors track the header declarations
+    src = open(os.path.join(ROOT, "include", "pic.h")).read()
+    assert "PIC_API_VERSION 1" in src and capi.API_VERSION == 1
+    assert ctypes.sizeof(capi.PicConfig) % 8 == 0
+    assert ctypes.sizeof(capi.PicStats) > 100
+
+
+def test_init_rejects_bad_config_without_gpu_work():
+    L = capi.load()
+    c = capi.PicConfig()
+    c.struct_size = 3        # wrong size: rejected before any CUDA call
+    c.version = capi.API_VERSION
+    h = ctypes.c_void_p()
+    r = L.pic_init(ctypes.byref(c), capi.ALLOC_FN(), capi.FREE_FN(), None, None, ctypes.byref(h))
+    assert r == capi.PIC_EINVAL and not h.value
+    assert L.pic_free(None) == capi.PIC_OK
