@@ -830,11 +830,15 @@ int orc_btd_get(const orc_sim* s, double* out, int* done) {
 /* ------------------------------------------------------------------ */
 /* moving window (Sec. 2: lab-frame runs follow the wake): the grid moves by
  * whole cells; fields are shifted toward -z and zero-filled at +z. */
-static void shift_array(orc_sim* s, double* F, long sh) {
+static void shift_array(orc_sim* s, double* F, long sh, int comp) {
+  int i0, i1, k0, k1;
+  vrange(s, comp, &i0, &i1, &k0, &k1);
   for (int i = 0; i <= s->c.nx; i++)
     for (int k = 0; k <= s->c.nz; k++) {
       long kk = k + sh;
-      F[IDX(s, i, k)] = kk <= s->c.nz ? F[IDX(s, i, (int)kk)] : 0.0;
+      double v = kk <= s->c.nz ? F[IDX(s, i, (int)kk)] : 0.0;
+      /* the PEC walls move with the grid: values stay on the component's valid range */
+      F[IDX(s, i, k)] = (i >= i0 && i <= i1 && k >= k0 && k <= k1) ? v : 0.0;
     }
 }
 
@@ -844,9 +848,10 @@ static void window_shift(orc_sim* s) {
   long want = (long)floor(s->c.window_beta * O_C * t / s->dz);
   long sh = want - s->shifts;
   if (sh <= 0) return;
-  for (int c = 0; c < 6; c++) shift_array(s, s->F[c], sh);
-  for (int c = 0; c < 3; c++) { shift_array(s, s->Ep[c], sh); shift_array(s, s->Eb[c], sh); }
-  shift_array(s, s->Byx, sh); shift_array(s, s->Byz, sh); shift_array(s, s->Eyx, sh); shift_array(s, s->Eyz, sh);
+  for (int c = 0; c < 6; c++) shift_array(s, s->F[c], sh, c);
+  for (int c = 0; c < 3; c++) { shift_array(s, s->Ep[c], sh, c); shift_array(s, s->Eb[c], sh, c); }
+  shift_array(s, s->Byx, sh, OBY); shift_array(s, s->Byz, sh, OBY);
+  shift_array(s, s->Eyx, sh, OEY); shift_array(s, s->Eyz, sh, OEY);
   s->shifts = want;
   s->z0 = want * s->dz;
 }
