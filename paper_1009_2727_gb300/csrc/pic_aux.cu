@@ -282,7 +282,13 @@ __global__ void k_rho(GridP g, Particles<T> p, const Ctrl* ctrl, int order, doub
   if (j >= ctrl->count) return;
   const double w = (double)p.w[j];
   if (w == 0.0) return;
-  const double X = p.x[j] / g.dx, Z = (p.z[j] - g.z0) / g.dz;
+  double X, Z;
+  if constexpr (CellPos<T>::value) {
+    X = cell_x(p.cell[j]) + (double)p.ox[j];
+    Z = cell_z(p.cell[j]) + (double)p.oz[j];
+  } else {
+    X = p.x[j] / g.dx; Z = (p.z[j] - g.z0) / g.dz;
+  }
   const int fx = (int)floor(X), fz = (int)floor(Z);
   for (int i = fx - 2; i <= fx + 3; i++)
     for (int k = fz - 2; k <= fz + 3; k++) {
@@ -331,11 +337,15 @@ __global__ void k_stats(GridP g, FieldPtrs<T> f, Particles<T> p, const Ctrl* ctr
 }
 
 template <class T>
-__global__ void k_shift_copy(GridP g, const T* src, T* dst, int sh) {
+__global__ void k_shift_copy(GridP g, const T* src, T* dst, int sh, int comp) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = blockIdx.y;
   if (k > g.nz) return;
-  dst[(long)i * g.ld + k] = k + sh <= g.nz ? src[(long)i * g.ld + k + sh] : T(0);
+  int i0, i1, k0, k1;
+  valid_range(comp, g.nx, g.nz, i0, i1, k0, k1);
+  // the PEC walls move with the grid: values stay on the component's valid range
+  const bool v = i >= i0 && i <= i1 && k >= k0 && k <= k1;
+  dst[(long)i * g.ld + k] = (v && k + sh <= g.nz) ? src[(long)i * g.ld + k + sh] : T(0);
 }
 
 __global__ void k_shift_chunks(Chunk* c, const Ctrl* ctrl, int sh) {
@@ -361,19 +371,37 @@ __global__ void k_convert_back(const double* src, T* dst, GridP g) {
 }
 
 template <class T>
-__global__ void k_compact(Particles<T> p, const Ctrl* ctrl, double* out6, uint32_t* ido, int* nout, int cap_out) {
+__global__ void k_compact(GridP g, Particles<T> p, const Ctrl* ctrl, double* out6, uint32_t* ido, int* nout,
+                          int cap_out) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= ctrl->count) return;
   if (p.w[j] == T(0)) return;
   const int o = atomicAdd(nout, 1);
   if (o >= cap_out) return;
-  out6[0 * (size_t)cap_out + o] = p.x[j];
-  out6[1 * (size_t)cap_out + o] = p.z[j];
+  if constexpr (CellPos<T>::value) {
+    out6[0 * (size_t)cap_out + o] = (cell_x(p.cell[j]) + (double)p.ox[j]) * g.dx;
+    out6[1 * (size_t)cap_out + o] = g.z0 + (cell_z(p.cell[j]) + (double)p.oz[j]) * g.dz;
+  } else {
+    out6[0 * (size_t)cap_out + o] = p.x[j];
+    out6[1 * (size_t)cap_out + o] = p.z[j];
+  }
   out6[2 * (size_t)cap_out + o] = p.ux[j];
   out6[3 * (size_t)cap_out + o] = p.uy[j];
   out6[4 * (size_t)cap_out + o] = p.uz[j];
   out6[5 * (size_t)cap_out + o] = p.w[j];
   ido[o] = p.id[j];
+}
+
+// moving window: grid-relative cells of the mixed path follow the grid
+template <class T>
+__global__ void k_shift_particles(Particles<T> p, const Ctrl* ctrl, int sh) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= ctrl->count) return;
+  if (p.w[j] == T(0)) return;
+  const uint32_t c = p.cell[j];
+  const int iz = cell_z(c) - sh;
+  if (iz < 0) { p.w[j] = T(0); return; }
+  p.cell[j] = pack_cell(cell_x(c), iz);
 }
 
 }  // namespace
@@ -437,9 +465,9 @@ void launch_stats(const GridP& g, const FieldPtrs<T>& f, Particles<T> p, const C
 }
 
 template <class T>
-void launch_shift(const GridP& g, T* arr, T* tmp, int sh, cudaStream_t s) {
+void launch_shift(const GridP& g, T* arr, T* tmp, int sh, int comp, cudaStream_t s) {
   dim3 grd((g.nz + 1 + 255) / 256, g.nx + 1);
-  k_shift_copy<T><<<grd, 256, 0, s>>>(g, arr, tmp, sh);
+  k_shift_copy<T><<<grd, 256, 0, s>>>(g, arr, tmp, sh, comp);
   cudaMemcpyAsync(arr, tmp, sizeof(T) * (size_t)(g.nx + 1) * g.ld, cudaMemcpyDeviceToDevice, s);
 }
 
@@ -460,11 +488,18 @@ void launch_convert_back(const double* src, T* dst, const GridP& g, cudaStream_t
 }
 
 template <class T>
-void launch_compact_copy(Particles<T> p, const Ctrl* ctrl, int cap, double* out6, uint32_t* id_out, int* nout,
-                         cudaStream_t s) {
+void launch_compact_copy(const GridP& g, Particles<T> p, const Ctrl* ctrl, int cap, double* out6, uint32_t* id_out,
+                         int* nout, cudaStream_t s) {
   cudaMemsetAsync(nout, 0, sizeof(int), s);
   if (cap <= 0) return;
-  k_compact<T><<<(cap + 255) / 256, 256, 0, s>>>(p, ctrl, out6, id_out, nout, cap);
+  k_compact<T><<<(cap + 255) / 256, 256, 0, s>>>(g, p, ctrl, out6, id_out, nout, cap);
+}
+
+template <class T>
+void launch_shift_particles(Particles<T> p, const Ctrl* ctrl, int cap, int sh, cudaStream_t s) {
+  if constexpr (CellPos<T>::value) {
+    if (cap > 0) k_shift_particles<T><<<(cap + 255) / 256, 256, 0, s>>>(p, ctrl, sh);
+  }
 }
 
 #define INST(T)                                                                                                   \
@@ -478,10 +513,12 @@ void launch_compact_copy(Particles<T> p, const Ctrl* ctrl, int cap, double* out6
   template void launch_rho<T>(const GridP&, Particles<T>, const Ctrl*, int, int, double, double*, cudaStream_t);  \
   template void launch_stats<T>(const GridP&, const FieldPtrs<T>&, Particles<T>, const Ctrl*, int, Beam<T>,       \
                                 double, double, double*, cudaStream_t);                                           \
-  template void launch_shift<T>(const GridP&, T*, T*, int, cudaStream_t);                                        \
+  template void launch_shift<T>(const GridP&, T*, T*, int, int, cudaStream_t);                                        \
   template void launch_convert<T>(const T*, double*, const GridP&, cudaStream_t);                                \
   template void launch_convert_back<T>(const double*, T*, const GridP&, cudaStream_t);                           \
-  template void launch_compact_copy<T>(Particles<T>, const Ctrl*, int, double*, uint32_t*, int*, cudaStream_t);
+  template void launch_compact_copy<T>(const GridP&, Particles<T>, const Ctrl*, int, double*, uint32_t*, int*,      \
+                                       cudaStream_t);                                                             \
+  template void launch_shift_particles<T>(Particles<T>, const Ctrl*, int, int, cudaStream_t);
 INST(float)
 INST(double)
 #undef INST

@@ -163,16 +163,18 @@ struct Sim : SimBase {
     filt_J = cf.filter_J && cf.filter_passes + cf.filter_compensate > 0;
     fs.passes = cf.filter_passes; fs.stride = cf.filter_stride; fs.compensate = cf.filter_compensate;
     const size_t N = (size_t)(cf.nx + 1) * g.ld;
+    g.cs = (long)N;
     auto grid = [&]() { return al<T>(N); };
-    for (int q = 0; q < 3; q++) {
-      f.E[q] = grid(); f.Eo[q] = grid(); f.B[q] = grid(); f.J[q] = grid(); f.Jn[q] = grid();
-      f.Bavg[q] = grid();
-      if (friedman) { f.Eb[q] = grid(); f.Ebn[q] = grid(); }
-      if (filt_gather) { f.fE[q] = grid(); f.fB[q] = grid(); }
-      if (!f.E[q] || !f.Eo[q] || !f.B[q] || !f.J[q] || !f.Jn[q] || !f.Bavg[q]) return c->fail(PIC_ENOMEM, "field allocation failed");
-      if (friedman && (!f.Eb[q] || !f.Ebn[q])) return c->fail(PIC_ENOMEM, "field allocation failed");
-      if (filt_gather && (!f.fE[q] || !f.fB[q])) return c->fail(PIC_ENOMEM, "field allocation failed");
-    }
+    // 3-component blocks (component stride N): E, E-other, B, J, J-other, Bavg, gather copies, E-bar
+    auto block = [&](T** dst) {
+      T* b = al<T>(3 * N);
+      for (int q = 0; q < 3; q++) dst[q] = b ? b + q * N : nullptr;
+      return b != nullptr;
+    };
+    bool ok = block(f.E) && block(f.Eo) && block(f.B) && block(f.J) && block(f.Jn) && block(f.Bavg);
+    if (friedman) ok = ok && block(f.Eb) && block(f.Ebn);
+    if (filt_gather) ok = ok && block(f.fE) && block(f.fB);
+    if (!ok) return c->fail(PIC_ENOMEM, "field allocation failed");
     if (cf.pml_cells > 0) {
       f.Byx = grid(); f.Byz = grid(); f.Eyx = grid(); f.Eyz = grid();
       if (!f.Byx || !f.Byz || !f.Eyx || !f.Eyz) return c->fail(PIC_ENOMEM, "PML allocation failed");
@@ -280,12 +282,20 @@ struct Sim : SimBase {
     if (pl.n0 <= 0.0) want = 4096;
     if (want > 2000000000LL) return c->fail(PIC_EOVERFLOW, "particle capacity above 2^31");
     cap = (int)want;
+    if (CellPos<T>::value && (cf.nx >= 65535 || cf.nz >= 65535)) return c->fail(PIC_EINVAL, "mixed precision needs nx, nz < 65535");
     Particles<T>* both[2] = {&P, &P2};
     for (Particles<T>* q : both) {
-      q->x = al<double>(cap); q->z = al<double>(cap);
+      bool okp;
+      if (CellPos<T>::value) {
+        q->cell = al<uint32_t>(cap); q->ox = al<float>(cap); q->oz = al<float>(cap);
+        okp = q->cell && q->ox && q->oz;
+      } else {
+        q->x = al<double>(cap); q->z = al<double>(cap);
+        okp = q->x && q->z;
+      }
       q->ux = al<T>(cap); q->uy = al<T>(cap); q->uz = al<T>(cap); q->w = al<T>(cap);
       q->id = al<uint32_t>(cap);
-      if (!q->x || !q->z || !q->ux || !q->uy || !q->uz || !q->w || !q->id) return c->fail(PIC_ENOMEM, "particle allocation failed");
+      if (!okp || !q->ux || !q->uy || !q->uz || !q->w || !q->id) return c->fail(PIC_ENOMEM, "particle allocation failed");
     }
     const int ntiles = sb.ntx * sb.ntz;
     const int inj_chunks = ((g.gx_hi - g.gx_lo + ip.xblock - 1) / ip.xblock) * 4;
@@ -411,17 +421,22 @@ struct Sim : SimBase {
     long long sh = want - shifts;
     if (sh <= 0) return;
     for (int q = 0; q < 3; q++) {
-      launch_shift<T>(g, f.E[q], tmp, (int)sh, c->stream);
-      launch_shift<T>(g, f.Eo[q], tmp, (int)sh, c->stream);
-      launch_shift<T>(g, f.B[q], tmp, (int)sh, c->stream);
-      if (friedman) launch_shift<T>(g, f.Eb[q], tmp, (int)sh, c->stream);
+      launch_shift<T>(g, f.E[q], tmp, (int)sh, EX + q, c->stream);
+      launch_shift<T>(g, f.Eo[q], tmp, (int)sh, EX + q, c->stream);
+      launch_shift<T>(g, f.B[q], tmp, (int)sh, BX + q, c->stream);
+      if (friedman) launch_shift<T>(g, f.Eb[q], tmp, (int)sh, EX + q, c->stream);
       c->launches += friedman ? 4 : 3;
     }
     if (cf.pml_cells > 0) {
       T* arrs[4] = {f.Byx, f.Byz, f.Eyx, f.Eyz};
-      for (int q = 0; q < 4; q++) { launch_shift<T>(g, arrs[q], tmp, (int)sh, c->stream); c->launches++; }
+      const int comps[4] = {BY, BY, EY, EY};
+      for (int q = 0; q < 4; q++) { launch_shift<T>(g, arrs[q], tmp, (int)sh, comps[q], c->stream); c->launches++; }
     }
-    if (loaded && chunks) { launch_shift_chunks(chunks, ctrl, (int)sh, chunk_cap, c->stream); c->launches++; }
+    if (loaded && chunks) {
+      launch_shift_chunks(chunks, ctrl, (int)sh, chunk_cap, c->stream);
+      launch_shift_particles<T>(P, ctrl, cap, (int)sh, c->stream);
+      c->launches += CellPos<T>::value ? 2 : 1;
+    }
     shifts = want;
     g.z0 = (double)want * g.dz;
   }
@@ -648,7 +663,7 @@ struct Sim : SimBase {
     uint32_t* ido = al<uint32_t>(cap);
     int* nout = al<int>(1);
     if (!out6 || !ido || !nout) return c->fail(PIC_ENOMEM, "staging allocation failed");
-    launch_compact_copy<T>(P, ctrl, cap, out6, ido, nout, c->stream);
+    launch_compact_copy<T>(g, P, ctrl, cap, out6, ido, nout, c->stream);
     int hn = 0;
     cudaStreamSynchronize(c->stream);
     cudaMemcpy(&hn, nout, 4, cudaMemcpyDeviceToHost);

@@ -22,6 +22,7 @@ enum StatusBits : int { ST_OVERFLOW = 1, ST_NAN = 2, ST_OUTSIDE = 4, ST_TIMEOUT 
 // Geometry passed by value to every kernel.
 struct GridP {
   int nx, nz, ld;            // cells; row stride (elements) of every grid array
+  long cs;                   // stride between the components of a 3-component block
   double dx, dz, dt;
   double z0;                 // grid origin along z (moving window)
   int gx_lo, gx_hi, gz_lo, gz_hi;  // particle domain (cells)
@@ -73,12 +74,25 @@ struct Chunk {
   int ix0, ix1, iz0, iz1;
 };
 
+// Particle storage (structure of arrays). The FP64 path keeps absolute
+// positions; the mixed path keeps the grid-relative cell (iz | ix << 16) and
+// the FP32 offset inside the cell, so that its push needs no FP64 arithmetic.
 template <class T>
 struct Particles {
-  double* x; double* z;
+  double* x; double* z;          // FP64 path [m]
+  uint32_t* cell;                // mixed path
+  float* ox; float* oz;          // mixed path, offsets in [0, 1)
   T* ux; T* uy; T* uz; T* w;
   uint32_t* id;
 };
+template <class T>
+struct CellPos { static constexpr bool value = false; };
+template <>
+struct CellPos<float> { static constexpr bool value = true; };
+
+__host__ __device__ inline uint32_t pack_cell(int ix, int iz) { return (uint32_t)iz | ((uint32_t)ix << 16); }
+__host__ __device__ inline int cell_x(uint32_t c) { return (int)(c >> 16); }
+__host__ __device__ inline int cell_z(uint32_t c) { return (int)(c & 0xffffu); }
 
 // Control block in device memory.
 struct Ctrl {
@@ -188,14 +202,16 @@ template <class T>
 void launch_stats(const GridP& g, const FieldPtrs<T>& f, Particles<T> p, const Ctrl* ctrl, int cap, Beam<T> b,
                   double gamma, double beta, double* out, cudaStream_t s);
 template <class T>
-void launch_shift(const GridP& g, T* arr, T* tmp, int sh, cudaStream_t s);
+void launch_shift(const GridP& g, T* arr, T* tmp, int sh, int comp, cudaStream_t s);
 void launch_shift_chunks(Chunk* chunks, Ctrl* ctrl, int sh, int chunk_cap, cudaStream_t s);
 template <class T>
 void launch_convert(const T* src, double* dst, const GridP& g, cudaStream_t s);
 template <class T>
 void launch_convert_back(const double* src, T* dst, const GridP& g, cudaStream_t s);
 template <class T>
-void launch_compact_copy(Particles<T> p, const Ctrl* ctrl, int cap, double* out6, uint32_t* id_out, int* nout,
-                         cudaStream_t s);
+void launch_compact_copy(const GridP& g, Particles<T> p, const Ctrl* ctrl, int cap, double* out6, uint32_t* id_out,
+                         int* nout, cudaStream_t s);
+template <class T>
+void launch_shift_particles(Particles<T> p, const Ctrl* ctrl, int cap, int sh, cudaStream_t s);
 
 }  // namespace picgb

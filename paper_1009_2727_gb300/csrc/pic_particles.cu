@@ -44,65 +44,72 @@ __device__ __forceinline__ void place(const T* w, int o, T* S) {
   }
 }
 
-template <class T>
-struct View {
-  const T* fe[6];   // gather fields
-  T* j[3];          // current
-  int ld, ox, oz;   // index = (i - ox)*ld + (k - oz)
-};
-
+// interpolation of one component from a block addressed as (i - ox)*ld + (k - oz)
 template <class T, int ORDER>
-__device__ __forceinline__ T interp(const T* F, const View<T>& v, int fi, int fk, const T* wx, const T* wz) {
+__device__ __forceinline__ T interp(const T* F, int ld, int ox, int oz, int fi, int fk, const T* wx, const T* wz) {
   constexpr int NG = St<ORDER>::NG;
   const int off = ORDER == 3 ? 1 : 0;
   T acc = T(0);
+  const T* row = F + (long)(fi - off - ox) * ld + (fk - off - oz);
 #pragma unroll
   for (int a = 0; a < NG; a++) {
-    const T* row = F + (long)(fi - off + a - v.ox) * v.ld + (fk - off - v.oz);
     T r = T(0);
 #pragma unroll
     for (int b = 0; b < NG; b++) r += row[b] * wz[b];
     acc += r * wx[a];
+    row += ld;
   }
   return acc;
 }
 
-template <class T, bool SMEM>
-__device__ __forceinline__ void jadd(T* p, T v) {
-  atomicAdd(p, v);
-}
-
 struct PushConst {
-  double dx, dz, dt, z0;
-  double xlo, xhi, zlo, zhi;
-  double qm_half;   // q dt/(2m)
-  double q;
+  double dx, dz, dt, z0;            // FP64 path
+  double xlo, xhi, zlo, zhi;        // FP64 path removal bounds [m]
+  int cx_lo, cx_hi, cz_lo, cz_hi;   // mixed path removal bounds [cells, hi exclusive]
+  float dtdx, dtdz;                 // mixed path
+  double qm_half;                   // q dt/(2m)
+  double kx, kz, ky;                // deposit: -q/(dz dt), -q/(dx dt), q/(dx dz)
 };
 
+// One particle: gather -> Boris -> move -> Esirkepov. E/B/J are 3-component
+// blocks (component stride cs) addressed as (i - ox)*ld + (k - oz).
 template <class T, int ORDER, bool SMEM>
-__device__ __forceinline__ void push_one(const View<T>& v, Particles<T>& p, int pi, const PushConst& pc,
-                                         int& bx0, int& bx1, int& bz0, int& bz1) {
+__device__ __forceinline__ void push_one(const T* __restrict__ Eb, const T* __restrict__ Bb, T* Jb, long cs, int ld,
+                                         int ox, int oz, Particles<T>& p, int pi, const PushConst& pc, int& bx0,
+                                         int& bx1, int& bz0, int& bz1) {
   constexpr int NG = St<ORDER>::NG, ND = St<ORDER>::ND;
+  constexpr bool CP = CellPos<T>::value;
   const T w = p.w[pi];
   if (w == T(0)) return;
-  const double x = p.x[pi], z = p.z[pi];
+  int fx, fz, fxh, fzh;
+  T tx, tz, txh, tzh;
+  double x = 0.0, z = 0.0, X = 0.0, Z = 0.0;
+  if constexpr (CP) {
+    const uint32_t c = p.cell[pi];
+    fx = cell_x(c); fz = cell_z(c);
+    tx = p.ox[pi]; tz = p.oz[pi];
+    fxh = tx >= T(0.5) ? fx : fx - 1; txh = tx >= T(0.5) ? tx - T(0.5) : tx + T(0.5);
+    fzh = tz >= T(0.5) ? fz : fz - 1; tzh = tz >= T(0.5) ? tz - T(0.5) : tz + T(0.5);
+  } else {
+    x = p.x[pi]; z = p.z[pi];
+    X = x / pc.dx; Z = (z - pc.z0) / pc.dz;
+    fx = (int)floor(X); fz = (int)floor(Z);
+    tx = T(X - fx); tz = T(Z - fz);
+    const double Xh = X - 0.5, Zh = Z - 0.5;
+    fxh = (int)floor(Xh); fzh = (int)floor(Zh);
+    txh = T(Xh - fxh); tzh = T(Zh - fzh);
+  }
   T ux = p.ux[pi], uy = p.uy[pi], uz = p.uz[pi];
-  const double X = x / pc.dx, Z = (z - pc.z0) / pc.dz;
-  const int fx = (int)floor(X), fz = (int)floor(Z);
-  const T tx = T(X - fx), tz = T(Z - fz);
-  const double Xh = X - 0.5, Zh = Z - 0.5;
-  const int fxh = (int)floor(Xh), fzh = (int)floor(Zh);
-  const T txh = T(Xh - fxh), tzh = T(Zh - fzh);
   T wxi[NG], wzi[NG], wxh[NG], wzh[NG];
   wts<T, ORDER>(tx, wxi); wts<T, ORDER>(tz, wzi);
   wts<T, ORDER>(txh, wxh); wts<T, ORDER>(tzh, wzh);
   // energy-conserving gather from each component's Yee location
-  const T Ex = interp<T, ORDER>(v.fe[0], v, fxh, fz, wxh, wzi);
-  const T Ey = interp<T, ORDER>(v.fe[1], v, fx, fz, wxi, wzi);
-  const T Ez = interp<T, ORDER>(v.fe[2], v, fx, fzh, wxi, wzh);
-  const T Bx = interp<T, ORDER>(v.fe[3], v, fx, fzh, wxi, wzh);
-  const T By = interp<T, ORDER>(v.fe[4], v, fxh, fzh, wxh, wzh);
-  const T Bz = interp<T, ORDER>(v.fe[5], v, fxh, fz, wxh, wzi);
+  const T Ex = interp<T, ORDER>(Eb, ld, ox, oz, fxh, fz, wxh, wzi);
+  const T Ey = interp<T, ORDER>(Eb + cs, ld, ox, oz, fx, fz, wxi, wzi);
+  const T Ez = interp<T, ORDER>(Eb + 2 * cs, ld, ox, oz, fx, fzh, wxi, wzh);
+  const T Bx = interp<T, ORDER>(Bb, ld, ox, oz, fx, fzh, wxi, wzh);
+  const T By = interp<T, ORDER>(Bb + cs, ld, ox, oz, fxh, fzh, wxh, wzh);
+  const T Bz = interp<T, ORDER>(Bb + 2 * cs, ld, ox, oz, fxh, fz, wxh, wzi);
   // relativistic Boris push
   const T k = T(pc.qm_half);
   const T ic2 = T(1.0 / (kC * kC));
@@ -121,12 +128,25 @@ __device__ __forceinline__ void push_one(const View<T>& v, Particles<T>& p, int 
   ux = plx + k * Ex; uy = ply + k * Ey; uz = plz + k * Ez;
   const T g1 = sqrt(T(1) + (ux * ux + uy * uy + uz * uz) * ic2);
   const T vx = ux / g1, vy = uy / g1, vz = uz / g1;
-  const double xn = x + pc.dt * (double)vx;
-  const double zn = z + pc.dt * (double)vz;
+  // move
+  int fxn, fzn;
+  T txn, tzn;
+  double xn = 0.0, zn = 0.0;
+  if constexpr (CP) {
+    const float ax = tx + pc.dtdx * vx, az = tz + pc.dtdz * vz;
+    int sx = (int)floorf(ax), sz = (int)floorf(az);
+    float rx = ax - (float)sx, rz = az - (float)sz;
+    if (rx >= 1.0f) { rx = 0.0f; sx++; }
+    if (rz >= 1.0f) { rz = 0.0f; sz++; }
+    fxn = fx + sx; fzn = fz + sz; txn = rx; tzn = rz;
+  } else {
+    xn = x + pc.dt * (double)vx;
+    zn = z + pc.dt * (double)vz;
+    const double Xn = xn / pc.dx, Zn = (zn - pc.z0) / pc.dz;
+    fxn = (int)floor(Xn); fzn = (int)floor(Zn);
+    txn = T(Xn - fxn); tzn = T(Zn - fzn);
+  }
   // Esirkepov deposition on an ND x ND window
-  const double Xn = xn / pc.dx, Zn = (zn - pc.z0) / pc.dz;
-  const int fxn = (int)floor(Xn), fzn = (int)floor(Zn);
-  const T txn = T(Xn - fxn), tzn = T(Zn - fzn);
   const int off = ORDER == 3 ? 1 : 0;
   const int bx = min(fx, fxn) - off, bz = min(fz, fzn) - off;
   T S0x[ND], S1x[ND], S0z[ND], S1z[ND];
@@ -140,13 +160,12 @@ __device__ __forceinline__ void push_one(const View<T>& v, Particles<T>& p, int 
   T DSx[ND], DSz[ND];
 #pragma unroll
   for (int a = 0; a < ND; a++) { DSx[a] = S1x[a] - S0x[a]; DSz[a] = S1z[a] - S0z[a]; }
-  const T qw = T(pc.q) * w;
-  const T cx = -qw / T(pc.dz * pc.dt);
-  const T cz = -qw / T(pc.dx * pc.dt);
-  const T cy = qw * vy / T(pc.dx * pc.dz);
-  T* Jx = v.j[0] + (long)(bx - v.ox) * v.ld + (bz - v.oz);
-  T* Jy = v.j[1] + (long)(bx - v.ox) * v.ld + (bz - v.oz);
-  T* Jz = v.j[2] + (long)(bx - v.ox) * v.ld + (bz - v.oz);
+  const T cx = T(pc.kx) * w;
+  const T cz = T(pc.kz) * w;
+  const T cy = T(pc.ky) * w * vy;
+  T* Jx = Jb + (long)(bx - ox) * ld + (bz - oz);
+  T* Jy = Jx + cs;
+  T* Jz = Jx + 2 * cs;
 #pragma unroll
   for (int b = 0; b < ND; b++) {
     const T fzb = S0z[b] + T(0.5) * DSz[b];
@@ -154,7 +173,7 @@ __device__ __forceinline__ void push_one(const View<T>& v, Particles<T>& p, int 
 #pragma unroll
     for (int a = 0; a < ND - 1; a++) {
       acc += cx * DSx[a] * fzb;
-      if (acc != T(0)) jadd<T, SMEM>(Jx + (long)a * v.ld + b, acc);
+      if (acc != T(0)) atomicAdd(Jx + (long)a * ld + b, acc);
     }
   }
 #pragma unroll
@@ -164,7 +183,7 @@ __device__ __forceinline__ void push_one(const View<T>& v, Particles<T>& p, int 
 #pragma unroll
     for (int b = 0; b < ND - 1; b++) {
       acc += cz * DSz[b] * fxa;
-      if (acc != T(0)) jadd<T, SMEM>(Jz + (long)a * v.ld + b, acc);
+      if (acc != T(0)) atomicAdd(Jz + (long)a * ld + b, acc);
     }
   }
   if (cy != T(0)) {
@@ -173,13 +192,20 @@ __device__ __forceinline__ void push_one(const View<T>& v, Particles<T>& p, int 
 #pragma unroll
       for (int b = 0; b < ND; b++) {
         T wy = S0x[a] * S0z[b] + T(0.5) * DSx[a] * S0z[b] + T(0.5) * S0x[a] * DSz[b] + DSx[a] * DSz[b] * T(1.0 / 3.0);
-        if (wy != T(0)) jadd<T, SMEM>(Jy + (long)a * v.ld + b, cy * wy);
+        if (wy != T(0)) atomicAdd(Jy + (long)a * ld + b, cy * wy);
       }
     }
   }
-  p.x[pi] = xn; p.z[pi] = zn;
+  bool gone;
+  if constexpr (CP) {
+    p.cell[pi] = pack_cell(fxn, fzn); p.ox[pi] = txn; p.oz[pi] = tzn;
+    gone = fxn < pc.cx_lo || fxn >= pc.cx_hi || fzn < pc.cz_lo || fzn >= pc.cz_hi;
+  } else {
+    p.x[pi] = xn; p.z[pi] = zn;
+    gone = xn < pc.xlo || xn >= pc.xhi || zn < pc.zlo || zn >= pc.zhi;
+  }
   p.ux[pi] = ux; p.uy[pi] = uy; p.uz[pi] = uz;
-  if (xn < pc.xlo || xn >= pc.xhi || zn < pc.zlo || zn >= pc.zhi) {
+  if (gone) {
     p.w[pi] = T(0);
   } else {
     bx0 = min(bx0, fxn); bx1 = max(bx1, fxn);
@@ -187,36 +213,44 @@ __device__ __forceinline__ void push_one(const View<T>& v, Particles<T>& p, int 
   }
 }
 
+// current cell of a particle (grid-relative); false for a non-finite position
 template <class T>
-__device__ __forceinline__ View<T> global_view(const FieldPtrs<T>& f, const GridP& g) {
-  View<T> v;
-  for (int q = 0; q < 3; q++) { v.fe[q] = f.fE[q]; v.fe[3 + q] = f.fB[q]; v.j[q] = f.J[q]; }
-  v.ld = g.ld; v.ox = 0; v.oz = 0;
-  return v;
+__device__ __forceinline__ bool particle_cell(const Particles<T>& p, int pi, const PushConst& pc, int& fx, int& fz) {
+  if constexpr (CellPos<T>::value) {
+    const uint32_t c = p.cell[pi];
+    fx = cell_x(c); fz = cell_z(c);
+    return true;
+  } else {
+    const double X = p.x[pi] / pc.dx, Z = (p.z[pi] - pc.z0) / pc.dz;
+    if (!(X == X) || !(Z == Z) || fabs(X) > 1e9 || fabs(Z) > 1e9) return false;
+    fx = (int)floor(X); fz = (int)floor(Z);
+    return true;
+  }
 }
 
 // global-memory path with an index guard: a particle whose stencil would leave
 // the arrays (only possible for corrupted or non-finite state) is removed and
 // flagged instead of being pushed.
 template <class T, int ORDER>
-__device__ __noinline__ void push_global_guarded(const View<T>& vg, const GridP& g, Particles<T>& p, int pi,
-                                                 const PushConst& pc, Ctrl* ctrl, int& bx0, int& bx1, int& bz0,
-                                                 int& bz1) {
+__device__ __noinline__ void push_global_guarded(const T* gE, const T* gB, T* gJ, const GridP& g, Particles<T>& p,
+                                                 int pi, const PushConst& pc, Ctrl* ctrl, int& bx0, int& bx1,
+                                                 int& bz0, int& bz1) {
   if (p.w[pi] == T(0)) return;
-  const double X = p.x[pi] / pc.dx, Z = (p.z[pi] - pc.z0) / pc.dz;
-  const bool ok = X >= St<ORDER>::LO + 1 && X < g.nx - St<ORDER>::HI - 1 && Z >= St<ORDER>::LO + 1 &&
-                  Z < g.nz - St<ORDER>::HI - 1;
+  int fx, fz;
+  const bool fin = particle_cell<T>(p, pi, pc, fx, fz);
+  const bool ok = fin && fx >= St<ORDER>::LO + 1 && fx < g.nx - St<ORDER>::HI - 1 && fz >= St<ORDER>::LO + 1 &&
+                  fz < g.nz - St<ORDER>::HI - 1;
   if (!ok) {
     p.w[pi] = T(0);
-    atomicOr(&ctrl->status, (X == X && Z == Z) ? ST_OUTSIDE : ST_NAN);
+    atomicOr(&ctrl->status, fin ? ST_OUTSIDE : ST_NAN);
     return;
   }
-  push_one<T, ORDER, false>(vg, p, pi, pc, bx0, bx1, bz0, bz1);
+  push_one<T, ORDER, false>(gE, gB, gJ, g.cs, g.ld, 0, 0, p, pi, pc, bx0, bx1, bz0, bz1);
 }
 
 template <class T, int ORDER>
-__global__ void __launch_bounds__(PB_THREADS) k_push(GridP g, FieldPtrs<T> f, Particles<T> p, Chunk* chunks,
-                                                     Ctrl* ctrl, int cap_nodes, PushConst pc) {
+__global__ void __launch_bounds__(PB_THREADS) k_push(GridP g, const T* gE, const T* gB, T* gJ, Particles<T> p,
+                                                     Chunk* chunks, Ctrl* ctrl, int cap_nodes, PushConst pc) {
   extern __shared__ unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);
   __shared__ int s_chunk;
@@ -247,25 +281,21 @@ __global__ void __launch_bounds__(PB_THREADS) k_push(GridP g, FieldPtrs<T> f, Pa
         const long gp = (long)(wx0 + li) * g.ld + (wz0 + lk);
 #pragma unroll
         for (int q = 0; q < 3; q++) {
-          sm[q * cap_nodes + e] = f.fE[q][gp];
-          sm[(3 + q) * cap_nodes + e] = f.fB[q][gp];
+          sm[q * cap_nodes + e] = gE[q * g.cs + gp];
+          sm[(3 + q) * cap_nodes + e] = gB[q * g.cs + gp];
           sm[(6 + q) * cap_nodes + e] = T(0);
         }
       }
       __syncthreads();
-      View<T> v;
-      for (int q = 0; q < 6; q++) v.fe[q] = sm + q * cap_nodes;
-      for (int q = 0; q < 3; q++) v.j[q] = sm + (6 + q) * cap_nodes;
-      v.ld = wzn; v.ox = wx0; v.oz = wz0;
-      View<T> vg = global_view<T>(f, g);
       for (int pi = ch.p0 + threadIdx.x; pi < ch.p1; pi += blockDim.x) {
         // a particle outside the chunk's box (should not happen) takes the global path
-        const double X = p.x[pi] / pc.dx, Z = (p.z[pi] - pc.z0) / pc.dz;
-        const int fx = (int)floor(X), fz = (int)floor(Z);
-        if (fx >= ch.ix0 && fx <= ch.ix1 && fz >= ch.iz0 && fz <= ch.iz1)
-          push_one<T, ORDER, true>(v, p, pi, pc, bx0, bx1, bz0, bz1);
+        int fx = 0, fz = 0;
+        const bool fin = particle_cell<T>(p, pi, pc, fx, fz);
+        if (fin && fx >= ch.ix0 && fx <= ch.ix1 && fz >= ch.iz0 && fz <= ch.iz1)
+          push_one<T, ORDER, true>(sm, sm + 3 * cap_nodes, sm + 6 * cap_nodes, cap_nodes, wzn, wx0, wz0, p, pi, pc,
+                                   bx0, bx1, bz0, bz1);
         else
-          push_global_guarded<T, ORDER>(vg, g, p, pi, pc, ctrl, bx0, bx1, bz0, bz1);
+          push_global_guarded<T, ORDER>(gE, gB, gJ, g, p, pi, pc, ctrl, bx0, bx1, bz0, bz1);
       }
       __syncthreads();
       for (int e = threadIdx.x; e < nn; e += blockDim.x) {
@@ -274,14 +304,13 @@ __global__ void __launch_bounds__(PB_THREADS) k_push(GridP g, FieldPtrs<T> f, Pa
 #pragma unroll
         for (int q = 0; q < 3; q++) {
           T val = sm[(6 + q) * cap_nodes + e];
-          if (val != T(0)) atomicAdd(f.J[q] + gp, val);
+          if (val != T(0)) atomicAdd(gJ + q * g.cs + gp, val);
         }
       }
     } else {
       if (threadIdx.x == 0) atomicAdd(&ctrl->overflow_chunks, 1);
-      View<T> vg = global_view<T>(f, g);
       for (int pi = ch.p0 + threadIdx.x; pi < ch.p1; pi += blockDim.x)
-        push_global_guarded<T, ORDER>(vg, g, p, pi, pc, ctrl, bx0, bx1, bz0, bz1);
+        push_global_guarded<T, ORDER>(gE, gB, gJ, g, p, pi, pc, ctrl, bx0, bx1, bz0, bz1);
     }
     // bounding box of the chunk's live particles for the next step
     bx0 = __reduce_min_sync(0xffffffffu, bx0); bx1 = __reduce_max_sync(0xffffffffu, bx1);
@@ -308,8 +337,13 @@ __global__ void k_sort_key(GridP g, Particles<T> p, SortBufs sb, const Ctrl* ctr
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   if (p.w[i] == T(0)) { sb.key[i] = -1; return; }
-  int cx = (int)floor(p.x[i] / g.dx);
-  int cz = (int)floor((p.z[i] - g.z0) / g.dz);
+  int cx, cz;
+  if constexpr (CellPos<T>::value) {
+    cx = cell_x(p.cell[i]); cz = cell_z(p.cell[i]);
+  } else {
+    cx = (int)floor(p.x[i] / g.dx);
+    cz = (int)floor((p.z[i] - g.z0) / g.dz);
+  }
   cx = min(max(cx, 0), g.nx - 1);
   cz = min(max(cz, 0), g.nz - 1);
   const int tile = (cx / sb.tx) * sb.ntz + (cz / sb.tz);
@@ -327,7 +361,11 @@ __global__ void k_sort_scatter(Particles<T> s, Particles<T> d, SortBufs sb, cons
   const int key = sb.key[i];
   if (key < 0) return;
   const int o = sb.bin_start[key] + sb.slot[i];
-  d.x[o] = s.x[i]; d.z[o] = s.z[i];
+  if constexpr (CellPos<T>::value) {
+    d.cell[o] = s.cell[i]; d.ox[o] = s.ox[i]; d.oz[o] = s.oz[i];
+  } else {
+    d.x[o] = s.x[i]; d.z[o] = s.z[i];
+  }
   d.ux[o] = s.ux[i]; d.uy[o] = s.uy[i]; d.uz[o] = s.uz[i];
   d.w[o] = s.w[i]; d.id[o] = s.id[i];
 }
@@ -449,8 +487,19 @@ __global__ void k_inject(GridP g, Particles<T> p, Chunk* chunks, Ctrl* ctrl, Inj
     if (o >= cap) { atomicOr(&ctrl->status, ST_OVERFLOW); continue; }
     const double zlat = (m + 0.5) * ip.h;
     const double n = ip.gamma * lab_density(ip, ip.gamma * zlat);
-    p.x[o] = (g.gx_lo + (a + 0.5) / ip.ppc_x) * g.dx;
-    p.z[o] = zlat - ip.beta * kC * ip.t;
+    const double zp = zlat - ip.beta * kC * ip.t;
+    if constexpr (CellPos<T>::value) {
+      const double Zr = (zp - g.z0) / gdz;
+      int iz = (int)floor(Zr);
+      float oz = (float)(Zr - iz);
+      if (oz >= 1.0f) { oz = 0.0f; iz++; }
+      p.cell[o] = pack_cell(g.gx_lo + (int)(a / ip.ppc_x), iz);
+      p.ox[o] = (float)(((a % ip.ppc_x) + 0.5) / ip.ppc_x);
+      p.oz[o] = oz;
+    } else {
+      p.x[o] = (g.gx_lo + (a + 0.5) / ip.ppc_x) * g.dx;
+      p.z[o] = zp;
+    }
     p.ux[o] = T(0); p.uy[o] = T(0);
     p.uz[o] = T(-ip.gamma * ip.beta * kC);
     p.w[o] = T(n * g.dx * gdz / (double)(ip.ppc_x * ip.ppc_z));
@@ -483,16 +532,18 @@ void launch_push(const GridP& g, const FieldPtrs<T>& f, Particles<T> p, Chunk* c
   pc.dx = g.dx; pc.dz = g.dz; pc.dt = g.dt; pc.z0 = g.z0;
   pc.xlo = g.gx_lo * g.dx; pc.xhi = g.gx_hi * g.dx;
   pc.zlo = g.z0 + g.gz_lo * g.dz; pc.zhi = g.z0 + g.gz_hi * g.dz + g.dz;
+  pc.cx_lo = g.gx_lo; pc.cx_hi = g.gx_hi; pc.cz_lo = g.gz_lo; pc.cz_hi = g.gz_hi + 1;
+  pc.dtdx = (float)(g.dt / g.dx); pc.dtdz = (float)(g.dt / g.dz);
   pc.qm_half = q * g.dt / (2.0 * m);
-  pc.q = q;
+  pc.kx = -q / (g.dz * g.dt); pc.kz = -q / (g.dx * g.dt); pc.ky = q / (g.dx * g.dz);
   const size_t sm = (size_t)9 * smem_nodes * sizeof(T);
   cudaMemsetAsync(&ctrl->next_chunk, 0, sizeof(int), s);
   if (order == 3) {
     cudaFuncSetAttribute(k_push<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_push<T, 3><<<grid_blocks, PB_THREADS, sm, s>>>(g, f, p, chunks, ctrl, smem_nodes, pc);
+    k_push<T, 3><<<grid_blocks, PB_THREADS, sm, s>>>(g, f.fE[0], f.fB[0], f.J[0], p, chunks, ctrl, smem_nodes, pc);
   } else {
     cudaFuncSetAttribute(k_push<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_push<T, 1><<<grid_blocks, PB_THREADS, sm, s>>>(g, f, p, chunks, ctrl, smem_nodes, pc);
+    k_push<T, 1><<<grid_blocks, PB_THREADS, sm, s>>>(g, f.fE[0], f.fB[0], f.J[0], p, chunks, ctrl, smem_nodes, pc);
   }
 }
 

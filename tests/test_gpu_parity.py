@@ -108,7 +108,7 @@ def test_parity_stage_physics_small_box_fp64(Sim, orc):
     w = W.shrink(W.stage_2d(), 96, 320)
     w["precision"] = "fp64"
     w["plasma"]["z_start_lab"] = 0.0
-    g, o = run_pair(Sim, orc, w, 30)
+    g, o = run_pair(Sim, orc, w, 100)
     check_fields(g, o, TOL64)
     check_particles(g, o, TOL64)
 
