@@ -90,6 +90,8 @@ typedef struct {
   int *alive;
   /* beam-only */
   double *tc, *zf0, *uxb, *uyb, *uzb; int *active;
+  /* ions: lattice position (m + 1/2) h of the row, fixed in the lab */
+  double *zl;
   long n, cap;
   double q, m;
 } orc_species;
@@ -501,6 +503,7 @@ static void sp_reserve(orc_species* p, long n) {
   RE(x, double); RE(z, double); RE(ux, double); RE(uy, double); RE(uz, double); RE(w, double);
   RE(id, uint32_t); RE(alive, int);
   RE(tc, double); RE(zf0, double); RE(uxb, double); RE(uyb, double); RE(uzb, double); RE(active, int);
+  RE(zl, double);
 #undef RE
   p->cap = cap;
 }
@@ -511,6 +514,7 @@ static void sp_push(orc_species* p, double x, double z, double ux, double uy, do
   p->x[j] = x; p->z[j] = z; p->ux[j] = ux; p->uy[j] = uy; p->uz[j] = uz; p->w[j] = w;
   p->id[j] = id; p->alive[j] = 1;
   p->tc[j] = 0; p->zf0[j] = 0; p->uxb[j] = 0; p->uyb[j] = 0; p->uzb[j] = 0; p->active[j] = 1;
+  p->zl[j] = 0;
 }
 
 static void sp_compact(orc_species* p) {
@@ -521,7 +525,7 @@ static void sp_compact(orc_species* p) {
       p->x[o] = p->x[j]; p->z[o] = p->z[j]; p->ux[o] = p->ux[j]; p->uy[o] = p->uy[j]; p->uz[o] = p->uz[j];
       p->w[o] = p->w[j]; p->id[o] = p->id[j]; p->alive[o] = 1;
       p->tc[o] = p->tc[j]; p->zf0[o] = p->zf0[j]; p->uxb[o] = p->uxb[j]; p->uyb[o] = p->uyb[j];
-      p->uzb[o] = p->uzb[j]; p->active[o] = p->active[j];
+      p->uzb[o] = p->uzb[j]; p->active[o] = p->active[j]; p->zl[o] = p->zl[j];
     }
     o++;
   }
@@ -592,7 +596,7 @@ void orc_destroy(orc_sim* s) {
   for (int j = 0; j < 3; j++) {
     orc_species* p = &s->sp[j];
     free(p->x); free(p->z); free(p->ux); free(p->uy); free(p->uz); free(p->w); free(p->id); free(p->alive);
-    free(p->tc); free(p->zf0); free(p->uxb); free(p->uyb); free(p->uzb); free(p->active);
+    free(p->tc); free(p->zf0); free(p->uxb); free(p->uyb); free(p->uzb); free(p->active); free(p->zl);
   }
   free(s->rzL); free(s->rtL); free(s->rout); free(s->rdone);
   for (int c = 0; c < 3; c++) free(s->ext[c]);
@@ -645,7 +649,10 @@ static void add_row(orc_sim* s, long m, double t) {
     double xp = (s->gx_lo + (a + 0.5) / s->pl.ppc_x) * s->dx;
     uint32_t id = (uint32_t)((uint64_t)m * (uint64_t)s->nxl + (uint64_t)a);
     sp_push(&s->sp[0], xp, zp, 0.0, 0.0, uz, w, id);
-    if (s->pl.ions) sp_push(&s->sp[1], xp, zp, 0.0, 0.0, uz, w, id);
+    if (s->pl.ions) {
+      sp_push(&s->sp[1], xp, zp, 0.0, 0.0, uz, w, id);
+      s->sp[1].zl[s->sp[1].n - 1] = zlat;
+    }
   }
 }
 
@@ -900,6 +907,12 @@ static void one_step(orc_sim* s) {
       double gm = sqrt(1.0 + (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]) / (O_C * O_C));
       double xn = p->x[q] + s->dt * u[0] / gm;
       double zn = p->z[q] + s->dt * u[2] / gm;
+      if (j == 1) {
+        /* ions are fixed in the lab: they stay on z'(t) = (m + 1/2) h - beta c t (PR-9, PR-12) */
+        xn = p->x[q];
+        p->z[q] = p->zl[q] - s->beta * O_C * tn;
+        zn = p->zl[q] - s->beta * O_C * tn1;
+      }
       if (j != 2) esirkepov(s, s->F[OJX], s->F[OJY], s->F[OJZ], p->x[q], p->z[q], xn, zn, u[1] / gm, p->q * p->w[q]);
       p->x[q] = xn; p->z[q] = zn; p->ux[q] = u[0]; p->uy[q] = u[1]; p->uz[q] = u[2];
       if (xn < xlo || xn >= xhi || zn < zlo || zn >= zhi) p->alive[q] = 0;
