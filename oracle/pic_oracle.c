@@ -893,6 +893,8 @@ static void one_step(orc_sim* s) {
         if (tn >= p->tc[q]) {
           p->active[q] = 1;
           p->ux[q] = p->uxb[q]; p->uy[q] = p->uyb[q]; p->uz[q] = p->uzb[q];
+          /* a particle whose crossing lies outside the particle domain never enters it (PR-20) */
+          if (p->x[q] < xlo || p->x[q] >= xhi || p->z[q] < zlo || p->z[q] >= zhi) { p->alive[q] = 0; continue; }
         } else {
           p->z[q] = p->zf0[q] + s->beam_vbar * tn1;
           continue;
