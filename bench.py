@@ -191,10 +191,13 @@ def main():
     ap.add_argument("--order", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--nz", type=int, default=0, help="smaller box for profiling captures (default: the full 4096)")
     args = ap.parse_args()
 
     from paper_1009_2727_gb300 import workloads as W
     w = W.stage_2d()
+    if args.nz:
+        w = W.shrink(w, w["nx"], args.nz)
     w["order"] = args.order
     w["precision"] = args.precision
     if args.impl == "reference":

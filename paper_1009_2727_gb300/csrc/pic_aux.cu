@@ -30,55 +30,64 @@ __device__ double lab_density_d(const InjectP& ip, double zl) {
   return ip.n0;
 }
 
-// R(k) = sum over live rows of w_m S(Z_m(t) - k) at two times; dR prefix-summed into C
+// R(k) = sum over live rows of w_m S(Z_m(t) - k) at two times (blockIdx.y selects the time);
+// the change R1 - R0 is prefix-summed into C by k_ion_prefix
 __global__ void k_ion_rows(GridP g, long long mlo, long long mhi, double t0, double t1, InjectP ip, int order,
                            double* R0, double* R1) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k > g.nz) return;
   const double reach = order == 3 ? 2.0 : 1.0;
   const double wfac = g.dx * g.dz / (double)(ip.ppc_x * ip.ppc_z);
-  double acc[2] = {0.0, 0.0};
-  const double ts[2] = {t0, t1};
-  for (int q = 0; q < 2; q++) {
-    const double shift = ip.beta * kC * ts[q];
-    long long ma = (long long)floor(((k - reach) * g.dz + g.z0 + shift) / ip.h - 0.5) - 1;
-    long long mb = (long long)ceil(((k + reach) * g.dz + g.z0 + shift) / ip.h - 0.5) + 1;
-    if (ma < mlo) ma = mlo;
-    if (mb > mhi - 1) mb = mhi - 1;
-    for (long long m = ma; m <= mb; m++) {
-      const double zlat = (m + 0.5) * ip.h;
-      const double Zm = (zlat - shift - g.z0) / g.dz;
-      const double sv = shape_val(order, Zm - k);
-      if (sv == 0.0) continue;
-      const double w = ip.gamma * lab_density_d(ip, ip.gamma * zlat) * wfac;
-      acc[q] += w * sv;
-    }
+  const double t = blockIdx.y == 0 ? t0 : t1;
+  const double shift = ip.beta * kC * t;
+  long long ma = (long long)floor(((k - reach) * g.dz + g.z0 + shift) / ip.h - 0.5) - 1;
+  long long mb = (long long)ceil(((k + reach) * g.dz + g.z0 + shift) / ip.h - 0.5) + 1;
+  if (ma < mlo) ma = mlo;
+  if (mb > mhi - 1) mb = mhi - 1;
+  double acc = 0.0;
+  for (long long m = ma; m <= mb; m++) {
+    const double zlat = (m + 0.5) * ip.h;
+    const double Zm = (zlat - shift - g.z0) / g.dz;
+    const double sv = shape_val(order, Zm - k);
+    if (sv == 0.0) continue;
+    acc += ip.gamma * lab_density_d(ip, ip.gamma * zlat) * wfac * sv;
   }
-  R0[k] = acc[0];
-  R1[k] = acc[1];
+  (blockIdx.y == 0 ? R0 : R1)[k] = acc;
 }
 
+// single block of 1024 threads: each thread sums a contiguous run, then a shuffle scan of the run totals
 __global__ void k_ion_prefix(int n, const double* R0, const double* R1, double* C) {
-  // single block: running prefix sum of R1 - R0 in chunks of blockDim
-  __shared__ double sh[1024];
-  __shared__ double carry;
-  if (threadIdx.x == 0) carry = 0.0;
+  __shared__ double ws[32];
+  const int per = (n + blockDim.x - 1) / blockDim.x;
+  const int b = threadIdx.x * per;
+  double loc = 0.0;
+  for (int j = 0; j < per; j++) {
+    const int k = b + j;
+    if (k < n) loc += R1[k] - R0[k];
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  double x = loc;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    double y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) ws[wid] = x;
   __syncthreads();
-  for (int base = 0; base < n; base += blockDim.x) {
-    const int k = base + threadIdx.x;
-    double v = k < n ? R1[k] - R0[k] : 0.0;
-    sh[threadIdx.x] = v;
-    __syncthreads();
-    for (int o = 1; o < (int)blockDim.x; o <<= 1) {
-      double y = threadIdx.x >= (unsigned)o ? sh[threadIdx.x - o] : 0.0;
-      __syncthreads();
-      sh[threadIdx.x] += y;
-      __syncthreads();
+  if (wid == 0) {
+    double v = lane < (int)(blockDim.x >> 5) ? ws[lane] : 0.0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      double y = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += y;
     }
-    if (k < n) C[k] = carry + sh[threadIdx.x];
-    __syncthreads();
-    if (threadIdx.x == blockDim.x - 1) carry += sh[threadIdx.x];
-    __syncthreads();
+    ws[lane] = v;
+  }
+  __syncthreads();
+  double run = (wid > 0 ? ws[wid - 1] : 0.0) + x - loc;
+  for (int j = 0; j < per; j++) {
+    const int k = b + j;
+    if (k < n) { run += R1[k] - R0[k]; C[k] = run; }
   }
 }
 
@@ -96,22 +105,30 @@ __device__ double emit_field(const LaserP& l, double x, double tp) {
   return (1.0 - l.beta_s) / dop * gv;
 }
 
+// blocks of 32 nodes: the surface current K of the pairs at nodes i0-2 .. i0+33 is computed once
+// (FP64 transcendental functions, spread over many SMs), then each node sums its neighbours
 template <class T>
 __global__ void k_antenna(GridP g, T* Jy, LaserP l, int order, double t0, double t1) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i > g.nx) return;
+  __shared__ double Ks[36];
+  const int i0 = blockIdx.x * 32;
   const double th = 0.5 * (t0 + t1);
   const double za0 = l.z_antenna + l.beta_s * kC * t0;
   const double za1 = l.z_antenna + l.beta_s * kC * t1;
   const double zlo = g.z0 + g.gz_lo * g.dz, zhi = g.z0 + g.gz_hi * g.dz;
   if (za0 < zlo || za0 >= zhi || za1 < zlo || za1 >= zhi) return;
+  for (int q = threadIdx.x; q < 36; q += blockDim.x) {
+    const int ia = i0 - 2 + q;
+    Ks[q] = (ia >= g.gx_lo && ia <= g.gx_hi) ? -2.0 * kEps0 * kC * emit_field(l, ia * g.dx, th) : 0.0;
+  }
+  __syncthreads();
+  const int i = i0 + threadIdx.x;
+  if (i > g.nx) return;
   const double Z0 = (za0 - g.z0) / g.dz, Z1 = (za1 - g.z0) / g.dz;
   const int fz = (int)floor(Z0 < Z1 ? Z0 : Z1);
   double kx = 0.0;
-  for (int ia = max(g.gx_lo, i - 2); ia <= min(g.gx_hi, i + 2); ia++) {
-    const double wx = shape_val(order, (double)(ia - i));
-    if (wx == 0.0) continue;
-    kx += -2.0 * kEps0 * kC * emit_field(l, ia * g.dx, th) * wx;
+  for (int d = -2; d <= 2; d++) {
+    const double wx = shape_val(order, (double)d);
+    if (wx != 0.0) kx += Ks[threadIdx.x + 2 + d] * wx;
   }
   if (kx == 0.0) return;
   for (int k = fz - 3; k <= fz + 4; k++) {
@@ -189,11 +206,17 @@ __global__ void k_beam_push(GridP g, FieldPtrs<T> f, Beam<T> b, int order, doubl
   if (j >= b.n) return;
   int fl = b.flag[j];
   if (!(fl & 1)) return;
+  const double xlo = g.gx_lo * g.dx, xhi = g.gx_hi * g.dx;
+  const double zlo = g.z0 + g.gz_lo * g.dz, zhi = g.z0 + g.gz_hi * g.dz + g.dz;
   if (!(fl & 2)) {
     if (tn >= b.tc[j]) {
       fl |= 2;
-      b.flag[j] = fl;
       b.ux[j] = b.uxb[j]; b.uy[j] = b.uyb[j]; b.uz[j] = b.uzb[j];
+      // a particle whose crossing lies outside the particle domain never enters it (PR-20)
+      const double xa = b.x[j], za = b.z[j];
+      if (xa < xlo || xa >= xhi || za < zlo || za >= zhi) fl &= ~1;
+      b.flag[j] = fl;
+      if (!(fl & 1)) return;
     } else {
       b.z[j] = b.zf0[j] + acc[2] * tn1;
       return;
@@ -223,8 +246,6 @@ __global__ void k_beam_push(GridP g, FieldPtrs<T> f, Beam<T> b, int order, doubl
   const double xn = x + g.dt * (double)(ux / g1);
   const double zn = z + g.dt * (double)(uz / g1);
   b.x[j] = xn; b.z[j] = zn; b.ux[j] = ux; b.uy[j] = uy; b.uz[j] = uz;
-  const double xlo = g.gx_lo * g.dx, xhi = g.gx_hi * g.dx;
-  const double zlo = g.z0 + g.gz_lo * g.dz, zhi = g.z0 + g.gz_hi * g.dz + g.dz;
   if (xn < xlo || xn >= xhi || zn < zlo || zn >= zhi) b.flag[j] = fl & ~1;
 }
 
@@ -408,13 +429,13 @@ __global__ void k_shift_particles(Particles<T> p, const Ctrl* ctrl, int sh) {
 
 void launch_ion_column(const GridP& g, long long mlo, long long mhi, double t0, double t1, const InjectP& ip,
                        int order, double* R0, double* R1, double* C, cudaStream_t s) {
-  k_ion_rows<<<(g.nz + 1 + 255) / 256, 256, 0, s>>>(g, mlo, mhi, t0, t1, ip, order, R0, R1);
+  k_ion_rows<<<dim3((g.nz + 1 + 31) / 32, 2), 32, 0, s>>>(g, mlo, mhi, t0, t1, ip, order, R0, R1);
   k_ion_prefix<<<1, 1024, 0, s>>>(g.nz + 1, R0, R1, C);
 }
 
 template <class T>
 void launch_antenna(const GridP& g, T* Jy, const LaserP& lp, int order, double t0, double t1, cudaStream_t s) {
-  k_antenna<T><<<(g.nx + 1 + 127) / 128, 128, 0, s>>>(g, Jy, lp, order, t0, t1);
+  k_antenna<T><<<(g.nx + 1 + 31) / 32, 32, 0, s>>>(g, Jy, lp, order, t0, t1);
 }
 
 template <class T>

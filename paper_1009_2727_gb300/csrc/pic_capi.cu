@@ -785,6 +785,8 @@ int pic_init(const pic_config* cfg, pic_alloc_fn alloc, pic_free_fn free_fn, voi
   if (h.dt > h.dt_cfl * (1.0 + 1e-12)) return PIC_ECFL;
   const int P = cfg->filter_passes + (cfg->filter_compensate ? 1 : 0);
   h.guard = cfg->particle_guard >= 0 ? cfg->particle_guard : (cfg->shape_order == 3 ? 3 : 2) + P * cfg->filter_stride + 2;
+  // particles must not read filtered fields, nor deposit current, within reach of the walls (PR-10)
+  if (h.guard < (cfg->shape_order == 3 ? 3 : 2) + P * cfg->filter_stride + 1) return PIC_EINVAL;
   const int L = cfg->pml_cells;
   h.gx_lo = L + h.guard; h.gx_hi = cfg->nx - L - h.guard;
   h.gz_lo = L + h.guard; h.gz_hi = cfg->nz - L - h.guard;

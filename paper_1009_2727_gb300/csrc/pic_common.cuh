@@ -67,6 +67,13 @@ struct FilterSpec {
   int passes, stride, compensate;
 };
 
+// composed taps of the multi-pass filter along one axis: c[j] at offset (j - P) * s, j = 0..2P
+template <class T>
+struct FilterTaps {
+  T c[33];
+  int P, s, H;
+};
+
 // Particle chunk: a contiguous particle range and the bounding box of the
 // cells its particles occupy (inclusive, grid-relative cells).
 struct Chunk {

@@ -98,142 +98,118 @@ __global__ void __launch_bounds__(256) k_faraday(GridP g, FieldPtrs<T> f, PmlTab
 }
 
 // ---------------------------------------------------------------------------
-// Shared-memory tile filter. The tile (TX x TZ outputs) is loaded with a halo
-// of H = passes*stride on each side; all x-passes run over the whole loaded
-// block, then all z-passes over the rows the tile needs. Values outside the
-// component's valid range are zero before and after every pass (PR-6).
+// Shared-memory tile filter. The n bilinear passes and the compensation pass of
+// Sec. 4.1 along one axis compose into one (2P+1)-tap convolution with taps at
+// multiples of the stride (P = n + compensation); the separable 2D filter is that
+// convolution along x, then along z. Away from the walls this is the pass-by-pass
+// filter up to rounding; within P*stride cells of a wall the pass-by-pass filter
+// would also re-zero values outside each component's valid range, but no particle
+// reads there and the deposited current is zero there (PR-6, PR-10), which the
+// particle guard enforces.
 constexpr int FT_X = 16;
 constexpr int FT_Z = 64;
-constexpr int FT_THREADS = 256;
-
-struct TileGeo {
-  int WX, WZ;        // loaded block
-  int gi0, gk0;      // global index of block (0,0)
-  int vi0, vi1, vk0, vk1;
-};
+constexpr int FT_TY = 4;
 
 template <class T>
-__device__ __forceinline__ bool tvalid(const TileGeo& t, int li, int lk) {
-  int gi = t.gi0 + li, gk = t.gk0 + lk;
-  return gi >= t.vi0 && gi <= t.vi1 && gk >= t.vk0 && gk <= t.vk1;
+__device__ __forceinline__ void load_tile(T* A, const T* src, const GridP& g, int gi0, int gk0, int WX, int WZ,
+                                          const double* ion_x, const double* ion_c, double ion_coef) {
+  for (int li = threadIdx.y; li < WX; li += FT_TY) {
+    const int gi = gi0 + li;
+    const bool rowok = gi >= 0 && gi <= g.nx;
+    const double ix = (rowok && ion_x) ? ion_coef * ion_x[gi] : 0.0;
+    for (int lk = threadIdx.x; lk < WZ; lk += FT_Z) {
+      const int gk = gk0 + lk;
+      T v = T(0);
+      if (rowok && gk >= 0 && gk <= g.nz) {
+        v = src[(long)gi * g.ld + gk];
+        if (ion_x) v += T(ix * ion_c[gk]);
+      }
+      A[li * WZ + lk] = v;
+    }
+  }
 }
 
+// x-pass: B1[ti][lk] = sum_j c_j A[ti + H + (j - P) s][lk] for the tile's rows
 template <class T>
-__device__ T* filter_tile(T* A, T* Bf, const TileGeo& t, const FilterSpec& fs, int H) {
-  const int s = fs.stride;
-  const int P = fs.passes + (fs.compensate ? 1 : 0);
-  // along x
-  for (int pass = 0; pass < P; pass++) {
-    T al = pass < fs.passes ? T(0.5) : T(0.5 * fs.passes + 1.0);
-    T be = (T(1) - al) * T(0.5);
-    for (int e = threadIdx.x; e < t.WX * t.WZ; e += blockDim.x) {
-      int li = e / t.WZ, lk = e - li * t.WZ;
-      T v = T(0);
-      if (tvalid<T>(t, li, lk)) {
-        T l = li - s >= 0 ? A[e - s * t.WZ] : T(0);
-        T r = li + s < t.WX ? A[e + s * t.WZ] : T(0);
-        v = al * A[e] + be * (l + r);
-      }
-      Bf[e] = v;
+__device__ __forceinline__ void xpass(const T* A, T* B1, const FilterTaps<T>& ft, int WZ) {
+  for (int ti = threadIdx.y; ti < FT_X; ti += FT_TY) {
+    for (int lk = threadIdx.x; lk < WZ; lk += FT_Z) {
+      const T* col = A + (ti + ft.H - ft.P * ft.s) * WZ + lk;
+      T acc = T(0);
+      for (int j = 0; j <= 2 * ft.P; j++) acc += ft.c[j] * col[j * ft.s * WZ];
+      B1[ti * WZ + lk] = acc;
     }
-    __syncthreads();
-    T* tmp = A; A = Bf; Bf = tmp;
   }
-  // along z (only the rows of the tile are needed)
-  for (int pass = 0; pass < P; pass++) {
-    T al = pass < fs.passes ? T(0.5) : T(0.5 * fs.passes + 1.0);
-    T be = (T(1) - al) * T(0.5);
-    const int rows = t.WX - 2 * H;
-    for (int e = threadIdx.x; e < rows * t.WZ; e += blockDim.x) {
-      int li = H + e / t.WZ, lk = e % t.WZ;
-      int q = li * t.WZ + lk;
-      T v = T(0);
-      if (tvalid<T>(t, li, lk)) {
-        T l = lk - s >= 0 ? A[q - s] : T(0);
-        T r = lk + s < t.WZ ? A[q + s] : T(0);
-        v = al * A[q] + be * (l + r);
-      }
-      Bf[q] = v;
-    }
-    __syncthreads();
-    T* tmp = A; A = Bf; Bf = tmp;
-  }
-  return A;
 }
 
+// z-pass value at (ti, tk)
 template <class T>
-__device__ void load_tile(T* A, const T* src, const GridP& g, const TileGeo& t,
-                          const double* ion_x, const double* ion_c, double ion_coef) {
-  for (int e = threadIdx.x; e < t.WX * t.WZ; e += blockDim.x) {
-    int li = e / t.WZ, lk = e - li * t.WZ;
-    int gi = t.gi0 + li, gk = t.gk0 + lk;
-    T v = T(0);
-    if (gi >= 0 && gi <= g.nx && gk >= 0 && gk <= g.nz) {
-      v = src[(long)gi * g.ld + gk];
-      if (ion_x) v += T(ion_coef * ion_x[gi] * ion_c[gk]);
-    }
-    A[e] = v;
-  }
+__device__ __forceinline__ T zpass(const T* B1, const FilterTaps<T>& ft, int WZ, int ti, int tk) {
+  const T* row = B1 + ti * WZ + tk + ft.H - ft.P * ft.s;
+  T acc = T(0);
+  for (int j = 0; j <= 2 * ft.P; j++) acc += ft.c[j] * row[j * ft.s];
+  return acc;
 }
 
 // gather copies: fE = F(E^n), fB = F(Bavg)
 template <class T>
-__global__ void __launch_bounds__(FT_THREADS) k_filter_fields(GridP g, FieldPtrs<T> f, FilterSpec fs) {
+__global__ void __launch_bounds__(FT_Z* FT_TY) k_filter_fields(GridP g, FieldPtrs<T> f, FilterTaps<T> ft) {
   extern __shared__ unsigned char smraw[];
   T* A = reinterpret_cast<T*>(smraw);
-  const int H = (fs.passes + (fs.compensate ? 1 : 0)) * fs.stride;
-  TileGeo t;
-  t.WX = FT_X + 2 * H; t.WZ = FT_Z + 2 * H;
-  T* Bf = A + t.WX * t.WZ;
+  const int H = ft.H;
+  const int WX = FT_X + 2 * H, WZ = FT_Z + 2 * H;
+  T* B1 = A + WX * WZ;
   const int i0 = blockIdx.y * FT_X, k0 = blockIdx.x * FT_Z;
-  t.gi0 = i0 - H; t.gk0 = k0 - H;
   for (int c = 0; c < 6; c++) {
     const T* src = c < 3 ? f.E[c] : f.Bavg[c - 3];
     T* dst = c < 3 ? f.fE[c] : f.fB[c - 3];
-    valid_range(c, g.nx, g.nz, t.vi0, t.vi1, t.vk0, t.vk1);
-    load_tile<T>(A, src, g, t, nullptr, nullptr, 0.0);
+    load_tile<T>(A, src, g, i0 - H, k0 - H, WX, WZ, nullptr, nullptr, 0.0);
     __syncthreads();
-    T* R = filter_tile<T>(A, Bf, t, fs, H);
-    for (int e = threadIdx.x; e < FT_X * FT_Z; e += blockDim.x) {
-      int ti = e / FT_Z, tk = e - ti * FT_Z;
-      int gi = i0 + ti, gk = k0 + tk;
-      if (gi <= g.nx && gk <= g.nz) dst[(long)gi * g.ld + gk] = R[(ti + H) * t.WZ + tk + H];
+    xpass<T>(A, B1, ft, WZ);
+    __syncthreads();
+    const int gk = k0 + threadIdx.x;
+    for (int ti = threadIdx.y; ti < FT_X; ti += FT_TY) {
+      const int gi = i0 + ti;
+      const T v = zpass<T>(B1, ft, WZ, ti, threadIdx.x);
+      if (gi <= g.nx && gk <= g.nz) dst[(long)gi * g.ld + gk] = v;
     }
     __syncthreads();
   }
 }
 
-// Ampere + PML-E, with the current filtered in the tile first
+// Ampere + PML-E, with the current (plus the ion column current) filtered in the tile first
 template <class T, bool FILT>
-__global__ void __launch_bounds__(FT_THREADS) k_ampere(GridP g, FieldPtrs<T> f, PmlTabs pt, FilterSpec fs,
-                                                       const double* ion_x, const double* ion_c, double ion_coef) {
+__global__ void __launch_bounds__(FT_Z* FT_TY) k_ampere(GridP g, FieldPtrs<T> f, PmlTabs pt, FilterTaps<T> ft,
+                                                        const double* ion_x, const double* ion_c, double ion_coef) {
   extern __shared__ unsigned char smraw[];
   T* A = reinterpret_cast<T*>(smraw);
-  const int H = FILT ? (fs.passes + (fs.compensate ? 1 : 0)) * fs.stride : 0;
-  TileGeo t;
-  t.WX = FT_X + 2 * H; t.WZ = FT_Z + 2 * H;
-  T* Bf = A + t.WX * t.WZ;
+  const int H = FILT ? ft.H : 0;
+  const int WX = FT_X + 2 * H, WZ = FT_Z + 2 * H;
+  T* B1 = A + WX * WZ;
   const int i0 = blockIdx.y * FT_X, k0 = blockIdx.x * FT_Z;
-  t.gi0 = i0 - H; t.gk0 = k0 - H;
   const T dt = T(g.dt);
   const T c2 = T(kC * kC);
   const T ie0 = T(1.0 / kEps0);
   const double c2d = kC * kC;
+  const int k = k0 + threadIdx.x;
   for (int c = 0; c < 3; c++) {
-    valid_range(c, g.nx, g.nz, t.vi0, t.vi1, t.vk0, t.vk1);
+    int vi0, vi1, vk0, vk1;
+    valid_range(c, g.nx, g.nz, vi0, vi1, vk0, vk1);
     const bool ion = (c == 2) && ion_x != nullptr;
-    load_tile<T>(A, f.J[c], g, t, ion ? ion_x : nullptr, ion_c, ion_coef);
+    load_tile<T>(A, f.J[c], g, i0 - H, k0 - H, WX, WZ, ion ? ion_x : nullptr, ion_c, ion_coef);
     __syncthreads();
-    T* R = FILT ? filter_tile<T>(A, Bf, t, fs, H) : A;
-    for (int e = threadIdx.x; e < FT_X * FT_Z; e += blockDim.x) {
-      int ti = e / FT_Z, tk = e - ti * FT_Z;
-      int i = i0 + ti, k = k0 + tk;
+    if (FILT) {
+      xpass<T>(A, B1, ft, WZ);
+      __syncthreads();
+    }
+    for (int ti = threadIdx.y; ti < FT_X; ti += FT_TY) {
+      const int i = i0 + ti;
       if (i > g.nx || k > g.nz) continue;
       const long p = (long)i * g.ld + k;
       f.Jn[c][p] = T(0);
-      const bool v = i >= t.vi0 && i <= t.vi1 && k >= t.vk0 && k <= t.vk1;
+      const bool v = i >= vi0 && i <= vi1 && k >= vk0 && k <= vk1;
       if (!v) { f.Eo[c][p] = T(0); continue; }
-      const T jv = R[(ti + H) * t.WZ + tk + H];
+      const T jv = FILT ? zpass<T>(B1, ft, WZ, ti, threadIdx.x) : A[ti * WZ + threadIdx.x];
       const T eo = f.E[c][p];
       T en;
       if (c == 0) {
@@ -286,41 +262,53 @@ void launch_faraday(const GridP& g, const FieldPtrs<T>& f, const PmlTabs& pt, do
   }
 }
 
-static size_t tile_smem(int H, size_t elem) { return 2 * (size_t)(FT_X + 2 * H) * (FT_Z + 2 * H) * elem; }
+static size_t tile_smem(int H, size_t elem) {
+  return ((size_t)(FT_X + 2 * H) * (FT_Z + 2 * H) + (size_t)FT_X * (FT_Z + 2 * H)) * elem;
+}
+
+template <class T>
+static FilterTaps<T> make_taps(const FilterSpec& fs) {
+  // compose n bilinear passes (alpha = 1/2) and the compensation pass (alpha_c = n/2 + 1)
+  double k[2 * 16 + 1] = {0.0};
+  int len = 1;
+  k[0] = 1.0;
+  const int P = fs.passes + (fs.compensate ? 1 : 0);
+  for (int p = 0; p < P; p++) {
+    const double al = p < fs.passes ? 0.5 : 0.5 * fs.passes + 1.0;
+    const double be = 0.5 * (1.0 - al);
+    double r[2 * 16 + 1] = {0.0};
+    for (int j = 0; j < len; j++) { r[j] += be * k[j]; r[j + 1] += al * k[j]; r[j + 2] += be * k[j]; }
+    len += 2;
+    for (int j = 0; j < len; j++) k[j] = r[j];
+  }
+  FilterTaps<T> ft;
+  ft.P = P; ft.s = fs.stride; ft.H = P * fs.stride;
+  for (int j = 0; j < 2 * 16 + 1; j++) ft.c[j] = T(j < len ? k[j] : 0.0);
+  return ft;
+}
 
 template <class T>
 void launch_filter_fields(const GridP& g, const FieldPtrs<T>& f, const FilterSpec& fs, bool enabled, cudaStream_t s) {
   if (!enabled) return;
-  const int H = (fs.passes + (fs.compensate ? 1 : 0)) * fs.stride;
-  dim3 grd((g.nz + 1 + FT_Z - 1) / FT_Z, (g.nx + 1 + FT_X - 1) / FT_X);
-  size_t sm = tile_smem(H, sizeof(T));
-  static bool attr_set[2] = {false, false};
-  if (!attr_set[sizeof(T) == 8]) {
-    cudaFuncSetAttribute(k_filter_fields<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_set[sizeof(T) == 8] = true;
-  }
-  k_filter_fields<T><<<grd, FT_THREADS, sm, s>>>(g, f, fs);
+  const FilterTaps<T> ft = make_taps<T>(fs);
+  dim3 grd((g.nz + 1 + FT_Z - 1) / FT_Z, (g.nx + 1 + FT_X - 1) / FT_X), blk(FT_Z, FT_TY);
+  size_t sm = tile_smem(ft.H, sizeof(T));
+  cudaFuncSetAttribute(k_filter_fields<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_filter_fields<T><<<grd, blk, sm, s>>>(g, f, ft);
 }
 
 template <class T>
 void launch_ampere(const GridP& g, const FieldPtrs<T>& f, const PmlTabs& pt, const FilterSpec& fs, bool filter_on,
                    const double* ion_x, const double* ion_c, double ion_coef, cudaStream_t s) {
-  const int H = filter_on ? (fs.passes + (fs.compensate ? 1 : 0)) * fs.stride : 0;
-  dim3 grd((g.nz + 1 + FT_Z - 1) / FT_Z, (g.nx + 1 + FT_X - 1) / FT_X);
-  size_t sm = tile_smem(H, sizeof(T));
-  static bool attr_set[2][2] = {{false, false}, {false, false}};
+  const FilterTaps<T> ft = make_taps<T>(fs);
+  dim3 grd((g.nz + 1 + FT_Z - 1) / FT_Z, (g.nx + 1 + FT_X - 1) / FT_X), blk(FT_Z, FT_TY);
   if (filter_on) {
-    if (!attr_set[sizeof(T) == 8][1]) {
-      cudaFuncSetAttribute(k_ampere<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      attr_set[sizeof(T) == 8][1] = true;
-    }
-    k_ampere<T, true><<<grd, FT_THREADS, sm, s>>>(g, f, pt, fs, ion_x, ion_c, ion_coef);
+    size_t sm = tile_smem(ft.H, sizeof(T));
+    cudaFuncSetAttribute(k_ampere<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_ampere<T, true><<<grd, blk, sm, s>>>(g, f, pt, ft, ion_x, ion_c, ion_coef);
   } else {
-    if (!attr_set[sizeof(T) == 8][0]) {
-      cudaFuncSetAttribute(k_ampere<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      attr_set[sizeof(T) == 8][0] = true;
-    }
-    k_ampere<T, false><<<grd, FT_THREADS, sm, s>>>(g, f, pt, fs, ion_x, ion_c, ion_coef);
+    size_t sm = tile_smem(0, sizeof(T));
+    k_ampere<T, false><<<grd, blk, sm, s>>>(g, f, pt, ft, ion_x, ion_c, ion_coef);
   }
 }
 

@@ -69,6 +69,7 @@ struct PushConst {
   float dtdx, dtdz;                 // mixed path
   double qm_half;                   // q dt/(2m)
   double kx, kz, ky;                // deposit: -q/(dz dt), -q/(dx dt), q/(dx dz)
+  float qm_half_f, kx_f, kz_f, ky_f;  // the same in FP32 for the mixed path
 };
 
 // One particle: gather -> Boris -> move -> Esirkepov. E/B/J are 3-component
@@ -111,7 +112,8 @@ __device__ __forceinline__ void push_one(const T* __restrict__ Eb, const T* __re
   const T By = interp<T, ORDER>(Bb + cs, ld, ox, oz, fxh, fzh, wxh, wzh);
   const T Bz = interp<T, ORDER>(Bb + 2 * cs, ld, ox, oz, fxh, fz, wxh, wzi);
   // relativistic Boris push
-  const T k = T(pc.qm_half);
+  T k;
+  if constexpr (CP) k = pc.qm_half_f; else k = T(pc.qm_half);
   const T ic2 = T(1.0 / (kC * kC));
   T umx = ux + k * Ex, umy = uy + k * Ey, umz = uz + k * Ez;
   T gm = sqrt(T(1) + (umx * umx + umy * umy + umz * umz) * ic2);
@@ -160,9 +162,12 @@ __device__ __forceinline__ void push_one(const T* __restrict__ Eb, const T* __re
   T DSx[ND], DSz[ND];
 #pragma unroll
   for (int a = 0; a < ND; a++) { DSx[a] = S1x[a] - S0x[a]; DSz[a] = S1z[a] - S0z[a]; }
-  const T cx = T(pc.kx) * w;
-  const T cz = T(pc.kz) * w;
-  const T cy = T(pc.ky) * w * vy;
+  T cx, cz, cy;
+  if constexpr (CP) {
+    cx = pc.kx_f * w; cz = pc.kz_f * w; cy = pc.ky_f * w * vy;
+  } else {
+    cx = T(pc.kx) * w; cz = T(pc.kz) * w; cy = T(pc.ky) * w * vy;
+  }
   T* Jx = Jb + (long)(bx - ox) * ld + (bz - oz);
   T* Jy = Jx + cs;
   T* Jz = Jx + 2 * cs;
@@ -249,7 +254,7 @@ __device__ __noinline__ void push_global_guarded(const T* gE, const T* gB, T* gJ
 }
 
 template <class T, int ORDER>
-__global__ void __launch_bounds__(PB_THREADS) k_push(GridP g, const T* gE, const T* gB, T* gJ, Particles<T> p,
+__global__ void __launch_bounds__(PB_THREADS, 4) k_push(GridP g, const T* gE, const T* gB, T* gJ, Particles<T> p,
                                                      Chunk* chunks, Ctrl* ctrl, int cap_nodes, PushConst pc) {
   extern __shared__ unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);
@@ -272,17 +277,19 @@ __global__ void __launch_bounds__(PB_THREADS) k_push(GridP g, const T* gE, const
     const int wx0 = ch.ix0 - St<ORDER>::LO, wx1 = ch.ix1 + St<ORDER>::HI;
     const int wz0 = ch.iz0 - St<ORDER>::LO, wz1 = ch.iz1 + St<ORDER>::HI;
     const int wxn = wx1 - wx0 + 1, wzn = wz1 - wz0 + 1;
-    const int nn = wxn * wzn;
+    const int lds = wzn;
+    const int nn = wxn * lds;
     const bool use_smem = nn <= cap_nodes && wx0 >= 0 && wz0 >= 0 && wx1 <= g.nx && wz1 <= g.nz;
     int bx0 = INT_MAX, bx1 = INT_MIN, bz0 = INT_MAX, bz1 = INT_MIN;
     if (use_smem) {
       for (int e = threadIdx.x; e < nn; e += blockDim.x) {
-        const int li = e / wzn, lk = e - li * wzn;
+        const int li = e / lds, lk = e - li * lds;
         const long gp = (long)(wx0 + li) * g.ld + (wz0 + lk);
+        const bool in = lk < wzn;
 #pragma unroll
         for (int q = 0; q < 3; q++) {
-          sm[q * cap_nodes + e] = gE[q * g.cs + gp];
-          sm[(3 + q) * cap_nodes + e] = gB[q * g.cs + gp];
+          sm[q * cap_nodes + e] = in ? gE[q * g.cs + gp] : T(0);
+          sm[(3 + q) * cap_nodes + e] = in ? gB[q * g.cs + gp] : T(0);
           sm[(6 + q) * cap_nodes + e] = T(0);
         }
       }
@@ -292,14 +299,15 @@ __global__ void __launch_bounds__(PB_THREADS) k_push(GridP g, const T* gE, const
         int fx = 0, fz = 0;
         const bool fin = particle_cell<T>(p, pi, pc, fx, fz);
         if (fin && fx >= ch.ix0 && fx <= ch.ix1 && fz >= ch.iz0 && fz <= ch.iz1)
-          push_one<T, ORDER, true>(sm, sm + 3 * cap_nodes, sm + 6 * cap_nodes, cap_nodes, wzn, wx0, wz0, p, pi, pc,
+          push_one<T, ORDER, true>(sm, sm + 3 * cap_nodes, sm + 6 * cap_nodes, cap_nodes, lds, wx0, wz0, p, pi, pc,
                                    bx0, bx1, bz0, bz1);
         else
           push_global_guarded<T, ORDER>(gE, gB, gJ, g, p, pi, pc, ctrl, bx0, bx1, bz0, bz1);
       }
       __syncthreads();
       for (int e = threadIdx.x; e < nn; e += blockDim.x) {
-        const int li = e / wzn, lk = e - li * wzn;
+        const int li = e / lds, lk = e - li * lds;
+        if (lk >= wzn) continue;
         const long gp = (long)(wx0 + li) * g.ld + (wz0 + lk);
 #pragma unroll
         for (int q = 0; q < 3; q++) {
@@ -536,6 +544,7 @@ void launch_push(const GridP& g, const FieldPtrs<T>& f, Particles<T> p, Chunk* c
   pc.dtdx = (float)(g.dt / g.dx); pc.dtdz = (float)(g.dt / g.dz);
   pc.qm_half = q * g.dt / (2.0 * m);
   pc.kx = -q / (g.dz * g.dt); pc.kz = -q / (g.dx * g.dt); pc.ky = q / (g.dx * g.dz);
+  pc.qm_half_f = (float)pc.qm_half; pc.kx_f = (float)pc.kx; pc.kz_f = (float)pc.kz; pc.ky_f = (float)pc.ky;
   const size_t sm = (size_t)9 * smem_nodes * sizeof(T);
   cudaMemsetAsync(&ctrl->next_chunk, 0, sizeof(int), s);
   if (order == 3) {
