@@ -202,6 +202,31 @@ int pic_get_particles(pic_ctx* ctx, int species, double* x, double* z, double* u
 int pic_get_stats(pic_ctx* ctx, pic_stats* out);
 const char* pic_last_error(pic_ctx* ctx);
 
+/* Largest nz accepted by pic_get_rho_noalloc (size of its static scratch). */
+#define PIC_NOALLOC_MAX_NZ 16384
+
+/* Charge density without any device allocation. Same result as
+ * pic_get_field(ctx, PIC_RHO, dst_device, 1), for callers that must not
+ * allocate device memory once their run is set up: for example an application
+ * whose device memory is entirely owned by its own pool allocator, or a
+ * real-time loop that cannot afford the latency and implicit device
+ * synchronisation of cudaMalloc/cudaFree. (The paper has no counterpart: this
+ * is a service of the library, not part of the method.)
+ *  - dst_device: caller-owned device buffer of (nx+1)*(nz+1) doubles, written in
+ *    the layout of pic_get_field. It is zeroed and filled on the context's
+ *    stream; the call returns without waiting (pic_sync or a stream
+ *    synchronisation makes the result visible to the host).
+ *  - The ion row density is staged in a file-scope static device array of
+ *    PIC_NOALLOC_MAX_NZ+1 doubles (128 KiB) that every GPU loading the library
+ *    keeps until the process exits. The first call on a device looks up that
+ *    array's device address (cudaGetSymbolAddress, with the device current);
+ *    make that first call before any stream capture.
+ *  - All calls share the array and it keeps the last call's contents; calls
+ *    whose work overlaps on the GPU (several contexts or streams at once) race.
+ *  - nz > PIC_NOALLOC_MAX_NZ is rejected with PIC_EINVAL (pic_last_error says
+ *    why). No cudaMalloc, cudaFree or allocator callback is used. */
+int pic_get_rho_noalloc(pic_ctx* ctx, double* dst_device);
+
 /* Number of kernel launches enqueued so far by this context (bench accounting). */
 int64_t pic_kernel_launches(pic_ctx* ctx);
 

@@ -27,7 +27,8 @@ STATUS_NAMES = {0: "PIC_OK", -1: "PIC_EINVAL", -2: "PIC_ENOMEM", -3: "PIC_ECFL",
 # every symbol include/pic.h declares
 EXPORTS = ("pic_init", "pic_load_plasma", "pic_inject_laser", "pic_step", "pic_sync", "pic_boosted_to_lab_diag",
            "pic_free", "pic_get_field", "pic_set_field", "pic_get_particles", "pic_get_stats", "pic_last_error",
-           "pic_kernel_launches", "pic_kernel_timing")
+           "pic_kernel_launches", "pic_kernel_timing", "pic_get_rho_noalloc")
+NOALLOC_MAX_NZ = 16384
 
 _D = ctypes.POINTER(ctypes.c_double)
 
@@ -142,5 +143,6 @@ def load(build_if_missing: bool = True):
         L.pic_kernel_launches.argtypes = [vp]
         L.pic_kernel_launches.restype = ctypes.c_int64
         L.pic_kernel_timing.argtypes = [vp, ctypes.c_int, ctypes.c_int, _D, ctypes.POINTER(ctypes.c_int64)]
+        L.pic_get_rho_noalloc.argtypes = [vp, _D]
         _lib = L
         return L

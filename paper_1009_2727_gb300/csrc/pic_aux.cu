@@ -7,6 +7,9 @@
 //  - the test beam through a plane (Sec. 3.1.1): Lorentz transform and push;
 //  - back-transformed lab-frame samples (Sec. 3.2, PR-16);
 //  - charge density, reductions, moving-window shift, copies.
+#include <mutex>
+
+#include "../../include/pic.h"
 #include "pic_common.cuh"
 
 namespace picgb {
@@ -427,6 +430,46 @@ __global__ void k_shift_particles(Particles<T> p, const Ctrl* ctrl, int sh) {
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// Charge density without device allocation: the ion row density R(k) goes to
+// this file-scope scratch instead of a context buffer. Its device address is
+// looked up once per device, with that device current.
+static __device__ __align__(256) double g_noalloc_rows[PIC_NOALLOC_MAX_NZ + 1];
+
+static double* noalloc_rows_address(int& err) {
+  static std::mutex mu;
+  static double* addr[256] = {nullptr};
+  int dev = 0;
+  err = (int)cudaGetDevice(&dev);
+  if (err != (int)cudaSuccess || dev < 0 || dev >= 256) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!addr[dev]) {
+    void* p = nullptr;
+    err = (int)cudaGetSymbolAddress(&p, g_noalloc_rows);
+    if (err != (int)cudaSuccess) return nullptr;
+    addr[dev] = (double*)p;
+  }
+  return addr[dev];
+}
+
+template <class T>
+int launch_rho_noalloc(const GridP& g, Particles<T> p, const Ctrl* ctrl, int cap, int order, bool ions,
+                       long long mlo, long long mhi, double t, const InjectP& ip, const double* ion_x, double* dst,
+                       cudaStream_t s) {
+  if (g.nz > PIC_NOALLOC_MAX_NZ) return 1;
+  int err = 0;
+  double* rows = noalloc_rows_address(err);
+  if (!rows) return 2;
+  cudaMemsetAsync(dst, 0, sizeof(double) * (size_t)(g.nx + 1) * (g.nz + 1), s);
+  if (cap > 0) k_rho<T><<<(cap + 255) / 256, 256, 0, s>>>(g, p, ctrl, order, -kQe, dst);
+  if (ions) {
+    // the same row-density kernel as the step, at one time (both outputs alias the scratch)
+    k_ion_rows<<<dim3((g.nz + 1 + 31) / 32, 1), 32, 0, s>>>(g, mlo, mhi, t, t, ip, order, rows, rows);
+    launch_ion_rho(g, ion_x, rows, kQe / (g.dx * g.dz), dst, s);
+  }
+  return cudaPeekAtLastError() == cudaSuccess ? 0 : 3;
+}
+
 void launch_ion_column(const GridP& g, long long mlo, long long mhi, double t0, double t1, const InjectP& ip,
                        int order, double* R0, double* R1, double* C, cudaStream_t s) {
   k_ion_rows<<<dim3((g.nz + 1 + 31) / 32, 2), 32, 0, s>>>(g, mlo, mhi, t0, t1, ip, order, R0, R1);
@@ -539,7 +582,9 @@ void launch_shift_particles(Particles<T> p, const Ctrl* ctrl, int cap, int sh, c
   template void launch_convert_back<T>(const double*, T*, const GridP&, cudaStream_t);                           \
   template void launch_compact_copy<T>(const GridP&, Particles<T>, const Ctrl*, int, double*, uint32_t*, int*,      \
                                        cudaStream_t);                                                             \
-  template void launch_shift_particles<T>(Particles<T>, const Ctrl*, int, int, cudaStream_t);
+  template void launch_shift_particles<T>(Particles<T>, const Ctrl*, int, int, cudaStream_t);                 \
+  template int launch_rho_noalloc<T>(const GridP&, Particles<T>, const Ctrl*, int, int, bool, long long,         \
+                                     long long, double, const InjectP&, const double*, double*, cudaStream_t);
 INST(float)
 INST(double)
 #undef INST

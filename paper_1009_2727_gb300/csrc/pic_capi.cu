@@ -621,6 +621,21 @@ struct Sim : SimBase {
     return cudaGetLastError() == cudaSuccess ? PIC_OK : c->fail(PIC_ECUDA, "CUDA error in get_field");
   }
 
+  int get_rho_noalloc(double* dst) {
+    long long mlo = row_first;
+    if (ions && loaded && step > 0) {
+      const double t = time_of(step);
+      mlo = std::max(row_first, (long long)std::ceil((zlo_prev + c->hg.beta * kC * t) / ip.h - 0.5));
+    }
+    int r = launch_rho_noalloc<T>(g, P, ctrl, loaded ? cap : 0, c->cfg.shape_order, ions && loaded, mlo, row_next,
+                                  time_of(step), ip, ion_x, dst, c->stream);
+    if (r == 1) return c->fail(PIC_EINVAL, "pic_get_rho_noalloc: nz exceeds PIC_NOALLOC_MAX_NZ");
+    if (r == 2) return c->fail(PIC_ECUDA, "pic_get_rho_noalloc: cudaGetSymbolAddress of the scratch failed");
+    if (r == 3) return c->fail(PIC_ECUDA, "pic_get_rho_noalloc: kernel launch failed");
+    c->launches += ions && loaded ? 4 : 2;
+    return PIC_OK;
+  }
+
   int set_field(int comp, const double* src) {
     if (comp < PIC_EX || comp > PIC_BZ) return c->fail(PIC_EINVAL, "only E and B can be set");
     cudaMemcpyAsync(stage, src, stage_n * 8, cudaMemcpyHostToDevice, c->stream);
@@ -869,6 +884,13 @@ int pic_get_field(pic_ctx* c, int comp, double* dst, int on_device) {
   if (!c || !dst) return PIC_EINVAL;
   if (c->status != PIC_OK) return c->status;
   return DISPATCH(c, get_field(comp, dst, on_device));
+}
+
+int pic_get_rho_noalloc(pic_ctx* c, double* dst_device) {
+  if (!c || !dst_device) return PIC_EINVAL;
+  if (c->status != PIC_OK) return c->status;
+  if (c->cfg.nz > PIC_NOALLOC_MAX_NZ) return c->fail(PIC_EINVAL, "pic_get_rho_noalloc: nz exceeds PIC_NOALLOC_MAX_NZ");
+  return DISPATCH(c, get_rho_noalloc(dst_device));
 }
 
 int pic_set_field(pic_ctx* c, int comp, const double* src) {

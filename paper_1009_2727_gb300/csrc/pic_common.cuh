@@ -220,5 +220,10 @@ void launch_compact_copy(const GridP& g, Particles<T> p, const Ctrl* ctrl, int c
                          int* nout, cudaStream_t s);
 template <class T>
 void launch_shift_particles(Particles<T> p, const Ctrl* ctrl, int cap, int sh, cudaStream_t s);
+// returns 0, or 1 (nz above the scratch size), 2 (scratch address lookup failed), 3 (launch error)
+template <class T>
+int launch_rho_noalloc(const GridP& g, Particles<T> p, const Ctrl* ctrl, int cap, int order, bool ions,
+                       long long mlo, long long mhi, double t, const InjectP& ip, const double* ion_x, double* dst,
+                       cudaStream_t s);
 
 }  // namespace picgb
