@@ -78,7 +78,8 @@ typedef struct {
   double pml_delta;       /* Delta in cells (paper: 5) */
   double pml_power;       /* profile exponent n (paper: 2) */
   int32_t pml_xi_exp;     /* 1: xi = exp(-sigma dt); 0: (1 - sigma dt/2)/(1 + sigma dt/2) */
-  int32_t filter_passes;  /* bilinear passes per axis (Eq. 3ptfilter, alpha = 1/2) */
+  int32_t filter_passes;  /* bilinear passes per axis (Eq. 3ptfilter, alpha = 1/2); passes plus the
+                             compensation pass <= 16 and (that count) x stride <= 32, else PIC_EINVAL */
   int32_t filter_stride;  /* stride s (Eq. 3ptfilter_stride) */
   int32_t filter_compensate; /* 1: one extra pass with alpha_c = n/2 + 1 */
   int32_t filter_J;       /* filter the deposited current */

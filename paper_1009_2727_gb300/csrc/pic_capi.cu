@@ -101,6 +101,7 @@ struct Sim : SimBase {
   T* tmp = nullptr;
   Ctrl* ctrl = nullptr;
   Ctrl* hmirror = nullptr;     // pinned
+  TileMaps tmaps{};
   // particles
   Particles<T> P{}, P2{};
   Chunk* chunks = nullptr;
@@ -219,6 +220,11 @@ struct Sim : SimBase {
     pt.cz_i = dz_t + 4 * nz1; pt.cz_h = dz_t + 5 * nz1;
     ctrl = al<Ctrl>(1);
     stats_buf = al<double>(8);
+    {
+      const int P = cf.filter_passes + (cf.filter_compensate ? 1 : 0);
+      const int H = (filt_gather || filt_J) ? P * cf.filter_stride : 0;
+      if (!make_tile_maps<T>(g, f, H, tmaps)) return c->fail(PIC_ECUDA, "TMA descriptor encoding failed");
+    }
     stage_n = (size_t)nx1 * nz1;
     stage = al<double>(stage_n);
     if (!ctrl || !stats_buf || !stage) return c->fail(PIC_ENOMEM, "allocation failed");
@@ -482,7 +488,7 @@ struct Sim : SimBase {
     tstart(1);
     launch_faraday<T>(g, f, pt, h.a2, h.b2, cf.theta, friedman, c->stream);
     // 2. gather copies
-    launch_filter_fields<T>(g, f, fs, filt_gather, c->stream);
+    launch_filter_fields<T>(g, f, fs, filt_gather, tmaps, ctrl, c->stream);
     tstop(1);
     c->launches += 1 + (filt_gather ? 1 : 0);
     // 3. particles
@@ -512,7 +518,7 @@ struct Sim : SimBase {
     }
     // 6-7. current filter + Ampere + PML-E
     tstart(1);
-    launch_ampere<T>(g, f, pt, fs, filt_J, (ions && loaded) ? ion_x : nullptr, ion_C, ion_coef, c->stream);
+    launch_ampere<T>(g, f, pt, fs, filt_J, (ions && loaded) ? ion_x : nullptr, ion_C, ion_coef, tmaps, ctrl, c->stream);
     tstop(1);
     c->launches++;
     for (int q = 0; q < 3; q++) {
@@ -783,6 +789,10 @@ int pic_init(const pic_config* cfg, pic_alloc_fn alloc, pic_free_fn free_fn, voi
   if (std::fabs(cfg->ck_alpha + 4 * cfg->ck_beta + 4 * cfg->ck_gamma - 1.0) > 1e-12) return PIC_EINVAL;
   if (cfg->theta < 0 || cfg->theta > 1) return PIC_EINVAL;
   if (cfg->filter_passes < 0 || cfg->filter_stride < 1 || cfg->pml_cells < 0) return PIC_EINVAL;
+  // the composed filter has at most 33 taps and a halo of at most 32 cells (staged tile in shared memory)
+  if (cfg->filter_passes + (cfg->filter_compensate ? 1 : 0) > 16 ||
+      (cfg->filter_passes + (cfg->filter_compensate ? 1 : 0)) * cfg->filter_stride > 32)
+    return PIC_EINVAL;
   std::unique_ptr<pic_ctx> c(new pic_ctx());
   c->cfg = *cfg;
   c->stream = (cudaStream_t)cuda_stream;

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace picgb {
@@ -134,11 +135,26 @@ __device__ __forceinline__ void weights1(R t, R* w) {
 template <class T>
 void launch_faraday(const GridP& g, const FieldPtrs<T>& f, const PmlTabs& pt, double a2, double b2,
                     double theta, bool friedman, cudaStream_t s);
+// TMA descriptors of the 3-component blocks read by the tile kernels (a 3D tensor
+// (nz+1) x (nx+1) x 3 per block; out-of-range elements read as zero)
+struct TileMaps {
+  CUtensorMap E[2];     // the two E buffers
+  CUtensorMap J[2];     // the two current buffers
+  CUtensorMap Bavg;
+  const void* Ebase[2];
+  const void* Jbase[2];
+  int H, HZ, BX, BZ;    // halo (cells), aligned z halo, box extents
+  bool ok;
+};
 template <class T>
-void launch_filter_fields(const GridP& g, const FieldPtrs<T>& f, const FilterSpec& fs, bool enabled, cudaStream_t s);
+bool make_tile_maps(const GridP& g, const FieldPtrs<T>& f, int H, TileMaps& tm);
+template <class T>
+void launch_filter_fields(const GridP& g, const FieldPtrs<T>& f, const FilterSpec& fs, bool enabled,
+                          const TileMaps& tm, Ctrl* ctrl, cudaStream_t s);
 template <class T>
 void launch_ampere(const GridP& g, const FieldPtrs<T>& f, const PmlTabs& pt, const FilterSpec& fs, bool filter_on,
-                   const double* ion_x, const double* ion_c, double ion_coef, cudaStream_t s);
+                   const double* ion_x, const double* ion_c, double ion_coef, const TileMaps& tm, Ctrl* ctrl,
+                   cudaStream_t s);
 
 template <class T>
 void launch_push(const GridP& g, const FieldPtrs<T>& f, Particles<T> p, Chunk* chunks, Ctrl* ctrl, int order,

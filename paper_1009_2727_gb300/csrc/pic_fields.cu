@@ -110,33 +110,75 @@ constexpr int FT_X = 16;
 constexpr int FT_Z = 64;
 constexpr int FT_TY = 4;
 
-template <class T>
-__device__ __forceinline__ void load_tile(T* A, const T* src, const GridP& g, int gi0, int gk0, int WX, int WZ,
-                                          const double* ion_x, const double* ion_c, double ion_coef) {
-  for (int li = threadIdx.y; li < WX; li += FT_TY) {
-    const int gi = gi0 + li;
-    const bool rowok = gi >= 0 && gi <= g.nx;
-    const double ix = (rowok && ion_x) ? ion_coef * ion_x[gi] : 0.0;
-    for (int lk = threadIdx.x; lk < WZ; lk += FT_Z) {
-      const int gk = gk0 + lk;
-      T v = T(0);
-      if (rowok && gk >= 0 && gk <= g.nz) {
-        v = src[(long)gi * g.ld + gk];
-        if (ion_x) v += T(ix * ion_c[gk]);
-      }
-      A[li * WZ + lk] = v;
-    }
-  }
+// ---------------------------------------------------------------------------
+// TMA staging: one elected thread issues a 3D bulk tensor copy of the tile +
+// halo (box BZ x BX x 1 of component c) into shared memory; completion is
+// signalled on an mbarrier through the transaction byte count. Components are
+// double-buffered, so the copy of component c+1 overlaps the filter of c.
+// Waits are bounded: on timeout the kernel records ST_TIMEOUT, waits (bounded
+// again) for its copies in flight and gives up the tile.
+constexpr long kWaitLimit = 1L << 24;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// x-pass: B1[ti][lk] = sum_j c_j A[ti + H + (j - P) s][lk] for the tile's rows
+__device__ __forceinline__ void tma_load_box(void* dst, const CUtensorMap* map, int z, int x, int c, uint64_t* bar,
+                                             uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+          "r"(smem_u32(dst)),
+      "l"((unsigned long long)map), "r"(z), "r"(x), "r"(c), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// bounded wait for the phase with the given parity; false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  for (long it = 0; it < kWaitLimit; it++) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// A tiled bulk-tensor copy needs a 128-byte aligned shared destination: the
+// staging buffers start at the dynamic shared base rounded up to 128 bytes and
+// lie a whole number of 128-byte lines apart.
 template <class T>
-__device__ __forceinline__ void xpass(const T* A, T* B1, const FilterTaps<T>& ft, int WZ) {
+__host__ __device__ __forceinline__ int tile_stride(const TileMaps& tm) {
+  const int line = 128 / (int)sizeof(T);
+  return (tm.BX * tm.BZ + line - 1) / line * line;
+}
+
+__device__ __forceinline__ unsigned char* align128(unsigned char* p) {
+  return p + ((128u - (smem_u32(p) & 127u)) & 127u);
+}
+
+// stage component c of a block into a shared buffer (leader thread only)
+template <class T>
+__device__ __forceinline__ void stage(T* buf, const CUtensorMap* map, int c, int gk0, int gi0, uint64_t* bar,
+                                      const TileMaps& tm) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  tma_load_box(buf, map, gk0, gi0, c, bar, (uint32_t)(tm.BX * tm.BZ * sizeof(T)));
+}
+
+// x-pass: B1[ti][lk] = sum_j c_j A[ti + H + (j - P) s][lk + zoff] for the tile's rows
+template <class T>
+__device__ __forceinline__ void xpass(const T* A, T* B1, const FilterTaps<T>& ft, int BZ, int zoff, int WZ) {
   for (int ti = threadIdx.y; ti < FT_X; ti += FT_TY) {
     for (int lk = threadIdx.x; lk < WZ; lk += FT_Z) {
-      const T* col = A + (ti + ft.H - ft.P * ft.s) * WZ + lk;
+      const T* col = A + (ti + ft.H - ft.P * ft.s) * BZ + lk + zoff;
       T acc = T(0);
-      for (int j = 0; j <= 2 * ft.P; j++) acc += ft.c[j] * col[j * ft.s * WZ];
+      for (int j = 0; j <= 2 * ft.P; j++) acc += ft.c[j] * col[j * ft.s * BZ];
       B1[ti * WZ + lk] = acc;
     }
   }
@@ -151,21 +193,48 @@ __device__ __forceinline__ T zpass(const T* B1, const FilterTaps<T>& ft, int WZ,
   return acc;
 }
 
+__device__ __forceinline__ void tile_timeout(Ctrl* ctrl, uint64_t* bar0, uint64_t* bar1) {
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    atomicOr(&ctrl->status, ST_TIMEOUT);
+    // bounded: let any copy still in flight land before the block exits
+    mbar_wait(bar0, 0); mbar_wait(bar0, 1);
+    mbar_wait(bar1, 0); mbar_wait(bar1, 1);
+  }
+}
+
 // gather copies: fE = F(E^n), fB = F(Bavg)
 template <class T>
-__global__ void __launch_bounds__(FT_Z* FT_TY) k_filter_fields(GridP g, FieldPtrs<T> f, FilterTaps<T> ft) {
-  extern __shared__ unsigned char smraw[];
-  T* A = reinterpret_cast<T*>(smraw);
+__global__ void __launch_bounds__(FT_Z* FT_TY) k_filter_fields(GridP g, FieldPtrs<T> f, FilterTaps<T> ft,
+                                                               const __grid_constant__ CUtensorMap mapE,
+                                                               const __grid_constant__ CUtensorMap mapB, TileMaps tm,
+                                                               Ctrl* ctrl) {
+  extern __shared__ __align__(128) unsigned char smraw[];
+  T* tile0 = reinterpret_cast<T*>(align128(smraw));
+  T* tile1 = tile0 + tile_stride<T>(tm);
   const int H = ft.H;
-  const int WX = FT_X + 2 * H, WZ = FT_Z + 2 * H;
-  T* B1 = A + WX * WZ;
+  const int WZ = FT_Z + 2 * H;
+  T* B1 = tile1 + tile_stride<T>(tm);
+  __shared__ __align__(8) uint64_t bar[2];
   const int i0 = blockIdx.y * FT_X, k0 = blockIdx.x * FT_Z;
+  const int gi0 = i0 - tm.H, gk0 = k0 - tm.HZ;
+  const bool leader = threadIdx.x == 0 && threadIdx.y == 0;
+  if (leader) {
+    mbar_init(&bar[0]);
+    mbar_init(&bar[1]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (leader) stage<T>(tile0, &mapE, 0, gk0, gi0, &bar[0], tm);
   for (int c = 0; c < 6; c++) {
-    const T* src = c < 3 ? f.E[c] : f.Bavg[c - 3];
+    T* A = (c & 1) ? tile1 : tile0;
+    if (leader && c + 1 < 6)
+      stage<T>((c & 1) ? tile0 : tile1, c + 1 < 3 ? &mapE : &mapB, (c + 1) % 3, gk0, gi0, &bar[(c + 1) & 1], tm);
+    if (!mbar_wait(&bar[c & 1], (c >> 1) & 1)) {
+      tile_timeout(ctrl, &bar[0], &bar[1]);
+      return;
+    }
     T* dst = c < 3 ? f.fE[c] : f.fB[c - 3];
-    load_tile<T>(A, src, g, i0 - H, k0 - H, WX, WZ, nullptr, nullptr, 0.0);
-    __syncthreads();
-    xpass<T>(A, B1, ft, WZ);
+    xpass<T>(A + (tm.H - H) * tm.BZ, B1, ft, tm.BZ, tm.HZ - H, WZ);
     __syncthreads();
     const int gk = k0 + threadIdx.x;
     for (int ti = threadIdx.y; ti < FT_X; ti += FT_TY) {
@@ -180,26 +249,55 @@ __global__ void __launch_bounds__(FT_Z* FT_TY) k_filter_fields(GridP g, FieldPtr
 // Ampere + PML-E, with the current (plus the ion column current) filtered in the tile first
 template <class T, bool FILT>
 __global__ void __launch_bounds__(FT_Z* FT_TY) k_ampere(GridP g, FieldPtrs<T> f, PmlTabs pt, FilterTaps<T> ft,
-                                                        const double* ion_x, const double* ion_c, double ion_coef) {
-  extern __shared__ unsigned char smraw[];
-  T* A = reinterpret_cast<T*>(smraw);
+                                                        const double* ion_x, const double* ion_c, double ion_coef,
+                                                        const __grid_constant__ CUtensorMap mapJ, TileMaps tm,
+                                                        Ctrl* ctrl) {
+  extern __shared__ __align__(128) unsigned char smraw[];
+  T* tile0 = reinterpret_cast<T*>(align128(smraw));
+  T* tile1 = tile0 + tile_stride<T>(tm);
   const int H = FILT ? ft.H : 0;
-  const int WX = FT_X + 2 * H, WZ = FT_Z + 2 * H;
-  T* B1 = A + WX * WZ;
+  const int WZ = FT_Z + 2 * H;
+  T* B1 = tile1 + tile_stride<T>(tm);
+  __shared__ __align__(8) uint64_t bar[2];
   const int i0 = blockIdx.y * FT_X, k0 = blockIdx.x * FT_Z;
+  const int gi0 = i0 - tm.H, gk0 = k0 - tm.HZ;
+  const bool leader = threadIdx.x == 0 && threadIdx.y == 0;
+  if (leader) {
+    mbar_init(&bar[0]);
+    mbar_init(&bar[1]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (leader) stage<T>(tile0, &mapJ, 0, gk0, gi0, &bar[0], tm);
   const T dt = T(g.dt);
   const T c2 = T(kC * kC);
   const T ie0 = T(1.0 / kEps0);
   const double c2d = kC * kC;
   const int k = k0 + threadIdx.x;
   for (int c = 0; c < 3; c++) {
+    T* A = (c & 1) ? tile1 : tile0;
+    if (leader && c + 1 < 3) stage<T>((c & 1) ? tile0 : tile1, &mapJ, c + 1, gk0, gi0, &bar[(c + 1) & 1], tm);
+    if (!mbar_wait(&bar[c & 1], (c >> 1) & 1)) {
+      tile_timeout(ctrl, &bar[0], &bar[1]);
+      return;
+    }
+    if (c == 2 && ion_x != nullptr) {
+      // rigid ion-column current added to Jz before the filter
+      for (int li = threadIdx.y; li < tm.BX; li += FT_TY) {
+        const int gi = gi0 + li;
+        if (gi < 0 || gi > g.nx) continue;
+        const double ix = ion_coef * ion_x[gi];
+        for (int lk = threadIdx.x; lk < tm.BZ; lk += FT_Z) {
+          const int gk = gk0 + lk;
+          if (gk >= 0 && gk <= g.nz) A[li * tm.BZ + lk] += T(ix * ion_c[gk]);
+        }
+      }
+      __syncthreads();
+    }
     int vi0, vi1, vk0, vk1;
     valid_range(c, g.nx, g.nz, vi0, vi1, vk0, vk1);
-    const bool ion = (c == 2) && ion_x != nullptr;
-    load_tile<T>(A, f.J[c], g, i0 - H, k0 - H, WX, WZ, ion ? ion_x : nullptr, ion_c, ion_coef);
-    __syncthreads();
     if (FILT) {
-      xpass<T>(A, B1, ft, WZ);
+      xpass<T>(A + (tm.H - H) * tm.BZ, B1, ft, tm.BZ, tm.HZ - H, WZ);
       __syncthreads();
     }
     for (int ti = threadIdx.y; ti < FT_X; ti += FT_TY) {
@@ -208,8 +306,11 @@ __global__ void __launch_bounds__(FT_Z* FT_TY) k_ampere(GridP g, FieldPtrs<T> f,
       const long p = (long)i * g.ld + k;
       f.Jn[c][p] = T(0);
       const bool v = i >= vi0 && i <= vi1 && k >= vk0 && k <= vk1;
-      if (!v) { f.Eo[c][p] = T(0); continue; }
-      const T jv = FILT ? zpass<T>(B1, ft, WZ, ti, threadIdx.x) : A[ti * WZ + threadIdx.x];
+      if (!v) {
+        f.Eo[c][p] = T(0);
+        continue;
+      }
+      const T jv = FILT ? zpass<T>(B1, ft, WZ, ti, threadIdx.x) : A[(ti + tm.H) * tm.BZ + threadIdx.x + tm.HZ];
       const T eo = f.E[c][p];
       T en;
       if (c == 0) {
@@ -262,8 +363,10 @@ void launch_faraday(const GridP& g, const FieldPtrs<T>& f, const PmlTabs& pt, do
   }
 }
 
-static size_t tile_smem(int H, size_t elem) {
-  return ((size_t)(FT_X + 2 * H) * (FT_Z + 2 * H) + (size_t)FT_X * (FT_Z + 2 * H)) * elem;
+template <class T>
+static size_t tile_smem(const TileMaps& tm, int H) {
+  // + 128: room to round the dynamic shared base up to a 128-byte line
+  return (2 * (size_t)tile_stride<T>(tm) + (size_t)FT_X * (FT_Z + 2 * H)) * sizeof(T) + 128;
 }
 
 template <class T>
@@ -277,38 +380,100 @@ static FilterTaps<T> make_taps(const FilterSpec& fs) {
     const double al = p < fs.passes ? 0.5 : 0.5 * fs.passes + 1.0;
     const double be = 0.5 * (1.0 - al);
     double r[2 * 16 + 1] = {0.0};
-    for (int j = 0; j < len; j++) { r[j] += be * k[j]; r[j + 1] += al * k[j]; r[j + 2] += be * k[j]; }
+    for (int j = 0; j < len; j++) {
+      r[j] += be * k[j];
+      r[j + 1] += al * k[j];
+      r[j + 2] += be * k[j];
+    }
     len += 2;
     for (int j = 0; j < len; j++) k[j] = r[j];
   }
   FilterTaps<T> ft;
-  ft.P = P; ft.s = fs.stride; ft.H = P * fs.stride;
+  ft.P = P;
+  ft.s = fs.stride;
+  ft.H = P * fs.stride;
   for (int j = 0; j < 2 * 16 + 1; j++) ft.c[j] = T(j < len ? k[j] : 0.0);
   return ft;
 }
 
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+// 3D tensor over a 3-component block: (nz+1) x (nx+1) x 3, rows ld elements apart, components cs apart
 template <class T>
-void launch_filter_fields(const GridP& g, const FieldPtrs<T>& f, const FilterSpec& fs, bool enabled, cudaStream_t s) {
+static bool encode_block(CUtensorMap* m, const void* base, const GridP& g, const TileMaps& tm) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn || !base) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)(g.nz + 1), (cuuint64_t)(g.nx + 1), 3};
+  const cuuint64_t strides[2] = {(cuuint64_t)g.ld * sizeof(T), (cuuint64_t)g.cs * sizeof(T)};
+  const cuuint32_t box[3] = {(cuuint32_t)tm.BZ, (cuuint32_t)tm.BX, 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  const CUtensorMapDataType dt = sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  return fn(m, dt, 3, const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
+template <class T>
+bool make_tile_maps(const GridP& g, const FieldPtrs<T>& f, int H, TileMaps& tm) {
+  // a box starts at z = k0 - HZ, which must be 16-byte aligned: k0 is a multiple of 64 and HZ of 4
+  tm.H = H;
+  tm.HZ = (H + 3) & ~3;
+  tm.BX = FT_X + 2 * H;
+  tm.BZ = FT_Z + 2 * tm.HZ;
+  tm.ok = false;
+  if (tm.BX > 256 || tm.BZ > 256) return false;
+  if (tile_smem<T>(tm, H) > 227 * 1024) return false;
+  tm.Ebase[0] = f.E[0];
+  tm.Ebase[1] = f.Eo[0];
+  tm.Jbase[0] = f.J[0];
+  tm.Jbase[1] = f.Jn[0];
+  const bool ok = encode_block<T>(&tm.E[0], f.E[0], g, tm) && encode_block<T>(&tm.E[1], f.Eo[0], g, tm) &&
+                  encode_block<T>(&tm.J[0], f.J[0], g, tm) && encode_block<T>(&tm.J[1], f.Jn[0], g, tm) &&
+                  encode_block<T>(&tm.Bavg, f.Bavg[0], g, tm);
+  tm.ok = ok;
+  return ok;
+}
+
+template <class T>
+void launch_filter_fields(const GridP& g, const FieldPtrs<T>& f, const FilterSpec& fs, bool enabled,
+                          const TileMaps& tm, Ctrl* ctrl, cudaStream_t s) {
   if (!enabled) return;
   const FilterTaps<T> ft = make_taps<T>(fs);
   dim3 grd((g.nz + 1 + FT_Z - 1) / FT_Z, (g.nx + 1 + FT_X - 1) / FT_X), blk(FT_Z, FT_TY);
-  size_t sm = tile_smem(ft.H, sizeof(T));
+  const size_t sm = tile_smem<T>(tm, ft.H);
+  const CUtensorMap& mE = tm.Ebase[0] == (const void*)f.E[0] ? tm.E[0] : tm.E[1];
   cudaFuncSetAttribute(k_filter_fields<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_filter_fields<T><<<grd, blk, sm, s>>>(g, f, ft);
+  k_filter_fields<T><<<grd, blk, sm, s>>>(g, f, ft, mE, tm.Bavg, tm, ctrl);
 }
 
 template <class T>
 void launch_ampere(const GridP& g, const FieldPtrs<T>& f, const PmlTabs& pt, const FilterSpec& fs, bool filter_on,
-                   const double* ion_x, const double* ion_c, double ion_coef, cudaStream_t s) {
+                   const double* ion_x, const double* ion_c, double ion_coef, const TileMaps& tm, Ctrl* ctrl,
+                   cudaStream_t s) {
   const FilterTaps<T> ft = make_taps<T>(fs);
   dim3 grd((g.nz + 1 + FT_Z - 1) / FT_Z, (g.nx + 1 + FT_X - 1) / FT_X), blk(FT_Z, FT_TY);
+  const CUtensorMap& mJ = tm.Jbase[0] == (const void*)f.J[0] ? tm.J[0] : tm.J[1];
+  const size_t sm = tile_smem<T>(tm, filter_on ? ft.H : 0);
   if (filter_on) {
-    size_t sm = tile_smem(ft.H, sizeof(T));
     cudaFuncSetAttribute(k_ampere<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_ampere<T, true><<<grd, blk, sm, s>>>(g, f, pt, ft, ion_x, ion_c, ion_coef);
+    k_ampere<T, true><<<grd, blk, sm, s>>>(g, f, pt, ft, ion_x, ion_c, ion_coef, mJ, tm, ctrl);
   } else {
-    size_t sm = tile_smem(0, sizeof(T));
-    k_ampere<T, false><<<grd, blk, sm, s>>>(g, f, pt, ft, ion_x, ion_c, ion_coef);
+    cudaFuncSetAttribute(k_ampere<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_ampere<T, false><<<grd, blk, sm, s>>>(g, f, pt, ft, ion_x, ion_c, ion_coef, mJ, tm, ctrl);
   }
 }
 
@@ -316,12 +481,14 @@ template void launch_faraday<float>(const GridP&, const FieldPtrs<float>&, const
                                     bool, cudaStream_t);
 template void launch_faraday<double>(const GridP&, const FieldPtrs<double>&, const PmlTabs&, double, double, double,
                                      bool, cudaStream_t);
-template void launch_filter_fields<float>(const GridP&, const FieldPtrs<float>&, const FilterSpec&, bool, cudaStream_t);
-template void launch_filter_fields<double>(const GridP&, const FieldPtrs<double>&, const FilterSpec&, bool,
-                                           cudaStream_t);
-template void launch_ampere<float>(const GridP&, const FieldPtrs<float>&, const PmlTabs&, const FilterSpec&, bool,
-                                   const double*, const double*, double, cudaStream_t);
-template void launch_ampere<double>(const GridP&, const FieldPtrs<double>&, const PmlTabs&, const FilterSpec&, bool,
-                                    const double*, const double*, double, cudaStream_t);
+#define INSTF(T)                                                                                                 \
+  template bool make_tile_maps<T>(const GridP&, const FieldPtrs<T>&, int, TileMaps&);                            \
+  template void launch_filter_fields<T>(const GridP&, const FieldPtrs<T>&, const FilterSpec&, bool, const TileMaps&, \
+                                        Ctrl*, cudaStream_t);                                                    \
+  template void launch_ampere<T>(const GridP&, const FieldPtrs<T>&, const PmlTabs&, const FilterSpec&, bool,       \
+                                 const double*, const double*, double, const TileMaps&, Ctrl*, cudaStream_t);
+INSTF(float)
+INSTF(double)
+#undef INSTF
 
 }  // namespace picgb

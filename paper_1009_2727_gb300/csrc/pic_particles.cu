@@ -171,33 +171,44 @@ __device__ __forceinline__ void push_one(const T* __restrict__ Eb, const T* __re
   T* Jx = Jb + (long)(bx - ox) * ld + (bz - oz);
   T* Jy = Jx + cs;
   T* Jz = Jx + 2 * cs;
+  // Esirkepov weights factorise: Jx(a,b) = Px[a] Fz[b] with Px the running sum of cx DSx and
+  // Fz = S0z + DSz/2 (likewise Jz), and Wy = S0z (S0x + DSx/2) + DSz (S0x/2 + DSx/3)
+  T Px[ND - 1], Pz[ND - 1];
+  {
+    T ax = T(0), az = T(0);
+#pragma unroll
+    for (int a = 0; a < ND - 1; a++) {
+      ax += cx * DSx[a]; Px[a] = ax;
+      az += cz * DSz[a]; Pz[a] = az;
+    }
+  }
 #pragma unroll
   for (int b = 0; b < ND; b++) {
     const T fzb = S0z[b] + T(0.5) * DSz[b];
-    T acc = T(0);
 #pragma unroll
     for (int a = 0; a < ND - 1; a++) {
-      acc += cx * DSx[a] * fzb;
-      if (acc != T(0)) atomicAdd(Jx + (long)a * ld + b, acc);
+      const T v = Px[a] * fzb;
+      if (v != T(0)) atomicAdd(Jx + (long)a * ld + b, v);
     }
   }
 #pragma unroll
   for (int a = 0; a < ND; a++) {
     const T fxa = S0x[a] + T(0.5) * DSx[a];
-    T acc = T(0);
 #pragma unroll
     for (int b = 0; b < ND - 1; b++) {
-      acc += cz * DSz[b] * fxa;
-      if (acc != T(0)) atomicAdd(Jz + (long)a * ld + b, acc);
+      const T v = fxa * Pz[b];
+      if (v != T(0)) atomicAdd(Jz + (long)a * ld + b, v);
     }
   }
   if (cy != T(0)) {
 #pragma unroll
     for (int a = 0; a < ND; a++) {
+      const T ay = cy * (S0x[a] + T(0.5) * DSx[a]);
+      const T by = cy * (T(0.5) * S0x[a] + DSx[a] * T(1.0 / 3.0));
 #pragma unroll
       for (int b = 0; b < ND; b++) {
-        T wy = S0x[a] * S0z[b] + T(0.5) * DSx[a] * S0z[b] + T(0.5) * S0x[a] * DSz[b] + DSx[a] * DSz[b] * T(1.0 / 3.0);
-        if (wy != T(0)) atomicAdd(Jy + (long)a * ld + b, cy * wy);
+        const T v = ay * S0z[b] + by * DSz[b];
+        if (v != T(0)) atomicAdd(Jy + (long)a * ld + b, v);
       }
     }
   }
@@ -295,6 +306,19 @@ __global__ void __launch_bounds__(PB_THREADS, 4) k_push(GridP g, const T* gE, co
       }
       __syncthreads();
       for (int pi = ch.p0 + threadIdx.x; pi < ch.p1; pi += blockDim.x) {
+        // prefetch the next particle of this thread into L1
+        const int pn = pi + blockDim.x;
+        if (pn < ch.p1) {
+          if constexpr (CellPos<T>::value) {
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(p.cell + pn));
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(p.ox + pn));
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(p.oz + pn));
+          }
+          asm volatile("prefetch.global.L1 [%0];" ::"l"(p.ux + pn));
+          asm volatile("prefetch.global.L1 [%0];" ::"l"(p.uy + pn));
+          asm volatile("prefetch.global.L1 [%0];" ::"l"(p.uz + pn));
+          asm volatile("prefetch.global.L1 [%0];" ::"l"(p.w + pn));
+        }
         // a particle outside the chunk's box (should not happen) takes the global path
         int fx = 0, fz = 0;
         const bool fin = particle_cell<T>(p, pi, pc, fx, fz);
