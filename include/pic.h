@@ -89,7 +89,7 @@ typedef struct {
   int32_t precision;      /* PIC_FP64 or PIC_MIXED (FP32 fields/momenta, FP64 positions and PML coefficients) */
   int32_t moving_window;  /* 1: the grid follows the wake at window_beta c */
   double window_beta;
-  int32_t tile_x, tile_z; /* particle tile in cells; 0 = default */
+  int32_t tile_x, tile_z; /* particle tile in cells (x, z); 0 = default 8 x 32; at most 1024 cells */
   int32_t sort_every;     /* steps between particle sorts; 0 = default */
   int32_t reserved[8];
 } pic_config;

@@ -230,7 +230,9 @@ struct Sim : SimBase {
     if (!ctrl || !stats_buf || !stage) return c->fail(PIC_ENOMEM, "allocation failed");
     if (cudaMallocHost(&hmirror, sizeof(Ctrl)) != cudaSuccess) hmirror = nullptr;
     // particle tiles
-    int tx = cf.tile_x > 0 ? cf.tile_x : 16, tz = cf.tile_z > 0 ? cf.tile_z : 16;
+    // default tile: 8 (x) by 32 (z) cells, so that a warp spans 32 consecutive z-cells
+    int tx = cf.tile_x > 0 ? cf.tile_x : 8, tz = cf.tile_z > 0 ? cf.tile_z : 32;
+    if (tx * tz > 1024) return c->fail(PIC_EINVAL, "tile_x * tile_z must not exceed 1024 cells");
     sb.tx = tx; sb.tz = tz;
     sb.ntx = (cf.nx + tx - 1) / tx; sb.ntz = (cf.nz + tz - 1) / tz;
     sb.R = 32;
@@ -307,16 +309,19 @@ struct Sim : SimBase {
     const int inj_chunks = ((g.gx_hi - g.gx_lo + ip.xblock - 1) / ip.xblock) * 4;
     chunk_cap = 2 * ntiles + cap / chunk_max + inj_chunks * (sort_every + 4) + 4096;
     chunks = al<Chunk>(chunk_cap);
-    const int nbins = ntiles * sb.R;
-    sb.cell_cnt = al<int>((size_t)cf.nx * cf.nz);
-    sb.bin_cnt = al<int>(nbins + 1);
-    sb.bin_start = al<int>(nbins + 1);
+    if (ntiles > 1024 * 1024) return c->fail(PIC_EINVAL, "too many particle tiles; enlarge tile_x/tile_z");
+    const size_t ncells = (size_t)ntiles * sb.tx * sb.tz;
+    sb.cell_cnt = al<int>(ncells);
+    sb.cell_start = al<int>(ncells);
+    sb.tile_cnt = al<int>(ntiles + 1);
+    sb.tile_start = al<int>(ntiles + 1);
     sb.key = al<int>(cap);
     sb.slot = al<int>(cap);
-    sb.scan_tmp = al<int>(1024 + (nbins + 1023) / 1024);
-    if (!chunks || !sb.cell_cnt || !sb.bin_cnt || !sb.bin_start || !sb.key || !sb.slot || !sb.scan_tmp)
+    sb.dest = al<int>(cap);
+    sb.scan_tmp = al<int>(1024 + (ntiles + 1023) / 1024);
+    if (!chunks || !sb.cell_cnt || !sb.cell_start || !sb.tile_cnt || !sb.tile_start || !sb.key || !sb.slot ||
+        !sb.dest || !sb.scan_tmp)
       return c->fail(PIC_ENOMEM, "sort allocation failed");
-    if (nbins > 1024 * 1024) return c->fail(PIC_EINVAL, "too many sort bins; enlarge tile_x/tile_z");
     if (ions) {
       ion_x = al<double>(cf.nx + 1);
       ion_R0 = al<double>(cf.nz + 1); ion_R1 = al<double>(cf.nz + 1); ion_C = al<double>(cf.nz + 1);

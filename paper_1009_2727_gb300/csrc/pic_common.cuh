@@ -161,11 +161,13 @@ void launch_push(const GridP& g, const FieldPtrs<T>& f, Particles<T> p, Chunk* c
                  int grid_blocks, int smem_nodes, double q, double m, cudaStream_t s);
 
 struct SortBufs {
-  int* cell_cnt;       // nx*nz
-  int* bin_cnt;        // ntiles*R (+1)
-  int* bin_start;      // ntiles*R + 1
-  int* key;            // per particle
-  int* slot;
+  int* cell_cnt;       // ntiles*tx*tz, cells in tile-major order: particles per cell
+  int* cell_start;     // ntiles*tx*tz: first entry of the cell in dest
+  int* tile_cnt;       // ntiles + 1
+  int* tile_start;     // ntiles + 1
+  int* key;            // per particle: tile-major cell (-1: dropped)
+  int* slot;           // per particle: rank in its cell
+  int* dest;           // per (cell, rank) entry: destination index
   int* scan_tmp;
   int ntx, ntz, tx, tz, R;
 };

@@ -361,8 +361,45 @@ __global__ void __launch_bounds__(PB_THREADS, 4) k_push(GridP g, const T* gE, co
   }
 }
 
+// block-wide exclusive scan of one int per thread (blockDim.x a multiple of 32, at most 1024)
+__device__ int block_excl_scan(int v, int* total) {
+  __shared__ int ws[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) ws[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int s = lane < (blockDim.x >> 5) ? ws[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    ws[lane] = s;
+  }
+  __syncthreads();
+  int pre = (wid > 0 ? ws[wid - 1] : 0) + x - v;
+  if (total) *total = ws[(blockDim.x >> 5) - 1];
+  __syncthreads();
+  return pre;
+}
+
 // ---------------------------------------------------------------------------
-// sort
+// sort: tiles of tx (x) by tz (z) cells, cells numbered tile-major with z
+// fastest inside a tile. Inside a tile the particles are ordered by rank in
+// their cell (ranks >= R-1 share the last group), then by cell, so that a warp
+// of a densely filled tile holds one particle from each of 32 consecutive
+// cells: its shared-memory gathers and current atomics fall in distinct banks.
+__device__ __forceinline__ int sort_cell(const SortBufs& sb, int cx, int cz) {
+  const int tile = (cx / sb.tx) * sb.ntz + cz / sb.tz;
+  return tile * (sb.tx * sb.tz) + (cx - (cx / sb.tx) * sb.tx) * sb.tz + (cz - (cz / sb.tz) * sb.tz);
+}
+
 template <class T>
 __global__ void k_sort_key(GridP g, Particles<T> p, SortBufs sb, const Ctrl* ctrl) {
   const int n = ctrl->count;
@@ -378,11 +415,48 @@ __global__ void k_sort_key(GridP g, Particles<T> p, SortBufs sb, const Ctrl* ctr
   }
   cx = min(max(cx, 0), g.nx - 1);
   cz = min(max(cz, 0), g.nz - 1);
-  const int tile = (cx / sb.tx) * sb.ntz + (cz / sb.tz);
-  const int r = atomicAdd(&sb.cell_cnt[(long)cx * g.nz + cz], 1);
-  const int bin = tile * sb.R + min(r, sb.R - 1);
-  sb.key[i] = bin;
-  sb.slot[i] = atomicAdd(&sb.bin_cnt[bin], 1);
+  const int c = sort_cell(sb, cx, cz);
+  sb.key[i] = c;
+  sb.slot[i] = atomicAdd(&sb.cell_cnt[c], 1);
+}
+
+// particles per tile (one block per tile, one thread per cell)
+__global__ void k_tile_count(SortBufs sb) {
+  const int tc = sb.tx * sb.tz;
+  const int cl = threadIdx.x;
+  int v = cl < tc ? sb.cell_cnt[(long)blockIdx.x * tc + cl] : 0;
+  int total;
+  block_excl_scan(v, &total);
+  if (threadIdx.x == 0) sb.tile_cnt[blockIdx.x] = total;
+}
+
+// destination of every (cell, rank) entry of a tile (one block per tile, one thread per cell)
+__global__ void k_tile_order(SortBufs sb) {
+  const int tc = sb.tx * sb.tz;
+  const int cl = threadIdx.x;
+  const long c = (long)blockIdx.x * tc + cl;
+  const int cnt = cl < tc ? sb.cell_cnt[c] : 0;
+  const int base = sb.tile_start[blockIdx.x];
+  int tot;
+  const int cstart = base + block_excl_scan(cnt, &tot);
+  if (cl < tc) sb.cell_start[c] = cstart;
+  int off = base;
+  int r = 0;
+  for (; r < sb.R - 1; r++) {
+    const int f = cnt > r;
+    if (!__syncthreads_or(f)) break;
+    int tr;
+    const int pos = block_excl_scan(f, &tr);
+    if (f) sb.dest[cstart + r] = off + pos;
+    off += tr;
+  }
+  // ranks >= R-1: the rest of each cell, cell after cell
+  const int m = r == sb.R - 1 ? max(cnt - r, 0) : 0;
+  if (__syncthreads_or(m > 0)) {
+    int tm;
+    const int pos = block_excl_scan(m, &tm);
+    for (int j = 0; j < m; j++) sb.dest[cstart + r + j] = off + pos + j;
+  }
 }
 
 template <class T>
@@ -392,7 +466,7 @@ __global__ void k_sort_scatter(Particles<T> s, Particles<T> d, SortBufs sb, cons
   if (i >= n) return;
   const int key = sb.key[i];
   if (key < 0) return;
-  const int o = sb.bin_start[key] + sb.slot[i];
+  const int o = sb.dest[sb.cell_start[key] + sb.slot[i]];
   if constexpr (CellPos<T>::value) {
     d.cell[o] = s.cell[i]; d.ox[o] = s.ox[i]; d.oz[o] = s.oz[i];
   } else {
@@ -406,7 +480,7 @@ __global__ void k_build_chunks(SortBufs sb, Chunk* chunks, Ctrl* ctrl, int chunk
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int ntiles = sb.ntx * sb.ntz;
   if (t >= ntiles) return;
-  const int p0 = sb.bin_start[t * sb.R], p1 = sb.bin_start[(t + 1) * sb.R];
+  const int p0 = sb.tile_start[t], p1 = sb.tile_start[t + 1];
   const int n = p1 - p0;
   if (n <= 0) return;
   const int nch = (n + chunk_max - 1) / chunk_max;
@@ -439,33 +513,6 @@ __global__ void k_scan_sums(const int* in, int n, int* sums) {
     s = __reduce_add_sync(0xffffffffu, s);
     if (threadIdx.x == 0) sums[blockIdx.x] = s;
   }
-}
-
-__device__ int block_excl_scan(int v, int* total) {
-  __shared__ int ws[32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  int x = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    int y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) ws[wid] = x;
-  __syncthreads();
-  if (wid == 0) {
-    int s = lane < (blockDim.x >> 5) ? ws[lane] : 0;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      int y = __shfl_up_sync(0xffffffffu, s, o);
-      if (lane >= o) s += y;
-    }
-    ws[lane] = s;
-  }
-  __syncthreads();
-  int pre = (wid > 0 ? ws[wid - 1] : 0) + x - v;
-  if (total) *total = ws[(blockDim.x >> 5) - 1];
-  __syncthreads();
-  return pre;
 }
 
 __global__ void k_scan_top(int* sums, int nb) {
@@ -614,17 +661,19 @@ static void exclusive_scan(const int* in, int n, int* out, int* tmp, cudaStream_
 template <class T>
 void launch_sort(const GridP& g, Particles<T> src, Particles<T> dst, SortBufs sb, Chunk* chunks, Ctrl* ctrl, int cap,
                  int chunk_max, int chunk_cap, cudaStream_t s) {
-  const int nbins = sb.ntx * sb.ntz * sb.R;
-  cudaMemsetAsync(sb.cell_cnt, 0, sizeof(int) * (size_t)g.nx * g.nz, s);
-  cudaMemsetAsync(sb.bin_cnt, 0, sizeof(int) * (size_t)(nbins + 1), s);
+  const int ntiles = sb.ntx * sb.ntz;
+  const int tc = sb.tx * sb.tz;
+  const int tb = (tc + 31) / 32 * 32;   // one thread per cell of a tile
+  cudaMemsetAsync(sb.cell_cnt, 0, sizeof(int) * (size_t)ntiles * tc, s);
   const int nb = (cap + 255) / 256;
   k_sort_key<T><<<nb, 256, 0, s>>>(g, src, sb, ctrl);
-  exclusive_scan(sb.bin_cnt, nbins, sb.bin_start, sb.scan_tmp, s);
+  k_tile_count<<<ntiles, tb, 0, s>>>(sb);
+  exclusive_scan(sb.tile_cnt, ntiles, sb.tile_start, sb.scan_tmp, s);
+  k_tile_order<<<ntiles, tb, 0, s>>>(sb);
   k_sort_scatter<T><<<nb, 256, 0, s>>>(src, dst, sb, ctrl);
   k_sort_finish_pre<<<1, 1, 0, s>>>(ctrl);
-  const int ntiles = sb.ntx * sb.ntz;
   k_build_chunks<<<(ntiles + 255) / 256, 256, 0, s>>>(sb, chunks, ctrl, chunk_max, chunk_cap, g.nx, g.nz);
-  k_sort_finish<<<1, 1, 0, s>>>(ctrl, sb.bin_start, nbins);
+  k_sort_finish<<<1, 1, 0, s>>>(ctrl, sb.tile_start, ntiles);
 }
 
 template <class T>
