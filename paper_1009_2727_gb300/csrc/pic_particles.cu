@@ -62,6 +62,38 @@ __device__ __forceinline__ T interp(const T* F, int ld, int ox, int oz, int fi, 
   return acc;
 }
 
+template <class T>
+struct Vec2;
+template <>
+struct Vec2<float> { typedef float2 type; };
+template <>
+struct Vec2<double> { typedef double2 type; };
+
+// interpolation of two components stored as pairs at the same Yee location
+template <class T, int ORDER>
+__device__ __forceinline__ void interp2(const typename Vec2<T>::type* F, int ld, int ox, int oz, int fi, int fk,
+                                        const T* wx, const T* wz, T& r0, T& r1) {
+  constexpr int NG = St<ORDER>::NG;
+  const int off = ORDER == 3 ? 1 : 0;
+  T a0 = T(0), a1 = T(0);
+  const typename Vec2<T>::type* row = F + (fi - off - ox) * ld + (fk - off - oz);
+#pragma unroll
+  for (int a = 0; a < NG; a++) {
+    T s0 = T(0), s1 = T(0);
+#pragma unroll
+    for (int b = 0; b < NG; b++) {
+      const typename Vec2<T>::type v = row[b];
+      s0 += v.x * wz[b];
+      s1 += v.y * wz[b];
+    }
+    a0 += s0 * wx[a];
+    a1 += s1 * wx[a];
+    row += ld;
+  }
+  r0 = a0;
+  r1 = a1;
+}
+
 struct PushConst {
   double dx, dz, dt, z0;            // FP64 path
   double xlo, xhi, zlo, zhi;        // FP64 path removal bounds [m]
@@ -73,7 +105,9 @@ struct PushConst {
 };
 
 // One particle: gather -> Boris -> move -> Esirkepov. E/B/J are 3-component
-// blocks (component stride cs) addressed as (i - ox)*ld + (k - oz).
+// blocks (component stride cs) addressed as (i - ox)*ld + (k - oz). With SMEM
+// the fields are the shared-memory window: pairs (Ex, Bz) and (Ez, Bx), which
+// share a Yee location, then Ey and By, each block cs elements long (Bb unused).
 template <class T, int ORDER, bool SMEM>
 __device__ __forceinline__ void push_one(const T* __restrict__ Eb, const T* __restrict__ Bb, T* Jb, long cs, int ld,
                                          int ox, int oz, Particles<T>& p, int pi, const PushConst& pc, int& bx0,
@@ -105,21 +139,39 @@ __device__ __forceinline__ void push_one(const T* __restrict__ Eb, const T* __re
   wts<T, ORDER>(tx, wxi); wts<T, ORDER>(tz, wzi);
   wts<T, ORDER>(txh, wxh); wts<T, ORDER>(tzh, wzh);
   // energy-conserving gather from each component's Yee location
-  const T Ex = interp<T, ORDER>(Eb, ld, ox, oz, fxh, fz, wxh, wzi);
-  const T Ey = interp<T, ORDER>(Eb + cs, ld, ox, oz, fx, fz, wxi, wzi);
-  const T Ez = interp<T, ORDER>(Eb + 2 * cs, ld, ox, oz, fx, fzh, wxi, wzh);
-  const T Bx = interp<T, ORDER>(Bb, ld, ox, oz, fx, fzh, wxi, wzh);
-  const T By = interp<T, ORDER>(Bb + cs, ld, ox, oz, fxh, fzh, wxh, wzh);
-  const T Bz = interp<T, ORDER>(Bb + 2 * cs, ld, ox, oz, fxh, fz, wxh, wzi);
-  // relativistic Boris push
+  T Ex, Ey, Ez, Bx, By, Bz;
+  if constexpr (SMEM) {
+    typedef typename Vec2<T>::type V2;
+    interp2<T, ORDER>(reinterpret_cast<const V2*>(Eb), ld, ox, oz, fxh, fz, wxh, wzi, Ex, Bz);
+    interp2<T, ORDER>(reinterpret_cast<const V2*>(Eb + 2 * cs), ld, ox, oz, fx, fzh, wxi, wzh, Ez, Bx);
+    Ey = interp<T, ORDER>(Eb + 4 * cs, ld, ox, oz, fx, fz, wxi, wzi);
+    By = interp<T, ORDER>(Eb + 5 * cs, ld, ox, oz, fxh, fzh, wxh, wzh);
+  } else {
+    Ex = interp<T, ORDER>(Eb, ld, ox, oz, fxh, fz, wxh, wzi);
+    Ey = interp<T, ORDER>(Eb + cs, ld, ox, oz, fx, fz, wxi, wzi);
+    Ez = interp<T, ORDER>(Eb + 2 * cs, ld, ox, oz, fx, fzh, wxi, wzh);
+    Bx = interp<T, ORDER>(Bb, ld, ox, oz, fx, fzh, wxi, wzh);
+    By = interp<T, ORDER>(Bb + cs, ld, ox, oz, fxh, fzh, wxh, wzh);
+    Bz = interp<T, ORDER>(Bb + 2 * cs, ld, ox, oz, fxh, fz, wxh, wzi);
+  }
+  // relativistic Boris push (the FP32 path takes 1/gamma from rsqrt and a fast
+  // reciprocal; the FP64 path divides)
   T k;
   if constexpr (CP) k = pc.qm_half_f; else k = T(pc.qm_half);
   const T ic2 = T(1.0 / (kC * kC));
   T umx = ux + k * Ex, umy = uy + k * Ey, umz = uz + k * Ez;
-  T gm = sqrt(T(1) + (umx * umx + umy * umy + umz * umz) * ic2);
-  T tbx = k * Bx / gm, tby = k * By / gm, tbz = k * Bz / gm;
-  T t2 = tbx * tbx + tby * tby + tbz * tbz;
-  T sf = T(2) / (T(1) + t2);
+  T tbx, tby, tbz, t2, sf;
+  if constexpr (CP) {
+    const float kig = k * rsqrtf(1.0f + (umx * umx + umy * umy + umz * umz) * ic2);
+    tbx = kig * Bx; tby = kig * By; tbz = kig * Bz;
+    t2 = tbx * tbx + tby * tby + tbz * tbz;
+    sf = __fdividef(2.0f, 1.0f + t2);
+  } else {
+    const T gm = sqrt(T(1) + (umx * umx + umy * umy + umz * umz) * ic2);
+    tbx = k * Bx / gm; tby = k * By / gm; tbz = k * Bz / gm;
+    t2 = tbx * tbx + tby * tby + tbz * tbz;
+    sf = T(2) / (T(1) + t2);
+  }
   T sbx = sf * tbx, sby = sf * tby, sbz = sf * tbz;
   T upx = umx + (umy * tbz - umz * tby);
   T upy = umy + (umz * tbx - umx * tbz);
@@ -128,8 +180,14 @@ __device__ __forceinline__ void push_one(const T* __restrict__ Eb, const T* __re
   T ply = umy + (upz * sbx - upx * sbz);
   T plz = umz + (upx * sby - upy * sbx);
   ux = plx + k * Ex; uy = ply + k * Ey; uz = plz + k * Ez;
-  const T g1 = sqrt(T(1) + (ux * ux + uy * uy + uz * uz) * ic2);
-  const T vx = ux / g1, vy = uy / g1, vz = uz / g1;
+  T vx, vy, vz;
+  if constexpr (CP) {
+    const float ig1 = rsqrtf(1.0f + (ux * ux + uy * uy + uz * uz) * ic2);
+    vx = ux * ig1; vy = uy * ig1; vz = uz * ig1;
+  } else {
+    const T g1 = sqrt(T(1) + (ux * ux + uy * uy + uz * uz) * ic2);
+    vx = ux / g1; vy = uy / g1; vz = uz / g1;
+  }
   // move
   int fxn, fzn;
   T txn, tzn;
@@ -267,8 +325,11 @@ __device__ __noinline__ void push_global_guarded(const T* gE, const T* gB, T* gJ
 template <class T, int ORDER>
 __global__ void __launch_bounds__(PB_THREADS, 4) k_push(GridP g, const T* gE, const T* gB, T* gJ, Particles<T> p,
                                                      Chunk* chunks, Ctrl* ctrl, int cap_nodes, PushConst pc) {
-  extern __shared__ unsigned char smraw[];
+  extern __shared__ __align__(16) unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);
+  typedef typename Vec2<T>::type V2;
+  V2* smA = reinterpret_cast<V2*>(sm);                  // (Ex, Bz)
+  V2* smB = reinterpret_cast<V2*>(sm + 2 * cap_nodes);  // (Ez, Bx)
   __shared__ int s_chunk;
   __shared__ int s_bb[4];
   const int nchunks = ctrl->nchunks;
@@ -297,12 +358,20 @@ __global__ void __launch_bounds__(PB_THREADS, 4) k_push(GridP g, const T* gE, co
         const int li = e / lds, lk = e - li * lds;
         const long gp = (long)(wx0 + li) * g.ld + (wz0 + lk);
         const bool in = lk < wzn;
-#pragma unroll
-        for (int q = 0; q < 3; q++) {
-          sm[q * cap_nodes + e] = in ? gE[q * g.cs + gp] : T(0);
-          sm[(3 + q) * cap_nodes + e] = in ? gB[q * g.cs + gp] : T(0);
-          sm[(6 + q) * cap_nodes + e] = T(0);
+        T ex = T(0), ey = T(0), ez = T(0), bx = T(0), by = T(0), bz = T(0);
+        if (in) {
+          ex = gE[gp]; ey = gE[g.cs + gp]; ez = gE[2 * g.cs + gp];
+          bx = gB[gp]; by = gB[g.cs + gp]; bz = gB[2 * g.cs + gp];
         }
+        V2 va, vb;
+        va.x = ex; va.y = bz;
+        vb.x = ez; vb.y = bx;
+        smA[e] = va;
+        smB[e] = vb;
+        sm[4 * cap_nodes + e] = ey;
+        sm[5 * cap_nodes + e] = by;
+#pragma unroll
+        for (int q = 0; q < 3; q++) sm[(6 + q) * cap_nodes + e] = T(0);
       }
       __syncthreads();
       for (int pi = ch.p0 + threadIdx.x; pi < ch.p1; pi += blockDim.x) {
@@ -323,8 +392,8 @@ __global__ void __launch_bounds__(PB_THREADS, 4) k_push(GridP g, const T* gE, co
         int fx = 0, fz = 0;
         const bool fin = particle_cell<T>(p, pi, pc, fx, fz);
         if (fin && fx >= ch.ix0 && fx <= ch.ix1 && fz >= ch.iz0 && fz <= ch.iz1)
-          push_one<T, ORDER, true>(sm, sm + 3 * cap_nodes, sm + 6 * cap_nodes, cap_nodes, lds, wx0, wz0, p, pi, pc,
-                                   bx0, bx1, bz0, bz1);
+          push_one<T, ORDER, true>(sm, nullptr, sm + 6 * cap_nodes, cap_nodes, lds, wx0, wz0, p, pi, pc, bx0, bx1,
+                                   bz0, bz1);
         else
           push_global_guarded<T, ORDER>(gE, gB, gJ, g, p, pi, pc, ctrl, bx0, bx1, bz0, bz1);
       }
