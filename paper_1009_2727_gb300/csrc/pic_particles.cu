@@ -10,6 +10,7 @@
 //    particles of different cells and their shared atomics do not collide);
 //  - plasma rows entering through the +z plane (Sec. 3.1.1, PR-12).
 #include <climits>
+#include <type_traits>
 
 #include "pic_common.cuh"
 
@@ -103,6 +104,58 @@ struct PushConst {
   double kx, kz, ky;                // deposit: -q/(dz dt), -q/(dx dt), q/(dx dz)
   float qm_half_f, kx_f, kz_f, ky_f;  // the same in FP32 for the mixed path
 };
+
+// Esirkepov current of one particle on an NDX (x) by ND (z) window whose first
+// node is Jx (Jy, Jz follow at component stride cs). The weights factorise:
+// Jx(a,b) = Px[a] Fz[b] with Px the running sum of cx DSx and Fz = S0z + DSz/2
+// (likewise Jz), and Wy = S0z (S0x + DSx/2) + DSz (S0x/2 + DSx/3). Zero
+// contributions are skipped (a slot that is zero on every lane of a warp costs
+// no shared-memory wavefront).
+template <class T, int ND, int NDX, bool SMEM>
+__device__ __forceinline__ void deposit(T* Jx, long cs, int ld, const T* S0x, const T* DSx, const T* S0z, const T* DSz,
+                                        T cx, T cy, T cz) {
+  typedef typename std::conditional<SMEM, int, long>::type Idx;
+  T* Jy = Jx + cs;
+  T* Jz = Jx + 2 * cs;
+  T Px[NDX - 1], Pz[ND - 1];
+  {
+    T ax = T(0), az = T(0);
+#pragma unroll
+    for (int a = 0; a < NDX - 1; a++) { ax += cx * DSx[a]; Px[a] = ax; }
+#pragma unroll
+    for (int b = 0; b < ND - 1; b++) { az += cz * DSz[b]; Pz[b] = az; }
+  }
+#pragma unroll
+  for (int b = 0; b < ND; b++) {
+    const T fzb = S0z[b] + T(0.5) * DSz[b];
+#pragma unroll
+    for (int a = 0; a < NDX - 1; a++) {
+      const T v = Px[a] * fzb;
+      if (v != T(0)) atomicAdd(Jx + (Idx)a * ld + b, v);
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < NDX; a++) {
+    const T fxa = S0x[a] + T(0.5) * DSx[a];
+#pragma unroll
+    for (int b = 0; b < ND - 1; b++) {
+      const T v = fxa * Pz[b];
+      if (v != T(0)) atomicAdd(Jz + (Idx)a * ld + b, v);
+    }
+  }
+  if (cy != T(0)) {
+#pragma unroll
+    for (int a = 0; a < NDX; a++) {
+      const T ay = cy * (S0x[a] + T(0.5) * DSx[a]);
+      const T by = cy * (T(0.5) * S0x[a] + DSx[a] * T(1.0 / 3.0));
+#pragma unroll
+      for (int b = 0; b < ND; b++) {
+        const T v = ay * S0z[b] + by * DSz[b];
+        if (v != T(0)) atomicAdd(Jy + (Idx)a * ld + b, v);
+      }
+    }
+  }
+}
 
 // One particle: gather -> Boris -> move -> Esirkepov. E/B/J are 3-component
 // blocks (component stride cs) addressed as (i - ox)*ld + (k - oz). With SMEM
@@ -227,48 +280,16 @@ __device__ __forceinline__ void push_one(const T* __restrict__ Eb, const T* __re
     cx = T(pc.kx) * w; cz = T(pc.kz) * w; cy = T(pc.ky) * w * vy;
   }
   T* Jx = Jb + (long)(bx - ox) * ld + (bz - oz);
-  T* Jy = Jx + cs;
-  T* Jz = Jx + 2 * cs;
-  // Esirkepov weights factorise: Jx(a,b) = Px[a] Fz[b] with Px the running sum of cx DSx and
-  // Fz = S0z + DSz/2 (likewise Jz), and Wy = S0z (S0x + DSx/2) + DSz (S0x/2 + DSx/3)
-  T Px[ND - 1], Pz[ND - 1];
-  {
-    T ax = T(0), az = T(0);
-#pragma unroll
-    for (int a = 0; a < ND - 1; a++) {
-      ax += cx * DSx[a]; Px[a] = ax;
-      az += cz * DSz[a]; Pz[a] = az;
-    }
-  }
-#pragma unroll
-  for (int b = 0; b < ND; b++) {
-    const T fzb = S0z[b] + T(0.5) * DSz[b];
-#pragma unroll
-    for (int a = 0; a < ND - 1; a++) {
-      const T v = Px[a] * fzb;
-      if (v != T(0)) atomicAdd(Jx + (long)a * ld + b, v);
-    }
-  }
-#pragma unroll
-  for (int a = 0; a < ND; a++) {
-    const T fxa = S0x[a] + T(0.5) * DSx[a];
-#pragma unroll
-    for (int b = 0; b < ND - 1; b++) {
-      const T v = fxa * Pz[b];
-      if (v != T(0)) atomicAdd(Jz + (long)a * ld + b, v);
-    }
-  }
-  if (cy != T(0)) {
-#pragma unroll
-    for (int a = 0; a < ND; a++) {
-      const T ay = cy * (S0x[a] + T(0.5) * DSx[a]);
-      const T by = cy * (T(0.5) * S0x[a] + DSx[a] * T(1.0 / 3.0));
-#pragma unroll
-      for (int b = 0; b < ND; b++) {
-        const T v = ay * S0z[b] + by * DSz[b];
-        if (v != T(0)) atomicAdd(Jy + (long)a * ld + b, v);
-      }
-    }
+  if constexpr (SMEM) {
+    // when no lane of the warp changes x-cell, column ND-1 of the x window is
+    // empty: the warp deposits on ND-1 columns
+    const bool xcross = fxn != fx;
+    if (__any_sync(__activemask(), xcross))
+      deposit<T, ND, ND, true>(Jx, cs, ld, S0x, DSx, S0z, DSz, cx, cy, cz);
+    else
+      deposit<T, ND, ND - 1, true>(Jx, cs, ld, S0x, DSx, S0z, DSz, cx, cy, cz);
+  } else {
+    deposit<T, ND, ND, false>(Jx, cs, ld, S0x, DSx, S0z, DSz, cx, cy, cz);
   }
   bool gone;
   if constexpr (CP) {
