@@ -33,12 +33,14 @@ __device__ double lab_density_d(const InjectP& ip, double zl) {
   return ip.n0;
 }
 
-// R(k) = sum over live rows of w_m S(Z_m(t) - k) at two times (blockIdx.y selects the time);
-// the change R1 - R0 is prefix-summed into C by k_ion_prefix
+// R(k) = sum over live rows of w_m S(Z_m(t) - k) at two times (blockIdx.y selects the time):
+// the row density of the rigid ions, for their charge density
 __global__ void k_ion_rows(GridP g, long long mlo, long long mhi, double t0, double t1, InjectP ip, int order,
                            double* R0, double* R1) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k > g.nz) return;
+  // one warp per (node k, time); the lanes stride over the lattice rows within the shape's reach
+  const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (k > g.nz) return;   // uniform over the warp
   const double reach = order == 3 ? 2.0 : 1.0;
   const double wfac = g.dx * g.dz / (double)(ip.ppc_x * ip.ppc_z);
   const double t = blockIdx.y == 0 ? t0 : t1;
@@ -48,97 +50,75 @@ __global__ void k_ion_rows(GridP g, long long mlo, long long mhi, double t0, dou
   if (ma < mlo) ma = mlo;
   if (mb > mhi - 1) mb = mhi - 1;
   double acc = 0.0;
-  for (long long m = ma; m <= mb; m++) {
+  for (long long m = ma + lane; m <= mb; m += 32) {
     const double zlat = (m + 0.5) * ip.h;
     const double Zm = (zlat - shift - g.z0) / g.dz;
     const double sv = shape_val(order, Zm - k);
     if (sv == 0.0) continue;
     acc += ip.gamma * lab_density_d(ip, ip.gamma * zlat) * wfac * sv;
   }
-  (blockIdx.y == 0 ? R0 : R1)[k] = acc;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) (blockIdx.y == 0 ? R0 : R1)[k] = acc;
 }
 
-// single block of 1024 threads: each thread sums a contiguous run, then a shuffle scan of the run totals
-__global__ void k_ion_prefix(int n, const double* R0, const double* R1, double* C) {
-  __shared__ double ws[32];
-  const int per = (n + blockDim.x - 1) / blockDim.x;
-  const int b = threadIdx.x * per;
-  double loc = 0.0;
-  for (int j = 0; j < per; j++) {
-    const int k = b + j;
-    if (k < n) loc += R1[k] - R0[k];
+// Column current of the rigid ions (PR-9): a lattice row m of line density n_m
+// moving from Z0 to Z1 (in cells) during the step carries through the face
+// above node k the charge n_m [CS(Z1, k) - CS(Z0, k)], with CS(Z, k) the sum of
+// the row's shape weights on the nodes <= k (the 1D Esirkepov current). One
+// thread per row adds its non-zero terms (at most NG+1 nodes) to C.
+__device__ __forceinline__ double cum_weight(int order, double Z, int k) {
+  const int fz = (int)floor(Z);
+  const double t = Z - fz;
+  const int off = order == 3 ? 1 : 0;
+  const int j = k - (fz - off);   // index of node k in the row's stencil
+  if (j < 0) return 0.0;
+  if (order == 3) {
+    if (j >= 3) return 1.0;
+    const double t2 = t * t, t3 = t2 * t, s = 1.0 - t;
+    const double w0 = s * s * s * (1.0 / 6.0);
+    if (j == 0) return w0;
+    const double w1 = 2.0 / 3.0 - t2 + 0.5 * t3;
+    if (j == 1) return w0 + w1;
+    return 1.0 - t3 * (1.0 / 6.0);
   }
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  double x = loc;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    double y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) ws[wid] = x;
-  __syncthreads();
-  if (wid == 0) {
-    double v = lane < (int)(blockDim.x >> 5) ? ws[lane] : 0.0;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      double y = __shfl_up_sync(0xffffffffu, v, o);
-      if (lane >= o) v += y;
-    }
-    ws[lane] = v;
-  }
-  __syncthreads();
-  double run = (wid > 0 ? ws[wid - 1] : 0.0) + x - loc;
-  for (int j = 0; j < per; j++) {
-    const int k = b + j;
-    if (k < n) { run += R1[k] - R0[k]; C[k] = run; }
+  return j >= 1 ? 1.0 : 1.0 - t;
+}
+
+__global__ void k_ion_current(GridP g, long long mlo, long long mhi, double t0, double t1, InjectP ip, int order,
+                              double* C) {
+  const long long m = mlo + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= mhi) return;
+  const double wfac = g.dx * g.dz / (double)(ip.ppc_x * ip.ppc_z);
+  const double zlat = (m + 0.5) * ip.h;
+  const double nm = ip.gamma * lab_density_d(ip, ip.gamma * zlat) * wfac;
+  if (nm == 0.0) return;
+  const double Z0 = (zlat - ip.beta * kC * t0 - g.z0) / g.dz;
+  const double Z1 = (zlat - ip.beta * kC * t1 - g.z0) / g.dz;
+  const int off = order == 3 ? 1 : 0, ng = order == 3 ? 4 : 2;
+  const int klo = (int)floor(fmin(Z0, Z1)) - off;
+  const int khi = (int)floor(fmax(Z0, Z1)) - off + ng - 2;
+  for (int k = max(klo, 0); k <= min(khi, g.nz); k++) {
+    const double d = cum_weight(order, Z1, k) - cum_weight(order, Z0, k);
+    if (d != 0.0) atomicAdd(&C[k], nm * d);
   }
 }
 
 // ---------------------------------------------------------------------------
-// antenna: J_y of one +/- pair per transverse node (Sec. 3.1.2)
-__device__ double emit_field(const LaserP& l, double x, double tp) {
-  const double om = 2.0 * kPi * kC / l.lambda0;
-  const double E0 = l.a0 * kMe * kC * om / kQe;
-  const double dop = (1.0 + l.beta) * l.gamma;
-  const double sl = (1.0 - l.beta_s) * tp / dop;
-  const double sig = l.tau / (2.0 * sqrt(log(2.0)));
-  const double dxr = x - l.x_center;
-  const double gv = E0 * exp(-dxr * dxr / (l.w0 * l.w0)) * exp(-(sl - l.t_peak) * (sl - l.t_peak) / (2.0 * sig * sig)) *
-                    sin(om * (sl - l.t_peak) + l.phase);
-  return (1.0 - l.beta_s) / dop * gv;
-}
-
-// blocks of 32 nodes: the surface current K of the pairs at nodes i0-2 .. i0+33 is computed once
-// (FP64 transcendental functions, spread over many SMs), then each node sums its neighbours
+// antenna: J_y of one +/- pair per transverse node (Sec. 3.1.2). The emitted
+// field factorises into a time factor (amp) and the transverse Gaussian; xs[i]
+// is that Gaussian already weighted by the x shape, and wz[] the z weights of
+// the antenna's positions at t^n and t^{n+1}, averaged and divided by dz.
 template <class T>
-__global__ void k_antenna(GridP g, T* Jy, LaserP l, int order, double t0, double t1) {
-  __shared__ double Ks[36];
-  const int i0 = blockIdx.x * 32;
-  const double th = 0.5 * (t0 + t1);
-  const double za0 = l.z_antenna + l.beta_s * kC * t0;
-  const double za1 = l.z_antenna + l.beta_s * kC * t1;
-  const double zlo = g.z0 + g.gz_lo * g.dz, zhi = g.z0 + g.gz_hi * g.dz;
-  if (za0 < zlo || za0 >= zhi || za1 < zlo || za1 >= zhi) return;
-  for (int q = threadIdx.x; q < 36; q += blockDim.x) {
-    const int ia = i0 - 2 + q;
-    Ks[q] = (ia >= g.gx_lo && ia <= g.gx_hi) ? -2.0 * kEps0 * kC * emit_field(l, ia * g.dx, th) : 0.0;
-  }
-  __syncthreads();
-  const int i = i0 + threadIdx.x;
+__global__ void k_antenna(GridP g, T* Jy, const double* xs, AntennaStep a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i > g.nx) return;
-  const double Z0 = (za0 - g.z0) / g.dz, Z1 = (za1 - g.z0) / g.dz;
-  const int fz = (int)floor(Z0 < Z1 ? Z0 : Z1);
-  double kx = 0.0;
-  for (int d = -2; d <= 2; d++) {
-    const double wx = shape_val(order, (double)d);
-    if (wx != 0.0) kx += Ks[threadIdx.x + 2 + d] * wx;
-  }
+  const double kx = a.amp * xs[i];
   if (kx == 0.0) return;
-  for (int k = fz - 3; k <= fz + 4; k++) {
-    if (k < 0 || k > g.nz) continue;
-    const double wz = 0.5 * (shape_val(order, Z0 - k) + shape_val(order, Z1 - k));
-    if (wz == 0.0) continue;
-    Jy[(long)i * g.ld + k] += T(kx * wz / g.dz);
+#pragma unroll
+  for (int j = 0; j < 8; j++) {
+    const int k = a.k0 + j;
+    if (a.wz[j] != 0.0 && k >= 0 && k <= g.nz) Jy[(long)i * g.ld + k] += T(kx * a.wz[j]);
   }
 }
 
@@ -464,21 +444,27 @@ int launch_rho_noalloc(const GridP& g, Particles<T> p, const Ctrl* ctrl, int cap
   if (cap > 0) k_rho<T><<<(cap + 255) / 256, 256, 0, s>>>(g, p, ctrl, order, -kQe, dst);
   if (ions) {
     // the same row-density kernel as the step, at one time (both outputs alias the scratch)
-    k_ion_rows<<<dim3((g.nz + 1 + 31) / 32, 1), 32, 0, s>>>(g, mlo, mhi, t, t, ip, order, rows, rows);
+    k_ion_rows<<<dim3((g.nz + 1 + 7) / 8, 1), 256, 0, s>>>(g, mlo, mhi, t, t, ip, order, rows, rows);
     launch_ion_rho(g, ion_x, rows, kQe / (g.dx * g.dz), dst, s);
   }
   return cudaPeekAtLastError() == cudaSuccess ? 0 : 3;
 }
 
 void launch_ion_column(const GridP& g, long long mlo, long long mhi, double t0, double t1, const InjectP& ip,
-                       int order, double* R0, double* R1, double* C, cudaStream_t s) {
-  k_ion_rows<<<dim3((g.nz + 1 + 31) / 32, 2), 32, 0, s>>>(g, mlo, mhi, t0, t1, ip, order, R0, R1);
-  k_ion_prefix<<<1, 1024, 0, s>>>(g.nz + 1, R0, R1, C);
+                       int order, double* C, cudaStream_t s) {
+  cudaMemsetAsync(C, 0, sizeof(double) * (size_t)(g.nz + 1), s);
+  const long long n = mhi - mlo;
+  if (n > 0) k_ion_current<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g, mlo, mhi, t0, t1, ip, order, C);
+}
+
+void launch_ion_rows(const GridP& g, long long mlo, long long mhi, double t, const InjectP& ip, int order, double* R,
+                     cudaStream_t s) {
+  k_ion_rows<<<dim3((g.nz + 1 + 7) / 8, 1), 256, 0, s>>>(g, mlo, mhi, t, t, ip, order, R, R);
 }
 
 template <class T>
-void launch_antenna(const GridP& g, T* Jy, const LaserP& lp, int order, double t0, double t1, cudaStream_t s) {
-  k_antenna<T><<<(g.nx + 1 + 31) / 32, 32, 0, s>>>(g, Jy, lp, order, t0, t1);
+void launch_antenna(const GridP& g, T* Jy, const double* xs, const AntennaStep& a, cudaStream_t s) {
+  k_antenna<T><<<(g.nx + 1 + 127) / 128, 128, 0, s>>>(g, Jy, xs, a);
 }
 
 template <class T>
@@ -567,7 +553,7 @@ void launch_shift_particles(Particles<T> p, const Ctrl* ctrl, int cap, int sh, c
 }
 
 #define INST(T)                                                                                                   \
-  template void launch_antenna<T>(const GridP&, T*, const LaserP&, int, double, double, cudaStream_t);           \
+  template void launch_antenna<T>(const GridP&, T*, const double*, const AntennaStep&, cudaStream_t);           \
   template void launch_beam_init<T>(Beam<T>, const double*, const double*, const double*, const double*,          \
                                     const double*, double, double, double, double, double, double*, cudaStream_t); \
   template void launch_beam_push<T>(const GridP&, const FieldPtrs<T>&, Beam<T>, int, double, double, double,      \

@@ -90,6 +90,15 @@ struct pic_ctx {
 
 namespace {
 
+// particle shape (Sec. 2.3): linear or cubic B-spline of the distance in cells
+static double host_shape(int order, double s) {
+  const double a = std::fabs(s);
+  if (order == 1) return a < 1.0 ? 1.0 - a : 0.0;
+  if (a < 1.0) return 2.0 / 3.0 - a * a + 0.5 * a * a * a;
+  if (a < 2.0) { const double t = 2.0 - a; return t * t * t / 6.0; }
+  return 0.0;
+}
+
 template <class T>
 struct Sim : SimBase {
   pic_ctx* c;
@@ -116,10 +125,11 @@ struct Sim : SimBase {
   double zlo_prev = 0.0;
   // ions
   bool ions = false;
-  double *ion_x = nullptr, *ion_R0 = nullptr, *ion_R1 = nullptr, *ion_C = nullptr;
+  double *ion_x = nullptr, *ion_R0 = nullptr, *ion_C = nullptr;
   // laser
   bool has_laser = false;
   LaserP lp{};
+  double* ant_xs = nullptr;    // transverse antenna profile, x shape applied (nx+1)
   // beam
   Beam<T> beam{};
   double* beam_scratch = nullptr;
@@ -324,8 +334,8 @@ struct Sim : SimBase {
       return c->fail(PIC_ENOMEM, "sort allocation failed");
     if (ions) {
       ion_x = al<double>(cf.nx + 1);
-      ion_R0 = al<double>(cf.nz + 1); ion_R1 = al<double>(cf.nz + 1); ion_C = al<double>(cf.nz + 1);
-      if (!ion_x || !ion_R0 || !ion_R1 || !ion_C) return c->fail(PIC_ENOMEM, "allocation failed");
+      ion_R0 = al<double>(cf.nz + 1); ion_C = al<double>(cf.nz + 1);
+      if (!ion_x || !ion_R0 || !ion_C) return c->fail(PIC_ENOMEM, "allocation failed");
       // transverse lattice profile sum_a S(X_a - i)
       std::vector<double> xp(cf.nx + 1, 0.0);
       for (int a = 0; a < ip.nxl; a++) {
@@ -333,12 +343,7 @@ struct Sim : SimBase {
         int fx = (int)std::floor(X);
         for (int i = fx - 2; i <= fx + 3; i++) {
           if (i < 0 || i > cf.nx) continue;
-          double s = std::fabs(X - i), v;
-          if (cf.shape_order == 1) v = s < 1.0 ? 1.0 - s : 0.0;
-          else if (s < 1.0) v = 2.0 / 3.0 - s * s + 0.5 * s * s * s;
-          else if (s < 2.0) { double t = 2.0 - s; v = t * t * t / 6.0; }
-          else v = 0.0;
-          xp[i] += v;
+          xp[i] += host_shape(cf.shape_order, X - i);
         }
       }
       cudaMemcpyAsync(ion_x, xp.data(), xp.size() * 8, cudaMemcpyHostToDevice, c->stream);
@@ -398,8 +403,53 @@ struct Sim : SimBase {
     lp.x_center = l->x_center; lp.phase = l->phase; lp.z_antenna = l->z_antenna; lp.beta_s = l->beta_s;
     lp.gamma = c->hg.gamma; lp.beta = c->hg.beta;
     if (!(l->lambda0 > 0) || !(l->w0 > 0) || !(l->tau_fwhm > 0)) return c->fail(PIC_EINVAL, "laser lambda0, w0, tau must be > 0");
+    // transverse Gaussian of the emitted field on the nodes inside the particle
+    // domain, spread by the x shape: xs[i] = sum_d S(d) G(i + d)
+    const pic_config& cf = c->cfg;
+    std::vector<double> G(cf.nx + 1, 0.0), xs(cf.nx + 1, 0.0);
+    for (int i = g.gx_lo; i <= g.gx_hi && i <= cf.nx; i++) {
+      const double dxr = i * g.dx - lp.x_center;
+      G[i] = std::exp(-dxr * dxr / (lp.w0 * lp.w0));
+    }
+    for (int i = 0; i <= cf.nx; i++)
+      for (int d = -2; d <= 2; d++) {
+        const int ia = i + d;
+        const double wx = host_shape(cf.shape_order, (double)d);
+        if (ia >= 0 && ia <= cf.nx && wx != 0.0) xs[i] += G[ia] * wx;
+      }
+    if (!ant_xs) ant_xs = al<double>(cf.nx + 1);
+    if (!ant_xs) return c->fail(PIC_ENOMEM, "allocation failed");
+    cudaMemcpyAsync(ant_xs, xs.data(), xs.size() * 8, cudaMemcpyHostToDevice, c->stream);
+    cudaStreamSynchronize(c->stream);
     has_laser = true;
     return PIC_OK;
+  }
+
+  // the antenna of one step [t0, t1] (Sec. 3.1.2): K_y = -2 eps0 c E_emit with
+  // E_emit = (1 - beta_s) / ((1 + beta) gamma) g(x, (1 - beta_s) t / ((1 + beta) gamma))
+  // evaluated at the mid time; false when the antenna is outside the particle domain
+  bool antenna_step(double t0, double t1, AntennaStep& a) const {
+    const int order = c->cfg.shape_order;
+    const double za0 = lp.z_antenna + lp.beta_s * kC * t0;
+    const double za1 = lp.z_antenna + lp.beta_s * kC * t1;
+    const double zlo = g.z0 + g.gz_lo * g.dz, zhi = g.z0 + g.gz_hi * g.dz;
+    if (za0 < zlo || za0 >= zhi || za1 < zlo || za1 >= zhi) return false;
+    const double om = 2.0 * kPi * kC / lp.lambda0;
+    const double E0 = lp.a0 * kMe * kC * om / kQe;
+    const double dop = (1.0 + lp.beta) * lp.gamma;
+    const double sl = (1.0 - lp.beta_s) * (0.5 * (t0 + t1)) / dop;
+    const double sig = lp.tau / (2.0 * std::sqrt(std::log(2.0)));
+    const double u = sl - lp.t_peak;
+    a.amp = -2.0 * kEps0 * kC * (1.0 - lp.beta_s) / dop * E0 * std::exp(-u * u / (2.0 * sig * sig)) *
+            std::sin(om * u + lp.phase);
+    const double Z0 = (za0 - g.z0) / g.dz, Z1 = (za1 - g.z0) / g.dz;
+    const int fz = (int)std::floor(Z0 < Z1 ? Z0 : Z1);
+    a.k0 = fz - 3;
+    for (int j = 0; j < 8; j++) {
+      const int k = a.k0 + j;
+      a.wz[j] = 0.5 * (host_shape(order, Z0 - k) + host_shape(order, Z1 - k)) / g.dz;
+    }
+    return true;
   }
 
   void btd_range(double ta, double tb, int& r0, int& r1) const {
@@ -508,8 +558,9 @@ struct Sim : SimBase {
       c->launches++;
     }
     // 4. antenna
-    if (has_laser) {
-      launch_antenna<T>(g, f.J[1], lp, cf.shape_order, tn, tn1, c->stream);
+    AntennaStep ast;
+    if (has_laser && antenna_step(tn, tn1, ast)) {
+      launch_antenna<T>(g, f.J[1], ant_xs, ast, c->stream);
       c->launches++;
     }
     // 5. ion column current
@@ -517,8 +568,8 @@ struct Sim : SimBase {
     if (ions && loaded) {
       long long mlo = std::max(row_first, (long long)std::ceil((zlo_prev + h.beta * kC * tn) / ip.h - 0.5));
       if (step == 0) mlo = row_first;
-      launch_ion_column(g, mlo, row_next, tn, tn1, ip, cf.shape_order, ion_R0, ion_R1, ion_C, c->stream);
-      c->launches += 2;
+      launch_ion_column(g, mlo, row_next, tn, tn1, ip, cf.shape_order, ion_C, c->stream);
+      c->launches += 1;
       ion_coef = -kQe / (g.dx * g.dt);
     }
     // 6-7. current filter + Ampere + PML-E
@@ -621,7 +672,7 @@ struct Sim : SimBase {
         const double t = time_of(step);
         long long mlo = std::max(row_first, (long long)std::ceil((zlo_prev + c->hg.beta * kC * t) / ip.h - 0.5));
         if (step == 0) mlo = row_first;
-        launch_ion_column(g, mlo, row_next, t, t, ip, c->cfg.shape_order, ion_R0, ion_R1, ion_C, c->stream);
+        launch_ion_rows(g, mlo, row_next, t, ip, c->cfg.shape_order, ion_R0, c->stream);
         launch_ion_rho(g, ion_x, ion_R0, kQe / (g.dx * g.dz), stage, c->stream);
       }
     } else {

@@ -191,14 +191,23 @@ void launch_inject(const GridP& g, Particles<T> p, Chunk* chunks, Ctrl* ctrl, co
 void launch_add_counts(Ctrl* ctrl, int dcount, int dchunks, cudaStream_t s);
 
 void launch_ion_column(const GridP& g, long long mlo, long long mhi, double t0, double t1, const InjectP& ip,
-                       int order, double* R0, double* R1, double* C, cudaStream_t s);
+                       int order, double* C, cudaStream_t s);
+// row densities R(k) of the rigid ions at time t (for the charge density)
+void launch_ion_rows(const GridP& g, long long mlo, long long mhi, double t, const InjectP& ip, int order, double* R,
+                     cudaStream_t s);
 
 struct LaserP {
   double lambda0, a0, w0, tau, t_peak, x_center, phase, z_antenna, beta_s;
   double gamma, beta;
 };
+// antenna current of one step: K_y(i) = amp * xs[i] on the rows k0 .. k0+7 with weights wz (1/dz included)
+struct AntennaStep {
+  double amp;
+  int k0;
+  double wz[8];
+};
 template <class T>
-void launch_antenna(const GridP& g, T* Jy, const LaserP& lp, int order, double t0, double t1, cudaStream_t s);
+void launch_antenna(const GridP& g, T* Jy, const double* xs, const AntennaStep& a, cudaStream_t s);
 
 template <class T>
 struct Beam {
