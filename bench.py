@@ -199,6 +199,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--nz", type=int, default=0, help="smaller box for profiling captures (default: the full 4096)")
+    ap.add_argument("--sort-every", type=int, default=0, help="steps between particle sorts (0: the library default)")
     args = ap.parse_args()
 
     from paper_1009_2727_gb300 import workloads as W
@@ -224,7 +225,7 @@ def main():
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_oracle_sample(w)
 
-    sim = Simulation(w, precision=args.precision)
+    sim = Simulation(w, precision=args.precision, sort_every=args.sort_every)
     stream = torch.cuda.current_stream()
     for _ in range(max(args.warmup, 3)):
         sim.step(1)
@@ -270,7 +271,7 @@ def main():
     if not args.no_e2e:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        s2 = Simulation(w, precision=args.precision)
+        s2 = Simulation(w, precision=args.precision, sort_every=args.sort_every)
         k2 = max(args.steps // 2, 10)
         for _ in range(k2):
             s2.step(1)

@@ -47,6 +47,7 @@ __host__ __device__ inline void valid_range(int comp, int nx, int nz, int& i0, i
 struct PmlTabs {
   const double *sx_i, *sx_h, *xx_i, *xx_h, *cx_i, *cx_h;
   const double *sz_i, *sz_h, *xz_i, *xz_h, *cz_i, *cz_h;
+  int iin0, iin1, kin0, kin1;   // nodes whose sigma is zero at both staggerings (the interior)
 };
 
 template <class T>

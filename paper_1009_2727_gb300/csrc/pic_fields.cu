@@ -18,82 +18,107 @@ struct FarK {
   T h1, h2;          // E-bar' = h1 E^n + h2 E-bar
 };
 
-template <class T, bool FRIED>
-__device__ __forceinline__ T eeff(const FieldPtrs<T>& f, const FarK<T>& q, const GridP& g, int c, int i, int k) {
-  if (i < 0 || i > g.nx || k < 0 || k > g.nz) return T(0);
-  const long p = (long)i * g.ld + k;
-  T e = f.E[c][p];
-  if (FRIED) e = q.c1 * e + q.c2 * f.Eo[c][p] + q.c3 * f.Eb[c][p];
-  return e;
-}
+constexpr int FT_X = 16;
+constexpr int FT_Z = 64;
+constexpr int FT_TY = 4;
 
-// Delta*_z at (i, k+1/2) of a field sampled at k, smoothed over x-neighbours (PR-2, PR-3)
+// Faraday + PML-B over a tile of FT_X x FT_Z nodes (threads FT_Z x FT_TY). The
+// Friedman field E_eff (Eq. 7) of the tile's nodes and a one-node halo is built
+// once in shared memory (zero outside the grid); the Friedman average update
+// is written from the same loads. Delta*_z, Delta*_x are the CK operators
+// reduced to 2D (PR-2, PR-3). Tiles clear of the PML take the plain update.
 template <class T, bool FRIED, bool CK>
-__device__ __forceinline__ T dstar_z(const FieldPtrs<T>& f, const FarK<T>& q, const GridP& g, int c, int i, int k) {
-  T d0 = eeff<T, FRIED>(f, q, g, c, i, k + 1) - eeff<T, FRIED>(f, q, g, c, i, k);
-  if (!CK) return d0 / T(g.dz);
-  T dp = eeff<T, FRIED>(f, q, g, c, i + 1, k + 1) - eeff<T, FRIED>(f, q, g, c, i + 1, k);
-  T dm = eeff<T, FRIED>(f, q, g, c, i - 1, k + 1) - eeff<T, FRIED>(f, q, g, c, i - 1, k);
-  return (q.a2 * d0 + q.b2 * (dp + dm)) / T(g.dz);
-}
-
-template <class T, bool FRIED, bool CK>
-__device__ __forceinline__ T dstar_x(const FieldPtrs<T>& f, const FarK<T>& q, const GridP& g, int c, int i, int k) {
-  T d0 = eeff<T, FRIED>(f, q, g, c, i + 1, k) - eeff<T, FRIED>(f, q, g, c, i, k);
-  if (!CK) return d0 / T(g.dx);
-  T dp = eeff<T, FRIED>(f, q, g, c, i + 1, k + 1) - eeff<T, FRIED>(f, q, g, c, i, k + 1);
-  T dm = eeff<T, FRIED>(f, q, g, c, i + 1, k - 1) - eeff<T, FRIED>(f, q, g, c, i, k - 1);
-  return (q.a2 * d0 + q.b2 * (dp + dm)) / T(g.dx);
-}
-
-template <class T, bool FRIED, bool CK>
-__global__ void __launch_bounds__(256) k_faraday(GridP g, FieldPtrs<T> f, PmlTabs pt, FarK<T> q) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  const int i = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i > g.nx || k > g.nz) return;
-  const long p = (long)i * g.ld + k;
-  const T dt = T(g.dt);
-  // Bx at (i, k+1/2): dBx/dt = Delta*_z Ey
-  if (k <= g.nz - 1) {
-    T d = dstar_z<T, FRIED, CK>(f, q, g, EY, i, k);
-    T bo = f.B[0][p], bn;
-    double sz = pt.sz_h[k];
-    if (sz > 0.0) bn = T(pt.xz_h[k] * (double)bo + pt.cz_h[k] * (double)d);
-    else bn = bo + dt * d;
-    f.B[0][p] = bn;
-    f.Bavg[0][p] = T(0.5) * (bo + bn);
-  }
-  // Bz at (i+1/2, k): dBz/dt = -Delta*_x Ey
-  if (i <= g.nx - 1) {
-    T d = dstar_x<T, FRIED, CK>(f, q, g, EY, i, k);
-    T bo = f.B[2][p], bn;
-    double sx = pt.sx_h[i];
-    if (sx > 0.0) bn = T(pt.xx_h[i] * (double)bo - pt.cx_h[i] * (double)d);
-    else bn = bo - dt * d;
-    f.B[2][p] = bn;
-    f.Bavg[2][p] = T(0.5) * (bo + bn);
-  }
-  // By at (i+1/2, k+1/2): dBy/dt = -Delta*_z Ex + Delta*_x Ez; split in the PML
-  if (i <= g.nx - 1 && k <= g.nz - 1) {
-    T a = dstar_z<T, FRIED, CK>(f, q, g, EX, i, k);
-    T b = dstar_x<T, FRIED, CK>(f, q, g, EZ, i, k);
-    T bo = f.B[1][p], bn;
-    double sx = pt.sx_h[i], sz = pt.sz_h[k];
-    if (sx > 0.0 || sz > 0.0) {
-      double yz = pt.xz_h[k] * (double)f.Byz[p] - pt.cz_h[k] * (double)a;
-      double yx = pt.xx_h[i] * (double)f.Byx[p] + pt.cx_h[i] * (double)b;
-      f.Byz[p] = T(yz);
-      f.Byx[p] = T(yx);
-      bn = T(yx) + T(yz);
-    } else {
-      bn = bo - dt * (a - b);
-    }
-    f.B[1][p] = bn;
-    f.Bavg[1][p] = T(0.5) * (bo + bn);
-  }
-  if (FRIED) {
+__global__ void __launch_bounds__(FT_Z* FT_TY) k_faraday(GridP g, FieldPtrs<T> f, PmlTabs pt, FarK<T> q) {
+  constexpr int SX = FT_X + 2, SZ = FT_Z + 2;
+  __shared__ T Ee[3][SX * SZ];
+  const int i0 = blockIdx.y * FT_X, k0 = blockIdx.x * FT_Z;
+  const int tid = threadIdx.y * FT_Z + threadIdx.x;
+  for (int e = tid; e < SX * SZ; e += FT_Z * FT_TY) {
+    const int li = e / SZ, lk = e - li * SZ;
+    const int i = i0 - 1 + li, k = k0 - 1 + lk;
+    const bool in = i >= 0 && i <= g.nx && k >= 0 && k <= g.nz;
+    const bool own = in && li >= 1 && li <= FT_X && lk >= 1 && lk <= FT_Z;
+    const long p = (long)i * g.ld + k;
 #pragma unroll
-    for (int c = 0; c < 3; c++) f.Ebn[c][p] = q.h1 * f.E[c][p] + q.h2 * f.Eb[c][p];
+    for (int c = 0; c < 3; c++) {
+      T v = T(0);
+      if (in) {
+        const T en = f.E[c][p];
+        if (FRIED) {
+          const T eb = f.Eb[c][p];
+          v = q.c1 * en + q.c2 * f.Eo[c][p] + q.c3 * eb;
+          if (own) f.Ebn[c][p] = q.h1 * en + q.h2 * eb;
+        } else {
+          v = en;
+        }
+      }
+      Ee[c][e] = v;
+    }
+  }
+  __syncthreads();
+  const bool interior = i0 >= pt.iin0 && i0 + FT_X - 1 <= pt.iin1 && k0 >= pt.kin0 && k0 + FT_Z - 1 <= pt.kin1;
+  const T dt = T(g.dt), idx = T(1.0 / g.dx), idz = T(1.0 / g.dz);
+  const int k = k0 + threadIdx.x;
+  for (int ti = threadIdx.y; ti < FT_X; ti += FT_TY) {
+    const int i = i0 + ti;
+    if (i > g.nx || k > g.nz) continue;
+    const long p = (long)i * g.ld + k;
+    const int s0 = (ti + 1) * SZ + threadIdx.x + 1;   // node (i, k) in the staged tile
+    // Delta*_z at (i, k+1/2) and Delta*_x at (i+1/2, k) of component c
+    auto dsz = [&](int c) {
+      const T* E = Ee[c];
+      const T d0 = E[s0 + 1] - E[s0];
+      if (!CK) return d0 * idz;
+      const T dp = E[s0 + SZ + 1] - E[s0 + SZ];
+      const T dm = E[s0 - SZ + 1] - E[s0 - SZ];
+      return (q.a2 * d0 + q.b2 * (dp + dm)) * idz;
+    };
+    auto dsx = [&](int c) {
+      const T* E = Ee[c];
+      const T d0 = E[s0 + SZ] - E[s0];
+      if (!CK) return d0 * idx;
+      const T dp = E[s0 + SZ + 1] - E[s0 + 1];
+      const T dm = E[s0 + SZ - 1] - E[s0 - 1];
+      return (q.a2 * d0 + q.b2 * (dp + dm)) * idx;
+    };
+    // Bx at (i, k+1/2): dBx/dt = Delta*_z Ey
+    if (k <= g.nz - 1) {
+      const T d = dsz(EY);
+      const T bo = f.B[0][p];
+      T bn;
+      if (!interior && pt.sz_h[k] > 0.0) bn = T(pt.xz_h[k] * (double)bo + pt.cz_h[k] * (double)d);
+      else bn = bo + dt * d;
+      f.B[0][p] = bn;
+      f.Bavg[0][p] = T(0.5) * (bo + bn);
+    }
+    // Bz at (i+1/2, k): dBz/dt = -Delta*_x Ey
+    if (i <= g.nx - 1) {
+      const T d = dsx(EY);
+      const T bo = f.B[2][p];
+      T bn;
+      if (!interior && pt.sx_h[i] > 0.0) bn = T(pt.xx_h[i] * (double)bo - pt.cx_h[i] * (double)d);
+      else bn = bo - dt * d;
+      f.B[2][p] = bn;
+      f.Bavg[2][p] = T(0.5) * (bo + bn);
+    }
+    // By at (i+1/2, k+1/2): dBy/dt = -Delta*_z Ex + Delta*_x Ez; split in the PML
+    if (i <= g.nx - 1 && k <= g.nz - 1) {
+      const T a = dsz(EX);
+      const T b = dsx(EZ);
+      const T bo = f.B[1][p];
+      T bn;
+      if (!interior && (pt.sx_h[i] > 0.0 || pt.sz_h[k] > 0.0)) {
+        double yz = pt.xz_h[k] * (double)f.Byz[p] - pt.cz_h[k] * (double)a;
+        double yx = pt.xx_h[i] * (double)f.Byx[p] + pt.cx_h[i] * (double)b;
+        f.Byz[p] = T(yz);
+        f.Byx[p] = T(yx);
+        bn = T(yx) + T(yz);
+      } else {
+        bn = bo - dt * (a - b);
+      }
+      f.B[1][p] = bn;
+      f.Bavg[1][p] = T(0.5) * (bo + bn);
+    }
   }
 }
 
@@ -106,10 +131,6 @@ __global__ void __launch_bounds__(256) k_faraday(GridP g, FieldPtrs<T> f, PmlTab
 // would also re-zero values outside each component's valid range, but no particle
 // reads there and the deposited current is zero there (PR-6, PR-10), which the
 // particle guard enforces.
-constexpr int FT_X = 16;
-constexpr int FT_Z = 64;
-constexpr int FT_TY = 4;
-
 // ---------------------------------------------------------------------------
 // TMA staging: one elected thread issues a 3D bulk tensor copy of the tile +
 // halo (box BZ x BX x 1 of component c) into shared memory; completion is
@@ -171,26 +192,101 @@ __device__ __forceinline__ void stage(T* buf, const CUtensorMap* map, int c, int
   tma_load_box(buf, map, gk0, gi0, c, bar, (uint32_t)(tm.BX * tm.BZ * sizeof(T)));
 }
 
-// x-pass: B1[ti][lk] = sum_j c_j A[ti + H + (j - P) s][lk + zoff] for the tile's rows
+// Composed filter over a staged tile: the x-pass writes B1 (FT_X rows of the
+// tile, WZ = FT_Z + 2H columns, row stride WZP), the z-pass writes Zb (FT_X x
+// FT_Z). A points at the element (tile row -H, tile column -H) of the staged
+// box, whose row stride is BZ.
+static_assert(FT_X == 16 && FT_TY == 4 && FT_Z == 64, "filter blocking assumes 16 x 64 tiles and 64 x 4 threads");
+
+__host__ __device__ constexpr int filter_wzp(int H) { return (FT_Z + 2 * H + 3) / 4 * 4; }
+
+// any number of passes and any stride (runtime tap loops)
 template <class T>
-__device__ __forceinline__ void xpass(const T* A, T* B1, const FilterTaps<T>& ft, int BZ, int zoff, int WZ) {
+__device__ __forceinline__ void filter_tile_any(const T* A, int BZ, T* B1, T* Zb, const FilterTaps<T>& ft) {
+  const int WZ = FT_Z + 2 * ft.H, WZP = filter_wzp(ft.H);
   for (int ti = threadIdx.y; ti < FT_X; ti += FT_TY) {
     for (int lk = threadIdx.x; lk < WZ; lk += FT_Z) {
-      const T* col = A + (ti + ft.H - ft.P * ft.s) * BZ + lk + zoff;
+      const T* col = A + (ti + ft.H - ft.P * ft.s) * BZ + lk;
       T acc = T(0);
       for (int j = 0; j <= 2 * ft.P; j++) acc += ft.c[j] * col[j * ft.s * BZ];
-      B1[ti * WZ + lk] = acc;
+      B1[ti * WZP + lk] = acc;
     }
   }
+  __syncthreads();
+  for (int ti = threadIdx.y; ti < FT_X; ti += FT_TY) {
+    const T* row = B1 + ti * WZP + threadIdx.x + ft.H - ft.P * ft.s;
+    T acc = T(0);
+    for (int j = 0; j <= 2 * ft.P; j++) acc += ft.c[j] * row[j * ft.s];
+    Zb[ti * FT_Z + threadIdx.x] = acc;
+  }
+  __syncthreads();
 }
 
-// z-pass value at (ti, tk)
+// P passes at stride 1 with the taps unrolled: each thread filters four
+// consecutive values from a register window of 4 + 2P inputs (x-pass: four rows
+// of one column; z-pass: four columns of one row, read as 16-byte vectors)
 template <class T>
-__device__ __forceinline__ T zpass(const T* B1, const FilterTaps<T>& ft, int WZ, int ti, int tk) {
-  const T* row = B1 + ti * WZ + tk + ft.H - ft.P * ft.s;
-  T acc = T(0);
-  for (int j = 0; j <= 2 * ft.P; j++) acc += ft.c[j] * row[j * ft.s];
-  return acc;
+struct Vec16;
+template <>
+struct Vec16<float> { typedef float4 type; static constexpr int n = 4; };
+template <>
+struct Vec16<double> { typedef double2 type; static constexpr int n = 2; };
+
+template <class T, int P>
+__device__ __forceinline__ void filter_tile_fixed(const T* A, int BZ, T* B1, T* Zb, const FilterTaps<T>& ft) {
+  constexpr int NT = 2 * P + 1, NW = 4 + 2 * P;
+  constexpr int WZ = FT_Z + 2 * P, WZP = filter_wzp(P);
+  {
+    const int r0 = 4 * threadIdx.y;
+    for (int lk = threadIdx.x; lk < WZ; lk += FT_Z) {
+      T v[NW];
+#pragma unroll
+      for (int j = 0; j < NW; j++) v[j] = A[(r0 + j) * BZ + lk];
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        T acc = T(0);
+#pragma unroll
+        for (int j = 0; j < NT; j++) acc += ft.c[j] * v[q + j];
+        B1[(r0 + q) * WZP + lk] = acc;
+      }
+    }
+  }
+  __syncthreads();
+  {
+    typedef typename Vec16<T>::type V;
+    constexpr int VN = Vec16<T>::n;
+    constexpr int NV = (NW + VN - 1) / VN;   // vectors covering the window (stays inside the row)
+    const int tid = threadIdx.y * FT_Z + threadIdx.x;
+    const int ti = tid >> 4, g4 = (tid & 15) * 4;
+    T v[NV * VN];
+    const V* row = reinterpret_cast<const V*>(B1 + ti * WZP + g4);
+#pragma unroll
+    for (int u = 0; u < NV; u++) {
+      const V x = row[u];
+      if constexpr (VN == 4) {
+        v[4 * u] = x.x; v[4 * u + 1] = x.y; v[4 * u + 2] = x.z; v[4 * u + 3] = x.w;
+      } else {
+        v[2 * u] = x.x; v[2 * u + 1] = x.y;
+      }
+    }
+    T o[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      T acc = T(0);
+#pragma unroll
+      for (int j = 0; j < NT; j++) acc += ft.c[j] * v[q + j];
+      o[q] = acc;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; q++) Zb[ti * FT_Z + g4 + q] = o[q];
+  }
+  __syncthreads();
+}
+
+template <class T, int PT>
+__device__ __forceinline__ void filter_tile(const T* A, int BZ, T* B1, T* Zb, const FilterTaps<T>& ft) {
+  if constexpr (PT > 0) filter_tile_fixed<T, PT>(A, BZ, B1, Zb, ft);
+  else filter_tile_any<T>(A, BZ, B1, Zb, ft);
 }
 
 __device__ __forceinline__ void tile_timeout(Ctrl* ctrl, uint64_t* bar0, uint64_t* bar1) {
@@ -202,8 +298,8 @@ __device__ __forceinline__ void tile_timeout(Ctrl* ctrl, uint64_t* bar0, uint64_
   }
 }
 
-// gather copies: fE = F(E^n), fB = F(Bavg)
-template <class T>
+// gather copies: fE = F(E^n), fB = F(Bavg). PT > 0: PT passes at stride 1.
+template <class T, int PT>
 __global__ void __launch_bounds__(FT_Z* FT_TY) k_filter_fields(GridP g, FieldPtrs<T> f, FilterTaps<T> ft,
                                                                const __grid_constant__ CUtensorMap mapE,
                                                                const __grid_constant__ CUtensorMap mapB, TileMaps tm,
@@ -212,8 +308,8 @@ __global__ void __launch_bounds__(FT_Z* FT_TY) k_filter_fields(GridP g, FieldPtr
   T* tile0 = reinterpret_cast<T*>(align128(smraw));
   T* tile1 = tile0 + tile_stride<T>(tm);
   const int H = ft.H;
-  const int WZ = FT_Z + 2 * H;
   T* B1 = tile1 + tile_stride<T>(tm);
+  T* Zb = B1 + FT_X * filter_wzp(H);
   __shared__ __align__(8) uint64_t bar[2];
   const int i0 = blockIdx.y * FT_X, k0 = blockIdx.x * FT_Z;
   const int gi0 = i0 - tm.H, gk0 = k0 - tm.HZ;
@@ -234,20 +330,18 @@ __global__ void __launch_bounds__(FT_Z* FT_TY) k_filter_fields(GridP g, FieldPtr
       return;
     }
     T* dst = c < 3 ? f.fE[c] : f.fB[c - 3];
-    xpass<T>(A + (tm.H - H) * tm.BZ, B1, ft, tm.BZ, tm.HZ - H, WZ);
-    __syncthreads();
+    filter_tile<T, PT>(A + (tm.H - H) * tm.BZ + (tm.HZ - H), tm.BZ, B1, Zb, ft);
     const int gk = k0 + threadIdx.x;
     for (int ti = threadIdx.y; ti < FT_X; ti += FT_TY) {
       const int gi = i0 + ti;
-      const T v = zpass<T>(B1, ft, WZ, ti, threadIdx.x);
-      if (gi <= g.nx && gk <= g.nz) dst[(long)gi * g.ld + gk] = v;
+      if (gi <= g.nx && gk <= g.nz) dst[(long)gi * g.ld + gk] = Zb[ti * FT_Z + threadIdx.x];
     }
-    __syncthreads();
+    // Zb and the other staging buffer are rewritten only after the next filter_tile's first barrier
   }
 }
 
 // Ampere + PML-E, with the current (plus the ion column current) filtered in the tile first
-template <class T, bool FILT>
+template <class T, bool FILT, int PT>
 __global__ void __launch_bounds__(FT_Z* FT_TY) k_ampere(GridP g, FieldPtrs<T> f, PmlTabs pt, FilterTaps<T> ft,
                                                         const double* ion_x, const double* ion_c, double ion_coef,
                                                         const __grid_constant__ CUtensorMap mapJ, TileMaps tm,
@@ -256,8 +350,8 @@ __global__ void __launch_bounds__(FT_Z* FT_TY) k_ampere(GridP g, FieldPtrs<T> f,
   T* tile0 = reinterpret_cast<T*>(align128(smraw));
   T* tile1 = tile0 + tile_stride<T>(tm);
   const int H = FILT ? ft.H : 0;
-  const int WZ = FT_Z + 2 * H;
   T* B1 = tile1 + tile_stride<T>(tm);
+  T* Zb = B1 + FT_X * filter_wzp(H);
   __shared__ __align__(8) uint64_t bar[2];
   const int i0 = blockIdx.y * FT_X, k0 = blockIdx.x * FT_Z;
   const int gi0 = i0 - tm.H, gk0 = k0 - tm.HZ;
@@ -272,6 +366,7 @@ __global__ void __launch_bounds__(FT_Z* FT_TY) k_ampere(GridP g, FieldPtrs<T> f,
   const T dt = T(g.dt);
   const T c2 = T(kC * kC);
   const T ie0 = T(1.0 / kEps0);
+  const T idx = T(1.0 / g.dx), idz = T(1.0 / g.dz);
   const double c2d = kC * kC;
   const int k = k0 + threadIdx.x;
   for (int c = 0; c < 3; c++) {
@@ -282,24 +377,30 @@ __global__ void __launch_bounds__(FT_Z* FT_TY) k_ampere(GridP g, FieldPtrs<T> f,
       return;
     }
     if (c == 2 && ion_x != nullptr) {
-      // rigid ion-column current added to Jz before the filter
+      // rigid ion-column current added to Jz before the filter (each thread
+      // converts its columns' factors once)
+      T cz[(256 + FT_Z - 1) / FT_Z];
+#pragma unroll
+      for (int u = 0; u < (256 + FT_Z - 1) / FT_Z; u++) {
+        const int lk = threadIdx.x + u * FT_Z, gk = gk0 + lk;
+        cz[u] = (lk < tm.BZ && gk >= 0 && gk <= g.nz) ? T(ion_c[gk]) : T(0);
+      }
       for (int li = threadIdx.y; li < tm.BX; li += FT_TY) {
         const int gi = gi0 + li;
         if (gi < 0 || gi > g.nx) continue;
-        const double ix = ion_coef * ion_x[gi];
-        for (int lk = threadIdx.x; lk < tm.BZ; lk += FT_Z) {
-          const int gk = gk0 + lk;
-          if (gk >= 0 && gk <= g.nz) A[li * tm.BZ + lk] += T(ix * ion_c[gk]);
+        const T ix = T(ion_coef * ion_x[gi]);
+#pragma unroll
+        for (int u = 0; u < (256 + FT_Z - 1) / FT_Z; u++) {
+          const int lk = threadIdx.x + u * FT_Z;
+          if (lk < tm.BZ) A[li * tm.BZ + lk] += ix * cz[u];
         }
       }
       __syncthreads();
     }
     int vi0, vi1, vk0, vk1;
     valid_range(c, g.nx, g.nz, vi0, vi1, vk0, vk1);
-    if (FILT) {
-      xpass<T>(A + (tm.H - H) * tm.BZ, B1, ft, tm.BZ, tm.HZ - H, WZ);
-      __syncthreads();
-    }
+    if (FILT) filter_tile<T, PT>(A + (tm.H - H) * tm.BZ + (tm.HZ - H), tm.BZ, B1, Zb, ft);
+    const bool interior = i0 >= pt.iin0 && i0 + FT_X - 1 <= pt.iin1 && k0 >= pt.kin0 && k0 + FT_Z - 1 <= pt.kin1;
     for (int ti = threadIdx.y; ti < FT_X; ti += FT_TY) {
       const int i = i0 + ti;
       if (i > g.nx || k > g.nz) continue;
@@ -310,24 +411,21 @@ __global__ void __launch_bounds__(FT_Z* FT_TY) k_ampere(GridP g, FieldPtrs<T> f,
         f.Eo[c][p] = T(0);
         continue;
       }
-      const T jv = FILT ? zpass<T>(B1, ft, WZ, ti, threadIdx.x) : A[(ti + tm.H) * tm.BZ + threadIdx.x + tm.HZ];
+      const T jv = FILT ? Zb[ti * FT_Z + threadIdx.x] : A[(ti + tm.H) * tm.BZ + threadIdx.x + tm.HZ];
       const T eo = f.E[c][p];
       T en;
       if (c == 0) {
-        T d = (f.B[1][p] - f.B[1][p - 1]) / T(g.dz);
-        double sz = pt.sz_i[k];
-        if (sz > 0.0) en = T(pt.xz_i[k] * (double)eo - c2d * pt.cz_i[k] * (double)d);
+        T d = (f.B[1][p] - f.B[1][p - 1]) * idz;
+        if (!interior && pt.sz_i[k] > 0.0) en = T(pt.xz_i[k] * (double)eo - c2d * pt.cz_i[k] * (double)d);
         else en = eo - dt * (c2 * d + jv * ie0);
       } else if (c == 2) {
-        T d = (f.B[1][p] - f.B[1][p - g.ld]) / T(g.dx);
-        double sx = pt.sx_i[i];
-        if (sx > 0.0) en = T(pt.xx_i[i] * (double)eo + c2d * pt.cx_i[i] * (double)d);
+        T d = (f.B[1][p] - f.B[1][p - g.ld]) * idx;
+        if (!interior && pt.sx_i[i] > 0.0) en = T(pt.xx_i[i] * (double)eo + c2d * pt.cx_i[i] * (double)d);
         else en = eo + dt * (c2 * d - jv * ie0);
       } else {
-        T dbx = (f.B[0][p] - f.B[0][p - 1]) / T(g.dz);
-        T dbz = (f.B[2][p] - f.B[2][p - g.ld]) / T(g.dx);
-        double sx = pt.sx_i[i], sz = pt.sz_i[k];
-        if (sx > 0.0 || sz > 0.0) {
+        T dbx = (f.B[0][p] - f.B[0][p - 1]) * idz;
+        T dbz = (f.B[2][p] - f.B[2][p - g.ld]) * idx;
+        if (!interior && (pt.sx_i[i] > 0.0 || pt.sz_i[k] > 0.0)) {
           double yz = pt.xz_i[k] * (double)f.Eyz[p] + c2d * pt.cz_i[k] * (double)dbx;
           double yx = pt.xx_i[i] * (double)f.Eyx[p] - c2d * pt.cx_i[i] * (double)dbz;
           f.Eyz[p] = T(yz);
@@ -352,7 +450,7 @@ void launch_faraday(const GridP& g, const FieldPtrs<T>& f, const PmlTabs& pt, do
   q.a2 = T(a2); q.b2 = T(b2);
   q.c1 = T(1.0 + theta / 4.0); q.c2 = T(-0.5); q.c3 = T(0.5 - theta / 4.0);
   q.h1 = T(1.0 - theta / 2.0); q.h2 = T(theta / 2.0);
-  dim3 blk(32, 8), grd((g.nz + 1 + 31) / 32, (g.nx + 1 + 7) / 8);
+  dim3 blk(FT_Z, FT_TY), grd((g.nz + 1 + FT_Z - 1) / FT_Z, (g.nx + 1 + FT_X - 1) / FT_X);
   const bool ck = b2 != 0.0;
   if (friedman) {
     if (ck) k_faraday<T, true, true><<<grd, blk, 0, s>>>(g, f, pt, q);
@@ -366,7 +464,7 @@ void launch_faraday(const GridP& g, const FieldPtrs<T>& f, const PmlTabs& pt, do
 template <class T>
 static size_t tile_smem(const TileMaps& tm, int H) {
   // + 128: room to round the dynamic shared base up to a 128-byte line
-  return (2 * (size_t)tile_stride<T>(tm) + (size_t)FT_X * (FT_Z + 2 * H)) * sizeof(T) + 128;
+  return (2 * (size_t)tile_stride<T>(tm) + (size_t)FT_X * filter_wzp(H) + (size_t)FT_X * FT_Z) * sizeof(T) + 128;
 }
 
 template <class T>
@@ -448,6 +546,17 @@ bool make_tile_maps(const GridP& g, const FieldPtrs<T>& f, int H, TileMaps& tm) 
   return ok;
 }
 
+// compile-time tap count for the common stride-1 filters; 0 = runtime loops
+template <class T>
+static int filter_pt(const FilterTaps<T>& ft) { return (ft.s == 1 && ft.P >= 1 && ft.P <= 6) ? ft.P : 0; }
+
+template <class T, int PT>
+static void run_filter_fields(dim3 grd, dim3 blk, size_t sm, cudaStream_t s, const GridP& g, const FieldPtrs<T>& f,
+                              const FilterTaps<T>& ft, const CUtensorMap& mE, const TileMaps& tm, Ctrl* ctrl) {
+  cudaFuncSetAttribute(k_filter_fields<T, PT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_filter_fields<T, PT><<<grd, blk, sm, s>>>(g, f, ft, mE, tm.Bavg, tm, ctrl);
+}
+
 template <class T>
 void launch_filter_fields(const GridP& g, const FieldPtrs<T>& f, const FilterSpec& fs, bool enabled,
                           const TileMaps& tm, Ctrl* ctrl, cudaStream_t s) {
@@ -456,8 +565,23 @@ void launch_filter_fields(const GridP& g, const FieldPtrs<T>& f, const FilterSpe
   dim3 grd((g.nz + 1 + FT_Z - 1) / FT_Z, (g.nx + 1 + FT_X - 1) / FT_X), blk(FT_Z, FT_TY);
   const size_t sm = tile_smem<T>(tm, ft.H);
   const CUtensorMap& mE = tm.Ebase[0] == (const void*)f.E[0] ? tm.E[0] : tm.E[1];
-  cudaFuncSetAttribute(k_filter_fields<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_filter_fields<T><<<grd, blk, sm, s>>>(g, f, ft, mE, tm.Bavg, tm, ctrl);
+  switch (filter_pt(ft)) {
+    case 1: run_filter_fields<T, 1>(grd, blk, sm, s, g, f, ft, mE, tm, ctrl); break;
+    case 2: run_filter_fields<T, 2>(grd, blk, sm, s, g, f, ft, mE, tm, ctrl); break;
+    case 3: run_filter_fields<T, 3>(grd, blk, sm, s, g, f, ft, mE, tm, ctrl); break;
+    case 4: run_filter_fields<T, 4>(grd, blk, sm, s, g, f, ft, mE, tm, ctrl); break;
+    case 5: run_filter_fields<T, 5>(grd, blk, sm, s, g, f, ft, mE, tm, ctrl); break;
+    case 6: run_filter_fields<T, 6>(grd, blk, sm, s, g, f, ft, mE, tm, ctrl); break;
+    default: run_filter_fields<T, 0>(grd, blk, sm, s, g, f, ft, mE, tm, ctrl); break;
+  }
+}
+
+template <class T, bool FILT, int PT>
+static void run_ampere(dim3 grd, dim3 blk, size_t sm, cudaStream_t s, const GridP& g, const FieldPtrs<T>& f,
+                       const PmlTabs& pt, const FilterTaps<T>& ft, const double* ion_x, const double* ion_c,
+                       double ion_coef, const CUtensorMap& mJ, const TileMaps& tm, Ctrl* ctrl) {
+  cudaFuncSetAttribute(k_ampere<T, FILT, PT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_ampere<T, FILT, PT><<<grd, blk, sm, s>>>(g, f, pt, ft, ion_x, ion_c, ion_coef, mJ, tm, ctrl);
 }
 
 template <class T>
@@ -468,12 +592,18 @@ void launch_ampere(const GridP& g, const FieldPtrs<T>& f, const PmlTabs& pt, con
   dim3 grd((g.nz + 1 + FT_Z - 1) / FT_Z, (g.nx + 1 + FT_X - 1) / FT_X), blk(FT_Z, FT_TY);
   const CUtensorMap& mJ = tm.Jbase[0] == (const void*)f.J[0] ? tm.J[0] : tm.J[1];
   const size_t sm = tile_smem<T>(tm, filter_on ? ft.H : 0);
-  if (filter_on) {
-    cudaFuncSetAttribute(k_ampere<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_ampere<T, true><<<grd, blk, sm, s>>>(g, f, pt, ft, ion_x, ion_c, ion_coef, mJ, tm, ctrl);
-  } else {
-    cudaFuncSetAttribute(k_ampere<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_ampere<T, false><<<grd, blk, sm, s>>>(g, f, pt, ft, ion_x, ion_c, ion_coef, mJ, tm, ctrl);
+  if (!filter_on) {
+    run_ampere<T, false, 0>(grd, blk, sm, s, g, f, pt, ft, ion_x, ion_c, ion_coef, mJ, tm, ctrl);
+    return;
+  }
+  switch (filter_pt(ft)) {
+    case 1: run_ampere<T, true, 1>(grd, blk, sm, s, g, f, pt, ft, ion_x, ion_c, ion_coef, mJ, tm, ctrl); break;
+    case 2: run_ampere<T, true, 2>(grd, blk, sm, s, g, f, pt, ft, ion_x, ion_c, ion_coef, mJ, tm, ctrl); break;
+    case 3: run_ampere<T, true, 3>(grd, blk, sm, s, g, f, pt, ft, ion_x, ion_c, ion_coef, mJ, tm, ctrl); break;
+    case 4: run_ampere<T, true, 4>(grd, blk, sm, s, g, f, pt, ft, ion_x, ion_c, ion_coef, mJ, tm, ctrl); break;
+    case 5: run_ampere<T, true, 5>(grd, blk, sm, s, g, f, pt, ft, ion_x, ion_c, ion_coef, mJ, tm, ctrl); break;
+    case 6: run_ampere<T, true, 6>(grd, blk, sm, s, g, f, pt, ft, ion_x, ion_c, ion_coef, mJ, tm, ctrl); break;
+    default: run_ampere<T, true, 0>(grd, blk, sm, s, g, f, pt, ft, ion_x, ion_c, ion_coef, mJ, tm, ctrl); break;
   }
 }
 
