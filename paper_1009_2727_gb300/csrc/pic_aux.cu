@@ -288,8 +288,11 @@ __global__ void k_rho(GridP g, Particles<T> p, const Ctrl* ctrl, int order, doub
   if (w == 0.0) return;
   double X, Z;
   if constexpr (CellPos<T>::value) {
+    int iz;
+    float tz;
+    frame_z(p.cell[j], p.oz[j], g.fr_sz, g.fr_fz, iz, tz);
     X = cell_x(p.cell[j]) + (double)p.ox[j];
-    Z = cell_z(p.cell[j]) + (double)p.oz[j];
+    Z = iz + (double)tz;
   } else {
     X = p.x[j] / g.dx; Z = (p.z[j] - g.z0) / g.dz;
   }
@@ -383,29 +386,34 @@ __global__ void k_compact(GridP g, Particles<T> p, const Ctrl* ctrl, double* out
   const int o = atomicAdd(nout, 1);
   if (o >= cap_out) return;
   if constexpr (CellPos<T>::value) {
+    int iz;
+    float tz;
+    frame_z(p.cell[j], p.oz[j], g.fr_sz, g.fr_fz, iz, tz);
     out6[0 * (size_t)cap_out + o] = (cell_x(p.cell[j]) + (double)p.ox[j]) * g.dx;
-    out6[1 * (size_t)cap_out + o] = g.z0 + (cell_z(p.cell[j]) + (double)p.oz[j]) * g.dz;
+    out6[1 * (size_t)cap_out + o] = g.z0 + (iz + (double)tz) * g.dz;
   } else {
     out6[0 * (size_t)cap_out + o] = p.x[j];
     out6[1 * (size_t)cap_out + o] = p.z[j];
   }
   out6[2 * (size_t)cap_out + o] = p.ux[j];
   out6[3 * (size_t)cap_out + o] = p.uy[j];
-  out6[4 * (size_t)cap_out + o] = p.uz[j];
+  out6[4 * (size_t)cap_out + o] = CellPos<T>::value ? (double)g.fr_u0 + (double)p.uz[j] : (double)p.uz[j];
   out6[5 * (size_t)cap_out + o] = p.w[j];
   ido[o] = p.id[j];
 }
 
-// moving window: grid-relative cells of the mixed path follow the grid
+// moving window: the stored cells of the mixed path move with the grid
 template <class T>
-__global__ void k_shift_particles(Particles<T> p, const Ctrl* ctrl, int sh) {
+__global__ void k_shift_particles(GridP g, Particles<T> p, const Ctrl* ctrl, int sh) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= ctrl->count) return;
   if (p.w[j] == T(0)) return;
   const uint32_t c = p.cell[j];
-  const int iz = cell_z(c) - sh;
-  if (iz < 0) { p.w[j] = T(0); return; }
-  p.cell[j] = pack_cell(cell_x(c), iz);
+  int iz;
+  float tz;
+  frame_z(c, p.oz[j], g.fr_sz, g.fr_fz, iz, tz);
+  if (iz - sh < 0) { p.w[j] = T(0); return; }
+  p.cell[j] = pack_cell(cell_x(c), (cell_z(c) - sh) & 0xffff);
 }
 
 }  // namespace
@@ -546,9 +554,9 @@ void launch_compact_copy(const GridP& g, Particles<T> p, const Ctrl* ctrl, int c
 }
 
 template <class T>
-void launch_shift_particles(Particles<T> p, const Ctrl* ctrl, int cap, int sh, cudaStream_t s) {
+void launch_shift_particles(const GridP& g, Particles<T> p, const Ctrl* ctrl, int cap, int sh, cudaStream_t s) {
   if constexpr (CellPos<T>::value) {
-    if (cap > 0) k_shift_particles<T><<<(cap + 255) / 256, 256, 0, s>>>(p, ctrl, sh);
+    if (cap > 0) k_shift_particles<T><<<(cap + 255) / 256, 256, 0, s>>>(g, p, ctrl, sh);
   }
 }
 
@@ -568,7 +576,7 @@ void launch_shift_particles(Particles<T> p, const Ctrl* ctrl, int cap, int sh, c
   template void launch_convert_back<T>(const double*, T*, const GridP&, cudaStream_t);                           \
   template void launch_compact_copy<T>(const GridP&, Particles<T>, const Ctrl*, int, double*, uint32_t*, int*,      \
                                        cudaStream_t);                                                             \
-  template void launch_shift_particles<T>(Particles<T>, const Ctrl*, int, int, cudaStream_t);                 \
+  template void launch_shift_particles<T>(const GridP&, Particles<T>, const Ctrl*, int, int, cudaStream_t);                 \
   template int launch_rho_noalloc<T>(const GridP&, Particles<T>, const Ctrl*, int, int, bool, long long,         \
                                      long long, double, const InjectP&, const double*, double*, cudaStream_t);
 INST(float)

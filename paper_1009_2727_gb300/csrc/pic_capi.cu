@@ -169,6 +169,8 @@ struct Sim : SimBase {
     g.dx = h.dx; g.dz = h.dz; g.dt = h.dt; g.z0 = 0.0;
     g.gx_lo = h.gx_lo; g.gx_hi = h.gx_hi; g.gz_lo = h.gz_lo; g.gz_hi = h.gz_hi;
     g.pml = cf.pml_cells;
+    g.fr_sz = 0; g.fr_fz = 0.0f;
+    g.fr_u0 = (float)(-h.gamma * h.beta * kC);
     friedman = cf.theta != 0.0;
     filt_gather = cf.filter_gather && cf.filter_passes + cf.filter_compensate > 0;
     filt_J = cf.filter_J && cf.filter_passes + cf.filter_compensate > 0;
@@ -272,6 +274,9 @@ struct Sim : SimBase {
   }
 
   double time_of(long long n) const { return (double)n * g.dt; }
+  // frame shift of the mixed path's stored z at step n: S = beta c t / dz (cells)
+  double frame_shift(long long n) const { return c->hg.beta * kC * time_of(n) / g.dz; }
+  void set_frame(long long n) { frame_of(frame_shift(n), g.fr_sz, g.fr_fz); }
   double zlo() const { return g.z0 + g.gz_lo * g.dz; }
   double zhi() const { return g.z0 + g.gz_hi * g.dz; }
 
@@ -290,6 +295,7 @@ struct Sim : SimBase {
   int load_plasma(const pic_plasma* p) {
     if (loaded) return c->fail(PIC_ESTATE, "plasma already loaded");
     pl = *p;
+    set_frame(step);
     const pic_config& cf = c->cfg;
     const HostGeom& h = c->hg;
     if (pl.ppc_x < 1 || pl.ppc_z < 1) return c->fail(PIC_EINVAL, "ppc must be >= 1");
@@ -504,7 +510,7 @@ struct Sim : SimBase {
     }
     if (loaded && chunks) {
       launch_shift_chunks(chunks, ctrl, (int)sh, chunk_cap, c->stream);
-      launch_shift_particles<T>(P, ctrl, cap, (int)sh, c->stream);
+      launch_shift_particles<T>(g, P, ctrl, cap, (int)sh, c->stream);
       c->launches += CellPos<T>::value ? 2 : 1;
     }
     shifts = want;
@@ -530,6 +536,7 @@ struct Sim : SimBase {
     const pic_config& cf = c->cfg;
     const HostGeom& h = c->hg;
     const double tn = time_of(step), tn1 = time_of(step + 1);
+    set_frame(step);
     window_shift();
     set_ptrs_for_step();
     btd(0);
@@ -558,10 +565,15 @@ struct Sim : SimBase {
     // 3. particles
     if (loaded && cap > 0) {
       tstart(0);
-      launch_push<T>(g, f, P, chunks, ctrl, cf.shape_order, push_grid, smem_nodes, -kQe, kMe, c->stream);
+      int fr1_sz;
+      float fr1_fz;
+      frame_of(frame_shift(step + 1), fr1_sz, fr1_fz);
+      launch_push<T>(g, f, P, chunks, ctrl, cf.shape_order, push_grid, smem_nodes, -kQe, kMe, c->hg.gamma, c->hg.beta,
+                     fr1_sz, fr1_fz, c->stream);
       tstop(0);
       c->launches++;
     }
+    set_frame(step + 1);   // the particles now hold their t^{n+1} positions
     if (beam.n > 0) {
       launch_beam_push<T>(g, f, beam, cf.shape_order, tn, tn1, 0.0, beam_scratch, c->stream);
       c->launches++;

@@ -28,6 +28,14 @@ struct GridP {
   double z0;                 // grid origin along z (moving window)
   int gx_lo, gx_hi, gz_lo, gz_hi;  // particle domain (cells)
   int pml;                   // PML cells (0 = none)
+  // mixed path: particle z is stored in the frame drifting with the plasma
+  // (-beta c); grid z = stored z - S with S = beta c t / dz = fr_sz + fr_fz
+  // (fr_sz modulo 2^16, fr_fz in [0, 1)) at the time of the stored positions
+  int fr_sz;
+  float fr_fz;
+  // mixed path: u_z is stored as u_z - fr_u0, fr_u0 = -gamma beta c (FP32), the
+  // plasma drift momentum, so that its changes keep FP32 precision
+  float fr_u0;
 };
 
 // Valid index range of each E/B component (PEC walls); J uses the E ranges.
@@ -84,8 +92,11 @@ struct Chunk {
 };
 
 // Particle storage (structure of arrays). The FP64 path keeps absolute
-// positions; the mixed path keeps the grid-relative cell (iz | ix << 16) and
-// the FP32 offset inside the cell, so that its push needs no FP64 arithmetic.
+// positions; the mixed path keeps a cell (iz | ix << 16) and the FP32 offset
+// inside it, so that its push needs no FP64 arithmetic. Its z is kept in the
+// frame drifting with the plasma (see GridP::fr_sz): a particle at the plasma
+// drift never changes its stored z, so the cold plasma keeps its place against
+// the rigid ions exactly instead of accumulating FP32 rounding every step.
 template <class T>
 struct Particles {
   double* x; double* z;          // FP64 path [m]
@@ -102,6 +113,31 @@ struct CellPos<float> { static constexpr bool value = true; };
 __host__ __device__ inline uint32_t pack_cell(int ix, int iz) { return (uint32_t)iz | ((uint32_t)ix << 16); }
 __host__ __device__ inline int cell_x(uint32_t c) { return (int)(c >> 16); }
 __host__ __device__ inline int cell_z(uint32_t c) { return (int)(c & 0xffffu); }
+
+// mixed path: grid cell and in-cell offset along z of a particle stored in the
+// drifting frame, for the frame shift (sz, fz) (the stored cell is taken
+// modulo 2^16, so S may grow without bound)
+__host__ __device__ inline void frame_z(uint32_t c, float oz, int sz, float fz, int& iz, float& tz) {
+  float t = oz - fz;
+  int b = 0;
+  if (t < 0.0f) {
+    t += 1.0f;
+    b = 1;
+    if (t >= 1.0f) { t = 0.0f; b = 0; }
+  }
+  iz = (cell_z(c) - sz - b) & 0xffff;
+  tz = t;
+}
+
+// frame shift S (cells, FP64) -> (S mod 2^16 integer part, FP32 fraction)
+inline void frame_of(double S, int& sz, float& fz) {
+  const double fl = __builtin_floor(S);
+  float f = (float)(S - fl);
+  long long si = (long long)fl;
+  if (f >= 1.0f) { f = 0.0f; si += 1; }
+  sz = (int)(si & 0xffff);
+  fz = f;
+}
 
 // Control block in device memory.
 struct Ctrl {
@@ -159,7 +195,8 @@ void launch_ampere(const GridP& g, const FieldPtrs<T>& f, const PmlTabs& pt, con
 
 template <class T>
 void launch_push(const GridP& g, const FieldPtrs<T>& f, Particles<T> p, Chunk* chunks, Ctrl* ctrl, int order,
-                 int grid_blocks, int smem_nodes, double q, double m, cudaStream_t s);
+                 int grid_blocks, int smem_nodes, double q, double m, double gamma_b, double beta_b, int fr1_sz,
+                 float fr1_fz, cudaStream_t s);
 
 struct SortBufs {
   int* cell_cnt;       // ntiles*tx*tz, cells in tile-major order: particles per cell
@@ -247,7 +284,7 @@ template <class T>
 void launch_compact_copy(const GridP& g, Particles<T> p, const Ctrl* ctrl, int cap, double* out6, uint32_t* id_out,
                          int* nout, cudaStream_t s);
 template <class T>
-void launch_shift_particles(Particles<T> p, const Ctrl* ctrl, int cap, int sh, cudaStream_t s);
+void launch_shift_particles(const GridP& g, Particles<T> p, const Ctrl* ctrl, int cap, int sh, cudaStream_t s);
 // returns 0, or 1 (nz above the scratch size), 2 (scratch address lookup failed), 3 (launch error)
 template <class T>
 int launch_rho_noalloc(const GridP& g, Particles<T> p, const Ctrl* ctrl, int cap, int order, bool ions,

@@ -103,6 +103,11 @@ struct PushConst {
   double qm_half;                   // q dt/(2m)
   double kx, kz, ky;                // deposit: -q/(dz dt), -q/(dx dt), q/(dx dz)
   float qm_half_f, kx_f, kz_f, ky_f;  // the same in FP32 for the mixed path
+  // mixed path: the plasma drift momentum u0 = -gamma beta c (FP32) and gamma0; the
+  // frame shift (GridP::fr_sz) at t^n and t^{n+1}
+  float u0z_f, g0_f, g0sq_f;
+  int fr0_sz, fr1_sz;
+  float fr0_fz, fr1_fz;
 };
 
 // Esirkepov current of one particle on an NDX (x) by ND (z) window whose first
@@ -172,10 +177,14 @@ __device__ __forceinline__ void push_one(const T* __restrict__ Eb, const T* __re
   int fx, fz, fxh, fzh;
   T tx, tz, txh, tzh;
   double x = 0.0, z = 0.0, X = 0.0, Z = 0.0;
+  uint32_t cs0 = 0;   // mixed path: stored cell and z offset (drifting frame)
+  float ozs = 0.0f;
   if constexpr (CP) {
-    const uint32_t c = p.cell[pi];
-    fx = cell_x(c); fz = cell_z(c);
-    tx = p.ox[pi]; tz = p.oz[pi];
+    cs0 = p.cell[pi];
+    ozs = p.oz[pi];
+    fx = cell_x(cs0);
+    frame_z(cs0, ozs, pc.fr0_sz, pc.fr0_fz, fz, tz);
+    tx = p.ox[pi];
     fxh = tx >= T(0.5) ? fx : fx - 1; txh = tx >= T(0.5) ? tx - T(0.5) : tx + T(0.5);
     fzh = tz >= T(0.5) ? fz : fz - 1; tzh = tz >= T(0.5) ? tz - T(0.5) : tz + T(0.5);
   } else {
@@ -207,37 +216,53 @@ __device__ __forceinline__ void push_one(const T* __restrict__ Eb, const T* __re
     By = interp<T, ORDER>(Bb + cs, ld, ox, oz, fxh, fzh, wxh, wzh);
     Bz = interp<T, ORDER>(Bb + 2 * cs, ld, ox, oz, fxh, fz, wxh, wzi);
   }
-  // relativistic Boris push (the FP32 path takes 1/gamma from rsqrt and a fast
-  // reciprocal; the FP64 path divides)
+  // relativistic Boris push
   T k;
   if constexpr (CP) k = pc.qm_half_f; else k = T(pc.qm_half);
   const T ic2 = T(1.0 / (kC * kC));
-  T umx = ux + k * Ex, umy = uy + k * Ey, umz = uz + k * Ez;
-  T tbx, tby, tbz, t2, sf;
-  if constexpr (CP) {
-    const float kig = k * rsqrtf(1.0f + (umx * umx + umy * umy + umz * umz) * ic2);
-    tbx = kig * Bx; tby = kig * By; tbz = kig * Bz;
-    t2 = tbx * tbx + tby * tby + tbz * tbz;
-    sf = __fdividef(2.0f, 1.0f + t2);
-  } else {
-    const T gm = sqrt(T(1) + (umx * umx + umy * umy + umz * umz) * ic2);
-    tbx = k * Bx / gm; tby = k * By / gm; tbz = k * Bz / gm;
-    t2 = tbx * tbx + tby * tby + tbz * tbz;
-    sf = T(2) / (T(1) + t2);
-  }
-  T sbx = sf * tbx, sby = sf * tby, sbz = sf * tbz;
-  T upx = umx + (umy * tbz - umz * tby);
-  T upy = umy + (umz * tbx - umx * tbz);
-  T upz = umz + (umx * tby - umy * tbx);
-  T plx = umx + (upy * sbz - upz * sby);
-  T ply = umy + (upz * sbx - upx * sbz);
-  T plz = umz + (upx * sby - upy * sbx);
-  ux = plx + k * Ex; uy = ply + k * Ey; uz = plz + k * Ez;
   T vx, vy, vz;
   if constexpr (CP) {
-    const float ig1 = rsqrtf(1.0f + (ux * ux + uy * uy + uz * uz) * ic2);
-    vx = ux * ig1; vy = uy * ig1; vz = uz * ig1;
+    // FP32 path: uz holds u_z - u0 (u0 = -gamma beta c, the plasma drift
+    // momentum), so the kicks and the rotation's change of u_z keep FP32
+    // precision; 1/gamma from rsqrt, 2/(1+t^2) from a fast reciprocal
+    const float u0 = pc.u0z_f;
+    const float umx = ux + k * Ex, umy = uy + k * Ey, dm = uz + k * Ez;
+    const float kig = k * rsqrtf(pc.g0sq_f + (umx * umx + umy * umy + dm * (2.0f * u0 + dm)) * ic2);
+    const float tbx = kig * Bx, tby = kig * By, tbz = kig * Bz;
+    const float t2 = tbx * tbx + tby * tby + tbz * tbz;
+    const float sf = __fdividef(2.0f, 1.0f + t2);
+    const float sbx = sf * tbx, sby = sf * tby, sbz = sf * tbz;
+    const float umz = u0 + dm;
+    const float upx = umx + (umy * tbz - umz * tby);
+    const float upy = umy + (umz * tbx - umx * tbz);
+    const float dp = dm + (umx * tby - umy * tbx);
+    const float upz = u0 + dp;
+    const float plx = umx + (upy * sbz - upz * sby);
+    const float ply = umy + (upz * sbx - upx * sbz);
+    const float dl = dm + (upx * sby - upy * sbx);
+    ux = plx + k * Ex; uy = ply + k * Ey; uz = dl + k * Ez;
+    // gamma^2 - gamma0^2 from the deviation; v_z - v0 (v0 = u0/gamma0, the plasma
+    // drift carried by the stored frame) formed from deviations, so that it is
+    // exactly zero for a particle at the drift momentum, whose stored z stays put
+    const float g2d = (ux * ux + uy * uy + uz * (2.0f * u0 + uz)) * ic2;
+    const float ig1 = rsqrtf(pc.g0sq_f + g2d);
+    vx = ux * ig1; vy = uy * ig1;
+    const float dg = __fdividef(g2d, __fdividef(1.0f, ig1) + pc.g0_f);   // gamma - gamma0
+    vz = (uz - u0 * __fdividef(dg, pc.g0_f)) * ig1;
   } else {
+    T umx = ux + k * Ex, umy = uy + k * Ey, umz = uz + k * Ez;
+    const T gm = sqrt(T(1) + (umx * umx + umy * umy + umz * umz) * ic2);
+    const T tbx = k * Bx / gm, tby = k * By / gm, tbz = k * Bz / gm;
+    const T t2 = tbx * tbx + tby * tby + tbz * tbz;
+    const T sf = T(2) / (T(1) + t2);
+    const T sbx = sf * tbx, sby = sf * tby, sbz = sf * tbz;
+    const T upx = umx + (umy * tbz - umz * tby);
+    const T upy = umy + (umz * tbx - umx * tbz);
+    const T upz = umz + (umx * tby - umy * tbx);
+    const T plx = umx + (upy * sbz - upz * sby);
+    const T ply = umy + (upz * sbx - upx * sbz);
+    const T plz = umz + (upx * sby - upy * sbx);
+    ux = plx + k * Ex; uy = ply + k * Ey; uz = plz + k * Ez;
     const T g1 = sqrt(T(1) + (ux * ux + uy * uy + uz * uz) * ic2);
     vx = ux / g1; vy = uy / g1; vz = uz / g1;
   }
@@ -245,13 +270,18 @@ __device__ __forceinline__ void push_one(const T* __restrict__ Eb, const T* __re
   int fxn, fzn;
   T txn, tzn;
   double xn = 0.0, zn = 0.0;
+  uint32_t csn = 0;
+  float ozn = 0.0f;
   if constexpr (CP) {
-    const float ax = tx + pc.dtdx * vx, az = tz + pc.dtdz * vz;
+    const float ax = tx + pc.dtdx * vx, az = ozs + pc.dtdz * vz;   // z in the drifting frame
     int sx = (int)floorf(ax), sz = (int)floorf(az);
     float rx = ax - (float)sx, rz = az - (float)sz;
     if (rx >= 1.0f) { rx = 0.0f; sx++; }
     if (rz >= 1.0f) { rz = 0.0f; sz++; }
-    fxn = fx + sx; fzn = fz + sz; txn = rx; tzn = rz;
+    fxn = fx + sx; txn = rx;
+    csn = pack_cell(fxn, (cell_z(cs0) + sz) & 0xffff);
+    ozn = rz;
+    frame_z(csn, ozn, pc.fr1_sz, pc.fr1_fz, fzn, tzn);
   } else {
     xn = x + pc.dt * (double)vx;
     zn = z + pc.dt * (double)vz;
@@ -293,7 +323,7 @@ __device__ __forceinline__ void push_one(const T* __restrict__ Eb, const T* __re
   }
   bool gone;
   if constexpr (CP) {
-    p.cell[pi] = pack_cell(fxn, fzn); p.ox[pi] = txn; p.oz[pi] = tzn;
+    p.cell[pi] = csn; p.ox[pi] = txn; p.oz[pi] = ozn;
     gone = fxn < pc.cx_lo || fxn >= pc.cx_hi || fzn < pc.cz_lo || fzn >= pc.cz_hi;
   } else {
     p.x[pi] = xn; p.z[pi] = zn;
@@ -313,7 +343,9 @@ template <class T>
 __device__ __forceinline__ bool particle_cell(const Particles<T>& p, int pi, const PushConst& pc, int& fx, int& fz) {
   if constexpr (CellPos<T>::value) {
     const uint32_t c = p.cell[pi];
-    fx = cell_x(c); fz = cell_z(c);
+    float tz;
+    fx = cell_x(c);
+    frame_z(c, p.oz[pi], pc.fr0_sz, pc.fr0_fz, fz, tz);
     return true;
   } else {
     const double X = p.x[pi] / pc.dx, Z = (p.z[pi] - pc.z0) / pc.dz;
@@ -498,7 +530,9 @@ __global__ void k_sort_key(GridP g, Particles<T> p, SortBufs sb, const Ctrl* ctr
   if (p.w[i] == T(0)) { sb.key[i] = -1; return; }
   int cx, cz;
   if constexpr (CellPos<T>::value) {
-    cx = cell_x(p.cell[i]); cz = cell_z(p.cell[i]);
+    float tz;
+    cx = cell_x(p.cell[i]);
+    frame_z(p.cell[i], p.oz[i], g.fr_sz, g.fr_fz, cz, tz);
   } else {
     cx = (int)floor(p.x[i] / g.dx);
     cz = (int)floor((p.z[i] - g.z0) / g.dz);
@@ -658,11 +692,12 @@ __global__ void k_inject(GridP g, Particles<T> p, Chunk* chunks, Ctrl* ctrl, Inj
     const double n = ip.gamma * lab_density(ip, ip.gamma * zlat);
     const double zp = zlat - ip.beta * kC * ip.t;
     if constexpr (CellPos<T>::value) {
-      const double Zr = (zp - g.z0) / gdz;
-      int iz = (int)floor(Zr);
-      float oz = (float)(Zr - iz);
+      // drifting frame: grid z + beta c t / dz, i.e. the row's lattice position
+      const double Zc = (zlat - g.z0) / gdz;
+      long long iz = (long long)floor(Zc);
+      float oz = (float)(Zc - (double)iz);
       if (oz >= 1.0f) { oz = 0.0f; iz++; }
-      p.cell[o] = pack_cell(g.gx_lo + (int)(a / ip.ppc_x), iz);
+      p.cell[o] = pack_cell(g.gx_lo + (int)(a / ip.ppc_x), (int)(iz & 0xffff));
       p.ox[o] = (float)(((a % ip.ppc_x) + 0.5) / ip.ppc_x);
       p.oz[o] = oz;
     } else {
@@ -670,7 +705,8 @@ __global__ void k_inject(GridP g, Particles<T> p, Chunk* chunks, Ctrl* ctrl, Inj
       p.z[o] = zp;
     }
     p.ux[o] = T(0); p.uy[o] = T(0);
-    p.uz[o] = T(-ip.gamma * ip.beta * kC);
+    // mixed path: the deviation from the drift momentum, which it starts at
+    p.uz[o] = CellPos<T>::value ? T(0) : T(-ip.gamma * ip.beta * kC);
     p.w[o] = T(n * g.dx * gdz / (double)(ip.ppc_x * ip.ppc_z));
     p.id[o] = (uint32_t)((unsigned long long)m * (unsigned long long)ip.nxl + (unsigned long long)a);
   }
@@ -696,7 +732,8 @@ __global__ void k_add_counts(Ctrl* ctrl, int dcount, int dchunks) {
 
 template <class T>
 void launch_push(const GridP& g, const FieldPtrs<T>& f, Particles<T> p, Chunk* chunks, Ctrl* ctrl, int order,
-                 int grid_blocks, int smem_nodes, double q, double m, cudaStream_t s) {
+                 int grid_blocks, int smem_nodes, double q, double m, double gamma_b, double beta_b, int fr1_sz,
+                 float fr1_fz, cudaStream_t s) {
   PushConst pc;
   pc.dx = g.dx; pc.dz = g.dz; pc.dt = g.dt; pc.z0 = g.z0;
   pc.xlo = g.gx_lo * g.dx; pc.xhi = g.gx_hi * g.dx;
@@ -706,6 +743,11 @@ void launch_push(const GridP& g, const FieldPtrs<T>& f, Particles<T> p, Chunk* c
   pc.qm_half = q * g.dt / (2.0 * m);
   pc.kx = -q / (g.dz * g.dt); pc.kz = -q / (g.dx * g.dt); pc.ky = q / (g.dx * g.dz);
   pc.qm_half_f = (float)pc.qm_half; pc.kx_f = (float)pc.kx; pc.kz_f = (float)pc.kz; pc.ky_f = (float)pc.ky;
+  pc.u0z_f = g.fr_u0;
+  pc.g0_f = (float)gamma_b;
+  pc.g0sq_f = (float)(1.0 + (double)g.fr_u0 * (double)g.fr_u0 / (kC * kC));
+  pc.fr0_sz = g.fr_sz; pc.fr0_fz = g.fr_fz;
+  pc.fr1_sz = fr1_sz; pc.fr1_fz = fr1_fz;
   const size_t sm = (size_t)9 * smem_nodes * sizeof(T);
   cudaMemsetAsync(&ctrl->next_chunk, 0, sizeof(int), s);
   if (order == 3) {
@@ -783,7 +825,7 @@ void launch_add_counts(Ctrl* ctrl, int dcount, int dchunks, cudaStream_t s) {
 
 #define INST(T)                                                                                                 \
   template void launch_push<T>(const GridP&, const FieldPtrs<T>&, Particles<T>, Chunk*, Ctrl*, int, int, int,   \
-                               double, double, cudaStream_t);                                                   \
+                               double, double, double, double, int, float, cudaStream_t);                       \
   template void launch_sort<T>(const GridP&, Particles<T>, Particles<T>, SortBufs, Chunk*, Ctrl*, int, int, int,\
                                cudaStream_t);                                                                   \
   template void launch_inject<T>(const GridP&, Particles<T>, Chunk*, Ctrl*, const InjectP&, int, int, cudaStream_t);
