@@ -38,6 +38,11 @@ if ROOT not in sys.path:
 BYTES_PER_PARTICLE = {"mixed": 60, "fp64": 88}
 # algorithmic bytes per cell-step of the field kernels (mixed, with Friedman): see the design notes
 BYTES_PER_CELL = {"mixed": 168, "fp64": 336}
+# measured DRAM bytes (read + write) per particle of one push launch, mixed precision, cubic shapes:
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of k_push on the 2048 x 256 stage box
+# (profiles/k_push_stage2d_2048x256_mixed.md: 322.76 MB for 6,487,608 electrons), scaled to the
+# full box by its particle count; None for configurations not captured
+TRAFFIC_BYTES_PER_PARTICLE = {("mixed", 3): 49.75}
 
 
 def measured_peaks() -> dict:
@@ -259,8 +264,12 @@ def main():
     bpp = BYTES_PER_PARTICLE[args.precision]
     push_avg_ms = push_ms / max(push_n, 1)
     achieved = n_avg * bpp / (push_avg_ms * 1e-3) / 1e9
+    tpp = TRAFFIC_BYTES_PER_PARTICLE.get((args.precision, args.order))
     roof = {"kernel": "k_push (gather + Boris + Esirkepov)", "bound": "hbm", "achieved": achieved, "peak": peak,
-            "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+            "unit": "GB/s", "frac": achieved / peak, "traffic": tpp * n_avg if tpp else None,
+            "traffic_source": "ncu dram bytes of k_push, 2048 x 256 box, scaled by particles" if tpp else None,
+            "note": "at cubic order the push is bound by instruction issue and the shared-memory pipe "
+                    "(ncu: 63% issue slots, 71% L1/shared, 14% DRAM), not by HBM",
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback",
             "algorithmic_bytes_per_particle": bpp, "push_ms_per_step": push_avg_ms,
             "share_of_step": push_avg_ms / (ms / args.steps)}
