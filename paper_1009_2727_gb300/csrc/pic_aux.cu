@@ -285,7 +285,7 @@ __global__ void k_rho(GridP g, Particles<T> p, const Ctrl* ctrl, int order, doub
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= ctrl->count) return;
   const double w = (double)p.w[j];
-  if (w == 0.0) return;
+  if (!(w > 0.0)) return;   // ghosts (negative weight) are ions, counted by the ion charge density
   double X, Z;
   if constexpr (CellPos<T>::value) {
     int iz;
@@ -319,7 +319,7 @@ __global__ void k_stats(GridP g, FieldPtrs<T> f, Particles<T> p, const Ctrl* ctr
   const long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const long nthr = (long)gridDim.x * blockDim.x;
   double ne = 0, na = 0, sg = 0, sg2 = 0, en = 0;
-  for (long j = tid; j < ctrl->count; j += nthr) ne += p.w[j] != T(0) ? 1.0 : 0.0;
+  for (long j = tid; j < ctrl->count; j += nthr) ne += p.w[j] > T(0) ? 1.0 : 0.0;
   for (long j = tid; j < b.n; j += nthr) {
     if ((b.flag[j] & 3) != 3) continue;
     const double ux = b.ux[j], uy = b.uy[j], uz = b.uz[j];
@@ -382,7 +382,7 @@ __global__ void k_compact(GridP g, Particles<T> p, const Ctrl* ctrl, double* out
                           int cap_out) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= ctrl->count) return;
-  if (p.w[j] == T(0)) return;
+  if (!(p.w[j] > T(0))) return;   // electrons only (ghosts carry ions)
   const int o = atomicAdd(nout, 1);
   if (o >= cap_out) return;
   if constexpr (CellPos<T>::value) {
@@ -399,7 +399,13 @@ __global__ void k_compact(GridP g, Particles<T> p, const Ctrl* ctrl, double* out
   out6[3 * (size_t)cap_out + o] = p.uy[j];
   out6[4 * (size_t)cap_out + o] = CellPos<T>::value ? (double)g.fr_u0 + (double)p.uz[j] : (double)p.uz[j];
   out6[5 * (size_t)cap_out + o] = p.w[j];
-  ido[o] = p.id[j];
+  if constexpr (CellPos<T>::value) {
+    // stored (row << kb) | column -> row * nxl + column
+    const uint32_t id = p.id[j];
+    ido[o] = (id >> g.il_kb) * (uint32_t)g.il_nxl + (id & ((1u << g.il_kb) - 1u));
+  } else {
+    ido[o] = p.id[j];
+  }
 }
 
 // moving window: the stored cells of the mixed path move with the grid
@@ -411,6 +417,16 @@ __global__ void k_shift_particles(GridP g, Particles<T> p, const Ctrl* ctrl, int
   const uint32_t c = p.cell[j];
   int iz;
   float tz;
+  if (p.w[j] < T(0)) {   // ghost: its lab-fixed ion (g.z0_cells is the origin before this shift)
+    uint32_t cs;
+    float ox, oz;
+    const uint32_t id = p.id[j];
+    lattice_site((int)(id >> g.il_kb), (int)(id & ((1u << g.il_kb) - 1u)), g.il_ppcx, g.il_ppcz, g.gx_lo,
+                 g.z0_cells, cs, ox, oz);
+    frame_z(cs, oz, g.fr_sz, g.fr_fz, iz, tz);
+    if (iz - sh < 0) p.w[j] = T(0);
+    return;
+  }
   frame_z(c, p.oz[j], g.fr_sz, g.fr_fz, iz, tz);
   if (iz - sh < 0) { p.w[j] = T(0); return; }
   p.cell[j] = pack_cell(cell_x(c), (cell_z(c) - sh) & 0xffff);

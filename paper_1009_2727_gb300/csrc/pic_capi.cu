@@ -122,6 +122,7 @@ struct Sim : SimBase {
   pic_plasma pl{};
   InjectP ip{};
   long long row_next = 0, row_first = 0;
+  bool pairs = false;        // mixed path: electrons carry the ions of their lattice sites
   double zlo_prev = 0.0;
   // ions
   bool ions = false;
@@ -171,6 +172,7 @@ struct Sim : SimBase {
     g.pml = cf.pml_cells;
     g.fr_sz = 0; g.fr_fz = 0.0f;
     g.fr_u0 = (float)(-h.gamma * h.beta * kC);
+    g.il_nxl = 0; g.il_ppcx = 1; g.il_ppcz = 1; g.il_kb = 0; g.z0_cells = 0;
     friedman = cf.theta != 0.0;
     filt_gather = cf.filter_gather && cf.filter_passes + cf.filter_compensate > 0;
     filt_J = cf.filter_J && cf.filter_passes + cf.filter_compensate > 0;
@@ -287,6 +289,12 @@ struct Sim : SimBase {
   long long rows_from(double t) const {
     return (long long)std::ceil((zlo() + c->hg.beta * kC * t) / ip.h - 0.5);
   }
+  // particle ids of rows [a, b): row * nxl + column (FP64 path) or (row << kb) | column (mixed)
+  bool ids_fit(long long a, long long b) const {
+    if (a < 0) return false;
+    if (CellPos<T>::value) return b <= (1LL << (32 - g.il_kb));
+    return b * (long long)ip.nxl <= (1LL << 32);
+  }
   bool row_has_density(long long m) const {
     double zlat = (m + 0.5) * ip.h;
     return c->hg.gamma * lab_density_h(pl, c->hg.gamma * zlat) > 0.0;
@@ -304,6 +312,15 @@ struct Sim : SimBase {
     ip.n0 = pl.n0; ip.z_start_lab = pl.z_start_lab; ip.ramp_lab = pl.ramp_lab; ip.length_lab = pl.length_lab;
     ip.ppc_x = pl.ppc_x; ip.ppc_z = pl.ppc_z;
     ip.nxl = (g.gx_hi - g.gx_lo) * pl.ppc_x;
+    g.il_nxl = ip.nxl; g.il_ppcx = pl.ppc_x; g.il_ppcz = pl.ppc_z;
+    g.il_kb = 0;
+    while ((1LL << g.il_kb) < ip.nxl) g.il_kb++;
+    // the mixed path lets every electron carry the lab-fixed ion of its lattice site
+    // (power-of-two particles per cell: the site follows from the id by shifts)
+    {
+      auto pow2 = [](int v) { return v > 0 && (v & (v - 1)) == 0; };
+      pairs = CellPos<T>::value && pl.ions != 0 && pl.n0 > 0.0 && pow2(pl.ppc_x) && pow2(pl.ppc_z);
+    }
     ip.xblock = 32;
     ions = pl.ions != 0 && pl.n0 > 0.0;
     // capacity: the particle domain full of plasma plus injection headroom
@@ -375,6 +392,7 @@ struct Sim : SimBase {
       while (a < b && !row_has_density(a)) a++;
       while (b > a && !row_has_density(b - 1)) b--;
       if (b > a) {
+        if (!ids_fit(a, b)) return c->fail(PIC_EOVERFLOW, "plasma rows exceed the 32-bit particle id space");
         ip.m_beg = a; ip.m_end = b; ip.t = t; ip.rblock = 8;
         if ((b - a) * (long long)ip.nxl > cap) return c->fail(PIC_EOVERFLOW, "initial plasma exceeds capacity");
         launch_inject<T>(g, P, chunks, ctrl, ip, cap, chunk_cap, c->stream);
@@ -515,6 +533,7 @@ struct Sim : SimBase {
     }
     shifts = want;
     g.z0 = (double)want * g.dz;
+    g.z0_cells = (int)want;
   }
 
   void refresh_count_bound(long long add) {
@@ -562,6 +581,9 @@ struct Sim : SimBase {
     launch_filter_fields<T>(g, f, fs, filt_gather, tmaps, ctrl, c->stream);
     tstop(1);
     c->launches += 1 + (filt_gather ? 1 : 0);
+    // ion rows live during this step: those inside the particle domain at t^n
+    long long mlo = std::max(row_first, (long long)std::ceil((zlo_prev + h.beta * kC * tn) / ip.h - 0.5));
+    if (step == 0) mlo = row_first;
     // 3. particles
     if (loaded && cap > 0) {
       tstart(0);
@@ -569,7 +591,7 @@ struct Sim : SimBase {
       float fr1_fz;
       frame_of(frame_shift(step + 1), fr1_sz, fr1_fz);
       launch_push<T>(g, f, P, chunks, ctrl, cf.shape_order, push_grid, smem_nodes, -kQe, kMe, c->hg.gamma, c->hg.beta,
-                     fr1_sz, fr1_fz, c->stream);
+                     fr1_sz, fr1_fz, (pairs && ions) ? 1 : 0, (int)mlo, c->stream);
       tstop(0);
       c->launches++;
     }
@@ -584,18 +606,17 @@ struct Sim : SimBase {
       launch_antenna<T>(g, f.J[1], ant_xs, ast, c->stream);
       c->launches++;
     }
-    // 5. ion column current
+    // 5. ion column current (unless every electron carries its ion)
     double ion_coef = 0.0;
-    if (ions && loaded) {
-      long long mlo = std::max(row_first, (long long)std::ceil((zlo_prev + h.beta * kC * tn) / ip.h - 0.5));
-      if (step == 0) mlo = row_first;
+    const bool column = ions && loaded && !pairs;
+    if (column) {
       launch_ion_column(g, mlo, row_next, tn, tn1, ip, cf.shape_order, ion_C, c->stream);
       c->launches += 1;
       ion_coef = -kQe / (g.dx * g.dt);
     }
     // 6-7. current filter + Ampere + PML-E
     tstart(1);
-    launch_ampere<T>(g, f, pt, fs, filt_J, (ions && loaded) ? ion_x : nullptr, ion_C, ion_coef, tmaps, ctrl, c->stream);
+    launch_ampere<T>(g, f, pt, fs, filt_J, column ? ion_x : nullptr, ion_C, ion_coef, tmaps, ctrl, c->stream);
     tstop(1);
     c->launches++;
     for (int q = 0; q < 3; q++) {
@@ -617,6 +638,7 @@ struct Sim : SimBase {
         long long add = (b - a) * (long long)ip.nxl;
         refresh_count_bound(add);
         if (count_ub + add > cap) return c->fail(PIC_EOVERFLOW, "particle capacity exceeded");
+        if (!ids_fit(a, b)) return c->fail(PIC_EOVERFLOW, "plasma rows exceed the 32-bit particle id space");
         ip.m_beg = a; ip.m_end = b; ip.t = tn1; ip.rblock = 4;
         launch_inject<T>(g, P, chunks, ctrl, ip, cap, chunk_cap, c->stream);
         c->launches += 2;

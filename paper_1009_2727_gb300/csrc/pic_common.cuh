@@ -36,6 +36,11 @@ struct GridP {
   // mixed path: u_z is stored as u_z - fr_u0, fr_u0 = -gamma beta c (FP32), the
   // plasma drift momentum, so that its changes keep FP32 precision
   float fr_u0;
+  // mixed path: the plasma lattice (rows of il_nxl particles, il_ppcx x il_ppcz
+  // per cell); the stored particle id is (row << il_kb) | column; the grid
+  // origin in cells (moving window shifts)
+  int il_nxl, il_ppcx, il_ppcz, il_kb;
+  int z0_cells;
 };
 
 // Valid index range of each E/B component (PEC walls); J uses the E ranges.
@@ -129,6 +134,28 @@ __host__ __device__ inline void frame_z(uint32_t c, float oz, int sz, float fz, 
   tz = t;
 }
 
+// Lattice site (row m, column a) of a plasma particle: the stored cell and
+// offsets (z in the drifting frame) that the particle gets at injection, and
+// that its lab-fixed ion keeps for ever (row m at z = (m + 1/2) dz / ppcz).
+// Integer arithmetic and FP32 divisions of small integers: for power-of-two
+// ppcx, ppcz these are exact, so lattice_site_pow2 (shifts) gives the same bits.
+__host__ __device__ inline void lattice_site(int m, int a, int ppcx, int ppcz, int gx_lo, int z0_cells,
+                                             uint32_t& cell, float& ox, float& oz) {
+  const int n2 = 2 * m + 1, d2 = 2 * ppcz;
+  cell = pack_cell(gx_lo + a / ppcx, (n2 / d2 - z0_cells) & 0xffff);
+  oz = (float)(n2 % d2) / (float)d2;
+  ox = ((float)(a % ppcx) + 0.5f) / (float)ppcx;
+}
+// the same for ppcx = 2^lpx, ppcz = 2^lpz, from the stored id (row << kb) | column
+__host__ __device__ inline void lattice_site_pow2(uint32_t id, int kb, int lpx, int lpz, int gx_lo, int z0_cells,
+                                                  uint32_t& cell, float& ox, float& oz) {
+  const int m = (int)(id >> kb), a = (int)(id & ((1u << kb) - 1u));
+  const int n2 = 2 * m + 1;
+  cell = pack_cell(gx_lo + (a >> lpx), ((n2 >> (lpz + 1)) - z0_cells) & 0xffff);
+  oz = (float)(n2 & ((2 << lpz) - 1)) * (1.0f / (float)(2 << lpz));
+  ox = ((float)(a & ((1 << lpx) - 1)) + 0.5f) * (1.0f / (float)(1 << lpx));
+}
+
 // frame shift S (cells, FP64) -> (S mod 2^16 integer part, FP32 fraction)
 inline void frame_of(double S, int& sz, float& fz) {
   const double fl = __builtin_floor(S);
@@ -196,7 +223,7 @@ void launch_ampere(const GridP& g, const FieldPtrs<T>& f, const PmlTabs& pt, con
 template <class T>
 void launch_push(const GridP& g, const FieldPtrs<T>& f, Particles<T> p, Chunk* chunks, Ctrl* ctrl, int order,
                  int grid_blocks, int smem_nodes, double q, double m, double gamma_b, double beta_b, int fr1_sz,
-                 float fr1_fz, cudaStream_t s);
+                 float fr1_fz, int pairs, int mlo, cudaStream_t s);
 
 struct SortBufs {
   int* cell_cnt;       // ntiles*tx*tz, cells in tile-major order: particles per cell

@@ -108,7 +108,39 @@ struct PushConst {
   float u0z_f, g0_f, g0sq_f;
   int fr0_sz, fr1_sz;
   float fr0_fz, fr1_fz;
+  // mixed path with lab-fixed ions: each electron carries the ion of its lattice
+  // site (pairs; power-of-two particles per cell); ion rows below mlo have left
+  // the particle domain; the stored id is (row << kb) | column
+  int pairs, mlo;
+  int kb, lpx, lpz, gx_lo, z0_cells;
 };
+
+// products and differences rounded on their own (no contraction into FMA)
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+
+// Lab-fixed ion of a lattice site (mixed path): its stored cell and offsets,
+// grid cells at t^n and t^{n+1}, and the shape weights of its Esirkepov J_z on
+// the window starting at (bx, bz) (bx, bz are set when set_window).
+template <int ORDER>
+struct IonSite {
+  uint32_t cell;
+  float ox, oz;
+  int fx, fz0, fz1;
+  float tz0, tz1;
+};
+
+__device__ __forceinline__ int site_row(uint32_t id, const PushConst& pc) { return (int)(id >> pc.kb); }
+
+template <int ORDER>
+__device__ __forceinline__ void ion_site(uint32_t id, const PushConst& pc, IonSite<ORDER>& s) {
+  lattice_site_pow2(id, pc.kb, pc.lpx, pc.lpz, pc.gx_lo, pc.z0_cells, s.cell, s.ox, s.oz);
+  s.fx = cell_x(s.cell);
+  frame_z(s.cell, s.oz, pc.fr0_sz, pc.fr0_fz, s.fz0, s.tz0);
+  frame_z(s.cell, s.oz, pc.fr1_sz, pc.fr1_fz, s.fz1, s.tz1);
+}
 
 // Esirkepov current of one particle on an NDX (x) by ND (z) window whose first
 // node is Jx (Jy, Jz follow at component stride cs). The weights factorise:
@@ -116,19 +148,29 @@ struct PushConst {
 // (likewise Jz), and Wy = S0z (S0x + DSx/2) + DSz (S0x/2 + DSx/3). Zero
 // contributions are skipped (a slot that is zero on every lane of a warp costs
 // no shared-memory wavefront).
+//
+// JZ: 0 = no J_z, 1 = the particle's J_z, 2 = the particle's J_z minus that of a
+// particle with x weights Sxi and z weight change DSzi on the same window (the
+// electron and its lattice ion): the two are combined before the atomic, with
+// separately rounded products, so that the large streaming currents cancel in
+// registers instead of in the accumulated current.
 template <class T, int ND, int NDX, bool SMEM>
 __device__ __forceinline__ void deposit(T* Jx, long cs, int ld, const T* S0x, const T* DSx, const T* S0z, const T* DSz,
-                                        T cx, T cy, T cz) {
+                                        T cx, T cy, T cz, int JZ = 1, const T* Sxi = nullptr,
+                                        const T* DSzi = nullptr) {
   typedef typename std::conditional<SMEM, int, long>::type Idx;
   T* Jy = Jx + cs;
   T* Jz = Jx + 2 * cs;
-  T Px[NDX - 1], Pz[ND - 1];
+  T Px[NDX - 1], Pz[ND - 1], Pzi[ND - 1];
   {
-    T ax = T(0), az = T(0);
+    T ax = T(0), az = T(0), ai = T(0);
 #pragma unroll
     for (int a = 0; a < NDX - 1; a++) { ax += cx * DSx[a]; Px[a] = ax; }
 #pragma unroll
-    for (int b = 0; b < ND - 1; b++) { az += cz * DSz[b]; Pz[b] = az; }
+    for (int b = 0; b < ND - 1; b++) {
+      az += cz * DSz[b]; Pz[b] = az;
+      if (JZ == 2) { ai += cz * DSzi[b]; Pzi[b] = ai; }
+    }
   }
 #pragma unroll
   for (int b = 0; b < ND; b++) {
@@ -139,13 +181,17 @@ __device__ __forceinline__ void deposit(T* Jx, long cs, int ld, const T* S0x, co
       if (v != T(0)) atomicAdd(Jx + (Idx)a * ld + b, v);
     }
   }
+  if (JZ != 0) {
 #pragma unroll
-  for (int a = 0; a < NDX; a++) {
-    const T fxa = S0x[a] + T(0.5) * DSx[a];
+    for (int a = 0; a < NDX; a++) {
+      const T fxa = S0x[a] + T(0.5) * DSx[a];
 #pragma unroll
-    for (int b = 0; b < ND - 1; b++) {
-      const T v = fxa * Pz[b];
-      if (v != T(0)) atomicAdd(Jz + (Idx)a * ld + b, v);
+      for (int b = 0; b < ND - 1; b++) {
+        T v;
+        if (JZ == 2) v = sub_rn(mul_rn(fxa, Pz[b]), mul_rn(Sxi[a], Pzi[b]));
+        else v = fxa * Pz[b];
+        if (v != T(0)) atomicAdd(Jz + (Idx)a * ld + b, v);
+      }
     }
   }
   if (cy != T(0)) {
@@ -162,6 +208,36 @@ __device__ __forceinline__ void deposit(T* Jx, long cs, int ld, const T* S0x, co
   }
 }
 
+// J_z of a lab-fixed ion alone (its electron has left, or their windows
+// differ): the electron formula with the same weight and the opposite charge
+template <class T, int ORDER, bool SMEM>
+__device__ __forceinline__ void ion_jz(T* Jb, long cs, int ld, int ox, int oz, const IonSite<ORDER>& s, T cz) {
+  constexpr int NG = St<ORDER>::NG, ND = St<ORDER>::ND;
+  typedef typename std::conditional<SMEM, int, long>::type Idx;
+  const int off = ORDER == 3 ? 1 : 0;
+  T wx[NG], w0[NG], w1[NG];
+  wts<T, ORDER>(T(s.ox), wx);
+  wts<T, ORDER>(T(s.tz0), w0);
+  wts<T, ORDER>(T(s.tz1), w1);
+  const int bx = s.fx - off, bz = min(s.fz0, s.fz1) - off;
+  T S0z[ND], S1z[ND];
+  place<T, ORDER>(w0, s.fz0 - off - bz, S0z);
+  place<T, ORDER>(w1, s.fz1 - off - bz, S1z);
+  T* Jz = Jb + 2 * cs + (Idx)(bx - ox) * ld + (bz - oz);
+  T Pz[ND - 1];
+  T az = T(0);
+#pragma unroll
+  for (int b = 0; b < ND - 1; b++) { az += cz * (S1z[b] - S0z[b]); Pz[b] = az; }
+#pragma unroll
+  for (int a = 0; a < NG; a++) {
+#pragma unroll
+    for (int b = 0; b < ND - 1; b++) {
+      const T v = -(wx[a] * Pz[b]);
+      if (v != T(0)) atomicAdd(Jz + (Idx)a * ld + b, v);
+    }
+  }
+}
+
 // One particle: gather -> Boris -> move -> Esirkepov. E/B/J are 3-component
 // blocks (component stride cs) addressed as (i - ox)*ld + (k - oz). With SMEM
 // the fields are the shared-memory window: pairs (Ex, Bz) and (Ez, Bx), which
@@ -174,6 +250,20 @@ __device__ __forceinline__ void push_one(const T* __restrict__ Eb, const T* __re
   constexpr bool CP = CellPos<T>::value;
   const T w = p.w[pi];
   if (w == T(0)) return;
+  if constexpr (CP) {
+    if (w < T(0)) {
+      // ghost: the lab-fixed ion of an electron that has left the domain; it
+      // deposits its J_z until its lattice row leaves too
+      const uint32_t id = p.id[pi];
+      if (site_row(id, pc) < pc.mlo) { p.w[pi] = T(0); return; }
+      IonSite<ORDER> is;
+      ion_site<ORDER>(id, pc, is);
+      ion_jz<T, ORDER, SMEM>(Jb, cs, ld, ox, oz, is, pc.kz_f * (-w));
+      bx0 = min(bx0, is.fx); bx1 = max(bx1, is.fx);
+      bz0 = min(bz0, is.fz1); bz1 = max(bz1, is.fz1);
+      return;
+    }
+  }
   int fx, fz, fxh, fzh;
   T tx, tz, txh, tzh;
   double x = 0.0, z = 0.0, X = 0.0, Z = 0.0;
@@ -309,17 +399,52 @@ __device__ __forceinline__ void push_one(const T* __restrict__ Eb, const T* __re
   } else {
     cx = T(pc.kx) * w; cz = T(pc.kz) * w; cy = T(pc.ky) * w * vy;
   }
+  // the lab-fixed ion of the particle's lattice site (mixed path): J_z of the
+  // pair is exactly zero when electron and ion made the same move (the cold
+  // streaming plasma); otherwise combined on a common window, or separate
+  int jz = 1;
+  bool ion_live = false, ion_sep = false;
+  IonSite<ORDER> is;
+  T Sxi[ND], DSzi[ND];
+  if constexpr (CP) {
+    if (pc.pairs) {
+      const uint32_t id = p.id[pi];
+      ion_live = site_row(id, pc) >= pc.mlo;
+      if (ion_live) {
+        ion_site<ORDER>(id, pc, is);
+        if (cs0 == is.cell && ozs == is.oz && tx == is.ox && csn == is.cell && ozn == is.oz && txn == is.ox) {
+          jz = 0;
+        } else if (is.fx - off == bx && min(is.fz0, is.fz1) - off == bz) {
+          jz = 2;
+          T wxi2[NG], w0i[NG], w1i[NG], S0zi[ND], S1zi[ND];
+          wts<T, ORDER>(T(is.ox), wxi2);
+          wts<T, ORDER>(T(is.tz0), w0i);
+          wts<T, ORDER>(T(is.tz1), w1i);
+          place<T, ORDER>(wxi2, 0, Sxi);
+          place<T, ORDER>(w0i, is.fz0 - off - bz, S0zi);
+          place<T, ORDER>(w1i, is.fz1 - off - bz, S1zi);
+#pragma unroll
+          for (int b = 0; b < ND; b++) DSzi[b] = S1zi[b] - S0zi[b];
+        } else {
+          ion_sep = true;
+        }
+      }
+    }
+  }
   T* Jx = Jb + (long)(bx - ox) * ld + (bz - oz);
   if constexpr (SMEM) {
     // when no lane of the warp changes x-cell, column ND-1 of the x window is
     // empty: the warp deposits on ND-1 columns
     const bool xcross = fxn != fx;
     if (__any_sync(__activemask(), xcross))
-      deposit<T, ND, ND, true>(Jx, cs, ld, S0x, DSx, S0z, DSz, cx, cy, cz);
+      deposit<T, ND, ND, true>(Jx, cs, ld, S0x, DSx, S0z, DSz, cx, cy, cz, jz, Sxi, DSzi);
     else
-      deposit<T, ND, ND - 1, true>(Jx, cs, ld, S0x, DSx, S0z, DSz, cx, cy, cz);
+      deposit<T, ND, ND - 1, true>(Jx, cs, ld, S0x, DSx, S0z, DSz, cx, cy, cz, jz, Sxi, DSzi);
   } else {
-    deposit<T, ND, ND, false>(Jx, cs, ld, S0x, DSx, S0z, DSz, cx, cy, cz);
+    deposit<T, ND, ND, false>(Jx, cs, ld, S0x, DSx, S0z, DSz, cx, cy, cz, jz, Sxi, DSzi);
+  }
+  if constexpr (CP) {
+    if (ion_sep) ion_jz<T, ORDER, SMEM>(Jb, cs, ld, ox, oz, is, cz);
   }
   bool gone;
   if constexpr (CP) {
@@ -331,7 +456,12 @@ __device__ __forceinline__ void push_one(const T* __restrict__ Eb, const T* __re
   }
   p.ux[pi] = ux; p.uy[pi] = uy; p.uz[pi] = uz;
   if (gone) {
-    p.w[pi] = T(0);
+    // an electron whose ion is still inside leaves a ghost that carries the ion
+    p.w[pi] = ion_live ? -w : T(0);
+    if (ion_live) {
+      bx0 = min(bx0, is.fx); bx1 = max(bx1, is.fx);
+      bz0 = min(bz0, is.fz1); bz1 = max(bz1, is.fz1);
+    }
   } else {
     bx0 = min(bx0, fxn); bx1 = max(bx1, fxn);
     bz0 = min(bz0, fzn); bz1 = max(bz1, fzn);
@@ -342,10 +472,11 @@ __device__ __forceinline__ void push_one(const T* __restrict__ Eb, const T* __re
 template <class T>
 __device__ __forceinline__ bool particle_cell(const Particles<T>& p, int pi, const PushConst& pc, int& fx, int& fz) {
   if constexpr (CellPos<T>::value) {
-    const uint32_t c = p.cell[pi];
-    float tz;
+    uint32_t c = p.cell[pi];
+    float oz = p.oz[pi], ox, tz;
+    if (p.w[pi] < T(0)) lattice_site_pow2(p.id[pi], pc.kb, pc.lpx, pc.lpz, pc.gx_lo, pc.z0_cells, c, ox, oz);
     fx = cell_x(c);
-    frame_z(c, p.oz[pi], pc.fr0_sz, pc.fr0_fz, fz, tz);
+    frame_z(c, oz, pc.fr0_sz, pc.fr0_fz, fz, tz);
     return true;
   } else {
     const double X = p.x[pi] / pc.dx, Z = (p.z[pi] - pc.z0) / pc.dz;
@@ -444,7 +575,19 @@ __global__ void __launch_bounds__(PB_THREADS, 4) k_push(GridP g, const T* gE, co
         // a particle outside the chunk's box (should not happen) takes the global path
         int fx = 0, fz = 0;
         const bool fin = particle_cell<T>(p, pi, pc, fx, fz);
-        if (fin && fx >= ch.ix0 && fx <= ch.ix1 && fz >= ch.iz0 && fz <= ch.iz1)
+        bool inbox = fin && fx >= ch.ix0 && fx <= ch.ix1 && fz >= ch.iz0 && fz <= ch.iz1;
+        if constexpr (CellPos<T>::value) {
+          // a live pair deposits its ion too: the ion's cell must be inside the box as well
+          if (inbox && pc.pairs && p.w[pi] > T(0) && site_row(p.id[pi], pc) >= pc.mlo) {
+            uint32_t c;
+            float sox, soz, tz;
+            int iz;
+            lattice_site_pow2(p.id[pi], pc.kb, pc.lpx, pc.lpz, pc.gx_lo, pc.z0_cells, c, sox, soz);
+            frame_z(c, soz, pc.fr0_sz, pc.fr0_fz, iz, tz);
+            inbox = cell_x(c) >= ch.ix0 && cell_x(c) <= ch.ix1 && iz >= ch.iz0 && iz <= ch.iz1;
+          }
+        }
+        if (inbox)
           push_one<T, ORDER, true>(sm, nullptr, sm + 6 * cap_nodes, cap_nodes, lds, wx0, wz0, p, pi, pc, bx0, bx1,
                                    bz0, bz1);
         else
@@ -530,9 +673,15 @@ __global__ void k_sort_key(GridP g, Particles<T> p, SortBufs sb, const Ctrl* ctr
   if (p.w[i] == T(0)) { sb.key[i] = -1; return; }
   int cx, cz;
   if constexpr (CellPos<T>::value) {
-    float tz;
-    cx = cell_x(p.cell[i]);
-    frame_z(p.cell[i], p.oz[i], g.fr_sz, g.fr_fz, cz, tz);
+    uint32_t c = p.cell[i];
+    float oz = p.oz[i], ox, tz;
+    if (p.w[i] < T(0)) {   // ghost: its lab-fixed ion
+      const uint32_t id = p.id[i];
+      lattice_site((int)(id >> g.il_kb), (int)(id & ((1u << g.il_kb) - 1u)), g.il_ppcx, g.il_ppcz, g.gx_lo,
+                   g.z0_cells, c, ox, oz);
+    }
+    cx = cell_x(c);
+    frame_z(c, oz, g.fr_sz, g.fr_fz, cz, tz);
   } else {
     cx = (int)floor(p.x[i] / g.dx);
     cz = (int)floor((p.z[i] - g.z0) / g.dz);
@@ -692,14 +841,13 @@ __global__ void k_inject(GridP g, Particles<T> p, Chunk* chunks, Ctrl* ctrl, Inj
     const double n = ip.gamma * lab_density(ip, ip.gamma * zlat);
     const double zp = zlat - ip.beta * kC * ip.t;
     if constexpr (CellPos<T>::value) {
-      // drifting frame: grid z + beta c t / dz, i.e. the row's lattice position
-      const double Zc = (zlat - g.z0) / gdz;
-      long long iz = (long long)floor(Zc);
-      float oz = (float)(Zc - (double)iz);
-      if (oz >= 1.0f) { oz = 0.0f; iz++; }
-      p.cell[o] = pack_cell(g.gx_lo + (int)(a / ip.ppc_x), (int)(iz & 0xffff));
-      p.ox[o] = (float)(((a % ip.ppc_x) + 0.5) / ip.ppc_x);
-      p.oz[o] = oz;
+      // drifting frame: the row's lattice position (grid z + beta c t / dz)
+      uint32_t c;
+      float sox, soz;
+      lattice_site((int)m, (int)a, ip.ppc_x, ip.ppc_z, g.gx_lo, g.z0_cells, c, sox, soz);
+      p.cell[o] = c;
+      p.ox[o] = sox;
+      p.oz[o] = soz;
     } else {
       p.x[o] = (g.gx_lo + (a + 0.5) / ip.ppc_x) * g.dx;
       p.z[o] = zp;
@@ -708,7 +856,8 @@ __global__ void k_inject(GridP g, Particles<T> p, Chunk* chunks, Ctrl* ctrl, Inj
     // mixed path: the deviation from the drift momentum, which it starts at
     p.uz[o] = CellPos<T>::value ? T(0) : T(-ip.gamma * ip.beta * kC);
     p.w[o] = T(n * g.dx * gdz / (double)(ip.ppc_x * ip.ppc_z));
-    p.id[o] = (uint32_t)((unsigned long long)m * (unsigned long long)ip.nxl + (unsigned long long)a);
+    if constexpr (CellPos<T>::value) p.id[o] = ((uint32_t)m << g.il_kb) | (uint32_t)a;
+    else p.id[o] = (uint32_t)((unsigned long long)m * (unsigned long long)ip.nxl + (unsigned long long)a);
   }
   if (threadIdx.x == 0 && cnt > 0) {
     const int ci = ctrl->nchunks + rb * nxb + xb;
@@ -733,7 +882,7 @@ __global__ void k_add_counts(Ctrl* ctrl, int dcount, int dchunks) {
 template <class T>
 void launch_push(const GridP& g, const FieldPtrs<T>& f, Particles<T> p, Chunk* chunks, Ctrl* ctrl, int order,
                  int grid_blocks, int smem_nodes, double q, double m, double gamma_b, double beta_b, int fr1_sz,
-                 float fr1_fz, cudaStream_t s) {
+                 float fr1_fz, int pairs, int mlo, cudaStream_t s) {
   PushConst pc;
   pc.dx = g.dx; pc.dz = g.dz; pc.dt = g.dt; pc.z0 = g.z0;
   pc.xlo = g.gx_lo * g.dx; pc.xhi = g.gx_hi * g.dx;
@@ -748,6 +897,11 @@ void launch_push(const GridP& g, const FieldPtrs<T>& f, Particles<T> p, Chunk* c
   pc.g0sq_f = (float)(1.0 + (double)g.fr_u0 * (double)g.fr_u0 / (kC * kC));
   pc.fr0_sz = g.fr_sz; pc.fr0_fz = g.fr_fz;
   pc.fr1_sz = fr1_sz; pc.fr1_fz = fr1_fz;
+  pc.pairs = pairs; pc.mlo = mlo;
+  pc.kb = g.il_kb; pc.gx_lo = g.gx_lo; pc.z0_cells = g.z0_cells;
+  pc.lpx = 0; pc.lpz = 0;
+  while ((1 << pc.lpx) < g.il_ppcx) pc.lpx++;
+  while ((1 << pc.lpz) < g.il_ppcz) pc.lpz++;
   const size_t sm = (size_t)9 * smem_nodes * sizeof(T);
   cudaMemsetAsync(&ctrl->next_chunk, 0, sizeof(int), s);
   if (order == 3) {
@@ -825,7 +979,7 @@ void launch_add_counts(Ctrl* ctrl, int dcount, int dchunks, cudaStream_t s) {
 
 #define INST(T)                                                                                                 \
   template void launch_push<T>(const GridP&, const FieldPtrs<T>&, Particles<T>, Chunk*, Ctrl*, int, int, int,   \
-                               double, double, double, double, int, float, cudaStream_t);                       \
+                               double, double, double, double, int, float, int, int, cudaStream_t);             \
   template void launch_sort<T>(const GridP&, Particles<T>, Particles<T>, SortBufs, Chunk*, Ctrl*, int, int, int,\
                                cudaStream_t);                                                                   \
   template void launch_inject<T>(const GridP&, Particles<T>, Chunk*, Ctrl*, const InjectP&, int, int, cudaStream_t);
