@@ -562,3 +562,75 @@ def test_btd_boosted_laser_seen_in_lab(orc):
             cr.append(t[j] + (t[j + 1] - t[j]) * ey[j] / (ey[j] - ey[j + 1]))
     assert len(cr) > 6
     assert 2 * np.mean(np.diff(cr)) == pytest.approx(T, rel=0.02)
+
+
+# ---------------------------------------------------------------------------
+# Linear wake (PR-15): a Gaussian pulse with a^2 = a0^2 exp(-zeta^2/sigma^2) drives, in a cold
+# uniform plasma, E_z,max / E0 = (sqrt(pi)/4) a0^2 k_p sigma exp(-k_p^2 sigma^2 / 4), E0 = m c w_p / e,
+# with wavelength 2 pi c / w_p (Esarey et al., the paper's linear-wake reference). The pulse is
+# wide (k_p w0 = 15) and resolved by 24 cells per laser wavelength with linear shapes, so that the
+# 2D and shape-smoothing corrections stay near 1%.
+LW_N0, LW_A0, LW_LAM = 2e25, 0.1, 0.8e-6
+
+
+def _linear_wake_case(gamma_boost, nz, plasma_start_cells):
+    wp = math.sqrt(LW_N0 * QE * QE / (EPS0 * ME))
+    kp = wp / C
+    sig = math.sqrt(2.0) / kp                      # k_p sigma = sqrt(2): the amplitude's maximum
+    tau = 2.0 * math.sqrt(math.log(2.0)) * sig / C  # intensity FWHM
+    dzl = LW_LAM / 24.0
+    beta = math.sqrt(1.0 - 1.0 / gamma_boost ** 2)
+    dzb = (1.0 + beta) * gamma_boost * dzl
+    nx, dx = 72, 2e-6
+    w = {"name": "linear_wake", "nx": nx, "nz": nz, "dz_lab": dzl, "dx": dx, "gamma_boost": gamma_boost,
+         "courant": 0.95, "dt": 0.0, "solver": W.SOLVERS["yee"], "theta": 0.0, "pml_cells": 8,
+         "pml_sigma_max": 4.0, "pml_delta": 5.0, "pml_power": 2.0, "pml_xi_exp": 1,
+         "filter_passes": 0, "filter_stride": 1, "filter_compensate": 0, "filter_J": 0, "filter_gather": 0,
+         "order": 1, "particle_guard": -1, "precision": "fp64",
+         "moving_window": int(gamma_boost == 1.0), "window_beta": 1.0 if gamma_boost == 1.0 else 0.0,
+         "plasma": {"n0": LW_N0, "z_start_lab": gamma_boost * plasma_start_cells * dzb, "ramp_lab": 1e-6,
+                    "length_lab": 0.0, "ppc_x": 1, "ppc_z": 1, "ions": 1},
+         "laser": {"lambda0": LW_LAM, "a0": LW_A0, "w0": 15.0 / kp, "tau_fwhm": tau,
+                   "t_peak": 3.2 * tau / (2.0 * math.sqrt(math.log(2.0))), "x_center": nx / 2 * dx,
+                   "phase": 0.0, "z_antenna": (nz - 70 if gamma_boost == 1.0 else 40) * dzb, "beta_s": 0.0}}
+    ez_lin = math.sqrt(math.pi) / 4 * LW_A0 ** 2 * kp * sig * math.exp(-(kp * sig) ** 2 / 4) * ME * C * wp / QE
+    return w, ez_lin, 2 * math.pi / kp / dzl, sig / dzl
+
+
+def _wake_behind_laser(s, nx, lp_cells, sig_cells):
+    """max |E_z| on the axis between 1.5 plasma wavelengths and 3 sigma behind the laser peak, and
+    the zero crossings of E_z there (cells)"""
+    ez, ey = s.field(2)[nx // 2], s.field(1)[nx // 2]
+    kl = int(np.argmax(np.abs(ey)))
+    a, b = max(kl - int(1.5 * lp_cells), 30), kl - int(3 * sig_cells)
+    seg = ez[a:b]
+    zc = [a + i + seg[i] / (seg[i] - seg[i + 1]) for i in range(len(seg) - 1) if seg[i] * seg[i + 1] < 0]
+    return np.abs(seg).max(), zc
+
+
+@pytest.fixture(scope="module")
+def lab_wake(orc):
+    w, ez_lin, lp, sg = _linear_wake_case(1.0, 600, 540)
+    s = orc.Sim(w)
+    s.step(520)
+    return (*_wake_behind_laser(s, w["nx"], lp, sg), ez_lin, lp)
+
+
+def test_linear_wake_amplitude_and_wavelength(lab_wake):
+    ez, zc, ez_lin, lp = lab_wake
+    assert ez == pytest.approx(ez_lin, rel=0.05)
+    # consecutive zero crossings half a plasma wavelength apart (wake phase velocity ~ c)
+    half = np.diff(zc)
+    assert len(half) >= 1 and half[-1] == pytest.approx(lp / 2, rel=0.03)
+
+
+def test_boosted_and_lab_frames_agree_on_the_wake(orc, lab_wake):
+    """the same pulse and plasma simulated in a frame boosted at gamma = 2: E_z is invariant under
+    the boost, so the wake amplitude behind the laser must agree with the lab run. The plasma starts
+    300 cells beyond the antenna, so that the pulse leaves the antenna in vacuum, as in the lab run."""
+    w, ez_lin, lp, sg = _linear_wake_case(2.0, 720, 340)
+    s = orc.Sim(w)
+    s.step(600)
+    ez_boost, _ = _wake_behind_laser(s, w["nx"], lp, sg)
+    assert ez_boost == pytest.approx(lab_wake[0], rel=0.04)
+    assert ez_boost == pytest.approx(ez_lin, rel=0.05)
