@@ -40,9 +40,9 @@ BYTES_PER_PARTICLE = {"mixed": 60, "fp64": 88}
 BYTES_PER_CELL = {"mixed": 168, "fp64": 336}
 # measured DRAM bytes (read + write) per particle of one push launch, mixed precision, cubic shapes:
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of k_push on the 2048 x 256 stage box
-# (profiles/k_push_stage2d_2048x256_mixed.md: 322.76 MB for 6,487,608 electrons), scaled to the
+# (profiles/k_push_stage2d_2048x256_mixed.md: 364.33 MB for 6,487,608 electrons), scaled to the
 # full box by its particle count; None for configurations not captured
-TRAFFIC_BYTES_PER_PARTICLE = {("mixed", 3): 49.75}
+TRAFFIC_BYTES_PER_PARTICLE = {("mixed", 3): 56.16}
 
 
 def measured_peaks() -> dict:
@@ -68,7 +68,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
@@ -196,7 +196,7 @@ def run_reference(args, w):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=8)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
@@ -268,8 +268,8 @@ def main():
     roof = {"kernel": "k_push (gather + Boris + Esirkepov)", "bound": "hbm", "achieved": achieved, "peak": peak,
             "unit": "GB/s", "frac": achieved / peak, "traffic": tpp * n_avg if tpp else None,
             "traffic_source": "ncu dram bytes of k_push, 2048 x 256 box, scaled by particles" if tpp else None,
-            "note": "at cubic order the push is bound by instruction issue and the shared-memory pipe "
-                    "(ncu: 63% issue slots, 71% L1/shared, 14% DRAM), not by HBM",
+            "note": "at cubic order the push is bound by instruction issue "
+                    "(ncu: 62% issue slots, 52% L1/shared, 15% DRAM), not by HBM",
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback",
             "algorithmic_bytes_per_particle": bpp, "push_ms_per_step": push_avg_ms,
             "share_of_step": push_avg_ms / (ms / args.steps)}
