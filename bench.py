@@ -193,6 +193,53 @@ def run_reference(args, w):
     return 0
 
 
+def run_ensemble(args):
+    """N uneven runs (seeded recipe) advanced together; also the same runs one after the other."""
+    import torch
+    from paper_1009_2727_gb300 import workloads as W
+    from paper_1009_2727_gb300.pic import Ensemble
+    torch.cuda.set_device(0)
+    ws = W.ensemble_2d(args.ensemble)
+    ens = Ensemble(ws)
+    ens.step(max(args.warmup, 3))
+    ens.sync()
+    n0 = sum(m.stats()["n_electrons"] for m in ens.members)
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    ens.step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    ens.sync()
+    n1 = sum(m.stats()["n_electrons"] for m in ens.members)
+    cells = sum(w["nx"] * w["nz"] for w in ws)
+    # the same runs one at a time, each on the caller's stream
+    seq_ms = 0.0
+    ens.close()
+    from paper_1009_2727_gb300.pic import Simulation
+    for w in ws:
+        s = Simulation(w)
+        s.step(max(args.warmup, 3))
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        s.step(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        seq_ms += ev0.elapsed_time(ev1)
+        s.close()
+    ps = 0.5 * (n0 + n1) * args.steps
+    line = {"metric": "ensemble particle-steps/s", "value": ps / (ms * 1e-3), "unit": "particle-steps/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "dtype": "f32+f64pos", "data": "synthetic",
+            "config": {"workload": f"ensemble_2d({args.ensemble}) seeded uneven runs", "runs": len(ws),
+                       "cells": cells, "electrons": int(0.5 * (n0 + n1))},
+            "sequential_ms_per_step": seq_ms / args.steps, "speedup_vs_sequential": seq_ms / ms}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -205,6 +252,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--nz", type=int, default=0, help="smaller box for profiling captures (default: the full 4096)")
     ap.add_argument("--sort-every", type=int, default=0, help="steps between particle sorts (0: the library default)")
+    ap.add_argument("--ensemble", type=int, default=0,
+                    help="time N uneven runs advanced together (pic_ensemble_*) instead of the stage")
     args = ap.parse_args()
 
     from paper_1009_2727_gb300 import workloads as W
@@ -215,6 +264,8 @@ def main():
     w["precision"] = args.precision
     if args.impl == "reference":
         return run_reference(args, w)
+    if args.ensemble:
+        return run_ensemble(args)
 
     import torch
     ws, rank, local = dist_env()

@@ -236,6 +236,55 @@ int64_t pic_kernel_launches(pic_ctx* ctx);
  * 1 = field kernels). Used by the benchmark for the per-kernel roofline. */
 int pic_kernel_timing(pic_ctx* ctx, int enable, int which, double* ms_total, int64_t* launches);
 
+/* ---- Autotuner of the particle layout (no counterpart in the paper) ----
+ * Picks the particle tile (tile_x, tile_z) from {8, 16, 32}^2 at a cadence of 32,
+ * then the sort cadence from {8, 16, 32, 64} for that tile, by timing `steps`
+ * steps (after 4 warm-up steps; a cadence trial runs at least two sort periods)
+ * of contexts built from cfg, plasma and laser (laser may be NULL) through
+ * pic_init/pic_load_plasma/pic_inject_laser with the given allocator and stream.
+ * The result is cached per (nx, nz, ppc_x, ppc_z, shape order, precision,
+ * gamma_boost) for the life of the process; a cached answer comes back without
+ * timing and with cached = 1. out->struct_size must be set by the caller.
+ * Returns PIC_EINVAL for bad arguments, PIC_ECUDA when no trial ran. */
+#define PIC_TUNE_MAX_TRIALS 16
+typedef struct pic_tune_result {
+  uint32_t struct_size;
+  uint32_t version;
+  int32_t tile_x, tile_z, sort_every;   /* the chosen layout */
+  double ms_per_step;                   /* its time per step in the trials */
+  int32_t n_trials;
+  int32_t trial_tile_x[PIC_TUNE_MAX_TRIALS];
+  int32_t trial_tile_z[PIC_TUNE_MAX_TRIALS];
+  int32_t trial_sort_every[PIC_TUNE_MAX_TRIALS];
+  double trial_ms[PIC_TUNE_MAX_TRIALS]; /* < 0: the trial failed */
+  int32_t cached;
+} pic_tune_result;
+
+int pic_autotune(const pic_config* cfg, const pic_plasma* plasma, const pic_laser* laser, int steps,
+                 pic_alloc_fn alloc, pic_free_fn free_fn, void* alloc_user, void* cuda_stream,
+                 pic_tune_result* out);
+
+/* ---- Ensemble of independent runs (no counterpart in the paper) ----
+ * n runs of uneven size (each its own pic_config, pic_plasma and pic_laser;
+ * lasers may be NULL, and a laser with lambda0 <= 0 means none) advanced together.
+ * Every run is an ordinary context on its own non-blocking CUDA stream, created
+ * and owned by the ensemble; pic_ensemble_step enqueues one step of every run
+ * before the next, so that the runs execute concurrently. The runs start after
+ * the work already on cuda_stream, and cuda_stream waits for all of them when
+ * pic_ensemble_step returns (pass NULL to skip both). pic_ensemble_member gives a
+ * run's context for the accessors (pic_get_field, pic_get_stats, ...); it stays
+ * owned by the ensemble. Errors: PIC_EINVAL for bad arguments, else the first
+ * failing call's status; pic_ensemble_sync returns the first run's error. */
+typedef struct pic_ens pic_ens;
+int pic_ensemble_create(int n, const pic_config* cfgs, const pic_plasma* plasmas, const pic_laser* lasers,
+                        pic_alloc_fn alloc, pic_free_fn free_fn, void* alloc_user, void* cuda_stream,
+                        pic_ens** out);
+int pic_ensemble_step(pic_ens* ens, int nsteps);
+int pic_ensemble_sync(pic_ens* ens);
+int pic_ensemble_size(pic_ens* ens);
+pic_ctx* pic_ensemble_member(pic_ens* ens, int index);
+int pic_ensemble_free(pic_ens* ens);
+
 #ifdef __cplusplus
 }
 #endif

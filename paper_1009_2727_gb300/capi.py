@@ -27,7 +27,9 @@ STATUS_NAMES = {0: "PIC_OK", -1: "PIC_EINVAL", -2: "PIC_ENOMEM", -3: "PIC_ECFL",
 # every symbol include/pic.h declares
 EXPORTS = ("pic_init", "pic_load_plasma", "pic_inject_laser", "pic_step", "pic_sync", "pic_boosted_to_lab_diag",
            "pic_free", "pic_get_field", "pic_set_field", "pic_get_particles", "pic_get_stats", "pic_last_error",
-           "pic_kernel_launches", "pic_kernel_timing", "pic_get_rho_noalloc")
+           "pic_kernel_launches", "pic_kernel_timing", "pic_get_rho_noalloc", "pic_autotune",
+           "pic_ensemble_create", "pic_ensemble_step", "pic_ensemble_sync", "pic_ensemble_size",
+           "pic_ensemble_member", "pic_ensemble_free")
 NOALLOC_MAX_NZ = 16384
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -100,6 +102,20 @@ class PicStats(ctypes.Structure):
     ]
 
 
+TUNE_MAX_TRIALS = 16
+
+
+class PicTuneResult(ctypes.Structure):
+    _fields_ = [
+        ("struct_size", ctypes.c_uint32), ("version", ctypes.c_uint32),
+        ("tile_x", ctypes.c_int32), ("tile_z", ctypes.c_int32), ("sort_every", ctypes.c_int32),
+        ("ms_per_step", ctypes.c_double), ("n_trials", ctypes.c_int32),
+        ("trial_tile_x", ctypes.c_int32 * TUNE_MAX_TRIALS), ("trial_tile_z", ctypes.c_int32 * TUNE_MAX_TRIALS),
+        ("trial_sort_every", ctypes.c_int32 * TUNE_MAX_TRIALS), ("trial_ms", ctypes.c_double * TUNE_MAX_TRIALS),
+        ("cached", ctypes.c_int32),
+    ]
+
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -144,5 +160,15 @@ def load(build_if_missing: bool = True):
         L.pic_kernel_launches.restype = ctypes.c_int64
         L.pic_kernel_timing.argtypes = [vp, ctypes.c_int, ctypes.c_int, _D, ctypes.POINTER(ctypes.c_int64)]
         L.pic_get_rho_noalloc.argtypes = [vp, _D]
+        L.pic_ensemble_create.argtypes = [ctypes.c_int, ctypes.POINTER(PicConfig), ctypes.POINTER(PicPlasma),
+                                          ctypes.POINTER(PicLaser), ALLOC_FN, FREE_FN, vp, vp, ctypes.POINTER(vp)]
+        L.pic_ensemble_step.argtypes = [vp, ctypes.c_int]
+        L.pic_ensemble_sync.argtypes = [vp]
+        L.pic_ensemble_size.argtypes = [vp]
+        L.pic_ensemble_member.argtypes = [vp, ctypes.c_int]
+        L.pic_ensemble_member.restype = vp
+        L.pic_ensemble_free.argtypes = [vp]
+        L.pic_autotune.argtypes = [ctypes.POINTER(PicConfig), ctypes.POINTER(PicPlasma), ctypes.POINTER(PicLaser),
+                                   ctypes.c_int, ALLOC_FN, FREE_FN, vp, vp, ctypes.POINTER(PicTuneResult)]
         _lib = L
         return L

@@ -348,8 +348,13 @@ struct Sim : SimBase {
       if (!okp || !q->ux || !q->uy || !q->uz || !q->w || !q->id) return c->fail(PIC_ENOMEM, "particle allocation failed");
     }
     const int ntiles = sb.ntx * sb.ntz;
-    const int inj_chunks = ((g.gx_hi - g.gx_lo + ip.xblock - 1) / ip.xblock) * 4;
-    chunk_cap = 2 * ntiles + cap / chunk_max + inj_chunks * (sort_every + 4) + 4096;
+    const int xblocks = (g.gx_hi - g.gx_lo + ip.xblock - 1) / ip.xblock;
+    const int inj_chunks = xblocks * 4;
+    // the initial load injects every row at once, in chunks of 8 rows by one x-block
+    const long long init_rows = std::max(0LL, rows_inside(time_of(step)) - rows_from(time_of(step)));
+    const long long init_chunks = (long long)xblocks * ((init_rows + 7) / 8);
+    chunk_cap = (int)std::max((long long)(2 * ntiles + cap / chunk_max), init_chunks) + inj_chunks * (sort_every + 4) +
+                4096;
     chunks = al<Chunk>(chunk_cap);
     if (ntiles > 1024 * 1024) return c->fail(PIC_EINVAL, "too many particle tiles; enlarge tile_x/tile_z");
     const size_t ncells = (size_t)ntiles * sb.tx * sb.tz;

@@ -1,0 +1,121 @@
+// Ensemble of independent runs (uneven grids, densities, boosts) advanced
+// together: every run is an ordinary context on its own non-blocking stream,
+// and a step of the ensemble enqueues one step of every run before waiting on
+// any, so that the GPU executes the runs concurrently (small runs alone leave
+// most SMs idle).
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "../../include/pic.h"
+
+struct pic_ens {
+  std::vector<pic_ctx*> ctx;
+  std::vector<cudaStream_t> streams;
+  cudaStream_t caller = nullptr;
+  cudaEvent_t start = nullptr;
+  std::vector<cudaEvent_t> done;
+};
+
+namespace {
+
+void destroy(pic_ens* e) {
+  for (pic_ctx* c : e->ctx) pic_free(c);
+  for (cudaStream_t s : e->streams) cudaStreamDestroy(s);
+  for (cudaEvent_t ev : e->done) cudaEventDestroy(ev);
+  if (e->start) cudaEventDestroy(e->start);
+  delete e;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pic_ensemble_create(int n, const pic_config* cfgs, const pic_plasma* plasmas, const pic_laser* lasers,
+                        pic_alloc_fn alloc, pic_free_fn free_fn, void* alloc_user, void* cuda_stream,
+                        pic_ens** out) {
+  if (!out) return PIC_EINVAL;
+  *out = nullptr;
+  if (n < 1 || !cfgs || !plasmas) return PIC_EINVAL;
+  pic_ens* e = new pic_ens();
+  e->caller = (cudaStream_t)cuda_stream;
+  if (cudaEventCreateWithFlags(&e->start, cudaEventDisableTiming) != cudaSuccess) {
+    destroy(e);
+    return PIC_ECUDA;
+  }
+  for (int i = 0; i < n; i++) {
+    cudaStream_t s = nullptr;
+    cudaEvent_t ev = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+      if (s) cudaStreamDestroy(s);
+      destroy(e);
+      return PIC_ECUDA;
+    }
+    e->streams.push_back(s);
+    e->done.push_back(ev);
+    pic_ctx* c = nullptr;
+    int r = pic_init(&cfgs[i], alloc, free_fn, alloc_user, s, &c);
+    if (r != PIC_OK) {
+      destroy(e);
+      return r;
+    }
+    e->ctx.push_back(c);
+    r = pic_load_plasma(c, &plasmas[i]);
+    if (r == PIC_OK && lasers && lasers[i].lambda0 > 0.0) r = pic_inject_laser(c, &lasers[i]);
+    if (r != PIC_OK) {
+      destroy(e);
+      return r;
+    }
+  }
+  *out = e;
+  return PIC_OK;
+}
+
+int pic_ensemble_step(pic_ens* e, int nsteps) {
+  if (!e || nsteps < 0) return PIC_EINVAL;
+  // the runs start after the work already on the caller's stream, and the caller's
+  // stream waits for all of them at the end
+  if (e->caller) {
+    cudaEventRecord(e->start, e->caller);
+    for (cudaStream_t s : e->streams) cudaStreamWaitEvent(s, e->start, 0);
+  }
+  for (int k = 0; k < nsteps; k++)
+    for (pic_ctx* c : e->ctx) {
+      const int r = pic_step(c, 1);
+      if (r != PIC_OK) return r;
+    }
+  if (e->caller) {
+    for (size_t i = 0; i < e->streams.size(); i++) {
+      cudaEventRecord(e->done[i], e->streams[i]);
+      cudaStreamWaitEvent(e->caller, e->done[i], 0);
+    }
+  }
+  return cudaGetLastError() == cudaSuccess ? PIC_OK : PIC_ECUDA;
+}
+
+int pic_ensemble_sync(pic_ens* e) {
+  if (!e) return PIC_EINVAL;
+  int first = PIC_OK;
+  for (pic_ctx* c : e->ctx) {
+    const int r = pic_sync(c);
+    if (r != PIC_OK && first == PIC_OK) first = r;
+  }
+  return first;
+}
+
+int pic_ensemble_size(pic_ens* e) { return e ? (int)e->ctx.size() : 0; }
+
+pic_ctx* pic_ensemble_member(pic_ens* e, int i) {
+  if (!e || i < 0 || i >= (int)e->ctx.size()) return nullptr;
+  return e->ctx[i];
+}
+
+int pic_ensemble_free(pic_ens* e) {
+  if (!e) return PIC_OK;
+  for (cudaStream_t s : e->streams) cudaStreamSynchronize(s);
+  destroy(e);
+  return PIC_OK;
+}
+
+}  // extern "C"

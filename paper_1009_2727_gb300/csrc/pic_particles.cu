@@ -693,8 +693,8 @@ __global__ void k_sort_key(GridP g, Particles<T> p, SortBufs sb, const Ctrl* ctr
   sb.slot[i] = atomicAdd(&sb.cell_cnt[c], 1);
 }
 
-// particles per tile (one block per tile, one thread per cell)
-__global__ void k_tile_count(SortBufs sb) {
+// particles per tile (one block per tile, one thread per cell; tiles of up to 1024 cells)
+__global__ void __launch_bounds__(1024) k_tile_count(SortBufs sb) {
   const int tc = sb.tx * sb.tz;
   const int cl = threadIdx.x;
   int v = cl < tc ? sb.cell_cnt[(long)blockIdx.x * tc + cl] : 0;
@@ -704,7 +704,7 @@ __global__ void k_tile_count(SortBufs sb) {
 }
 
 // destination of every (cell, rank) entry of a tile (one block per tile, one thread per cell)
-__global__ void k_tile_order(SortBufs sb) {
+__global__ void __launch_bounds__(1024) k_tile_order(SortBufs sb) {
   const int tc = sb.tx * sb.tz;
   const int cl = threadIdx.x;
   const long c = (long)blockIdx.x * tc + cl;

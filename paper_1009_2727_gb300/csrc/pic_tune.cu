@@ -1,0 +1,116 @@
+// Autotuner of the particle layout: the tile shape of the particle sort and the
+// sort cadence, timed on the first steps of the run itself and cached per run
+// shape. Every trial is an ordinary context built through the public ABI, so a
+// tuned configuration is exactly what the caller then runs.
+#include <cuda_runtime.h>
+
+#include <map>
+#include <mutex>
+#include <tuple>
+
+#include "../../include/pic.h"
+
+namespace {
+
+// trial sets: tiles of 8/16/32 cells on each axis, then cadences around the default
+constexpr int kTiles[3] = {8, 16, 32};
+constexpr int kCadences[4] = {8, 16, 32, 64};
+
+typedef std::tuple<int, int, int, int, int, int, long long> Key;   // nx, nz, ppc_x, ppc_z, order, precision, gamma*1e6
+
+std::mutex g_mu;
+std::map<Key, pic_tune_result> g_cache;
+
+Key key_of(const pic_config* c, const pic_plasma* p) {
+  return Key(c->nx, c->nz, p->ppc_x, p->ppc_z, c->shape_order, c->precision, (long long)(c->gamma_boost * 1e6));
+}
+
+// one trial: a context with this layout, warm-up steps, then timed steps (ms per step; < 0 on failure)
+double trial(const pic_config* cfg0, const pic_plasma* pl, const pic_laser* laser, int tx, int tz, int sort_every,
+             int warm, int steps, pic_alloc_fn alloc, pic_free_fn free_fn, void* user, void* stream) {
+  pic_config cfg = *cfg0;
+  cfg.tile_x = tx;
+  cfg.tile_z = tz;
+  cfg.sort_every = sort_every;
+  pic_ctx* ctx = nullptr;
+  if (pic_init(&cfg, alloc, free_fn, user, stream, &ctx) != PIC_OK) return -1.0;
+  double ms = -1.0;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (pic_load_plasma(ctx, pl) == PIC_OK && (!laser || pic_inject_laser(ctx, laser) == PIC_OK) &&
+      pic_step(ctx, warm) == PIC_OK && pic_sync(ctx) == PIC_OK && cudaEventCreate(&e0) == cudaSuccess &&
+      cudaEventCreate(&e1) == cudaSuccess) {
+    cudaEventRecord(e0, (cudaStream_t)stream);
+    const int r = pic_step(ctx, steps);
+    cudaEventRecord(e1, (cudaStream_t)stream);
+    float t = 0.0f;
+    if (r == PIC_OK && pic_sync(ctx) == PIC_OK && cudaEventSynchronize(e1) == cudaSuccess &&
+        cudaEventElapsedTime(&t, e0, e1) == cudaSuccess)
+      ms = (double)t / steps;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  pic_free(ctx);
+  return ms;
+}
+
+void record(pic_tune_result* o, int tx, int tz, int se, double ms) {
+  if (o->n_trials >= PIC_TUNE_MAX_TRIALS) return;
+  const int i = o->n_trials++;
+  o->trial_tile_x[i] = tx;
+  o->trial_tile_z[i] = tz;
+  o->trial_sort_every[i] = se;
+  o->trial_ms[i] = ms;
+}
+
+}  // namespace
+
+extern "C" int pic_autotune(const pic_config* cfg, const pic_plasma* plasma, const pic_laser* laser, int steps,
+                            pic_alloc_fn alloc, pic_free_fn free_fn, void* alloc_user, void* cuda_stream,
+                            pic_tune_result* out) {
+  if (!cfg || !plasma || !out || out->struct_size != sizeof(pic_tune_result)) return PIC_EINVAL;
+  if (steps < 1) return PIC_EINVAL;
+  const Key key = key_of(cfg, plasma);
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_cache.find(key);
+    if (it != g_cache.end()) {
+      *out = it->second;
+      out->cached = 1;
+      return PIC_OK;
+    }
+  }
+  pic_tune_result r{};
+  r.struct_size = sizeof(pic_tune_result);
+  r.version = PIC_API_VERSION;
+  const int warm = 4;
+  // 1. tile shape at the default cadence
+  double best = -1.0;
+  int btx = 0, btz = 0;
+  for (int tx : kTiles)
+    for (int tz : kTiles) {
+      const double ms = trial(cfg, plasma, laser, tx, tz, 32, warm, steps, alloc, free_fn, alloc_user, cuda_stream);
+      record(&r, tx, tz, 32, ms);
+      if (ms > 0.0 && (best < 0.0 || ms < best)) { best = ms; btx = tx; btz = tz; }
+    }
+  if (best < 0.0) return PIC_ECUDA;
+  // 2. sort cadence for that tile, each timed over at least one sort period
+  int bse = 32;
+  double bse_ms = -1.0;
+  for (int se : kCadences) {
+    const int n = steps > 2 * se ? steps : 2 * se;
+    const double ms = trial(cfg, plasma, laser, btx, btz, se, warm, n, alloc, free_fn, alloc_user, cuda_stream);
+    record(&r, btx, btz, se, ms);
+    if (ms > 0.0 && (bse_ms < 0.0 || ms < bse_ms)) { bse_ms = ms; bse = se; }
+  }
+  r.tile_x = btx;
+  r.tile_z = btz;
+  r.sort_every = bse;
+  r.ms_per_step = bse_ms > 0.0 ? bse_ms : best;
+  r.cached = 0;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_cache[key] = r;
+  }
+  *out = r;
+  return PIC_OK;
+}

@@ -23,9 +23,119 @@ class PicError(RuntimeError):
     pass
 
 
+def make_config(w: dict, precision: int, tile=None, sort_every: int = 0) -> capi.PicConfig:
+    """pic_config from a workload dict (SI units)."""
+    c = capi.PicConfig()
+    c.struct_size = ctypes.sizeof(capi.PicConfig)
+    c.version = capi.API_VERSION
+    c.dim = 2
+    c.nx, c.nz = int(w["nx"]), int(w["nz"])
+    c.dz_lab, c.dx = float(w["dz_lab"]), float(w["dx"])
+    c.gamma_boost = float(w.get("gamma_boost", 1.0))
+    c.courant = float(w.get("courant", 0.9))
+    c.dt = float(w.get("dt", 0.0) or 0.0)
+    c.ck_alpha, c.ck_beta, c.ck_gamma = (float(v) for v in w.get("solver", (1.0, 0.0, 0.0)))
+    c.theta = float(w.get("theta", 0.0))
+    c.pml_cells = int(w.get("pml_cells", 0))
+    c.pml_sigma_max = float(w.get("pml_sigma_max", 4.0))
+    c.pml_delta = float(w.get("pml_delta", 5.0))
+    c.pml_power = float(w.get("pml_power", 2.0))
+    c.pml_xi_exp = int(w.get("pml_xi_exp", 1))
+    c.filter_passes = int(w.get("filter_passes", 0))
+    c.filter_stride = int(w.get("filter_stride", 1))
+    c.filter_compensate = int(w.get("filter_compensate", 0))
+    c.filter_J = int(w.get("filter_J", 0))
+    c.filter_gather = int(w.get("filter_gather", 0))
+    c.shape_order = int(w.get("order", 3))
+    c.particle_guard = int(w.get("particle_guard", -1))
+    c.precision = precision
+    c.moving_window = int(w.get("moving_window", 0))
+    c.window_beta = float(w.get("window_beta", 0.0))
+    if tile:
+        c.tile_x, c.tile_z = int(tile[0]), int(tile[1])
+    c.sort_every = int(sort_every)
+    return c
+
+
+def make_plasma(p: dict | None, beam: dict | None, keep: list) -> capi.PicPlasma:
+    """pic_plasma from a plasma dict and an optional lab-frame test beam (arrays kept alive in keep)."""
+    pl = capi.PicPlasma()
+    pl.struct_size = ctypes.sizeof(capi.PicPlasma)
+    pl.version = capi.API_VERSION
+    if p:
+        pl.n0 = float(p["n0"])
+        pl.z_start_lab = float(p.get("z_start_lab", 0.0))
+        pl.ramp_lab = float(p.get("ramp_lab", 0.0))
+        pl.length_lab = float(p.get("length_lab", 0.0))
+        pl.ppc_x, pl.ppc_z = int(p["ppc_x"]), int(p["ppc_z"])
+        pl.ions = int(p.get("ions", 1))
+    else:
+        pl.ppc_x = pl.ppc_z = 1
+    if beam:
+        arrs = [np.ascontiguousarray(beam[k], dtype=np.float64) for k in ("x", "z", "ux", "uy", "uz")]
+        keep.append(arrs)
+        pl.beam_n = arrs[0].size
+        pl.beam_x, pl.beam_z, pl.beam_ux, pl.beam_uy, pl.beam_uz = (_p(a) for a in arrs)
+        pl.beam_t_lab = float(beam.get("t_lab", 0.0))
+        pl.beam_z_plane_lab = float(beam["z_plane_lab"])
+    return pl
+
+
+def make_laser(l: dict, nx: int, dx: float) -> capi.PicLaser:
+    la = capi.PicLaser()
+    la.struct_size = ctypes.sizeof(capi.PicLaser)
+    la.version = capi.API_VERSION
+    la.lambda0, la.a0, la.w0 = float(l["lambda0"]), float(l["a0"]), float(l["w0"])
+    la.tau_fwhm, la.t_peak = float(l["tau_fwhm"]), float(l.get("t_peak", 0.0))
+    la.x_center = float(l.get("x_center", 0.5 * nx * dx))
+    la.phase, la.z_antenna, la.beta_s = float(l.get("phase", 0.0)), float(l["z_antenna"]), float(l.get("beta_s", 0.0))
+    return la
+
+
+def torch_allocator(device_index: int):
+    """allocator callbacks on PyTorch's caching allocator (keep the returned pair alive)"""
+    import torch
+
+    def _alloc(nbytes, stream, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), device_index, stream)
+        except Exception:
+            return None
+
+    def _free(ptr, nbytes, stream, user):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    return capi.ALLOC_FN(_alloc), capi.FREE_FN(_free)
+
+
+def autotune(w: dict, steps: int = 16, precision: str | None = None, stream=None) -> dict:
+    """Tile shape and sort cadence for this workload, timed on its first steps (pic_autotune; the
+    result is cached per run shape inside the library)."""
+    import torch
+    L = capi.load()
+    prec = precision or w.get("precision", "fp64")
+    c = make_config(w, capi.PIC_FP64 if prec == "fp64" else capi.PIC_MIXED)
+    keep = []
+    pl = make_plasma(w.get("plasma"), w.get("beam"), keep)
+    la = make_laser(w["laser"], int(w["nx"]), float(w["dx"])) if w.get("laser") else None
+    st = stream if stream is not None else torch.cuda.current_stream()
+    acb, fcb = torch_allocator(torch.cuda.current_device())
+    out = capi.PicTuneResult()
+    out.struct_size = ctypes.sizeof(capi.PicTuneResult)
+    r = L.pic_autotune(ctypes.byref(c), ctypes.byref(pl), ctypes.byref(la) if la is not None else None, int(steps),
+                       acb, fcb, None, ctypes.c_void_p(st.cuda_stream), ctypes.byref(out))
+    if r != 0:
+        raise PicError(f"pic_autotune failed: {capi.STATUS_NAMES.get(r, r)}")
+    n = out.n_trials
+    return {"tile": (out.tile_x, out.tile_z), "sort_every": out.sort_every, "ms_per_step": out.ms_per_step,
+            "cached": bool(out.cached),
+            "trials": [((out.trial_tile_x[i], out.trial_tile_z[i]), out.trial_sort_every[i], out.trial_ms[i])
+                       for i in range(n)]}
+
+
 class Simulation:
     def __init__(self, w: dict, precision: str | None = None, stream=None, tile=None, sort_every: int = 0,
-                 use_torch_allocator: bool = True):
+                 use_torch_allocator: bool = True, tune: bool = False):
         import torch
         if not torch.cuda.is_available():
             raise PicError("a CUDA device is required (the library has no CPU path)")
@@ -37,51 +147,15 @@ class Simulation:
         prec = precision or w.get("precision", "fp64")
         self.precision = capi.PIC_FP64 if prec == "fp64" else capi.PIC_MIXED
         self.nx, self.nz = int(w["nx"]), int(w["nz"])
-        c = capi.PicConfig()
-        c.struct_size = ctypes.sizeof(capi.PicConfig)
-        c.version = capi.API_VERSION
-        c.dim = 2
-        c.nx, c.nz = self.nx, self.nz
-        c.dz_lab, c.dx = float(w["dz_lab"]), float(w["dx"])
-        c.gamma_boost = float(w.get("gamma_boost", 1.0))
-        c.courant = float(w.get("courant", 0.9))
-        c.dt = float(w.get("dt", 0.0) or 0.0)
-        c.ck_alpha, c.ck_beta, c.ck_gamma = (float(v) for v in w.get("solver", (1.0, 0.0, 0.0)))
-        c.theta = float(w.get("theta", 0.0))
-        c.pml_cells = int(w.get("pml_cells", 0))
-        c.pml_sigma_max = float(w.get("pml_sigma_max", 4.0))
-        c.pml_delta = float(w.get("pml_delta", 5.0))
-        c.pml_power = float(w.get("pml_power", 2.0))
-        c.pml_xi_exp = int(w.get("pml_xi_exp", 1))
-        c.filter_passes = int(w.get("filter_passes", 0))
-        c.filter_stride = int(w.get("filter_stride", 1))
-        c.filter_compensate = int(w.get("filter_compensate", 0))
-        c.filter_J = int(w.get("filter_J", 0))
-        c.filter_gather = int(w.get("filter_gather", 0))
-        c.shape_order = int(w.get("order", 3))
-        c.particle_guard = int(w.get("particle_guard", -1))
-        c.precision = self.precision
-        c.moving_window = int(w.get("moving_window", 0))
-        c.window_beta = float(w.get("window_beta", 0.0))
-        if tile:
-            c.tile_x, c.tile_z = int(tile[0]), int(tile[1])
-        c.sort_every = int(sort_every)
+        if tune:
+            t = autotune(w, precision=prec, stream=self.stream)
+            tile, sort_every = t["tile"], t["sort_every"]
+            self.tuned = t
+        c = make_config(w, self.precision, tile, sort_every)
         self._cfg = c
         self._keep = []
         if use_torch_allocator:
-            dev = self.device.index
-
-            def _alloc(nbytes, stream, user):
-                try:
-                    return torch.cuda.caching_allocator_alloc(int(nbytes), dev, stream)
-                except Exception:
-                    return None
-
-            def _free(ptr, nbytes, stream, user):
-                torch.cuda.caching_allocator_delete(ptr)
-
-            self._alloc_cb = capi.ALLOC_FN(_alloc)
-            self._free_cb = capi.FREE_FN(_free)
+            self._alloc_cb, self._free_cb = torch_allocator(self.device.index)
         else:
             self._alloc_cb = capi.ALLOC_FN()
             self._free_cb = capi.FREE_FN()
@@ -103,35 +177,11 @@ class Simulation:
             raise PicError(f"{what} failed: {capi.STATUS_NAMES.get(r, r)} {msg}")
 
     def load_plasma(self, p: dict | None, beam: dict | None = None):
-        pl = capi.PicPlasma()
-        pl.struct_size = ctypes.sizeof(capi.PicPlasma)
-        pl.version = capi.API_VERSION
-        if p:
-            pl.n0 = float(p["n0"])
-            pl.z_start_lab = float(p.get("z_start_lab", 0.0))
-            pl.ramp_lab = float(p.get("ramp_lab", 0.0))
-            pl.length_lab = float(p.get("length_lab", 0.0))
-            pl.ppc_x, pl.ppc_z = int(p["ppc_x"]), int(p["ppc_z"])
-            pl.ions = int(p.get("ions", 1))
-        else:
-            pl.ppc_x = pl.ppc_z = 1
-        if beam:
-            arrs = [np.ascontiguousarray(beam[k], dtype=np.float64) for k in ("x", "z", "ux", "uy", "uz")]
-            self._keep.append(arrs)
-            pl.beam_n = arrs[0].size
-            pl.beam_x, pl.beam_z, pl.beam_ux, pl.beam_uy, pl.beam_uz = (_p(a) for a in arrs)
-            pl.beam_t_lab = float(beam.get("t_lab", 0.0))
-            pl.beam_z_plane_lab = float(beam["z_plane_lab"])
+        pl = make_plasma(p, beam, self._keep)
         self._check(self.L.pic_load_plasma(self.h, ctypes.byref(pl)), "pic_load_plasma")
 
     def inject_laser(self, l: dict):
-        la = capi.PicLaser()
-        la.struct_size = ctypes.sizeof(capi.PicLaser)
-        la.version = capi.API_VERSION
-        la.lambda0, la.a0, la.w0 = float(l["lambda0"]), float(l["a0"]), float(l["w0"])
-        la.tau_fwhm, la.t_peak = float(l["tau_fwhm"]), float(l.get("t_peak", 0.0))
-        la.x_center = float(l.get("x_center", 0.5 * self.nx * float(self.w["dx"])))
-        la.phase, la.z_antenna, la.beta_s = float(l.get("phase", 0.0)), float(l["z_antenna"]), float(l.get("beta_s", 0.0))
+        la = make_laser(l, self.nx, float(self.w["dx"]))
         self._check(self.L.pic_inject_laser(self.h, ctypes.byref(la)), "pic_inject_laser")
 
     def step(self, n: int = 1):
@@ -221,6 +271,87 @@ class Simulation:
         h = getattr(self, "h", None)
         if h:
             self.L.pic_free(h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _Member(Simulation):
+    """a run of an Ensemble: the accessors of Simulation on a context the ensemble owns"""
+
+    def __init__(self, ens, h, w, precision):
+        import torch
+        self.L, self.h, self.w, self.torch = ens.L, h, dict(w), torch
+        self.device = ens.device
+        self.stream = None
+        self.precision = precision
+        self.nx, self.nz = int(w["nx"]), int(w["nz"])
+        self._keep = []
+
+    def step(self, n: int = 1):
+        raise PicError("a member of an ensemble advances with the ensemble")
+
+    def close(self):
+        self.h = None     # owned by the ensemble
+
+
+class Ensemble:
+    """Independent runs of uneven size advanced together (pic_ensemble_*): each run has its own
+    stream and the runs of one step execute concurrently."""
+
+    def __init__(self, ws: list, precision: str | None = None, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise PicError("a CUDA device is required (the library has no CPU path)")
+        self.L = capi.load()
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        st = stream if stream is not None else torch.cuda.current_stream()
+        n = len(ws)
+        precs = [(precision or w.get("precision", "fp64")) for w in ws]
+        self._keep = []
+        cfgs = (capi.PicConfig * n)(*[make_config(w, capi.PIC_FP64 if p == "fp64" else capi.PIC_MIXED)
+                                      for w, p in zip(ws, precs)])
+        pls = (capi.PicPlasma * n)(*[make_plasma(w.get("plasma"), w.get("beam"), self._keep) for w in ws])
+        las = (capi.PicLaser * n)()
+        for i, w in enumerate(ws):
+            if w.get("laser"):
+                las[i] = make_laser(w["laser"], int(w["nx"]), float(w["dx"]))
+        self._alloc_cb, self._free_cb = torch_allocator(self.device.index)
+        h = ctypes.c_void_p()
+        r = self.L.pic_ensemble_create(n, cfgs, pls, las, self._alloc_cb, self._free_cb, None,
+                                       ctypes.c_void_p(st.cuda_stream), ctypes.byref(h))
+        if r != 0:
+            raise PicError(f"pic_ensemble_create failed: {capi.STATUS_NAMES.get(r, r)}")
+        self.h = h
+        self.members = [_Member(self, self.L.pic_ensemble_member(h, i), w,
+                                capi.PIC_FP64 if p == "fp64" else capi.PIC_MIXED)
+                        for i, (w, p) in enumerate(zip(ws, precs))]
+
+    def step(self, n: int = 1):
+        r = self.L.pic_ensemble_step(self.h, int(n))
+        if r != 0:
+            raise PicError(f"pic_ensemble_step failed: {capi.STATUS_NAMES.get(r, r)}")
+
+    def sync(self):
+        r = self.L.pic_ensemble_sync(self.h)
+        if r != 0:
+            raise PicError(f"pic_ensemble_sync failed: {capi.STATUS_NAMES.get(r, r)}")
+
+    def __len__(self):
+        return len(self.members)
+
+    def __getitem__(self, i):
+        return self.members[i]
+
+    def close(self):
+        if getattr(self, "h", None):
+            for m in self.members:
+                m.h = None
+            self.L.pic_ensemble_free(self.h)
             self.h = None
 
     def __del__(self):

@@ -117,3 +117,37 @@ def lab_beam(n: int, seed: int, gamma_b: float, R_b: float, L_b: float, z_c: flo
     g = gamma_b * (1.0 + spread * rng.normal(0.0, 1.0, n))
     uz = np.sqrt(g * g - 1.0) * c
     return x, z, np.zeros(n), np.zeros(n), uz
+
+
+def ensemble_2d(n: int = 64, seed: int = 4) -> list:
+    """Uneven 2D boosted-frame runs sampled from a seeded generator: nz ~ U{512..4096} (multiples of
+    64), nx ~ U{128..256} (multiples of 16), log10 n0 ~ U(23, 25) m^-3, a0 ~ U(0.5, 2.5),
+    w0 ~ U(6, 25) um, tau ~ U(20, 60) fs, gamma_boost ~ U(5, 30), particles per cell 2x2 or 4x4 (the
+    power-of-two counts of 4..16), mixed precision, the stage's solver and filter settings."""
+    rng = np.random.default_rng(seed)
+    runs = []
+    for i in range(n):
+        nz = int(rng.integers(8, 65)) * 64
+        nx = int(rng.integers(8, 17)) * 16
+        g = float(rng.uniform(5.0, 30.0))
+        n0 = float(10.0 ** rng.uniform(23.0, 25.0))
+        a0 = float(rng.uniform(0.5, 2.5))
+        w0 = float(rng.uniform(6e-6, 25e-6))
+        tau = float(rng.uniform(20e-15, 60e-15))
+        ppc = int(rng.choice([2, 4]))
+        dz_b = (1.0 + np.sqrt(1.0 - 1.0 / g ** 2)) * g * LAMBDA0 / 64.0
+        dx = 0.65e-6
+        runs.append({
+            "name": f"ensemble_{i}_{nz}x{nx}_g{g:.1f}",
+            "nx": nx, "nz": nz, "dz_lab": LAMBDA0 / 64.0, "dx": dx,
+            "gamma_boost": g, "courant": 0.99, "dt": 0.0,
+            "solver": SOLVERS["ck"], "theta": 0.1,
+            "pml_cells": 16, "pml_sigma_max": 4.0, "pml_delta": 5.0, "pml_power": 2.0, "pml_xi_exp": 1,
+            "filter_passes": 4, "filter_stride": 1, "filter_compensate": 1, "filter_J": 1, "filter_gather": 1,
+            "order": 3, "particle_guard": -1, "moving_window": 0, "window_beta": 0.0, "precision": "mixed",
+            "plasma": {"n0": n0, "z_start_lab": g * 40 * dz_b, "ramp_lab": 4e-6, "length_lab": 0.0,
+                       "ppc_x": ppc, "ppc_z": ppc, "ions": 1},
+            "laser": {"lambda0": LAMBDA0, "a0": a0, "w0": w0, "tau_fwhm": tau, "t_peak": 1.5 * tau,
+                      "x_center": 0.5 * nx * dx, "phase": 0.0, "z_antenna": 34 * dz_b, "beta_s": 0.0},
+        })
+    return runs

@@ -40,3 +40,32 @@ def test_init_rejects_bad_config_without_gpu_work():
     r = L.pic_init(ctypes.byref(c), capi.ALLOC_FN(), capi.FREE_FN(), None, None, ctypes.byref(h))
     assert r == capi.PIC_EINVAL and not h.value
     assert L.pic_free(None) == capi.PIC_OK
+
+
+def test_ctypes_mirrors_match_c_layout(tmp_path):
+    """every field offset and struct size of the ctypes mirrors equals the C compiler's for include/pic.h"""
+    import shutil
+    import subprocess
+    import pytest
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    structs = {"pic_config": capi.PicConfig, "pic_plasma": capi.PicPlasma, "pic_laser": capi.PicLaser,
+               "pic_btd_req": capi.PicBtdReq, "pic_btd_out": capi.PicBtdOut, "pic_stats": capi.PicStats,
+               "pic_tune_result": capi.PicTuneResult}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "pic.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f in py._fields_:
+            lines.append(f'  printf("{cname} {f[0]} %zu\\n", offsetof({cname}, {f[0]}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f in py._fields_:
+            assert got[(cname, f[0])] == getattr(py, f[0]).offset, (cname, f[0])

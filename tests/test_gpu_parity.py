@@ -206,3 +206,42 @@ def test_mixed_vs_fp64_full_stage(Sim):
         assert inner <= tol, (comp, inner)
     for s in sims.values():
         s.close()
+
+
+def test_autotune_times_layouts_and_caches(Sim, orc):
+    from paper_1009_2727_gb300.pic import autotune
+    w = W.shrink(W.stage_2d(), 256, 512)
+    t = autotune(w, steps=8)
+    tiles = [(a, b) for a in (8, 16, 32) for b in (8, 16, 32)]
+    assert not t["cached"] and len(t["trials"]) == 13
+    assert all(ms > 0 for _, _, ms in t["trials"])
+    assert t["tile"] in tiles and t["sort_every"] in (8, 16, 32, 64)
+    # the chosen tile is the fastest of the tile trials (all at cadence 32)
+    tile_trials = t["trials"][:9]
+    assert [tr[0] for tr in tile_trials] == tiles
+    assert t["tile"] == min(tile_trials, key=lambda tr: tr[2])[0]
+    t2 = autotune(w, steps=8)
+    assert t2["cached"] and t2["tile"] == t["tile"] and t2["sort_every"] == t["sort_every"]
+    # the layout changes the order of the current sums only: FP64 runs agree with the oracle in any layout
+    wp = W.shrink(W.parity_2d(), 48, 160)
+    g, o = run_pair(Sim, orc, wp, 30, tile=(8, 8), sort_every=4)
+    check_fields(g, o, TOL64)
+    check_particles(g, o, TOL64)
+
+
+def test_ensemble_runs_match_runs_alone(Sim):
+    """three uneven FP64 runs advanced together on their own streams give what each gives alone"""
+    from paper_1009_2727_gb300.pic import Ensemble
+    ws = [W.shrink(W.parity_2d(), 48, 160), W.shrink(W.parity_2d(), 64, 256), W.shrink(W.parity_2d(), 40, 192)]
+    ws[1]["plasma"]["n0"] = 3e24
+    ens = Ensemble(ws, precision="fp64")
+    ens.step(25)
+    ens.sync()
+    for i, w in enumerate(ws):
+        alone = Sim(w, precision="fp64")
+        alone.step(25)
+        alone.sync()
+        check_fields(ens[i], alone, 1e-12)
+        assert ens[i].stats()["n_electrons"] == alone.stats()["n_electrons"]
+        alone.close()
+    ens.close()
