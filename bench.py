@@ -240,6 +240,76 @@ def run_ensemble(args):
     return 0
 
 
+def run_surrogate(args):
+    """Stage surrogate: label N seeded stage runs through the ensemble, train the library's MLP on the valid
+    ones, score it on N/4 fresh runs, and time serving (device-resident queries, and host to host)."""
+    import numpy as np
+    import torch
+    from paper_1009_2727_gb300 import workloads as W
+    from paper_1009_2727_gb300 import surrogate as S
+    torch.cuda.set_device(0)
+    n_tr = args.surrogate
+    n_te = max(n_tr // 4, 8)
+    tr, te = W.surrogate_runs(n_tr, seed=1), W.surrogate_runs(n_te, seed=2)
+    t0 = time.time()
+    Xtr, Ytr, oktr = S.stage_labels(tr)
+    t_label = time.time() - t0
+    Xte, Yte, okte = S.stage_labels(te)
+    sur = S.Surrogate(hidden=(256, 256, 256), seed=0)
+    t0 = time.time()
+    curve = sur.fit(Xtr[oktr], Ytr[oktr], epochs=600, batch=32, lr=1e-3, weight_decay=1e-4)
+    torch.cuda.synchronize()
+    t_fit = time.time() - t0
+    pred, inside = sur.predict(Xte[okte])
+    m = inside
+    yt = Yte[okte][m]
+    r2 = 1.0 - ((pred[m] - yt) ** 2).mean(0) / np.maximum(yt.var(0), 1e-30)
+    # serving: Q standardised queries resident on the device, timed with events on the MLP's stream
+    Q = 1 << 20
+    rng = np.random.default_rng(0)
+    q = rng.uniform(Xtr.min(0), Xtr.max(0), (Q, 6))
+    xd = torch.as_tensor(((q - sur.xm) / sur.xs).astype(np.float32)).cuda()
+    yd = torch.empty((Q, 4), dtype=torch.float32, device="cuda")
+    net = sur.net
+    stream = net.stream
+    for _ in range(max(args.warmup, 3)):
+        net.forward_device(xd.data_ptr(), Q, yd.data_ptr())
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        net.forward_device(xd.data_ptr(), Q, yd.data_ptr())
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    t0 = time.time()
+    for _ in range(3):
+        sur.predict(q)
+    e2e_s = (time.time() - t0) / 3
+    w = [6, 256, 256, 256, 4]
+    flops = 2 * sum(w[i] * w[i + 1] for i in range(len(w) - 1))
+    peaks = measured_peaks()
+    achieved = flops * Q / (ms * 1e-3) / 1e12
+    run_steps = sum(r["steps"] for r in tr)
+    line = {"metric": "surrogate queries/s", "value": Q / (ms * 1e-3), "unit": "queries/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True,
+            "dtype": "bf16 (fp32 accumulate)", "data": "synthetic",
+            "config": {"workload": "stage surrogate 6-256-256-256-4 over surrogate_runs (1600 x 96 cells, mixed)",
+                       "train_runs": n_tr, "valid_train_runs": int(oktr.sum()), "heldout_runs": int(okte.sum()),
+                       "queries_per_step": Q},
+            "heldout_r2": dict(zip(S.OUTPUTS, [round(float(v), 4) for v in r2])),
+            "heldout_inside_box": float(inside.mean()),
+            "labeling": {"runs_per_s": n_tr / t_label, "run_steps_per_s": run_steps / t_label, "seconds": t_label},
+            "training": {"seconds": t_fit, "epochs": 600, "final_loss": float(curve[-1])},
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peaks.get("bf16_tflops"),
+                         "unit": "TFLOP/s", "frac": achieved / peaks["bf16_tflops"] if peaks.get("bf16_tflops") else None,
+                         "traffic": None},
+            "e2e": {"value": Q / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": Q * 6 * 4,
+                    "d2h_bytes_per_step": Q * 4 * 4}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -254,6 +324,8 @@ def main():
     ap.add_argument("--sort-every", type=int, default=0, help="steps between particle sorts (0: the library default)")
     ap.add_argument("--ensemble", type=int, default=0,
                     help="time N uneven runs advanced together (pic_ensemble_*) instead of the stage")
+    ap.add_argument("--surrogate", type=int, default=0,
+                    help="label N stage runs, train the stage surrogate on them and time its serving")
     args = ap.parse_args()
 
     from paper_1009_2727_gb300 import workloads as W
@@ -266,6 +338,8 @@ def main():
         return run_reference(args, w)
     if args.ensemble:
         return run_ensemble(args)
+    if args.surrogate:
+        return run_surrogate(args)
 
     import torch
     ws, rank, local = dist_env()

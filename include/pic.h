@@ -155,6 +155,10 @@ typedef struct {
   int32_t gx_lo, gx_hi, gz_lo, gz_hi; /* particle domain in cells */
   int64_t sorts, overflow_chunks;     /* runtime counters */
   double z0;              /* grid origin (moving window) [m] */
+  double trap_gamma_lab;  /* in: a threshold > 0 to use, else 0; out: the threshold used, by default
+                             2 gamma_w, gamma_w = omega_laser / omega_p (0: no laser or plasma) */
+  double trapped_charge;  /* charge of the plasma electrons whose lab-frame gamma exceeds it, per unit
+                             length along y [C/m] */
 } pic_stats;
 
 /* Create a context: validates cfg (coefficient normalisation, shape order,
@@ -284,6 +288,31 @@ int pic_ensemble_sync(pic_ens* ens);
 int pic_ensemble_size(pic_ens* ens);
 pic_ctx* pic_ensemble_member(pic_ens* ens, int index);
 int pic_ensemble_free(pic_ens* ens);
+
+/* ---- Multilayer perceptron for the stage surrogate (no counterpart in the paper) ----
+ * widths[0] -> widths[1] -> ... -> widths[n_layers]; GELU (exact, erf form) after every layer but the
+ * last. Parameters: per layer l = 1..n_layers the weight W_l (widths[l] x widths[l-1], row-major) then
+ * the bias b_l (widths[l]); FP32 master copies updated by AdamW, BF16 copies used by every product;
+ * activations stored in BF16; products accumulate in FP32. Initial weights are uniform in
+ * +-sqrt(6 / fan_in) (half that for the last layer) from a splitmix64 sequence seeded by seed; biases 0.
+ * Device pointers: x (n x widths[0]), t and y (n x widths[n_layers]), FP32 row-major, on the MLP's
+ * stream. pic_mlp_grad returns the mean squared error of the outputs against t and its gradient with
+ * respect to all parameters (host buffers, pic_mlp_param_count floats). pic_mlp_train runs `epochs`
+ * passes of minibatches of `batch` rows in a splitmix64-shuffled order (the remainder of each pass is
+ * skipped) with AdamW (beta 0.9/0.999, eps 1e-8, decoupled weight decay); loss_curve (host, epochs
+ * floats, may be NULL) receives each pass's mean batch loss. Errors: PIC_EINVAL, PIC_ENOMEM, PIC_ECUDA. */
+typedef struct pic_mlp pic_mlp;
+int pic_mlp_create(int n_layers, const int* widths, uint64_t seed, pic_alloc_fn alloc, pic_free_fn free_fn,
+                   void* alloc_user, void* cuda_stream, pic_mlp** out);
+int pic_mlp_free(pic_mlp* mlp);
+int64_t pic_mlp_param_count(pic_mlp* mlp);
+int pic_mlp_get_params(pic_mlp* mlp, float* dst_host);
+int pic_mlp_set_params(pic_mlp* mlp, const float* src_host);
+int pic_mlp_forward(pic_mlp* mlp, const float* x_device, int64_t n, float* y_device);
+int pic_mlp_grad(pic_mlp* mlp, const float* x_device, const float* t_device, int n, float* loss_host,
+                 float* grad_host);
+int pic_mlp_train(pic_mlp* mlp, const float* x_device, const float* t_device, int n, int epochs, int batch,
+                  float lr, float weight_decay, uint64_t seed, float* loss_curve_host);
 
 #ifdef __cplusplus
 }

@@ -29,7 +29,9 @@ EXPORTS = ("pic_init", "pic_load_plasma", "pic_inject_laser", "pic_step", "pic_s
            "pic_free", "pic_get_field", "pic_set_field", "pic_get_particles", "pic_get_stats", "pic_last_error",
            "pic_kernel_launches", "pic_kernel_timing", "pic_get_rho_noalloc", "pic_autotune",
            "pic_ensemble_create", "pic_ensemble_step", "pic_ensemble_sync", "pic_ensemble_size",
-           "pic_ensemble_member", "pic_ensemble_free")
+           "pic_ensemble_member", "pic_ensemble_free",
+           "pic_mlp_create", "pic_mlp_free", "pic_mlp_param_count", "pic_mlp_get_params", "pic_mlp_set_params",
+           "pic_mlp_forward", "pic_mlp_grad", "pic_mlp_train")
 NOALLOC_MAX_NZ = 16384
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -99,6 +101,7 @@ class PicStats(ctypes.Structure):
         ("gx_lo", ctypes.c_int32), ("gx_hi", ctypes.c_int32), ("gz_lo", ctypes.c_int32), ("gz_hi", ctypes.c_int32),
         ("sorts", ctypes.c_int64), ("overflow_chunks", ctypes.c_int64),
         ("z0", ctypes.c_double),
+        ("trap_gamma_lab", ctypes.c_double), ("trapped_charge", ctypes.c_double),
     ]
 
 
@@ -168,6 +171,18 @@ def load(build_if_missing: bool = True):
         L.pic_ensemble_member.argtypes = [vp, ctypes.c_int]
         L.pic_ensemble_member.restype = vp
         L.pic_ensemble_free.argtypes = [vp]
+        _F = ctypes.POINTER(ctypes.c_float)
+        L.pic_mlp_create.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_uint64, ALLOC_FN, FREE_FN,
+                                     vp, vp, ctypes.POINTER(vp)]
+        L.pic_mlp_free.argtypes = [vp]
+        L.pic_mlp_param_count.argtypes = [vp]
+        L.pic_mlp_param_count.restype = ctypes.c_int64
+        L.pic_mlp_get_params.argtypes = [vp, _F]
+        L.pic_mlp_set_params.argtypes = [vp, _F]
+        L.pic_mlp_forward.argtypes = [vp, vp, ctypes.c_int64, vp]
+        L.pic_mlp_grad.argtypes = [vp, vp, vp, ctypes.c_int, _F, _F]
+        L.pic_mlp_train.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_float,
+                                    ctypes.c_float, ctypes.c_uint64, _F]
         L.pic_autotune.argtypes = [ctypes.POINTER(PicConfig), ctypes.POINTER(PicPlasma), ctypes.POINTER(PicLaser),
                                    ctypes.c_int, ALLOC_FN, FREE_FN, vp, vp, ctypes.POINTER(PicTuneResult)]
         _lib = L

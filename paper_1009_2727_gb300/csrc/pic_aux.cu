@@ -314,12 +314,24 @@ __global__ void k_ion_rho(GridP g, const double* ion_x, const double* R, double 
 
 template <class T>
 __global__ void k_stats(GridP g, FieldPtrs<T> f, Particles<T> p, const Ctrl* ctrl, Beam<T> b, double gam, double be,
-                        double* out) {
-  // out: [0] n_e, [1] n_beam_active, [2] sum gamma_lab, [3] sum gamma_lab^2, [4] field energy
+                        double trap, double* out) {
+  // out: [0] n_e, [1] n_beam_active, [2] sum gamma_lab, [3] sum gamma_lab^2, [4] field energy,
+  // [5] weight of the electrons with lab-frame gamma above trap
   const long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const long nthr = (long)gridDim.x * blockDim.x;
-  double ne = 0, na = 0, sg = 0, sg2 = 0, en = 0;
-  for (long j = tid; j < ctrl->count; j += nthr) ne += p.w[j] > T(0) ? 1.0 : 0.0;
+  double ne = 0, na = 0, sg = 0, sg2 = 0, en = 0, wt = 0;
+  for (long j = tid; j < ctrl->count; j += nthr) {
+    const double w = (double)p.w[j];
+    if (!(w > 0.0)) continue;
+    ne += 1.0;
+    if (trap > 0.0) {
+      // boosted-frame momentum (the mixed path stores u_z - u0) -> lab-frame gamma
+      const double ux = p.ux[j], uy = p.uy[j];
+      const double uz = CellPos<T>::value ? (double)g.fr_u0 + (double)p.uz[j] : (double)p.uz[j];
+      const double gp = sqrt(1.0 + (ux * ux + uy * uy + uz * uz) / (kC * kC));
+      if (gam * (gp + be * uz / kC) > trap) wt += w;
+    }
+  }
   for (long j = tid; j < b.n; j += nthr) {
     if ((b.flag[j] & 3) != 3) continue;
     const double ux = b.ux[j], uy = b.uy[j], uz = b.uz[j];
@@ -340,7 +352,7 @@ __global__ void k_stats(GridP g, FieldPtrs<T> f, Particles<T> p, const Ctrl* ctr
     en += 0.5 * (kEps0 * e2 + b2 / mu0) * g.dx * g.dz;
   }
   atomicAdd(&out[0], ne); atomicAdd(&out[1], na); atomicAdd(&out[2], sg); atomicAdd(&out[3], sg2);
-  atomicAdd(&out[4], en);
+  atomicAdd(&out[4], en); atomicAdd(&out[5], wt);
 }
 
 template <class T>
@@ -532,10 +544,10 @@ void launch_ion_rho(const GridP& g, const double* ion_x, const double* R, double
 
 template <class T>
 void launch_stats(const GridP& g, const FieldPtrs<T>& f, Particles<T> p, const Ctrl* ctrl, int cap, Beam<T> b,
-                  double gamma, double beta, double* out, cudaStream_t s) {
+                  double gamma, double beta, double trap, double* out, cudaStream_t s) {
   (void)cap;
   cudaMemsetAsync(out, 0, 8 * sizeof(double), s);
-  k_stats<T><<<304, 256, 0, s>>>(g, f, p, ctrl, b, gamma, beta, out);
+  k_stats<T><<<304, 256, 0, s>>>(g, f, p, ctrl, b, gamma, beta, trap, out);
 }
 
 template <class T>
@@ -586,7 +598,7 @@ void launch_shift_particles(const GridP& g, Particles<T> p, const Ctrl* ctrl, in
                               const double*, double, double, double, T*, int*, cudaStream_t);                     \
   template void launch_rho<T>(const GridP&, Particles<T>, const Ctrl*, int, int, double, double*, cudaStream_t);  \
   template void launch_stats<T>(const GridP&, const FieldPtrs<T>&, Particles<T>, const Ctrl*, int, Beam<T>,       \
-                                double, double, double*, cudaStream_t);                                           \
+                                double, double, double, double*, cudaStream_t);                                           \
   template void launch_shift<T>(const GridP&, T*, T*, int, int, cudaStream_t);                                        \
   template void launch_convert<T>(const T*, double*, const GridP&, cudaStream_t);                                \
   template void launch_convert_back<T>(const double*, T*, const GridP&, cudaStream_t);                           \

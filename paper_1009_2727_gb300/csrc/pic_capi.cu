@@ -816,7 +816,14 @@ struct Sim : SimBase {
 
   int stats(pic_stats* o) {
     set_ptrs_for_step();
-    launch_stats<T>(g, f, P, ctrl, cap, beam, c->hg.gamma, c->hg.beta, stats_buf, c->stream);
+    // trapping threshold (PR-19): twice the wake's Lorentz factor gamma_w = omega_laser / omega_p (lab),
+    // unless the caller asks for another one
+    double trap = o->trap_gamma_lab > 0.0 ? o->trap_gamma_lab : 0.0;
+    if (trap == 0.0 && has_laser && loaded && pl.n0 > 0.0) {
+      const double wp = std::sqrt(pl.n0 * kQe * kQe / (kEps0 * kMe));
+      trap = 2.0 * (2.0 * kPi * kC / lp.lambda0) / wp;
+    }
+    launch_stats<T>(g, f, P, ctrl, cap, beam, c->hg.gamma, c->hg.beta, trap, stats_buf, c->stream);
     double h[8];
     Ctrl hc;
     cudaStreamSynchronize(c->stream);
@@ -833,6 +840,8 @@ struct Sim : SimBase {
     o->gx_lo = g.gx_lo; o->gx_hi = g.gx_hi; o->gz_lo = g.gz_lo; o->gz_hi = g.gz_hi;
     o->sorts = sorts; o->overflow_chunks = hc.overflow_chunks;
     o->z0 = g.z0;
+    o->trap_gamma_lab = trap;
+    o->trapped_charge = kQe * h[5];
     return cudaGetLastError() == cudaSuccess ? PIC_OK : c->fail(PIC_ECUDA, "CUDA error in stats");
   }
 

@@ -299,7 +299,7 @@ void launch_rho(const GridP& g, Particles<T> p, const Ctrl* ctrl, int cap, int o
 void launch_ion_rho(const GridP& g, const double* ion_x, const double* R, double coef, double* rho, cudaStream_t s);
 template <class T>
 void launch_stats(const GridP& g, const FieldPtrs<T>& f, Particles<T> p, const Ctrl* ctrl, int cap, Beam<T> b,
-                  double gamma, double beta, double* out, cudaStream_t s);
+                  double gamma, double beta, double trap, double* out, cudaStream_t s);
 template <class T>
 void launch_shift(const GridP& g, T* arr, T* tmp, int sh, int comp, cudaStream_t s);
 void launch_shift_chunks(Chunk* chunks, Ctrl* ctrl, int sh, int chunk_cap, cudaStream_t s);

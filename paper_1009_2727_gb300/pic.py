@@ -225,10 +225,12 @@ class Simulation:
         out["active"] = (fl[:m] & 2) != 0
         return out
 
-    def stats(self) -> dict:
+    def stats(self, trap_gamma_lab: float = 0.0) -> dict:
+        """diagnostics; trap_gamma_lab > 0 replaces the default trapping threshold (twice gamma_w)"""
         s = capi.PicStats()
         s.struct_size = ctypes.sizeof(capi.PicStats)
         s.version = capi.API_VERSION
+        s.trap_gamma_lab = float(trap_gamma_lab)
         self._check(self.L.pic_get_stats(self.h, ctypes.byref(s)), "pic_get_stats")
         return {k: getattr(s, k) for k, _ in capi.PicStats._fields_ if k not in ("struct_size", "version")}
 

@@ -131,7 +131,7 @@ def ensemble_2d(n: int = 64, seed: int = 4) -> list:
         nx = int(rng.integers(8, 17)) * 16
         g = float(rng.uniform(5.0, 30.0))
         n0 = float(10.0 ** rng.uniform(23.0, 25.0))
-        a0 = float(rng.uniform(0.5, 2.5))
+        a0 = float(rng.uniform(0.5, 2.0))
         w0 = float(rng.uniform(6e-6, 25e-6))
         tau = float(rng.uniform(20e-15, 60e-15))
         ppc = int(rng.choice([2, 4]))
@@ -149,5 +149,72 @@ def ensemble_2d(n: int = 64, seed: int = 4) -> list:
                        "ppc_x": ppc, "ppc_z": ppc, "ions": 1},
             "laser": {"lambda0": LAMBDA0, "a0": a0, "w0": w0, "tau_fwhm": tau, "t_peak": 1.5 * tau,
                       "x_center": 0.5 * nx * dx, "phase": 0.0, "z_antenna": 34 * dz_b, "beta_s": 0.0},
+        })
+    return runs
+
+
+def surrogate_runs(n: int, seed: int) -> list:
+    """Stage runs for the surrogate's training and held-out sets, sampled from a seeded generator over
+    (log10 n0 in [23.5, 25] m^-3, a0 in [0.5, 2], w0 in [8, 20] um, tau in [20, 40] fs,
+    stage length L in [0.2, 0.8] mm (lab), gamma_boost in [4, 6]).
+
+    Reduced resolution so that thousands of runs fit in minutes: lambda/dz = 16 in the lab, dx = 1.5 um
+    (dz <= dx in the boosted frame up to gamma 7.5), 1600 (z) x 96 (x) cells, 2 x 2 particles per cell, CK
+    at c dt = dz/sqrt(2) (the paper's low-instability step), theta = 0.1, four passes + compensation,
+    cubic shapes, mixed precision, fixed grid. A 256-particle lab test beam at the wake's Lorentz factor
+    starts half a plasma wavelength behind the laser peak and becomes active when it crosses the plasma
+    entrance; the antenna, at rest, sits far enough from the lower z edge that this crossing (which the
+    boost moves back by gamma beta lambda_p / 2) lies inside the box. The plasma of length L starts far
+    enough beyond the antenna that the whole pulse has left the antenna before the plasma, streaming
+    towards it, arrives (the antenna stays in vacuum while it emits). Each run carries its inputs under
+    "inputs", its step count under "steps" (the laser's tail has then left the plasma's end) and under
+    "emit_steps" the step at which the antenna has finished emitting."""
+    rng = np.random.default_rng(seed)
+    c = 299792458.0
+    qe, me, eps0 = 1.602176634e-19, 9.1093837015e-31, 8.8541878128e-12
+    runs = []
+    for i in range(n):
+        ln0 = float(rng.uniform(23.5, 25.0))
+        a0 = float(rng.uniform(0.5, 2.0))
+        w0 = float(rng.uniform(8e-6, 20e-6))
+        tau = float(rng.uniform(20e-15, 40e-15))
+        L = float(rng.uniform(0.2e-3, 0.8e-3))
+        g = float(rng.uniform(4.0, 6.0))
+        n0 = 10.0 ** ln0
+        beta = np.sqrt(1.0 - 1.0 / g ** 2)
+        dz_lab = LAMBDA0 / 16.0
+        dz_b = (1.0 + beta) * g * dz_lab
+        nx, nz, dx = 96, 1600, 1.5e-6
+        dt = dz_b / (np.sqrt(2.0) * c)
+        t_peak = 1.6 * tau
+        wp = np.sqrt(n0 * qe * qe / (eps0 * me))
+        lam_p = 2 * np.pi * c / wp
+        gw = (2 * np.pi * c / LAMBDA0) / wp
+        z_ant = (48 + np.ceil(g * beta * (0.5 * lam_p + 4e-6) / dz_b)) * dz_b
+        # the antenna at rest emits for (1 + beta) gamma 2 t_peak; the plasma closes in at beta c
+        t_emit = (1.0 + beta) * g * 2.0 * t_peak
+        gap = (np.ceil(beta * c * t_emit / dz_b) + 24) * dz_b
+        z_start_lab = g * (z_ant + gap)
+        # laser peak in the lab at t = 0 (emitted at t' = (1+beta) gamma t_peak by the antenna at rest)
+        z_peak0 = z_ant / ((1.0 + beta) * g) - c * t_peak
+        x, z, ux, uy, uz = lab_beam(256, seed=seed * 100003 + i, gamma_b=gw, R_b=1e-6, L_b=0.5e-6,
+                                    z_c=z_peak0 - 0.5 * lam_p, x_c=0.5 * nx * dx)
+        # the pulse's tail leaves the antenna at t_emit; the plasma's end (gap + ramp + L/gamma beyond the
+        # antenna at t = 0, moving at -beta c) then meets it after the closing distance / (1 + beta) c
+        z_end = gap + (20e-6 + L) / g
+        steps = int((t_emit + (z_end - beta * c * t_emit) / ((1.0 + beta) * c)) / dt) + 50
+        runs.append({
+            "name": f"surrogate_{seed}_{i}", "inputs": [ln0, a0, w0 * 1e6, tau * 1e15, L * 1e3, g],
+            "steps": steps, "emit_steps": int(t_emit / dt) + 1, "lambda_p": lam_p, "gamma_w": gw,
+            "nx": nx, "nz": nz, "dz_lab": dz_lab, "dx": dx, "gamma_boost": g, "courant": 0.99, "dt": dt,
+            "solver": SOLVERS["ck"], "theta": 0.1,
+            "pml_cells": 16, "pml_sigma_max": 4.0, "pml_delta": 5.0, "pml_power": 2.0, "pml_xi_exp": 1,
+            "filter_passes": 4, "filter_stride": 1, "filter_compensate": 1, "filter_J": 1, "filter_gather": 1,
+            "order": 3, "particle_guard": -1, "moving_window": 0, "window_beta": 0.0, "precision": "mixed",
+            "plasma": {"n0": n0, "z_start_lab": z_start_lab, "ramp_lab": 20e-6, "length_lab": L,
+                       "ppc_x": 2, "ppc_z": 2, "ions": 1},
+            "laser": {"lambda0": LAMBDA0, "a0": a0, "w0": w0, "tau_fwhm": tau, "t_peak": t_peak,
+                      "x_center": 0.5 * nx * dx, "phase": 0.0, "z_antenna": z_ant, "beta_s": 0.0},
+            "beam": {"x": x, "z": z, "ux": ux, "uy": uy, "uz": uz, "t_lab": 0.0, "z_plane_lab": z_start_lab},
         })
     return runs

@@ -111,6 +111,30 @@ def test_parity_stage_physics_small_box_fp64(Sim, orc):
     g, o = run_pair(Sim, orc, w, 100)
     check_fields(g, o, TOL64)
     check_particles(g, o, TOL64)
+    # trapped-charge diagnostic: plasma electrons above a lab-frame Lorentz factor, lab gamma = gamma_b
+    # (gamma' + beta_b u'_z / c). The electrons the pulse has not reached sit at lab gamma 1 to rounding, so
+    # the threshold is taken in a gap between two of the disturbed electrons near their median: no electron
+    # lies within rounding of it and the count is exact.
+    po = o.particles(0)
+    po = {k: v[po["alive"]] for k, v in po.items()}
+    c, qe = 299792458.0, 1.602176634e-19
+    gb = float(w["gamma_boost"])
+    bb = np.sqrt(1.0 - 1.0 / gb ** 2)
+    gp = np.sqrt(1.0 + (po["ux"] ** 2 + po["uy"] ** 2 + po["uz"] ** 2) / c ** 2)
+    glab = gb * (gp + bb * po["uz"] / c)
+    s_ = np.sort(glab[glab > 1.0 + 1e-9])
+    assert s_.size > 1000
+    i = s_.size // 2 + int(np.argmax(np.diff(s_[s_.size // 2:]) > 1e-9 * s_[s_.size // 2:-1]))
+    thr = 0.5 * (s_[i] + s_[i + 1])
+    assert s_[i + 1] - s_[i] > 1e-9 * thr
+    ref = qe * po["w"][glab > thr].sum()
+    st = g.stats(trap_gamma_lab=thr)
+    assert st["trap_gamma_lab"] == thr
+    assert ref > 100 * qe * po["w"].max()
+    assert st["trapped_charge"] == pytest.approx(ref, rel=1e-12)
+    me, eps0 = 9.1093837015e-31, 8.8541878128e-12
+    wp = np.sqrt(w["plasma"]["n0"] * qe * qe / (eps0 * me))
+    assert g.stats()["trap_gamma_lab"] == pytest.approx(2.0 * (2.0 * np.pi * c / w["laser"]["lambda0"]) / wp, rel=1e-12)
 
 
 def test_parity_2d_mixed(Sim, orc):

@@ -1,0 +1,137 @@
+"""Stage surrogate on the GPU: the library's BF16 multilayer perceptron against the FP64 oracle of the same
+network (oracle/mlp.py), its training, and a small end-to-end surrogate over stage runs.
+
+Tolerances follow from BF16 (8 significant bits, unit roundoff 2^-9 ~ 2e-3): the GPU multiplies BF16
+weights (the oracle is given the same BF16-rounded weights, FP32 biases) by BF16-stored inputs and
+activations and accumulates in FP32, so each layer's output carries a relative error of a few 2^-9;
+over three layers the outputs stay within 2e-2 of the largest output and the gradient within 3e-2 in
+relative L2 norm.
+"""
+import numpy as np
+import pytest
+
+from paper_1009_2727_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1009_2727_gb300 import surrogate
+    return surrogate
+
+
+def bf16(a):
+    """round FP32 values to the nearest BF16 (ties to even), returned as FP64"""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def bf16_weights(p, widths):
+    """the weights rounded to BF16, the biases kept in FP32, in the flat layout"""
+    q = np.asarray(p, dtype=np.float64).copy()
+    o = 0
+    for l in range(1, len(widths)):
+        nw = widths[l] * widths[l - 1]
+        q[o:o + nw] = bf16(p[o:o + nw])
+        o += nw + widths[l]
+    return q
+
+
+def smooth_target(x):
+    return np.stack([np.sin(x[:, 0]) + 0.5 * x[:, 1] * x[:, 2], np.cos(x[:, 3] - x[:, 4]),
+                     np.tanh(x[:, 5] + x[:, 0]), x[:, 1] ** 2 - 0.3 * x[:, 4]], axis=1)
+
+
+def test_bf16_rounding_helper():
+    assert bf16(np.float32(1.0 + 2.0 ** -8))[()] == 1.0                   # tie to even (down)
+    assert bf16(np.float32(1.0 + 3 * 2.0 ** -8))[()] == 1.0 + 2.0 ** -6   # tie to even (up)
+    assert bf16(np.float32(1.0 + 2.0 ** -8 + 2.0 ** -20))[()] == 1.0 + 2.0 ** -7
+
+
+@pytest.mark.parametrize("widths,n", [([6, 96, 80, 4], 150), ([6, 256, 256, 256, 4], 333), ([3, 1, 5], 1)])
+def test_mlp_forward_and_gradient_match_oracle(S, widths, n):
+    """several 64-row and 64-column tiles with ragged tails, the surrogate's own shape, and a degenerate
+    one-unit layer with a single sample"""
+    from oracle import mlp as ref
+    rng = np.random.default_rng(11)
+    net = S.MLP(widths, seed=5)
+    p = net.get_params().astype(np.float64)
+    p += rng.normal(0, 0.05, p.size)          # non-zero biases
+    net.set_params(p)
+    p32 = net.get_params()
+    x = rng.normal(0, 1, (n, widths[0]))
+    t = rng.normal(0, 1, (n, widths[-1]))
+    pq = bf16_weights(p32, widths)
+    y_ref, _ = ref.forward(pq, widths, bf16(x))
+    y = net.forward(x)
+    assert np.abs(y - y_ref).max() <= 2e-2 * np.abs(y_ref).max()
+    loss_ref, g_ref = ref.loss_and_grad(pq, widths, bf16(x), t)
+    loss, g = net.grad(x, t)
+    assert loss == pytest.approx(loss_ref, rel=2e-2)
+    assert np.linalg.norm(g - g_ref) <= 3e-2 * np.linalg.norm(g_ref)
+    net.close()
+
+
+def test_mlp_forward_over_chunks_matches_rows(S):
+    """a batch larger than one 65536-row chunk with a ragged last chunk: sampled rows against the oracle"""
+    from oracle import mlp as ref
+    widths = [6, 64, 64, 4]
+    net = S.MLP(widths, seed=2)
+    rng = np.random.default_rng(3)
+    x = rng.normal(0, 1, (65536 + 777, 6))
+    y = net.forward(x)
+    pq = bf16_weights(net.get_params(), widths)
+    rows = np.concatenate([rng.choice(65536, 200, replace=False), 65536 + np.arange(777)])
+    y_ref, _ = ref.forward(pq, widths, bf16(x[rows]))
+    assert np.abs(y[rows] - y_ref).max() <= 2e-2 * np.abs(y_ref).max()
+    net.close()
+
+
+def test_mlp_training_fits_and_is_deterministic(S):
+    rng = np.random.default_rng(7)
+    x = rng.uniform(-1.5, 1.5, (2048, 6))
+    t = smooth_target(x)
+    xh = rng.uniform(-1.5, 1.5, (512, 6))
+    curves, params = [], []
+    for _ in range(2):
+        net = S.MLP([6, 128, 128, 4], seed=1)
+        curves.append(net.train(x, t, epochs=120, batch=64, lr=2e-3, weight_decay=1e-4, seed=9))
+        params.append(net.get_params())
+        err = np.sqrt(np.mean((net.forward(xh) - smooth_target(xh)) ** 2))
+        net.close()
+    c = curves[0]
+    assert np.all(np.isfinite(c)) and c[-1] < 0.05 * c[0], (c[0], c[-1])
+    assert err < 0.1 * np.sqrt(np.mean(smooth_target(xh) ** 2))
+    # the sample order and the products are deterministic: same seed, same parameters
+    assert np.array_equal(params[0], params[1])
+
+
+def test_stage_surrogate_end_to_end(S):
+    """a handful of stage runs through the ensemble: finite, plausible labels; the fitted surrogate
+    reproduces its training set and flags a query outside the sampled box"""
+    runs = W.surrogate_runs(6, seed=21)
+    X, Y, ok = S.stage_labels(runs, batch=6)
+    assert np.all(np.isfinite(Y)) and ok.sum() >= 5, ok
+    X, Y = X[ok], Y[ok]
+    runs = [r for r, v in zip(runs, ok) if v]
+    c, qe, me, eps0 = 299792458.0, 1.602176634e-19, 9.1093837015e-31, 8.8541878128e-12
+    for r, y in zip(runs, Y):
+        n0 = 10.0 ** r["inputs"][0]
+        E0 = me * c * np.sqrt(n0 * qe * qe / (eps0 * me)) / qe      # cold wave-breaking field
+        assert 1e-3 < y[0] * 1e9 / E0 < 3.0, (r["inputs"], y)
+        assert -0.05 <= y[3] <= 1.0, (r["inputs"], y)
+        assert 0.0 <= y[2] < 100.0
+    sur = S.Surrogate(hidden=(64, 64), seed=3)
+    curve = sur.fit(X, Y, epochs=1500, batch=6, lr=3e-3, weight_decay=0.0)
+    assert curve[-1] < 0.05 * curve[0]
+    pred, inside = sur.predict(X)
+    assert inside.all()
+    assert np.all(np.abs(pred - Y) <= 0.25 * Y.std(0) + 1e-9)
+    q = X[:1].copy()
+    q[0, 5] = 20.0            # a boost outside the sampled range
+    assert not sur.predict(q)[1][0]

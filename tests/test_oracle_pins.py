@@ -634,3 +634,28 @@ def test_boosted_and_lab_frames_agree_on_the_wake(orc, lab_wake):
     ez_boost, _ = _wake_behind_laser(s, w["nx"], lp, sg)
     assert ez_boost == pytest.approx(lab_wake[0], rel=0.04)
     assert ez_boost == pytest.approx(ez_lin, rel=0.05)
+
+
+# ---------------------------------------------------------------------------
+# Surrogate network (CPU reference of the library's MLP): its analytic gradient equals central finite
+# differences of its loss, and GELU matches its definition z Phi(z).
+def test_mlp_reference_gradient_matches_finite_differences():
+    from oracle import mlp
+    rng = np.random.default_rng(5)
+    widths = [3, 7, 5, 2]
+    npar = sum(widths[l] * widths[l - 1] + widths[l] for l in range(1, len(widths)))
+    p = rng.normal(0.0, 0.7, npar)
+    x = rng.normal(0.0, 1.0, (9, 3))
+    t = rng.normal(0.0, 1.0, (9, 2))
+    loss, g = mlp.loss_and_grad(p, widths, x, t)
+    h = 1e-6
+    fd = np.empty(npar)
+    for i in range(npar):
+        e = np.zeros(npar)
+        e[i] = h
+        fd[i] = (mlp.loss_and_grad(p + e, widths, x, t)[0] - mlp.loss_and_grad(p - e, widths, x, t)[0]) / (2 * h)
+    assert np.max(np.abs(g - fd)) <= 1e-7 * max(1.0, np.max(np.abs(fd)))
+    # GELU = z Phi(z), Phi the standard normal distribution function
+    z = np.linspace(-4, 4, 17)
+    phi = np.array([0.5 * (1 + math.erf(v / math.sqrt(2))) for v in z])
+    assert np.allclose(mlp.gelu(z), z * phi, rtol=0, atol=1e-15)
