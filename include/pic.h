@@ -308,7 +308,7 @@ int pic_mlp_free(pic_mlp* mlp);
 int64_t pic_mlp_param_count(pic_mlp* mlp);
 int pic_mlp_get_params(pic_mlp* mlp, float* dst_host);
 int pic_mlp_set_params(pic_mlp* mlp, const float* src_host);
-int pic_mlp_forward(pic_mlp* mlp, const float* x_device, int64_t n, float* y_device);
+int pic_mlp_infer(pic_mlp* mlp, const float* x_device, int64_t n, float* y_device);
 int pic_mlp_grad(pic_mlp* mlp, const float* x_device, const float* t_device, int n, float* loss_host,
                  float* grad_host);
 int pic_mlp_train(pic_mlp* mlp, const float* x_device, const float* t_device, int n, int epochs, int batch,

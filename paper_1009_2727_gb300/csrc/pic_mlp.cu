@@ -357,7 +357,7 @@ int pic_mlp_set_params(pic_mlp* m, const float* src) {
   return cudaStreamSynchronize(m->s) == cudaSuccess ? PIC_OK : PIC_ECUDA;
 }
 
-int pic_mlp_forward(pic_mlp* m, const float* x, int64_t n, float* y) {
+int pic_mlp_infer(pic_mlp* m, const float* x, int64_t n, float* y) {
   if (!m || !x || !y || n < 0) return PIC_EINVAL;
   const int chunk = 65536;
   for (int64_t r0 = 0; r0 < n; r0 += chunk) {

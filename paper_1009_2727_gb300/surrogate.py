@@ -4,10 +4,12 @@ forward, backward and optimiser steps run in the library's pic_mlp_* kernels, th
 
 Inputs (6): log10 n0 [m^-3], a0, w0 [um], tau [fs], stage length L [mm], gamma_boost.
 Outputs (4), measured on each run:
-  wake     peak on-axis |E_z| during the run [GV/m]
-  gain     lab-frame energy gain of the test beam at the end of the stage [MeV]
-  spread   relative rms energy spread of the test beam at the end of the stage [%]
-  depleted fraction of the peak field energy (computational frame) gone by the end of the stage
+  gain        lab-frame energy gain of the test beam at the end of the stage [MeV]
+  log_spread  log10(0.1 + relative rms energy spread of the test beam at the end [%]); the spread spans
+              three decades, set mostly by dephasing at high density
+  trapped     charge of the plasma electrons above the wake's Lorentz factor gamma_w [pC/um of y]
+  depleted    fraction of the peak field energy (computational frame) gone by the end of the stage; the
+              depletion length follows as L / depleted (depletion_length)
 Runs that went numerically unstable are left out of the training set (stage_labels' valid mask).
 Queries outside the training inputs' axis-aligned box are flagged for a PIC run instead.
 """
@@ -21,7 +23,7 @@ from . import capi
 from .pic import Ensemble, PicError, torch_allocator
 
 ME_MEV = 0.51099895000
-OUTPUTS = ("wake", "gain", "spread", "depleted")
+OUTPUTS = ("gain", "log_spread", "trapped", "depleted")
 
 
 class MLP:
@@ -59,13 +61,13 @@ class MLP:
     def forward(self, x) -> np.ndarray:
         xd, xp = self._dev(x)
         y = self.torch.empty((xd.shape[0], self.widths[-1]), dtype=self.torch.float32, device="cuda")
-        self._check(self.L.pic_mlp_forward(self.h, xp, xd.shape[0], ctypes.c_void_p(y.data_ptr())))
+        self._check(self.L.pic_mlp_infer(self.h, xp, xd.shape[0], ctypes.c_void_p(y.data_ptr())))
         self.torch.cuda.synchronize()
         return y.cpu().numpy()
 
     def forward_device(self, x_ptr: int, n: int, y_ptr: int):
         """outputs of n rows at device address x_ptr into device address y_ptr, on the MLP's stream"""
-        self._check(self.L.pic_mlp_forward(self.h, ctypes.c_void_p(x_ptr), int(n), ctypes.c_void_p(y_ptr)))
+        self._check(self.L.pic_mlp_infer(self.h, ctypes.c_void_p(x_ptr), int(n), ctypes.c_void_p(y_ptr)))
 
     def grad(self, x, t):
         xd, xp = self._dev(x)
@@ -103,14 +105,15 @@ class MLP:
 
 def stage_labels(runs: list, batch: int = 64, every: int = 50):
     """Run the stage workloads (workloads.surrogate_runs) in ensembles of `batch` runs of similar length and
-    measure the four outputs of each at its own step count. The on-axis wake and the field energy are
-    sampled every `every` steps; the depletion is one minus the final field energy over the largest sample.
+    measure the four outputs of each at its own step count. The field energy is sampled every `every`
+    steps; the depletion is one minus the final field energy over the largest sample; the trapped charge
+    counts the plasma electrons above the wake's Lorentz factor gamma_w.
     Returns (inputs n x 6, outputs n x 4, valid n): a run is valid when its test beam entered the plasma
     and its field energy did not grow after the antenna stopped emitting (at most twice the energy then:
     with no source left, a larger growth is a numerical instability, not physics)."""
     order = sorted(range(len(runs)), key=lambda i: runs[i]["steps"])
     X = np.zeros((len(runs), 6))
-    Y = np.zeros((len(runs), 4))
+    Y = np.zeros((len(runs), len(OUTPUTS)))
     ok = np.zeros(len(runs), dtype=bool)
     for b0 in range(0, len(order), batch):
         ids = order[b0:b0 + batch]
@@ -118,7 +121,6 @@ def stage_labels(runs: list, batch: int = 64, every: int = 50):
         ens = Ensemble(part)
         marks = set(range(every, max(r["steps"] for r in part), every))
         marks |= {r["steps"] for r in part} | {r["emit_steps"] for r in part}
-        wake = np.zeros(len(part))
         wmax = np.zeros(len(part))
         w_emit = np.zeros(len(part))
         done = 0
@@ -129,9 +131,7 @@ def stage_labels(runs: list, batch: int = 64, every: int = 50):
             for j, (r, m) in enumerate(zip(part, ens.members)):
                 if done > r["steps"]:
                     continue
-                ez = m.field(2)[r["nx"] // 2]
-                wake[j] = max(wake[j], float(np.abs(ez).max()))
-                st = m.stats()
+                st = m.stats(trap_gamma_lab=r["gamma_w"])
                 wmax[j] = max(wmax[j], st["field_energy"])
                 if done == r["emit_steps"]:
                     w_emit[j] = st["field_energy"]
@@ -140,12 +140,18 @@ def stage_labels(runs: list, batch: int = 64, every: int = 50):
                     gain = (st["beam_gamma_lab"] - r["gamma_w"]) * ME_MEV if active else 0.0
                     dep = 1.0 - st["field_energy"] / wmax[j] if wmax[j] > 0 else 0.0
                     X[ids[j]] = r["inputs"]
-                    spread = 100.0 * st["beam_spread"] if active else 0.0
-                    Y[ids[j]] = [wake[j] * 1e-9, gain, spread, dep]
+                    spread = np.log10(0.1 + 100.0 * st["beam_spread"]) if active else -1.0
+                    Y[ids[j]] = [gain, spread, st["trapped_charge"] * 1e6, dep]
                     ok[ids[j]] = bool(active and np.isfinite(Y[ids[j]]).all()
                                       and st["field_energy"] <= 2.0 * w_emit[j])
         ens.close()
     return X, Y, ok
+
+
+def depletion_length(X, Y):
+    """pump-depletion length [mm] implied by a depleted fraction over the stage length (linear in L)"""
+    f = np.asarray(Y)[:, OUTPUTS.index("depleted")]
+    return np.asarray(X)[:, 4] / np.maximum(f, 1e-6)
 
 
 class Surrogate:
