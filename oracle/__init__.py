@@ -5,9 +5,10 @@ arm of ``bench.py`` may import this package. The product path (the CUDA
 library behind ``include/pic.h`` and its Python binding) never imports it, and
 this package imports nothing from the product.
 
-``pic_oracle.c`` restates the method of Vay et al., "Modeling laser wakefield
-accelerators in a Lorentz boosted frame" (arXiv:1009.2727) in plain double
-precision loops; this module builds it with gcc and exposes it through ctypes.
+``pic_oracle.c`` (2-1/2D) and ``pic_oracle3d.c`` (3D) restate the method of
+Vay et al., "Modeling laser wakefield accelerators in a Lorentz boosted frame"
+(arXiv:1009.2727) in plain double precision loops; this module builds them
+with gcc into one library and exposes it through ctypes.
 ``boost.py`` holds the paper's analytic frame/speed-up formulas (Sec. 2).
 """
 from __future__ import annotations
@@ -22,7 +23,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liboracle.so")
-_SRC = os.path.join(_HERE, "pic_oracle.c")
+_SRCS = [os.path.join(_HERE, "pic_oracle.c"), os.path.join(_HERE, "pic_oracle3d.c")]
 _lock = threading.Lock()
 _lib = None
 
@@ -32,13 +33,13 @@ COMPONENTS = ("Ex", "Ey", "Ez", "Bx", "By", "Bz", "Jx", "Jy", "Jz")
 
 
 def build(force: bool = False) -> str:
-    """Compile pic_oracle.c into oracle/_build/liboracle.so (plain gcc, no FMA contraction)."""
+    """Compile the oracle sources into oracle/_build/liboracle.so (plain gcc, no FMA contraction)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(_SRC):
+    if not force and os.path.exists(_SO) and all(os.path.getmtime(_SO) >= os.path.getmtime(f) for f in _SRCS):
         return _SO
     tmp = _SO + f".{os.getpid()}.tmp"
     cmd = ["gcc", "-std=c99", "-O2", "-fPIC", "-shared", "-ffp-contract=off",
-           "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+           "-fno-fast-math", "-o", tmp, *_SRCS, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _SO)
     return _SO
@@ -71,6 +72,34 @@ class _Laser(ctypes.Structure):
     _fields_ = [("lambda0", ctypes.c_double), ("a0", ctypes.c_double), ("w0", ctypes.c_double),
                 ("tau_fwhm", ctypes.c_double), ("t_peak", ctypes.c_double), ("x_center", ctypes.c_double),
                 ("phase", ctypes.c_double), ("z_antenna", ctypes.c_double), ("beta_s", ctypes.c_double)]
+
+
+class _Config3(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("dz_lab", ctypes.c_double), ("dx", ctypes.c_double), ("dy", ctypes.c_double),
+        ("gamma_boost", ctypes.c_double), ("courant", ctypes.c_double), ("dt_override", ctypes.c_double),
+        ("ck_alpha", ctypes.c_double), ("ck_beta", ctypes.c_double), ("ck_gamma", ctypes.c_double),
+        ("theta", ctypes.c_double),
+        ("pml_cells", ctypes.c_int), ("pml_sigma_max", ctypes.c_double), ("pml_delta", ctypes.c_double),
+        ("pml_power", ctypes.c_double), ("pml_xi_exp", ctypes.c_int),
+        ("filter_passes", ctypes.c_int), ("filter_stride", ctypes.c_int), ("filter_compensate", ctypes.c_int),
+        ("filter_J", ctypes.c_int), ("filter_gather", ctypes.c_int),
+        ("order", ctypes.c_int), ("particle_guard", ctypes.c_int),
+        ("periodic_x", ctypes.c_int), ("periodic_y", ctypes.c_int), ("periodic_z", ctypes.c_int),
+    ]
+
+
+class _Plasma3(ctypes.Structure):
+    _fields_ = [("n0", ctypes.c_double), ("z_start_lab", ctypes.c_double), ("ramp_lab", ctypes.c_double),
+                ("length_lab", ctypes.c_double), ("ppc_x", ctypes.c_int), ("ppc_y", ctypes.c_int),
+                ("ppc_z", ctypes.c_int), ("ions", ctypes.c_int)]
+
+
+class _Laser3(ctypes.Structure):
+    _fields_ = [("lambda0", ctypes.c_double), ("a0", ctypes.c_double), ("w0", ctypes.c_double),
+                ("tau_fwhm", ctypes.c_double), ("t_peak", ctypes.c_double), ("x_center", ctypes.c_double),
+                ("y_center", ctypes.c_double), ("phase", ctypes.c_double), ("z_antenna", ctypes.c_double)]
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -120,6 +149,27 @@ def lib():
             L.orc_cfl_3d.argtypes = [ctypes.c_double] * 7
             L.orc_filter_line.argtypes = [_D, _D, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int]
             L.orc_boris.argtypes = [_D, _D, _D, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+            vp = ctypes.c_void_p
+            L.o3_create.restype = vp
+            L.o3_create.argtypes = [ctypes.POINTER(_Config3)]
+            L.o3_destroy.argtypes = [vp]
+            L.o3_step.argtypes = [vp, ctypes.c_int]
+            L.o3_load_plasma.argtypes = [vp, ctypes.POINTER(_Plasma3)]
+            L.o3_set_laser.argtypes = [vp, ctypes.POINTER(_Laser3)]
+            L.o3_set_beam.argtypes = [vp, ctypes.c_long, _D, _D, _D, _D, _D, _D, ctypes.c_double, ctypes.c_double]
+            L.o3_info.argtypes = [vp, _D]
+            for f in ("o3_get_field", "o3_set_field", "o3_get_gather_field", "o3_filter_field"):
+                getattr(L, f).argtypes = [vp, ctypes.c_int, _D]
+            L.o3_num_particles.restype = ctypes.c_long
+            L.o3_num_particles.argtypes = [vp, ctypes.c_int]
+            L.o3_get_particles.argtypes = [vp, ctypes.c_int] + [_D] * 7 + [ctypes.POINTER(ctypes.c_uint32),
+                                                                            ctypes.POINTER(ctypes.c_int)]
+            L.o3_set_particles.argtypes = [vp, ctypes.c_int, ctypes.c_long] + [_D] * 7
+            L.o3_rho.argtypes = [vp, _D]
+            L.o3_diag.argtypes = [vp, _D]
+            L.o3_btd_set.argtypes = [vp, ctypes.c_int, _D, _D]
+            L.o3_btd_get.argtypes = [vp, _D, ctypes.POINTER(ctypes.c_int)]
+            L.o3_deposit_one.argtypes = [vp] + [ctypes.c_double] * 7
             _lib = L
     return _lib
 
@@ -316,3 +366,148 @@ class Sim:
         r = np.zeros((self.nx + 1) * (self.nz + 1))
         self.L.orc_rho_one(self.h, _p(r), x, z, qw)
         return r.reshape(self.nx + 1, self.nz + 1)
+
+
+# ----------------------------------------------------------------------------
+# 3D
+def _mk_config3(w: dict) -> _Config3:
+    c = _Config3()
+    c.nx, c.ny, c.nz = int(w["nx"]), int(w["ny"]), int(w["nz"])
+    c.dz_lab, c.dx, c.dy = float(w["dz_lab"]), float(w["dx"]), float(w["dy"])
+    c.gamma_boost = float(w.get("gamma_boost", 1.0))
+    c.courant = float(w.get("courant", 0.9))
+    c.dt_override = float(w.get("dt", 0.0) or 0.0)
+    a, b, g = w.get("solver", (1.0, 0.0, 0.0))
+    c.ck_alpha, c.ck_beta, c.ck_gamma = float(a), float(b), float(g)
+    c.theta = float(w.get("theta", 0.0))
+    c.pml_cells = int(w.get("pml_cells", 0))
+    c.pml_sigma_max = float(w.get("pml_sigma_max", 4.0))
+    c.pml_delta = float(w.get("pml_delta", 5.0))
+    c.pml_power = float(w.get("pml_power", 2.0))
+    c.pml_xi_exp = int(w.get("pml_xi_exp", 1))
+    c.filter_passes = int(w.get("filter_passes", 0))
+    c.filter_stride = int(w.get("filter_stride", 1))
+    c.filter_compensate = int(w.get("filter_compensate", 0))
+    c.filter_J = int(w.get("filter_J", 0))
+    c.filter_gather = int(w.get("filter_gather", 0))
+    c.order = int(w.get("order", 3))
+    c.particle_guard = int(w.get("particle_guard", -1))
+    c.periodic_x = int(w.get("periodic_x", 0))
+    c.periodic_y = int(w.get("periodic_y", 0))
+    c.periodic_z = int(w.get("periodic_z", 0))
+    return c
+
+
+class Sim3:
+    """One 3D oracle simulation built from a 3D workload dict (nx, ny, nz, dx, dy, ...)."""
+
+    def __init__(self, w: dict):
+        self.L = lib()
+        self.w = dict(w)
+        self._cfg = _mk_config3(w)
+        self.h = self.L.o3_create(ctypes.byref(self._cfg))
+        info = self.info()
+        self.nx, self.ny, self.nz = int(w["nx"]), int(w["ny"]), int(w["nz"])
+        self.shape = (self.nx + 1, self.ny + 1, self.nz + 1)
+        self.dx, self.dy, self.dz, self.dt = info["dx"], info["dy"], info["dz"], info["dt"]
+        if w.get("plasma"):
+            p = w["plasma"]
+            pl = _Plasma3(float(p["n0"]), float(p.get("z_start_lab", 0.0)), float(p.get("ramp_lab", 0.0)),
+                          float(p.get("length_lab", 0.0)), int(p["ppc_x"]), int(p["ppc_y"]), int(p["ppc_z"]),
+                          int(p.get("ions", 1)))
+            self.L.o3_load_plasma(self.h, ctypes.byref(pl))
+        if w.get("beam"):
+            b = w["beam"]
+            self.set_beam(b["x"], b["y"], b["z"], b["ux"], b["uy"], b["uz"], b["t_lab"], b["z_plane_lab"])
+        if w.get("laser"):
+            l = w["laser"]
+            la = _Laser3(float(l["lambda0"]), float(l["a0"]), float(l["w0"]), float(l["tau_fwhm"]),
+                         float(l.get("t_peak", 0.0)), float(l.get("x_center", 0.5 * self.nx * self.dx)),
+                         float(l.get("y_center", 0.5 * self.ny * self.dy)), float(l.get("phase", 0.0)),
+                         float(l["z_antenna"]))
+            self.L.o3_set_laser(self.h, ctypes.byref(la))
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            self.L.o3_destroy(h)
+            self.h = None
+
+    def info(self) -> dict:
+        o = np.zeros(15)
+        self.L.o3_info(self.h, _p(o))
+        keys = ("dx", "dy", "dz", "dt", "gamma", "beta", "step", "t", "guard",
+                "gx_lo", "gx_hi", "gy_lo", "gy_hi", "gz_lo", "gz_hi")
+        return dict(zip(keys, o.tolist()))
+
+    def step(self, n: int = 1):
+        self.L.o3_step(self.h, int(n))
+
+    def field(self, comp: int) -> np.ndarray:
+        out = np.zeros(int(np.prod(self.shape)))
+        self.L.o3_get_field(self.h, comp, _p(out))
+        return out.reshape(self.shape)
+
+    def set_field(self, comp: int, a: np.ndarray):
+        a = np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+        self.L.o3_set_field(self.h, comp, _p(a))
+
+    def gather_field(self, comp: int) -> np.ndarray:
+        out = np.zeros(int(np.prod(self.shape)))
+        self.L.o3_get_gather_field(self.h, comp, _p(out))
+        return out.reshape(self.shape)
+
+    def filter_field(self, comp: int, a: np.ndarray) -> np.ndarray:
+        b = np.ascontiguousarray(a, dtype=np.float64).reshape(-1).copy()
+        self.L.o3_filter_field(self.h, comp, _p(b))
+        return b.reshape(self.shape)
+
+    def rho(self) -> np.ndarray:
+        out = np.zeros(int(np.prod(self.shape)))
+        self.L.o3_rho(self.h, _p(out))
+        return out.reshape(self.shape)
+
+    def particles(self, species: int = 0) -> dict:
+        n = self.L.o3_num_particles(self.h, species)
+        keys = ("x", "y", "z", "ux", "uy", "uz", "w")
+        arrs = {k: np.zeros(n) for k in keys}
+        ids = np.zeros(n, dtype=np.uint32)
+        flag = np.zeros(n, dtype=np.int32)
+        self.L.o3_get_particles(self.h, species, *(_p(arrs[k]) for k in keys),
+                                ids.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                                flag.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+        arrs["id"] = ids
+        arrs["alive"] = (flag & 1) != 0
+        arrs["active"] = (flag & 2) != 0
+        return arrs
+
+    def set_particles(self, species: int, x, y, z, ux, uy, uz, w):
+        a = [np.ascontiguousarray(v, dtype=np.float64) for v in (x, y, z, ux, uy, uz, w)]
+        self.L.o3_set_particles(self.h, species, a[0].size, *(_p(v) for v in a))
+
+    def set_beam(self, x, y, z, ux, uy, uz, t_lab: float, z_plane: float):
+        a = [np.ascontiguousarray(v, dtype=np.float64) for v in (x, y, z, ux, uy, uz)]
+        self._beam = a
+        self.L.o3_set_beam(self.h, a[0].size, *(_p(v) for v in a), float(t_lab), float(z_plane))
+
+    def diag(self) -> dict:
+        o = np.zeros(5)
+        self.L.o3_diag(self.h, _p(o))
+        return dict(zip(("n_e", "n_beam", "gamma_lab", "spread", "field_energy"), o.tolist()))
+
+    def btd_set(self, zL: np.ndarray, tL: np.ndarray):
+        zL = np.ascontiguousarray(zL, dtype=np.float64)
+        tL = np.ascontiguousarray(tL, dtype=np.float64)
+        self._nrows = zL.size
+        self.L.o3_btd_set(self.h, zL.size, _p(zL), _p(tL))
+
+    def btd_get(self):
+        out = np.zeros(self._nrows * 6 * (self.nx + 1) * (self.ny + 1))
+        done = np.zeros(self._nrows * 2, dtype=np.int32)
+        self.L.o3_btd_get(self.h, _p(out), done.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+        return out.reshape(self._nrows, 6, self.nx + 1, self.ny + 1), done.reshape(self._nrows, 2)
+
+    def deposit_one(self, p0, p1, qw):
+        """current of one particle moved from p0 to p1 (x, y, z), deposited into the (zeroed) J arrays"""
+        self.L.o3_deposit_one(self.h, *[float(v) for v in p0], *[float(v) for v in p1], float(qw))
+        return [self.field(JX + c) for c in range(3)]

@@ -103,6 +103,80 @@ def shrink(w: dict, nx: int, nz: int, **over) -> dict:
     return v
 
 
+def parity_3d() -> dict:
+    """Plain FP64 parity workload in 3D: 64 (z) x 24 (y) x 24 (x) cells, gamma_boost = 5.
+
+    dz = lambda0/16 in the lab (boosted 0.4949 um), dx = dy = 0.99 um (two boosted cells), Courant 0.9
+    with the CK2 coefficients, 4-cell PML on every face, one bilinear pass (no compensation) on J and
+    on the gathered fields, cubic shapes, n0 = 1e18 cm^-3 with a 4-cell ramp, 1 x 1 x 2 particles per
+    cell, ions fixed in the lab; Gaussian laser a0 = 1, w0 = 4 um, tau = 20 fs, y-polarised.
+    """
+    dzb = 0.4949e-6
+    return {
+        "name": "parity_3d_64x24x24_g5", "dim": 3,
+        "nx": 24, "ny": 24, "nz": 64,
+        "dz_lab": LAMBDA0 / 16.0, "dx": 2 * dzb, "dy": 2 * dzb,
+        "gamma_boost": 5.0, "courant": 0.9, "dt": 0.0,
+        "solver": SOLVERS["ck2"], "theta": 0.0,
+        "pml_cells": 4, "pml_sigma_max": 4.0, "pml_delta": 5.0, "pml_power": 2.0, "pml_xi_exp": 1,
+        "filter_passes": 1, "filter_stride": 1, "filter_compensate": 0, "filter_J": 1, "filter_gather": 1,
+        "order": 3, "particle_guard": -1,
+        "moving_window": 0, "window_beta": 0.0,
+        "precision": "fp64",
+        "plasma": {"n0": 1e24, "z_start_lab": 5.0 * 22 * dzb, "ramp_lab": 5.0 * 4 * dzb,
+                   "length_lab": 0.0, "ppc_x": 1, "ppc_y": 1, "ppc_z": 2, "ions": 1},
+        "laser": {"lambda0": LAMBDA0, "a0": 1.0, "w0": 4e-6, "tau_fwhm": 20e-15, "t_peak": 20e-15,
+                  "x_center": 12 * 2 * dzb, "y_center": 12 * 2 * dzb, "phase": 0.0, "z_antenna": 14 * dzb,
+                  "beta_s": 0.0},
+        "steps": 60,
+    }
+
+
+def stage_3d(gamma_boost: float = 30.0) -> dict:
+    """Mixed-precision 3D boosted-frame stage: 1024 (z) x 128 (y) x 128 (x) cells.
+
+    gamma_boost = 30, lambda/dz = 32 in the lab (boosted dz* = (1+beta) gamma lambda/32), dx = dy = 2 dz*
+    (the transverse-to-longitudinal ratio of the paper's gamma = 130 runs), CK2 coefficients at the
+    paper's low-instability step c dt = dz/sqrt(2), Friedman theta = 0.1, 16-cell PML, 4 passes +
+    compensation, cubic shapes, n0 = 1e18 cm^-3, 1 x 1 x 2 particles per cell (ions fixed in the lab);
+    Gaussian laser a0 = 1.5, w0 = 20 um, tau = 60 fs; the box is full of plasma that keeps streaming
+    in through the +z plane.
+    """
+    g = float(gamma_boost)
+    beta = np.sqrt(1.0 - 1.0 / g ** 2)
+    dzb = (1.0 + beta) * g * LAMBDA0 / 32.0
+    c = 299792458.0
+    nx = ny = 128
+    return {
+        "name": f"stage_3d_1024x128x128_g{g:g}", "dim": 3,
+        "nx": nx, "ny": ny, "nz": 1024,
+        "dz_lab": LAMBDA0 / 32.0, "dx": 2 * dzb, "dy": 2 * dzb,
+        "gamma_boost": g, "courant": 0.99, "dt": dzb / (np.sqrt(2.0) * c),
+        "solver": SOLVERS["ck2"], "theta": 0.1,
+        "pml_cells": 16, "pml_sigma_max": 4.0, "pml_delta": 5.0, "pml_power": 2.0, "pml_xi_exp": 1,
+        "filter_passes": 4, "filter_stride": 1, "filter_compensate": 1, "filter_J": 1, "filter_gather": 1,
+        "order": 3, "particle_guard": -1,
+        "moving_window": 0, "window_beta": 0.0,
+        "precision": "mixed",
+        "plasma": {"n0": 1e24, "z_start_lab": 0.0, "ramp_lab": 0.0, "length_lab": 0.0,
+                   "ppc_x": 1, "ppc_y": 1, "ppc_z": 2, "ions": 1},
+        "laser": {"lambda0": LAMBDA0, "a0": 1.5, "w0": 20e-6, "tau_fwhm": 60e-15, "t_peak": 120e-15,
+                  "x_center": 0.5 * nx * 2 * dzb, "y_center": 0.5 * ny * 2 * dzb, "phase": 0.0,
+                  "z_antenna": 40 * dzb, "beta_s": 0.0},
+    }
+
+
+def shrink3(w: dict, nx: int, ny: int, nz: int, **over) -> dict:
+    """the same 3D workload on a smaller box (laser recentred transversely)"""
+    v = copy.deepcopy(w)
+    v["nx"], v["ny"], v["nz"] = nx, ny, nz
+    if v.get("laser"):
+        v["laser"]["x_center"] = 0.5 * nx * v["dx"]
+        v["laser"]["y_center"] = 0.5 * ny * v["dy"]
+    v.update(over)
+    return v
+
+
 def lab_beam(n: int, seed: int, gamma_b: float, R_b: float, L_b: float, z_c: float, x_c: float,
              spread: float = 0.0):
     """Seeded lab-frame test beam (Table Tablephyspar2d profiles): transverse exp(-r^2/(8 R_b^2)),

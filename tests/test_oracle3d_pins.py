@@ -1,0 +1,215 @@
+"""Pins of the 3D FP64 oracle against what the paper and the mathematics fix.
+
+Closed forms (the 3D numerical dispersion of Eq. num_disp, the filter gain per axis), exact invariants
+(discrete charge conservation of the 3D Esirkepov scheme, Gauss's law over full steps with the antenna's
+dual particle arrays) and reductions to the separately pinned 2-1/2D oracle (fields independent of y,
+a deposit summed over y).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1009_2727_gb300 import workloads as W
+
+C = 299792458.0
+QE = 1.602176634e-19
+EPS0 = 8.8541878128e-12
+
+
+def vacuum3(nx, ny, nz, solver="yee", dx=1e-6, dy=1e-6, dz=1e-6, courant=0.95, theta=0.0, periodic=True, **kw):
+    w = {"dim": 3, "nx": nx, "ny": ny, "nz": nz, "dz_lab": dz, "dx": dx, "dy": dy, "gamma_boost": 1.0,
+         "courant": courant, "solver": W.SOLVERS[solver] if isinstance(solver, str) else solver,
+         "theta": theta, "pml_cells": 0, "order": 3,
+         "periodic_x": int(periodic), "periodic_y": int(periodic), "periodic_z": int(periodic)}
+    w.update(kw)
+    return w
+
+
+# ---------------------------------------------------------------------------
+# Eq. num_disp in 3D: a vacuum Fourier mode advances by the root of the dispersion relation. With
+# K_a = 2 sin(k_a d_a/2)/d_a and C_a = alpha + 2 beta (c_b + c_c) + 4 gamma c_b c_c, the leapfrog
+# eigenmode has E.K = 0, Omega = 2 sin(omega dt/2)/dt = c sqrt(sum C_a K_a^2) and B = (K* x E)/Omega,
+# K* = (C_x K_x, C_y K_y, C_z K_z), each component sampled at its own Yee position.
+ST = {0: (0.5, 0, 0), 1: (0, 0.5, 0), 2: (0, 0, 0.5), 3: (0, 0.5, 0.5), 4: (0.5, 0, 0.5), 5: (0.5, 0.5, 0)}
+
+
+def _mode3(w, s, m, n, e_dir):
+    a, b, g = w["solver"]
+    nn = (w["nx"], w["ny"], w["nz"])
+    d = (s.dx, s.dy, s.dz)
+    k = [2 * np.pi * m[q] / (nn[q] * d[q]) for q in range(3)]
+    K = np.array([2 * np.sin(k[q] * d[q] / 2) / d[q] for q in range(3)])
+    cc = [np.cos(k[q] * d[q]) for q in range(3)]
+    Cq = [a + 2 * b * (cc[(q + 1) % 3] + cc[(q + 2) % 3]) + 4 * g * cc[(q + 1) % 3] * cc[(q + 2) % 3]
+          for q in range(3)]
+    Ks = np.array([Cq[q] * K[q] for q in range(3)])
+    Om = C * math.sqrt(float(np.sum(np.array(Cq) * K * K)))
+    om = 2 * math.asin(Om * s.dt / 2) / s.dt
+    E = np.array(e_dir, dtype=float)
+    E = E - K * (E @ K) / (K @ K)              # discrete transversality E.K = 0
+    E /= np.abs(E).max()
+    B = np.cross(Ks, E) / Om
+    idx = np.meshgrid(*[np.arange(nn[q] + 1) for q in range(3)], indexing="ij")
+
+    def wave(comp, t):
+        ph = sum(k[q] * (idx[q] + ST[comp][q]) * d[q] for q in range(3))
+        return np.cos(ph - om * t)
+    out = {}
+    for c in range(3):
+        out[c] = E[c] * wave(c, n * s.dt)
+        out[3 + c] = B[c] * wave(3 + c, (n - 0.5) * s.dt)
+    return out
+
+
+@pytest.mark.parametrize("name", ["yee", "ck", "ck2", "ck5"])
+@pytest.mark.parametrize("dx,dy,dz", [(1e-6, 1e-6, 1e-6), (1.3e-6, 2.0e-6, 0.6e-6)])
+def test_3d_vacuum_mode_follows_dispersion(orc, name, dx, dy, dz):
+    w = vacuum3(10, 8, 12, name, dx=dx, dy=dy, dz=dz, courant=0.97)
+    for m, e in (((1, 0, 0), (0, 1, 0)), ((0, 2, 3), (1, 0, 0)), ((2, 3, 5), (0.3, -1, 0.4)), ((4, 3, 5), (1, 1, 1))):
+        s = orc.Sim3(w)
+        f0 = _mode3(w, s, m, 0, e)
+        for comp in range(6):
+            s.set_field(comp, f0[comp])
+        N = 30
+        s.step(N)
+        fN = _mode3(w, s, m, N, e)
+        scale = max(np.abs(fN[c]).max() for c in range(3))
+        for comp in range(6):
+            got = s.field(comp)[:10, :8, :12]
+            ref = fN[comp][:10, :8, :12]
+            sc = scale if comp < 3 else max(np.abs(fN[c]).max() for c in range(3, 6))
+            assert np.abs(got - ref).max() <= 1e-10 * sc, (name, m, comp)
+
+
+def test_3d_fields_independent_of_y_match_2d(orc):
+    """the enlarged 3D operator restricted to d/dy = 0 is the 2D operator of PR-3: a y-independent
+    random state advances exactly like the 2-1/2D oracle (CK coefficients, Friedman damping)"""
+    rng = np.random.default_rng(3)
+    nx, nz = 12, 14
+    common = dict(dx=1.1e-6, dz=0.8e-6, courant=0.9, theta=0.3)
+    w2 = {"nx": nx, "nz": nz, "dz_lab": common["dz"], "dx": common["dx"], "gamma_boost": 1.0,
+          "courant": 0.9, "solver": W.SOLVERS["ck"], "theta": 0.3, "pml_cells": 0, "order": 3,
+          "periodic_x": 1, "periodic_z": 1}
+    s2 = orc.Sim(w2)
+    w3 = vacuum3(nx, 4, nz, "ck", dx=common["dx"], dy=1.7e-6, dz=common["dz"], courant=0.9, theta=0.3)
+    w3["dt"] = s2.dt
+    s3 = orc.Sim3(w3)
+    for comp in range(6):
+        f = np.zeros((nx + 1, nz + 1))
+        f[:nx, :nz] = rng.standard_normal((nx, nz)) * (1.0 if comp < 3 else 1.0 / C)
+        s2.set_field(comp, f)
+        s3.set_field(comp, np.repeat(f[:, None, :], 5, axis=1))
+    s2.step(25)
+    s3.step(25)
+    for comp in range(6):
+        a2 = s2.field(comp)[:nx, :nz]
+        a3 = s3.field(comp)[:nx, :4, :nz]
+        assert np.abs(a3 - a2[:, None, :]).max() <= 1e-12 * np.abs(a2).max(), comp
+
+
+# ---------------------------------------------------------------------------
+# 3D filter: the gain of a periodic mode is the product of the 1D gains along x, y and z (Sec. 4.1)
+@pytest.mark.parametrize("n,stride,comp", [(1, 1, 0), (4, 1, 1), (2, 2, 1)])
+def test_3d_filter_gain_is_product_of_axis_gains(orc, n, stride, comp):
+    w = vacuum3(16, 12, 20, filter_passes=n, filter_stride=stride, filter_compensate=comp)
+    s = orc.Sim3(w)
+    m = (3, 2, 5)
+    k = [2 * np.pi * m[0] / 16, 2 * np.pi * m[1] / 12, 2 * np.pi * m[2] / 20]
+    i, j, l = np.meshgrid(np.arange(17), np.arange(13), np.arange(21), indexing="ij")
+    f = np.cos(k[0] * i + k[1] * j + k[2] * l + 0.4)
+
+    def G(kk):
+        g = (0.5 + 0.5 * np.cos(stride * kk)) ** n
+        if comp:
+            ac = n / 2 + 1
+            g *= ac + (1 - ac) * np.cos(stride * kk)
+        return g
+    got = s.filter_field(1, f)[:16, :12, :20]
+    assert np.abs(got - G(k[0]) * G(k[1]) * G(k[2]) * f[:16, :12, :20]).max() < 1e-13
+
+
+# ---------------------------------------------------------------------------
+# Esirkepov in 3D: discrete continuity d(rho)/dt + div J = 0 exactly, and the total current q v
+def _rho1(orc, w, pos, qw):
+    s = orc.Sim3(w)
+    s.set_particles(0, [pos[0]], [pos[1]], [pos[2]], [0.0], [0.0], [0.0], [qw / -QE])
+    return s.rho()
+
+
+@pytest.mark.parametrize("order", [1, 3])
+def test_3d_esirkepov_continuity_and_total_current(orc, order):
+    w = vacuum3(16, 16, 16, dx=1.1e-6, dy=0.9e-6, dz=0.7e-6, periodic=False, order=order)
+    rng = np.random.default_rng(5 + order)
+    for _ in range(8):
+        s = orc.Sim3(w)
+        d = np.array([s.dx, s.dy, s.dz])
+        p0 = rng.uniform(6, 9, 3) * d
+        p1 = p0 + rng.uniform(-0.95, 0.95, 3) * d
+        qw = -QE * 2.3e7
+        Jx, Jy, Jz = s.deposit_one(p0, p1, qw)
+        r0, r1 = _rho1(orc, w, p0, qw), _rho1(orc, w, p1, qw)
+        div = np.zeros_like(r0)
+        div[1:] += (Jx[1:] - Jx[:-1]) / s.dx
+        div[0] += Jx[0] / s.dx
+        div[:, 1:] += (Jy[:, 1:] - Jy[:, :-1]) / s.dy
+        div[:, 0] += Jy[:, 0] / s.dy
+        div[:, :, 1:] += (Jz[:, :, 1:] - Jz[:, :, :-1]) / s.dz
+        div[:, :, 0] += Jz[:, :, 0] / s.dz
+        res = (r1 - r0) / s.dt + div
+        scale = np.abs(r1 - r0).max() / s.dt
+        assert np.abs(res).max() <= 1e-12 * scale
+        vol = s.dx * s.dy * s.dz
+        for J, a in ((Jx, 0), (Jy, 1), (Jz, 2)):
+            assert J.sum() * vol == pytest.approx(qw * (p1[a] - p0[a]) / s.dt, rel=1e-12)
+
+
+def test_3d_deposit_summed_over_y_is_the_2d_deposit(orc):
+    """a particle moving in the x-z plane: sum_j J3D dy equals the 2-1/2D Esirkepov current"""
+    w3 = vacuum3(16, 10, 16, dx=1.1e-6, dy=0.9e-6, dz=0.7e-6, periodic=False)
+    s3 = orc.Sim3(w3)
+    w2 = {"nx": 16, "nz": 16, "dz_lab": 0.7e-6, "dx": 1.1e-6, "gamma_boost": 1.0, "courant": 0.9,
+          "solver": W.SOLVERS["yee"], "theta": 0.0, "pml_cells": 0, "order": 3}
+    s2 = orc.Sim(w2)
+    w2["dt"] = s3.dt
+    s2 = orc.Sim(w2)
+    rng = np.random.default_rng(9)
+    for _ in range(4):
+        s3 = orc.Sim3(w3)
+        x0, z0 = rng.uniform(6, 9) * s3.dx, rng.uniform(6, 9) * s3.dz
+        x1, z1 = x0 + rng.uniform(-0.9, 0.9) * s3.dx, z0 + rng.uniform(-0.9, 0.9) * s3.dz
+        y = 4.3 * s3.dy
+        qw = -QE * 1e8
+        J3 = s3.deposit_one((x0, y, z0), (x1, y, z1), qw)
+        J2 = s2.deposit_one(x0, z0, x1, z1, 0.0, qw)
+        for a in (0, 2):
+            ref = J2[a]
+            assert np.abs(J3[a].sum(axis=1) * s3.dy - ref).max() <= 1e-12 * np.abs(ref).max()
+        assert np.abs(J3[1]).max() == 0.0
+
+
+# ---------------------------------------------------------------------------
+# Gauss's law over full steps (Sec. 4.2.2 with PR-8 and the dual antenna arrays of Sec. 3.1.2):
+# div E - F(rho)/eps0 stays at round-off in the interior, rho including the antenna pairs
+@pytest.mark.slow
+def test_3d_gauss_law_full_step_with_antenna(orc):
+    w = W.shrink3(W.parity_3d(), 32, 32, 56)
+    w["laser"]["z_antenna"] = 24 * 0.4949e-6
+    s = orc.Sim3(w)
+    info = s.info()
+    s.step(24)
+    Ex, Ey, Ez = s.field(0), s.field(1), s.field(2)
+    div = np.zeros_like(Ex)
+    div[1:] += (Ex[1:] - Ex[:-1]) / s.dx
+    div[:, 1:] += (Ey[:, 1:] - Ey[:, :-1]) / s.dy
+    div[:, :, 1:] += (Ez[:, :, 1:] - Ez[:, :, :-1]) / s.dz
+    frho = s.filter_field(1, s.rho())
+    G = div - frho / EPS0
+    lo = [int(info[f"g{a}_lo"]) + 5 for a in "xyz"]
+    hi = [int(info[f"g{a}_hi"]) - 5 for a in "xyz"]
+    sl = (slice(lo[0], hi[0]), slice(lo[1], hi[1]), slice(lo[2], hi[2]))
+    p = s.particles(0)
+    n_e = np.abs(p["w"]).max() * 2 / (s.dx * s.dy * s.dz)
+    scale = QE * n_e / EPS0
+    assert np.abs(div[sl]).max() > 1e-7 * scale       # the laser and the antenna did separate charge
+    assert np.abs(G[sl]).max() < 1e-11 * scale
