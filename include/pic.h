@@ -2,8 +2,8 @@
  * pic.h — C ABI of the GB300-native boosted-frame electromagnetic PIC step.
  *
  * The library advances a 2-1/2D (x,z; all six field components, three momentum
- * components, fields independent of y) laser-wakefield simulation in a Lorentz
- * boosted frame, following J.-L. Vay, C.G.R. Geddes, E. Cormier-Michel,
+ * components, fields independent of y) or a 3D (x,y,z) laser-wakefield
+ * simulation in a Lorentz boosted frame, following J.-L. Vay, C.G.R. Geddes, E. Cormier-Michel,
  * D.P. Grote, "Modeling laser wakefield accelerators in a Lorentz boosted
  * frame" (arXiv:1009.2727). Every step runs in the library's CUDA kernels
  * (sm_103a) on one GPU and one caller-supplied CUDA stream.
@@ -22,6 +22,11 @@
  *    is at i*(nz+1)+k in every buffer this ABI copies out. Each component sits
  *    at its own Yee position: Ex (i+1/2,k), Ey (i,k), Ez (i,k+1/2),
  *    Bx (i,k+1/2), By (i+1/2,k+1/2), Bz (i+1/2,k); J like E.
+ *  - 3D (pic_config.dim = 3): arrays are (nx+1) x (ny+1) x (nz+1), element
+ *    (i,j,k) at (i*(ny+1)+j)*(nz+1)+k; Ex (i+1/2,j,k), Ey (i,j+1/2,k),
+ *    Ez (i,j,k+1/2), Bx (i,j+1/2,k+1/2), By (i+1/2,j,k+1/2), Bz (i+1/2,j+1/2,k).
+ *    3D contexts have no moving window, autotuner or pic_get_rho_noalloc;
+ *    the laser antenna is at rest (beta_s = 0).
  */
 #ifndef PIC_H
 #define PIC_H
@@ -64,7 +69,7 @@ typedef void (*pic_free_fn)(void* ptr, size_t bytes, void* stream, void* user);
  * PIC_API_VERSION. */
 typedef struct {
   uint32_t struct_size, version;
-  int32_t dim;            /* 2 (x,z). 3 is reserved. */
+  int32_t dim;            /* 2 (x,z) or 3 (x,y,z) */
   int32_t nx, nz;         /* cells along x and z; the PML occupies pml_cells on each side */
   double dz_lab;          /* lab longitudinal cell [m]; the computational cell is (1+beta) gamma dz_lab (Sec. 5.1.1) */
   double dx;              /* transverse cell [m] */
@@ -91,7 +96,10 @@ typedef struct {
   double window_beta;
   int32_t tile_x, tile_z; /* particle tile in cells (x, z); 0 = default 8 x 32; at most 1024 cells */
   int32_t sort_every;     /* steps between particle sorts; 0 = default */
-  int32_t reserved[8];
+  int32_t ny;             /* 3D: cells along y (the PML occupies pml_cells on each side) */
+  int32_t reserved0;
+  double dy;              /* 3D: transverse cell along y [m] */
+  int32_t reserved[4];
 } pic_config;
 
 /* Cold plasma fixed in the lab (Sec. 3.1.1), on a regular lattice, entering the
@@ -110,18 +118,24 @@ typedef struct {
   int64_t beam_n;
   const double *beam_x, *beam_z, *beam_ux, *beam_uy, *beam_uz;
   double beam_t_lab, beam_z_plane_lab;
-  int32_t reserved[8];
+  const double* beam_y;   /* 3D: beam y positions (host, beam_n values) */
+  int32_t ppc_y;          /* 3D: macro-particles per cell along y (0 = 1) */
+  int32_t reserved[5];
 } pic_plasma;
 
 /* Gaussian laser injected through a plane (Sec. 3.1.2). The lab waveform at the
  * antenna is E0 exp(-(x-x_center)^2/w0^2) exp(-(s-t_peak)^2/(2 sigma_t^2))
- * sin(omega (s - t_peak) + phase), sigma_t = tau_fwhm/(2 sqrt(ln 2)), y-polarised. */
+ * sin(omega (s - t_peak) + phase), sigma_t = tau_fwhm/(2 sqrt(ln 2)), y-polarised;
+ * in 3D the transverse factor is exp(-((x-x_center)^2 + (y-y_center)^2)/w0^2) and
+ * the current comes from dual particle arrays (one pair per transverse node of the
+ * particle domain, the moving partner displaced along y, Esirkepov deposition). */
 typedef struct {
   uint32_t struct_size, version;
   double lambda0, a0, w0, tau_fwhm, t_peak, x_center, phase;
   double z_antenna;       /* antenna position in the computational frame at t' = 0 [m] */
   double beta_s;          /* antenna-plane velocity / c in the computational frame */
-  int32_t reserved[8];
+  double y_center;        /* 3D: laser axis position along y [m] */
+  int32_t reserved[6];
 } pic_laser;
 
 /* Back-transformed diagnostics (Sec. 3.2): n_rows lab samples (z_lab[r], t_lab[r])
@@ -151,7 +165,7 @@ typedef struct {
   int64_t n_beam_active;
   double beam_gamma_lab;  /* mean lab-frame Lorentz factor of the active test beam */
   double beam_spread;     /* rms(gamma_lab)/mean */
-  double field_energy;    /* per unit length along y [J/m] */
+  double field_energy;    /* per unit length along y [J/m] in 2D; [J] in 3D */
   int32_t gx_lo, gx_hi, gz_lo, gz_hi; /* particle domain in cells */
   int64_t sorts, overflow_chunks;     /* runtime counters */
   double z0;              /* grid origin (moving window) [m] */
@@ -205,6 +219,9 @@ int pic_set_field(pic_ctx* ctx, int comp, const double* src);
 int pic_get_particles(pic_ctx* ctx, int species, double* x, double* z, double* ux, double* uy,
                       double* uz, double* w, uint32_t* id, int32_t* flags, int64_t* count);
 int pic_get_stats(pic_ctx* ctx, pic_stats* out);
+/* 3D contexts: the y positions [m] of the particles pic_get_particles returns,
+ * in the same order (*count as there); PIC_EINVAL for 2D contexts. */
+int pic_get_particles_y(pic_ctx* ctx, int species, double* y, int64_t* count);
 const char* pic_last_error(pic_ctx* ctx);
 
 /* Largest nz accepted by pic_get_rho_noalloc (size of its static scratch). */

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpicgb.so")
-UNITS = ["pic_fields.cu", "pic_particles.cu", "pic_aux.cu", "pic_capi.cu", "pic_tune.cu", "pic_ensemble.cu", "pic_mlp.cu"]
+UNITS = ["pic_fields.cu", "pic_particles.cu", "pic_aux.cu", "pic_capi.cu", "pic_tune.cu", "pic_ensemble.cu", "pic_mlp.cu", "pic_3d.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off", "--expt-relaxed-constexpr"]
 
@@ -30,7 +30,7 @@ def _nvcc() -> str:
 
 def _deps() -> list[str]:
     inc = os.path.join(os.path.dirname(HERE), "include", "pic.h")
-    return [os.path.join(SRC, u) for u in UNITS] + [os.path.join(SRC, "pic_common.cuh"), inc]
+    return [os.path.join(SRC, u) for u in UNITS] + [os.path.join(SRC, "pic_common.cuh"), os.path.join(SRC, "pic_3d.h"), inc]
 
 
 def up_to_date() -> bool:

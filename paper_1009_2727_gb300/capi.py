@@ -26,7 +26,8 @@ STATUS_NAMES = {0: "PIC_OK", -1: "PIC_EINVAL", -2: "PIC_ENOMEM", -3: "PIC_ECFL",
 
 # every symbol include/pic.h declares
 EXPORTS = ("pic_init", "pic_load_plasma", "pic_inject_laser", "pic_step", "pic_sync", "pic_boosted_to_lab_diag",
-           "pic_free", "pic_get_field", "pic_set_field", "pic_get_particles", "pic_get_stats", "pic_last_error",
+           "pic_free", "pic_get_field", "pic_set_field", "pic_get_particles", "pic_get_stats",
+           "pic_get_particles_y", "pic_last_error",
            "pic_kernel_launches", "pic_kernel_timing", "pic_get_rho_noalloc", "pic_autotune",
            "pic_ensemble_create", "pic_ensemble_step", "pic_ensemble_sync", "pic_ensemble_size",
            "pic_ensemble_member", "pic_ensemble_free",
@@ -52,7 +53,8 @@ class PicConfig(ctypes.Structure):
         ("shape_order", ctypes.c_int32), ("particle_guard", ctypes.c_int32), ("precision", ctypes.c_int32),
         ("moving_window", ctypes.c_int32), ("window_beta", ctypes.c_double),
         ("tile_x", ctypes.c_int32), ("tile_z", ctypes.c_int32), ("sort_every", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 8),
+        ("ny", ctypes.c_int32), ("reserved0", ctypes.c_int32), ("dy", ctypes.c_double),
+        ("reserved", ctypes.c_int32 * 4),
     ]
 
 
@@ -65,7 +67,7 @@ class PicPlasma(ctypes.Structure):
         ("beam_n", ctypes.c_int64),
         ("beam_x", _D), ("beam_z", _D), ("beam_ux", _D), ("beam_uy", _D), ("beam_uz", _D),
         ("beam_t_lab", ctypes.c_double), ("beam_z_plane_lab", ctypes.c_double),
-        ("reserved", ctypes.c_int32 * 8),
+        ("beam_y", _D), ("ppc_y", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5),
     ]
 
 
@@ -75,7 +77,7 @@ class PicLaser(ctypes.Structure):
         ("lambda0", ctypes.c_double), ("a0", ctypes.c_double), ("w0", ctypes.c_double),
         ("tau_fwhm", ctypes.c_double), ("t_peak", ctypes.c_double), ("x_center", ctypes.c_double),
         ("phase", ctypes.c_double), ("z_antenna", ctypes.c_double), ("beta_s", ctypes.c_double),
-        ("reserved", ctypes.c_int32 * 8),
+        ("y_center", ctypes.c_double), ("reserved", ctypes.c_int32 * 6),
     ]
 
 
@@ -157,6 +159,7 @@ def load(build_if_missing: bool = True):
                                         ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_int32),
                                         ctypes.POINTER(ctypes.c_int64)]
         L.pic_get_stats.argtypes = [vp, ctypes.POINTER(PicStats)]
+        L.pic_get_particles_y.argtypes = [vp, ctypes.c_int, _D, ctypes.POINTER(ctypes.c_int64)]
         L.pic_last_error.argtypes = [vp]
         L.pic_last_error.restype = ctypes.c_char_p
         L.pic_kernel_launches.argtypes = [vp]

@@ -1,0 +1,1599 @@
+// 3D (x, y, z) boosted-frame PIC step on the GPU: the same method as the
+// 2-1/2D path, written for three dimensions (Vay et al., arXiv:1009.2727).
+//  - Faraday with the enlarged operator of Sec. 4.2, Delta*_a = (alpha +
+//    beta S1 + gamma S2) Delta_a, S1/S2 the transverse neighbours one full
+//    cell away (PR-2), Friedman E_eff (Eq. Faraday_Friedman), split-field PML
+//    on all six faces (App. II): each component is the sum of two parts, one
+//    per derivative direction, each damped by its own axis' sigma.
+//  - Ampere with the Yee operator and the same split PML.
+//  - Composed multi-pass bilinear filter per axis (Sec. 4.1) on the current
+//    and on the gathered fields.
+//  - Energy-conserving gather from the Yee positions with linear or cubic
+//    B-splines, Boris push, 3D Esirkepov deposition (Esirkepov 2001).
+//  - Cold plasma through the +z plane on a ppc_x x ppc_y x ppc_z lattice,
+//    rigid ions fixed in the lab as a separable column current; the laser
+//    from dual particle arrays (Sec. 3.1.2), one pair per transverse node
+//    whose moving partner is displaced along y and deposits with Esirkepov.
+//  - Test beam through a plane, lab-frame samples (Sec. 3.2), diagnostics.
+// Layout: node (i,j,k) of every component at (i*(ny+1)+j)*ldz + k, ldz the
+// padded z extent; Ex (i+1/2,j,k), Ey (i,j+1/2,k), Ez (i,j,k+1/2),
+// Bx (i,j+1/2,k+1/2), By (i+1/2,j,k+1/2), Bz (i+1/2,j+1/2,k); J like E.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "pic_3d.h"
+#include "pic_common.cuh"
+
+namespace picgb {
+namespace {
+
+struct G3 {
+  int n[3];        // cells along x, y, z
+  int ldz;         // padded z extent of every array
+  long cs;         // elements per component array
+  double d[3];     // cell sizes
+  double dt;
+  int lo[3], hi[3];  // particle domain [cells]
+};
+
+__host__ __device__ inline long nid(const G3& g, int i, int j, int k) {
+  return ((long)i * (g.n[1] + 1) + j) * g.ldz + k;
+}
+
+// valid index range of component c (0..5: E then B; J uses E) along an axis: half-staggered 0..n-1,
+// integer 1..n-1 for E (tangential E vanishes on the PEC walls) and 0..n for B
+__host__ __device__ inline void vr(int c, int axis, const G3& g, int& lo, int& hi) {
+  const int n = g.n[axis];
+  const bool half = c < 3 ? (c == axis) : (c - 3 != axis);
+  if (half) { lo = 0; hi = n - 1; }
+  else if (c < 3) { lo = 1; hi = n - 1; }
+  else { lo = 0; hi = n; }
+}
+
+__host__ __device__ inline bool in_valid(int c, const G3& g, int i, int j, int k) {
+  int lo, hi;
+  vr(c, 0, g, lo, hi); if (i < lo || i > hi) return false;
+  vr(c, 1, g, lo, hi); if (j < lo || j > hi) return false;
+  vr(c, 2, g, lo, hi); if (k < lo || k > hi) return false;
+  return true;
+}
+
+template <class T>
+__device__ __forceinline__ T rd3(const G3& g, const T* F, int i, int j, int k) {
+  if (i < 0 || i > g.n[0] || j < 0 || j > g.n[1] || k < 0 || k > g.n[2]) return T(0);
+  return F[nid(g, i, j, k)];
+}
+
+__device__ __forceinline__ bool node_of(const G3& g, long p, int& i, int& j, int& k) {
+  const long nz1 = g.n[2] + 1, ny1 = g.n[1] + 1;
+  if (p >= (long)(g.n[0] + 1) * ny1 * nz1) return false;
+  k = (int)(p % nz1);
+  const long r = p / nz1;
+  j = (int)(r % ny1);
+  i = (int)(r / ny1);
+  return true;
+}
+
+struct Pml3 {
+  const double* sg[3][2];   // sigma [axis][half]
+  const double* xi[3][2];
+  const double* cf[3][2];   // (1 - xi)/sigma, dt where sigma = 0
+};
+
+template <class T>
+struct Taps3 {
+  T c[33];
+  int P, s;
+};
+
+// ---------------------------------------------------------------------------
+// fields
+template <class T>
+__global__ void k3_eeff(long n, const T* E, const T* Ep, const T* Eb, T* Ee, T c1, T c2, T c3) {
+  const long p = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n) Ee[p] = c1 * E[p] - c2 * Ep[p] + c3 * Eb[p];
+}
+
+// Delta*_a F at node (i,j,k) (result half a cell above along a): alpha D(0,0) + beta (four axial
+// neighbours) + gamma (four diagonal neighbours), D the difference along a on the transverse offsets
+template <class T>
+__device__ T dstar3(const G3& g, const T* F, int a, int i, int j, int k, T ca, T cb, T cg, T inv_d) {
+  const int b = a == 0 ? 1 : 0, c = a == 2 ? 1 : 2;
+  T D[3][3];
+#pragma unroll
+  for (int o1 = -1; o1 <= 1; o1++)
+#pragma unroll
+    for (int o2 = -1; o2 <= 1; o2++) {
+      const int pi = i + (b == 0 ? o1 : 0) + (c == 0 ? o2 : 0);
+      const int pj = j + (b == 1 ? o1 : 0) + (c == 1 ? o2 : 0);
+      const int pk = k + (b == 2 ? o1 : 0) + (c == 2 ? o2 : 0);
+      D[o1 + 1][o2 + 1] = rd3(g, F, pi + (a == 0), pj + (a == 1), pk + (a == 2)) - rd3(g, F, pi, pj, pk);
+    }
+  const T s1 = D[0][1] + D[2][1] + D[1][0] + D[1][2];
+  const T s2 = D[0][0] + D[0][2] + D[2][0] + D[2][2];
+  return (ca * D[1][1] + cb * s1 + cg * s2) * inv_d;
+}
+
+template <class T>
+__global__ void k3_faraday(G3 g, Pml3 pm, const T* Ee, T* B, T* Bs, T* fB, T ca, T cb, T cg, T dtT) {
+  int i, j, k;
+  if (!node_of(g, (long)blockIdx.x * blockDim.x + threadIdx.x, i, j, k)) return;
+  const long p = nid(g, i, j, k);
+  const int idx[3] = {i, j, k};
+  for (int q = 0; q < 3; q++) {
+    const T old = B[q * g.cs + p];
+    T nw = old;
+    if (in_valid(3 + q, g, i, j, k)) {
+      const int u = (q + 1) % 3, v = (q + 2) % 3;
+      const T du = dstar3(g, Ee + v * g.cs, u, i, j, k, ca, cb, cg, T(1.0 / g.d[u]));
+      const T dv = dstar3(g, Ee + u * g.cs, v, i, j, k, ca, cb, cg, T(1.0 / g.d[v]));
+      const double su = pm.sg[u][1][idx[u]], sv = pm.sg[v][1][idx[v]];
+      if (su > 0.0 || sv > 0.0) {
+        T* Pu = Bs + (2 * q) * g.cs;
+        T* Pv = Bs + (2 * q + 1) * g.cs;
+        const T a = T(pm.xi[u][1][idx[u]] * (double)Pu[p] - pm.cf[u][1][idx[u]] * (double)du);
+        const T b = T(pm.xi[v][1][idx[v]] * (double)Pv[p] + pm.cf[v][1][idx[v]] * (double)dv);
+        Pu[p] = a;
+        Pv[p] = b;
+        nw = a + b;
+      } else {
+        nw = old - dtT * (du - dv);
+      }
+      B[q * g.cs + p] = nw;
+    }
+    fB[q * g.cs + p] = T(0.5) * (old + nw);
+  }
+}
+
+// Friedman history (PR-1): E-bar <- (1 - theta/2) E + (theta/2) E-bar, E^{n-1} <- E, gather copy <- E
+template <class T>
+__global__ void k3_friedman(long n, const T* E, T* Ep, T* Eb, T* fE, T a, T b) {
+  const long p = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const T e = E[p];
+  Eb[p] = a * e + b * Eb[p];
+  Ep[p] = e;
+  fE[p] = e;
+}
+
+template <class T>
+__global__ void k3_ampere(G3 g, Pml3 pm, T* E, T* Es, const T* B, const T* J, T dtc2, T dte) {
+  int i, j, k;
+  if (!node_of(g, (long)blockIdx.x * blockDim.x + threadIdx.x, i, j, k)) return;
+  const long p = nid(g, i, j, k);
+  const int idx[3] = {i, j, k};
+  const double c2 = kC * kC;
+  for (int q = 0; q < 3; q++) {
+    if (!in_valid(q, g, i, j, k)) continue;
+    const int u = (q + 1) % 3, v = (q + 2) % 3;
+    // dE_q/dt = c^2 (Delta_u B_v - Delta_v B_u) - J_q/eps0, backward differences
+    const T* Bv = B + v * g.cs;
+    const T* Bu = B + u * g.cs;
+    const T du = (rd3(g, Bv, i, j, k) - rd3(g, Bv, i - (u == 0), j - (u == 1), k - (u == 2))) * T(1.0 / g.d[u]);
+    const T dv = (rd3(g, Bu, i, j, k) - rd3(g, Bu, i - (v == 0), j - (v == 1), k - (v == 2))) * T(1.0 / g.d[v]);
+    const double su = pm.sg[u][0][idx[u]], sv = pm.sg[v][0][idx[v]];
+    if (su > 0.0 || sv > 0.0) {
+      T* Pu = Es + (2 * q) * g.cs;
+      T* Pv = Es + (2 * q + 1) * g.cs;
+      const T a = T(pm.xi[u][0][idx[u]] * (double)Pu[p] + c2 * pm.cf[u][0][idx[u]] * (double)du);
+      const T b = T(pm.xi[v][0][idx[v]] * (double)Pv[p] - c2 * pm.cf[v][0][idx[v]] * (double)dv);
+      Pu[p] = a;
+      Pv[p] = b;
+      E[q * g.cs + p] = a + b;
+    } else {
+      E[q * g.cs + p] = E[q * g.cs + p] + (dtc2 * (du - dv) - dte * J[q * g.cs + p]);
+    }
+  }
+}
+
+// one axis of the composed filter: out = sum_m c_m F(node + (m - P) s e_axis), zero off the valid range
+template <class T>
+__global__ void k3_filter_axis(G3 g, const T* src, T* dst, int comp, int axis, Taps3<T> t) {
+  int i, j, k;
+  if (!node_of(g, (long)blockIdx.x * blockDim.x + threadIdx.x, i, j, k)) return;
+  const long p = nid(g, i, j, k);
+  if (!in_valid(comp, g, i, j, k)) {
+    dst[p] = T(0);
+    return;
+  }
+  T acc = T(0);
+  for (int m = 0; m <= 2 * t.P; m++) {
+    const int o = (m - t.P) * t.s;
+    acc += t.c[m] * rd3(g, src, i + (axis == 0 ? o : 0), j + (axis == 1 ? o : 0), k + (axis == 2 ? o : 0));
+  }
+  dst[p] = acc;
+}
+
+// ---------------------------------------------------------------------------
+// particles
+template <class T>
+struct Parts3 {
+  double* x; double* y; double* z;
+  T* ux; T* uy; T* uz; T* w;
+  uint32_t* id;
+  int* fl;          // bit 0: alive
+};
+
+struct Ctrl3 {
+  int count;
+  int status;
+  int pad[2];
+  double red[8];
+};
+
+template <class T, int ORD>
+__device__ __forceinline__ void shape_w(T t, T* w) {
+  if (ORD == 3) weights3<T>(t, w);
+  else weights1<T>(t, w);
+}
+
+// fields at a particle: each component from its own Yee position, the same shape along every axis
+template <class T, int ORD>
+__device__ void gather3(const G3& g, const T* const* fE, const T* const* fB, const double* pos, T* E, T* B) {
+  constexpr int NS = ORD == 3 ? 4 : 2;
+  constexpr int SH = ORD == 3 ? 1 : 0;
+  T w[3][2][NS];
+  int b[3][2];
+#pragma unroll
+  for (int a = 0; a < 3; a++)
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+      const double X = pos[a] / g.d[a] - 0.5 * h;
+      const double f = floor(X);
+      shape_w<T, ORD>(T(X - f), w[a][h]);
+      b[a][h] = (int)f - SH;
+    }
+#pragma unroll
+  for (int c = 0; c < 6; c++) {
+    const T* F = c < 3 ? fE[c] : fB[c - 3];
+    const int hx = c < 3 ? (c == 0) : (c != 3), hy = c < 3 ? (c == 1) : (c != 4), hz = c < 3 ? (c == 2) : (c != 5);
+    T acc = T(0);
+    for (int l0 = 0; l0 < NS; l0++) {
+      const T w0 = w[0][hx][l0];
+      for (int l1 = 0; l1 < NS; l1++) {
+        const T w01 = w0 * w[1][hy][l1];
+        for (int l2 = 0; l2 < NS; l2++)
+          acc += rd3(g, F, b[0][hx] + l0, b[1][hy] + l1, b[2][hz] + l2) * (w01 * w[2][hz][l2]);
+      }
+    }
+    if (c < 3) E[c] = acc;
+    else B[c - 3] = acc;
+  }
+}
+
+// relativistic Boris push (textbook): u^{n-1/2} -> u^{n+1/2}, u = gamma v
+template <class T>
+__device__ __forceinline__ void boris3(T* u, const T* E, const T* B, T k) {
+  const T ic2 = T(1.0 / (kC * kC));
+  const T um0 = u[0] + k * E[0], um1 = u[1] + k * E[1], um2 = u[2] + k * E[2];
+  const T gm = sqrt(T(1) + (um0 * um0 + um1 * um1 + um2 * um2) * ic2);
+  const T t0 = k * B[0] / gm, t1 = k * B[1] / gm, t2 = k * B[2] / gm;
+  const T tt = t0 * t0 + t1 * t1 + t2 * t2;
+  const T s0 = T(2) * t0 / (T(1) + tt), s1 = T(2) * t1 / (T(1) + tt), s2 = T(2) * t2 / (T(1) + tt);
+  const T up0 = um0 + (um1 * t2 - um2 * t1), up1 = um1 + (um2 * t0 - um0 * t2), up2 = um2 + (um0 * t1 - um1 * t0);
+  const T pl0 = um0 + (up1 * s2 - up2 * s1), pl1 = um1 + (up2 * s0 - up0 * s2), pl2 = um2 + (up0 * s1 - up1 * s0);
+  u[0] = pl0 + k * E[0];
+  u[1] = pl1 + k * E[1];
+  u[2] = pl2 + k * E[2];
+}
+
+// Esirkepov deposition in 3D (Esirkepov 2001) of charge*weight qw from p0 to p1 (moves below one cell):
+// W_q = DS_q (S0_u S0_v + DS_u S0_v/2 + S0_u DS_v/2 + DS_u DS_v/3), J_q prefix sums of -qw/(d_u d_v dt) W_q
+template <class T, int ORD>
+__device__ void esirkepov3d(const G3& g, T* const* J, const double* p0, const double* p1, double qw) {
+  constexpr int NS = ORD == 3 ? 4 : 2;
+  constexpr int SH = ORD == 3 ? 1 : 0;
+  constexpr int W = NS + 1;
+  T S0[3][W], DS[3][W];
+  int base[3];
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    const double A0 = p0[a] / g.d[a], A1 = p1[a] / g.d[a];
+    const double f0 = floor(A0), f1 = floor(A1);
+    base[a] = (int)(f0 < f1 ? f0 : f1) - SH;
+    T w0[NS], w1[NS];
+    shape_w<T, ORD>(T(A0 - f0), w0);
+    shape_w<T, ORD>(T(A1 - f1), w1);
+    const int o0 = (int)f0 - SH - base[a], o1 = (int)f1 - SH - base[a];
+#pragma unroll
+    for (int m = 0; m < W; m++) {
+      const T s0 = (m - o0 >= 0 && m - o0 < NS) ? w0[m - o0] : T(0);
+      const T s1 = (m - o1 >= 0 && m - o1 < NS) ? w1[m - o1] : T(0);
+      S0[a][m] = s0;
+      DS[a][m] = s1 - s0;
+    }
+  }
+  const double vol_dt = g.d[0] * g.d[1] * g.d[2] * g.dt;
+#pragma unroll
+  for (int q = 0; q < 3; q++) {
+    const int u = (q + 1) % 3, v = (q + 2) % 3;
+    const T cq = T(-qw * g.d[q] / vol_dt);
+    for (int mu = 0; mu < W; mu++)
+      for (int mv = 0; mv < W; mv++) {
+        const T tr = S0[u][mu] * S0[v][mv] + T(0.5) * DS[u][mu] * S0[v][mv] + T(0.5) * S0[u][mu] * DS[v][mv] +
+                     DS[u][mu] * DS[v][mv] / T(3);
+        if (tr == T(0)) continue;
+        T acc = T(0);
+        for (int mq = 0; mq < W; mq++) {
+          acc += cq * DS[q][mq] * tr;
+          if (acc == T(0)) continue;
+          int id3[3];
+          id3[q] = base[q] + mq; id3[u] = base[u] + mu; id3[v] = base[v] + mv;
+          if (id3[0] < 0 || id3[0] > g.n[0] || id3[1] < 0 || id3[1] > g.n[1] || id3[2] < 0 || id3[2] > g.n[2]) continue;
+          atomicAdd(J[q] + nid(g, id3[0], id3[1], id3[2]), acc);
+        }
+      }
+  }
+}
+
+template <class T>
+struct Fld3 {
+  const T* fE[3];
+  const T* fB[3];
+  T* J[3];
+};
+
+template <class T, int ORD>
+__global__ void __launch_bounds__(128) k3_push(G3 g, Fld3<T> f, Parts3<T> p, const Ctrl3* ctrl, T kq, double qe) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= ctrl->count) return;
+  if (!(p.fl[j] & 1)) return;
+  const double pos[3] = {p.x[j], p.y[j], p.z[j]};
+  T E[3], B[3];
+  gather3<T, ORD>(g, f.fE, f.fB, pos, E, B);
+  T u[3] = {p.ux[j], p.uy[j], p.uz[j]};
+  boris3<T>(u, E, B, kq);
+  const T gm = sqrt(T(1) + (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]) * T(1.0 / (kC * kC)));
+  const double pn[3] = {pos[0] + g.dt * (double)(u[0] / gm), pos[1] + g.dt * (double)(u[1] / gm),
+                        pos[2] + g.dt * (double)(u[2] / gm)};
+  esirkepov3d<T, ORD>(g, f.J, pos, pn, qe * (double)p.w[j]);
+  p.x[j] = pn[0]; p.y[j] = pn[1]; p.z[j] = pn[2];
+  p.ux[j] = u[0]; p.uy[j] = u[1]; p.uz[j] = u[2];
+  bool out = false;
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    const double lo = g.lo[a] * g.d[a];
+    const double hi = g.hi[a] * g.d[a] + (a == 2 ? g.d[2] : 0.0);
+    if (pn[a] < lo || pn[a] >= hi) out = true;
+  }
+  if (out) p.fl[j] = 0;
+}
+
+// ---------------------------------------------------------------------------
+// plasma: lattice rows, rigid ions as a separable column current
+struct Lat3 {
+  double h, gamma, beta, n0, z_start_lab, ramp_lab, length_lab;
+  int ppc[3];
+  int nxl, nyl;
+};
+
+__host__ __device__ inline double lab_density3(const Lat3& L, double zl) {
+  if (zl < L.z_start_lab) return 0.0;
+  const double r = zl - L.z_start_lab;
+  if (L.ramp_lab > 0.0 && r < L.ramp_lab) return L.n0 * r / L.ramp_lab;
+  const double plateau_end = L.ramp_lab + L.length_lab;
+  if (L.length_lab > 0.0 && r >= plateau_end) return 0.0;
+  return L.n0;
+}
+
+struct Rows8 {
+  long long m[8];
+  int n;
+};
+
+template <class T>
+__global__ void k3_inject(G3 g, Parts3<T> p, const Ctrl3* ctrl, Lat3 L, Rows8 rows, double t) {
+  const long per = (long)L.nxl * L.nyl;
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= per * rows.n) return;
+  const int r = (int)(e / per);
+  const long ab = e - (long)r * per;
+  const int a = (int)(ab / L.nyl), b = (int)(ab - (long)a * L.nyl);
+  const long long m = rows.m[r];
+  const double zlat = (m + 0.5) * L.h;
+  const double n = L.gamma * lab_density3(L, L.gamma * zlat);
+  const long q = (long)ctrl->count + e;
+  p.x[q] = (g.lo[0] + (a + 0.5) / L.ppc[0]) * g.d[0];
+  p.y[q] = (g.lo[1] + (b + 0.5) / L.ppc[1]) * g.d[1];
+  p.z[q] = zlat - L.beta * kC * t;
+  p.ux[q] = T(0);
+  p.uy[q] = T(0);
+  p.uz[q] = T(-L.gamma * L.beta * kC);
+  p.w[q] = T(n * g.d[0] * g.d[1] * g.d[2] / (double)(L.ppc[0] * L.ppc[1] * L.ppc[2]));
+  p.id[q] = (uint32_t)((unsigned long long)m * (unsigned long long)per + (unsigned long long)(a * (long)L.nyl + b));
+  p.fl[q] = 1;
+}
+
+__global__ void k3_add_count(Ctrl3* c, int d) { c->count += d; }
+
+// sum over n >= 0 of S(u + n): the prefix of the shape samples (Esirkepov's 1D flux)
+__device__ __forceinline__ double cum_shape(int order, double u) {
+  const double r = order == 3 ? 2.0 : 1.0;
+  if (u >= r) return 0.0;
+  if (u <= -r) return 1.0;
+  double acc = 0.0;
+  for (int n = 0; n < 5; n++) {
+    const double s = fabs(u + n);
+    double v = 0.0;
+    if (order == 1) v = s < 1.0 ? 1.0 - s : 0.0;
+    else if (s < 1.0) v = 2.0 / 3.0 - s * s + 0.5 * s * s * s;
+    else if (s < 2.0) { const double t = 2.0 - s; v = t * t * t / 6.0; }
+    acc += v;
+  }
+  return acc;
+}
+
+// Z(k) = sum over the live ion rows of w_m (C(Z1 - k) - C(Z0 - k)): the z-prefix of the rows' shape change
+__global__ void k3_ion_z(G3 g, Lat3 L, int order, long long mlo, long long mhi, double t0, double t1, double* Zs) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k > g.n[2]) return;
+  const double dz = g.d[2];
+  const double vsh = L.beta * kC;
+  long long m0 = (long long)floor(((k - 4) * dz + vsh * t0) / L.h - 0.5);
+  long long m1 = (long long)ceil(((k + 4) * dz + vsh * t0) / L.h - 0.5);
+  if (m0 < mlo) m0 = mlo;
+  if (m1 > mhi - 1) m1 = mhi - 1;
+  double acc = 0.0;
+  for (long long m = m0; m <= m1; m++) {
+    const double zl = (m + 0.5) * L.h;
+    const double n = L.gamma * lab_density3(L, L.gamma * zl);
+    if (n <= 0.0) continue;
+    const double w = n * g.d[0] * g.d[1] * g.d[2] / (double)(L.ppc[0] * L.ppc[1] * L.ppc[2]);
+    const double Z0 = (zl - vsh * t0) / dz, Z1 = (zl - vsh * t1) / dz;
+    acc += w * (cum_shape(order, Z1 - k) - cum_shape(order, Z0 - k));
+  }
+  Zs[k] = acc;
+}
+
+// J_z += coef Tx(i) Ty(j) Z(k), coef = -q_ion/(dx dy dt)
+template <class T>
+__global__ void k3_ion_jz(G3 g, const double* Tx, const double* Ty, const double* Zs, double coef, T* Jz) {
+  int i, j, k;
+  if (!node_of(g, (long)blockIdx.x * blockDim.x + threadIdx.x, i, j, k)) return;
+  const double v = coef * Tx[i] * Ty[j] * Zs[k];
+  if (v != 0.0) Jz[nid(g, i, j, k)] += T(v);
+}
+
+// charge density of the ion rows at time t: q/(dV) Tx(i) Ty(j) sum_m w_m S(Z_m - k)
+__global__ void k3_ion_rho(G3 g, Lat3 L, int order, long long mlo, long long mhi, double t, const double* Tx,
+                           const double* Ty, double* rho) {
+  int i, j, k;
+  if (!node_of(g, (long)blockIdx.x * blockDim.x + threadIdx.x, i, j, k)) return;
+  if (Tx[i] == 0.0 || Ty[j] == 0.0) return;
+  const double dz = g.d[2], vsh = L.beta * kC;
+  long long m0 = (long long)floor(((k - 3) * dz + vsh * t) / L.h - 0.5);
+  long long m1 = (long long)ceil(((k + 3) * dz + vsh * t) / L.h - 0.5);
+  if (m0 < mlo) m0 = mlo;
+  if (m1 > mhi - 1) m1 = mhi - 1;
+  double acc = 0.0;
+  for (long long m = m0; m <= m1; m++) {
+    const double zl = (m + 0.5) * L.h;
+    const double n = L.gamma * lab_density3(L, L.gamma * zl);
+    if (n <= 0.0) continue;
+    const double w = n * g.d[0] * g.d[1] * g.d[2] / (double)(L.ppc[0] * L.ppc[1] * L.ppc[2]);
+    const double Z = (zl - vsh * t) / dz;
+    const double s = fabs(Z - k);
+    double v = 0.0;
+    if (order == 1) v = s < 1.0 ? 1.0 - s : 0.0;
+    else if (s < 1.0) v = 2.0 / 3.0 - s * s + 0.5 * s * s * s;
+    else if (s < 2.0) { const double tt = 2.0 - s; v = tt * tt * tt / 6.0; }
+    acc += w * v;
+  }
+  rho[nid(g, i, j, k)] += kQe * Tx[i] * Ty[j] * acc / (g.d[0] * g.d[1] * g.d[2]);
+}
+
+template <class T>
+__global__ void k3_particle_rho(G3 g, Parts3<T> p, const Ctrl3* ctrl, int order, double q, double* rho) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= ctrl->count || !(p.fl[j] & 1)) return;
+  const double pos[3] = {p.x[j], p.y[j], p.z[j]};
+  const double qw = q * (double)p.w[j] / (g.d[0] * g.d[1] * g.d[2]);
+  double w[3][4];
+  int b[3];
+  const int NS = order == 3 ? 4 : 2, SH = order == 3 ? 1 : 0;
+  for (int a = 0; a < 3; a++) {
+    const double X = pos[a] / g.d[a], f = floor(X);
+    if (order == 3) weights3<double>(X - f, w[a]);
+    else weights1<double>(X - f, w[a]);
+    b[a] = (int)f - SH;
+  }
+  for (int l0 = 0; l0 < NS; l0++)
+    for (int l1 = 0; l1 < NS; l1++)
+      for (int l2 = 0; l2 < NS; l2++) {
+        const int i = b[0] + l0, jj = b[1] + l1, k = b[2] + l2;
+        if (i < 0 || i > g.n[0] || jj < 0 || jj > g.n[1] || k < 0 || k > g.n[2]) continue;
+        atomicAdd(rho + nid(g, i, jj, k), qw * w[0][l0] * w[1][l1] * w[2][l2]);
+      }
+}
+
+// ---------------------------------------------------------------------------
+// laser antenna: dual particle arrays (Sec. 3.1.2)
+struct Ant3 {
+  double x_center, y_center, w0, za;
+  double D0, D1;     // displacement factors before and after the step (delta = G(x, y) D)
+  double Q;          // charge of the moving partner
+  int order;
+};
+
+template <class T>
+__global__ void k3_antenna(G3 g, T* Jy, Ant3 a) {
+  const int nyp = g.hi[1] - g.lo[1] + 1;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (g.hi[0] - g.lo[0] + 1) * nyp) return;
+  const int i = g.lo[0] + e / nyp, j = g.lo[1] + e % nyp;
+  const double x = i * g.d[0], y = j * g.d[1];
+  const double rx = x - a.x_center, ry = y - a.y_center;
+  const double G = exp(-(rx * rx + ry * ry) / (a.w0 * a.w0));
+  const double y0 = y + G * a.D0, y1 = y + G * a.D1;
+  if (y0 == y1) return;
+  const int NS = a.order == 3 ? 4 : 2, SH = a.order == 3 ? 1 : 0;
+  double wx[4], wz[4], S0y[5], DSy[5];
+  {
+    const double X = x / g.d[0], fx = floor(X), Z = a.za / g.d[2], fz = floor(Z);
+    if (a.order == 3) { weights3<double>(X - fx, wx); weights3<double>(Z - fz, wz); }
+    else { weights1<double>(X - fx, wx); weights1<double>(Z - fz, wz); }
+    const double A0 = y0 / g.d[1], A1 = y1 / g.d[1], f0 = floor(A0), f1 = floor(A1);
+    const int by = (int)(f0 < f1 ? f0 : f1) - SH;
+    double w0[4], w1[4];
+    if (a.order == 3) { weights3<double>(A0 - f0, w0); weights3<double>(A1 - f1, w1); }
+    else { weights1<double>(A0 - f0, w0); weights1<double>(A1 - f1, w1); }
+    const int o0 = (int)f0 - SH - by, o1 = (int)f1 - SH - by;
+    for (int m = 0; m <= NS; m++) {
+      const double s0 = (m - o0 >= 0 && m - o0 < NS) ? w0[m - o0] : 0.0;
+      const double s1 = (m - o1 >= 0 && m - o1 < NS) ? w1[m - o1] : 0.0;
+      S0y[m] = s0;
+      DSy[m] = s1 - s0;
+    }
+    const int bx = (int)fx - SH, bz = (int)fz - SH;
+    // J_y(j+1/2) - J_y(j-1/2) = -Q/(dx dz dt) W_y, W_y = DS_y S0_z S0_x
+    const double cy = -a.Q / (g.d[0] * g.d[2] * g.dt);
+    for (int lz = 0; lz < NS; lz++)
+      for (int lx = 0; lx < NS; lx++) {
+        const double tr = wz[lz] * wx[lx];
+        if (tr == 0.0) continue;
+        double acc = 0.0;
+        for (int m = 0; m <= NS; m++) {
+          acc += cy * DSy[m] * tr;
+          if (acc == 0.0) continue;
+          const int ii = bx + lx, jj = by + m, kk = bz + lz;
+          if (ii < 0 || ii > g.n[0] || jj < 0 || jj > g.n[1] || kk < 0 || kk > g.n[2]) continue;
+          atomicAdd(Jy + nid(g, ii, jj, kk), T(acc));
+        }
+      }
+  }
+}
+
+// charge of the antenna pairs (the moving partner +Q, its fixed twin -Q) added to rho
+__global__ void k3_antenna_rho(G3 g, Ant3 a, double* rho) {
+  const int nyp = g.hi[1] - g.lo[1] + 1;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (g.hi[0] - g.lo[0] + 1) * nyp) return;
+  const int i = g.lo[0] + e / nyp, j = g.lo[1] + e % nyp;
+  const double x = i * g.d[0], y = j * g.d[1];
+  const double rx = x - a.x_center, ry = y - a.y_center;
+  const double dl = exp(-(rx * rx + ry * ry) / (a.w0 * a.w0)) * a.D1;
+  if (dl == 0.0) return;
+  const int NS = a.order == 3 ? 4 : 2, SH = a.order == 3 ? 1 : 0;
+  const double pos[2][3] = {{x, y + dl, a.za}, {x, y, a.za}};
+  for (int s = 0; s < 2; s++) {
+    const double q = (s == 0 ? a.Q : -a.Q) / (g.d[0] * g.d[1] * g.d[2]);
+    double w[3][4];
+    int b[3];
+    for (int ax = 0; ax < 3; ax++) {
+      const double X = pos[s][ax] / g.d[ax], f = floor(X);
+      if (a.order == 3) weights3<double>(X - f, w[ax]);
+      else weights1<double>(X - f, w[ax]);
+      b[ax] = (int)f - SH;
+    }
+    for (int l0 = 0; l0 < NS; l0++)
+      for (int l1 = 0; l1 < NS; l1++)
+        for (int l2 = 0; l2 < NS; l2++) {
+          const int ii = b[0] + l0, jj = b[1] + l1, kk = b[2] + l2;
+          if (ii < 0 || ii > g.n[0] || jj < 0 || jj > g.n[1] || kk < 0 || kk > g.n[2]) continue;
+          atomicAdd(rho + nid(g, ii, jj, kk), q * w[0][l0] * w[1][l1] * w[2][l2]);
+        }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// test beam (Sec. 3.1.1)
+template <class T>
+struct Beam3 {
+  double *x, *y, *z;
+  T *ux, *uy, *uz;
+  double *tc, *zf0;
+  T *uxb, *uyb, *uzb;
+  int* fl;    // bit 0 alive, bit 1 active
+  int n;
+};
+
+__global__ void k3_beam_vz(int n, const double* ux, const double* uy, const double* uz, double* acc) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const double gj = sqrt(1.0 + (ux[j] * ux[j] + uy[j] * uy[j] + uz[j] * uz[j]) / (kC * kC));
+  atomicAdd(&acc[0], uz[j] / gj);
+}
+
+template <class T>
+__global__ void k3_beam_transform(Beam3<T> b, const double* lx, const double* ly, const double* lz,
+                                  const double* lux, const double* luy, const double* luz, double t_lab,
+                                  double z_plane, double gam, double be, double* acc) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= b.n) return;
+  const double betab = acc[0] / b.n / kC;
+  const double gj = sqrt(1.0 + (lux[j] * lux[j] + luy[j] * luy[j] + luz[j] * luz[j]) / (kC * kC));
+  const double vx = lux[j] / gj, vy = luy[j] / gj, vz = luz[j] / gj;
+  const double tcross = t_lab + (z_plane - lz[j]) / vz;
+  b.x[j] = lx[j] + vx * (tcross - t_lab);
+  b.y[j] = ly[j] + vy * (tcross - t_lab);
+  const double tpc = gam * (tcross - be * z_plane / kC);
+  const double zpc = gam * (z_plane - be * kC * tcross);
+  const double den = 1.0 - be * betab;
+  const double vxp = vx / (gam * den), vyp = vy / (gam * den), vzp = (vz - be * kC) / den;
+  const double v2 = (vxp * vxp + vyp * vyp + vzp * vzp) / (kC * kC);
+  const double gp = 1.0 / sqrt(1.0 - v2);
+  b.uxb[j] = T(gp * vxp); b.uyb[j] = T(gp * vyp); b.uzb[j] = T(gp * vzp);
+  b.ux[j] = b.uxb[j]; b.uy[j] = b.uyb[j]; b.uz[j] = b.uzb[j];
+  b.tc[j] = tpc;
+  b.zf0[j] = zpc;
+  b.fl[j] = 1;
+  atomicAdd(&acc[1], vzp);
+}
+
+template <class T>
+__global__ void k3_beam_finish(Beam3<T> b, double t_now, double* acc) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= b.n) return;
+  const double vbar = acc[1] / b.n;
+  const double zf = b.zf0[j] - vbar * b.tc[j];
+  b.zf0[j] = zf;
+  b.z[j] = zf + vbar * t_now;
+  if (j == 0) acc[2] = vbar;
+}
+
+template <class T, int ORD>
+__global__ void k3_beam_push(G3 g, Fld3<T> f, Beam3<T> b, double tn, double tn1, const double* acc, T kq) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= b.n) return;
+  int fl = b.fl[j];
+  if (!(fl & 1)) return;
+  double lo[3], hi[3];
+  for (int a = 0; a < 3; a++) { lo[a] = g.lo[a] * g.d[a]; hi[a] = g.hi[a] * g.d[a]; }
+  hi[2] += g.d[2];
+  if (!(fl & 2)) {
+    if (tn >= b.tc[j]) {
+      fl |= 2;
+      b.ux[j] = b.uxb[j]; b.uy[j] = b.uyb[j]; b.uz[j] = b.uzb[j];
+      const double q[3] = {b.x[j], b.y[j], b.z[j]};
+      for (int a = 0; a < 3; a++)
+        if (q[a] < lo[a] || q[a] >= hi[a]) fl &= ~1;
+      b.fl[j] = fl;
+      if (!(fl & 1)) return;
+    } else {
+      b.z[j] = b.zf0[j] + acc[2] * tn1;
+      return;
+    }
+  }
+  const double pos[3] = {b.x[j], b.y[j], b.z[j]};
+  T E[3], B[3];
+  gather3<T, ORD>(g, f.fE, f.fB, pos, E, B);
+  T u[3] = {b.ux[j], b.uy[j], b.uz[j]};
+  boris3<T>(u, E, B, kq);
+  const T gm = sqrt(T(1) + (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]) * T(1.0 / (kC * kC)));
+  double pn[3];
+  for (int a = 0; a < 3; a++) pn[a] = pos[a] + g.dt * (double)(u[a] / gm);
+  b.x[j] = pn[0]; b.y[j] = pn[1]; b.z[j] = pn[2];
+  b.ux[j] = u[0]; b.uy[j] = u[1]; b.uz[j] = u[2];
+  for (int a = 0; a < 3; a++)
+    if (pn[a] < lo[a] || pn[a] >= hi[a]) fl &= ~1;
+  b.fl[j] = fl;
+}
+
+// ---------------------------------------------------------------------------
+// lab-frame samples (Sec. 3.2, PR-16): one transverse slice per row
+template <class T>
+__device__ __forceinline__ double interp_z3(const G3& g, const T* F, int i, int j, double zp, double stz) {
+  const double Z = zp / g.d[2] - stz;
+  const double kf = floor(Z);
+  const int k = (int)kf;
+  const double f = Z - kf;
+  return (1.0 - f) * (double)rd3(g, F, i, j, k) + f * (double)rd3(g, F, i, j, k + 1);
+}
+
+template <class T>
+__global__ void k3_btd(G3 g, const T* E, const T* B, T* out, int which, double wgt, double zp, double gam, double be) {
+  const int nyp = g.n[1] + 1;
+  const long plane = (long)(g.n[0] + 1) * nyp;
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= plane) return;
+  const int i = (int)(e / nyp), j = (int)(e - (long)i * nyp);
+  if (which == 0) {
+    const double ex = interp_z3(g, E, i, j, zp, 0.0);
+    const double ey = interp_z3(g, E + g.cs, i, j, zp, 0.0);
+    const double ez = interp_z3(g, E + 2 * g.cs, i, j, zp, 0.5);
+    out[0 * plane + e] += T(wgt * gam * ex);
+    out[1 * plane + e] += T(wgt * gam * ey);
+    out[2 * plane + e] += T(wgt * ez);
+    out[3 * plane + e] += T(wgt * (-gam * be * ey / kC));
+    out[4 * plane + e] += T(wgt * (gam * be * ex / kC));
+  } else {
+    const double bx = interp_z3(g, B, i, j, zp, 0.5);
+    const double by = interp_z3(g, B + g.cs, i, j, zp, 0.5);
+    const double bz = interp_z3(g, B + 2 * g.cs, i, j, zp, 0.0);
+    out[0 * plane + e] += T(wgt * gam * be * kC * by);
+    out[1 * plane + e] += T(wgt * (-gam * be * kC * bx));
+    out[3 * plane + e] += T(wgt * gam * bx);
+    out[4 * plane + e] += T(wgt * gam * by);
+    out[5 * plane + e] += T(wgt * bz);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// diagnostics: out [0] n_e, [1] n_beam_active, [2] sum gamma_lab, [3] sum gamma_lab^2, [4] field energy,
+// [5] weight of the electrons above the trapping threshold
+template <class T>
+__global__ void k3_stats(G3 g, const T* E, const T* B, Parts3<T> p, const Ctrl3* ctrl, Beam3<T> b, double gam,
+                         double be, double trap, double* out) {
+  __shared__ double red[6][256];
+  const long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long nthr = (long)gridDim.x * blockDim.x;
+  double v[6] = {0, 0, 0, 0, 0, 0};
+  for (long j = tid; j < ctrl->count; j += nthr) {
+    if (!(p.fl[j] & 1)) continue;
+    v[0] += 1.0;
+    if (trap > 0.0) {
+      const double ux = p.ux[j], uy = p.uy[j], uz = p.uz[j];
+      const double gp = sqrt(1.0 + (ux * ux + uy * uy + uz * uz) / (kC * kC));
+      if (gam * (gp + be * uz / kC) > trap) v[5] += (double)p.w[j];
+    }
+  }
+  for (long j = tid; j < b.n; j += nthr) {
+    if ((b.fl[j] & 3) != 3) continue;
+    const double ux = b.ux[j], uy = b.uy[j], uz = b.uz[j];
+    const double gp = sqrt(1.0 + (ux * ux + uy * uy + uz * uz) / (kC * kC));
+    const double gl = gam * (gp + be * uz / kC);
+    v[1] += 1; v[2] += gl; v[3] += gl * gl;
+  }
+  const double dV = g.d[0] * g.d[1] * g.d[2];
+  for (long q = tid; q < g.cs; q += nthr) {
+    const double e2 = (double)E[q] * E[q] + (double)E[g.cs + q] * E[g.cs + q] + (double)E[2 * g.cs + q] * E[2 * g.cs + q];
+    const double b2 = (double)B[q] * B[q] + (double)B[g.cs + q] * B[g.cs + q] + (double)B[2 * g.cs + q] * B[2 * g.cs + q];
+    v[4] += 0.5 * (kEps0 * e2 + b2 * (kEps0 * kC * kC)) * dV;
+  }
+  for (int c = 0; c < 6; c++) red[c][threadIdx.x] = v[c];
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o)
+      for (int c = 0; c < 6; c++) red[c][threadIdx.x] += red[c][threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int c = 0; c < 6; c++) atomicAdd(out + c, red[c][0]);
+}
+
+// ---------------------------------------------------------------------------
+// compaction of the live particles into the other buffer set
+__global__ void k3_live_per_block(const int* fl, const Ctrl3* ctrl, int* bc) {
+  __shared__ int s;
+  if (threadIdx.x == 0) s = 0;
+  __syncthreads();
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int live = (j < ctrl->count && (fl[j] & 1)) ? 1 : 0;
+  const int wsum = __popc(__ballot_sync(0xffffffffu, live));
+  if ((threadIdx.x & 31) == 0 && wsum) atomicAdd(&s, wsum);
+  __syncthreads();
+  if (threadIdx.x == 0) bc[blockIdx.x] = s;
+}
+
+// exclusive scan of nb block counts by one block of 1024 threads; the total becomes the new count
+__global__ void __launch_bounds__(1024) k3_scan_blocks(int* bc, int nb, Ctrl3* ctrl) {
+  __shared__ int part[1024];
+  const int per = (nb + 1023) / 1024;
+  const int b0 = threadIdx.x * per, b1 = min(nb, b0 + per);
+  int s = 0;
+  for (int b = b0; b < b1; b++) s += bc[b];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    const int v = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int run = part[threadIdx.x] - s;
+  for (int b = b0; b < b1; b++) {
+    const int c = bc[b];
+    bc[b] = run;
+    run += c;
+  }
+  if (threadIdx.x == 1023) ctrl->count = part[1023];
+}
+
+template <class T>
+__global__ void k3_scatter(Parts3<T> src, Parts3<T> dst, const int* bo, int n_old) {
+  __shared__ int wo[8];
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int live = (j < n_old && (src.fl[j] & 1)) ? 1 : 0;
+  const unsigned m = __ballot_sync(0xffffffffu, live);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) wo[wid] = __popc(m);
+  __syncthreads();
+  int off = bo[blockIdx.x];
+  for (int w = 0; w < wid; w++) off += wo[w];
+  if (!live) return;
+  const int q = off + __popc(m & ((1u << lane) - 1u));
+  dst.x[q] = src.x[j]; dst.y[q] = src.y[j]; dst.z[q] = src.z[j];
+  dst.ux[q] = src.ux[j]; dst.uy[q] = src.uy[j]; dst.uz[q] = src.uz[j];
+  dst.w[q] = src.w[j]; dst.id[q] = src.id[j]; dst.fl[q] = 1;
+}
+
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void k3_out_field(G3 g, const T* F, double* dst) {
+  int i, j, k;
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (!node_of(g, e, i, j, k)) return;
+  dst[e] = (double)F[nid(g, i, j, k)];
+}
+
+template <class T>
+__global__ void k3_in_field(G3 g, const double* src, T* F) {
+  int i, j, k;
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (!node_of(g, e, i, j, k)) return;
+  F[nid(g, i, j, k)] = T(src[e]);
+}
+
+__global__ void k3_out_rho(G3 g, const double* rho, double* dst) {
+  int i, j, k;
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (!node_of(g, e, i, j, k)) return;
+  dst[e] = rho[nid(g, i, j, k)];
+}
+
+// ---------------------------------------------------------------------------
+double cfl3(double a, double b, double gg, double dx, double dy, double dz, double theta) {
+  const double kx = 1.0 / (dx * dx), ky = 1.0 / (dy * dy), kz = 1.0 / (dz * dz);
+  double m = std::min(dx, std::min(dy, dz));
+  const double pair = std::max(kx + ky, std::max(kx + kz, ky + kz));
+  const double t1 = (a - 4.0 * gg) * pair, t2 = (a - 4.0 * b + 4.0 * gg) * (kx + ky + kz);
+  if (t1 > 0 && 1.0 / std::sqrt(t1) < m) m = 1.0 / std::sqrt(t1);
+  if (t2 > 0 && 1.0 / std::sqrt(t2) < m) m = 1.0 / std::sqrt(t2);
+  return m / kC * std::sqrt((2.0 + theta) / (2.0 + 3.0 * theta));
+}
+
+double host_sigma(const pic_config& c, double pos, int n, double d_cell) {
+  const int L = c.pml_cells;
+  if (L <= 0) return 0.0;
+  double d = 0.0;
+  if (pos < L) d = L - pos;
+  if (pos > n - L) d = pos - (n - L);
+  if (d <= 0.0) return 0.0;
+  return c.pml_sigma_max * kC / d_cell * std::pow(d / c.pml_delta, c.pml_power);
+}
+
+double shape_h(int order, double s) {
+  const double a = std::fabs(s);
+  if (order == 1) return a < 1.0 ? 1.0 - a : 0.0;
+  if (a < 1.0) return 2.0 / 3.0 - a * a + 0.5 * a * a * a;
+  if (a < 2.0) { const double t = 2.0 - a; return t * t * t / 6.0; }
+  return 0.0;
+}
+
+inline unsigned nblk(long n, int b) { return (unsigned)((n + b - 1) / b); }
+
+template <class T>
+struct Sim3 : Sim3Api {
+  pic_config cfg;
+  G3 g;
+  cudaStream_t s;
+  pic_alloc_fn alloc;
+  pic_free_fn freef;
+  void* user;
+  std::vector<std::pair<void*, size_t>> allocs;
+  std::string err;
+  int st = PIC_OK;
+  int64_t nl = 0;
+  double gamma = 1, beta = 0;
+  long step = 0;
+  // fields (3-component blocks)
+  T *E = nullptr, *B = nullptr, *J = nullptr, *Ep = nullptr, *Eb = nullptr, *Ee = nullptr;
+  T *Es = nullptr, *Bs = nullptr;     // 6 split parts each
+  T *fE = nullptr, *fB = nullptr, *tmp = nullptr;
+  double* rho = nullptr;              // scratch for PIC_RHO
+  double* out_d = nullptr;            // copy-out scratch
+  Pml3 pm;
+  Taps3<T> taps;
+  int P = 0;
+  // particles
+  Parts3<T> P2[2];
+  int cur = 0;
+  long cap = 0, count_ub = 0;
+  Ctrl3* ctrl = nullptr;
+  int* blk = nullptr;
+  long blk_cap = 0;
+  int compact_every = 16, since_compact = 0;
+  int64_t compactions = 0;
+  // plasma
+  bool loaded = false;
+  Lat3 lat;
+  long long row_next = 0, mlo = 0;
+  double* Tx = nullptr;
+  double* Ty = nullptr;
+  double* Zs = nullptr;
+  bool ions = false;
+  // laser
+  bool has_laser = false;
+  pic_laser las;
+  double E0 = 0, Qpair = 0, Dn = 0;
+  // beam
+  Beam3<T> bm{};
+  bool has_beam = false;
+  double* bacc = nullptr;
+  double* sred = nullptr;
+  // lab samples
+  std::vector<double> rz, rt;
+  std::vector<int> rdone;
+  T* rout = nullptr;
+  // timing
+  bool timing_on = false;
+  double t_ms = 0;
+  int64_t t_n = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+  ~Sim3() override {
+    if (s) cudaStreamSynchronize(s);
+    for (auto& a : allocs) {
+      if (freef) freef(a.first, a.second, (void*)s, user);
+      else cudaFree(a.first);
+    }
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+  }
+
+  int fail(int code, const std::string& m) {
+    if (st == PIC_OK) { st = code; err = m; }
+    return code;
+  }
+
+  template <class X>
+  X* dal(size_t n) {
+    size_t bytes = (n * sizeof(X) + 255) & ~size_t(255);
+    if (!bytes) bytes = 256;
+    void* p = nullptr;
+    if (alloc) p = alloc(bytes, (void*)s, user);
+    else if (cudaMalloc(&p, bytes) != cudaSuccess) p = nullptr;
+    if (!p) return nullptr;
+    allocs.emplace_back(p, bytes);
+    cudaMemsetAsync(p, 0, bytes, s);
+    return (X*)p;
+  }
+
+  void dfree(void* p) {
+    for (size_t i = 0; i < allocs.size(); i++)
+      if (allocs[i].first == p) {
+        cudaStreamSynchronize(s);
+        if (freef) freef(p, allocs[i].second, (void*)s, user);
+        else cudaFree(p);
+        allocs.erase(allocs.begin() + i);
+        return;
+      }
+  }
+
+  long nodes() const { return (long)(g.n[0] + 1) * (g.n[1] + 1) * (g.n[2] + 1); }
+
+  int init(const pic_config* c) {
+    cfg = *c;
+    gamma = c->gamma_boost < 1.0 ? 1.0 : c->gamma_boost;
+    beta = std::sqrt(1.0 - 1.0 / (gamma * gamma));
+    g.n[0] = c->nx; g.n[1] = c->ny; g.n[2] = c->nz;
+    g.d[0] = c->dx; g.d[1] = c->dy; g.d[2] = (1.0 + beta) * gamma * c->dz_lab;   // Sec. 5.1.1
+    const double dt_cfl = cfl3(c->ck_alpha, c->ck_beta, c->ck_gamma, g.d[0], g.d[1], g.d[2], c->theta);
+    g.dt = c->dt > 0.0 ? c->dt : c->courant * dt_cfl;
+    if (!(g.dt > 0.0)) return fail(PIC_EINVAL, "dt <= 0");
+    if (g.dt > dt_cfl * (1.0 + 1e-12)) return fail(PIC_ECFL, "dt above the 3D stability limit");
+    P = c->filter_passes + (c->filter_compensate ? 1 : 0);
+    const int guard = c->particle_guard >= 0 ? c->particle_guard : (c->shape_order == 3 ? 3 : 2) + P * c->filter_stride + 2;
+    if (guard < (c->shape_order == 3 ? 3 : 2) + P * c->filter_stride + 1) return fail(PIC_EINVAL, "particle guard too small");
+    for (int a = 0; a < 3; a++) {
+      g.lo[a] = c->pml_cells + guard;
+      g.hi[a] = g.n[a] - c->pml_cells - guard;
+      if (g.hi[a] - g.lo[a] < 2 || g.lo[a] < 4) return fail(PIC_EINVAL, "3D box too small for the PML and guard");
+    }
+    const int align = 128 / (int)sizeof(T);
+    g.ldz = ((c->nz + 1 + align - 1) / align) * align;
+    g.cs = (long)(c->nx + 1) * (c->ny + 1) * g.ldz;
+    const size_t cs = (size_t)g.cs;
+    E = dal<T>(3 * cs); B = dal<T>(3 * cs); J = dal<T>(3 * cs); Ep = dal<T>(3 * cs); Eb = dal<T>(3 * cs);
+    Ee = dal<T>(3 * cs); fE = dal<T>(3 * cs); fB = dal<T>(3 * cs); tmp = dal<T>(cs);
+    Es = dal<T>(6 * cs); Bs = dal<T>(6 * cs);
+    ctrl = dal<Ctrl3>(1);
+    bacc = dal<double>(8);
+    sred = dal<double>(8);
+    if (!E || !B || !J || !Ep || !Eb || !Ee || !fE || !fB || !tmp || !Es || !Bs || !ctrl || !bacc || !sred)
+      return fail(PIC_ENOMEM, "allocation failed");
+    // PML tables per axis, integer and half positions
+    for (int a = 0; a < 3; a++) {
+      const int n = g.n[a];
+      std::vector<double> sgv(n + 2), xiv(n + 2), cfv(n + 2);
+      for (int h = 0; h < 2; h++) {
+        for (int i = 0; i <= n + 1; i++) {
+          const double sg = i <= n ? host_sigma(cfg, i + 0.5 * h, n, g.d[a]) : 0.0;
+          const double xi = c->pml_xi_exp ? std::exp(-sg * g.dt) : (1.0 - 0.5 * sg * g.dt) / (1.0 + 0.5 * sg * g.dt);
+          sgv[i] = sg;
+          xiv[i] = xi;
+          cfv[i] = sg > 0.0 ? (1.0 - xi) / sg : g.dt;
+        }
+        double* d_s = dal<double>(n + 2);
+        double* d_x = dal<double>(n + 2);
+        double* d_c = dal<double>(n + 2);
+        if (!d_s || !d_x || !d_c) return fail(PIC_ENOMEM, "allocation failed");
+        cudaMemcpyAsync(d_s, sgv.data(), sizeof(double) * (n + 2), cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(d_x, xiv.data(), sizeof(double) * (n + 2), cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(d_c, cfv.data(), sizeof(double) * (n + 2), cudaMemcpyHostToDevice, s);
+        cudaStreamSynchronize(s);
+        pm.sg[a][h] = d_s; pm.xi[a][h] = d_x; pm.cf[a][h] = d_c;
+      }
+    }
+    // composed filter taps along one axis: P passes of (1-a)/2, a, (1-a)/2 at stride s
+    std::vector<double> t(2 * P + 1, 0.0);
+    t[P] = 1.0;
+    for (int q = 0; q < P; q++) {
+      const double al = q < c->filter_passes ? 0.5 : 0.5 * c->filter_passes + 1.0;
+      std::vector<double> o(2 * P + 1, 0.0);
+      for (int m = 0; m <= 2 * P; m++) {
+        o[m] += al * t[m];
+        if (m > 0) o[m] += 0.5 * (1.0 - al) * t[m - 1];
+        if (m < 2 * P) o[m] += 0.5 * (1.0 - al) * t[m + 1];
+      }
+      t = o;
+    }
+    for (int m = 0; m < 33; m++) taps.c[m] = m <= 2 * P ? T(t[m]) : T(0);
+    taps.P = P;
+    taps.s = c->filter_stride;
+    cudaEventCreate(&ev0);
+    cudaEventCreate(&ev1);
+    return cudaGetLastError() == cudaSuccess ? PIC_OK : fail(PIC_ECUDA, "CUDA error in 3D init");
+  }
+
+  // ---- particles --------------------------------------------------------
+  int alloc_parts(long n) {
+    for (int b = 0; b < 2; b++) {
+      Parts3<T>& q = P2[b];
+      q.x = dal<double>(n); q.y = dal<double>(n); q.z = dal<double>(n);
+      q.ux = dal<T>(n); q.uy = dal<T>(n); q.uz = dal<T>(n); q.w = dal<T>(n);
+      q.id = dal<uint32_t>(n); q.fl = dal<int>(n);
+      if (!q.x || !q.y || !q.z || !q.ux || !q.uy || !q.uz || !q.w || !q.id || !q.fl) return PIC_ENOMEM;
+    }
+    cap = n;
+    return PIC_OK;
+  }
+
+  void free_parts(Parts3<T>& q) {
+    void* ps[9] = {q.x, q.y, q.z, q.ux, q.uy, q.uz, q.w, q.id, q.fl};
+    for (void* p : ps) if (p) dfree(p);
+    q = Parts3<T>{};
+  }
+
+  int read_count() {
+    int c = 0;
+    cudaMemcpyAsync(&c, &ctrl->count, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return -1;
+    return c;
+  }
+
+  int compact() {
+    const int n_old = read_count();
+    if (n_old < 0) return fail(PIC_ECUDA, "CUDA error before compaction");
+    if (n_old == 0) { count_ub = 0; return PIC_OK; }
+    const long nb = (n_old + 255) / 256;
+    if (nb > blk_cap) {
+      if (blk) dfree(blk);
+      blk = dal<int>(nb);
+      if (!blk) return fail(PIC_ENOMEM, "allocation failed");
+      blk_cap = nb;
+    }
+    k3_live_per_block<<<(unsigned)nb, 256, 0, s>>>(P2[cur].fl, ctrl, blk);
+    k3_scan_blocks<<<1, 1024, 0, s>>>(blk, (int)nb, ctrl);
+    k3_scatter<T><<<(unsigned)nb, 256, 0, s>>>(P2[cur], P2[1 - cur], blk, n_old);
+    nl += 3;
+    cur = 1 - cur;
+    const int n_new = read_count();
+    if (n_new < 0) return fail(PIC_ECUDA, "CUDA error in compaction");
+    count_ub = n_new;
+    since_compact = 0;
+    compactions++;
+    return PIC_OK;
+  }
+
+  int grow(long need) {
+    long ncap = std::max(need + need / 4, 2 * cap);
+    Parts3<T> old[2] = {P2[0], P2[1]};
+    const int c = read_count();
+    if (c < 0) return fail(PIC_ECUDA, "CUDA error");
+    P2[0] = Parts3<T>{}; P2[1] = Parts3<T>{};
+    const long ocap = cap;
+    if (alloc_parts(ncap) != PIC_OK) return fail(PIC_ENOMEM, "particle allocation failed");
+    const Parts3<T>& o = old[cur];
+    Parts3<T>& d = P2[cur];
+    if (c > 0) {
+      cudaMemcpyAsync(d.x, o.x, 8 * (size_t)c, cudaMemcpyDeviceToDevice, s);
+      cudaMemcpyAsync(d.y, o.y, 8 * (size_t)c, cudaMemcpyDeviceToDevice, s);
+      cudaMemcpyAsync(d.z, o.z, 8 * (size_t)c, cudaMemcpyDeviceToDevice, s);
+      cudaMemcpyAsync(d.ux, o.ux, sizeof(T) * c, cudaMemcpyDeviceToDevice, s);
+      cudaMemcpyAsync(d.uy, o.uy, sizeof(T) * c, cudaMemcpyDeviceToDevice, s);
+      cudaMemcpyAsync(d.uz, o.uz, sizeof(T) * c, cudaMemcpyDeviceToDevice, s);
+      cudaMemcpyAsync(d.w, o.w, sizeof(T) * c, cudaMemcpyDeviceToDevice, s);
+      cudaMemcpyAsync(d.id, o.id, 4 * (size_t)c, cudaMemcpyDeviceToDevice, s);
+      cudaMemcpyAsync(d.fl, o.fl, 4 * (size_t)c, cudaMemcpyDeviceToDevice, s);
+    }
+    (void)ocap;
+    free_parts(old[0]);
+    free_parts(old[1]);
+    return cudaStreamSynchronize(s) == cudaSuccess ? PIC_OK : fail(PIC_ECUDA, "CUDA error while growing");
+  }
+
+  double z_hi() const { return g.hi[2] * g.d[2]; }
+  double z_lo() const { return g.lo[2] * g.d[2]; }
+  double time_of(long n) const { return (double)n * g.dt; }
+
+  long long rows_inside(double t) const { return (long long)std::ceil((z_hi() + beta * kC * t) / lat.h - 0.5); }
+
+  double row_density(long long m) const { return gamma * lab_density3(lat, gamma * ((m + 0.5) * lat.h)); }
+
+  // create the electron rows [m0, m1) with density > 0 at time t
+  int inject_rows(long long m0, long long m1, double t) {
+    std::vector<long long> rows;
+    for (long long m = m0; m < m1; m++)
+      if (row_density(m) > 0.0) rows.push_back(m);
+    const long per = (long)lat.nxl * lat.nyl;
+    const long add = (long)rows.size() * per;
+    if (add == 0) return PIC_OK;
+    if (count_ub + add > cap) {
+      if (compact() != PIC_OK) return st;
+      if (count_ub + add > cap && grow(count_ub + add) != PIC_OK) return st;
+    }
+    for (size_t r0 = 0; r0 < rows.size(); r0 += 8) {
+      Rows8 R;
+      R.n = (int)std::min<size_t>(8, rows.size() - r0);
+      for (int q = 0; q < R.n; q++) R.m[q] = rows[r0 + q];
+      const long n = per * R.n;
+      k3_inject<T><<<nblk(n, 256), 256, 0, s>>>(g, P2[cur], ctrl, lat, R, t);
+      k3_add_count<<<1, 1, 0, s>>>(ctrl, (int)n);
+      nl += 2;
+      count_ub += n;
+    }
+    return PIC_OK;
+  }
+
+  int load_plasma(const pic_plasma* p) override {
+    if (loaded) return fail(PIC_ESTATE, "plasma already loaded");
+    const int ppc_y = p->ppc_y > 0 ? p->ppc_y : 1;
+    if (p->ppc_x < 1 || p->ppc_z < 1 || p->n0 < 0) return fail(PIC_EINVAL, "bad plasma");
+    lat.h = g.d[2] / p->ppc_z;
+    lat.gamma = gamma; lat.beta = beta;
+    lat.n0 = p->n0; lat.z_start_lab = p->z_start_lab; lat.ramp_lab = p->ramp_lab; lat.length_lab = p->length_lab;
+    lat.ppc[0] = p->ppc_x; lat.ppc[1] = ppc_y; lat.ppc[2] = p->ppc_z;
+    lat.nxl = (g.hi[0] - g.lo[0]) * p->ppc_x;
+    lat.nyl = (g.hi[1] - g.lo[1]) * ppc_y;
+    ions = p->ions != 0;
+    const double t = time_of(step);
+    const long long m_end = rows_inside(t);
+    const long long m_beg = (long long)std::ceil((z_lo() + beta * kC * t) / lat.h - 0.5);
+    const long per = (long)lat.nxl * lat.nyl;
+    const long rows_box = m_end - m_beg + 1;
+    const double rows_per_step = beta * kC * g.dt / lat.h + 1.0;
+    long want = (long)((rows_box + rows_per_step * (compact_every + 2)) * per * 1.1) + 1024;
+    if (alloc_parts(want) != PIC_OK) return fail(PIC_ENOMEM, "particle allocation failed");
+    count_ub = 0;
+    if (inject_rows(m_beg, m_end, t) != PIC_OK) return st;
+    row_next = m_end;
+    mlo = m_beg;
+    if (ions) {
+      std::vector<double> tx(g.n[0] + 1, 0.0), ty(g.n[1] + 1, 0.0);
+      for (int a = 0; a < lat.nxl; a++) {
+        const double X = g.lo[0] + (a + 0.5) / lat.ppc[0];
+        for (int i = 0; i <= g.n[0]; i++) tx[i] += shape_h(cfg.shape_order, X - i);
+      }
+      for (int b = 0; b < lat.nyl; b++) {
+        const double Y = g.lo[1] + (b + 0.5) / lat.ppc[1];
+        for (int j = 0; j <= g.n[1]; j++) ty[j] += shape_h(cfg.shape_order, Y - j);
+      }
+      Tx = dal<double>(g.n[0] + 1); Ty = dal<double>(g.n[1] + 1); Zs = dal<double>(g.n[2] + 1);
+      if (!Tx || !Ty || !Zs) return fail(PIC_ENOMEM, "allocation failed");
+      cudaMemcpyAsync(Tx, tx.data(), sizeof(double) * tx.size(), cudaMemcpyHostToDevice, s);
+      cudaMemcpyAsync(Ty, ty.data(), sizeof(double) * ty.size(), cudaMemcpyHostToDevice, s);
+      cudaStreamSynchronize(s);
+    }
+    // optional test beam
+    if (p->beam_n > 0) {
+      if (!p->beam_x || !p->beam_y || !p->beam_z || !p->beam_ux || !p->beam_uy || !p->beam_uz)
+        return fail(PIC_EINVAL, "3D test beam needs x, y, z and the three momenta");
+      const int n = (int)p->beam_n;
+      bm.n = n;
+      bm.x = dal<double>(n); bm.y = dal<double>(n); bm.z = dal<double>(n);
+      bm.ux = dal<T>(n); bm.uy = dal<T>(n); bm.uz = dal<T>(n);
+      bm.tc = dal<double>(n); bm.zf0 = dal<double>(n);
+      bm.uxb = dal<T>(n); bm.uyb = dal<T>(n); bm.uzb = dal<T>(n); bm.fl = dal<int>(n);
+      double* lab = dal<double>(6 * (size_t)n);
+      if (!bm.x || !bm.fl || !lab) return fail(PIC_ENOMEM, "allocation failed");
+      const double* srcs[6] = {p->beam_x, p->beam_y, p->beam_z, p->beam_ux, p->beam_uy, p->beam_uz};
+      for (int q = 0; q < 6; q++)
+        cudaMemcpyAsync(lab + (size_t)q * n, srcs[q], 8 * (size_t)n, cudaMemcpyHostToDevice, s);
+      cudaMemsetAsync(bacc, 0, 8 * sizeof(double), s);
+      k3_beam_vz<<<nblk(n, 256), 256, 0, s>>>(n, lab + 3 * (size_t)n, lab + 4 * (size_t)n, lab + 5 * (size_t)n, bacc);
+      k3_beam_transform<T><<<nblk(n, 256), 256, 0, s>>>(bm, lab, lab + n, lab + 2 * (size_t)n, lab + 3 * (size_t)n,
+                                                        lab + 4 * (size_t)n, lab + 5 * (size_t)n, p->beam_t_lab,
+                                                        p->beam_z_plane_lab, gamma, beta, bacc);
+      k3_beam_finish<T><<<nblk(n, 256), 256, 0, s>>>(bm, time_of(step), bacc);
+      nl += 3;
+      cudaStreamSynchronize(s);
+      dfree(lab);
+      has_beam = true;
+    }
+    loaded = true;
+    return cudaGetLastError() == cudaSuccess ? PIC_OK : fail(PIC_ECUDA, "CUDA error in 3D plasma load");
+  }
+
+  int set_laser(const pic_laser* l) override {
+    if (l->beta_s != 0.0) return fail(PIC_EINVAL, "3D antenna: the plane is at rest in the computational frame");
+    las = *l;
+    const double om = 2.0 * kPi * kC / l->lambda0;
+    E0 = l->a0 * kMe * kC * om / kQe;
+    const double dop = (1.0 + beta) * gamma;
+    Qpair = 200.0 * kEps0 * E0 * g.d[0] * g.d[1] / dop;
+    Dn = 0.0;
+    has_laser = true;
+    return PIC_OK;
+  }
+
+  bool antenna_inside() const { return has_laser && las.z_antenna >= z_lo() && las.z_antenna < z_hi(); }
+
+  // time factor of the emitted field: E_emit = G(x, y) emit_t(t'), PR-14 with beta_s = 0
+  double emit_t(double tp) const {
+    const double om = 2.0 * kPi * kC / las.lambda0;
+    const double dop = (1.0 + beta) * gamma;
+    const double sl = tp / dop;
+    const double sig = las.tau_fwhm / (2.0 * std::sqrt(std::log(2.0)));
+    return E0 * std::exp(-(sl - las.t_peak) * (sl - las.t_peak) / (2.0 * sig * sig)) *
+           std::sin(om * (sl - las.t_peak) + las.phase) / dop;
+  }
+
+  Ant3 ant_params(double D0, double D1) const {
+    Ant3 a;
+    a.x_center = las.x_center; a.y_center = las.y_center; a.w0 = las.w0; a.za = las.z_antenna;
+    a.D0 = D0; a.D1 = D1; a.Q = Qpair; a.order = cfg.shape_order;
+    return a;
+  }
+
+  // ---- one step (order of PR-1) ------------------------------------------
+  void btd_part(int which, int post) {
+    if (rz.empty()) return;
+    const long plane = (long)(g.n[0] + 1) * (g.n[1] + 1);
+    for (size_t r = 0; r < rz.size(); r++) {
+      const double tp = gamma * (rt[r] - beta * rz[r] / kC);
+      const double zp = gamma * (rz[r] - beta * kC * rt[r]);
+      double ta, tb;
+      if (which == 0) { ta = time_of(step); tb = time_of(step + 1); }
+      else { ta = time_of(step) - 0.5 * g.dt; tb = ta + g.dt; }
+      if (!(tp >= ta && tp < tb)) continue;
+      const double f = (tp - ta) / g.dt;
+      const double wgt = post ? f : 1.0 - f;
+      k3_btd<T><<<nblk(plane, 256), 256, 0, s>>>(g, E, B, rout + r * 6 * plane, which, wgt, zp, gamma, beta);
+      nl++;
+      if (post) rdone[2 * r + which] = 1;
+    }
+  }
+
+  void filter3(T* F, int comp) {
+    // x: F -> tmp, y: tmp -> F, z: F -> tmp, then tmp -> F by a copy
+    const long nn = nodes();
+    k3_filter_axis<T><<<nblk(nn, 256), 256, 0, s>>>(g, F, tmp, comp, 0, taps);
+    k3_filter_axis<T><<<nblk(nn, 256), 256, 0, s>>>(g, tmp, F, comp, 1, taps);
+    k3_filter_axis<T><<<nblk(nn, 256), 256, 0, s>>>(g, F, tmp, comp, 2, taps);
+    cudaMemcpyAsync(F, tmp, sizeof(T) * g.cs, cudaMemcpyDeviceToDevice, s);
+    nl += 3;
+  }
+
+  int one_step() {
+    const long nn = nodes();
+    const long n3 = 3 * g.cs;
+    const double th = cfg.theta;
+    btd_part(0, 0);
+    btd_part(1, 0);
+    // 1. Faraday + Friedman + PML-B (B^{n-1/2} -> B^{n+1/2}), gather copies
+    k3_eeff<T><<<nblk(n3, 256), 256, 0, s>>>(n3, E, Ep, Eb, Ee, T(1.0 + th / 4.0), T(0.5), T(0.5 - th / 4.0));
+    k3_faraday<T><<<nblk(nn, 128), 128, 0, s>>>(g, pm, Ee, B, Bs, fB, T(cfg.ck_alpha), T(cfg.ck_beta),
+                                                 T(cfg.ck_gamma), T(g.dt));
+    k3_friedman<T><<<nblk(n3, 256), 256, 0, s>>>(n3, E, Ep, Eb, fE, T(1.0 - th / 2.0), T(th / 2.0));
+    nl += 3;
+    if (cfg.filter_gather && P > 0)
+      for (int c = 0; c < 3; c++) { filter3(fE + c * g.cs, c); filter3(fB + c * g.cs, 3 + c); }
+    // 2. particles
+    cudaMemsetAsync(J, 0, sizeof(T) * 3 * g.cs, s);
+    Fld3<T> f;
+    for (int c = 0; c < 3; c++) { f.fE[c] = fE + c * g.cs; f.fB[c] = fB + c * g.cs; f.J[c] = J + c * g.cs; }
+    const T kq = T(-kQe * g.dt / (2.0 * kMe));
+    if (loaded && count_ub > 0) {
+      if (timing_on) cudaEventRecord(ev0, s);
+      if (cfg.shape_order == 3)
+        k3_push<T, 3><<<nblk(count_ub, 128), 128, 0, s>>>(g, f, P2[cur], ctrl, kq, -kQe);
+      else
+        k3_push<T, 1><<<nblk(count_ub, 128), 128, 0, s>>>(g, f, P2[cur], ctrl, kq, -kQe);
+      nl++;
+      if (timing_on) {
+        cudaEventRecord(ev1, s);
+        cudaEventSynchronize(ev1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, ev0, ev1);
+        t_ms += ms;
+        t_n++;
+      }
+    }
+    const double tn = time_of(step), tn1 = time_of(step + 1);
+    if (loaded && ions && row_next > mlo) {
+      k3_ion_z<<<nblk(g.n[2] + 1, 128), 128, 0, s>>>(g, lat, cfg.shape_order, mlo, row_next, tn, tn1, Zs);
+      k3_ion_jz<T><<<nblk(nn, 256), 256, 0, s>>>(g, Tx, Ty, Zs, -kQe / (g.d[0] * g.d[1] * g.dt), J + 2 * g.cs);
+      nl += 2;
+    }
+    if (has_beam) {
+      if (cfg.shape_order == 3)
+        k3_beam_push<T, 3><<<nblk(bm.n, 128), 128, 0, s>>>(g, f, bm, tn, tn1, bacc, kq);
+      else
+        k3_beam_push<T, 1><<<nblk(bm.n, 128), 128, 0, s>>>(g, f, bm, tn, tn1, bacc, kq);
+      nl++;
+    }
+    // 3. antenna: the moving partners' displacement G(x, y) D_n -> G D_{n+1}
+    if (antenna_inside()) {
+      const double th_ = tn + 0.5 * g.dt;
+      const double dD = -2.0 * kEps0 * kC * emit_t(th_) * g.d[0] * g.d[1] / Qpair * g.dt;
+      const Ant3 a = ant_params(Dn, Dn + dD);
+      const int npair = (g.hi[0] - g.lo[0] + 1) * (g.hi[1] - g.lo[1] + 1);
+      k3_antenna<T><<<nblk(npair, 128), 128, 0, s>>>(g, J + g.cs, a);
+      nl++;
+      Dn += dD;
+    }
+    // 4. current filter, Ampere + PML-E
+    if (cfg.filter_J && P > 0)
+      for (int c = 0; c < 3; c++) filter3(J + c * g.cs, c);
+    k3_ampere<T><<<nblk(nn, 128), 128, 0, s>>>(g, pm, E, Es, B, J, T(g.dt * kC * kC), T(g.dt / kEps0));
+    nl++;
+    btd_part(0, 1);
+    btd_part(1, 1);
+    // 5. ion rows that left the particle domain, inflow through z_hi
+    if (loaded) {
+      while (mlo < row_next && (mlo + 0.5) * lat.h - beta * kC * tn1 < z_lo()) mlo++;
+      const long long m_end = rows_inside(tn1);
+      if (m_end > row_next) {
+        if (inject_rows(row_next, m_end, tn1) != PIC_OK) return st;
+        row_next = m_end;
+      }
+      if (++since_compact >= compact_every && compact() != PIC_OK) return st;
+    }
+    step++;
+    return PIC_OK;
+  }
+
+  int run(int n) override {
+    if (st != PIC_OK) return st;
+    for (int q = 0; q < n; q++)
+      if (one_step() != PIC_OK) return st;
+    return cudaGetLastError() == cudaSuccess ? PIC_OK : fail(PIC_ECUDA, "CUDA error in 3D step");
+  }
+
+  int sync() override {
+    const cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(PIC_ECUDA, std::string("CUDA error: ") + cudaGetErrorString(e));
+    return st;
+  }
+
+  // ---- lab-frame samples -------------------------------------------------
+  int btd_set(const pic_btd_req* r) override {
+    if (r->n_rows <= 0 || !r->z_lab || !r->t_lab) return fail(PIC_EINVAL, "empty lab-sample request");
+    rz.assign(r->z_lab, r->z_lab + r->n_rows);
+    rt.assign(r->t_lab, r->t_lab + r->n_rows);
+    rdone.assign(2 * r->n_rows, 0);
+    if (rout) dfree(rout);
+    rout = dal<T>((size_t)r->n_rows * 6 * (g.n[0] + 1) * (g.n[1] + 1));
+    return rout ? PIC_OK : fail(PIC_ENOMEM, "allocation failed");
+  }
+
+  int btd_get(pic_btd_out* o) override {
+    if (!rout) return fail(PIC_ESTATE, "no lab-sample request");
+    const size_t n = rz.size() * 6 * (size_t)(g.n[0] + 1) * (g.n[1] + 1);
+    cudaMemcpyAsync(o->data, rout, n * sizeof(T), o->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
+    long long filled = 0;
+    for (size_t r = 0; r < rz.size(); r++) filled += rdone[2 * r] && rdone[2 * r + 1];
+    if (o->done)
+      cudaMemcpyAsync(o->done, rdone.data(), sizeof(int) * rdone.size(),
+                      o->on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, s);
+    o->n_rows_filled = filled;
+    return cudaStreamSynchronize(s) == cudaSuccess ? PIC_OK : fail(PIC_ECUDA, "CUDA error in btd_get");
+  }
+
+  // ---- accessors -----------------------------------------------------------
+  const T* comp_ptr(int comp) const {
+    if (comp < 3) return E + comp * g.cs;
+    if (comp < 6) return B + (comp - 3) * g.cs;
+    return J + (comp - 6) * g.cs;
+  }
+
+  int get_field(int comp, double* dst, int on_device) override {
+    if (comp < 0 || comp > PIC_RHO) return fail(PIC_EINVAL, "bad component");
+    const long nn = nodes();
+    if (!out_d) { out_d = dal<double>(nn); if (!out_d) return fail(PIC_ENOMEM, "allocation failed"); }
+    if (comp == PIC_RHO) {
+      if (!rho) { rho = dal<double>(g.cs); if (!rho) return fail(PIC_ENOMEM, "allocation failed"); }
+      cudaMemsetAsync(rho, 0, sizeof(double) * g.cs, s);
+      if (loaded && count_ub > 0) {
+        k3_particle_rho<T><<<nblk(count_ub, 128), 128, 0, s>>>(g, P2[cur], ctrl, cfg.shape_order, -kQe, rho);
+        nl++;
+      }
+      if (loaded && ions && row_next > mlo) {
+        k3_ion_rho<<<nblk(nn, 128), 128, 0, s>>>(g, lat, cfg.shape_order, mlo, row_next, time_of(step), Tx, Ty, rho);
+        nl++;
+      }
+      if (antenna_inside() && Dn != 0.0) {
+        const int npair = (g.hi[0] - g.lo[0] + 1) * (g.hi[1] - g.lo[1] + 1);
+        k3_antenna_rho<<<nblk(npair, 128), 128, 0, s>>>(g, ant_params(Dn, Dn), rho);
+        nl++;
+      }
+      k3_out_rho<<<nblk(nn, 256), 256, 0, s>>>(g, rho, out_d);
+    } else {
+      k3_out_field<T><<<nblk(nn, 256), 256, 0, s>>>(g, comp_ptr(comp), out_d);
+    }
+    nl++;
+    cudaMemcpyAsync(dst, out_d, sizeof(double) * nn, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
+    return cudaStreamSynchronize(s) == cudaSuccess ? PIC_OK : fail(PIC_ECUDA, "CUDA error in get_field");
+  }
+
+  int set_field(int comp, const double* src) override {
+    if (comp < 0 || comp > 8) return fail(PIC_EINVAL, "bad component");
+    const long nn = nodes();
+    if (!out_d) { out_d = dal<double>(nn); if (!out_d) return fail(PIC_ENOMEM, "allocation failed"); }
+    cudaMemcpyAsync(out_d, src, sizeof(double) * nn, cudaMemcpyHostToDevice, s);
+    k3_in_field<T><<<nblk(nn, 256), 256, 0, s>>>(g, out_d, const_cast<T*>(comp_ptr(comp)));
+    nl++;
+    return cudaStreamSynchronize(s) == cudaSuccess ? PIC_OK : fail(PIC_ECUDA, "CUDA error in set_field");
+  }
+
+  int get_particles(int species, double* x, double* y, double* z, double* ux, double* uy, double* uz, double* w,
+                    uint32_t* id, int32_t* flags, int64_t* count) override {
+    if (species != PIC_ELECTRONS && species != PIC_BEAM) return fail(PIC_EINVAL, "bad species");
+    std::vector<int> fl;
+    long n = 0;
+    const bool el = species == PIC_ELECTRONS;
+    if (el) {
+      if (!loaded) { *count = 0; return PIC_OK; }
+      n = read_count();
+      if (n < 0) return fail(PIC_ECUDA, "CUDA error");
+    } else {
+      n = has_beam ? bm.n : 0;
+    }
+    fl.resize(n);
+    if (n) cudaMemcpy(fl.data(), el ? P2[cur].fl : bm.fl, 4 * (size_t)n, cudaMemcpyDeviceToHost);
+    long live = 0;
+    for (long q = 0; q < n; q++) live += (fl[q] & 1) != 0;
+    if (!x && !y && !z && !ux && !uy && !uz && !w && !id && !flags) { *count = live; return PIC_OK; }
+    if (*count < live) return fail(PIC_EINVAL, "output capacity too small");
+    std::vector<double> vd(n);
+    std::vector<T> vt(n);
+    std::vector<uint32_t> vi(n);
+    auto pickd = [&](const double* src, double* dst) {
+      if (!dst || !n) return;
+      cudaMemcpy(vd.data(), src, 8 * (size_t)n, cudaMemcpyDeviceToHost);
+      long o = 0;
+      for (long q = 0; q < n; q++) if (fl[q] & 1) dst[o++] = vd[q];
+    };
+    auto pickt = [&](const T* src, double* dst) {
+      if (!dst || !n) return;
+      cudaMemcpy(vt.data(), src, sizeof(T) * (size_t)n, cudaMemcpyDeviceToHost);
+      long o = 0;
+      for (long q = 0; q < n; q++) if (fl[q] & 1) dst[o++] = (double)vt[q];
+    };
+    if (el) {
+      const Parts3<T>& p = P2[cur];
+      pickd(p.x, x); pickd(p.y, y); pickd(p.z, z); pickt(p.ux, ux); pickt(p.uy, uy); pickt(p.uz, uz); pickt(p.w, w);
+      if (id && n) {
+        cudaMemcpy(vi.data(), p.id, 4 * (size_t)n, cudaMemcpyDeviceToHost);
+        long o = 0;
+        for (long q = 0; q < n; q++) if (fl[q] & 1) id[o++] = vi[q];
+      }
+    } else {
+      pickd(bm.x, x); pickd(bm.y, y); pickd(bm.z, z); pickt(bm.ux, ux); pickt(bm.uy, uy); pickt(bm.uz, uz);
+      if (w) { long o = 0; for (long q = 0; q < n; q++) if (fl[q] & 1) w[o++] = 1.0; }
+      if (id) { long o = 0; for (long q = 0; q < n; q++) if (fl[q] & 1) id[o++] = (uint32_t)q; }
+    }
+    if (flags) { long o = 0; for (long q = 0; q < n; q++) if (fl[q] & 1) flags[o++] = fl[q]; }
+    *count = live;
+    return cudaGetLastError() == cudaSuccess ? PIC_OK : fail(PIC_ECUDA, "CUDA error in get_particles");
+  }
+
+  int stats(pic_stats* o) override {
+    double trap = o->trap_gamma_lab > 0.0 ? o->trap_gamma_lab : 0.0;
+    if (trap == 0.0 && has_laser && loaded && lat.n0 > 0.0) {
+      const double wp = std::sqrt(lat.n0 * kQe * kQe / (kEps0 * kMe));
+      trap = 2.0 * (2.0 * kPi * kC / las.lambda0) / wp;
+    }
+    cudaMemsetAsync(sred, 0, 8 * sizeof(double), s);
+    k3_stats<T><<<304, 256, 0, s>>>(g, E, B, P2[cur], ctrl, bm, gamma, beta, trap, sred);
+    nl++;
+    double h[8];
+    cudaMemcpyAsync(h, sred, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return fail(PIC_ECUDA, "CUDA error in stats");
+    o->step = step; o->t = time_of(step);
+    o->dt = g.dt; o->dx = g.d[0]; o->dz = g.d[2]; o->gamma = gamma; o->beta = beta;
+    o->n_electrons = loaded ? (int64_t)h[0] : 0;
+    o->n_beam_active = (int64_t)h[1];
+    o->beam_gamma_lab = h[1] > 0 ? h[2] / h[1] : 0.0;
+    const double var = h[1] > 0 ? h[3] / h[1] - o->beam_gamma_lab * o->beam_gamma_lab : 0.0;
+    o->beam_spread = o->beam_gamma_lab > 0 ? std::sqrt(var > 0 ? var : 0) / o->beam_gamma_lab : 0.0;
+    o->field_energy = h[4];
+    o->gx_lo = g.lo[0]; o->gx_hi = g.hi[0]; o->gz_lo = g.lo[2]; o->gz_hi = g.hi[2];
+    o->sorts = compactions; o->overflow_chunks = 0;
+    o->z0 = 0.0;
+    o->trap_gamma_lab = trap;
+    o->trapped_charge = kQe * h[5];
+    return PIC_OK;
+  }
+
+  int64_t launches() const override { return nl; }
+
+  int kernel_timing(int enable, int which, double* ms_total, int64_t* n) override {
+    if (which != 0) return fail(PIC_EINVAL, "3D timing covers the push kernel (which = 0) only");
+    if (enable >= 0) {
+      timing_on = enable != 0;
+      if (enable) { t_ms = 0; t_n = 0; }
+    }
+    if (ms_total) *ms_total = t_ms;
+    if (n) *n = t_n;
+    return PIC_OK;
+  }
+
+  int status() const override { return st; }
+  const std::string& error() const override { return err; }
+};
+
+}  // namespace
+
+Sim3Api* make_sim3(const pic_config* cfg, pic_alloc_fn alloc, pic_free_fn free_fn, void* user, cudaStream_t s,
+                   int* status, std::string* err) {
+  if (cfg->ny < 8 || !(cfg->dy > 0)) {
+    *status = PIC_EINVAL;
+    if (err) *err = "3D needs ny >= 8 and dy > 0";
+    return nullptr;
+  }
+  if (cfg->moving_window) {
+    *status = PIC_EINVAL;
+    if (err) *err = "3D runs have no moving window";
+    return nullptr;
+  }
+  Sim3Api* r = nullptr;
+  int rc;
+  if (cfg->precision == PIC_FP64) {
+    auto* p = new Sim3<double>();
+    p->s = s; p->alloc = alloc; p->freef = free_fn; p->user = user;
+    rc = p->init(cfg);
+    r = p;
+  } else {
+    auto* p = new Sim3<float>();
+    p->s = s; p->alloc = alloc; p->freef = free_fn; p->user = user;
+    rc = p->init(cfg);
+    r = p;
+  }
+  if (rc != PIC_OK) {
+    if (err) *err = r->error();
+    delete r;
+    *status = rc;
+    return nullptr;
+  }
+  *status = PIC_OK;
+  return r;
+}
+
+}  // namespace picgb

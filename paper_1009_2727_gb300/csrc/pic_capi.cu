@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "../../include/pic.h"
+#include "pic_3d.h"
 #include "pic_common.cuh"
 
 namespace picgb {
@@ -63,6 +64,7 @@ struct pic_ctx {
   int status = PIC_OK;
   int64_t launches = 0;
   std::unique_ptr<SimBase> sim;
+  std::unique_ptr<picgb::Sim3Api> s3;   // 3D contexts
 
   void* dalloc(size_t bytes) {
     if (bytes == 0) bytes = 16;
@@ -895,7 +897,26 @@ int pic_init(const pic_config* cfg, pic_alloc_fn alloc, pic_free_fn free_fn, voi
   if (!out) return PIC_EINVAL;
   *out = nullptr;
   if (!cfg || cfg->struct_size != sizeof(pic_config) || cfg->version != PIC_API_VERSION) return PIC_EINVAL;
-  if (cfg->dim != 2) return PIC_EINVAL;
+  if (cfg->dim != 2 && cfg->dim != 3) return PIC_EINVAL;
+  if (cfg->dim == 3) {
+    if (cfg->nx < 8 || cfg->nz < 8 || !(cfg->dx > 0) || !(cfg->dz_lab > 0)) return PIC_EINVAL;
+    if (cfg->shape_order != 1 && cfg->shape_order != 3) return PIC_EINVAL;
+    if (cfg->precision != PIC_FP64 && cfg->precision != PIC_MIXED) return PIC_EINVAL;
+    if (std::fabs(cfg->ck_alpha + 4 * cfg->ck_beta + 4 * cfg->ck_gamma - 1.0) > 1e-12) return PIC_EINVAL;
+    if (cfg->theta < 0 || cfg->theta > 1) return PIC_EINVAL;
+    if (cfg->filter_passes < 0 || cfg->filter_stride < 1 || cfg->pml_cells < 0) return PIC_EINVAL;
+    if (cfg->filter_passes + (cfg->filter_compensate ? 1 : 0) > 16) return PIC_EINVAL;
+    std::unique_ptr<pic_ctx> c(new pic_ctx());
+    c->cfg = *cfg;
+    c->stream = (cudaStream_t)cuda_stream;
+    c->alloc = alloc; c->freef = free_fn; c->user = alloc_user;
+    int st = PIC_OK;
+    std::string e;
+    c->s3.reset(picgb::make_sim3(cfg, alloc, free_fn, alloc_user, c->stream, &st, &e));
+    if (!c->s3) return st;
+    *out = c.release();
+    return PIC_OK;
+  }
   if (cfg->nx < 8 || cfg->nz < 8 || !(cfg->dx > 0) || !(cfg->dz_lab > 0)) return PIC_EINVAL;
   if (cfg->shape_order != 1 && cfg->shape_order != 3) return PIC_EINVAL;
   if (cfg->precision != PIC_FP64 && cfg->precision != PIC_MIXED) return PIC_EINVAL;
@@ -957,6 +978,7 @@ int pic_load_plasma(pic_ctx* c, const pic_plasma* p) {
   if (!c) return PIC_EINVAL;
   if (!p || p->struct_size != sizeof(pic_plasma) || p->version != PIC_API_VERSION) return c->fail(PIC_EINVAL, "bad pic_plasma");
   if (c->status != PIC_OK) return c->status;
+  if (c->s3) return c->s3->load_plasma(p);
   return DISPATCH(c, load_plasma(p));
 }
 
@@ -964,6 +986,7 @@ int pic_inject_laser(pic_ctx* c, const pic_laser* l) {
   if (!c) return PIC_EINVAL;
   if (!l || l->struct_size != sizeof(pic_laser) || l->version != PIC_API_VERSION) return c->fail(PIC_EINVAL, "bad pic_laser");
   if (c->status != PIC_OK) return c->status;
+  if (c->s3) return c->s3->set_laser(l);
   return DISPATCH(c, set_laser(l));
 }
 
@@ -971,11 +994,13 @@ int pic_step(pic_ctx* c, int nsteps) {
   if (!c) return PIC_EINVAL;
   if (nsteps < 0) return c->fail(PIC_EINVAL, "nsteps < 0");
   if (c->status != PIC_OK) return c->status;
+  if (c->s3) return c->s3->run(nsteps);
   return DISPATCH(c, run(nsteps));
 }
 
 int pic_sync(pic_ctx* c) {
   if (!c) return PIC_EINVAL;
+  if (c->s3) return c->s3->sync();
   int r = DISPATCH(c, sync());
   return c->status != PIC_OK ? c->status : r;
 }
@@ -985,10 +1010,12 @@ int pic_boosted_to_lab_diag(pic_ctx* c, const pic_btd_req* req, pic_btd_out* out
   if (c->status != PIC_OK) return c->status;
   if (req && !out) {
     if (req->struct_size != sizeof(pic_btd_req) || req->version != PIC_API_VERSION) return c->fail(PIC_EINVAL, "bad pic_btd_req");
+    if (c->s3) return c->s3->btd_set(req);
     return DISPATCH(c, btd_set(req));
   }
   if (!req && out) {
     if (out->struct_size != sizeof(pic_btd_out) || out->version != PIC_API_VERSION) return c->fail(PIC_EINVAL, "bad pic_btd_out");
+    if (c->s3) return c->s3->btd_get(out);
     return DISPATCH(c, btd_get(out));
   }
   return c->fail(PIC_EINVAL, "pass exactly one of req and out");
@@ -997,6 +1024,7 @@ int pic_boosted_to_lab_diag(pic_ctx* c, const pic_btd_req* req, pic_btd_out* out
 int pic_free(pic_ctx* c) {
   if (!c) return PIC_OK;
   cudaStreamSynchronize(c->stream);
+  c->s3.reset();
   c->sim.reset();
   c->release_all();
   delete c;
@@ -1006,12 +1034,14 @@ int pic_free(pic_ctx* c) {
 int pic_get_field(pic_ctx* c, int comp, double* dst, int on_device) {
   if (!c || !dst) return PIC_EINVAL;
   if (c->status != PIC_OK) return c->status;
+  if (c->s3) return c->s3->get_field(comp, dst, on_device);
   return DISPATCH(c, get_field(comp, dst, on_device));
 }
 
 int pic_get_rho_noalloc(pic_ctx* c, double* dst_device) {
   if (!c || !dst_device) return PIC_EINVAL;
   if (c->status != PIC_OK) return c->status;
+  if (c->s3) return c->fail(PIC_EINVAL, "pic_get_rho_noalloc: 2D contexts only");
   if (c->cfg.nz > PIC_NOALLOC_MAX_NZ) return c->fail(PIC_EINVAL, "pic_get_rho_noalloc: nz exceeds PIC_NOALLOC_MAX_NZ");
   return DISPATCH(c, get_rho_noalloc(dst_device));
 }
@@ -1019,6 +1049,7 @@ int pic_get_rho_noalloc(pic_ctx* c, double* dst_device) {
 int pic_set_field(pic_ctx* c, int comp, const double* src) {
   if (!c || !src) return PIC_EINVAL;
   if (c->status != PIC_OK) return c->status;
+  if (c->s3) return c->s3->set_field(comp, src);
   return DISPATCH(c, set_field(comp, src));
 }
 
@@ -1026,25 +1057,41 @@ int pic_get_particles(pic_ctx* c, int species, double* x, double* z, double* ux,
                       uint32_t* id, int32_t* flags, int64_t* count) {
   if (!c || !count) return PIC_EINVAL;
   if (c->status != PIC_OK) return c->status;
+  if (c->s3) return c->s3->get_particles(species, x, nullptr, z, ux, uy, uz, w, id, flags, count);
   return DISPATCH(c, get_particles(species, x, z, ux, uy, uz, w, id, flags, count));
+}
+
+int pic_get_particles_y(pic_ctx* c, int species, double* y, int64_t* count) {
+  if (!c || !count) return PIC_EINVAL;
+  if (c->status != PIC_OK) return c->status;
+  if (!c->s3) return c->fail(PIC_EINVAL, "pic_get_particles_y: 3D contexts only");
+  if (!y) return c->s3->get_particles(species, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                      nullptr, count);
+  return c->s3->get_particles(species, nullptr, y, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, count);
 }
 
 int pic_get_stats(pic_ctx* c, pic_stats* out) {
   if (!c || !out) return PIC_EINVAL;
   if (out->struct_size != sizeof(pic_stats) || out->version != PIC_API_VERSION) return c->fail(PIC_EINVAL, "bad pic_stats");
   if (c->status != PIC_OK) return c->status;
+  if (c->s3) return c->s3->stats(out);
   return DISPATCH(c, stats(out));
 }
 
 const char* pic_last_error(pic_ctx* c) {
   if (!c) return "null context";
+  if (c->s3) return c->s3->error().c_str();
   return c->err.empty() ? "" : c->err.c_str();
 }
 
-int64_t pic_kernel_launches(pic_ctx* c) { return c ? c->launches : 0; }
+int64_t pic_kernel_launches(pic_ctx* c) {
+  if (!c) return 0;
+  return c->s3 ? c->s3->launches() : c->launches;
+}
 
 int pic_kernel_timing(pic_ctx* c, int enable, int which, double* ms_total, int64_t* launches) {
   if (!c) return PIC_EINVAL;
+  if (c->s3) return c->s3->kernel_timing(enable, which, ms_total, launches);
   return DISPATCH(c, kernel_timing(enable, which, ms_total, launches));
 }
 

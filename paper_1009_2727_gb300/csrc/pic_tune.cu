@@ -68,7 +68,7 @@ extern "C" int pic_autotune(const pic_config* cfg, const pic_plasma* plasma, con
                             pic_alloc_fn alloc, pic_free_fn free_fn, void* alloc_user, void* cuda_stream,
                             pic_tune_result* out) {
   if (!cfg || !plasma || !out || out->struct_size != sizeof(pic_tune_result)) return PIC_EINVAL;
-  if (steps < 1) return PIC_EINVAL;
+  if (steps < 1 || cfg->dim != 2) return PIC_EINVAL;
   const Key key = key_of(cfg, plasma);
   {
     std::lock_guard<std::mutex> lk(g_mu);

@@ -28,8 +28,10 @@ def make_config(w: dict, precision: int, tile=None, sort_every: int = 0) -> capi
     c = capi.PicConfig()
     c.struct_size = ctypes.sizeof(capi.PicConfig)
     c.version = capi.API_VERSION
-    c.dim = 2
+    c.dim = int(w.get("dim", 2))
     c.nx, c.nz = int(w["nx"]), int(w["nz"])
+    if c.dim == 3:
+        c.ny, c.dy = int(w["ny"]), float(w["dy"])
     c.dz_lab, c.dx = float(w["dz_lab"]), float(w["dx"])
     c.gamma_boost = float(w.get("gamma_boost", 1.0))
     c.courant = float(w.get("courant", 0.9))
@@ -68,6 +70,7 @@ def make_plasma(p: dict | None, beam: dict | None, keep: list) -> capi.PicPlasma
         pl.ramp_lab = float(p.get("ramp_lab", 0.0))
         pl.length_lab = float(p.get("length_lab", 0.0))
         pl.ppc_x, pl.ppc_z = int(p["ppc_x"]), int(p["ppc_z"])
+        pl.ppc_y = int(p.get("ppc_y", 0))
         pl.ions = int(p.get("ions", 1))
     else:
         pl.ppc_x = pl.ppc_z = 1
@@ -76,12 +79,16 @@ def make_plasma(p: dict | None, beam: dict | None, keep: list) -> capi.PicPlasma
         keep.append(arrs)
         pl.beam_n = arrs[0].size
         pl.beam_x, pl.beam_z, pl.beam_ux, pl.beam_uy, pl.beam_uz = (_p(a) for a in arrs)
+        if "y" in beam:
+            ya = np.ascontiguousarray(beam["y"], dtype=np.float64)
+            keep.append(ya)
+            pl.beam_y = _p(ya)
         pl.beam_t_lab = float(beam.get("t_lab", 0.0))
         pl.beam_z_plane_lab = float(beam["z_plane_lab"])
     return pl
 
 
-def make_laser(l: dict, nx: int, dx: float) -> capi.PicLaser:
+def make_laser(l: dict, nx: int, dx: float, ny: int = 0, dy: float = 0.0) -> capi.PicLaser:
     la = capi.PicLaser()
     la.struct_size = ctypes.sizeof(capi.PicLaser)
     la.version = capi.API_VERSION
@@ -89,6 +96,7 @@ def make_laser(l: dict, nx: int, dx: float) -> capi.PicLaser:
     la.tau_fwhm, la.t_peak = float(l["tau_fwhm"]), float(l.get("t_peak", 0.0))
     la.x_center = float(l.get("x_center", 0.5 * nx * dx))
     la.phase, la.z_antenna, la.beta_s = float(l.get("phase", 0.0)), float(l["z_antenna"]), float(l.get("beta_s", 0.0))
+    la.y_center = float(l.get("y_center", 0.5 * ny * dy))
     return la
 
 
@@ -147,6 +155,9 @@ class Simulation:
         prec = precision or w.get("precision", "fp64")
         self.precision = capi.PIC_FP64 if prec == "fp64" else capi.PIC_MIXED
         self.nx, self.nz = int(w["nx"]), int(w["nz"])
+        self.dim = int(w.get("dim", 2))
+        self.ny = int(w["ny"]) if self.dim == 3 else 0
+        self.shape = (self.nx + 1, self.ny + 1, self.nz + 1) if self.dim == 3 else (self.nx + 1, self.nz + 1)
         if tune:
             t = autotune(w, precision=prec, stream=self.stream)
             tile, sort_every = t["tile"], t["sort_every"]
@@ -181,7 +192,7 @@ class Simulation:
         self._check(self.L.pic_load_plasma(self.h, ctypes.byref(pl)), "pic_load_plasma")
 
     def inject_laser(self, l: dict):
-        la = make_laser(l, self.nx, float(self.w["dx"]))
+        la = make_laser(l, self.nx, float(self.w["dx"]), self.ny, float(self.w.get("dy", 0.0)))
         self._check(self.L.pic_inject_laser(self.h, ctypes.byref(la)), "pic_inject_laser")
 
     def step(self, n: int = 1):
@@ -191,12 +202,12 @@ class Simulation:
         self._check(self.L.pic_sync(self.h), "pic_sync")
 
     def field(self, comp: int) -> np.ndarray:
-        out = np.zeros((self.nx + 1) * (self.nz + 1))
+        out = np.zeros(int(np.prod(self.shape)))
         self._check(self.L.pic_get_field(self.h, comp, _p(out), 0), "pic_get_field")
-        return out.reshape(self.nx + 1, self.nz + 1)
+        return out.reshape(self.shape)
 
     def field_device(self, comp: int):
-        t = self.torch.empty((self.nx + 1, self.nz + 1), dtype=self.torch.float64, device=self.device)
+        t = self.torch.empty(self.shape, dtype=self.torch.float64, device=self.device)
         ptr = ctypes.cast(ctypes.c_void_p(t.data_ptr()), _D)
         self._check(self.L.pic_get_field(self.h, comp, ptr, 1), "pic_get_field")
         return t
@@ -220,6 +231,11 @@ class Simulation:
                     "pic_get_particles")
         m = int(n.value)
         out = {k: v[:m] for k, v in a.items()}
+        if getattr(self, "dim", 2) == 3:
+            y = np.zeros(cnt)
+            n = ctypes.c_int64(cnt)
+            self._check(self.L.pic_get_particles_y(self.h, species, _p(y), ctypes.byref(n)), "pic_get_particles_y")
+            out["y"] = y[:m]
         out["id"] = ids[:m]
         out["alive"] = (fl[:m] & 1) != 0
         out["active"] = (fl[:m] & 2) != 0
@@ -292,6 +308,9 @@ class _Member(Simulation):
         self.stream = None
         self.precision = precision
         self.nx, self.nz = int(w["nx"]), int(w["nz"])
+        self.dim = int(w.get("dim", 2))
+        self.ny = int(w["ny"]) if self.dim == 3 else 0
+        self.shape = (self.nx + 1, self.ny + 1, self.nz + 1) if self.dim == 3 else (self.nx + 1, self.nz + 1)
         self._keep = []
 
     def step(self, n: int = 1):
@@ -321,7 +340,8 @@ class Ensemble:
         las = (capi.PicLaser * n)()
         for i, w in enumerate(ws):
             if w.get("laser"):
-                las[i] = make_laser(w["laser"], int(w["nx"]), float(w["dx"]))
+                las[i] = make_laser(w["laser"], int(w["nx"]), float(w["dx"]), int(w.get("ny", 0)),
+                                    float(w.get("dy", 0.0)))
         self._alloc_cb, self._free_cb = torch_allocator(self.device.index)
         h = ctypes.c_void_p()
         r = self.L.pic_ensemble_create(n, cfgs, pls, las, self._alloc_cb, self._free_cb, None,
