@@ -36,6 +36,8 @@ if ROOT not in sys.path:
 # algorithmic bytes per electron particle-step of the push kernel (mixed): read x,z (2x8),
 # u (3x4), w (4); write x,z (2x8), u (3x4)
 BYTES_PER_PARTICLE = {"mixed": 60, "fp64": 88}
+# 3D: read and write x, y, z (3 x 8), u (3 x 4 or 3 x 8), read w
+BYTES_PER_PARTICLE_3D = {"mixed": 76, "fp64": 104}
 # algorithmic bytes per cell-step of the field kernels (mixed, with Friedman): see the design notes
 BYTES_PER_CELL = {"mixed": 168, "fp64": 336}
 # measured DRAM bytes (read + write) per particle of one push launch, mixed precision, cubic shapes:
@@ -162,6 +164,28 @@ def cpu_oracle_sample(w: dict, seconds: float = 15.0, max_steps: int = 40) -> di
     return {"value": n * steps / dt, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
             "sample": f"{ws['name']}: {n} electrons (+ as many ions), {steps} steps, {dt:.1f} s "
                       f"(setup {setup:.1f} s), single thread"}
+
+
+def cpu_oracle_sample3(w: dict, seconds: float = 15.0, max_steps: int = 40) -> dict:
+    """The 3D oracle, as it stands, on a bounded sample of the 3D workload: the same numerics on a box
+    of 128 (z) x 64 (y) x 64 (x) cells, a few steps."""
+    import oracle
+    from paper_1009_2727_gb300 import workloads as W
+    ws = W.shrink3(w, 64, 64, 128)
+    ws["precision"] = "fp64"
+    t0 = time.perf_counter()
+    s = oracle.Sim3(ws)
+    setup = time.perf_counter() - t0
+    n = len(s.particles(0)["x"])
+    steps = 0
+    t0 = time.perf_counter()
+    while steps < max_steps and (time.perf_counter() - t0) < seconds:
+        s.step(1)
+        steps += 1
+    dt = time.perf_counter() - t0
+    return {"value": n * steps / dt, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"{ws['name']} on 128 x 64 x 64 cells: {n} electrons (+ as many ions), {steps} steps, "
+                      f"{dt:.1f} s (setup {setup:.1f} s), single thread"}
 
 
 def run_reference(args, w):
@@ -338,12 +362,15 @@ def main():
                     help="time N uneven runs advanced together (pic_ensemble_*) instead of the stage")
     ap.add_argument("--surrogate", type=int, default=0,
                     help="label N stage runs, train the stage surrogate on them and time its serving")
+    ap.add_argument("--dim", type=int, default=2, choices=[2, 3],
+                    help="3: the 3D stage (1024 x 128 x 128 cells, gamma 30) instead of the 2D one")
     args = ap.parse_args()
 
     from paper_1009_2727_gb300 import workloads as W
-    w = W.stage_2d()
+    three = args.dim == 3
+    w = W.stage_3d() if three else W.stage_2d()
     if args.nz:
-        w = W.shrink(w, w["nx"], args.nz)
+        w = W.shrink3(w, w["nx"], w["ny"], args.nz) if three else W.shrink(w, w["nx"], args.nz)
     w["order"] = args.order
     w["precision"] = args.precision
     if args.impl == "reference":
@@ -365,7 +392,7 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = cpu_oracle_sample(w)
+        cpu = cpu_oracle_sample3(w) if three else cpu_oracle_sample(w)
 
     sim = Simulation(w, precision=args.precision, sort_every=args.sort_every)
     stream = torch.cuda.current_stream()
@@ -398,15 +425,17 @@ def main():
     # roofline of the dominant kernel
     peaks = measured_peaks()
     peak = peaks.get("hbm_gbs", 6800.0)
-    bpp = BYTES_PER_PARTICLE[args.precision]
+    bpp = (BYTES_PER_PARTICLE_3D if three else BYTES_PER_PARTICLE)[args.precision]
     push_avg_ms = push_ms / max(push_n, 1)
     achieved = n_avg * bpp / (push_avg_ms * 1e-3) / 1e9
-    tpp = TRAFFIC_BYTES_PER_PARTICLE.get((args.precision, args.order))
-    roof = {"kernel": "k_push (gather + Boris + Esirkepov)", "bound": "hbm", "achieved": achieved, "peak": peak,
+    tpp = None if three else TRAFFIC_BYTES_PER_PARTICLE.get((args.precision, args.order))
+    roof = {"kernel": "k3_push (3D gather + Boris + Esirkepov)" if three else "k_push (gather + Boris + Esirkepov)",
+            "bound": "hbm", "achieved": achieved, "peak": peak,
             "unit": "GB/s", "frac": achieved / peak, "traffic": tpp * n_avg if tpp else None,
             "traffic_source": "ncu dram bytes of k_push, 2048 x 256 box, scaled by particles" if tpp else None,
-            "note": "at cubic order the push is bound by instruction issue "
-                    "(ncu: 62% issue slots, 52% L1/shared, 15% DRAM), not by HBM",
+            "note": ("3D push: global-memory gather and global atomics, no tile staging yet" if three else
+                     "at cubic order the push is bound by instruction issue "
+                     "(ncu: 62% issue slots, 52% L1/shared, 15% DRAM), not by HBM"),
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback",
             "algorithmic_bytes_per_particle": bpp, "push_ms_per_step": push_avg_ms,
             "share_of_step": push_avg_ms / (ms / args.steps)}
@@ -440,11 +469,14 @@ def main():
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64pos" if args.precision == "mixed" else "f64", "data": "synthetic",
-            "config": {"workload": w["name"], "grid": [w["nz"], w["nx"]], "ppc": 16, "gamma_boost": w["gamma_boost"],
-                       "solver": "CK", "theta": w["theta"], "filter": "4 passes + compensation",
+            "config": {"workload": w["name"],
+                       "grid": [w["nz"], w["ny"], w["nx"]] if three else [w["nz"], w["nx"]],
+                       "ppc": 2 if three else 16, "gamma_boost": w["gamma_boost"],
+                       "solver": "CK2" if three else "CK", "theta": w["theta"], "filter": "4 passes + compensation",
                        "shape_order": args.order, "precision": args.precision, "electrons": int(n_avg),
-                       "cell_steps_per_s": w["nx"] * w["nz"] * args.steps * ws / (ms_max * 1e-3),
-                       "l2": "inputs larger than L2 (particle arrays ~0.9 GB)",
+                       "cell_steps_per_s": w["nx"] * w.get("ny", 1) * w["nz"] * args.steps * ws / (ms_max * 1e-3),
+                       "l2": "inputs larger than L2 (particle arrays ~0.5 GB, fields ~2.6 GB)" if three else
+                             "inputs larger than L2 (particle arrays ~0.9 GB)",
                        "parallelism": f"{ws} independent replicas" if ws > 1 else "1 GPU"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
         }

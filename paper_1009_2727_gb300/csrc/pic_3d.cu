@@ -79,10 +79,14 @@ __device__ __forceinline__ bool node_of(const G3& g, long p, int& i, int& j, int
   return true;
 }
 
+// PML tables per axis at integer and half positions, in the path's own real type: the FP64 path keeps them
+// in FP64; the mixed path rounds them to FP32 once (on this GPU an FP64 operation per PML node and
+// component would make the field sweeps FP64-pipe bound)
+template <class T>
 struct Pml3 {
-  const double* sg[3][2];   // sigma [axis][half]
-  const double* xi[3][2];
-  const double* cf[3][2];   // (1 - xi)/sigma, dt where sigma = 0
+  const T* sg[3][2];   // sigma [axis][half]
+  const T* xi[3][2];
+  const T* cf[3][2];   // (1 - xi)/sigma, dt where sigma = 0
 };
 
 template <class T>
@@ -100,44 +104,64 @@ __global__ void k3_eeff(long n, const T* E, const T* Ep, const T* Eb, T* Ee, T c
 }
 
 // Delta*_a F at node (i,j,k) (result half a cell above along a): alpha D(0,0) + beta (four axial
-// neighbours) + gamma (four diagonal neighbours), D the difference along a on the transverse offsets
-template <class T>
-__device__ T dstar3(const G3& g, const T* F, int a, int i, int j, int k, T ca, T cb, T cg, T inv_d) {
+// neighbours) + gamma (four diagonal neighbours), D the difference along a on the transverse offsets.
+// IN: the node and its stencil are inside the array (no bounds checks).
+template <class T, bool IN>
+__device__ __forceinline__ T dstar3(const G3& g, const T* F, int a, int i, int j, int k, T ca, T cb, T cg, T inv_d) {
   const int b = a == 0 ? 1 : 0, c = a == 2 ? 1 : 2;
+  const long sx = (long)(g.n[1] + 1) * g.ldz, sy = g.ldz;
+  const long st[3] = {sx, sy, 1};
+  const long p = nid(g, i, j, k);
   T D[3][3];
 #pragma unroll
   for (int o1 = -1; o1 <= 1; o1++)
 #pragma unroll
     for (int o2 = -1; o2 <= 1; o2++) {
-      const int pi = i + (b == 0 ? o1 : 0) + (c == 0 ? o2 : 0);
-      const int pj = j + (b == 1 ? o1 : 0) + (c == 1 ? o2 : 0);
-      const int pk = k + (b == 2 ? o1 : 0) + (c == 2 ? o2 : 0);
-      D[o1 + 1][o2 + 1] = rd3(g, F, pi + (a == 0), pj + (a == 1), pk + (a == 2)) - rd3(g, F, pi, pj, pk);
+      if (IN) {
+        const long q = p + o1 * st[b] + o2 * st[c];
+        D[o1 + 1][o2 + 1] = F[q + st[a]] - F[q];
+      } else {
+        const int pi = i + (b == 0 ? o1 : 0) + (c == 0 ? o2 : 0);
+        const int pj = j + (b == 1 ? o1 : 0) + (c == 1 ? o2 : 0);
+        const int pk = k + (b == 2 ? o1 : 0) + (c == 2 ? o2 : 0);
+        D[o1 + 1][o2 + 1] = rd3(g, F, pi + (a == 0), pj + (a == 1), pk + (a == 2)) - rd3(g, F, pi, pj, pk);
+      }
     }
   const T s1 = D[0][1] + D[2][1] + D[1][0] + D[1][2];
   const T s2 = D[0][0] + D[0][2] + D[2][0] + D[2][2];
   return (ca * D[1][1] + cb * s1 + cg * s2) * inv_d;
 }
 
+// z nodes per thread of the grid sweeps (a block width apart)
+constexpr int KPT = 4;
+
 template <class T>
-__global__ void k3_faraday(G3 g, Pml3 pm, const T* Ee, T* B, T* Bs, T* fB, T ca, T cb, T cg, T dtT) {
-  int i, j, k;
-  if (!node_of(g, (long)blockIdx.x * blockDim.x + threadIdx.x, i, j, k)) return;
+__device__ __forceinline__ void faraday_node(const G3& g, const Pml3<T>& pm, const T* Ee, T* B, T* Bs, T* fB, T ca, T cb,
+                                             T cg, T dtT, int i, int j, int k) {
   const long p = nid(g, i, j, k);
   const int idx[3] = {i, j, k};
+  const bool in = i >= 1 && i < g.n[0] && j >= 1 && j < g.n[1] && k >= 1 && k < g.n[2];
+#pragma unroll
   for (int q = 0; q < 3; q++) {
     const T old = B[q * g.cs + p];
     T nw = old;
-    if (in_valid(3 + q, g, i, j, k)) {
+    // every B component is valid on the interior nodes
+    if (in || in_valid(3 + q, g, i, j, k)) {
       const int u = (q + 1) % 3, v = (q + 2) % 3;
-      const T du = dstar3(g, Ee + v * g.cs, u, i, j, k, ca, cb, cg, T(1.0 / g.d[u]));
-      const T dv = dstar3(g, Ee + u * g.cs, v, i, j, k, ca, cb, cg, T(1.0 / g.d[v]));
-      const double su = pm.sg[u][1][idx[u]], sv = pm.sg[v][1][idx[v]];
-      if (su > 0.0 || sv > 0.0) {
+      T du, dv;
+      if (in) {
+        du = dstar3<T, true>(g, Ee + v * g.cs, u, i, j, k, ca, cb, cg, T(1.0 / g.d[u]));
+        dv = dstar3<T, true>(g, Ee + u * g.cs, v, i, j, k, ca, cb, cg, T(1.0 / g.d[v]));
+      } else {
+        du = dstar3<T, false>(g, Ee + v * g.cs, u, i, j, k, ca, cb, cg, T(1.0 / g.d[u]));
+        dv = dstar3<T, false>(g, Ee + u * g.cs, v, i, j, k, ca, cb, cg, T(1.0 / g.d[v]));
+      }
+      const T su = pm.sg[u][1][idx[u]], sv = pm.sg[v][1][idx[v]];
+      if (su > T(0) || sv > T(0)) {
         T* Pu = Bs + (2 * q) * g.cs;
         T* Pv = Bs + (2 * q + 1) * g.cs;
-        const T a = T(pm.xi[u][1][idx[u]] * (double)Pu[p] - pm.cf[u][1][idx[u]] * (double)du);
-        const T b = T(pm.xi[v][1][idx[v]] * (double)Pv[p] + pm.cf[v][1][idx[v]] * (double)dv);
+        const T a = pm.xi[u][1][idx[u]] * Pu[p] - pm.cf[u][1][idx[u]] * du;
+        const T b = pm.xi[v][1][idx[v]] * Pv[p] + pm.cf[v][1][idx[v]] * dv;
         Pu[p] = a;
         Pv[p] = b;
         nw = a + b;
@@ -147,6 +171,19 @@ __global__ void k3_faraday(G3 g, Pml3 pm, const T* Ee, T* B, T* Bs, T* fB, T ca,
       B[q * g.cs + p] = nw;
     }
     fB[q * g.cs + p] = T(0.5) * (old + nw);
+  }
+}
+
+// KPT z nodes per thread, a block width apart
+template <class T>
+__global__ void __launch_bounds__(128) k3_faraday(G3 g, Pml3<T> pm, const T* Ee, T* B, T* Bs, T* fB, T ca, T cb, T cg,
+                                                  T dtT) {
+  const int k0 = blockIdx.x * blockDim.x * KPT + threadIdx.x, j = blockIdx.y, i = blockIdx.z;
+#pragma unroll
+  for (int kk = 0; kk < KPT; kk++) {
+    const int k = k0 + kk * blockDim.x;
+    if (k > g.n[2]) break;
+    faraday_node<T>(g, pm, Ee, B, Bs, fB, ca, cb, cg, dtT, i, j, k);
   }
 }
 
@@ -162,26 +199,36 @@ __global__ void k3_friedman(long n, const T* E, T* Ep, T* Eb, T* fE, T a, T b) {
 }
 
 template <class T>
-__global__ void k3_ampere(G3 g, Pml3 pm, T* E, T* Es, const T* B, const T* J, T dtc2, T dte) {
-  int i, j, k;
-  if (!node_of(g, (long)blockIdx.x * blockDim.x + threadIdx.x, i, j, k)) return;
+__device__ __forceinline__ void ampere_node(const G3& g, const Pml3<T>& pm, T* E, T* Es, const T* B, const T* J, T dtc2,
+                                            T dte, int i, int j, int k) {
   const long p = nid(g, i, j, k);
   const int idx[3] = {i, j, k};
-  const double c2 = kC * kC;
+  const T c2 = T(kC * kC);
+  const bool in = i >= 1 && j >= 1 && k >= 1;
+  // E is valid off the PEC walls: 1..n-1 on integer axes, 0..n-1 on its own half axis
+  const bool allv = in && i < g.n[0] && j < g.n[1] && k < g.n[2];
+  const long st[3] = {(long)(g.n[1] + 1) * g.ldz, g.ldz, 1};
+#pragma unroll
   for (int q = 0; q < 3; q++) {
-    if (!in_valid(q, g, i, j, k)) continue;
+    if (!allv && !in_valid(q, g, i, j, k)) continue;
     const int u = (q + 1) % 3, v = (q + 2) % 3;
     // dE_q/dt = c^2 (Delta_u B_v - Delta_v B_u) - J_q/eps0, backward differences
     const T* Bv = B + v * g.cs;
     const T* Bu = B + u * g.cs;
-    const T du = (rd3(g, Bv, i, j, k) - rd3(g, Bv, i - (u == 0), j - (u == 1), k - (u == 2))) * T(1.0 / g.d[u]);
-    const T dv = (rd3(g, Bu, i, j, k) - rd3(g, Bu, i - (v == 0), j - (v == 1), k - (v == 2))) * T(1.0 / g.d[v]);
-    const double su = pm.sg[u][0][idx[u]], sv = pm.sg[v][0][idx[v]];
-    if (su > 0.0 || sv > 0.0) {
+    T du, dv;
+    if (in) {
+      du = (Bv[p] - Bv[p - st[u]]) * T(1.0 / g.d[u]);
+      dv = (Bu[p] - Bu[p - st[v]]) * T(1.0 / g.d[v]);
+    } else {
+      du = (rd3(g, Bv, i, j, k) - rd3(g, Bv, i - (u == 0), j - (u == 1), k - (u == 2))) * T(1.0 / g.d[u]);
+      dv = (rd3(g, Bu, i, j, k) - rd3(g, Bu, i - (v == 0), j - (v == 1), k - (v == 2))) * T(1.0 / g.d[v]);
+    }
+    const T su = pm.sg[u][0][idx[u]], sv = pm.sg[v][0][idx[v]];
+    if (su > T(0) || sv > T(0)) {
       T* Pu = Es + (2 * q) * g.cs;
       T* Pv = Es + (2 * q + 1) * g.cs;
-      const T a = T(pm.xi[u][0][idx[u]] * (double)Pu[p] + c2 * pm.cf[u][0][idx[u]] * (double)du);
-      const T b = T(pm.xi[v][0][idx[v]] * (double)Pv[p] - c2 * pm.cf[v][0][idx[v]] * (double)dv);
+      const T a = pm.xi[u][0][idx[u]] * Pu[p] + c2 * pm.cf[u][0][idx[u]] * du;
+      const T b = pm.xi[v][0][idx[v]] * Pv[p] - c2 * pm.cf[v][0][idx[v]] * dv;
       Pu[p] = a;
       Pv[p] = b;
       E[q * g.cs + p] = a + b;
@@ -191,22 +238,70 @@ __global__ void k3_ampere(G3 g, Pml3 pm, T* E, T* Es, const T* B, const T* J, T 
   }
 }
 
-// one axis of the composed filter: out = sum_m c_m F(node + (m - P) s e_axis), zero off the valid range
 template <class T>
-__global__ void k3_filter_axis(G3 g, const T* src, T* dst, int comp, int axis, Taps3<T> t) {
-  int i, j, k;
-  if (!node_of(g, (long)blockIdx.x * blockDim.x + threadIdx.x, i, j, k)) return;
-  const long p = nid(g, i, j, k);
-  if (!in_valid(comp, g, i, j, k)) {
-    dst[p] = T(0);
-    return;
+__global__ void __launch_bounds__(128) k3_ampere(G3 g, Pml3<T> pm, T* E, T* Es, const T* B, const T* J, T dtc2, T dte) {
+  const int k0 = blockIdx.x * blockDim.x * KPT + threadIdx.x, j = blockIdx.y, i = blockIdx.z;
+#pragma unroll
+  for (int kk = 0; kk < KPT; kk++) {
+    const int k = k0 + kk * blockDim.x;
+    if (k > g.n[2]) break;
+    ampere_node<T>(g, pm, E, Es, B, J, dtc2, dte, i, j, k);
   }
-  T acc = T(0);
-  for (int m = 0; m <= 2 * t.P; m++) {
-    const int o = (m - t.P) * t.s;
-    acc += t.c[m] * rd3(g, src, i + (axis == 0 ? o : 0), j + (axis == 1 ? o : 0), k + (axis == 2 ? o : 0));
+}
+
+// one axis of the composed filter: out = sum_m c_m F(node + (m - P) s e_axis), zero off the valid range.
+// PT > 0: the pass count P is the template constant (taps unrolled); PT = 0: any P. Each thread filters
+// KPT z nodes a block width apart (coalesced).
+template <class T, int PT>
+__global__ void __launch_bounds__(128) k3_filter_axis(G3 g, const T* __restrict__ src, T* __restrict__ dst, int comp,
+                                                      int axis, Taps3<T> t) {
+  const int k0 = blockIdx.x * blockDim.x * KPT + threadIdx.x, j = blockIdx.y, i = blockIdx.z;
+  if (k0 > g.n[2]) return;
+  const int P = PT > 0 ? PT : t.P;
+  const long st = axis == 0 ? (long)(g.n[1] + 1) * g.ldz : axis == 1 ? (long)g.ldz : 1L;
+  const int R = P * t.s;
+  const long ss = st * t.s;
+  const int n = g.n[axis];
+#pragma unroll
+  for (int kk = 0; kk < KPT; kk++) {
+    const int k = k0 + kk * blockDim.x;
+    if (k > g.n[2]) break;
+    const long p = nid(g, i, j, k);
+    if (!in_valid(comp, g, i, j, k)) {
+      dst[p] = T(0);
+      continue;
+    }
+    const int id = axis == 0 ? i : axis == 1 ? j : k;
+    const T* q0 = src + p - R * st;
+    T acc = T(0);
+    if (id - R >= 0 && id + R <= n) {
+      if (PT > 0) {
+#pragma unroll
+        for (int m = 0; m <= 2 * PT; m++) acc += t.c[m] * q0[m * ss];
+      } else {
+        for (int m = 0; m <= 2 * P; m++) acc += t.c[m] * q0[m * ss];
+      }
+    } else {
+      for (int m = 0; m <= 2 * P; m++) {
+        const int o = id + (m - P) * t.s;
+        if (o >= 0 && o <= n) acc += t.c[m] * q0[m * ss];
+      }
+    }
+    dst[p] = acc;
   }
-  dst[p] = acc;
+}
+
+template <class T>
+void launch_filter_axis(const G3& g, dim3 grid, const T* src, T* dst, int comp, int axis, const Taps3<T>& t,
+                        cudaStream_t s) {
+  switch (t.P) {
+    case 1: k3_filter_axis<T, 1><<<grid, 128, 0, s>>>(g, src, dst, comp, axis, t); break;
+    case 2: k3_filter_axis<T, 2><<<grid, 128, 0, s>>>(g, src, dst, comp, axis, t); break;
+    case 3: k3_filter_axis<T, 3><<<grid, 128, 0, s>>>(g, src, dst, comp, axis, t); break;
+    case 4: k3_filter_axis<T, 4><<<grid, 128, 0, s>>>(g, src, dst, comp, axis, t); break;
+    case 5: k3_filter_axis<T, 5><<<grid, 128, 0, s>>>(g, src, dst, comp, axis, t); break;
+    default: k3_filter_axis<T, 0><<<grid, 128, 0, s>>>(g, src, dst, comp, axis, t); break;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -282,55 +377,6 @@ __device__ __forceinline__ void boris3(T* u, const T* E, const T* B, T k) {
   u[2] = pl2 + k * E[2];
 }
 
-// Esirkepov deposition in 3D (Esirkepov 2001) of charge*weight qw from p0 to p1 (moves below one cell):
-// W_q = DS_q (S0_u S0_v + DS_u S0_v/2 + S0_u DS_v/2 + DS_u DS_v/3), J_q prefix sums of -qw/(d_u d_v dt) W_q
-template <class T, int ORD>
-__device__ void esirkepov3d(const G3& g, T* const* J, const double* p0, const double* p1, double qw) {
-  constexpr int NS = ORD == 3 ? 4 : 2;
-  constexpr int SH = ORD == 3 ? 1 : 0;
-  constexpr int W = NS + 1;
-  T S0[3][W], DS[3][W];
-  int base[3];
-#pragma unroll
-  for (int a = 0; a < 3; a++) {
-    const double A0 = p0[a] / g.d[a], A1 = p1[a] / g.d[a];
-    const double f0 = floor(A0), f1 = floor(A1);
-    base[a] = (int)(f0 < f1 ? f0 : f1) - SH;
-    T w0[NS], w1[NS];
-    shape_w<T, ORD>(T(A0 - f0), w0);
-    shape_w<T, ORD>(T(A1 - f1), w1);
-    const int o0 = (int)f0 - SH - base[a], o1 = (int)f1 - SH - base[a];
-#pragma unroll
-    for (int m = 0; m < W; m++) {
-      const T s0 = (m - o0 >= 0 && m - o0 < NS) ? w0[m - o0] : T(0);
-      const T s1 = (m - o1 >= 0 && m - o1 < NS) ? w1[m - o1] : T(0);
-      S0[a][m] = s0;
-      DS[a][m] = s1 - s0;
-    }
-  }
-  const double vol_dt = g.d[0] * g.d[1] * g.d[2] * g.dt;
-#pragma unroll
-  for (int q = 0; q < 3; q++) {
-    const int u = (q + 1) % 3, v = (q + 2) % 3;
-    const T cq = T(-qw * g.d[q] / vol_dt);
-    for (int mu = 0; mu < W; mu++)
-      for (int mv = 0; mv < W; mv++) {
-        const T tr = S0[u][mu] * S0[v][mv] + T(0.5) * DS[u][mu] * S0[v][mv] + T(0.5) * S0[u][mu] * DS[v][mv] +
-                     DS[u][mu] * DS[v][mv] / T(3);
-        if (tr == T(0)) continue;
-        T acc = T(0);
-        for (int mq = 0; mq < W; mq++) {
-          acc += cq * DS[q][mq] * tr;
-          if (acc == T(0)) continue;
-          int id3[3];
-          id3[q] = base[q] + mq; id3[u] = base[u] + mu; id3[v] = base[v] + mv;
-          if (id3[0] < 0 || id3[0] > g.n[0] || id3[1] < 0 || id3[1] > g.n[1] || id3[2] < 0 || id3[2] > g.n[2]) continue;
-          atomicAdd(J[q] + nid(g, id3[0], id3[1], id3[2]), acc);
-        }
-      }
-  }
-}
-
 template <class T>
 struct Fld3 {
   const T* fE[3];
@@ -338,30 +384,280 @@ struct Fld3 {
   T* J[3];
 };
 
-template <class T, int ORD>
-__global__ void __launch_bounds__(128) k3_push(G3 g, Fld3<T> f, Parts3<T> p, const Ctrl3* ctrl, T kq, double qe) {
+// ---------------------------------------------------------------------------
+// tiled push: particles sorted by tiles of TX x TY x TZ cells; one CTA per tile stages the six
+// gather fields of the tile and its halo in shared memory, accumulates the current of its particles
+// in a shared window with shared-memory atomics, and adds the window to J once
+constexpr int TX = 4, TY = 4, TZ = 16;
+// window nodes cell0-3 .. cell0+T+3: the gather and deposit stencils of a particle within half a cell of
+// its tile (tile-local coordinate in [-1/2, T+1/2), which absorbs the rounding of the sort's cell index
+// against the push's FP32 tile-local coordinate) moving less than one cell
+constexpr int WM = 3;
+constexpr int WX = TX + 2 * WM + 1, WY = TY + 2 * WM + 1, WZ = TZ + 2 * WM + 1;
+constexpr int WN = WX * WY * WZ;
+
+struct Tiles3 {
+  int nt[3];
+  int* cnt;      // particles per tile (filled by the key pass)
+  int* start;    // exclusive scan of cnt
+  int* key;      // per particle: tile, -1 when dropped
+  int* rank;     // per particle: rank inside its tile
+};
+
+__device__ __forceinline__ int tile_of(const G3& g, const Tiles3& t, const double* pos) {
+  const int ci = (int)floor(pos[0] / g.d[0]), cj = (int)floor(pos[1] / g.d[1]), ck = (int)floor(pos[2] / g.d[2]);
+  if (ci < 0 || cj < 0 || ck < 0 || ci >= g.n[0] || cj >= g.n[1] || ck >= g.n[2]) return -1;
+  return ((ci / TX) * t.nt[1] + cj / TY) * t.nt[2] + ck / TZ;
+}
+
+// tile key and rank of every live particle (warp-aggregated counters); every slot below n (the host's
+// bound on the count) gets a key, -1 beyond the device count, so that the scatter reads no stale key
+template <class T>
+__global__ void k3_tile_key(G3 g, Parts3<T> p, const Ctrl3* ctrl, Tiles3 t, int n) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= ctrl->count) return;
-  if (!(p.fl[j] & 1)) return;
-  const double pos[3] = {p.x[j], p.y[j], p.z[j]};
-  T E[3], B[3];
-  gather3<T, ORD>(g, f.fE, f.fB, pos, E, B);
-  T u[3] = {p.ux[j], p.uy[j], p.uz[j]};
-  boris3<T>(u, E, B, kq);
-  const T gm = sqrt(T(1) + (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]) * T(1.0 / (kC * kC)));
-  const double pn[3] = {pos[0] + g.dt * (double)(u[0] / gm), pos[1] + g.dt * (double)(u[1] / gm),
-                        pos[2] + g.dt * (double)(u[2] / gm)};
-  esirkepov3d<T, ORD>(g, f.J, pos, pn, qe * (double)p.w[j]);
-  p.x[j] = pn[0]; p.y[j] = pn[1]; p.z[j] = pn[2];
-  p.ux[j] = u[0]; p.uy[j] = u[1]; p.uz[j] = u[2];
-  bool out = false;
+  const bool in = j < ctrl->count;
+  int key = -1;
+  if (in && (p.fl[j] & 1)) {
+    const double pos[3] = {p.x[j], p.y[j], p.z[j]};
+    key = tile_of(g, t, pos);
+  }
+  const unsigned act = __ballot_sync(0xffffffffu, key >= 0);
+  if (key >= 0) {
+    const unsigned grp = __match_any_sync(act, key);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(grp) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(t.cnt + key, __popc(grp));
+    base = __shfl_sync(grp, base, leader);
+    t.rank[j] = base + __popc(grp & ((1u << lane) - 1u));
+  }
+  if (j < n) t.key[j] = key;
+}
+
+// exclusive scan of the tile counts by one block; the total becomes the particle count
+__global__ void __launch_bounds__(1024) k3_scan_tiles(const int* cnt, int* start, int n, Ctrl3* ctrl) {
+  __shared__ int part[1024];
+  const int per = (n + 1023) / 1024;
+  const int b0 = threadIdx.x * per, b1 = min(n, b0 + per);
+  int s = 0;
+  for (int b = b0; b < b1; b++) s += cnt[b];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    const int v = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int run = part[threadIdx.x] - s;
+  for (int b = b0; b < b1; b++) {
+    start[b] = run;
+    run += cnt[b];
+  }
+  if (threadIdx.x == 1023) {
+    start[n] = part[1023];
+    ctrl->count = part[1023];
+  }
+}
+
+template <class T>
+__global__ void k3_tile_scatter(Parts3<T> src, Parts3<T> dst, Tiles3 t, int n_old) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n_old) return;
+  const int key = t.key[j];
+  if (key < 0) return;
+  const int q = t.start[key] + t.rank[j];
+  dst.x[q] = src.x[j]; dst.y[q] = src.y[j]; dst.z[q] = src.z[j];
+  dst.ux[q] = src.ux[j]; dst.uy[q] = src.uy[j]; dst.uz[q] = src.uz[j];
+  dst.w[q] = src.w[j]; dst.id[q] = src.id[j]; dst.fl[q] = 1;
+}
+
+template <class T, int ORD>
+__global__ void __launch_bounds__(256) k3_push_tiles(G3 g, Fld3<T> f, Parts3<T> p, Tiles3 t, Ctrl3* ctrl, T kq,
+                                                     double qe) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* sF = reinterpret_cast<T*>(smraw);        // 6 x WN gather fields
+  T* sJ = sF + 6 * WN;                        // 3 x WN current
+  const int tile = blockIdx.x;
+  const int p0 = t.start[tile], p1 = t.start[tile + 1];
+  if (p1 <= p0) return;
+  const int tz = tile % t.nt[2], r = tile / t.nt[2];
+  const int ty = r % t.nt[1], tx = r / t.nt[1];
+  const int c0[3] = {tx * TX, ty * TY, tz * TZ};          // the tile's first cell; the window starts WM before
+  for (int e = threadIdx.x; e < 6 * WN; e += blockDim.x) {
+    const int c = e / WN, n = e - c * WN;
+    const int a = n / (WY * WZ), rr = n - a * (WY * WZ), b = rr / WZ, k = rr - b * WZ;
+    const T* F = c < 3 ? f.fE[c] : f.fB[c - 3];
+    sF[e] = rd3(g, F, c0[0] - WM + a, c0[1] - WM + b, c0[2] - WM + k);
+  }
+  for (int e = threadIdx.x; e < 3 * WN; e += blockDim.x) sJ[e] = T(0);
+  __syncthreads();
+  constexpr int NS = ORD == 3 ? 4 : 2;
+  constexpr int SH = ORD == 3 ? 1 : 0;
+  constexpr int W = NS + 1;
+  // tile-local coordinates in cells: X = (pos - c0 d) / d; everything below runs in T (FP32 on the mixed
+  // path: one FP64 subtraction and multiplication per axis to enter, one FP64 addition to leave)
+  double org[3], inv[3];
+  T dT[3], invT[3], lo[3], hi[3];
 #pragma unroll
   for (int a = 0; a < 3; a++) {
-    const double lo = g.lo[a] * g.d[a];
-    const double hi = g.hi[a] * g.d[a] + (a == 2 ? g.d[2] : 0.0);
-    if (pn[a] < lo || pn[a] >= hi) out = true;
+    org[a] = c0[a] * g.d[a];
+    inv[a] = 1.0 / g.d[a];
+    dT[a] = T(g.d[a]);
+    invT[a] = T(inv[a]);
+    lo[a] = T(g.lo[a] - c0[a]);
+    hi[a] = T(g.hi[a] - c0[a] + (a == 2 ? 1 : 0));
   }
-  if (out) p.fl[j] = 0;
+  const double vol_dt = g.d[0] * g.d[1] * g.d[2] * g.dt;
+  const T dtT = T(g.dt);
+  // J_q per unit weight: -q/(d_u d_v dt)
+  T cqw[3];
+#pragma unroll
+  for (int a = 0; a < 3; a++) cqw[a] = T(-qe * g.d[a] / vol_dt);
+  for (int j = p0 + threadIdx.x; j < p1; j += blockDim.x) {
+    const double pos[3] = {p.x[j], p.y[j], p.z[j]};
+    T X[3];
+    bool inside = true;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      X[a] = T((pos[a] - org[a]) * inv[a]);
+      const int ext = a == 0 ? TX : a == 1 ? TY : TZ;
+      if (!(X[a] >= T(-0.5)) || !(X[a] < T(ext) + T(0.5))) inside = false;
+    }
+    // the window covers the tile's cells and half a cell around them: a particle further out (never
+    // expected after the sort) is left untouched and flagged
+    if (!inside) {
+      atomicOr(&ctrl->status, (int)ST_OUTSIDE);
+      continue;
+    }
+    // gather from the staged window (window index = local cell + WM)
+    T wg[3][2][NS];
+    int bl[3][2];
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        const T Xs = X[a] - T(0.5) * T(h);
+        const T fl = floor(Xs);
+        shape_w<T, ORD>(Xs - fl, wg[a][h]);
+        bl[a][h] = (int)fl - SH + WM;
+      }
+    T EB[6];
+#pragma unroll
+    for (int c = 0; c < 6; c++) {
+      const int hx = c < 3 ? (c == 0) : (c != 3), hy = c < 3 ? (c == 1) : (c != 4), hz = c < 3 ? (c == 2) : (c != 5);
+      const T* F = sF + c * WN;
+      T acc = T(0);
+#pragma unroll
+      for (int l0 = 0; l0 < NS; l0++)
+#pragma unroll
+        for (int l1 = 0; l1 < NS; l1++) {
+          const T w01 = wg[0][hx][l0] * wg[1][hy][l1];
+          const T* row = F + ((bl[0][hx] + l0) * WY + (bl[1][hy] + l1)) * WZ + bl[2][hz];
+#pragma unroll
+          for (int l2 = 0; l2 < NS; l2++) acc += row[l2] * (w01 * wg[2][hz][l2]);
+        }
+      EB[c] = acc;
+    }
+    T u[3] = {p.ux[j], p.uy[j], p.uz[j]};
+    boris3<T>(u, EB, EB + 3, kq);
+    const T gm = sqrt(T(1) + (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]) * T(1.0 / (kC * kC)));
+    T X1[3], Dm[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      Dm[a] = dtT * (u[a] / gm);          // displacement [m]
+      X1[a] = X[a] + Dm[a] * invT[a];
+    }
+    // Esirkepov into the shared window
+    T S0[3][W], DS[3][W];
+    int base[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      const T f0 = floor(X[a]), f1 = floor(X1[a]);
+      base[a] = (int)(f0 < f1 ? f0 : f1) - SH;
+      T wa[NS], wb[NS];
+      shape_w<T, ORD>(X[a] - f0, wa);
+      shape_w<T, ORD>(X1[a] - f1, wb);
+      // each stencil starts at base or one cell above (moves below one cell): select with constant indices
+      const bool up0 = f0 > f1, up1 = f1 > f0;
+#pragma unroll
+      for (int m = 0; m < W; m++) {
+        const T s0 = up0 ? (m > 0 ? wa[m - 1] : T(0)) : (m < NS ? wa[m] : T(0));
+        const T s1 = up1 ? (m > 0 ? wb[m - 1] : T(0)) : (m < NS ? wb[m] : T(0));
+        S0[a][m] = s0;
+        DS[a][m] = s1 - s0;
+      }
+      base[a] += WM;
+    }
+    // the prefix along q of W_q = DS_q tr(u, v) factorises: J_q(m_q, m_u, m_v) = cq tr(m_u, m_v) C_q(m_q),
+    // C_q the running sum of DS_q; all loops unrolled so that the stencils stay in registers
+    T Cm[3][W];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      T run = T(0);
+#pragma unroll
+      for (int m = 0; m < W; m++) {
+        run += DS[a][m];
+        Cm[a][m] = run;
+      }
+    }
+    const T wj = p.w[j];
+#pragma unroll
+    for (int q = 0; q < 3; q++) {
+      const int u1 = (q + 1) % 3, v1 = (q + 2) % 3;
+      bool moved = false;
+#pragma unroll
+      for (int m = 0; m < W; m++) moved |= DS[q][m] != T(0);
+      if (!moved) continue;
+      const T cq = cqw[q] * wj;
+      T* Jq = sJ + q * WN;
+#pragma unroll
+      for (int mu = 0; mu < W; mu++)
+#pragma unroll
+        for (int mv = 0; mv < W; mv++) {
+          const T tr = S0[u1][mu] * S0[v1][mv] + T(0.5) * DS[u1][mu] * S0[v1][mv] +
+                       T(0.5) * S0[u1][mu] * DS[v1][mv] + DS[u1][mu] * DS[v1][mv] / T(3);
+          if (tr == T(0)) continue;
+          const T ct = cq * tr;
+#pragma unroll
+          for (int mq = 0; mq < W; mq++) {
+            const T v = ct * Cm[q][mq];
+            if (v == T(0)) continue;
+            int id3[3];
+            id3[q] = base[q] + mq; id3[u1] = base[u1] + mu; id3[v1] = base[v1] + mv;
+            atomicAdd(Jq + (id3[0] * WY + id3[1]) * WZ + id3[2], v);
+          }
+        }
+    }
+    const double pn[3] = {pos[0] + (double)Dm[0], pos[1] + (double)Dm[1], pos[2] + (double)Dm[2]};
+    p.x[j] = pn[0]; p.y[j] = pn[1]; p.z[j] = pn[2];
+    p.ux[j] = u[0]; p.uy[j] = u[1]; p.uz[j] = u[2];
+    bool out = false;
+    if (sizeof(T) == 8) {
+      // FP64 path: the removal decision on the physical position, as the method states it
+#pragma unroll
+      for (int a = 0; a < 3; a++) {
+        const double lop = g.lo[a] * g.d[a];
+        const double hip = g.hi[a] * g.d[a] + (a == 2 ? g.d[2] : 0.0);
+        if (pn[a] < lop || pn[a] >= hip) out = true;
+      }
+    } else {
+#pragma unroll
+      for (int a = 0; a < 3; a++)
+        if (X1[a] < lo[a] || X1[a] >= hi[a]) out = true;
+    }
+    if (out) p.fl[j] = 0;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 3 * WN; e += blockDim.x) {
+    const T v = sJ[e];
+    if (v == T(0)) continue;
+    const int c = e / WN, n = e - c * WN;
+    const int a = n / (WY * WZ), rr = n - a * (WY * WZ), b = rr / WZ, k = rr - b * WZ;
+    const int i = c0[0] - WM + a, jj = c0[1] - WM + b, kk = c0[2] - WM + k;
+    if (i < 0 || i > g.n[0] || jj < 0 || jj > g.n[1] || kk < 0 || kk > g.n[2]) continue;
+    atomicAdd(f.J[c] + nid(g, i, jj, kk), v);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -904,10 +1200,10 @@ struct Sim3 : Sim3Api {
   // fields (3-component blocks)
   T *E = nullptr, *B = nullptr, *J = nullptr, *Ep = nullptr, *Eb = nullptr, *Ee = nullptr;
   T *Es = nullptr, *Bs = nullptr;     // 6 split parts each
-  T *fE = nullptr, *fB = nullptr, *tmp = nullptr;
+  T *fE = nullptr, *fB = nullptr, *tmp = nullptr, *tmp2 = nullptr;
   double* rho = nullptr;              // scratch for PIC_RHO
   double* out_d = nullptr;            // copy-out scratch
-  Pml3 pm;
+  Pml3<T> pm;
   Taps3<T> taps;
   int P = 0;
   // particles
@@ -917,8 +1213,10 @@ struct Sim3 : Sim3Api {
   Ctrl3* ctrl = nullptr;
   int* blk = nullptr;
   long blk_cap = 0;
-  int compact_every = 16, since_compact = 0;
   int64_t compactions = 0;
+  Tiles3 tl{};
+  int ntiles = 0;
+  long key_cap = 0;
   // plasma
   bool loaded = false;
   Lat3 lat;
@@ -1010,32 +1308,32 @@ struct Sim3 : Sim3Api {
     g.cs = (long)(c->nx + 1) * (c->ny + 1) * g.ldz;
     const size_t cs = (size_t)g.cs;
     E = dal<T>(3 * cs); B = dal<T>(3 * cs); J = dal<T>(3 * cs); Ep = dal<T>(3 * cs); Eb = dal<T>(3 * cs);
-    Ee = dal<T>(3 * cs); fE = dal<T>(3 * cs); fB = dal<T>(3 * cs); tmp = dal<T>(cs);
+    Ee = dal<T>(3 * cs); fE = dal<T>(3 * cs); fB = dal<T>(3 * cs); tmp = dal<T>(cs); tmp2 = dal<T>(cs);
     Es = dal<T>(6 * cs); Bs = dal<T>(6 * cs);
     ctrl = dal<Ctrl3>(1);
     bacc = dal<double>(8);
     sred = dal<double>(8);
-    if (!E || !B || !J || !Ep || !Eb || !Ee || !fE || !fB || !tmp || !Es || !Bs || !ctrl || !bacc || !sred)
+    if (!E || !B || !J || !Ep || !Eb || !Ee || !fE || !fB || !tmp || !tmp2 || !Es || !Bs || !ctrl || !bacc || !sred)
       return fail(PIC_ENOMEM, "allocation failed");
     // PML tables per axis, integer and half positions
     for (int a = 0; a < 3; a++) {
       const int n = g.n[a];
-      std::vector<double> sgv(n + 2), xiv(n + 2), cfv(n + 2);
+      std::vector<T> sgv(n + 2), xiv(n + 2), cfv(n + 2);
       for (int h = 0; h < 2; h++) {
         for (int i = 0; i <= n + 1; i++) {
           const double sg = i <= n ? host_sigma(cfg, i + 0.5 * h, n, g.d[a]) : 0.0;
           const double xi = c->pml_xi_exp ? std::exp(-sg * g.dt) : (1.0 - 0.5 * sg * g.dt) / (1.0 + 0.5 * sg * g.dt);
-          sgv[i] = sg;
-          xiv[i] = xi;
-          cfv[i] = sg > 0.0 ? (1.0 - xi) / sg : g.dt;
+          sgv[i] = T(sg);
+          xiv[i] = T(xi);
+          cfv[i] = T(sg > 0.0 ? (1.0 - xi) / sg : g.dt);
         }
-        double* d_s = dal<double>(n + 2);
-        double* d_x = dal<double>(n + 2);
-        double* d_c = dal<double>(n + 2);
+        T* d_s = dal<T>(n + 2);
+        T* d_x = dal<T>(n + 2);
+        T* d_c = dal<T>(n + 2);
         if (!d_s || !d_x || !d_c) return fail(PIC_ENOMEM, "allocation failed");
-        cudaMemcpyAsync(d_s, sgv.data(), sizeof(double) * (n + 2), cudaMemcpyHostToDevice, s);
-        cudaMemcpyAsync(d_x, xiv.data(), sizeof(double) * (n + 2), cudaMemcpyHostToDevice, s);
-        cudaMemcpyAsync(d_c, cfv.data(), sizeof(double) * (n + 2), cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(d_s, sgv.data(), sizeof(T) * (n + 2), cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(d_x, xiv.data(), sizeof(T) * (n + 2), cudaMemcpyHostToDevice, s);
+        cudaMemcpyAsync(d_c, cfv.data(), sizeof(T) * (n + 2), cudaMemcpyHostToDevice, s);
         cudaStreamSynchronize(s);
         pm.sg[a][h] = d_s; pm.xi[a][h] = d_x; pm.cf[a][h] = d_c;
       }
@@ -1056,6 +1354,16 @@ struct Sim3 : Sim3Api {
     for (int m = 0; m < 33; m++) taps.c[m] = m <= 2 * P ? T(t[m]) : T(0);
     taps.P = P;
     taps.s = c->filter_stride;
+    tl.nt[0] = (g.n[0] + TX - 1) / TX;
+    tl.nt[1] = (g.n[1] + TY - 1) / TY;
+    tl.nt[2] = (g.n[2] + TZ - 1) / TZ;
+    ntiles = tl.nt[0] * tl.nt[1] * tl.nt[2];
+    tl.cnt = dal<int>(ntiles + 1);
+    tl.start = dal<int>(ntiles + 1);
+    if (!tl.cnt || !tl.start) return fail(PIC_ENOMEM, "allocation failed");
+    const int smem = (int)(9 * WN * sizeof(T));
+    cudaFuncSetAttribute(k3_push_tiles<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k3_push_tiles<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     cudaEventCreate(&ev0);
     cudaEventCreate(&ev1);
     return cudaGetLastError() == cudaSuccess ? PIC_OK : fail(PIC_ECUDA, "CUDA error in 3D init");
@@ -1070,6 +1378,11 @@ struct Sim3 : Sim3Api {
       q.id = dal<uint32_t>(n); q.fl = dal<int>(n);
       if (!q.x || !q.y || !q.z || !q.ux || !q.uy || !q.uz || !q.w || !q.id || !q.fl) return PIC_ENOMEM;
     }
+    if (tl.key) dfree(tl.key);
+    if (tl.rank) dfree(tl.rank);
+    tl.key = dal<int>(n);
+    tl.rank = dal<int>(n);
+    if (!tl.key || !tl.rank) return PIC_ENOMEM;
     cap = n;
     return PIC_OK;
   }
@@ -1106,9 +1419,18 @@ struct Sim3 : Sim3Api {
     const int n_new = read_count();
     if (n_new < 0) return fail(PIC_ECUDA, "CUDA error in compaction");
     count_ub = n_new;
-    since_compact = 0;
-    compactions++;
     return PIC_OK;
+  }
+
+  // particles into tile order (dropping the dead ones) in the other buffer set
+  void sort_tiles() {
+    cudaMemsetAsync(tl.cnt, 0, sizeof(int) * (ntiles + 1), s);
+    k3_tile_key<T><<<nblk(count_ub, 256), 256, 0, s>>>(g, P2[cur], ctrl, tl, (int)count_ub);
+    k3_scan_tiles<<<1, 1024, 0, s>>>(tl.cnt, tl.start, ntiles, ctrl);
+    k3_tile_scatter<T><<<nblk(count_ub, 256), 256, 0, s>>>(P2[cur], P2[1 - cur], tl, (int)count_ub);
+    nl += 3;
+    cur = 1 - cur;
+    compactions++;
   }
 
   int grow(long need) {
@@ -1188,7 +1510,7 @@ struct Sim3 : Sim3Api {
     const long per = (long)lat.nxl * lat.nyl;
     const long rows_box = m_end - m_beg + 1;
     const double rows_per_step = beta * kC * g.dt / lat.h + 1.0;
-    long want = (long)((rows_box + rows_per_step * (compact_every + 2)) * per * 1.1) + 1024;
+    long want = (long)((rows_box + rows_per_step * 64) * per * 1.1) + 1024;
     if (alloc_parts(want) != PIC_OK) return fail(PIC_ENOMEM, "particle allocation failed");
     count_ub = 0;
     if (inject_rows(m_beg, m_end, t) != PIC_OK) return st;
@@ -1290,13 +1612,13 @@ struct Sim3 : Sim3Api {
     }
   }
 
+  dim3 grid3() const { return dim3(nblk(g.n[2] + 1, 128 * KPT), g.n[1] + 1, g.n[0] + 1); }
+
   void filter3(T* F, int comp) {
-    // x: F -> tmp, y: tmp -> F, z: F -> tmp, then tmp -> F by a copy
-    const long nn = nodes();
-    k3_filter_axis<T><<<nblk(nn, 256), 256, 0, s>>>(g, F, tmp, comp, 0, taps);
-    k3_filter_axis<T><<<nblk(nn, 256), 256, 0, s>>>(g, tmp, F, comp, 1, taps);
-    k3_filter_axis<T><<<nblk(nn, 256), 256, 0, s>>>(g, F, tmp, comp, 2, taps);
-    cudaMemcpyAsync(F, tmp, sizeof(T) * g.cs, cudaMemcpyDeviceToDevice, s);
+    // x: F -> tmp, y: tmp -> tmp2, z: tmp2 -> F
+    launch_filter_axis<T>(g, grid3(), F, tmp, comp, 0, taps, s);
+    launch_filter_axis<T>(g, grid3(), tmp, tmp2, comp, 1, taps, s);
+    launch_filter_axis<T>(g, grid3(), tmp2, F, comp, 2, taps, s);
     nl += 3;
   }
 
@@ -1308,8 +1630,8 @@ struct Sim3 : Sim3Api {
     btd_part(1, 0);
     // 1. Faraday + Friedman + PML-B (B^{n-1/2} -> B^{n+1/2}), gather copies
     k3_eeff<T><<<nblk(n3, 256), 256, 0, s>>>(n3, E, Ep, Eb, Ee, T(1.0 + th / 4.0), T(0.5), T(0.5 - th / 4.0));
-    k3_faraday<T><<<nblk(nn, 128), 128, 0, s>>>(g, pm, Ee, B, Bs, fB, T(cfg.ck_alpha), T(cfg.ck_beta),
-                                                 T(cfg.ck_gamma), T(g.dt));
+    k3_faraday<T><<<grid3(), 128, 0, s>>>(g, pm, Ee, B, Bs, fB, T(cfg.ck_alpha), T(cfg.ck_beta), T(cfg.ck_gamma),
+                                          T(g.dt));
     k3_friedman<T><<<nblk(n3, 256), 256, 0, s>>>(n3, E, Ep, Eb, fE, T(1.0 - th / 2.0), T(th / 2.0));
     nl += 3;
     if (cfg.filter_gather && P > 0)
@@ -1320,11 +1642,13 @@ struct Sim3 : Sim3Api {
     for (int c = 0; c < 3; c++) { f.fE[c] = fE + c * g.cs; f.fB[c] = fB + c * g.cs; f.J[c] = J + c * g.cs; }
     const T kq = T(-kQe * g.dt / (2.0 * kMe));
     if (loaded && count_ub > 0) {
+      sort_tiles();
+      const int smem = (int)(9 * WN * sizeof(T));
       if (timing_on) cudaEventRecord(ev0, s);
       if (cfg.shape_order == 3)
-        k3_push<T, 3><<<nblk(count_ub, 128), 128, 0, s>>>(g, f, P2[cur], ctrl, kq, -kQe);
+        k3_push_tiles<T, 3><<<ntiles, 256, smem, s>>>(g, f, P2[cur], tl, ctrl, kq, -kQe);
       else
-        k3_push<T, 1><<<nblk(count_ub, 128), 128, 0, s>>>(g, f, P2[cur], ctrl, kq, -kQe);
+        k3_push_tiles<T, 1><<<ntiles, 256, smem, s>>>(g, f, P2[cur], tl, ctrl, kq, -kQe);
       nl++;
       if (timing_on) {
         cudaEventRecord(ev1, s);
@@ -1361,7 +1685,7 @@ struct Sim3 : Sim3Api {
     // 4. current filter, Ampere + PML-E
     if (cfg.filter_J && P > 0)
       for (int c = 0; c < 3; c++) filter3(J + c * g.cs, c);
-    k3_ampere<T><<<nblk(nn, 128), 128, 0, s>>>(g, pm, E, Es, B, J, T(g.dt * kC * kC), T(g.dt / kEps0));
+    k3_ampere<T><<<grid3(), 128, 0, s>>>(g, pm, E, Es, B, J, T(g.dt * kC * kC), T(g.dt / kEps0));
     nl++;
     btd_part(0, 1);
     btd_part(1, 1);
@@ -1373,7 +1697,6 @@ struct Sim3 : Sim3Api {
         if (inject_rows(row_next, m_end, tn1) != PIC_OK) return st;
         row_next = m_end;
       }
-      if (++since_compact >= compact_every && compact() != PIC_OK) return st;
     }
     step++;
     return PIC_OK;
@@ -1389,6 +1712,9 @@ struct Sim3 : Sim3Api {
   int sync() override {
     const cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail(PIC_ECUDA, std::string("CUDA error: ") + cudaGetErrorString(e));
+    int dst = 0;
+    cudaMemcpy(&dst, &ctrl->status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (dst & ST_OUTSIDE) return fail(PIC_EOVERFLOW, "a particle left its tile's window (not pushed)");
     return st;
   }
 
