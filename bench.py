@@ -45,6 +45,9 @@ BYTES_PER_CELL = {"mixed": 168, "fp64": 336}
 # (profiles/k_push_stage2d_2048x256_mixed.md: 364.33 MB for 6,487,608 electrons), scaled to the
 # full box by its particle count; None for configurations not captured
 TRAFFIC_BYTES_PER_PARTICLE = {("mixed", 3): 56.16}
+# 3D: ncu dram bytes of k3_push_tiles on the 256 x 128 x 128 box (profiles/k3_push_tiles_stage3d_256x128x128_mixed.md:
+# 197.95 MB for 2,356,608 electrons), scaled to the full box by its particle count
+TRAFFIC_BYTES_PER_PARTICLE_3D = {("mixed", 3): 84.0}
 
 
 def measured_peaks() -> dict:
@@ -428,12 +431,14 @@ def main():
     bpp = (BYTES_PER_PARTICLE_3D if three else BYTES_PER_PARTICLE)[args.precision]
     push_avg_ms = push_ms / max(push_n, 1)
     achieved = n_avg * bpp / (push_avg_ms * 1e-3) / 1e9
-    tpp = None if three else TRAFFIC_BYTES_PER_PARTICLE.get((args.precision, args.order))
-    roof = {"kernel": "k3_push (3D gather + Boris + Esirkepov)" if three else "k_push (gather + Boris + Esirkepov)",
+    tpp = (TRAFFIC_BYTES_PER_PARTICLE_3D if three else TRAFFIC_BYTES_PER_PARTICLE).get((args.precision, args.order))
+    roof = {"kernel": "k3_push_tiles (3D gather + Boris + Esirkepov)" if three else "k_push (gather + Boris + Esirkepov)",
             "bound": "hbm", "achieved": achieved, "peak": peak,
             "unit": "GB/s", "frac": achieved / peak, "traffic": tpp * n_avg if tpp else None,
-            "traffic_source": "ncu dram bytes of k_push, 2048 x 256 box, scaled by particles" if tpp else None,
-            "note": ("3D push: global-memory gather and global atomics, no tile staging yet" if three else
+            "traffic_source": ("ncu dram bytes of k3_push_tiles, 256 x 128 x 128 box, scaled by particles" if three
+                               else "ncu dram bytes of k_push, 2048 x 256 box, scaled by particles") if tpp else None,
+            "note": ("3D push on sorted 4x4x16-cell tiles with shared-memory windows: latency-bound at a quarter "
+                     "occupancy (ncu: 35% issue slots, 44% L1/shared, 2% DRAM)" if three else
                      "at cubic order the push is bound by instruction issue "
                      "(ncu: 62% issue slots, 52% L1/shared, 15% DRAM), not by HBM"),
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback",
