@@ -326,6 +326,13 @@ int64_t pic_mlp_param_count(pic_mlp* mlp);
 int pic_mlp_get_params(pic_mlp* mlp, float* dst_host);
 int pic_mlp_set_params(pic_mlp* mlp, const float* src_host);
 int pic_mlp_infer(pic_mlp* mlp, const float* x_device, int64_t n, float* y_device);
+/* pic_mlp_infer is asynchronous. With every padded width (multiple of 16) <= 256 and at most 16 layers it
+ * runs one fused tcgen05 kernel (128 rows per CTA, BF16 operands in shared memory, FP32 accumulators in
+ * tensor memory, weights rebuilt into packed images after any parameter change); otherwise, or after
+ * pic_mlp_use_tensor_cores(mlp, 0), the tiled CUDA-core GEMMs (PIC_EINVAL when enabling is impossible).
+ * pic_mlp_status synchronises the stream and returns PIC_ETIMEOUT if a bounded tensor-core wait gave up. */
+int pic_mlp_use_tensor_cores(pic_mlp* mlp, int enable);
+int pic_mlp_status(pic_mlp* mlp);
 int pic_mlp_grad(pic_mlp* mlp, const float* x_device, const float* t_device, int n, float* loss_host,
                  float* grad_host);
 int pic_mlp_train(pic_mlp* mlp, const float* x_device, const float* t_device, int n, int epochs, int batch,

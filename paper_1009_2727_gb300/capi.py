@@ -32,7 +32,7 @@ EXPORTS = ("pic_init", "pic_load_plasma", "pic_inject_laser", "pic_step", "pic_s
            "pic_ensemble_create", "pic_ensemble_step", "pic_ensemble_sync", "pic_ensemble_size",
            "pic_ensemble_member", "pic_ensemble_free",
            "pic_mlp_create", "pic_mlp_free", "pic_mlp_param_count", "pic_mlp_get_params", "pic_mlp_set_params",
-           "pic_mlp_infer", "pic_mlp_grad", "pic_mlp_train")
+           "pic_mlp_infer", "pic_mlp_grad", "pic_mlp_train", "pic_mlp_use_tensor_cores", "pic_mlp_status")
 NOALLOC_MAX_NZ = 16384
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -183,6 +183,8 @@ def load(build_if_missing: bool = True):
         L.pic_mlp_get_params.argtypes = [vp, _F]
         L.pic_mlp_set_params.argtypes = [vp, _F]
         L.pic_mlp_infer.argtypes = [vp, vp, ctypes.c_int64, vp]
+        L.pic_mlp_use_tensor_cores.argtypes = [vp, ctypes.c_int]
+        L.pic_mlp_status.argtypes = [vp]
         L.pic_mlp_grad.argtypes = [vp, vp, vp, ctypes.c_int, _F, _F]
         L.pic_mlp_train.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_float,
                                     ctypes.c_float, ctypes.c_uint64, _F]

@@ -147,6 +147,200 @@ uint64_t splitmix64(uint64_t& s) {
   return z ^ (z >> 31);
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core inference (tcgen05): one CTA takes 128 rows through every layer. Each layer's weights
+// come as a prepacked BF16 image (K-major, no swizzle, padded to multiples of 16) by one bulk TMA copy
+// into shared memory; the activations of the 128 rows sit in shared memory in the same canonical layout;
+// one thread issues the K/16 tcgen05.mma (M = 128, N = padded width, BF16 x BF16 -> FP32) into a TMEM
+// accumulator; the four warps read their 32 TMEM lanes (one row per thread), add the bias, apply GELU
+// and write the next layer's operand (or the FP32 outputs) in place.
+constexpr int TC_M = 128;
+constexpr int TC_THREADS = 512;                            // 16 warps: 4 TMEM lane groups x 4 column groups
+constexpr int TC_MAXW = 256;                              // padded width limit of this kernel
+constexpr int TC_A_BYTES = TC_M * TC_MAXW * 2;            // activations
+constexpr int TC_B_BYTES = TC_MAXW * TC_MAXW * 2;         // one layer's weights
+constexpr int TC_SMEM = TC_A_BYTES + TC_B_BYTES + 64;
+constexpr int TC_MAXL = 16;
+
+__host__ __device__ inline int pad16(int v) { return (v + 15) & ~15; }
+
+// byte offset of element (r, k) of an operand with Kp columns: 8 x 8 core matrices of 128 contiguous
+// bytes (a row of 8 elements every 16 bytes), K-groups 128 bytes apart, 8-row groups Kp * 16 bytes apart
+__host__ __device__ inline uint32_t canon_off(int r, int k, int Kp) {
+  return (uint32_t)((r >> 3) * (Kp * 16) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+__global__ void k_pack_weights(const __nv_bfloat16* W, int N, int K, int Np, int Kp, __nv_bfloat16* img) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= Np * Kp) return;
+  const int r = e / Kp, k = e - r * Kp;
+  img[canon_off(r, k, Kp) >> 1] = (r < N && k < K) ? W[(long)r * K + k] : __float2bfloat16(0.0f);
+}
+
+struct TcLayer {
+  const __nv_bfloat16* img;
+  const float* bias;
+  int N, K, Np, Kp;
+};
+struct TcNet {
+  TcLayer l[TC_MAXL];
+  int L, k0;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: start, LBO (K direction), SBO (8-row groups), fixed version bits 46-47,
+// no swizzle
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// wait for the phase of an mbarrier, giving up after about half a second (then the error flag is set)
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err) {
+  const uint64_t t0 = global_ns();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (global_ns() - t0 > 500000000ull) {
+      atomicExch(err, 1);
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+
+__global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_fwd_tc(TcNet net, const float* __restrict__ x, long n,
+                                                             float* __restrict__ y, int* err) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  unsigned char* A = sm;
+  unsigned char* Bw = sm + TC_A_BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + TC_A_BYTES + TC_B_BYTES);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // TMEM lanes 32 (warp % 4) .. +31 are this warp's rows; chunks of 16 columns go round-robin to warp / 4
+  const int lgrp = warp & 3, cgrp = warp >> 2;
+  const int rloc = lgrp * 32 + lane;
+  const long row0 = (long)blockIdx.x * TC_M;
+  const uint32_t barW = smem_u32(&bars[0]), barM = smem_u32(&bars[1]);
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(barW) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(barM) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_u32(tslot))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  // the 128 input rows, BF16, zero padded, in the first layer's operand layout
+  {
+    const int Kp = net.l[0].Kp, nk8 = Kp / 8;
+    for (int e = tid; e < TC_M * nk8; e += TC_THREADS) {
+      const int rr = e / nk8, k8 = e - rr * nk8;
+      const long r = row0 + rr;
+      __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+      for (int q = 0; q < 8; q++) {
+        const int k = k8 * 8 + q;
+        v[q] = __float2bfloat16((r < n && k < net.k0) ? x[r * net.k0 + k] : 0.0f);
+      }
+      *reinterpret_cast<uint4*>(A + canon_off(rr, k8 * 8, Kp)) = *reinterpret_cast<const uint4*>(v);
+    }
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  uint32_t phW = 0, phM = 0;
+  bool ok = true;
+  // the weights of layer l arrive by one bulk copy, issued for the next layer as soon as the current
+  // layer's products have completed (it overlaps the epilogue)
+  auto load_weights = [&](int l) {
+    const uint32_t bytes = (uint32_t)(net.l[l].Np * net.l[l].Kp * 2);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(barW), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(Bw)),
+                 "l"(net.l[l].img), "r"(bytes), "r"(barW)
+                 : "memory");
+  };
+  if (tid == 0) load_weights(0);
+  for (int l = 0; l < net.L; l++) {
+    const TcLayer Ly = net.l[l];
+    ok = __syncthreads_and(mbar_wait(barW, phW, err) ? 1 : 0) != 0;
+    phW ^= 1u;
+    if (!ok) break;
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(Ly.Np >> 3) << 17) |
+                             ((uint32_t)(TC_M >> 4) << 24);
+      const uint32_t sbo = (uint32_t)(Ly.Kp * 16);
+      for (int ks = 0; ks < Ly.Kp / 16; ks++) {
+        const uint64_t ad = smem_desc(smem_u32(A) + ks * 256, 128, sbo);
+        const uint64_t bd = smem_desc(smem_u32(Bw) + ks * 256, 128, sbo);
+        const uint32_t acc = ks > 0 ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+            : "memory");
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(barM)
+                   : "memory");
+    }
+    ok = __syncthreads_and(mbar_wait(barM, phM, err) ? 1 : 0) != 0;
+    phM ^= 1u;
+    if (!ok) break;
+    if (tid == 0 && l + 1 < net.L) load_weights(l + 1);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const bool last = l == net.L - 1;
+    const long r = row0 + rloc;
+    for (int c0 = 16 * cgrp; c0 < Ly.Np; c0 += 64) {
+      uint32_t v[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          : "r"(tmem + ((uint32_t)(lgrp * 32) << 16) + (uint32_t)c0)
+          : "memory");
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      float f[16];
+#pragma unroll
+      for (int q = 0; q < 16; q++) f[q] = __uint_as_float(v[q]) + (c0 + q < Ly.N ? Ly.bias[c0 + q] : 0.0f);
+      if (!last) {
+        __align__(16) __nv_bfloat16 h[16];
+#pragma unroll
+        for (int q = 0; q < 16; q++) h[q] = __float2bfloat16(c0 + q < Ly.N ? gelu_f(f[q]) : 0.0f);
+        *reinterpret_cast<uint4*>(A + canon_off(rloc, c0, Ly.Np)) = *reinterpret_cast<const uint4*>(h);
+        *reinterpret_cast<uint4*>(A + canon_off(rloc, c0 + 8, Ly.Np)) = *reinterpret_cast<const uint4*>(h + 8);
+      } else if (r < n) {
+#pragma unroll
+        for (int q = 0; q < 16; q++)
+          if (c0 + q < Ly.N) y[r * Ly.N + c0 + q] = f[q];
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  }
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
+}
+
 }  // namespace
 
 struct pic_mlp {
@@ -174,6 +368,12 @@ struct pic_mlp {
   int curve_cap = 0;
   float* xb = nullptr;
   float* tb = nullptr;
+  // tensor-core inference: packed weight images per layer, rebuilt when the BF16 weights change
+  bool tc_ok = false;                   // every padded width <= 256
+  bool tc_dirty = true;
+  bool use_tc = true;
+  std::vector<__nv_bfloat16*> img;
+  int* err = nullptr;                   // device flag: a tensor-core wait gave up
   cudaStream_t s = nullptr;
   pic_alloc_fn alloc = nullptr;
   pic_free_fn freef = nullptr;
@@ -302,7 +502,15 @@ int pic_mlp_create(int n_layers, const int* widths, uint64_t seed, pic_alloc_fn 
   m->m = mlp_al<float>(m, off);
   m->v = mlp_al<float>(m, off);
   m->loss = mlp_al<float>(m, 1);
-  if (!m->p || !m->pb || !m->g || !m->m || !m->v || !m->loss) {
+  m->err = mlp_al<int>(m, 1);
+  m->tc_ok = n_layers <= TC_MAXL;
+  for (int l = 0; l <= n_layers; l++) m->tc_ok = m->tc_ok && pad16(widths[l]) <= TC_MAXW;
+  if (m->tc_ok) {
+    for (int l = 1; l <= n_layers; l++) m->img.push_back(mlp_al<__nv_bfloat16>(m, (size_t)pad16(widths[l]) * pad16(widths[l - 1])));
+    for (auto* q : m->img) m->tc_ok = m->tc_ok && q;
+    cudaFuncSetAttribute(k_mlp_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+  }
+  if (!m->p || !m->pb || !m->g || !m->m || !m->v || !m->loss || !m->err) {
     mlp_release(m);
     delete m;
     return PIC_ENOMEM;
@@ -321,6 +529,7 @@ int pic_mlp_create(int n_layers, const int* widths, uint64_t seed, pic_alloc_fn 
   k_to_bf16<<<(unsigned)((off + 255) / 256), 256, 0, m->s>>>(off, m->p, m->pb);
   cudaMemsetAsync(m->m, 0, off * sizeof(float), m->s);
   cudaMemsetAsync(m->v, 0, off * sizeof(float), m->s);
+  cudaMemsetAsync(m->err, 0, sizeof(int), m->s);
   if (cudaStreamSynchronize(m->s) != cudaSuccess) {
     mlp_release(m);
     delete m;
@@ -352,6 +561,7 @@ int pic_mlp_set_params(pic_mlp* m, const float* src) {
   cudaMemcpyAsync(m->p, src, m->np * sizeof(float), cudaMemcpyHostToDevice, m->s);
   k_to_bf16<<<(unsigned)((m->np + 255) / 256), 256, 0, m->s>>>(m->np, m->p, m->pb);
   m->adam_t = 0;
+  m->tc_dirty = true;
   cudaMemsetAsync(m->m, 0, m->np * sizeof(float), m->s);
   cudaMemsetAsync(m->v, 0, m->np * sizeof(float), m->s);
   return cudaStreamSynchronize(m->s) == cudaSuccess ? PIC_OK : PIC_ECUDA;
@@ -359,6 +569,31 @@ int pic_mlp_set_params(pic_mlp* m, const float* src) {
 
 int pic_mlp_infer(pic_mlp* m, const float* x, int64_t n, float* y) {
   if (!m || !x || !y || n < 0) return PIC_EINVAL;
+  if (n == 0) return PIC_OK;
+  if (m->tc_ok && m->use_tc) {
+    if (m->tc_dirty) {
+      for (int l = 1; l <= m->L; l++) {
+        const int N = m->w[l], K = m->w[l - 1], Np = pad16(N), Kp = pad16(K);
+        k_pack_weights<<<(Np * Kp + 255) / 256, 256, 0, m->s>>>(m->pb + m->off_w[l - 1], N, K, Np, Kp, m->img[l - 1]);
+      }
+      m->tc_dirty = false;
+    }
+    TcNet net{};
+    net.L = m->L;
+    net.k0 = m->w[0];
+    for (int l = 1; l <= m->L; l++) {
+      TcLayer& t = net.l[l - 1];
+      t.img = m->img[l - 1];
+      t.bias = m->p + m->off_b[l - 1];
+      t.N = m->w[l];
+      t.K = m->w[l - 1];
+      t.Np = pad16(t.N);
+      t.Kp = pad16(t.K);
+    }
+    const long blocks = (n + TC_M - 1) / TC_M;
+    k_mlp_fwd_tc<<<(unsigned)blocks, TC_THREADS, TC_SMEM, m->s>>>(net, x, (long)n, y, m->err);
+    return cudaGetLastError() == cudaSuccess ? PIC_OK : PIC_ECUDA;
+  }
   const int chunk = 65536;
   for (int64_t r0 = 0; r0 < n; r0 += chunk) {
     const int nb = (int)(n - r0 < chunk ? n - r0 : chunk);
@@ -368,6 +603,21 @@ int pic_mlp_infer(pic_mlp* m, const float* x, int64_t n, float* y) {
                     m->s);
   }
   return cudaGetLastError() == cudaSuccess ? PIC_OK : PIC_ECUDA;
+}
+
+int pic_mlp_use_tensor_cores(pic_mlp* m, int enable) {
+  if (!m) return PIC_EINVAL;
+  if (enable && !m->tc_ok) return PIC_EINVAL;
+  m->use_tc = enable != 0;
+  return PIC_OK;
+}
+
+int pic_mlp_status(pic_mlp* m) {
+  if (!m) return PIC_EINVAL;
+  if (cudaStreamSynchronize(m->s) != cudaSuccess) return PIC_ECUDA;
+  int e = 0;
+  if (cudaMemcpy(&e, m->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return PIC_ECUDA;
+  return e ? PIC_ETIMEOUT : PIC_OK;
 }
 
 int pic_mlp_grad(pic_mlp* m, const float* x, const float* t, int n, float* loss_host, float* grad_host) {
@@ -397,6 +647,7 @@ int pic_mlp_train(pic_mlp* m, const float* x, const float* t, int n, int epochs,
     m->curve_cap = epochs;
   }
   if (epochs > 0) cudaMemsetAsync(m->curve, 0, (size_t)epochs * sizeof(float), m->s);
+  m->tc_dirty = true;
   // the host draws every epoch's order up front (pinned by the seed), one upload per epoch
   std::vector<int> perm(n);
   uint64_t st = seed;

@@ -58,11 +58,15 @@ class MLP:
         p = np.ascontiguousarray(p, dtype=np.float32)
         self._check(self.L.pic_mlp_set_params(self.h, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
 
+    def use_tensor_cores(self, enable: bool = True):
+        """serve with the fused tcgen05 kernel (default when every padded width <= 256) or the CUDA-core GEMMs"""
+        self._check(self.L.pic_mlp_use_tensor_cores(self.h, int(bool(enable))))
+
     def forward(self, x) -> np.ndarray:
         xd, xp = self._dev(x)
         y = self.torch.empty((xd.shape[0], self.widths[-1]), dtype=self.torch.float32, device="cuda")
         self._check(self.L.pic_mlp_infer(self.h, xp, xd.shape[0], ctypes.c_void_p(y.data_ptr())))
-        self.torch.cuda.synchronize()
+        self._check(self.L.pic_mlp_status(self.h))
         return y.cpu().numpy()
 
     def forward_device(self, x_ptr: int, n: int, y_ptr: int):

@@ -77,6 +77,34 @@ def test_mlp_forward_and_gradient_match_oracle(S, widths, n):
     net.close()
 
 
+@pytest.mark.parametrize("widths,n", [([6, 256, 256, 256, 4], 1000), ([6, 96, 80, 4], 333), ([3, 1, 5], 1),
+                                      ([16, 128, 16], 128)])
+def test_mlp_tensor_core_inference_matches_oracle_and_cuda_cores(S, widths, n):
+    """the fused tcgen05 inference kernel: several 128-row tiles with a ragged last one, padded widths,
+    a one-unit layer and a single row, an exact tile; against the oracle and the CUDA-core GEMM path"""
+    from oracle import mlp as ref
+    rng = np.random.default_rng(17)
+    net = S.MLP(widths, seed=8)
+    p = net.get_params().astype(np.float64)
+    p += rng.normal(0, 0.05, p.size)
+    net.set_params(p)
+    x = rng.normal(0, 1, (n, widths[0]))
+    y_tc = net.forward(x)
+    net.use_tensor_cores(False)
+    y_cc = net.forward(x)
+    net.use_tensor_cores(True)
+    y_ref, _ = ref.forward(bf16_weights(net.get_params(), widths), widths, bf16(x))
+    scale = np.abs(y_ref).max()
+    assert np.abs(y_tc - y_ref).max() <= 2e-2 * scale
+    assert np.abs(y_tc - y_cc).max() <= 2e-2 * scale
+    # after a parameter change the packed weights are rebuilt
+    net.set_params(p * 0.5)
+    y2 = net.forward(x)
+    y2_ref, _ = ref.forward(bf16_weights(net.get_params(), widths), widths, bf16(x))
+    assert np.abs(y2 - y2_ref).max() <= 2e-2 * np.abs(y2_ref).max()
+    net.close()
+
+
 def test_mlp_forward_over_chunks_matches_rows(S):
     """a batch larger than one 65536-row chunk with a ragged last chunk: sampled rows against the oracle"""
     from oracle import mlp as ref
