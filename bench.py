@@ -42,9 +42,9 @@ BYTES_PER_PARTICLE_3D = {"mixed": 76, "fp64": 104}
 BYTES_PER_CELL = {"mixed": 168, "fp64": 336}
 # measured DRAM bytes (read + write) per particle of one push launch, mixed precision, cubic shapes:
 # ncu dram__bytes_read.sum + dram__bytes_write.sum of k_push on the 2048 x 256 stage box
-# (profiles/k_push_stage2d_2048x256_mixed.md: 364.33 MB for 6,487,608 electrons), scaled to the
+# (profiles/k_push_stage2d_2048x256_mixed.md: 385.22 MB for 6,487,608 electrons), scaled to the
 # full box by its particle count; None for configurations not captured
-TRAFFIC_BYTES_PER_PARTICLE = {("mixed", 3): 56.16}
+TRAFFIC_BYTES_PER_PARTICLE = {("mixed", 3): 59.38}
 # 3D: ncu dram bytes of k3_push_tiles on the 256 x 128 x 128 box (profiles/k3_push_tiles_stage3d_256x128x128_mixed.md:
 # 197.95 MB for 2,356,608 electrons), scaled to the full box by its particle count
 TRAFFIC_BYTES_PER_PARTICLE_3D = {("mixed", 3): 84.0}
@@ -451,7 +451,7 @@ def main():
             "note": ("3D push on sorted 4x4x16-cell tiles with shared-memory windows: latency-bound at a quarter "
                      "occupancy (ncu: 35% issue slots, 44% L1/shared, 2% DRAM)" if three else
                      "at cubic order the push is bound by instruction issue "
-                     "(ncu: 62% issue slots, 52% L1/shared, 15% DRAM), not by HBM"),
+                     "(ncu: 65% issue slots, 59% L1/shared, 19% DRAM), not by HBM"),
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback",
             "algorithmic_bytes_per_particle": bpp, "push_ms_per_step": push_avg_ms,
             "share_of_step": push_avg_ms / (ms / args.steps)}

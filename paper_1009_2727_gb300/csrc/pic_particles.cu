@@ -507,7 +507,7 @@ __device__ __noinline__ void push_global_guarded(const T* gE, const T* gB, T* gJ
 }
 
 template <class T, int ORDER>
-__global__ void __launch_bounds__(PB_THREADS, 4) k_push(GridP g, const T* gE, const T* gB, T* gJ, Particles<T> p,
+__global__ void __launch_bounds__(PB_THREADS, 5) k_push(GridP g, const T* gE, const T* gB, T* gJ, Particles<T> p,
                                                      Chunk* chunks, Ctrl* ctrl, int cap_nodes, PushConst pc) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);

@@ -232,6 +232,27 @@ def test_mixed_vs_fp64_full_stage(Sim):
         s.close()
 
 
+@pytest.mark.parametrize("k", [0, 2, 4])
+def test_mixed_vs_fp64_complete_stage_wake_and_beam(Sim, k):
+    """A complete stage (workloads.surrogate_runs, 1600 x 96 cells, CK at c dt = dz/sqrt(2)): the pulse
+    crosses the whole plasma and the test beam rides the wake. Mixed against FP64 at the end: the beam's
+    energy gain and lab Lorentz factor within 1e-3 (measured 3e-7 - 2e-5), the wake E_z within 1e-3 in
+    relative L2 (measured 1e-5 - 5e-5)."""
+    r = W.surrogate_runs(8, seed=5)[k]
+    sims = {p: Sim(r, precision=p) for p in ("mixed", "fp64")}
+    for s in sims.values():
+        s.step(r["steps"])
+        s.sync()
+    sm, sd = sims["mixed"].stats(), sims["fp64"].stats()
+    assert sm["n_beam_active"] == sd["n_beam_active"] > 0
+    assert sm["beam_gamma_lab"] == pytest.approx(sd["beam_gamma_lab"], rel=1e-3)
+    gain_m, gain_d = sm["beam_gamma_lab"] - r["gamma_w"], sd["beam_gamma_lab"] - r["gamma_w"]
+    assert abs(gain_m - gain_d) <= 1e-3 * abs(gain_d)
+    assert rel(sims["mixed"].field(2), sims["fp64"].field(2)) <= 1e-3
+    for s in sims.values():
+        s.close()
+
+
 def test_autotune_times_layouts_and_caches(Sim, orc):
     from paper_1009_2727_gb300.pic import autotune
     w = W.shrink(W.stage_2d(), 256, 512)
