@@ -240,6 +240,15 @@ def run_ensemble(args):
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
     ens.sync()
+    # host time to enqueue one ensemble step on idle queues (does the host or the GPU set the pace?)
+    enq = []
+    for _ in range(5):
+        torch.cuda.synchronize()
+        th0 = time.perf_counter()
+        ens.step(1)
+        enq.append((time.perf_counter() - th0) * 1e3)
+    enqueue_ms = float(sorted(enq)[len(enq) // 2])
+    torch.cuda.synchronize()
     n1 = sum(m.stats()["n_electrons"] for m in ens.members)
     cells = sum(w["nx"] * w["nz"] for w in ws)
     # the same runs one at a time, each on the caller's stream
@@ -262,7 +271,8 @@ def run_ensemble(args):
             "higher_is_better": True, "dtype": "f32+f64pos", "data": "synthetic",
             "config": {"workload": f"ensemble_2d({args.ensemble}) seeded uneven runs", "runs": len(ws),
                        "cells": cells, "electrons": int(0.5 * (n0 + n1))},
-            "sequential_ms_per_step": seq_ms / args.steps, "speedup_vs_sequential": seq_ms / ms}
+            "sequential_ms_per_step": seq_ms / args.steps, "speedup_vs_sequential": seq_ms / ms,
+            "host_enqueue_ms_per_step": enqueue_ms}
     print(json.dumps(line), flush=True)
     return 0
 
