@@ -227,7 +227,10 @@ def run_ensemble(args):
     from paper_1009_2727_gb300.pic import Ensemble
     torch.cuda.set_device(0)
     ws = W.ensemble_2d(args.ensemble)
-    ens = Ensemble(ws)
+    t_tune = time.perf_counter()
+    ens = Ensemble(ws, tune=args.tune or False)
+    t_tune = time.perf_counter() - t_tune
+    ens_tuned = ens.tuned
     ens.step(max(args.warmup, 3))
     ens.sync()
     n0 = sum(m.stats()["n_electrons"] for m in ens.members)
@@ -255,8 +258,9 @@ def run_ensemble(args):
     seq_ms = 0.0
     ens.close()
     from paper_1009_2727_gb300.pic import Simulation
-    for w in ws:
-        s = Simulation(w)
+    for i, w in enumerate(ws):
+        lay = {"tile": ens_tuned[i]["tile"], "sort_every": ens_tuned[i]["sort_every"]} if args.tune else {}
+        s = Simulation(w, **lay)
         s.step(max(args.warmup, 3))
         torch.cuda.synchronize()
         ev0.record(stream)
@@ -272,7 +276,10 @@ def run_ensemble(args):
             "config": {"workload": f"ensemble_2d({args.ensemble}) seeded uneven runs", "runs": len(ws),
                        "cells": cells, "electrons": int(0.5 * (n0 + n1))},
             "sequential_ms_per_step": seq_ms / args.steps, "speedup_vs_sequential": seq_ms / ms,
-            "host_enqueue_ms_per_step": enqueue_ms}
+            "host_enqueue_ms_per_step": enqueue_ms,
+            "autotuned": args.tune or None, "setup_s": t_tune,
+            "ensemble_trials": ens_tuned[0].get("trials") if args.tune == "ensemble" else None,
+            "tiles": sorted({(t["tile"][0], t["tile"][1], t["sort_every"]) for t in ens_tuned}) if args.tune else None}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -384,6 +391,8 @@ def main():
     ap.add_argument("--sort-every", type=int, default=0, help="steps between particle sorts (0: the library default)")
     ap.add_argument("--ensemble", type=int, default=0,
                     help="time N uneven runs advanced together (pic_ensemble_*) instead of the stage")
+    ap.add_argument("--tune", default="", choices=["", "runs", "ensemble"],
+                    help="with --ensemble: layouts from pic_autotune per run, or from pic_ensemble_autotune")
     ap.add_argument("--surrogate", type=int, default=0,
                     help="label N stage runs, train the stage surrogate on them and time its serving")
     ap.add_argument("--dim", type=int, default=2, choices=[2, 3],

@@ -305,6 +305,14 @@ int pic_ensemble_sync(pic_ens* ens);
 int pic_ensemble_size(pic_ens* ens);
 pic_ctx* pic_ensemble_member(pic_ens* ens, int index);
 int pic_ensemble_free(pic_ens* ens);
+/* The particle tile and sort cadence for a whole ensemble: each candidate layout (tiles 8x32, 8x16, 16x16,
+ * 16x32, 32x32, 8x8 at cadence 32; 8x32 at cadences 16 and 64) is given to every run, the ensemble is
+ * created, stepped 4 times, then timed over `steps` ensemble steps on cuda_stream; out receives the
+ * fastest layout, its ms per ensemble step and every trial (ms < 0 for a failed one). The runs' own
+ * tile_x/tile_z/sort_every in cfgs are ignored. Errors: PIC_EINVAL, PIC_ECUDA (no candidate ran). */
+int pic_ensemble_autotune(int n, const pic_config* cfgs, const pic_plasma* plasmas, const pic_laser* lasers,
+                          int steps, pic_alloc_fn alloc, pic_free_fn free_fn, void* alloc_user, void* cuda_stream,
+                          pic_tune_result* out);
 
 /* ---- Multilayer perceptron for the stage surrogate (no counterpart in the paper) ----
  * widths[0] -> widths[1] -> ... -> widths[n_layers]; GELU (exact, erf form) after every layer but the

@@ -30,7 +30,7 @@ EXPORTS = ("pic_init", "pic_load_plasma", "pic_inject_laser", "pic_step", "pic_s
            "pic_get_particles_y", "pic_last_error",
            "pic_kernel_launches", "pic_kernel_timing", "pic_get_rho_noalloc", "pic_autotune",
            "pic_ensemble_create", "pic_ensemble_step", "pic_ensemble_sync", "pic_ensemble_size",
-           "pic_ensemble_member", "pic_ensemble_free",
+           "pic_ensemble_member", "pic_ensemble_free", "pic_ensemble_autotune",
            "pic_mlp_create", "pic_mlp_free", "pic_mlp_param_count", "pic_mlp_get_params", "pic_mlp_set_params",
            "pic_mlp_infer", "pic_mlp_grad", "pic_mlp_train", "pic_mlp_use_tensor_cores", "pic_mlp_status")
 NOALLOC_MAX_NZ = 16384
@@ -174,6 +174,9 @@ def load(build_if_missing: bool = True):
         L.pic_ensemble_member.argtypes = [vp, ctypes.c_int]
         L.pic_ensemble_member.restype = vp
         L.pic_ensemble_free.argtypes = [vp]
+        L.pic_ensemble_autotune.argtypes = [ctypes.c_int, ctypes.POINTER(PicConfig), ctypes.POINTER(PicPlasma),
+                                            ctypes.POINTER(PicLaser), ctypes.c_int, ALLOC_FN, FREE_FN, vp, vp,
+                                            ctypes.POINTER(PicTuneResult)]
         _F = ctypes.POINTER(ctypes.c_float)
         L.pic_mlp_create.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_uint64, ALLOC_FN, FREE_FN,
                                      vp, vp, ctypes.POINTER(vp)]

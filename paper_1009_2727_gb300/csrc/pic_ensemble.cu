@@ -74,22 +74,19 @@ int pic_ensemble_create(int n, const pic_config* cfgs, const pic_plasma* plasmas
 
 int pic_ensemble_step(pic_ens* e, int nsteps) {
   if (!e || nsteps < 0) return PIC_EINVAL;
-  // the runs start after the work already on the caller's stream, and the caller's
-  // stream waits for all of them at the end
-  if (e->caller) {
-    cudaEventRecord(e->start, e->caller);
-    for (cudaStream_t s : e->streams) cudaStreamWaitEvent(s, e->start, 0);
-  }
+  // the runs start after the work already on the caller's stream, and the caller's stream waits for all
+  // of them at the end (also when it is the legacy default stream, handle 0: the runs' streams are
+  // non-blocking and would not synchronise with it implicitly)
+  cudaEventRecord(e->start, e->caller);
+  for (cudaStream_t s : e->streams) cudaStreamWaitEvent(s, e->start, 0);
   for (int k = 0; k < nsteps; k++)
     for (pic_ctx* c : e->ctx) {
       const int r = pic_step(c, 1);
       if (r != PIC_OK) return r;
     }
-  if (e->caller) {
-    for (size_t i = 0; i < e->streams.size(); i++) {
-      cudaEventRecord(e->done[i], e->streams[i]);
-      cudaStreamWaitEvent(e->caller, e->done[i], 0);
-    }
+  for (size_t i = 0; i < e->streams.size(); i++) {
+    cudaEventRecord(e->done[i], e->streams[i]);
+    cudaStreamWaitEvent(e->caller, e->done[i], 0);
   }
   return cudaGetLastError() == cudaSuccess ? PIC_OK : PIC_ECUDA;
 }
@@ -109,6 +106,66 @@ int pic_ensemble_size(pic_ens* e) { return e ? (int)e->ctx.size() : 0; }
 pic_ctx* pic_ensemble_member(pic_ens* e, int i) {
   if (!e || i < 0 || i >= (int)e->ctx.size()) return nullptr;
   return e->ctx[i];
+}
+
+// Layout of the whole ensemble: the particle tile and sort cadence shared by all runs, chosen by timing
+// the ensemble itself (a layout that is fastest for one run alone on the GPU is not the fastest when the
+// runs share it: small tiles multiply the chunk windows every run stages).
+int pic_ensemble_autotune(int n, const pic_config* cfgs, const pic_plasma* plasmas, const pic_laser* lasers,
+                          int steps, pic_alloc_fn alloc, pic_free_fn free_fn, void* alloc_user, void* cuda_stream,
+                          pic_tune_result* out) {
+  if (!out || out->struct_size != sizeof(pic_tune_result) || n < 1 || !cfgs || !plasmas || steps < 1)
+    return PIC_EINVAL;
+  static const int cand[][3] = {{8, 32, 32}, {8, 16, 32}, {16, 16, 32}, {16, 32, 32},
+                                {32, 32, 32}, {8, 32, 16}, {8, 32, 64}, {8, 8, 32}};
+  const int ncand = (int)(sizeof(cand) / sizeof(cand[0]));
+  pic_tune_result r{};
+  r.struct_size = sizeof(pic_tune_result);
+  r.version = PIC_API_VERSION;
+  double best = -1.0;
+  std::vector<pic_config> c(cfgs, cfgs + n);
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return PIC_ECUDA;
+  for (int q = 0; q < ncand; q++) {
+    for (int i = 0; i < n; i++) {
+      c[i].tile_x = cand[q][0];
+      c[i].tile_z = cand[q][1];
+      c[i].sort_every = cand[q][2];
+    }
+    pic_ens* e = nullptr;
+    double ms = -1.0;
+    if (pic_ensemble_create(n, c.data(), plasmas, lasers, alloc, free_fn, alloc_user, cuda_stream, &e) == PIC_OK &&
+        pic_ensemble_step(e, 4) == PIC_OK && pic_ensemble_sync(e) == PIC_OK) {
+      cudaEventRecord(e0, st);
+      const int rr = pic_ensemble_step(e, steps);
+      cudaEventRecord(e1, st);
+      float t = 0.0f;
+      if (rr == PIC_OK && pic_ensemble_sync(e) == PIC_OK && cudaEventSynchronize(e1) == cudaSuccess &&
+          cudaEventElapsedTime(&t, e0, e1) == cudaSuccess)
+        ms = (double)t / steps;
+    }
+    pic_ensemble_free(e);
+    if (r.n_trials < PIC_TUNE_MAX_TRIALS) {
+      const int i = r.n_trials++;
+      r.trial_tile_x[i] = cand[q][0];
+      r.trial_tile_z[i] = cand[q][1];
+      r.trial_sort_every[i] = cand[q][2];
+      r.trial_ms[i] = ms;
+    }
+    if (ms > 0.0 && (best < 0.0 || ms < best)) {
+      best = ms;
+      r.tile_x = cand[q][0];
+      r.tile_z = cand[q][1];
+      r.sort_every = cand[q][2];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (best < 0.0) return PIC_ECUDA;
+  r.ms_per_step = best;
+  *out = r;
+  return PIC_OK;
 }
 
 int pic_ensemble_free(pic_ens* e) {

@@ -324,7 +324,10 @@ class Ensemble:
     """Independent runs of uneven size advanced together (pic_ensemble_*): each run has its own
     stream and the runs of one step execute concurrently."""
 
-    def __init__(self, ws: list, precision: str | None = None, stream=None):
+    def __init__(self, ws: list, precision: str | None = None, stream=None, tune=False):
+        """tune: False (each run's own configuration), "runs" (each run's tile and sort cadence from
+        pic_autotune, timed on that run alone) or "ensemble" (one layout for all runs from
+        pic_ensemble_autotune, timed on the ensemble itself)"""
         import torch
         if not torch.cuda.is_available():
             raise PicError("a CUDA device is required (the library has no CPU path)")
@@ -334,8 +337,36 @@ class Ensemble:
         n = len(ws)
         precs = [(precision or w.get("precision", "fp64")) for w in ws]
         self._keep = []
-        cfgs = (capi.PicConfig * n)(*[make_config(w, capi.PIC_FP64 if p == "fp64" else capi.PIC_MIXED)
-                                      for w, p in zip(ws, precs)])
+        self.tuned = []
+        layouts = [(None, 0)] * n
+        if tune == "runs" or tune is True:
+            for i, (w, p) in enumerate(zip(ws, precs)):
+                t = autotune(w, steps=8, precision=p, stream=st)
+                self.tuned.append(t)
+                layouts[i] = (t["tile"], t["sort_every"])
+        elif tune == "ensemble":
+            c0 = (capi.PicConfig * n)(*[make_config(w, capi.PIC_FP64 if p == "fp64" else capi.PIC_MIXED)
+                                        for w, p in zip(ws, precs)])
+            p0 = (capi.PicPlasma * n)(*[make_plasma(w.get("plasma"), w.get("beam"), self._keep) for w in ws])
+            l0 = (capi.PicLaser * n)()
+            for i, w in enumerate(ws):
+                if w.get("laser"):
+                    l0[i] = make_laser(w["laser"], int(w["nx"]), float(w["dx"]), int(w.get("ny", 0)),
+                                       float(w.get("dy", 0.0)))
+            acb, fcb = torch_allocator(self.device.index)
+            out = capi.PicTuneResult()
+            out.struct_size = ctypes.sizeof(capi.PicTuneResult)
+            r = self.L.pic_ensemble_autotune(n, c0, p0, l0, 8, acb, fcb, None, ctypes.c_void_p(st.cuda_stream),
+                                             ctypes.byref(out))
+            if r != 0:
+                raise PicError(f"pic_ensemble_autotune failed: {capi.STATUS_NAMES.get(r, r)}")
+            t = {"tile": (out.tile_x, out.tile_z), "sort_every": out.sort_every, "ms_per_step": out.ms_per_step,
+                 "trials": [((out.trial_tile_x[i], out.trial_tile_z[i]), out.trial_sort_every[i], out.trial_ms[i])
+                            for i in range(out.n_trials)]}
+            self.tuned = [t] * n
+            layouts = [(t["tile"], t["sort_every"])] * n
+        cfgs = (capi.PicConfig * n)(*[make_config(w, capi.PIC_FP64 if p == "fp64" else capi.PIC_MIXED, tl, se)
+                                      for w, p, (tl, se) in zip(ws, precs, layouts)])
         pls = (capi.PicPlasma * n)(*[make_plasma(w.get("plasma"), w.get("beam"), self._keep) for w in ws])
         las = (capi.PicLaser * n)()
         for i, w in enumerate(ws):
