@@ -67,6 +67,8 @@ typedef struct {
   int periodic_x, periodic_z; /* fields only (test option) */
   int moving_window;
   double window_beta;
+  int filter_strides[4];      /* > 0: the wide-band filter of Sec. 4.1, the product over these strides of
+                                 (n passes + compensation) at each stride, e.g. 1,2,3 for S(1:2:3); else 0 */
 } orc_config;
 
 typedef struct {
@@ -385,12 +387,17 @@ static void filter_pass_axis(orc_sim* s, int comp, double* F, int axis, int stri
   memcpy(F, out, sizeof(double) * s->ncell);
 }
 
+/* With a stride set (Sec. 4.1, wide-band filters combining strides): along each axis, for each stride
+ * of the set in turn, the n passes and the compensation pass at that stride. */
 static void filter_component(orc_sim* s, int comp, double* F) {
-  int n = s->c.filter_passes, st = s->c.filter_stride;
-  for (int axis = 0; axis < 2; axis++) {
-    for (int p = 0; p < n; p++) filter_pass_axis(s, comp, F, axis, st, 0.5);
-    if (s->c.filter_compensate) filter_pass_axis(s, comp, F, axis, st, 0.5 * n + 1.0);
-  }
+  int n = s->c.filter_passes;
+  int set[4] = { s->c.filter_stride, 0, 0, 0 };
+  if (s->c.filter_strides[0] > 0) for (int q = 0; q < 4; q++) set[q] = s->c.filter_strides[q];
+  for (int axis = 0; axis < 2; axis++)
+    for (int q = 0; q < 4 && set[q] > 0; q++) {
+      for (int p = 0; p < n; p++) filter_pass_axis(s, comp, F, axis, set[q], 0.5);
+      if (s->c.filter_compensate) filter_pass_axis(s, comp, F, axis, set[q], 0.5 * n + 1.0);
+    }
 }
 
 /* exported: apply the configured filter to a caller array of a component */
@@ -575,7 +582,12 @@ orc_sim* orc_create(const orc_config* cfg) {
   int g = cfg->particle_guard;
   if (g < 0) {
     int P = cfg->filter_passes + (cfg->filter_compensate ? 1 : 0);
-    g = (cfg->order == 3 ? 3 : 2) + P * cfg->filter_stride + 2;
+    int ssum = cfg->filter_stride;
+    if (cfg->filter_strides[0] > 0) {
+      ssum = 0;
+      for (int q = 0; q < 4 && cfg->filter_strides[q] > 0; q++) ssum += cfg->filter_strides[q];
+    }
+    g = (cfg->order == 3 ? 3 : 2) + P * ssum + 2;
   }
   s->c.particle_guard = g;
   int L = cfg->pml_cells > 0 ? cfg->pml_cells : 0;

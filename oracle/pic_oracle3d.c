@@ -57,6 +57,7 @@ typedef struct {
   int filter_passes, filter_stride, filter_compensate, filter_J, filter_gather;
   int order, particle_guard;
   int periodic_x, periodic_y, periodic_z;   /* fields only (test option) */
+  int filter_strides[4];      /* > 0: product over these strides of (n passes + compensation), Sec. 4.1 */
 } o3_config;
 
 typedef struct {
@@ -281,12 +282,17 @@ static void filter_pass_axis(o3_sim* s, int comp, double* F, int axis, int strid
   memcpy(F, out, sizeof(double) * s->ncell);
 }
 
+/* With a stride set (Sec. 4.1, wide-band filters combining strides): along each axis, for each stride
+ * of the set in turn, the n passes and the compensation pass at that stride. */
 static void filter_component(o3_sim* s, int comp, double* F) {
-  int n = s->c.filter_passes, st = s->c.filter_stride;
-  for (int axis = 0; axis < 3; axis++) {
-    for (int p = 0; p < n; p++) filter_pass_axis(s, comp, F, axis, st, 0.5);
-    if (s->c.filter_compensate) filter_pass_axis(s, comp, F, axis, st, 0.5 * n + 1.0);
-  }
+  int n = s->c.filter_passes;
+  int set[4] = { s->c.filter_stride, 0, 0, 0 };
+  if (s->c.filter_strides[0] > 0) for (int q = 0; q < 4; q++) set[q] = s->c.filter_strides[q];
+  for (int axis = 0; axis < 3; axis++)
+    for (int q = 0; q < 4 && set[q] > 0; q++) {
+      for (int p = 0; p < n; p++) filter_pass_axis(s, comp, F, axis, set[q], 0.5);
+      if (s->c.filter_compensate) filter_pass_axis(s, comp, F, axis, set[q], 0.5 * n + 1.0);
+    }
 }
 
 void o3_filter_field(o3_sim* s, int comp, double* F) { filter_component(s, comp, F); }
@@ -449,7 +455,12 @@ o3_sim* o3_create(const o3_config* cfg) {
   int g = cfg->particle_guard;
   if (g < 0) {
     int P = cfg->filter_passes + (cfg->filter_compensate ? 1 : 0);
-    g = (cfg->order == 3 ? 3 : 2) + P * cfg->filter_stride + 2;
+    int ssum = cfg->filter_stride;
+    if (cfg->filter_strides[0] > 0) {
+      ssum = 0;
+      for (int q = 0; q < 4 && cfg->filter_strides[q] > 0; q++) ssum += cfg->filter_strides[q];
+    }
+    g = (cfg->order == 3 ? 3 : 2) + P * ssum + 2;
   }
   s->c.particle_guard = g;
   int L = cfg->pml_cells > 0 ? cfg->pml_cells : 0;

@@ -213,3 +213,20 @@ def test_3d_gauss_law_full_step_with_antenna(orc):
     scale = QE * n_e / EPS0
     assert np.abs(div[sl]).max() > 1e-7 * scale       # the laser and the antenna did separate charge
     assert np.abs(G[sl]).max() < 1e-11 * scale
+
+
+def test_3d_wide_band_filter_gain(orc):
+    """S(1:2) in 3D: the gain of a periodic mode is the product over the three axes and both strides of
+    g(s, 1/2, k)^4 g(s, 3/2, k)"""
+    w = vacuum3(16, 12, 20, filter_passes=4, filter_compensate=1, filter_strides=[1, 2])
+    s = orc.Sim3(w)
+    m = (3, 2, 5)
+    k = [2 * np.pi * m[0] / 16, 2 * np.pi * m[1] / 12, 2 * np.pi * m[2] / 20]
+    i, j, l = np.meshgrid(np.arange(17), np.arange(13), np.arange(21), indexing="ij")
+    f = np.cos(k[0] * i + k[1] * j + k[2] * l + 0.4)
+
+    def G(st, kk):
+        return (0.5 + 0.5 * np.cos(st * kk)) ** 4 * (3 - 2 * np.cos(st * kk))
+    gain = np.prod([G(st, kk) for st in (1, 2) for kk in k])
+    got = s.filter_field(1, f)[:16, :12, :20]
+    assert np.abs(got - gain * f[:16, :12, :20]).max() < 1e-13
