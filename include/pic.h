@@ -84,7 +84,8 @@ typedef struct {
   double pml_power;       /* profile exponent n (paper: 2) */
   int32_t pml_xi_exp;     /* 1: xi = exp(-sigma dt); 0: (1 - sigma dt/2)/(1 + sigma dt/2) */
   int32_t filter_passes;  /* bilinear passes per axis (Eq. 3ptfilter, alpha = 1/2); passes plus the
-                             compensation pass <= 16 and (that count) x stride <= 32, else PIC_EINVAL */
+                             compensation pass <= 16 and the halo (that count) x (stride, or the sum of
+                             filter_stride_set) <= 40, else PIC_EINVAL */
   int32_t filter_stride;  /* stride s (Eq. 3ptfilter_stride) */
   int32_t filter_compensate; /* 1: one extra pass with alpha_c = n/2 + 1 */
   int32_t filter_J;       /* filter the deposited current */
@@ -99,7 +100,10 @@ typedef struct {
   int32_t ny;             /* 3D: cells along y (the PML occupies pml_cells on each side) */
   int32_t reserved0;
   double dy;              /* 3D: transverse cell along y [m] */
-  int32_t reserved[4];
+  int32_t filter_stride_set[4]; /* wide-band filter (Sec. 4.1): along each axis the passes (and the
+                                   compensation pass) are applied at each of these strides in turn, e.g.
+                                   {1, 2, 3, 0}; 0-terminated, all zero = the single filter_stride;
+                                   a negative entry or a stride after a 0 is PIC_EINVAL */
 } pic_config;
 
 /* Cold plasma fixed in the lab (Sec. 3.1.1), on a regular lattice, entering the

@@ -54,7 +54,7 @@ class PicConfig(ctypes.Structure):
         ("moving_window", ctypes.c_int32), ("window_beta", ctypes.c_double),
         ("tile_x", ctypes.c_int32), ("tile_z", ctypes.c_int32), ("sort_every", ctypes.c_int32),
         ("ny", ctypes.c_int32), ("reserved0", ctypes.c_int32), ("dy", ctypes.c_double),
-        ("reserved", ctypes.c_int32 * 4),
+        ("filter_stride_set", ctypes.c_int32 * 4),
     ]
 
 

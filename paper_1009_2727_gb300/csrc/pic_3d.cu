@@ -91,7 +91,7 @@ struct Pml3 {
 
 template <class T>
 struct Taps3 {
-  T c[33];
+  T c[2 * FILTER_HMAX + 1];
   int P, s;
 };
 
@@ -1296,8 +1296,13 @@ struct Sim3 : Sim3Api {
     if (!(g.dt > 0.0)) return fail(PIC_EINVAL, "dt <= 0");
     if (g.dt > dt_cfl * (1.0 + 1e-12)) return fail(PIC_ECFL, "dt above the 3D stability limit");
     P = c->filter_passes + (c->filter_compensate ? 1 : 0);
-    const int guard = c->particle_guard >= 0 ? c->particle_guard : (c->shape_order == 3 ? 3 : 2) + P * c->filter_stride + 2;
-    if (guard < (c->shape_order == 3 ? 3 : 2) + P * c->filter_stride + 1) return fail(PIC_EINVAL, "particle guard too small");
+    FilterSpec fs{};
+    fs.passes = c->filter_passes; fs.stride = c->filter_stride; fs.compensate = c->filter_compensate;
+    for (int q = 0; q < 4; q++) fs.strides[q] = c->filter_stride_set[q];
+    const int H = filter_halo(fs);
+    if (H > FILTER_HMAX) return fail(PIC_EINVAL, "filter halo too wide");
+    const int guard = c->particle_guard >= 0 ? c->particle_guard : (c->shape_order == 3 ? 3 : 2) + H + 2;
+    if (guard < (c->shape_order == 3 ? 3 : 2) + H + 1) return fail(PIC_EINVAL, "particle guard too small");
     for (int a = 0; a < 3; a++) {
       g.lo[a] = c->pml_cells + guard;
       g.hi[a] = g.n[a] - c->pml_cells - guard;
@@ -1338,22 +1343,29 @@ struct Sim3 : Sim3Api {
         pm.sg[a][h] = d_s; pm.xi[a][h] = d_x; pm.cf[a][h] = d_c;
       }
     }
-    // composed filter taps along one axis: P passes of (1-a)/2, a, (1-a)/2 at stride s
-    std::vector<double> t(2 * P + 1, 0.0);
-    t[P] = 1.0;
-    for (int q = 0; q < P; q++) {
-      const double al = q < c->filter_passes ? 0.5 : 0.5 * c->filter_passes + 1.0;
-      std::vector<double> o(2 * P + 1, 0.0);
-      for (int m = 0; m <= 2 * P; m++) {
-        o[m] += al * t[m];
-        if (m > 0) o[m] += 0.5 * (1.0 - al) * t[m - 1];
-        if (m < 2 * P) o[m] += 0.5 * (1.0 - al) * t[m + 1];
+    // composed filter taps along one axis: P passes of (1-a)/2, a, (1-a)/2 at stride s; a wide-band filter
+    // (the passes repeated at each stride of a set) is composed densely over offsets -H..H (stride 1)
+    const bool wide = fs.strides[0] > 0;
+    const int R = wide ? H : P;
+    std::vector<double> t(2 * R + 1, 0.0);
+    t[R] = 1.0;
+    for (int q = 0; q < (wide ? 4 : 1); q++) {
+      const int st = wide ? fs.strides[q] : 1;
+      if (st <= 0) break;
+      for (int p = 0; p < P; p++) {
+        const double al = p < c->filter_passes ? 0.5 : 0.5 * c->filter_passes + 1.0;
+        std::vector<double> o(2 * R + 1, 0.0);
+        for (int m = 0; m <= 2 * R; m++) {
+          o[m] += al * t[m];
+          if (m - st >= 0) o[m] += 0.5 * (1.0 - al) * t[m - st];
+          if (m + st <= 2 * R) o[m] += 0.5 * (1.0 - al) * t[m + st];
+        }
+        t = o;
       }
-      t = o;
     }
-    for (int m = 0; m < 33; m++) taps.c[m] = m <= 2 * P ? T(t[m]) : T(0);
-    taps.P = P;
-    taps.s = c->filter_stride;
+    for (int m = 0; m < 2 * FILTER_HMAX + 1; m++) taps.c[m] = m <= 2 * R ? T(t[m]) : T(0);
+    taps.P = R;
+    taps.s = wide ? 1 : c->filter_stride;
     tl.nt[0] = (g.n[0] + TX - 1) / TX;
     tl.nt[1] = (g.n[1] + TY - 1) / TY;
     tl.nt[2] = (g.n[2] + TZ - 1) / TZ;

@@ -179,6 +179,7 @@ struct Sim : SimBase {
     filt_gather = cf.filter_gather && cf.filter_passes + cf.filter_compensate > 0;
     filt_J = cf.filter_J && cf.filter_passes + cf.filter_compensate > 0;
     fs.passes = cf.filter_passes; fs.stride = cf.filter_stride; fs.compensate = cf.filter_compensate;
+    for (int q = 0; q < 4; q++) fs.strides[q] = cf.filter_stride_set[q];
     const size_t N = (size_t)(cf.nx + 1) * g.ld;
     g.cs = (long)N;
     auto grid = [&]() { return al<T>(N); };
@@ -246,7 +247,7 @@ struct Sim : SimBase {
     stats_buf = al<double>(8);
     {
       const int P = cf.filter_passes + (cf.filter_compensate ? 1 : 0);
-      const int H = (filt_gather || filt_J) ? P * cf.filter_stride : 0;
+      const int H = (filt_gather || filt_J) ? filter_halo(fs) : 0;
       if (!make_tile_maps<T>(g, f, H, tmaps)) return c->fail(PIC_ECUDA, "TMA descriptor encoding failed");
     }
     stage_n = (size_t)nx1 * nz1;
@@ -898,6 +899,16 @@ int pic_init(const pic_config* cfg, pic_alloc_fn alloc, pic_free_fn free_fn, voi
   *out = nullptr;
   if (!cfg || cfg->struct_size != sizeof(pic_config) || cfg->version != PIC_API_VERSION) return PIC_EINVAL;
   if (cfg->dim != 2 && cfg->dim != 3) return PIC_EINVAL;
+  // the composed filter: at most 16 passes per stride and a halo of at most FILTER_HMAX cells; a stride set
+  // is non-negative and 0-terminated
+  FilterSpec fs0{};
+  fs0.passes = cfg->filter_passes; fs0.stride = cfg->filter_stride; fs0.compensate = cfg->filter_compensate;
+  for (int q = 0; q < 4; q++) {
+    fs0.strides[q] = cfg->filter_stride_set[q];
+    if (fs0.strides[q] < 0 || (q > 0 && fs0.strides[q] > 0 && fs0.strides[q - 1] <= 0)) return PIC_EINVAL;
+  }
+  const int Hf = filter_halo(fs0);
+  if (cfg->filter_passes + (cfg->filter_compensate ? 1 : 0) > 16 || Hf > FILTER_HMAX) return PIC_EINVAL;
   if (cfg->dim == 3) {
     if (cfg->nx < 8 || cfg->nz < 8 || !(cfg->dx > 0) || !(cfg->dz_lab > 0)) return PIC_EINVAL;
     if (cfg->shape_order != 1 && cfg->shape_order != 3) return PIC_EINVAL;
@@ -905,7 +916,6 @@ int pic_init(const pic_config* cfg, pic_alloc_fn alloc, pic_free_fn free_fn, voi
     if (std::fabs(cfg->ck_alpha + 4 * cfg->ck_beta + 4 * cfg->ck_gamma - 1.0) > 1e-12) return PIC_EINVAL;
     if (cfg->theta < 0 || cfg->theta > 1) return PIC_EINVAL;
     if (cfg->filter_passes < 0 || cfg->filter_stride < 1 || cfg->pml_cells < 0) return PIC_EINVAL;
-    if (cfg->filter_passes + (cfg->filter_compensate ? 1 : 0) > 16) return PIC_EINVAL;
     std::unique_ptr<pic_ctx> c(new pic_ctx());
     c->cfg = *cfg;
     c->stream = (cudaStream_t)cuda_stream;
@@ -923,10 +933,6 @@ int pic_init(const pic_config* cfg, pic_alloc_fn alloc, pic_free_fn free_fn, voi
   if (std::fabs(cfg->ck_alpha + 4 * cfg->ck_beta + 4 * cfg->ck_gamma - 1.0) > 1e-12) return PIC_EINVAL;
   if (cfg->theta < 0 || cfg->theta > 1) return PIC_EINVAL;
   if (cfg->filter_passes < 0 || cfg->filter_stride < 1 || cfg->pml_cells < 0) return PIC_EINVAL;
-  // the composed filter has at most 33 taps and a halo of at most 32 cells (staged tile in shared memory)
-  if (cfg->filter_passes + (cfg->filter_compensate ? 1 : 0) > 16 ||
-      (cfg->filter_passes + (cfg->filter_compensate ? 1 : 0)) * cfg->filter_stride > 32)
-    return PIC_EINVAL;
   std::unique_ptr<pic_ctx> c(new pic_ctx());
   c->cfg = *cfg;
   c->stream = (cudaStream_t)cuda_stream;
@@ -942,10 +948,9 @@ int pic_init(const pic_config* cfg, pic_alloc_fn alloc, pic_free_fn free_fn, voi
   h.dt = cfg->dt > 0.0 ? cfg->dt : cfg->courant * h.dt_cfl;
   if (!(h.dt > 0.0)) return PIC_EINVAL;
   if (h.dt > h.dt_cfl * (1.0 + 1e-12)) return PIC_ECFL;
-  const int P = cfg->filter_passes + (cfg->filter_compensate ? 1 : 0);
-  h.guard = cfg->particle_guard >= 0 ? cfg->particle_guard : (cfg->shape_order == 3 ? 3 : 2) + P * cfg->filter_stride + 2;
+  h.guard = cfg->particle_guard >= 0 ? cfg->particle_guard : (cfg->shape_order == 3 ? 3 : 2) + Hf + 2;
   // particles must not read filtered fields, nor deposit current, within reach of the walls (PR-10)
-  if (h.guard < (cfg->shape_order == 3 ? 3 : 2) + P * cfg->filter_stride + 1) return PIC_EINVAL;
+  if (h.guard < (cfg->shape_order == 3 ? 3 : 2) + Hf + 1) return PIC_EINVAL;
   const int L = cfg->pml_cells;
   h.gx_lo = L + h.guard; h.gx_hi = cfg->nx - L - h.guard;
   h.gz_lo = L + h.guard; h.gz_hi = cfg->nz - L - h.guard;

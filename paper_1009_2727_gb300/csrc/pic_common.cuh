@@ -80,12 +80,26 @@ struct FieldPtrs {
 
 struct FilterSpec {
   int passes, stride, compensate;
+  int strides[4];   // wide-band filter: the passes repeated at each of these strides (0-terminated); else none
 };
 
-// composed taps of the multi-pass filter along one axis: c[j] at offset (j - P) * s, j = 0..2P
+// total halo of the filter along one axis: (passes + compensation) times the sum of its strides
+inline int filter_halo(const FilterSpec& fs) {
+  const int P = fs.passes + (fs.compensate ? 1 : 0);
+  int ss = fs.stride;
+  if (fs.strides[0] > 0) {
+    ss = 0;
+    for (int q = 0; q < 4 && fs.strides[q] > 0; q++) ss += fs.strides[q];
+  }
+  return P * ss;
+}
+constexpr int FILTER_HMAX = 40;
+
+// composed taps of the multi-pass filter along one axis: c[j] at offset (j - P) * s, j = 0..2P (a wide-band
+// filter is stored densely: s = 1, P = H)
 template <class T>
 struct FilterTaps {
-  T c[33];
+  T c[2 * FILTER_HMAX + 1];
   int P, s, H;
 };
 

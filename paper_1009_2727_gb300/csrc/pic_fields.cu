@@ -469,28 +469,54 @@ static size_t tile_smem(const TileMaps& tm, int H) {
 
 template <class T>
 static FilterTaps<T> make_taps(const FilterSpec& fs) {
-  // compose n bilinear passes (alpha = 1/2) and the compensation pass (alpha_c = n/2 + 1)
-  double k[2 * 16 + 1] = {0.0};
-  int len = 1;
-  k[0] = 1.0;
+  // compose n bilinear passes (alpha = 1/2) and the compensation pass (alpha_c = n/2 + 1) at one stride, or,
+  // for a wide-band filter, at each stride of the set in turn, into one tap array
   const int P = fs.passes + (fs.compensate ? 1 : 0);
-  for (int p = 0; p < P; p++) {
-    const double al = p < fs.passes ? 0.5 : 0.5 * fs.passes + 1.0;
-    const double be = 0.5 * (1.0 - al);
-    double r[2 * 16 + 1] = {0.0};
-    for (int j = 0; j < len; j++) {
-      r[j] += be * k[j];
-      r[j + 1] += al * k[j];
-      r[j + 2] += be * k[j];
-    }
-    len += 2;
-    for (int j = 0; j < len; j++) k[j] = r[j];
-  }
   FilterTaps<T> ft;
-  ft.P = P;
-  ft.s = fs.stride;
-  ft.H = P * fs.stride;
-  for (int j = 0; j < 2 * 16 + 1; j++) ft.c[j] = T(j < len ? k[j] : 0.0);
+  if (fs.strides[0] <= 0) {
+    double k[2 * FILTER_HMAX + 1] = {0.0};
+    int len = 1;
+    k[0] = 1.0;
+    for (int p = 0; p < P; p++) {
+      const double al = p < fs.passes ? 0.5 : 0.5 * fs.passes + 1.0;
+      const double be = 0.5 * (1.0 - al);
+      double r[2 * FILTER_HMAX + 1] = {0.0};
+      for (int j = 0; j < len; j++) {
+        r[j] += be * k[j];
+        r[j + 1] += al * k[j];
+        r[j + 2] += be * k[j];
+      }
+      len += 2;
+      for (int j = 0; j < len; j++) k[j] = r[j];
+    }
+    ft.P = P;
+    ft.s = fs.stride;
+    ft.H = P * fs.stride;
+    for (int j = 0; j < 2 * FILTER_HMAX + 1; j++) ft.c[j] = T(j < len ? k[j] : 0.0);
+    return ft;
+  }
+  const int H = filter_halo(fs);
+  double k[2 * FILTER_HMAX + 1] = {0.0};   // offsets -H..H
+  k[H] = 1.0;
+  for (int q = 0; q < 4 && fs.strides[q] > 0; q++) {
+    const int st = fs.strides[q];
+    for (int p = 0; p < P; p++) {
+      const double al = p < fs.passes ? 0.5 : 0.5 * fs.passes + 1.0;
+      const double be = 0.5 * (1.0 - al);
+      double r[2 * FILTER_HMAX + 1] = {0.0};
+      for (int j = 0; j <= 2 * H; j++) {
+        if (k[j] == 0.0) continue;
+        r[j] += al * k[j];
+        if (j - st >= 0) r[j - st] += be * k[j];
+        if (j + st <= 2 * H) r[j + st] += be * k[j];
+      }
+      for (int j = 0; j <= 2 * H; j++) k[j] = r[j];
+    }
+  }
+  ft.P = H;
+  ft.s = 1;
+  ft.H = H;
+  for (int j = 0; j < 2 * FILTER_HMAX + 1; j++) ft.c[j] = T(j <= 2 * H ? k[j] : 0.0);
   return ft;
 }
 

@@ -161,6 +161,19 @@ def test_3d_beam_and_lab_samples_fp64(Sim, orc):
         assert st["beam_gamma_lab"] == pytest.approx(dg["gamma_lab"], rel=1e-12)
 
 
+def test_3d_wide_band_filter_strides_fp64(Sim, orc):
+    """wide-band filter (Sec. 4.1): one pass and the compensation pass at strides 1 and 2 along each axis"""
+    w = W.shrink3(W.parity_3d(), 40, 40, 64)
+    w.update(filter_passes=1, filter_compensate=1, filter_strides=[1, 2])
+    g = Sim(w, precision="fp64")
+    o = orc.Sim3(w)
+    g.step(40)
+    o.step(40)
+    g.sync()
+    check_fields(g, o, TOL64)
+    check_particles(g, o, TOL64)
+
+
 def test_3d_mixed_vs_oracle(Sim, orc):
     w = case()
     g = Sim(w, precision="mixed")

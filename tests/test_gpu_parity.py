@@ -137,6 +137,17 @@ def test_parity_stage_physics_small_box_fp64(Sim, orc):
     assert g.stats()["trap_gamma_lab"] == pytest.approx(2.0 * (2.0 * np.pi * c / w["laser"]["lambda0"]) / wp, rel=1e-12)
 
 
+def test_wide_band_filter_strides_fp64(Sim, orc):
+    """wide-band filter (Sec. 4.1): two passes and the compensation pass at each of the strides 1, 2 and 3,
+    on J and on the gathered fields, over the stage workload's numerics (halo 18 cells per axis)"""
+    w = W.shrink(W.stage_2d(), 128, 320, filter_passes=2, filter_compensate=1, filter_strides=[1, 2, 3])
+    w["precision"] = "fp64"
+    w["plasma"]["z_start_lab"] = 0.0
+    g, o = run_pair(Sim, orc, w, 40)
+    check_fields(g, o, TOL64)
+    check_particles(g, o, TOL64)
+
+
 def test_parity_2d_mixed(Sim, orc):
     w = W.shrink(W.parity_2d(), 48, 160)
     g, o = run_pair(Sim, orc, w, 40, precision="mixed")
