@@ -136,7 +136,9 @@ typedef struct {
 typedef struct {
   uint32_t struct_size, version;
   double lambda0, a0, w0, tau_fwhm, t_peak, x_center, phase;
-  double z_antenna;       /* antenna position in the computational frame at t' = 0 [m] */
+  double z_antenna;       /* antenna position in the computational frame at t' = 0 [m]; the antenna
+                             emits only while it lies inside the particle domain (past the PML and the
+                             particle guard, whose default width grows with the filter's halo) */
   double beta_s;          /* antenna-plane velocity / c in the computational frame */
   double y_center;        /* 3D: laser axis position along y [m] */
   int32_t reserved[6];

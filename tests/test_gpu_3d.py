@@ -162,14 +162,20 @@ def test_3d_beam_and_lab_samples_fp64(Sim, orc):
 
 
 def test_3d_wide_band_filter_strides_fp64(Sim, orc):
-    """wide-band filter (Sec. 4.1): one pass and the compensation pass at strides 1 and 2 along each axis"""
-    w = W.shrink3(W.parity_3d(), 40, 40, 64)
+    """wide-band filter (Sec. 4.1): one pass and the compensation pass at strides 1 and 2 along each axis
+    (halo 6, default guard 11); the antenna and the plasma edge sit inside the wider particle domain"""
+    w = W.shrink3(W.parity_3d(), 40, 40, 80)
     w.update(filter_passes=1, filter_compensate=1, filter_strides=[1, 2])
+    dzb = 0.4949e-6
+    w["laser"]["z_antenna"] = 17 * dzb
+    w["plasma"]["z_start_lab"] = 5.0 * 25 * dzb
     g = Sim(w, precision="fp64")
     o = orc.Sim3(w)
     g.step(40)
     o.step(40)
     g.sync()
+    assert o.info()["guard"] == 11
+    assert np.abs(o.field(1)).max() > 1e10
     check_fields(g, o, TOL64)
     check_particles(g, o, TOL64)
 
