@@ -377,6 +377,21 @@ def run_surrogate(args):
     return 0
 
 
+def wide_band(w, strides, three):
+    """the stage with a wide-band filter (its passes + compensation at each stride); the default particle
+    guard grows with the halo, so the antenna moves to 4 cells inside the particle domain"""
+    w = dict(w)
+    w["filter_strides"] = strides
+    w["laser"] = dict(w["laser"])
+    gam = w["gamma_boost"]
+    dz = (1.0 + (1.0 - 1.0 / gam ** 2) ** 0.5) * gam * w["dz_lab"]
+    halo = (w["filter_passes"] + (1 if w["filter_compensate"] else 0)) * sum(strides)
+    guard = (3 if w["order"] == 3 else 2) + halo + 2
+    w["laser"]["z_antenna"] = max(w["laser"]["z_antenna"], (w["pml_cells"] + guard + 4) * dz)
+    w["name"] = w["name"] + "_S(" + ":".join(str(v) for v in strides) + ")"
+    return w
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -397,6 +412,9 @@ def main():
                     help="label N stage runs, train the stage surrogate on them and time its serving")
     ap.add_argument("--dim", type=int, default=2, choices=[2, 3],
                     help="3: the 3D stage (1024 x 128 x 128 cells, gamma 30) instead of the 2D one")
+    ap.add_argument("--filter-strides", default="",
+                    help="wide-band filter, e.g. 1,2,4: the stage's passes + compensation at each stride "
+                         "(the antenna moves past the wider particle guard)")
     args = ap.parse_args()
 
     from paper_1009_2727_gb300 import workloads as W
@@ -406,6 +424,8 @@ def main():
         w = W.shrink3(w, w["nx"], w["ny"], args.nz) if three else W.shrink(w, w["nx"], args.nz)
     w["order"] = args.order
     w["precision"] = args.precision
+    if args.filter_strides:
+        w = wide_band(w, [int(v) for v in args.filter_strides.split(",")], three)
     if args.impl == "reference":
         return run_reference(args, w)
     if args.ensemble:
@@ -451,6 +471,11 @@ def main():
     launches = sim.launches() - l0
     ms = ev0.elapsed_time(ev1)
     push_ms, push_n = sim.timing(False)
+    # field kernels (Faraday, filters, Ampere) over a shorter run after the timed region
+    kf = max(min(args.steps, 50), 1)
+    sim.timing(True, 1)
+    sim.step(kf)
+    field_ms, _ = sim.timing(False)
     sim.sync()
     n_e1 = sim.stats()["n_electrons"]
     n_avg = 0.5 * (n_e + n_e1)
@@ -473,6 +498,7 @@ def main():
                      "(ncu: 65% issue slots, 59% L1/shared, 19% DRAM), not by HBM"),
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback",
             "algorithmic_bytes_per_particle": bpp, "push_ms_per_step": push_avg_ms,
+            "field_kernels_ms_per_step": field_ms / kf,
             "share_of_step": push_avg_ms / (ms / args.steps)}
     sim.close()
     del sim
@@ -507,7 +533,10 @@ def main():
             "config": {"workload": w["name"],
                        "grid": [w["nz"], w["ny"], w["nx"]] if three else [w["nz"], w["nx"]],
                        "ppc": 2 if three else 16, "gamma_boost": w["gamma_boost"],
-                       "solver": "CK2" if three else "CK", "theta": w["theta"], "filter": "4 passes + compensation",
+                       "solver": "CK2" if three else "CK", "theta": w["theta"],
+                       "filter": "4 passes + compensation" + (
+                           " at each stride of S(" + ":".join(str(v) for v in w["filter_strides"]) + ")"
+                           if w.get("filter_strides") else ""),
                        "shape_order": args.order, "precision": args.precision, "electrons": int(n_avg),
                        "cell_steps_per_s": w["nx"] * w.get("ny", 1) * w["nz"] * args.steps * ws / (ms_max * 1e-3),
                        "l2": "inputs larger than L2 (particle arrays ~0.5 GB, fields ~2.6 GB)" if three else

@@ -37,6 +37,7 @@ struct G3 {
   int ldz;         // padded z extent of every array
   long cs;         // elements per component array
   double d[3];     // cell sizes
+  double id[3];    // their inverses (host division, so the sweeps run no FP64 divide)
   double dt;
   int lo[3], hi[3];  // particle domain [cells]
 };
@@ -44,6 +45,8 @@ struct G3 {
 __host__ __device__ inline long nid(const G3& g, int i, int j, int k) {
   return ((long)i * (g.n[1] + 1) + j) * g.ldz + k;
 }
+
+inline unsigned nblk(long n, int b) { return (unsigned)((n + b - 1) / b); }
 
 // valid index range of component c (0..5: E then B; J uses E) along an axis: half-staggered 0..n-1,
 // integer 1..n-1 for E (tangential E vanishes on the PEC walls) and 0..n for B
@@ -87,6 +90,13 @@ struct Pml3 {
   const T* sg[3][2];   // sigma [axis][half]
   const T* xi[3][2];
   const T* cf[3][2];   // (1 - xi)/sigma, dt where sigma = 0
+  T id[3];             // inverse cell sizes in the path's type (no FP64 conversion in the sweeps)
+};
+
+// current per unit weight of the push, -q d_a/(d_x d_y d_z dt) per axis, computed on the host
+template <class T>
+struct Cq3 {
+  T v[3];
 };
 
 template <class T>
@@ -97,93 +107,90 @@ struct Taps3 {
 
 // ---------------------------------------------------------------------------
 // fields
-template <class T>
-__global__ void k3_eeff(long n, const T* E, const T* Ep, const T* Eb, T* Ee, T c1, T c2, T c3) {
-  const long p = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p < n) Ee[p] = c1 * E[p] - c2 * Ep[p] + c3 * Eb[p];
-}
+// Faraday with the enlarged operator, Friedman's E_eff and the split PML for B (PR-1, PR-2), over a tile
+// of FX x FY x FZ nodes. E_eff = c1 E^n - c2 E^{n-1} + c3 E-bar^{n-2} is formed while the tile and a
+// one-node halo are staged in shared memory (zero off the grid); each thread then updates the three B
+// components of FX nodes along x.
+//   Delta*_a F at a node (result half a cell above along a) = (alpha D(0,0) + beta (four axial neighbours)
+//   + gamma (four diagonal neighbours)) / d_a, D the difference along a on the transverse offsets.
+constexpr int FX = 4, FY = 8, FZ = 32;
+// z nodes per thread of the other grid sweeps (a block width apart)
+constexpr int KPT = 4;
 
-// Delta*_a F at node (i,j,k) (result half a cell above along a): alpha D(0,0) + beta (four axial
-// neighbours) + gamma (four diagonal neighbours), D the difference along a on the transverse offsets.
-// IN: the node and its stencil are inside the array (no bounds checks).
-template <class T, bool IN>
-__device__ __forceinline__ T dstar3(const G3& g, const T* F, int a, int i, int j, int k, T ca, T cb, T cg, T inv_d) {
+template <class T>
+__device__ __forceinline__ T dstar_s(const T* S, int a, int c0, T ca, T cb, T cg, T inv_d) {
+  constexpr int SY = FY + 2, SZ = FZ + 2;
+  constexpr int st[3] = {SY * SZ, SZ, 1};
   const int b = a == 0 ? 1 : 0, c = a == 2 ? 1 : 2;
-  const long sx = (long)(g.n[1] + 1) * g.ldz, sy = g.ldz;
-  const long st[3] = {sx, sy, 1};
-  const long p = nid(g, i, j, k);
   T D[3][3];
 #pragma unroll
   for (int o1 = -1; o1 <= 1; o1++)
 #pragma unroll
     for (int o2 = -1; o2 <= 1; o2++) {
-      if (IN) {
-        const long q = p + o1 * st[b] + o2 * st[c];
-        D[o1 + 1][o2 + 1] = F[q + st[a]] - F[q];
-      } else {
-        const int pi = i + (b == 0 ? o1 : 0) + (c == 0 ? o2 : 0);
-        const int pj = j + (b == 1 ? o1 : 0) + (c == 1 ? o2 : 0);
-        const int pk = k + (b == 2 ? o1 : 0) + (c == 2 ? o2 : 0);
-        D[o1 + 1][o2 + 1] = rd3(g, F, pi + (a == 0), pj + (a == 1), pk + (a == 2)) - rd3(g, F, pi, pj, pk);
-      }
+      const int q = c0 + o1 * st[b] + o2 * st[c];
+      D[o1 + 1][o2 + 1] = S[q + st[a]] - S[q];
     }
   const T s1 = D[0][1] + D[2][1] + D[1][0] + D[1][2];
   const T s2 = D[0][0] + D[0][2] + D[2][0] + D[2][2];
   return (ca * D[1][1] + cb * s1 + cg * s2) * inv_d;
 }
 
-// z nodes per thread of the grid sweeps (a block width apart)
-constexpr int KPT = 4;
-
 template <class T>
-__device__ __forceinline__ void faraday_node(const G3& g, const Pml3<T>& pm, const T* Ee, T* B, T* Bs, T* fB, T ca, T cb,
-                                             T cg, T dtT, int i, int j, int k) {
-  const long p = nid(g, i, j, k);
-  const int idx[3] = {i, j, k};
-  const bool in = i >= 1 && i < g.n[0] && j >= 1 && j < g.n[1] && k >= 1 && k < g.n[2];
+__global__ void __launch_bounds__(256) k3_faraday_tile(G3 g, Pml3<T> pm, const T* __restrict__ E,
+                                                       const T* __restrict__ Ep, const T* __restrict__ Eb, T* B, T* Bs,
+                                                       T* fB, T c1, T c2, T c3, T ca, T cb, T cg, T dtT) {
+  constexpr int SX = FX + 2, SY = FY + 2, SZ = FZ + 2, SN = SX * SY * SZ;
+  __shared__ T se[3][SN];   // index (x * SY + y) * SZ + z, tile origin at (1, 1, 1)
+  const int i0 = blockIdx.z * FX, j0 = blockIdx.y * FY, k0 = blockIdx.x * FZ;
+  const int tid = threadIdx.y * FZ + threadIdx.x;
+  for (int e = tid; e < SN; e += FZ * FY) {
+    const int lz = e % SZ, r = e / SZ, ly = r % SY, lx = r / SY;
+    const int i = i0 - 1 + lx, j = j0 - 1 + ly, k = k0 - 1 + lz;
+    if (i >= 0 && i <= g.n[0] && j >= 0 && j <= g.n[1] && k >= 0 && k <= g.n[2]) {
+      const long p = nid(g, i, j, k);
 #pragma unroll
-  for (int q = 0; q < 3; q++) {
-    const T old = B[q * g.cs + p];
-    T nw = old;
-    // every B component is valid on the interior nodes
-    if (in || in_valid(3 + q, g, i, j, k)) {
-      const int u = (q + 1) % 3, v = (q + 2) % 3;
-      T du, dv;
-      if (in) {
-        du = dstar3<T, true>(g, Ee + v * g.cs, u, i, j, k, ca, cb, cg, T(1.0 / g.d[u]));
-        dv = dstar3<T, true>(g, Ee + u * g.cs, v, i, j, k, ca, cb, cg, T(1.0 / g.d[v]));
-      } else {
-        du = dstar3<T, false>(g, Ee + v * g.cs, u, i, j, k, ca, cb, cg, T(1.0 / g.d[u]));
-        dv = dstar3<T, false>(g, Ee + u * g.cs, v, i, j, k, ca, cb, cg, T(1.0 / g.d[v]));
-      }
-      const T su = pm.sg[u][1][idx[u]], sv = pm.sg[v][1][idx[v]];
-      if (su > T(0) || sv > T(0)) {
-        T* Pu = Bs + (2 * q) * g.cs;
-        T* Pv = Bs + (2 * q + 1) * g.cs;
-        const T a = pm.xi[u][1][idx[u]] * Pu[p] - pm.cf[u][1][idx[u]] * du;
-        const T b = pm.xi[v][1][idx[v]] * Pv[p] + pm.cf[v][1][idx[v]] * dv;
-        Pu[p] = a;
-        Pv[p] = b;
-        nw = a + b;
-      } else {
-        nw = old - dtT * (du - dv);
-      }
-      B[q * g.cs + p] = nw;
+      for (int q = 0; q < 3; q++) se[q][e] = c1 * E[q * g.cs + p] - c2 * Ep[q * g.cs + p] + c3 * Eb[q * g.cs + p];
+    } else {
+#pragma unroll
+      for (int q = 0; q < 3; q++) se[q][e] = T(0);
     }
-    fB[q * g.cs + p] = T(0.5) * (old + nw);
   }
-}
-
-// KPT z nodes per thread, a block width apart
-template <class T>
-__global__ void __launch_bounds__(128) k3_faraday(G3 g, Pml3<T> pm, const T* Ee, T* B, T* Bs, T* fB, T ca, T cb, T cg,
-                                                  T dtT) {
-  const int k0 = blockIdx.x * blockDim.x * KPT + threadIdx.x, j = blockIdx.y, i = blockIdx.z;
+  __syncthreads();
+  const int j = j0 + threadIdx.y, k = k0 + threadIdx.x;
+  if (j > g.n[1] || k > g.n[2]) return;
 #pragma unroll
-  for (int kk = 0; kk < KPT; kk++) {
-    const int k = k0 + kk * blockDim.x;
-    if (k > g.n[2]) break;
-    faraday_node<T>(g, pm, Ee, B, Bs, fB, ca, cb, cg, dtT, i, j, k);
+  for (int lx = 0; lx < FX; lx++) {
+    const int i = i0 + lx;
+    if (i > g.n[0]) break;
+    const long p = nid(g, i, j, k);
+    const int c0 = ((lx + 1) * SY + threadIdx.y + 1) * SZ + threadIdx.x + 1;
+    const int idx[3] = {i, j, k};
+    const bool in = i >= 1 && i < g.n[0] && j >= 1 && j < g.n[1] && k >= 1 && k < g.n[2];
+#pragma unroll
+    for (int q = 0; q < 3; q++) {
+      const T old = B[q * g.cs + p];
+      T nw = old;
+      // every B component is valid on the interior nodes
+      if (in || in_valid(3 + q, g, i, j, k)) {
+        const int u = (q + 1) % 3, v = (q + 2) % 3;
+        const T du = dstar_s<T>(se[v], u, c0, ca, cb, cg, pm.id[u]);
+        const T dv = dstar_s<T>(se[u], v, c0, ca, cb, cg, pm.id[v]);
+        const T su = pm.sg[u][1][idx[u]], sv = pm.sg[v][1][idx[v]];
+        if (su > T(0) || sv > T(0)) {
+          T* Pu = Bs + (2 * q) * g.cs;
+          T* Pv = Bs + (2 * q + 1) * g.cs;
+          const T a = pm.xi[u][1][idx[u]] * Pu[p] - pm.cf[u][1][idx[u]] * du;
+          const T b = pm.xi[v][1][idx[v]] * Pv[p] + pm.cf[v][1][idx[v]] * dv;
+          Pu[p] = a;
+          Pv[p] = b;
+          nw = a + b;
+        } else {
+          nw = old - dtT * (du - dv);
+        }
+        B[q * g.cs + p] = nw;
+      }
+      fB[q * g.cs + p] = T(0.5) * (old + nw);
+    }
   }
 }
 
@@ -217,11 +224,11 @@ __device__ __forceinline__ void ampere_node(const G3& g, const Pml3<T>& pm, T* E
     const T* Bu = B + u * g.cs;
     T du, dv;
     if (in) {
-      du = (Bv[p] - Bv[p - st[u]]) * T(1.0 / g.d[u]);
-      dv = (Bu[p] - Bu[p - st[v]]) * T(1.0 / g.d[v]);
+      du = (Bv[p] - Bv[p - st[u]]) * pm.id[u];
+      dv = (Bu[p] - Bu[p - st[v]]) * pm.id[v];
     } else {
-      du = (rd3(g, Bv, i, j, k) - rd3(g, Bv, i - (u == 0), j - (u == 1), k - (u == 2))) * T(1.0 / g.d[u]);
-      dv = (rd3(g, Bu, i, j, k) - rd3(g, Bu, i - (v == 0), j - (v == 1), k - (v == 2))) * T(1.0 / g.d[v]);
+      du = (rd3(g, Bv, i, j, k) - rd3(g, Bv, i - (u == 0), j - (u == 1), k - (u == 2))) * pm.id[u];
+      dv = (rd3(g, Bu, i, j, k) - rd3(g, Bu, i - (v == 0), j - (v == 1), k - (v == 2))) * pm.id[v];
     }
     const T su = pm.sg[u][0][idx[u]], sv = pm.sg[v][0][idx[v]];
     if (su > T(0) || sv > T(0)) {
@@ -291,9 +298,128 @@ __global__ void __launch_bounds__(128) k3_filter_axis(G3 g, const T* __restrict_
   }
 }
 
+// x or y axis of the composed filter (stride 1, PT taps each side): a register window slides along the
+// axis; each thread owns one segment of one line (one z node, one index of the other transverse axis,
+// nodes [a, b) along the axis), reads each node of the segment and its 2 PT neighbours once, and sums the
+// taps in the same order as k3_filter_axis. Nodes off the grid read as zero.
+template <class T, int PT>
+__global__ void __launch_bounds__(128) k3_filter_slide(G3 g, const T* __restrict__ src, T* __restrict__ dst, int comp,
+                                                       int axis, int seg, Taps3<T> t) {
+  constexpr int W = 2 * PT + 1;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x, o = blockIdx.y;
+  if (k > g.n[2]) return;
+  const int n = axis == 0 ? g.n[0] : g.n[1];
+  const int a = blockIdx.z * seg, b = min(a + seg, n + 1);
+  int lo0, hi0, lo1, hi1, lo2, hi2;
+  vr(comp, 0, g, lo0, hi0);
+  vr(comp, 1, g, lo1, hi1);
+  vr(comp, 2, g, lo2, hi2);
+  const int loa = axis == 0 ? lo0 : lo1, hia = axis == 0 ? hi0 : hi1;
+  const bool other = (axis == 0 ? (o >= lo1 && o <= hi1) : (o >= lo0 && o <= hi0)) && k >= lo2 && k <= hi2;
+  const long st = axis == 0 ? (long)(g.n[1] + 1) * g.ldz : (long)g.ldz;
+  const long base = axis == 0 ? nid(g, 0, o, k) : nid(g, o, 0, k);
+  T c[W];
+#pragma unroll
+  for (int m = 0; m < W; m++) c[m] = t.c[m];
+  // w[m] = src at index i - PT + m
+  T w[W];
+#pragma unroll
+  for (int m = 0; m < W; m++) {
+    const int q = a + m - PT;
+    w[m] = (q >= 0 && q <= n) ? src[base + q * st] : T(0);
+  }
+  for (int i0 = a; i0 < b; i0 += W) {
+#pragma unroll
+    for (int r = 0; r < W; r++) {
+      const int i = i0 + r;
+      if (i < b) {
+        T acc = T(0);
+#pragma unroll
+        for (int m = 0; m < W; m++) acc += c[m] * w[m];
+        dst[base + i * st] = (other && i >= loa && i <= hia) ? acc : T(0);
+      }
+#pragma unroll
+      for (int m = 0; m < W - 1; m++) w[m] = w[m + 1];
+      const int q = i + PT + 1;
+      w[W - 1] = (i + 1 < b && q <= n) ? src[base + q * st] : T(0);
+    }
+  }
+}
+
+// 16-byte shared-memory load of 16 / sizeof(T) consecutive values
+__device__ __forceinline__ void ld16(const float* p, float* v) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
+  v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ __forceinline__ void ld16(const double* p, double* v) {
+  const double2 q = *reinterpret_cast<const double2*>(p);
+  v[0] = q.x; v[1] = q.y;
+}
+
+// z axis of the composed filter (stride 1): each block stages a row segment of 128 * ZR nodes and an
+// 8-node halo in shared memory; each thread reads its ZR + 16 staged values with 16-byte loads and sums
+// the taps of ZR consecutive outputs in the same order as k3_filter_axis.
+constexpr int ZR = 4, ZHA = 8;
+template <class T, int PT>
+__global__ void __launch_bounds__(128) k3_filter_zs(G3 g, const T* __restrict__ src, T* __restrict__ dst, int comp,
+                                                    Taps3<T> t) {
+  static_assert(PT <= ZHA, "filter halo above the staged halo");
+  constexpr int SEG = 128 * ZR, NV = ZR + 2 * ZHA, VL = 16 / (int)sizeof(T);
+  __shared__ __align__(16) T row[SEG + 2 * ZHA];
+  const int kb = blockIdx.x * SEG, j = blockIdx.y, i = blockIdx.z;
+  const int n = g.n[2];
+  const long base = nid(g, i, j, 0);
+  for (int e = threadIdx.x; e < SEG + 2 * ZHA; e += 128) {
+    const int q = kb - ZHA + e;
+    row[e] = (q >= 0 && q <= n) ? src[base + q] : T(0);
+  }
+  __syncthreads();
+  int lo0, hi0, lo1, hi1, lo2, hi2;
+  vr(comp, 0, g, lo0, hi0);
+  vr(comp, 1, g, lo1, hi1);
+  vr(comp, 2, g, lo2, hi2);
+  const bool other = i >= lo0 && i <= hi0 && j >= lo1 && j <= hi1;
+  const int l0 = ZR * threadIdx.x;
+  T v[NV];
+#pragma unroll
+  for (int q = 0; q < NV / VL; q++) ld16(row + l0 + q * VL, v + q * VL);
+#pragma unroll
+  for (int r = 0; r < ZR; r++) {
+    const int k = kb + l0 + r;
+    if (k > n) break;
+    T acc = T(0);
+#pragma unroll
+    for (int m = 0; m <= 2 * PT; m++) acc += t.c[m] * v[r + ZHA - PT + m];
+    dst[base + k] = (other && k >= lo2 && k <= hi2) ? acc : T(0);
+  }
+}
+
+template <class T, int PT>
+void launch_filter_fast(const G3& g, const T* src, T* dst, int comp, int axis, const Taps3<T>& t, cudaStream_t s) {
+  if (axis == 2) {
+    k3_filter_zs<T, PT><<<dim3(nblk(g.n[2] + 1, 128 * ZR), g.n[1] + 1, g.n[0] + 1), 128, 0, s>>>(g, src, dst, comp, t);
+  } else {
+    // segments of about 32 nodes along the axis: enough lines in flight to cover the load latency
+    const int n1 = (axis == 0 ? g.n[0] : g.n[1]) + 1;
+    const int nseg = std::max(1, n1 / 32), seg = (n1 + nseg - 1) / nseg;
+    k3_filter_slide<T, PT><<<dim3(nblk(g.n[2] + 1, 128), axis == 0 ? g.n[1] + 1 : g.n[0] + 1, nblk(n1, seg)), 128, 0,
+                             s>>>(g, src, dst, comp, axis, seg, t);
+  }
+}
+
 template <class T>
 void launch_filter_axis(const G3& g, dim3 grid, const T* src, T* dst, int comp, int axis, const Taps3<T>& t,
                         cudaStream_t s) {
+  if (t.s == 1) {
+    switch (t.P) {
+      case 1: launch_filter_fast<T, 1>(g, src, dst, comp, axis, t, s); return;
+      case 2: launch_filter_fast<T, 2>(g, src, dst, comp, axis, t, s); return;
+      case 3: launch_filter_fast<T, 3>(g, src, dst, comp, axis, t, s); return;
+      case 4: launch_filter_fast<T, 4>(g, src, dst, comp, axis, t, s); return;
+      case 5: launch_filter_fast<T, 5>(g, src, dst, comp, axis, t, s); return;
+      default: break;
+    }
+  }
   switch (t.P) {
     case 1: k3_filter_axis<T, 1><<<grid, 128, 0, s>>>(g, src, dst, comp, axis, t); break;
     case 2: k3_filter_axis<T, 2><<<grid, 128, 0, s>>>(g, src, dst, comp, axis, t); break;
@@ -405,7 +531,7 @@ struct Tiles3 {
 };
 
 __device__ __forceinline__ int tile_of(const G3& g, const Tiles3& t, const double* pos) {
-  const int ci = (int)floor(pos[0] / g.d[0]), cj = (int)floor(pos[1] / g.d[1]), ck = (int)floor(pos[2] / g.d[2]);
+  const int ci = (int)floor(pos[0] * g.id[0]), cj = (int)floor(pos[1] * g.id[1]), ck = (int)floor(pos[2] * g.id[2]);
   if (ci < 0 || cj < 0 || ck < 0 || ci >= g.n[0] || cj >= g.n[1] || ck >= g.n[2]) return -1;
   return ((ci / TX) * t.nt[1] + cj / TY) * t.nt[2] + ck / TZ;
 }
@@ -474,7 +600,7 @@ __global__ void k3_tile_scatter(Parts3<T> src, Parts3<T> dst, Tiles3 t, int n_ol
 
 template <class T, int ORD>
 __global__ void __launch_bounds__(256) k3_push_tiles(G3 g, Fld3<T> f, Parts3<T> p, Tiles3 t, Ctrl3* ctrl, T kq,
-                                                     double qe) {
+                                                     Cq3<T> cq) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sF = reinterpret_cast<T*>(smraw);        // 6 x WN gather fields
   T* sJ = sF + 6 * WN;                        // 3 x WN current
@@ -502,18 +628,17 @@ __global__ void __launch_bounds__(256) k3_push_tiles(G3 g, Fld3<T> f, Parts3<T> 
 #pragma unroll
   for (int a = 0; a < 3; a++) {
     org[a] = c0[a] * g.d[a];
-    inv[a] = 1.0 / g.d[a];
+    inv[a] = g.id[a];
     dT[a] = T(g.d[a]);
     invT[a] = T(inv[a]);
     lo[a] = T(g.lo[a] - c0[a]);
     hi[a] = T(g.hi[a] - c0[a] + (a == 2 ? 1 : 0));
   }
-  const double vol_dt = g.d[0] * g.d[1] * g.d[2] * g.dt;
   const T dtT = T(g.dt);
-  // J_q per unit weight: -q/(d_u d_v dt)
+  // J_q per unit weight: -q/(d_u d_v dt), from the host
   T cqw[3];
 #pragma unroll
-  for (int a = 0; a < 3; a++) cqw[a] = T(-qe * g.d[a] / vol_dt);
+  for (int a = 0; a < 3; a++) cqw[a] = cq.v[a];
   for (int j = p0 + threadIdx.x; j < p1; j += blockDim.x) {
     const double pos[3] = {p.x[j], p.y[j], p.z[j]};
     T X[3];
@@ -1056,10 +1181,24 @@ __global__ void k3_stats(G3 g, const T* E, const T* B, Parts3<T> p, const Ctrl3*
     v[1] += 1; v[2] += gl; v[3] += gl * gl;
   }
   const double dV = g.d[0] * g.d[1] * g.d[2];
-  for (long q = tid; q < g.cs; q += nthr) {
-    const double e2 = (double)E[q] * E[q] + (double)E[g.cs + q] * E[g.cs + q] + (double)E[2 * g.cs + q] * E[2 * g.cs + q];
-    const double b2 = (double)B[q] * B[q] + (double)B[g.cs + q] * B[g.cs + q] + (double)B[2 * g.cs + q] * B[2 * g.cs + q];
-    v[4] += 0.5 * (kEps0 * e2 + b2 * (kEps0 * kC * kC)) * dV;
+  if (sizeof(T) == 4) {
+    // FP32 fields: each thread sums its nodes' energy density in FP32 (a few hundred terms), the blocks
+    // and the grid reduce in FP64 (the FP64 pipe of this GPU is narrow)
+    T acc = T(0);
+    for (long q = tid; q < g.cs; q += nthr) {
+      const T e2 = E[q] * E[q] + E[g.cs + q] * E[g.cs + q] + E[2 * g.cs + q] * E[2 * g.cs + q];
+      const T b2 = B[q] * B[q] + B[g.cs + q] * B[g.cs + q] + B[2 * g.cs + q] * B[2 * g.cs + q];
+      acc += T(kEps0) * e2 + b2 * T(kEps0 * kC * kC);
+    }
+    v[4] = 0.5 * (double)acc * dV;
+  } else {
+    for (long q = tid; q < g.cs; q += nthr) {
+      const double e2 =
+          (double)E[q] * E[q] + (double)E[g.cs + q] * E[g.cs + q] + (double)E[2 * g.cs + q] * E[2 * g.cs + q];
+      const double b2 =
+          (double)B[q] * B[q] + (double)B[g.cs + q] * B[g.cs + q] + (double)B[2 * g.cs + q] * B[2 * g.cs + q];
+      v[4] += 0.5 * (kEps0 * e2 + b2 * (kEps0 * kC * kC)) * dV;
+    }
   }
   for (int c = 0; c < 6; c++) red[c][threadIdx.x] = v[c];
   __syncthreads();
@@ -1181,7 +1320,6 @@ double shape_h(int order, double s) {
   return 0.0;
 }
 
-inline unsigned nblk(long n, int b) { return (unsigned)((n + b - 1) / b); }
 
 template <class T>
 struct Sim3 : Sim3Api {
@@ -1198,13 +1336,14 @@ struct Sim3 : Sim3Api {
   double gamma = 1, beta = 0;
   long step = 0;
   // fields (3-component blocks)
-  T *E = nullptr, *B = nullptr, *J = nullptr, *Ep = nullptr, *Eb = nullptr, *Ee = nullptr;
+  T *E = nullptr, *B = nullptr, *J = nullptr, *Ep = nullptr, *Eb = nullptr;
   T *Es = nullptr, *Bs = nullptr;     // 6 split parts each
   T *fE = nullptr, *fB = nullptr, *tmp = nullptr, *tmp2 = nullptr;
   double* rho = nullptr;              // scratch for PIC_RHO
   double* out_d = nullptr;            // copy-out scratch
   Pml3<T> pm;
   Taps3<T> taps;
+  Cq3<T> cq_e;
   int P = 0;
   // particles
   Parts3<T> P2[2];
@@ -1240,6 +1379,7 @@ struct Sim3 : Sim3Api {
   T* rout = nullptr;
   // timing
   bool timing_on = false;
+  int timing_which = 0;   // 0: the push kernel; 1: the field kernels (Faraday, Friedman, filters, Ampere)
   double t_ms = 0;
   int64_t t_n = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -1291,8 +1431,11 @@ struct Sim3 : Sim3Api {
     beta = std::sqrt(1.0 - 1.0 / (gamma * gamma));
     g.n[0] = c->nx; g.n[1] = c->ny; g.n[2] = c->nz;
     g.d[0] = c->dx; g.d[1] = c->dy; g.d[2] = (1.0 + beta) * gamma * c->dz_lab;   // Sec. 5.1.1
+    for (int a = 0; a < 3; a++) g.id[a] = 1.0 / g.d[a];
     const double dt_cfl = cfl3(c->ck_alpha, c->ck_beta, c->ck_gamma, g.d[0], g.d[1], g.d[2], c->theta);
     g.dt = c->dt > 0.0 ? c->dt : c->courant * dt_cfl;
+    const double vol_dt = g.d[0] * g.d[1] * g.d[2] * g.dt;
+    for (int a = 0; a < 3; a++) cq_e.v[a] = T(kQe * g.d[a] / vol_dt);   // -q d_a/(d_x d_y d_z dt), q = -e
     if (!(g.dt > 0.0)) return fail(PIC_EINVAL, "dt <= 0");
     if (g.dt > dt_cfl * (1.0 + 1e-12)) return fail(PIC_ECFL, "dt above the 3D stability limit");
     P = c->filter_passes + (c->filter_compensate ? 1 : 0);
@@ -1313,12 +1456,12 @@ struct Sim3 : Sim3Api {
     g.cs = (long)(c->nx + 1) * (c->ny + 1) * g.ldz;
     const size_t cs = (size_t)g.cs;
     E = dal<T>(3 * cs); B = dal<T>(3 * cs); J = dal<T>(3 * cs); Ep = dal<T>(3 * cs); Eb = dal<T>(3 * cs);
-    Ee = dal<T>(3 * cs); fE = dal<T>(3 * cs); fB = dal<T>(3 * cs); tmp = dal<T>(cs); tmp2 = dal<T>(cs);
+    fE = dal<T>(3 * cs); fB = dal<T>(3 * cs); tmp = dal<T>(cs); tmp2 = dal<T>(cs);
     Es = dal<T>(6 * cs); Bs = dal<T>(6 * cs);
     ctrl = dal<Ctrl3>(1);
     bacc = dal<double>(8);
     sred = dal<double>(8);
-    if (!E || !B || !J || !Ep || !Eb || !Ee || !fE || !fB || !tmp || !tmp2 || !Es || !Bs || !ctrl || !bacc || !sred)
+    if (!E || !B || !J || !Ep || !Eb || !fE || !fB || !tmp || !tmp2 || !Es || !Bs || !ctrl || !bacc || !sred)
       return fail(PIC_ENOMEM, "allocation failed");
     // PML tables per axis, integer and half positions
     for (int a = 0; a < 3; a++) {
@@ -1341,6 +1484,7 @@ struct Sim3 : Sim3Api {
         cudaMemcpyAsync(d_c, cfv.data(), sizeof(T) * (n + 2), cudaMemcpyHostToDevice, s);
         cudaStreamSynchronize(s);
         pm.sg[a][h] = d_s; pm.xi[a][h] = d_x; pm.cf[a][h] = d_c;
+        pm.id[a] = T(g.id[a]);
       }
     }
     // composed filter taps along one axis: P passes of (1-a)/2, a, (1-a)/2 at stride s; a wide-band filter
@@ -1634,6 +1778,20 @@ struct Sim3 : Sim3Api {
     nl += 3;
   }
 
+  // CUDA events around the launches of the timed kernel class (host waits for the end event)
+  void tbeg(int which) {
+    if (timing_on && timing_which == which) cudaEventRecord(ev0, s);
+  }
+  void tend(int which) {
+    if (!(timing_on && timing_which == which)) return;
+    cudaEventRecord(ev1, s);
+    cudaEventSynchronize(ev1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, ev0, ev1);
+    t_ms += ms;
+    t_n++;
+  }
+
   int one_step() {
     const long nn = nodes();
     const long n3 = 3 * g.cs;
@@ -1641,13 +1799,15 @@ struct Sim3 : Sim3Api {
     btd_part(0, 0);
     btd_part(1, 0);
     // 1. Faraday + Friedman + PML-B (B^{n-1/2} -> B^{n+1/2}), gather copies
-    k3_eeff<T><<<nblk(n3, 256), 256, 0, s>>>(n3, E, Ep, Eb, Ee, T(1.0 + th / 4.0), T(0.5), T(0.5 - th / 4.0));
-    k3_faraday<T><<<grid3(), 128, 0, s>>>(g, pm, Ee, B, Bs, fB, T(cfg.ck_alpha), T(cfg.ck_beta), T(cfg.ck_gamma),
-                                          T(g.dt));
+    tbeg(1);
+    k3_faraday_tile<T><<<dim3(nblk(g.n[2] + 1, FZ), nblk(g.n[1] + 1, FY), nblk(g.n[0] + 1, FX)), dim3(FZ, FY), 0, s>>>(
+        g, pm, E, Ep, Eb, B, Bs, fB, T(1.0 + th / 4.0), T(0.5), T(0.5 - th / 4.0), T(cfg.ck_alpha), T(cfg.ck_beta),
+        T(cfg.ck_gamma), T(g.dt));
     k3_friedman<T><<<nblk(n3, 256), 256, 0, s>>>(n3, E, Ep, Eb, fE, T(1.0 - th / 2.0), T(th / 2.0));
-    nl += 3;
+    nl += 2;
     if (cfg.filter_gather && P > 0)
       for (int c = 0; c < 3; c++) { filter3(fE + c * g.cs, c); filter3(fB + c * g.cs, 3 + c); }
+    tend(1);
     // 2. particles
     cudaMemsetAsync(J, 0, sizeof(T) * 3 * g.cs, s);
     Fld3<T> f;
@@ -1656,20 +1816,13 @@ struct Sim3 : Sim3Api {
     if (loaded && count_ub > 0) {
       sort_tiles();
       const int smem = (int)(9 * WN * sizeof(T));
-      if (timing_on) cudaEventRecord(ev0, s);
+      tbeg(0);
       if (cfg.shape_order == 3)
-        k3_push_tiles<T, 3><<<ntiles, 256, smem, s>>>(g, f, P2[cur], tl, ctrl, kq, -kQe);
+        k3_push_tiles<T, 3><<<ntiles, 256, smem, s>>>(g, f, P2[cur], tl, ctrl, kq, cq_e);
       else
-        k3_push_tiles<T, 1><<<ntiles, 256, smem, s>>>(g, f, P2[cur], tl, ctrl, kq, -kQe);
+        k3_push_tiles<T, 1><<<ntiles, 256, smem, s>>>(g, f, P2[cur], tl, ctrl, kq, cq_e);
       nl++;
-      if (timing_on) {
-        cudaEventRecord(ev1, s);
-        cudaEventSynchronize(ev1);
-        float ms = 0;
-        cudaEventElapsedTime(&ms, ev0, ev1);
-        t_ms += ms;
-        t_n++;
-      }
+      tend(0);
     }
     const double tn = time_of(step), tn1 = time_of(step + 1);
     if (loaded && ions && row_next > mlo) {
@@ -1695,10 +1848,12 @@ struct Sim3 : Sim3Api {
       Dn += dD;
     }
     // 4. current filter, Ampere + PML-E
+    tbeg(1);
     if (cfg.filter_J && P > 0)
       for (int c = 0; c < 3; c++) filter3(J + c * g.cs, c);
     k3_ampere<T><<<grid3(), 128, 0, s>>>(g, pm, E, Es, B, J, T(g.dt * kC * kC), T(g.dt / kEps0));
     nl++;
+    tend(1);
     btd_part(0, 1);
     btd_part(1, 1);
     // 5. ion rows that left the particle domain, inflow through z_hi
@@ -1859,7 +2014,7 @@ struct Sim3 : Sim3Api {
       trap = 2.0 * (2.0 * kPi * kC / las.lambda0) / wp;
     }
     cudaMemsetAsync(sred, 0, 8 * sizeof(double), s);
-    k3_stats<T><<<304, 256, 0, s>>>(g, E, B, P2[cur], ctrl, bm, gamma, beta, trap, sred);
+    k3_stats<T><<<152 * 8, 256, 0, s>>>(g, E, B, P2[cur], ctrl, bm, gamma, beta, trap, sred);
     nl++;
     double h[8];
     cudaMemcpyAsync(h, sred, sizeof(h), cudaMemcpyDeviceToHost, s);
@@ -1883,9 +2038,10 @@ struct Sim3 : Sim3Api {
   int64_t launches() const override { return nl; }
 
   int kernel_timing(int enable, int which, double* ms_total, int64_t* n) override {
-    if (which != 0) return fail(PIC_EINVAL, "3D timing covers the push kernel (which = 0) only");
+    if (which != 0 && which != 1) return PIC_EINVAL;
     if (enable >= 0) {
       timing_on = enable != 0;
+      timing_which = which;
       if (enable) { t_ms = 0; t_n = 0; }
     }
     if (ms_total) *ms_total = t_ms;

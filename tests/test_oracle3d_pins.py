@@ -217,7 +217,7 @@ def test_3d_gauss_law_full_step_with_antenna(orc):
 
 def test_3d_wide_band_filter_gain(orc):
     """S(1:2) in 3D: the gain of a periodic mode is the product over the three axes and both strides of
-    g(s, 1/2, k)^4 g(s, 3/2, k)"""
+    g(s, 1/2, k)^4 g(s, 3, k), the compensation pass at alpha_c = n/2 + 1 = 3 for n = 4"""
     w = vacuum3(16, 12, 20, filter_passes=4, filter_compensate=1, filter_strides=[1, 2])
     s = orc.Sim3(w)
     m = (3, 2, 5)

@@ -663,7 +663,8 @@ def test_mlp_reference_gradient_matches_finite_differences():
 
 # ---------------------------------------------------------------------------
 # Sec. 4.1: wide-band filters combining strides, S(1:2), S(1:2:3), S(1:2:4): along each axis the product
-# over the strides s of G_s = g(s, 1/2, k)^4 g(s, 3/2, k), g(s, a, k) = a + (1 - a) cos(s k)
+# over the strides s of G_s = g(s, 1/2, k)^4 g(s, 3, k), g(s, a, k) = a + (1 - a) cos(s k); the compensation
+# pass takes alpha_c = n/2 + 1 = 3 for n = 4 (the text's value; the figure captions print 3/2)
 def _G(s, k, n=4):
     ac = n / 2 + 1
     return (0.5 + 0.5 * np.cos(s * k)) ** n * (ac + (1 - ac) * np.cos(s * k))
