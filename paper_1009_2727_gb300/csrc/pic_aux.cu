@@ -313,23 +313,72 @@ __global__ void k_ion_rho(GridP g, const double* ion_x, const double* R, double 
 }
 
 template <class T>
-__global__ void k_stats(GridP g, FieldPtrs<T> f, Particles<T> p, const Ctrl* ctrl, Beam<T> b, double gam, double be,
-                        double trap, double* out) {
+__global__ void __launch_bounds__(256) k_stats(GridP g, FieldPtrs<T> f, Particles<T> p, const Ctrl* ctrl, Beam<T> b,
+                                               double gam, double be, double trap, double* out) {
   // out: [0] n_e, [1] n_beam_active, [2] sum gamma_lab, [3] sum gamma_lab^2, [4] field energy,
   // [5] weight of the electrons with lab-frame gamma above trap
+  __shared__ double red[6][256];
   const long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const long nthr = (long)gridDim.x * blockDim.x;
   double ne = 0, na = 0, sg = 0, sg2 = 0, en = 0, wt = 0;
-  for (long j = tid; j < ctrl->count; j += nthr) {
-    const double w = (double)p.w[j];
-    if (!(w > 0.0)) continue;
-    ne += 1.0;
-    if (trap > 0.0) {
-      // boosted-frame momentum (the mixed path stores u_z - u0) -> lab-frame gamma
-      const double ux = p.ux[j], uy = p.uy[j];
-      const double uz = CellPos<T>::value ? (double)g.fr_u0 + (double)p.uz[j] : (double)p.uz[j];
-      const double gp = sqrt(1.0 + (ux * ux + uy * uy + uz * uz) / (kC * kC));
-      if (gam * (gp + be * uz / kC) > trap) wt += w;
+  const int nz1 = g.nz + 1;
+  const int ncell = (g.nx + 1) * nz1;
+  if (sizeof(T) == 4) {
+    // FP32 path (momenta and fields in FP32): the lab-gamma test and the per-thread sums (a few dozen
+    // particles, a few nodes) in FP32, the block and grid sums in FP64; the FP64 pipe of this GPU is narrow
+    const float ic2 = float(1.0 / (kC * kC)), ic = float(1.0 / kC);
+    const float gamf = float(gam), bef = float(be), trapf = float(trap);
+    int nef = 0;
+    float wtf = 0.f;
+    for (long j = tid; j < ctrl->count; j += nthr) {
+      const float w = float(p.w[j]);
+      if (!(w > 0.f)) continue;
+      nef++;
+      if (trap > 0.0) {
+        // boosted-frame momentum (the mixed path stores u_z - u0) -> lab-frame gamma
+        const float ux = float(p.ux[j]), uy = float(p.uy[j]);
+        const float uz = CellPos<T>::value ? g.fr_u0 + float(p.uz[j]) : float(p.uz[j]);
+        const float gp = sqrtf(1.f + (ux * ux + uy * uy + uz * uz) * ic2);
+        if (gamf * (gp + bef * uz * ic) > trapf) wtf += w;
+      }
+    }
+    ne = nef;
+    wt = wtf;
+    const float e0 = float(kEps0), imu0 = float(kEps0 * kC * kC);
+    float enf = 0.f;
+    for (int e = (int)tid; e < ncell; e += (int)nthr) {
+      const int i = e / nz1, k = e - i * nz1;
+      const long q = (long)i * g.ld + k;
+      float e2 = 0.f, b2 = 0.f;
+      for (int c = 0; c < 3; c++) {
+        const float ev = float(f.E[c][q]), bv = float(f.B[c][q]);
+        e2 += ev * ev; b2 += bv * bv;
+      }
+      enf += e0 * e2 + b2 * imu0;
+    }
+    en = 0.5 * (double)enf * g.dx * g.dz;
+  } else {
+    for (long j = tid; j < ctrl->count; j += nthr) {
+      const double w = (double)p.w[j];
+      if (!(w > 0.0)) continue;
+      ne += 1.0;
+      if (trap > 0.0) {
+        const double ux = p.ux[j], uy = p.uy[j];
+        const double uz = CellPos<T>::value ? (double)g.fr_u0 + (double)p.uz[j] : (double)p.uz[j];
+        const double gp = sqrt(1.0 + (ux * ux + uy * uy + uz * uz) / (kC * kC));
+        if (gam * (gp + be * uz / kC) > trap) wt += w;
+      }
+    }
+    const double mu0 = 1.0 / (kEps0 * kC * kC);
+    for (int e = (int)tid; e < ncell; e += (int)nthr) {
+      const int i = e / nz1, k = e - i * nz1;
+      const long q = (long)i * g.ld + k;
+      double e2 = 0, b2 = 0;
+      for (int c = 0; c < 3; c++) {
+        const double ev = f.E[c][q], bv = f.B[c][q];
+        e2 += ev * ev; b2 += bv * bv;
+      }
+      en += 0.5 * (kEps0 * e2 + b2 / mu0) * g.dx * g.dz;
     }
   }
   for (long j = tid; j < b.n; j += nthr) {
@@ -339,20 +388,16 @@ __global__ void k_stats(GridP g, FieldPtrs<T> f, Particles<T> p, const Ctrl* ctr
     const double gl = gam * (gp + be * uz / kC);
     na += 1; sg += gl; sg2 += gl * gl;
   }
-  const long ncell = (long)(g.nx + 1) * (g.nz + 1);
-  const double mu0 = 1.0 / (kEps0 * kC * kC);
-  for (long e = tid; e < ncell; e += nthr) {
-    const long i = e / (g.nz + 1), k = e - i * (g.nz + 1);
-    const long q = i * g.ld + k;
-    double e2 = 0, b2 = 0;
-    for (int c = 0; c < 3; c++) {
-      const double ev = f.E[c][q], bv = f.B[c][q];
-      e2 += ev * ev; b2 += bv * bv;
-    }
-    en += 0.5 * (kEps0 * e2 + b2 / mu0) * g.dx * g.dz;
+  red[0][threadIdx.x] = ne; red[1][threadIdx.x] = na; red[2][threadIdx.x] = sg;
+  red[3][threadIdx.x] = sg2; red[4][threadIdx.x] = en; red[5][threadIdx.x] = wt;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o)
+      for (int c = 0; c < 6; c++) red[c][threadIdx.x] += red[c][threadIdx.x + o];
+    __syncthreads();
   }
-  atomicAdd(&out[0], ne); atomicAdd(&out[1], na); atomicAdd(&out[2], sg); atomicAdd(&out[3], sg2);
-  atomicAdd(&out[4], en); atomicAdd(&out[5], wt);
+  if (threadIdx.x == 0)
+    for (int c = 0; c < 6; c++) atomicAdd(&out[c], red[c][0]);
 }
 
 template <class T>
@@ -547,7 +592,7 @@ void launch_stats(const GridP& g, const FieldPtrs<T>& f, Particles<T> p, const C
                   double gamma, double beta, double trap, double* out, cudaStream_t s) {
   (void)cap;
   cudaMemsetAsync(out, 0, 8 * sizeof(double), s);
-  k_stats<T><<<304, 256, 0, s>>>(g, f, p, ctrl, b, gamma, beta, trap, out);
+  k_stats<T><<<152 * 8, 256, 0, s>>>(g, f, p, ctrl, b, gamma, beta, trap, out);
 }
 
 template <class T>
