@@ -560,29 +560,44 @@ __global__ void k3_tile_key(G3 g, Parts3<T> p, const Ctrl3* ctrl, Tiles3 t, int 
   if (j < n) t.key[j] = key;
 }
 
-// exclusive scan of the tile counts by one block; the total becomes the particle count
+// exclusive scan of the tile counts by one block, in chunks of 8192 counts staged with coalesced loads
+// (each thread sums eight consecutive counts); the total becomes the particle count
 __global__ void __launch_bounds__(1024) k3_scan_tiles(const int* cnt, int* start, int n, Ctrl3* ctrl) {
+  constexpr int CH = 8192, PER = CH / 1024;
+  __shared__ int buf[CH];
   __shared__ int part[1024];
-  const int per = (n + 1023) / 1024;
-  const int b0 = threadIdx.x * per, b1 = min(n, b0 + per);
-  int s = 0;
-  for (int b = b0; b < b1; b++) s += cnt[b];
-  part[threadIdx.x] = s;
-  __syncthreads();
-  for (int o = 1; o < 1024; o <<= 1) {
-    const int v = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
+  int carry = 0;
+  for (int c0 = 0; c0 < n; c0 += CH) {
+    for (int e = threadIdx.x; e < CH; e += 1024) buf[e] = c0 + e < n ? cnt[c0 + e] : 0;
     __syncthreads();
-    part[threadIdx.x] += v;
+    int s = 0;
+#pragma unroll
+    for (int q = 0; q < PER; q++) s += buf[threadIdx.x * PER + q];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+      const int v = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
+      __syncthreads();
+      part[threadIdx.x] += v;
+      __syncthreads();
+    }
+    int run = carry + part[threadIdx.x] - s;
+#pragma unroll
+    for (int q = 0; q < PER; q++) {
+      const int v = buf[threadIdx.x * PER + q];
+      buf[threadIdx.x * PER + q] = run;
+      run += v;
+    }
+    const int tot = part[1023];
+    __syncthreads();
+    for (int e = threadIdx.x; e < CH; e += 1024)
+      if (c0 + e < n) start[c0 + e] = buf[e];
+    carry += tot;
     __syncthreads();
   }
-  int run = part[threadIdx.x] - s;
-  for (int b = b0; b < b1; b++) {
-    start[b] = run;
-    run += cnt[b];
-  }
-  if (threadIdx.x == 1023) {
-    start[n] = part[1023];
-    ctrl->count = part[1023];
+  if (threadIdx.x == 0) {
+    start[n] = carry;
+    ctrl->count = carry;
   }
 }
 
@@ -853,7 +868,7 @@ __device__ __forceinline__ double cum_shape(int order, double u) {
 __global__ void k3_ion_z(G3 g, Lat3 L, int order, long long mlo, long long mhi, double t0, double t1, double* Zs) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k > g.n[2]) return;
-  const double dz = g.d[2];
+  const double dz = g.d[2], idz = g.id[2];
   const double vsh = L.beta * kC;
   long long m0 = (long long)floor(((k - 4) * dz + vsh * t0) / L.h - 0.5);
   long long m1 = (long long)ceil(((k + 4) * dz + vsh * t0) / L.h - 0.5);
@@ -865,19 +880,28 @@ __global__ void k3_ion_z(G3 g, Lat3 L, int order, long long mlo, long long mhi, 
     const double n = L.gamma * lab_density3(L, L.gamma * zl);
     if (n <= 0.0) continue;
     const double w = n * g.d[0] * g.d[1] * g.d[2] / (double)(L.ppc[0] * L.ppc[1] * L.ppc[2]);
-    const double Z0 = (zl - vsh * t0) / dz, Z1 = (zl - vsh * t1) / dz;
+    const double Z0 = (zl - vsh * t0) * idz, Z1 = (zl - vsh * t1) * idz;
     acc += w * (cum_shape(order, Z1 - k) - cum_shape(order, Z0 - k));
   }
   Zs[k] = acc;
 }
 
-// J_z += coef Tx(i) Ty(j) Z(k), coef = -q_ion/(dx dy dt)
+// J_z += coef Tx(i) Ty(j) Z(k), coef = -q_ion/(dx dy dt), on the nodes where T_x T_y is non-zero
+// (i0 + blockIdx.z, j0 + blockIdx.y); KPT z nodes per thread, a block width apart
 template <class T>
-__global__ void k3_ion_jz(G3 g, const double* Tx, const double* Ty, const double* Zs, double coef, T* Jz) {
-  int i, j, k;
-  if (!node_of(g, (long)blockIdx.x * blockDim.x + threadIdx.x, i, j, k)) return;
-  const double v = coef * Tx[i] * Ty[j] * Zs[k];
-  if (v != 0.0) Jz[nid(g, i, j, k)] += T(v);
+__global__ void __launch_bounds__(128) k3_ion_jz(G3 g, const double* Tx, const double* Ty, const double* Zs,
+                                                 double coef, int i0, int j0, T* Jz) {
+  const int i = i0 + blockIdx.z, j = j0 + blockIdx.y;
+  const double f = coef * Tx[i] * Ty[j];
+  if (f == 0.0) return;
+  const int kb = blockIdx.x * 128 * KPT + threadIdx.x;
+#pragma unroll
+  for (int kk = 0; kk < KPT; kk++) {
+    const int k = kb + kk * 128;
+    if (k > g.n[2]) break;
+    const double v = f * Zs[k];
+    if (v != 0.0) Jz[nid(g, i, j, k)] += T(v);
+  }
 }
 
 // charge density of the ion rows at time t: q/(dV) Tx(i) Ty(j) sum_m w_m S(Z_m - k)
@@ -1363,6 +1387,7 @@ struct Sim3 : Sim3Api {
   double* Tx = nullptr;
   double* Ty = nullptr;
   double* Zs = nullptr;
+  int ion_i0 = 0, ion_i1 = 0, ion_j0 = 0, ion_j1 = 0;   // node range where T_x, T_y are non-zero
   bool ions = false;
   // laser
   bool has_laser = false;
@@ -1682,6 +1707,12 @@ struct Sim3 : Sim3Api {
         const double Y = g.lo[1] + (b + 0.5) / lat.ppc[1];
         for (int j = 0; j <= g.n[1]; j++) ty[j] += shape_h(cfg.shape_order, Y - j);
       }
+      ion_i0 = g.n[0]; ion_i1 = 0; ion_j0 = g.n[1]; ion_j1 = 0;
+      for (int i = 0; i <= g.n[0]; i++)
+        if (tx[i] != 0.0) { ion_i0 = std::min(ion_i0, i); ion_i1 = std::max(ion_i1, i); }
+      for (int j = 0; j <= g.n[1]; j++)
+        if (ty[j] != 0.0) { ion_j0 = std::min(ion_j0, j); ion_j1 = std::max(ion_j1, j); }
+      if (ion_i1 < ion_i0 || ion_j1 < ion_j0) { ion_i0 = ion_i1 = ion_j0 = ion_j1 = 0; }
       Tx = dal<double>(g.n[0] + 1); Ty = dal<double>(g.n[1] + 1); Zs = dal<double>(g.n[2] + 1);
       if (!Tx || !Ty || !Zs) return fail(PIC_ENOMEM, "allocation failed");
       cudaMemcpyAsync(Tx, tx.data(), sizeof(double) * tx.size(), cudaMemcpyHostToDevice, s);
@@ -1826,8 +1857,9 @@ struct Sim3 : Sim3Api {
     }
     const double tn = time_of(step), tn1 = time_of(step + 1);
     if (loaded && ions && row_next > mlo) {
-      k3_ion_z<<<nblk(g.n[2] + 1, 128), 128, 0, s>>>(g, lat, cfg.shape_order, mlo, row_next, tn, tn1, Zs);
-      k3_ion_jz<T><<<nblk(nn, 256), 256, 0, s>>>(g, Tx, Ty, Zs, -kQe / (g.d[0] * g.d[1] * g.dt), J + 2 * g.cs);
+      k3_ion_z<<<nblk(g.n[2] + 1, 32), 32, 0, s>>>(g, lat, cfg.shape_order, mlo, row_next, tn, tn1, Zs);
+      k3_ion_jz<T><<<dim3(nblk(g.n[2] + 1, 128 * KPT), ion_j1 - ion_j0 + 1, ion_i1 - ion_i0 + 1), 128, 0, s>>>(
+          g, Tx, Ty, Zs, -kQe / (g.d[0] * g.d[1] * g.dt), ion_i0, ion_j0, J + 2 * g.cs);
       nl += 2;
     }
     if (has_beam) {
