@@ -59,7 +59,7 @@ class _Config(ctypes.Structure):
         ("order", ctypes.c_int), ("particle_guard", ctypes.c_int),
         ("periodic_x", ctypes.c_int), ("periodic_z", ctypes.c_int),
         ("moving_window", ctypes.c_int), ("window_beta", ctypes.c_double),
-        ("filter_strides", ctypes.c_int * 4),
+        ("filter_strides", ctypes.c_int * 4), ("gather_nodal", ctypes.c_int),
     ]
 
 
@@ -88,7 +88,7 @@ class _Config3(ctypes.Structure):
         ("filter_J", ctypes.c_int), ("filter_gather", ctypes.c_int),
         ("order", ctypes.c_int), ("particle_guard", ctypes.c_int),
         ("periodic_x", ctypes.c_int), ("periodic_y", ctypes.c_int), ("periodic_z", ctypes.c_int),
-        ("filter_strides", ctypes.c_int * 4),
+        ("filter_strides", ctypes.c_int * 4), ("gather_nodal", ctypes.c_int),
     ]
 
 
@@ -235,6 +235,7 @@ def _mk_config(w: dict) -> _Config:
     c.window_beta = float(w.get("window_beta", 0.0))
     for q, v in enumerate(list(w.get("filter_strides", []))[:4]):
         c.filter_strides[q] = int(v)
+    c.gather_nodal = 1 if w.get("gather", "energy") == "momentum" else 0
     return c
 
 
@@ -401,6 +402,7 @@ def _mk_config3(w: dict) -> _Config3:
     c.periodic_z = int(w.get("periodic_z", 0))
     for q, v in enumerate(list(w.get("filter_strides", []))[:4]):
         c.filter_strides[q] = int(v)
+    c.gather_nodal = 1 if w.get("gather", "energy") == "momentum" else 0
     return c
 
 

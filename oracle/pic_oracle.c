@@ -69,6 +69,8 @@ typedef struct {
   double window_beta;
   int filter_strides[4];      /* > 0: the wide-band filter of Sec. 4.1, the product over these strides of
                                  (n passes + compensation) at each stride, e.g. 1,2,3 for S(1:2:3); else 0 */
+  int gather_nodal;           /* 0: 'energy conserving' gather from the Yee locations (Sec. 5);
+                                 1: 'momentum conserving': the fields are first interpolated to the nodes */
 } orc_config;
 
 typedef struct {
@@ -400,6 +402,24 @@ static void filter_component(orc_sim* s, int comp, double* F) {
     }
 }
 
+/* 'Momentum conserving' gather (Sec. 5, scan of the time step): the staggered gather copy of a component
+ * is first interpolated to the grid nodes, as the mean of its two nearest values along each half-integer
+ * axis (four for a component staggered along x and z); values off the grid count as zero. */
+static void to_nodes(orc_sim* s, int comp, double* F) {
+  int hx = STX[comp] != 0.0, hz = STZ[comp] != 0.0;
+  double* out = s->tmp;
+  for (int i = 0; i <= s->c.nx; i++)
+    for (int k = 0; k <= s->c.nz; k++) {
+      double v;
+      if (hx && hz) v = 0.25 * (rd(s, F, i - 1, k - 1) + rd(s, F, i, k - 1) + rd(s, F, i - 1, k) + rd(s, F, i, k));
+      else if (hx) v = 0.5 * (rd(s, F, i - 1, k) + rd(s, F, i, k));
+      else if (hz) v = 0.5 * (rd(s, F, i, k - 1) + rd(s, F, i, k));
+      else v = F[IDX(s, i, k)];
+      out[IDX(s, i, k)] = v;
+    }
+  memcpy(F, out, sizeof(double) * s->ncell);
+}
+
 /* exported: apply the configured filter to a caller array of a component */
 void orc_filter_field(orc_sim* s, int comp, double* F) { filter_component(s, comp, F); }
 
@@ -415,10 +435,10 @@ static void gather(const orc_sim* s, double x, double z, double* E, double* B) {
   for (int c = 0; c < 6; c++) {
     double acc = 0.0;
     for (int i = fx - 3; i <= fx + 3; i++) {
-      double wx = orc_shape(ord, X - (i + STX[c]));
+      double wx = orc_shape(ord, X - (i + (s->c.gather_nodal ? 0.0 : STX[c])));
       if (wx == 0.0) continue;
       for (int k = fz - 3; k <= fz + 3; k++) {
-        double wz = orc_shape(ord, Z - (k + STZ[c]));
+        double wz = orc_shape(ord, Z - (k + (s->c.gather_nodal ? 0.0 : STZ[c])));
         if (wz == 0.0) continue;
         acc += rd(s, src[c], i, k) * wx * wz;
       }
@@ -892,6 +912,8 @@ static void one_step(orc_sim* s) {
   if (s->c.filter_gather) {
     for (int c = 0; c < 3; c++) { filter_component(s, OEX + c, s->fE[c]); filter_component(s, OBX + c, s->fB[c]); }
   }
+  if (s->c.gather_nodal)
+    for (int c = 0; c < 3; c++) { to_nodes(s, OEX + c, s->fE[c]); to_nodes(s, OBX + c, s->fB[c]); }
   /* 3-5. particles: gather, Boris, move, Esirkepov */
   for (int c = OJX; c <= OJZ; c++) memset(s->F[c], 0, sizeof(double) * s->ncell);
   double xlo = s->gx_lo * s->dx, xhi = s->gx_hi * s->dx;

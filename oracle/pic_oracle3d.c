@@ -58,6 +58,7 @@ typedef struct {
   int order, particle_guard;
   int periodic_x, periodic_y, periodic_z;   /* fields only (test option) */
   int filter_strides[4];      /* > 0: product over these strides of (n passes + compensation), Sec. 4.1 */
+  int gather_nodal;           /* 1: 'momentum conserving' gather from node-interpolated fields (Sec. 5) */
 } o3_config;
 
 typedef struct {
@@ -297,6 +298,28 @@ static void filter_component(o3_sim* s, int comp, double* F) {
 
 void o3_filter_field(o3_sim* s, int comp, double* F) { filter_component(s, comp, F); }
 
+/* 'Momentum conserving' gather (Sec. 5): the staggered gather copy interpolated to the nodes, the mean of
+ * the two nearest values along each half-integer axis of the component (four along two axes); values
+ * off the grid count as zero. */
+static void to_nodes(o3_sim* s, int comp, double* F) {
+  int h[3] = { SX[comp] != 0.0, SY[comp] != 0.0, SZ[comp] != 0.0 };
+  double* out = s->tmp;
+  for (int i = 0; i <= s->c.nx; i++)
+    for (int j = 0; j <= s->c.ny; j++)
+      for (int k = 0; k <= s->c.nz; k++) {
+        double acc = 0.0;
+        int cnt = 0;
+        for (int a = 0; a <= h[0]; a++)
+          for (int b = 0; b <= h[1]; b++)
+            for (int c = 0; c <= h[2]; c++) {
+              acc += rd(s, F, i - h[0] + a, j - h[1] + b, k - h[2] + c);
+              cnt++;
+            }
+        out[I3(s, i, j, k)] = acc / cnt;
+      }
+  memcpy(F, out, sizeof(double) * s->ncell);
+}
+
 /* ------------------------------------------------------------------ */
 static void gather(const o3_sim* s, double x, double y, double z, double* E, double* B) {
   int ord = s->c.order;
@@ -307,13 +330,14 @@ static void gather(const o3_sim* s, double x, double y, double z, double* E, dou
   for (int c = 0; c < 6; c++) {
     double acc = 0.0;
     for (int i = fx - 3; i <= fx + 3; i++) {
-      double wx = orc_shape(ord, X - (i + SX[c]));
+      const int nod = s->c.gather_nodal;
+      double wx = orc_shape(ord, X - (i + (nod ? 0.0 : SX[c])));
       if (wx == 0.0) continue;
       for (int j = fy - 3; j <= fy + 3; j++) {
-        double wy = orc_shape(ord, Y - (j + SY[c]));
+        double wy = orc_shape(ord, Y - (j + (nod ? 0.0 : SY[c])));
         if (wy == 0.0) continue;
         for (int k = fz - 3; k <= fz + 3; k++) {
-          double wz = orc_shape(ord, Z - (k + SZ[c]));
+          double wz = orc_shape(ord, Z - (k + (nod ? 0.0 : SZ[c])));
           if (wz == 0.0) continue;
           acc += rd(s, src[c], i, j, k) * wx * wy * wz;
         }
@@ -724,6 +748,8 @@ static void one_step(o3_sim* s) {
     }
   if (s->c.filter_gather)
     for (int c = 0; c < 3; c++) { filter_component(s, QEX + c, s->fE[c]); filter_component(s, QBX + c, s->fB[c]); }
+  if (s->c.gather_nodal)
+    for (int c = 0; c < 3; c++) { to_nodes(s, QEX + c, s->fE[c]); to_nodes(s, QBX + c, s->fB[c]); }
   for (int c = QJX; c <= QJZ; c++) memset(s->F[c], 0, sizeof(double) * s->ncell);
   double lo[3], hi[3];
   double dd[3] = { s->dx, s->dy, s->dz };

@@ -230,3 +230,26 @@ def test_3d_wide_band_filter_gain(orc):
     gain = np.prod([G(st, kk) for st in (1, 2) for kk in k])
     got = s.filter_field(1, f)[:16, :12, :20]
     assert np.abs(got - gain * f[:16, :12, :20]).max() < 1e-13
+
+
+def test_3d_momentum_conserving_gather_copies_at_the_nodes(orc):
+    """Sec. 5, 'momentum conserving' gather in 3D: the node value of each gather copy is the mean of its
+    nearest staggered values (two along one half-integer axis, four along two); a field quadratic along a
+    half-integer axis gains exactly 1/4 per such axis, a linear one is exact"""
+    n = (14, 12, 16)
+    s = orc.Sim3(vacuum3(*n, periodic=False, gather="momentum"))
+    I, J, K = np.meshgrid(*[np.arange(m + 1, dtype=float) for m in n], indexing="ij")
+    # E_q depends only on its own coordinate (curl free); B is static (Faraday leaves it unchanged)
+    s.set_field(0, (I + 0.5) ** 2 + (I + 0.5))
+    s.set_field(1, 2.0 * (J + 0.5) ** 2)
+    s.set_field(2, -(K + 0.5) ** 2 + 3.0)
+    s.set_field(3, (J + 0.5) ** 2 + (K + 0.5) ** 2 + (J + 0.5) * (K + 0.5))
+    s.set_field(4, (I + 0.5) * (K + 0.5) + 1.0)
+    s.set_field(5, (I + 0.5) ** 2 - (J + 0.5))
+    s.step(1)
+    want = {0: I ** 2 + 0.25 + I, 1: 2.0 * (J ** 2 + 0.25), 2: -(K ** 2 + 0.25) + 3.0,
+            3: J ** 2 + K ** 2 + J * K + 0.5, 4: I * K + 1.0, 5: I ** 2 + 0.25 - J}
+    sl = tuple(slice(3, m - 2) for m in n)
+    for c in range(6):
+        got = s.gather_field(c)
+        assert np.abs(got[sl] - want[c][sl]).max() < 1e-12 * np.abs(want[c][sl]).max(), c

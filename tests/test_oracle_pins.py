@@ -699,3 +699,69 @@ def test_wide_band_filters_match_n_pass_falloff_and_pass_counts():
         assert k_half(wide) == pytest.approx(k_half(npass), rel=0.03)
         passes = 5 * len(strides)
         assert round((n + 1) / passes, 1) == printed
+
+
+# ---------------------------------------------------------------------------
+# Sec. 5, scan of the time step: the 'momentum conserving' gather first interpolates the staggered gather
+# copies to the grid nodes (the mean of the two nearest values along each half-integer axis, four for a
+# component staggered along x and z), then gathers with the node-centred shape.
+@pytest.mark.parametrize("solver", ["yee", "ck"])
+def test_momentum_conserving_gather_copies_at_the_nodes(orc, solver):
+    """curl-free E and a static B: the node values of a linear field are exact, and a quadratic X^2 (X in
+    cells along a half-integer axis) gains exactly 1/4, the mean of (X - 1/2)^2 and (X + 1/2)^2"""
+    nx, nz = 24, 28
+    w = vacuum(nx, nz, solver, periodic=False, gather="momentum")
+    s = orc.Sim(w)
+    I, K = np.meshgrid(np.arange(nx + 1, dtype=float), np.arange(nz + 1, dtype=float), indexing="ij")
+
+    def fx(X):
+        return 1.0 + 2.0 * X + 0.5 * X ** 2
+
+    def fz(Z):
+        return -3.0 + 0.7 * Z - 0.25 * Z ** 2
+    # staggered samples: Ex (i+1/2, k), Ey (i, k), Ez (i, k+1/2), Bx (i, k+1/2), By (i+1/2, k+1/2), Bz (i+1/2, k)
+    s.set_field(0, fx(I + 0.5))
+    s.set_field(1, np.full_like(I, 0.4))
+    s.set_field(2, fz(K + 0.5))
+    s.set_field(3, fz(K + 0.5))
+    s.set_field(4, (I + 0.5) ** 2 + (K + 0.5) ** 2 + (I + 0.5) * (K + 0.5))
+    s.set_field(5, fx(I + 0.5))
+    s.step(1)
+    want = {0: fx(I) + 0.5 * 0.25, 1: np.full_like(I, 0.4), 2: fz(K) - 0.25 * 0.25, 3: fz(K) - 0.25 * 0.25,
+            4: I ** 2 + K ** 2 + I * K + 0.5, 5: fx(I) + 0.5 * 0.25}
+    sl = (slice(3, nx - 2), slice(3, nz - 2))
+    for c in range(6):
+        got = s.gather_field(c)
+        assert np.abs(got[sl] - want[c][sl]).max() < 1e-12 * np.abs(want[c][sl]).max(), c
+    # the 'energy conserving' default keeps the copies on the Yee locations
+    s2 = orc.Sim(vacuum(nx, nz, solver, periodic=False))
+    s2.set_field(4, (I + 0.5) ** 2 + (K + 0.5) ** 2)
+    s2.step(1)
+    assert np.abs(s2.gather_field(4)[sl] - ((I + 0.5) ** 2 + (K + 0.5) ** 2)[sl]).max() < 1e-12
+
+
+@pytest.mark.parametrize("order", [1, 3])
+def test_gather_schemes_on_quadratic_field(orc, order):
+    """electrons at rest in a static E_x = X^2 (X = x/dx): one Boris step gives u_x = (q/m) dt E_x(particle).
+    The cubic B-spline reproduces linear functions and adds its variance 1/3 times f''/2; linear
+    interpolation adds t (1 - t), t the particle's offset from the sample below. The Yee-located ('energy
+    conserving') gather samples E_x at X = i + 1/2; the node-interpolated ('momentum conserving') one
+    samples the node values i^2 + 1/4 at X = i, the 1/4 from averaging the staggered samples"""
+    nx, nz = 20, 16
+    for scheme, shift, extra in (("energy", 0.5, 0.0), ("momentum", 0.0, 0.25)):
+        w = vacuum(nx, nz, "yee", periodic=False, order=order, gather=scheme)
+        w["plasma"] = {"n0": 1e10, "z_start_lab": 0.0, "ramp_lab": 0.0, "length_lab": 0.0, "ppc_x": 2, "ppc_z": 1,
+                       "ions": 0}
+        s = orc.Sim(w)
+        I = np.arange(nx + 1, dtype=float)[:, None] * np.ones((1, nz + 1))
+        s.set_field(0, (I + 0.5) ** 2)
+        s.step(1)
+        p = s.particles(0)
+        p = {k: v[p["alive"]] for k, v in p.items()}
+        assert p["x"].size > 20
+        X = p["x"] / s.dx
+        t = (X - shift) - np.floor(X - shift)
+        var = 1.0 / 3.0 if order == 3 else t * (1.0 - t)
+        qe, me = 1.602176634e-19, 9.1093837015e-31
+        ex = p["ux"] / (-qe / me * s.dt)
+        assert np.abs(ex - (X ** 2 + var + extra)).max() < 1e-9 * np.abs(X ** 2).max(), scheme
