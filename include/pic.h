@@ -98,7 +98,10 @@ typedef struct {
   int32_t tile_x, tile_z; /* particle tile in cells (x, z); 0 = default 8 x 32; at most 1024 cells */
   int32_t sort_every;     /* steps between particle sorts; 0 = default */
   int32_t ny;             /* 3D: cells along y (the PML occupies pml_cells on each side) */
-  int32_t reserved0;
+  int32_t gather_scheme;  /* 0: 'energy conserving' gather from the Yee locations (Sec. 5, the paper's
+                             default); 1: 'momentum conserving': the gather copies are first
+                             interpolated to the nodes (mean of the two, or four, nearest staggered
+                             values), then gathered with node-centred shapes; else PIC_EINVAL */
   double dy;              /* 3D: transverse cell along y [m] */
   int32_t filter_stride_set[4]; /* wide-band filter (Sec. 4.1): along each axis the passes (and the
                                    compensation pass) are applied at each of these strides in turn, e.g.

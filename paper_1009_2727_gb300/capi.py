@@ -53,7 +53,7 @@ class PicConfig(ctypes.Structure):
         ("shape_order", ctypes.c_int32), ("particle_guard", ctypes.c_int32), ("precision", ctypes.c_int32),
         ("moving_window", ctypes.c_int32), ("window_beta", ctypes.c_double),
         ("tile_x", ctypes.c_int32), ("tile_z", ctypes.c_int32), ("sort_every", ctypes.c_int32),
-        ("ny", ctypes.c_int32), ("reserved0", ctypes.c_int32), ("dy", ctypes.c_double),
+        ("ny", ctypes.c_int32), ("gather_scheme", ctypes.c_int32), ("dy", ctypes.c_double),
         ("filter_stride_set", ctypes.c_int32 * 4),
     ]
 

@@ -430,6 +430,47 @@ void launch_filter_axis(const G3& g, dim3 grid, const T* src, T* dst, int comp, 
   }
 }
 
+// 'momentum conserving' gather (Sec. 5): node values of the six gather copies, the mean of the nearest
+// staggered values along each half-integer axis of the component (two along one axis, four along two);
+// values off the grid count as zero. dst holds Ex, Ey, Ez, Bx, By, Bz, cs elements each.
+template <class T>
+__global__ void __launch_bounds__(128) k3_nodal(G3 g, const T* __restrict__ fE, const T* __restrict__ fB,
+                                                T* __restrict__ dst) {
+  const int k0 = blockIdx.x * blockDim.x * KPT + threadIdx.x, j = blockIdx.y, i = blockIdx.z;
+  const long sx = (long)(g.n[1] + 1) * g.ldz, sy = g.ldz;
+#pragma unroll
+  for (int kk = 0; kk < KPT; kk++) {
+    const int k = k0 + kk * blockDim.x;
+    if (k > g.n[2]) break;
+    const long p = nid(g, i, j, k);
+    const bool ok[3] = {i >= 1, j >= 1, k >= 1};
+    const long st[3] = {sx, sy, 1};
+#pragma unroll
+    for (int c = 0; c < 6; c++) {
+      // half-integer axes: E_q along q; B_q along the other two
+      const int h0 = c < 3 ? (c == 0) : (c != 3), h1 = c < 3 ? (c == 1) : (c != 4), h2 = c < 3 ? (c == 2) : (c != 5);
+      const T* F = (c < 3 ? fE + c * g.cs : fB + (c - 3) * g.cs) + p;
+      const int h[3] = {h0, h1, h2};
+      T acc = T(0);
+      int cnt = 0;
+#pragma unroll
+      for (int a = 0; a <= 1; a++)
+#pragma unroll
+        for (int b = 0; b <= 1; b++)
+#pragma unroll
+          for (int e = 0; e <= 1; e++) {
+            if ((a && !h[0]) || (b && !h[1]) || (e && !h[2])) continue;
+            // neighbour offset -1 + a along a half axis, 0 along an integer one
+            const int o0 = h[0] ? a - 1 : 0, o1 = h[1] ? b - 1 : 0, o2 = h[2] ? e - 1 : 0;
+            const bool in = (o0 == 0 || ok[0]) && (o1 == 0 || ok[1]) && (o2 == 0 || ok[2]);
+            acc += in ? F[o0 * st[0] + o1 * st[1] + o2 * st[2]] : T(0);
+            cnt++;
+          }
+      dst[c * g.cs + p] = cnt == 4 ? T(0.25) * acc : cnt == 2 ? T(0.5) * acc : acc;
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // particles
 template <class T>
@@ -455,7 +496,8 @@ __device__ __forceinline__ void shape_w(T t, T* w) {
 
 // fields at a particle: each component from its own Yee position, the same shape along every axis
 template <class T, int ORD>
-__device__ void gather3(const G3& g, const T* const* fE, const T* const* fB, const double* pos, T* E, T* B) {
+__device__ void gather3(const G3& g, const T* const* fE, const T* const* fB, const double* pos, T* E, T* B,
+                        bool nodal) {
   constexpr int NS = ORD == 3 ? 4 : 2;
   constexpr int SH = ORD == 3 ? 1 : 0;
   T w[3][2][NS];
@@ -472,7 +514,9 @@ __device__ void gather3(const G3& g, const T* const* fE, const T* const* fB, con
 #pragma unroll
   for (int c = 0; c < 6; c++) {
     const T* F = c < 3 ? fE[c] : fB[c - 3];
-    const int hx = c < 3 ? (c == 0) : (c != 3), hy = c < 3 ? (c == 1) : (c != 4), hz = c < 3 ? (c == 2) : (c != 5);
+    // Yee locations, or the nodes for the 'momentum conserving' gather
+    const int hx = nodal ? 0 : c < 3 ? (c == 0) : (c != 3), hy = nodal ? 0 : c < 3 ? (c == 1) : (c != 4),
+              hz = nodal ? 0 : c < 3 ? (c == 2) : (c != 5);
     T acc = T(0);
     for (int l0 = 0; l0 < NS; l0++) {
       const T w0 = w[0][hx][l0];
@@ -613,7 +657,7 @@ __global__ void k3_tile_scatter(Parts3<T> src, Parts3<T> dst, Tiles3 t, int n_ol
   dst.w[q] = src.w[j]; dst.id[q] = src.id[j]; dst.fl[q] = 1;
 }
 
-template <class T, int ORD>
+template <class T, int ORD, bool MC>
 __global__ void __launch_bounds__(256) k3_push_tiles(G3 g, Fld3<T> f, Parts3<T> p, Tiles3 t, Ctrl3* ctrl, T kq,
                                                      Cq3<T> cq) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -685,7 +729,9 @@ __global__ void __launch_bounds__(256) k3_push_tiles(G3 g, Fld3<T> f, Parts3<T> 
     T EB[6];
 #pragma unroll
     for (int c = 0; c < 6; c++) {
-      const int hx = c < 3 ? (c == 0) : (c != 3), hy = c < 3 ? (c == 1) : (c != 4), hz = c < 3 ? (c == 2) : (c != 5);
+      // Yee locations; every component at the nodes for the 'momentum conserving' gather (MC)
+      const int hx = MC ? 0 : c < 3 ? (c == 0) : (c != 3), hy = MC ? 0 : c < 3 ? (c == 1) : (c != 4),
+                hz = MC ? 0 : c < 3 ? (c == 2) : (c != 5);
       const T* F = sF + c * WN;
       T acc = T(0);
 #pragma unroll
@@ -1102,7 +1148,8 @@ __global__ void k3_beam_finish(Beam3<T> b, double t_now, double* acc) {
 }
 
 template <class T, int ORD>
-__global__ void k3_beam_push(G3 g, Fld3<T> f, Beam3<T> b, double tn, double tn1, const double* acc, T kq) {
+__global__ void k3_beam_push(G3 g, Fld3<T> f, Beam3<T> b, double tn, double tn1, const double* acc, T kq,
+                             int nodal) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= b.n) return;
   int fl = b.fl[j];
@@ -1126,7 +1173,7 @@ __global__ void k3_beam_push(G3 g, Fld3<T> f, Beam3<T> b, double tn, double tn1,
   }
   const double pos[3] = {b.x[j], b.y[j], b.z[j]};
   T E[3], B[3];
-  gather3<T, ORD>(g, f.fE, f.fB, pos, E, B);
+  gather3<T, ORD>(g, f.fE, f.fB, pos, E, B, nodal != 0);
   T u[3] = {b.ux[j], b.uy[j], b.uz[j]};
   boris3<T>(u, E, B, kq);
   const T gm = sqrt(T(1) + (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]) * T(1.0 / (kC * kC)));
@@ -1368,6 +1415,8 @@ struct Sim3 : Sim3Api {
   Pml3<T> pm;
   Taps3<T> taps;
   Cq3<T> cq_e;
+  bool nodal = false;     // 'momentum conserving' gather (pic_config.gather_scheme = 1)
+  T* nF = nullptr;        // its node values: Ex, Ey, Ez, Bx, By, Bz
   int P = 0;
   // particles
   Parts3<T> P2[2];
@@ -1481,6 +1530,11 @@ struct Sim3 : Sim3Api {
     g.cs = (long)(c->nx + 1) * (c->ny + 1) * g.ldz;
     const size_t cs = (size_t)g.cs;
     E = dal<T>(3 * cs); B = dal<T>(3 * cs); J = dal<T>(3 * cs); Ep = dal<T>(3 * cs); Eb = dal<T>(3 * cs);
+    nodal = c->gather_scheme == 1;
+    if (nodal) {
+      nF = dal<T>(6 * cs);
+      if (!nF) return fail(PIC_ENOMEM, "allocation failed");
+    }
     fE = dal<T>(3 * cs); fB = dal<T>(3 * cs); tmp = dal<T>(cs); tmp2 = dal<T>(cs);
     Es = dal<T>(6 * cs); Bs = dal<T>(6 * cs);
     ctrl = dal<Ctrl3>(1);
@@ -1543,8 +1597,10 @@ struct Sim3 : Sim3Api {
     tl.start = dal<int>(ntiles + 1);
     if (!tl.cnt || !tl.start) return fail(PIC_ENOMEM, "allocation failed");
     const int smem = (int)(9 * WN * sizeof(T));
-    cudaFuncSetAttribute(k3_push_tiles<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(k3_push_tiles<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k3_push_tiles<T, 3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k3_push_tiles<T, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k3_push_tiles<T, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k3_push_tiles<T, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     cudaEventCreate(&ev0);
     cudaEventCreate(&ev1);
     return cudaGetLastError() == cudaSuccess ? PIC_OK : fail(PIC_ECUDA, "CUDA error in 3D init");
@@ -1843,15 +1899,25 @@ struct Sim3 : Sim3Api {
     cudaMemsetAsync(J, 0, sizeof(T) * 3 * g.cs, s);
     Fld3<T> f;
     for (int c = 0; c < 3; c++) { f.fE[c] = fE + c * g.cs; f.fB[c] = fB + c * g.cs; f.J[c] = J + c * g.cs; }
+    if (nodal) {
+      // 'momentum conserving' gather: the copies interpolated to the nodes
+      k3_nodal<T><<<grid3(), 128, 0, s>>>(g, fE, fB, nF);
+      nl++;
+      for (int c = 0; c < 3; c++) { f.fE[c] = nF + c * g.cs; f.fB[c] = nF + (3 + c) * g.cs; }
+    }
     const T kq = T(-kQe * g.dt / (2.0 * kMe));
     if (loaded && count_ub > 0) {
       sort_tiles();
       const int smem = (int)(9 * WN * sizeof(T));
       tbeg(0);
-      if (cfg.shape_order == 3)
-        k3_push_tiles<T, 3><<<ntiles, 256, smem, s>>>(g, f, P2[cur], tl, ctrl, kq, cq_e);
+      if (cfg.shape_order == 3 && !nodal)
+        k3_push_tiles<T, 3, false><<<ntiles, 256, smem, s>>>(g, f, P2[cur], tl, ctrl, kq, cq_e);
+      else if (cfg.shape_order == 3)
+        k3_push_tiles<T, 3, true><<<ntiles, 256, smem, s>>>(g, f, P2[cur], tl, ctrl, kq, cq_e);
+      else if (!nodal)
+        k3_push_tiles<T, 1, false><<<ntiles, 256, smem, s>>>(g, f, P2[cur], tl, ctrl, kq, cq_e);
       else
-        k3_push_tiles<T, 1><<<ntiles, 256, smem, s>>>(g, f, P2[cur], tl, ctrl, kq, cq_e);
+        k3_push_tiles<T, 1, true><<<ntiles, 256, smem, s>>>(g, f, P2[cur], tl, ctrl, kq, cq_e);
       nl++;
       tend(0);
     }
@@ -1864,9 +1930,9 @@ struct Sim3 : Sim3Api {
     }
     if (has_beam) {
       if (cfg.shape_order == 3)
-        k3_beam_push<T, 3><<<nblk(bm.n, 128), 128, 0, s>>>(g, f, bm, tn, tn1, bacc, kq);
+        k3_beam_push<T, 3><<<nblk(bm.n, 128), 128, 0, s>>>(g, f, bm, tn, tn1, bacc, kq, nodal ? 1 : 0);
       else
-        k3_beam_push<T, 1><<<nblk(bm.n, 128), 128, 0, s>>>(g, f, bm, tn, tn1, bacc, kq);
+        k3_beam_push<T, 1><<<nblk(bm.n, 128), 128, 0, s>>>(g, f, bm, tn, tn1, bacc, kq, nodal ? 1 : 0);
       nl++;
     }
     // 3. antenna: the moving partners' displacement G(x, y) D_n -> G D_{n+1}

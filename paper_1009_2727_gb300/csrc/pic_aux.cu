@@ -184,7 +184,8 @@ __device__ T gather_global(const T* F, const GridP& g, int order, double X, doub
 }
 
 template <class T>
-__global__ void k_beam_push(GridP g, FieldPtrs<T> f, Beam<T> b, int order, double tn, double tn1, const double* acc) {
+__global__ void k_beam_push(GridP g, FieldPtrs<T> f, Beam<T> b, int order, double tn, double tn1, int nodal,
+                            const double* acc) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= b.n) return;
   int fl = b.flag[j];
@@ -207,12 +208,16 @@ __global__ void k_beam_push(GridP g, FieldPtrs<T> f, Beam<T> b, int order, doubl
   }
   const double x = b.x[j], z = b.z[j];
   const double X = x / g.dx, Z = (z - g.z0) / g.dz;
-  const double E[3] = {(double)gather_global<T>(f.fE[0], g, order, X, Z, 0.5, 0.0),
-                       (double)gather_global<T>(f.fE[1], g, order, X, Z, 0.0, 0.0),
-                       (double)gather_global<T>(f.fE[2], g, order, X, Z, 0.0, 0.5)};
-  const double B[3] = {(double)gather_global<T>(f.fB[0], g, order, X, Z, 0.0, 0.5),
-                       (double)gather_global<T>(f.fB[1], g, order, X, Z, 0.5, 0.5),
-                       (double)gather_global<T>(f.fB[2], g, order, X, Z, 0.5, 0.0)};
+  // Yee locations, or the node values of the 'momentum conserving' gather (offsets 0)
+  const double h = nodal ? 0.0 : 0.5;
+  const T* const* gE = nodal ? f.nE : f.fE;
+  const T* const* gB = nodal ? f.nB : f.fB;
+  const double E[3] = {(double)gather_global<T>(gE[0], g, order, X, Z, h, 0.0),
+                       (double)gather_global<T>(gE[1], g, order, X, Z, 0.0, 0.0),
+                       (double)gather_global<T>(gE[2], g, order, X, Z, 0.0, h)};
+  const double B[3] = {(double)gather_global<T>(gB[0], g, order, X, Z, 0.0, h),
+                       (double)gather_global<T>(gB[1], g, order, X, Z, h, h),
+                       (double)gather_global<T>(gB[2], g, order, X, Z, h, 0.0)};
   const T k = T(-kQe * g.dt / (2.0 * kMe));
   const T ic2 = T(1.0 / (kC * kC));
   T ux = b.ux[j], uy = b.uy[j], uz = b.uz[j];
@@ -560,10 +565,38 @@ void launch_beam_init(Beam<T> b, const double* lx, const double* lz, const doubl
 }
 
 template <class T>
-void launch_beam_push(const GridP& g, const FieldPtrs<T>& f, Beam<T> b, int order, double tn, double tn1, double,
+void launch_beam_push(const GridP& g, const FieldPtrs<T>& f, Beam<T> b, int order, double tn, double tn1, int nodal,
                       const double* scratch, cudaStream_t s) {
   if (b.n <= 0) return;
-  k_beam_push<T><<<(b.n + 127) / 128, 128, 0, s>>>(g, f, b, order, tn, tn1, scratch);
+  k_beam_push<T><<<(b.n + 127) / 128, 128, 0, s>>>(g, f, b, order, tn, tn1, nodal, scratch);
+}
+
+// 'momentum conserving' gather (Sec. 5): each gather copy interpolated to the nodes, the mean of its two
+// nearest values along each half-integer axis (four for B_y, staggered along x and z); values off the
+// grid count as zero
+template <class T>
+__global__ void k_nodal(GridP g, FieldPtrs<T> f) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y;
+  if (k > g.nz) return;
+  const long q = (long)i * g.ld + k;
+  const bool il = i >= 1, kl = k >= 1;
+  const long qx = q - g.ld, qz = q - 1, qxz = q - g.ld - 1;
+  const T* Ex = f.fE[0];
+  const T* Ez = f.fE[2];
+  const T* Bx = f.fB[0];
+  const T* By = f.fB[1];
+  const T* Bz = f.fB[2];
+  f.nE[0][q] = T(0.5) * ((il ? Ex[qx] : T(0)) + Ex[q]);
+  f.nE[1][q] = f.fE[1][q];
+  f.nE[2][q] = T(0.5) * ((kl ? Ez[qz] : T(0)) + Ez[q]);
+  f.nB[0][q] = T(0.5) * ((kl ? Bx[qz] : T(0)) + Bx[q]);
+  f.nB[1][q] = T(0.25) * ((il && kl ? By[qxz] : T(0)) + (kl ? By[qz] : T(0)) + (il ? By[qx] : T(0)) + By[q]);
+  f.nB[2][q] = T(0.5) * ((il ? Bz[qx] : T(0)) + Bz[q]);
+}
+
+template <class T>
+void launch_nodal(const GridP& g, const FieldPtrs<T>& f, cudaStream_t s) {
+  k_nodal<T><<<dim3((g.nz + 1 + 127) / 128, g.nx + 1), 128, 0, s>>>(g, f);
 }
 
 template <class T>
@@ -637,8 +670,9 @@ void launch_shift_particles(const GridP& g, Particles<T> p, const Ctrl* ctrl, in
   template void launch_antenna<T>(const GridP&, T*, const double*, const AntennaStep&, cudaStream_t);           \
   template void launch_beam_init<T>(Beam<T>, const double*, const double*, const double*, const double*,          \
                                     const double*, double, double, double, double, double, double*, cudaStream_t); \
-  template void launch_beam_push<T>(const GridP&, const FieldPtrs<T>&, Beam<T>, int, double, double, double,      \
+  template void launch_beam_push<T>(const GridP&, const FieldPtrs<T>&, Beam<T>, int, double, double, int,         \
                                     const double*, cudaStream_t);                                                 \
+  template void launch_nodal<T>(const GridP&, const FieldPtrs<T>&, cudaStream_t);                                 \
   template void launch_btd<T>(const GridP&, const FieldPtrs<T>&, int, int, int, int, const int*, const double*,   \
                               const double*, double, double, double, T*, int*, cudaStream_t);                     \
   template void launch_rho<T>(const GridP&, Particles<T>, const Ctrl*, int, int, double, double*, cudaStream_t);  \

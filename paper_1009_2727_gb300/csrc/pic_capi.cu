@@ -151,6 +151,7 @@ struct Sim : SimBase {
   double* stage = nullptr;    // (nx+1)*(nz+1) doubles
   size_t stage_n = 0;
   // timing
+  bool nodal = false;   // 'momentum conserving' gather (pic_config.gather_scheme = 1)
   bool timing = false;
   int timing_which = 0;
   std::vector<cudaEvent_t> ev;
@@ -192,6 +193,8 @@ struct Sim : SimBase {
     bool ok = block(f.E) && block(f.Eo) && block(f.B) && block(f.J) && block(f.Jn) && block(f.Bavg);
     if (friedman) ok = ok && block(f.Eb) && block(f.Ebn);
     if (filt_gather) ok = ok && block(f.fE) && block(f.fB);
+    nodal = cf.gather_scheme == 1;
+    if (nodal) ok = ok && block(f.nE) && block(f.nB);
     if (!ok) return c->fail(PIC_ENOMEM, "field allocation failed");
     if (cf.pml_cells > 0) {
       f.Byx = grid(); f.Byz = grid(); f.Eyx = grid(); f.Eyz = grid();
@@ -585,10 +588,11 @@ struct Sim : SimBase {
     // 1. Faraday + Friedman + PML-B (B^{n-1/2} -> B^{n+1/2}, Bavg)
     tstart(1);
     launch_faraday<T>(g, f, pt, h.a2, h.b2, cf.theta, friedman, c->stream);
-    // 2. gather copies
+    // 2. gather copies (interpolated to the nodes for the 'momentum conserving' gather)
     launch_filter_fields<T>(g, f, fs, filt_gather, tmaps, ctrl, c->stream);
+    if (nodal) launch_nodal<T>(g, f, c->stream);
     tstop(1);
-    c->launches += 1 + (filt_gather ? 1 : 0);
+    c->launches += 1 + (filt_gather ? 1 : 0) + (nodal ? 1 : 0);
     // ion rows live during this step: those inside the particle domain at t^n
     long long mlo = std::max(row_first, (long long)std::ceil((zlo_prev + h.beta * kC * tn) / ip.h - 0.5));
     if (step == 0) mlo = row_first;
@@ -599,13 +603,13 @@ struct Sim : SimBase {
       float fr1_fz;
       frame_of(frame_shift(step + 1), fr1_sz, fr1_fz);
       launch_push<T>(g, f, P, chunks, ctrl, cf.shape_order, push_grid, smem_nodes, -kQe, kMe, c->hg.gamma, c->hg.beta,
-                     fr1_sz, fr1_fz, (pairs && ions) ? 1 : 0, (int)mlo, c->stream);
+                     fr1_sz, fr1_fz, (pairs && ions) ? 1 : 0, (int)mlo, nodal ? 1 : 0, c->stream);
       tstop(0);
       c->launches++;
     }
     set_frame(step + 1);   // the particles now hold their t^{n+1} positions
     if (beam.n > 0) {
-      launch_beam_push<T>(g, f, beam, cf.shape_order, tn, tn1, 0.0, beam_scratch, c->stream);
+      launch_beam_push<T>(g, f, beam, cf.shape_order, tn, tn1, nodal ? 1 : 0, beam_scratch, c->stream);
       c->launches++;
     }
     // 4. antenna
@@ -899,6 +903,7 @@ int pic_init(const pic_config* cfg, pic_alloc_fn alloc, pic_free_fn free_fn, voi
   *out = nullptr;
   if (!cfg || cfg->struct_size != sizeof(pic_config) || cfg->version != PIC_API_VERSION) return PIC_EINVAL;
   if (cfg->dim != 2 && cfg->dim != 3) return PIC_EINVAL;
+  if (cfg->gather_scheme != 0 && cfg->gather_scheme != 1) return PIC_EINVAL;
   // the composed filter: at most 16 passes per stride and a halo of at most FILTER_HMAX cells; a stride set
   // is non-negative and 0-terminated
   FilterSpec fs0{};

@@ -75,6 +75,8 @@ struct FieldPtrs {
   T* Bavg[3];   // (B^{n-1/2} + B^{n+1/2})/2
   T* fE[3];     // gather copies
   T* fB[3];
+  T* nE[3];     // 'momentum conserving' gather: the copies interpolated to the nodes (3 x cs each, contiguous)
+  T* nB[3];
   T* Byx; T* Byz; T* Eyx; T* Eyz;  // split PML parts (full-size, used in the PML only)
 };
 
@@ -237,7 +239,7 @@ void launch_ampere(const GridP& g, const FieldPtrs<T>& f, const PmlTabs& pt, con
 template <class T>
 void launch_push(const GridP& g, const FieldPtrs<T>& f, Particles<T> p, Chunk* chunks, Ctrl* ctrl, int order,
                  int grid_blocks, int smem_nodes, double q, double m, double gamma_b, double beta_b, int fr1_sz,
-                 float fr1_fz, int pairs, int mlo, cudaStream_t s);
+                 float fr1_fz, int pairs, int mlo, int nodal, cudaStream_t s);
 
 struct SortBufs {
   int* cell_cnt;       // ntiles*tx*tz, cells in tile-major order: particles per cell
@@ -299,8 +301,11 @@ void launch_beam_init(Beam<T> b, const double* lx, const double* lz, const doubl
                       const double* luz, double t_lab, double z_plane, double gamma, double beta, double t_now,
                       double* scratch, cudaStream_t s);
 template <class T>
-void launch_beam_push(const GridP& g, const FieldPtrs<T>& f, Beam<T> b, int order, double tn, double tn1,
-                      double vbar_dev_unused, const double* scratch, cudaStream_t s);
+void launch_beam_push(const GridP& g, const FieldPtrs<T>& f, Beam<T> b, int order, double tn, double tn1, int nodal,
+                      const double* scratch, cudaStream_t s);
+// 'momentum conserving' gather (Sec. 5): f.nE / f.nB = the gather copies interpolated to the nodes
+template <class T>
+void launch_nodal(const GridP& g, const FieldPtrs<T>& f, cudaStream_t s);
 
 template <class T>
 void launch_btd(const GridP& g, const FieldPtrs<T>& f, int which, int post, int r0, int r1, const int* order_idx,

@@ -242,7 +242,7 @@ __device__ __forceinline__ void ion_jz(T* Jb, long cs, int ld, int ox, int oz, c
 // blocks (component stride cs) addressed as (i - ox)*ld + (k - oz). With SMEM
 // the fields are the shared-memory window: pairs (Ex, Bz) and (Ez, Bx), which
 // share a Yee location, then Ey and By, each block cs elements long (Bb unused).
-template <class T, int ORDER, bool SMEM>
+template <class T, int ORDER, bool SMEM, bool MC = false>
 __device__ __forceinline__ void push_one(const T* __restrict__ Eb, const T* __restrict__ Bb, T* Jb, long cs, int ld,
                                          int ox, int oz, Particles<T>& p, int pi, const PushConst& pc, int& bx0,
                                          int& bx1, int& bz0, int& bz1) {
@@ -289,9 +289,26 @@ __device__ __forceinline__ void push_one(const T* __restrict__ Eb, const T* __re
   T ux = p.ux[pi], uy = p.uy[pi], uz = p.uz[pi];
   T wxi[NG], wzi[NG], wxh[NG], wzh[NG];
   wts<T, ORDER>(tx, wxi); wts<T, ORDER>(tz, wzi);
+  T Ex, Ey, Ez, Bx, By, Bz;
+  if constexpr (MC) {
+    // 'momentum conserving' gather (Sec. 5): every gather copy already holds node values
+    if constexpr (SMEM) {
+      typedef typename Vec2<T>::type V2;
+      interp2<T, ORDER>(reinterpret_cast<const V2*>(Eb), ld, ox, oz, fx, fz, wxi, wzi, Ex, Bz);
+      interp2<T, ORDER>(reinterpret_cast<const V2*>(Eb + 2 * cs), ld, ox, oz, fx, fz, wxi, wzi, Ez, Bx);
+      Ey = interp<T, ORDER>(Eb + 4 * cs, ld, ox, oz, fx, fz, wxi, wzi);
+      By = interp<T, ORDER>(Eb + 5 * cs, ld, ox, oz, fx, fz, wxi, wzi);
+    } else {
+      Ex = interp<T, ORDER>(Eb, ld, ox, oz, fx, fz, wxi, wzi);
+      Ey = interp<T, ORDER>(Eb + cs, ld, ox, oz, fx, fz, wxi, wzi);
+      Ez = interp<T, ORDER>(Eb + 2 * cs, ld, ox, oz, fx, fz, wxi, wzi);
+      Bx = interp<T, ORDER>(Bb, ld, ox, oz, fx, fz, wxi, wzi);
+      By = interp<T, ORDER>(Bb + cs, ld, ox, oz, fx, fz, wxi, wzi);
+      Bz = interp<T, ORDER>(Bb + 2 * cs, ld, ox, oz, fx, fz, wxi, wzi);
+    }
+  } else {
   wts<T, ORDER>(txh, wxh); wts<T, ORDER>(tzh, wzh);
   // energy-conserving gather from each component's Yee location
-  T Ex, Ey, Ez, Bx, By, Bz;
   if constexpr (SMEM) {
     typedef typename Vec2<T>::type V2;
     interp2<T, ORDER>(reinterpret_cast<const V2*>(Eb), ld, ox, oz, fxh, fz, wxh, wzi, Ex, Bz);
@@ -305,6 +322,7 @@ __device__ __forceinline__ void push_one(const T* __restrict__ Eb, const T* __re
     Bx = interp<T, ORDER>(Bb, ld, ox, oz, fx, fzh, wxi, wzh);
     By = interp<T, ORDER>(Bb + cs, ld, ox, oz, fxh, fzh, wxh, wzh);
     Bz = interp<T, ORDER>(Bb + 2 * cs, ld, ox, oz, fxh, fz, wxh, wzi);
+  }
   }
   // relativistic Boris push
   T k;
@@ -489,7 +507,7 @@ __device__ __forceinline__ bool particle_cell(const Particles<T>& p, int pi, con
 // global-memory path with an index guard: a particle whose stencil would leave
 // the arrays (only possible for corrupted or non-finite state) is removed and
 // flagged instead of being pushed.
-template <class T, int ORDER>
+template <class T, int ORDER, bool MC>
 __device__ __noinline__ void push_global_guarded(const T* gE, const T* gB, T* gJ, const GridP& g, Particles<T>& p,
                                                  int pi, const PushConst& pc, Ctrl* ctrl, int& bx0, int& bx1,
                                                  int& bz0, int& bz1) {
@@ -503,10 +521,10 @@ __device__ __noinline__ void push_global_guarded(const T* gE, const T* gB, T* gJ
     atomicOr(&ctrl->status, fin ? ST_OUTSIDE : ST_NAN);
     return;
   }
-  push_one<T, ORDER, false>(gE, gB, gJ, g.cs, g.ld, 0, 0, p, pi, pc, bx0, bx1, bz0, bz1);
+  push_one<T, ORDER, false, MC>(gE, gB, gJ, g.cs, g.ld, 0, 0, p, pi, pc, bx0, bx1, bz0, bz1);
 }
 
-template <class T, int ORDER>
+template <class T, int ORDER, bool MC>
 __global__ void __launch_bounds__(PB_THREADS, 5) k_push(GridP g, const T* gE, const T* gB, T* gJ, Particles<T> p,
                                                      Chunk* chunks, Ctrl* ctrl, int cap_nodes, PushConst pc) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -588,10 +606,10 @@ __global__ void __launch_bounds__(PB_THREADS, 5) k_push(GridP g, const T* gE, co
           }
         }
         if (inbox)
-          push_one<T, ORDER, true>(sm, nullptr, sm + 6 * cap_nodes, cap_nodes, lds, wx0, wz0, p, pi, pc, bx0, bx1,
-                                   bz0, bz1);
+          push_one<T, ORDER, true, MC>(sm, nullptr, sm + 6 * cap_nodes, cap_nodes, lds, wx0, wz0, p, pi, pc, bx0,
+                                       bx1, bz0, bz1);
         else
-          push_global_guarded<T, ORDER>(gE, gB, gJ, g, p, pi, pc, ctrl, bx0, bx1, bz0, bz1);
+          push_global_guarded<T, ORDER, MC>(gE, gB, gJ, g, p, pi, pc, ctrl, bx0, bx1, bz0, bz1);
       }
       __syncthreads();
       for (int e = threadIdx.x; e < nn; e += blockDim.x) {
@@ -607,7 +625,7 @@ __global__ void __launch_bounds__(PB_THREADS, 5) k_push(GridP g, const T* gE, co
     } else {
       if (threadIdx.x == 0) atomicAdd(&ctrl->overflow_chunks, 1);
       for (int pi = ch.p0 + threadIdx.x; pi < ch.p1; pi += blockDim.x)
-        push_global_guarded<T, ORDER>(gE, gB, gJ, g, p, pi, pc, ctrl, bx0, bx1, bz0, bz1);
+        push_global_guarded<T, ORDER, MC>(gE, gB, gJ, g, p, pi, pc, ctrl, bx0, bx1, bz0, bz1);
     }
     // bounding box of the chunk's live particles for the next step
     bx0 = __reduce_min_sync(0xffffffffu, bx0); bx1 = __reduce_max_sync(0xffffffffu, bx1);
@@ -882,7 +900,7 @@ __global__ void k_add_counts(Ctrl* ctrl, int dcount, int dchunks) {
 template <class T>
 void launch_push(const GridP& g, const FieldPtrs<T>& f, Particles<T> p, Chunk* chunks, Ctrl* ctrl, int order,
                  int grid_blocks, int smem_nodes, double q, double m, double gamma_b, double beta_b, int fr1_sz,
-                 float fr1_fz, int pairs, int mlo, cudaStream_t s) {
+                 float fr1_fz, int pairs, int mlo, int nodal, cudaStream_t s) {
   PushConst pc;
   pc.dx = g.dx; pc.dz = g.dz; pc.dt = g.dt; pc.z0 = g.z0;
   pc.xlo = g.gx_lo * g.dx; pc.xhi = g.gx_hi * g.dx;
@@ -904,12 +922,21 @@ void launch_push(const GridP& g, const FieldPtrs<T>& f, Particles<T> p, Chunk* c
   while ((1 << pc.lpz) < g.il_ppcz) pc.lpz++;
   const size_t sm = (size_t)9 * smem_nodes * sizeof(T);
   cudaMemsetAsync(&ctrl->next_chunk, 0, sizeof(int), s);
-  if (order == 3) {
-    cudaFuncSetAttribute(k_push<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_push<T, 3><<<grid_blocks, PB_THREADS, sm, s>>>(g, f.fE[0], f.fB[0], f.J[0], p, chunks, ctrl, smem_nodes, pc);
+  // 'momentum conserving' gather: the node-interpolated copies; else the Yee-located gather copies
+  const T* gE = nodal ? f.nE[0] : f.fE[0];
+  const T* gB = nodal ? f.nB[0] : f.fB[0];
+  if (order == 3 && !nodal) {
+    cudaFuncSetAttribute(k_push<T, 3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_push<T, 3, false><<<grid_blocks, PB_THREADS, sm, s>>>(g, gE, gB, f.J[0], p, chunks, ctrl, smem_nodes, pc);
+  } else if (order == 3) {
+    cudaFuncSetAttribute(k_push<T, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_push<T, 3, true><<<grid_blocks, PB_THREADS, sm, s>>>(g, gE, gB, f.J[0], p, chunks, ctrl, smem_nodes, pc);
+  } else if (!nodal) {
+    cudaFuncSetAttribute(k_push<T, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_push<T, 1, false><<<grid_blocks, PB_THREADS, sm, s>>>(g, gE, gB, f.J[0], p, chunks, ctrl, smem_nodes, pc);
   } else {
-    cudaFuncSetAttribute(k_push<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_push<T, 1><<<grid_blocks, PB_THREADS, sm, s>>>(g, f.fE[0], f.fB[0], f.J[0], p, chunks, ctrl, smem_nodes, pc);
+    cudaFuncSetAttribute(k_push<T, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_push<T, 1, true><<<grid_blocks, PB_THREADS, sm, s>>>(g, gE, gB, f.J[0], p, chunks, ctrl, smem_nodes, pc);
   }
 }
 
@@ -918,20 +945,20 @@ int push_occupancy(int order, bool dbl, int smem_nodes) {
   if (dbl) {
     size_t sm = (size_t)9 * smem_nodes * sizeof(double);
     if (order == 3) {
-      cudaFuncSetAttribute(k_push<double, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_push<double, 3>, PB_THREADS, sm);
+      cudaFuncSetAttribute(k_push<double, 3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_push<double, 3, false>, PB_THREADS, sm);
     } else {
-      cudaFuncSetAttribute(k_push<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_push<double, 1>, PB_THREADS, sm);
+      cudaFuncSetAttribute(k_push<double, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_push<double, 1, false>, PB_THREADS, sm);
     }
   } else {
     size_t sm = (size_t)9 * smem_nodes * sizeof(float);
     if (order == 3) {
-      cudaFuncSetAttribute(k_push<float, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_push<float, 3>, PB_THREADS, sm);
+      cudaFuncSetAttribute(k_push<float, 3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_push<float, 3, false>, PB_THREADS, sm);
     } else {
-      cudaFuncSetAttribute(k_push<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_push<float, 1>, PB_THREADS, sm);
+      cudaFuncSetAttribute(k_push<float, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_push<float, 1, false>, PB_THREADS, sm);
     }
   }
   return nb > 0 ? nb : 1;
@@ -979,7 +1006,7 @@ void launch_add_counts(Ctrl* ctrl, int dcount, int dchunks, cudaStream_t s) {
 
 #define INST(T)                                                                                                 \
   template void launch_push<T>(const GridP&, const FieldPtrs<T>&, Particles<T>, Chunk*, Ctrl*, int, int, int,   \
-                               double, double, double, double, int, float, int, int, cudaStream_t);             \
+                               double, double, double, double, int, float, int, int, int, cudaStream_t);        \
   template void launch_sort<T>(const GridP&, Particles<T>, Particles<T>, SortBufs, Chunk*, Ctrl*, int, int, int,\
                                cudaStream_t);                                                                   \
   template void launch_inject<T>(const GridP&, Particles<T>, Chunk*, Ctrl*, const InjectP&, int, int, cudaStream_t);

@@ -48,6 +48,7 @@ def make_config(w: dict, precision: int, tile=None, sort_every: int = 0) -> capi
     c.filter_compensate = int(w.get("filter_compensate", 0))
     for q, v in enumerate(list(w.get("filter_strides", []))[:4]):
         c.filter_stride_set[q] = int(v)
+    c.gather_scheme = {"energy": 0, "momentum": 1}[w.get("gather", "energy")]
     c.filter_J = int(w.get("filter_J", 0))
     c.filter_gather = int(w.get("filter_gather", 0))
     c.shape_order = int(w.get("order", 3))

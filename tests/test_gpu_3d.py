@@ -107,8 +107,9 @@ def test_3d_linear_shapes_and_yee_fp64(Sim, orc):
     check_particles(g, o, TOL64)
 
 
-def test_3d_beam_and_lab_samples_fp64(Sim, orc):
-    w = case()
+@pytest.mark.parametrize("gather", ["energy", "momentum"])
+def test_3d_beam_and_lab_samples_fp64(Sim, orc, gather):
+    w = case(gather=gather)
     rng = np.random.default_rng(12)
     n = 64
     x = w["laser"]["x_center"] + rng.normal(0, 1e-6, n)
@@ -176,6 +177,19 @@ def test_3d_wide_band_filter_strides_fp64(Sim, orc):
     g.sync()
     assert o.info()["guard"] == 11
     assert np.abs(o.field(1)).max() > 1e10
+    check_fields(g, o, TOL64)
+    check_particles(g, o, TOL64)
+
+
+@pytest.mark.parametrize("order", [3, 1])
+def test_3d_momentum_conserving_gather_fp64(Sim, orc, order):
+    """'momentum conserving' gather (Sec. 5) in 3D: node-interpolated gather copies, node-centred shapes"""
+    w = case(order=order, gather="momentum")
+    g = Sim(w, precision="fp64")
+    o = orc.Sim3(w)
+    g.step(30)
+    o.step(30)
+    g.sync()
     check_fields(g, o, TOL64)
     check_particles(g, o, TOL64)
 

@@ -153,6 +153,29 @@ def test_wide_band_filter_strides_fp64(Sim, orc):
     check_particles(g, o, TOL64)
 
 
+@pytest.mark.parametrize("order", [3, 1])
+def test_momentum_conserving_gather_fp64(Sim, orc, order):
+    """'momentum conserving' gather (Sec. 5): the gather copies interpolated to the nodes, then gathered with
+    node-centred shapes, on the parity workload with the filter on J and on the gathered fields"""
+    w = W.shrink(W.parity_2d(), 48, 160, order=order, gather="momentum")
+    g, o = run_pair(Sim, orc, w, 40)
+    check_fields(g, o, TOL64)
+    check_particles(g, o, TOL64)
+    # the run differs from the Yee-located gather
+    e = Sim(W.shrink(W.parity_2d(), 48, 160, order=order), precision="fp64")
+    e.step(40)
+    e.sync()
+    assert rel(e.field(2), g.field(2)) > 1e-6
+
+
+def test_momentum_conserving_gather_stage_mixed(Sim, orc):
+    """the mixed path with the node-interpolated gather on the stage numerics, against the FP64 oracle"""
+    w = W.shrink(W.stage_2d(), 96, 320, gather="momentum")
+    w["plasma"]["z_start_lab"] = 0.0
+    g, o = run_pair(Sim, orc, w, 60, precision="mixed")
+    check_fields(g, o, TOLMIX)
+
+
 def test_parity_2d_mixed(Sim, orc):
     w = W.shrink(W.parity_2d(), 48, 160)
     g, o = run_pair(Sim, orc, w, 40, precision="mixed")
@@ -170,8 +193,9 @@ def test_moving_window_lab_frame_fp64(Sim, orc):
     check_particles(g, o, TOL64)
 
 
-def test_test_beam_and_lab_stations_fp64(Sim, orc):
-    w = W.shrink(W.parity_2d(), 48, 200)
+@pytest.mark.parametrize("gather", ["energy", "momentum"])
+def test_test_beam_and_lab_stations_fp64(Sim, orc, gather):
+    w = W.shrink(W.parity_2d(), 48, 200, gather=gather)
     w["plasma"] = None
     x, z, ux, uy, uz = W.lab_beam(64, seed=3, gamma_b=20.0, R_b=1e-6, L_b=1e-6, z_c=0.0, x_c=24 * 1.98e-6)
     beam = {"x": x, "z": z, "ux": ux, "uy": uy, "uz": uz, "t_lab": 0.0, "z_plane_lab": 100e-6}
