@@ -377,6 +377,21 @@ def run_surrogate(args):
     return 0
 
 
+def run_dt_scan(args):
+    """the time-step scan of the instability (Sec. 5) for the Yee-located and the node-interpolated gather"""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1009_2727_gb300 import stability
+    t0 = time.time()
+    runs = stability.dt_scan((0.5, 0.55, 0.6, 0.65, 0.7071, 0.75, 0.8))
+    line = {"metric": "high_k_Ez_power", "unit": "(V/m)^2 summed over k dz > pi/4", "higher_is_better": False,
+            "data": "synthetic", "config": {"workload": "stage_2d_4096x256_g13", "precision": "mixed",
+                                            "times": "t = m dz/(sqrt(2) c), m = 1200, 1800, 2400"},
+            "runs": runs, "wall_s": time.time() - t0}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def wide_band(w, strides, three):
     """the stage with a wide-band filter (its passes + compensation at each stride); the default particle
     guard grows with the halo, so the antenna moves to 4 cells inside the particle domain"""
@@ -412,6 +427,10 @@ def main():
                     help="label N stage runs, train the stage surrogate on them and time its serving")
     ap.add_argument("--dim", type=int, default=2, choices=[2, 3],
                     help="3: the 3D stage (1024 x 128 x 128 cells, gamma 30) instead of the 2D one")
+    ap.add_argument("--gather", default="energy", choices=["energy", "momentum"],
+                    help="momentum: the 'momentum conserving' gather (fields interpolated to the nodes first)")
+    ap.add_argument("--dt-scan", action="store_true",
+                    help="instability level (high-k E_z power at fixed times) against c dt/dz for both gather schemes")
     ap.add_argument("--filter-strides", default="",
                     help="wide-band filter, e.g. 1,2,4: the stage's passes + compensation at each stride "
                          "(the antenna moves past the wider particle guard)")
@@ -424,10 +443,13 @@ def main():
         w = W.shrink3(w, w["nx"], w["ny"], args.nz) if three else W.shrink(w, w["nx"], args.nz)
     w["order"] = args.order
     w["precision"] = args.precision
+    w["gather"] = args.gather
     if args.filter_strides:
         w = wide_band(w, [int(v) for v in args.filter_strides.split(",")], three)
     if args.impl == "reference":
         return run_reference(args, w)
+    if args.dt_scan:
+        return run_dt_scan(args)
     if args.ensemble:
         return run_ensemble(args)
     if args.surrogate:
@@ -538,6 +560,7 @@ def main():
                            " at each stride of S(" + ":".join(str(v) for v in w["filter_strides"]) + ")"
                            if w.get("filter_strides") else ""),
                        "shape_order": args.order, "precision": args.precision, "electrons": int(n_avg),
+                       "gather": args.gather,
                        "cell_steps_per_s": w["nx"] * w.get("ny", 1) * w["nz"] * args.steps * ws / (ms_max * 1e-3),
                        "l2": "inputs larger than L2 (particle arrays ~0.5 GB, fields ~2.6 GB)" if three else
                              "inputs larger than L2 (particle arrays ~0.9 GB)",
