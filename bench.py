@@ -421,8 +421,12 @@ def main():
     ap.add_argument("--sort-every", type=int, default=0, help="steps between particle sorts (0: the library default)")
     ap.add_argument("--ensemble", type=int, default=0,
                     help="time N uneven runs advanced together (pic_ensemble_*) instead of the stage")
-    ap.add_argument("--tune", default="", choices=["", "runs", "ensemble"],
-                    help="with --ensemble: layouts from pic_autotune per run, or from pic_ensemble_autotune")
+    ap.add_argument("--tune", default="", choices=["", "runs", "ensemble", "layout"],
+                    help="with --ensemble: layouts from pic_autotune per run, or from pic_ensemble_autotune; "
+                         "layout (default without --ensemble): the single run's tile and sort cadence from "
+                         "pic_autotune, before the timed steps")
+    ap.add_argument("--no-tune", action="store_true", help="the library's default particle layout")
+    ap.add_argument("--tile", default="", help="fixed particle tile x,z (no tuning), e.g. 8,16")
     ap.add_argument("--surrogate", type=int, default=0,
                     help="label N stage runs, train the stage surrogate on them and time its serving")
     ap.add_argument("--dim", type=int, default=2, choices=[2, 3],
@@ -469,7 +473,19 @@ def main():
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_oracle_sample3(w) if three else cpu_oracle_sample(w)
 
-    sim = Simulation(w, precision=args.precision, sort_every=args.sort_every)
+    tuned = None
+    if args.tile:
+        tl = tuple(int(v) for v in args.tile.split(","))
+        tuned = {"tile": tl, "sort_every": args.sort_every, "wall_s": 0.0, "trials": []}
+        sim = Simulation(w, precision=args.precision, tile=tl, sort_every=args.sort_every)
+    elif args.tune in ("", "layout") and not args.no_tune and not three and not args.sort_every:
+        from paper_1009_2727_gb300.pic import autotune
+        t_tune = time.perf_counter()
+        tuned = autotune(w, precision=args.precision)
+        tuned["wall_s"] = time.perf_counter() - t_tune
+        sim = Simulation(w, precision=args.precision, tile=tuned["tile"], sort_every=tuned["sort_every"])
+    else:
+        sim = Simulation(w, precision=args.precision, sort_every=args.sort_every)
     stream = torch.cuda.current_stream()
     for _ in range(max(args.warmup, 3)):
         sim.step(1)
@@ -529,7 +545,13 @@ def main():
     if not args.no_e2e:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        s2 = Simulation(w, precision=args.precision, sort_every=args.sort_every)
+        if tuned and args.tile:
+            s2 = Simulation(w, precision=args.precision, tile=tuned["tile"], sort_every=args.sort_every)
+        elif tuned:
+            # the public call with tune=True: pic_autotune (its result cached per run shape) and pic_init
+            s2 = Simulation(w, precision=args.precision, tune=True)
+        else:
+            s2 = Simulation(w, precision=args.precision, sort_every=args.sort_every)
         k2 = max(args.steps // 2, 10)
         for _ in range(k2):
             s2.step(1)
@@ -543,7 +565,8 @@ def main():
         e2e_v, _ = job_throughput(n2 * k2, wall * 1e3, ws)
         e2e = {"value": e2e_v, "unit": "particle-steps/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": ctypes.sizeof(capi.PicStats),
-               "note": f"wall clock of pic_init + pic_load_plasma + {k2} x (pic_step + pic_get_stats)"}
+               "note": ("wall clock of " + ("pic_autotune (cached per run shape) + " if tuned else "") +
+                        f"pic_init + pic_load_plasma + {k2} x (pic_step + pic_get_stats)")}
         s2.close()
 
     if rank == 0:
@@ -561,6 +584,11 @@ def main():
                            if w.get("filter_strides") else ""),
                        "shape_order": args.order, "precision": args.precision, "electrons": int(n_avg),
                        "gather": args.gather,
+                       "layout": ({"tile_x": tuned["tile"][0], "tile_z": tuned["tile"][1],
+                                   "sort_every": tuned["sort_every"],
+                                   "source": "--tile" if args.tile else "pic_autotune",
+                                   "tune_wall_s": tuned["wall_s"], "trials": len(tuned["trials"])}
+                                  if tuned else "library default"),
                        "cell_steps_per_s": w["nx"] * w.get("ny", 1) * w["nz"] * args.steps * ws / (ms_max * 1e-3),
                        "l2": "inputs larger than L2 (particle arrays ~0.5 GB, fields ~2.6 GB)" if three else
                              "inputs larger than L2 (particle arrays ~0.9 GB)",
