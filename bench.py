@@ -41,12 +41,13 @@ BYTES_PER_PARTICLE_3D = {"mixed": 76, "fp64": 104}
 # algorithmic bytes per cell-step of the field kernels (mixed, with Friedman): see the design notes
 BYTES_PER_CELL = {"mixed": 168, "fp64": 336}
 # measured DRAM bytes (read + write) per particle of one push launch, mixed precision, cubic shapes:
-# ncu dram__bytes_read.sum + dram__bytes_write.sum of k_push on the 2048 x 256 stage box
-# (profiles/k_push_stage2d_2048x256_mixed.md: 385.22 MB for 6,487,608 electrons), scaled to the
-# full box by its particle count; None for configurations not captured
-TRAFFIC_BYTES_PER_PARTICLE = {("mixed", 3): 59.38}
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of k_push on the 2048 x 256 stage box with the tuned
+# layout (8 x 16-cell tiles, sort every 64 steps; profiles/k_push_stage2d_2048x256_mixed.md: 382.41 MB
+# for 6,496,584 electrons), scaled to the full box by its particle count; None for other configurations
+TRAFFIC_BYTES_PER_PARTICLE = {("mixed", 3): 58.87}
+TRAFFIC_LAYOUT = ((8, 16), 64)
 # 3D: ncu dram bytes of k3_push_tiles on the 256 x 128 x 128 box (profiles/k3_push_tiles_stage3d_256x128x128_mixed.md:
-# 197.95 MB for 2,356,608 electrons), scaled to the full box by its particle count
+# 198.06 MB for 2,356,608 electrons), scaled to the full box by its particle count
 TRAFFIC_BYTES_PER_PARTICLE_3D = {("mixed", 3): 84.0}
 
 
@@ -525,11 +526,16 @@ def main():
     push_avg_ms = push_ms / max(push_n, 1)
     achieved = n_avg * bpp / (push_avg_ms * 1e-3) / 1e9
     tpp = (TRAFFIC_BYTES_PER_PARTICLE_3D if three else TRAFFIC_BYTES_PER_PARTICLE).get((args.precision, args.order))
+    if not three and (not tuned or (tuple(tuned["tile"]), tuned["sort_every"]) != TRAFFIC_LAYOUT
+                      or args.gather != "energy"):
+        tpp = None     # the counters were taken with the tuned layout and the Yee-located gather
+    if three and args.gather != "energy":
+        tpp = None
     roof = {"kernel": "k3_push_tiles (3D gather + Boris + Esirkepov)" if three else "k_push (gather + Boris + Esirkepov)",
             "bound": "hbm", "achieved": achieved, "peak": peak,
             "unit": "GB/s", "frac": achieved / peak, "traffic": tpp * n_avg if tpp else None,
             "traffic_source": ("ncu dram bytes of k3_push_tiles, 256 x 128 x 128 box, scaled by particles" if three
-                               else "ncu dram bytes of k_push, 2048 x 256 box, scaled by particles") if tpp else None,
+                               else "ncu dram bytes of k_push, 2048 x 256 box, tuned layout, scaled by particles") if tpp else None,
             "note": ("3D push on sorted 4x4x16-cell tiles with shared-memory windows: latency-bound at a quarter "
                      "occupancy (ncu: 35% issue slots, 44% L1/shared, 2% DRAM)" if three else
                      "at cubic order the push is bound by instruction issue "
