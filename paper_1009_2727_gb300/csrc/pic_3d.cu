@@ -1235,13 +1235,34 @@ __global__ void k3_stats(G3 g, const T* E, const T* B, Parts3<T> p, const Ctrl3*
   const long tid = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const long nthr = (long)gridDim.x * blockDim.x;
   double v[6] = {0, 0, 0, 0, 0, 0};
-  for (long j = tid; j < ctrl->count; j += nthr) {
-    if (!(p.fl[j] & 1)) continue;
-    v[0] += 1.0;
-    if (trap > 0.0) {
-      const double ux = p.ux[j], uy = p.uy[j], uz = p.uz[j];
-      const double gp = sqrt(1.0 + (ux * ux + uy * uy + uz * uz) / (kC * kC));
-      if (gam * (gp + be * uz / kC) > trap) v[5] += (double)p.w[j];
+  const long n = ctrl->count;
+  if (sizeof(T) == 4) {
+    // FP32 momenta: the lab-gamma test and the per-thread sums in FP32, loads issued without a branch
+    const float ic2 = float(1.0 / (kC * kC)), ic = float(1.0 / kC);
+    const float gamf = float(gam), bef = float(be), trapf = float(trap);
+    int ne = 0;
+    float wt = 0.f;
+#pragma unroll 4
+    for (long j = tid; j < n; j += nthr) {
+      const bool live = (p.fl[j] & 1) != 0;
+      ne += live ? 1 : 0;
+      if (trap > 0.0) {
+        const float ux = float(p.ux[j]), uy = float(p.uy[j]), uz = float(p.uz[j]), w = float(p.w[j]);
+        const float gp = sqrtf(1.f + (ux * ux + uy * uy + uz * uz) * ic2);
+        if (live && gamf * (gp + bef * uz * ic) > trapf) wt += w;
+      }
+    }
+    v[0] = ne;
+    v[5] = wt;
+  } else {
+    for (long j = tid; j < n; j += nthr) {
+      if (!(p.fl[j] & 1)) continue;
+      v[0] += 1.0;
+      if (trap > 0.0) {
+        const double ux = p.ux[j], uy = p.uy[j], uz = p.uz[j];
+        const double gp = sqrt(1.0 + (ux * ux + uy * uy + uz * uz) / (kC * kC));
+        if (gam * (gp + be * uz / kC) > trap) v[5] += (double)p.w[j];
+      }
     }
   }
   for (long j = tid; j < b.n; j += nthr) {
@@ -1256,6 +1277,7 @@ __global__ void k3_stats(G3 g, const T* E, const T* B, Parts3<T> p, const Ctrl3*
     // FP32 fields: each thread sums its nodes' energy density in FP32 (a few hundred terms), the blocks
     // and the grid reduce in FP64 (the FP64 pipe of this GPU is narrow)
     T acc = T(0);
+#pragma unroll 4
     for (long q = tid; q < g.cs; q += nthr) {
       const T e2 = E[q] * E[q] + E[g.cs + q] * E[g.cs + q] + E[2 * g.cs + q] * E[2 * g.cs + q];
       const T b2 = B[q] * B[q] + B[g.cs + q] * B[g.cs + q] + B[2 * g.cs + q] * B[2 * g.cs + q];

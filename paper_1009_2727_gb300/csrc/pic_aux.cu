@@ -335,22 +335,29 @@ __global__ void __launch_bounds__(256) k_stats(GridP g, FieldPtrs<T> f, Particle
     const float gamf = float(gam), bef = float(be), trapf = float(trap);
     int nef = 0;
     float wtf = 0.f;
-    for (long j = tid; j < ctrl->count; j += nthr) {
-      const float w = float(p.w[j]);
-      if (!(w > 0.f)) continue;
-      nef++;
-      if (trap > 0.0) {
+    const long n = ctrl->count;
+    if (trap > 0.0) {
+      // every load of an iteration issued at once (no branch before them), four iterations in flight
+#pragma unroll 4
+      for (long j = tid; j < n; j += nthr) {
+        const float w = float(p.w[j]);
         // boosted-frame momentum (the mixed path stores u_z - u0) -> lab-frame gamma
         const float ux = float(p.ux[j]), uy = float(p.uy[j]);
         const float uz = CellPos<T>::value ? g.fr_u0 + float(p.uz[j]) : float(p.uz[j]);
+        const bool live = w > 0.f;
+        nef += live ? 1 : 0;
         const float gp = sqrtf(1.f + (ux * ux + uy * uy + uz * uz) * ic2);
-        if (gamf * (gp + bef * uz * ic) > trapf) wtf += w;
+        if (live && gamf * (gp + bef * uz * ic) > trapf) wtf += w;
       }
+    } else {
+#pragma unroll 4
+      for (long j = tid; j < n; j += nthr) nef += float(p.w[j]) > 0.f ? 1 : 0;
     }
     ne = nef;
     wt = wtf;
     const float e0 = float(kEps0), imu0 = float(kEps0 * kC * kC);
     float enf = 0.f;
+#pragma unroll 4
     for (int e = (int)tid; e < ncell; e += (int)nthr) {
       const int i = e / nz1, k = e - i * nz1;
       const long q = (long)i * g.ld + k;
