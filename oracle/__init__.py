@@ -5,7 +5,7 @@ arm of ``bench.py`` may import this package. The product path (the CUDA
 library behind ``include/pic.h`` and its Python binding) never imports it, and
 this package imports nothing from the product.
 
-``pic_oracle.c`` (2-1/2D) and ``pic_oracle3d.c`` (3D) restate the method of
+``pic_oracle.c`` (2-1/2D), ``pic_oracle3d.c`` (3D) and ``pic_oracle1d.c`` (1D) restate the method of
 Vay et al., "Modeling laser wakefield accelerators in a Lorentz boosted frame"
 (arXiv:1009.2727) in plain double precision loops; this module builds them
 with gcc into one library and exposes it through ctypes.
@@ -23,7 +23,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liboracle.so")
-_SRCS = [os.path.join(_HERE, "pic_oracle.c"), os.path.join(_HERE, "pic_oracle3d.c")]
+_SRCS = [os.path.join(_HERE, "pic_oracle.c"), os.path.join(_HERE, "pic_oracle3d.c"),
+         os.path.join(_HERE, "pic_oracle1d.c")]
 _lock = threading.Lock()
 _lib = None
 
@@ -104,6 +105,30 @@ class _Laser3(ctypes.Structure):
                 ("y_center", ctypes.c_double), ("phase", ctypes.c_double), ("z_antenna", ctypes.c_double)]
 
 
+class _Config1(ctypes.Structure):
+    _fields_ = [
+        ("nz", ctypes.c_int), ("dz_lab", ctypes.c_double), ("gamma_boost", ctypes.c_double),
+        ("courant", ctypes.c_double), ("dt_override", ctypes.c_double), ("theta", ctypes.c_double),
+        ("pml_cells", ctypes.c_int), ("pml_sigma_max", ctypes.c_double), ("pml_delta", ctypes.c_double),
+        ("pml_power", ctypes.c_double), ("pml_xi_exp", ctypes.c_int),
+        ("filter_passes", ctypes.c_int), ("filter_stride", ctypes.c_int), ("filter_compensate", ctypes.c_int),
+        ("filter_J", ctypes.c_int), ("filter_gather", ctypes.c_int),
+        ("order", ctypes.c_int), ("particle_guard", ctypes.c_int),
+        ("moving_window", ctypes.c_int), ("window_beta", ctypes.c_double),
+        ("filter_strides", ctypes.c_int * 4), ("gather_nodal", ctypes.c_int),
+    ]
+
+
+class _Plasma1(ctypes.Structure):
+    _fields_ = [("n0", ctypes.c_double), ("z_start_lab", ctypes.c_double), ("ramp_lab", ctypes.c_double),
+                ("length_lab", ctypes.c_double), ("ppc_z", ctypes.c_int), ("ions", ctypes.c_int)]
+
+
+class _Laser1(ctypes.Structure):
+    _fields_ = [("lambda0", ctypes.c_double), ("a0", ctypes.c_double), ("tau_fwhm", ctypes.c_double),
+                ("t_peak", ctypes.c_double), ("phase", ctypes.c_double), ("z_antenna", ctypes.c_double)]
+
+
 _D = ctypes.POINTER(ctypes.c_double)
 
 
@@ -172,6 +197,21 @@ def lib():
             L.o3_btd_set.argtypes = [vp, ctypes.c_int, _D, _D]
             L.o3_btd_get.argtypes = [vp, _D, ctypes.POINTER(ctypes.c_int)]
             L.o3_deposit_one.argtypes = [vp] + [ctypes.c_double] * 7
+            L.o1_create.restype = vp
+            L.o1_create.argtypes = [ctypes.POINTER(_Config1)]
+            L.o1_destroy.argtypes = [vp]
+            L.o1_step.argtypes = [vp, ctypes.c_int]
+            L.o1_load_plasma.argtypes = [vp, ctypes.POINTER(_Plasma1)]
+            L.o1_set_laser.argtypes = [vp, ctypes.POINTER(_Laser1)]
+            L.o1_info.argtypes = [vp, _D]
+            for f in ("o1_get_field", "o1_set_field", "o1_get_gather_field", "o1_filter_field"):
+                getattr(L, f).argtypes = [vp, ctypes.c_int, _D]
+            L.o1_num_particles.restype = ctypes.c_long
+            L.o1_num_particles.argtypes = [vp, ctypes.c_int]
+            L.o1_get_particles.argtypes = [vp, ctypes.c_int] + [_D] * 5 + [ctypes.POINTER(ctypes.c_uint32)]
+            L.o1_rho.argtypes = [vp, _D]
+            L.o1_diag.argtypes = [vp, _D]
+            L.o1_deposit_one.argtypes = [vp] + [ctypes.c_double] * 5
             _lib = L
     return _lib
 
@@ -519,3 +559,112 @@ class Sim3:
         """current of one particle moved from p0 to p1 (x, y, z), deposited into the (zeroed) J arrays"""
         self.L.o3_deposit_one(self.h, *[float(v) for v in p0], *[float(v) for v in p1], float(qw))
         return [self.field(JX + c) for c in range(3)]
+
+
+def _mk_config1(w: dict) -> _Config1:
+    c = _Config1()
+    c.nz = int(w["nz"])
+    c.dz_lab = float(w["dz_lab"])
+    c.gamma_boost = float(w.get("gamma_boost", 1.0))
+    c.courant = float(w.get("courant", 0.95))
+    c.dt_override = float(w.get("dt", 0.0))
+    c.theta = float(w.get("theta", 0.0))
+    c.pml_cells = int(w.get("pml_cells", 0))
+    c.pml_sigma_max = float(w.get("pml_sigma_max", 4.0))
+    c.pml_delta = float(w.get("pml_delta", 5.0))
+    c.pml_power = float(w.get("pml_power", 2.0))
+    c.pml_xi_exp = int(w.get("pml_xi_exp", 1))
+    c.filter_passes = int(w.get("filter_passes", 0))
+    c.filter_stride = int(w.get("filter_stride", 1))
+    c.filter_compensate = int(w.get("filter_compensate", 0))
+    c.filter_J = int(w.get("filter_J", 0))
+    c.filter_gather = int(w.get("filter_gather", 0))
+    c.order = int(w.get("order", 3))
+    c.particle_guard = int(w.get("particle_guard", -1))
+    c.moving_window = int(w.get("moving_window", 0))
+    c.window_beta = float(w.get("window_beta", 0.0))
+    for q, v in enumerate(list(w.get("filter_strides", []))[:4]):
+        c.filter_strides[q] = int(v)
+    c.gather_nodal = 1 if w.get("gather", "energy") == "momentum" else 0
+    return c
+
+
+class Sim1:
+    """One 1D oracle simulation (fields and positions along z only) built from a workload dict with
+    dim = 1 (nz, dz_lab, ...; the plasma's ppc_z; the laser's lambda0, a0, tau_fwhm, t_peak, z_antenna)."""
+
+    def __init__(self, w: dict):
+        self.L = lib()
+        self.w = dict(w)
+        self._cfg = _mk_config1(w)
+        self.h = self.L.o1_create(ctypes.byref(self._cfg))
+        info = self.info()
+        self.nz = int(w["nz"])
+        self.dz, self.dt = info["dz"], info["dt"]
+        if w.get("plasma"):
+            p = w["plasma"]
+            pl = _Plasma1(float(p["n0"]), float(p.get("z_start_lab", 0.0)), float(p.get("ramp_lab", 0.0)),
+                          float(p.get("length_lab", 0.0)), int(p["ppc_z"]), int(p.get("ions", 1)))
+            self.L.o1_load_plasma(self.h, ctypes.byref(pl))
+        if w.get("laser"):
+            l = w["laser"]
+            la = _Laser1(float(l["lambda0"]), float(l["a0"]), float(l["tau_fwhm"]), float(l.get("t_peak", 0.0)),
+                         float(l.get("phase", 0.0)), float(l["z_antenna"]))
+            self.L.o1_set_laser(self.h, ctypes.byref(la))
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            self.L.o1_destroy(h)
+            self.h = None
+
+    def info(self) -> dict:
+        o = np.zeros(10)
+        self.L.o1_info(self.h, _p(o))
+        keys = ("dz", "dt", "gamma", "beta", "step", "t", "guard", "gz_lo", "gz_hi", "z0")
+        return dict(zip(keys, o.tolist()))
+
+    def step(self, n: int = 1):
+        self.L.o1_step(self.h, int(n))
+
+    def field(self, comp: int) -> np.ndarray:
+        out = np.zeros(self.nz + 1)
+        self.L.o1_get_field(self.h, comp, _p(out))
+        return out
+
+    def set_field(self, comp: int, a: np.ndarray):
+        a = np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+        self.L.o1_set_field(self.h, comp, _p(a))
+
+    def gather_field(self, comp: int) -> np.ndarray:
+        out = np.zeros(self.nz + 1)
+        self.L.o1_get_gather_field(self.h, comp, _p(out))
+        return out
+
+    def filter_field(self, comp: int, a: np.ndarray) -> np.ndarray:
+        b = np.ascontiguousarray(a, dtype=np.float64).reshape(-1).copy()
+        self.L.o1_filter_field(self.h, comp, _p(b))
+        return b
+
+    def rho(self) -> np.ndarray:
+        out = np.zeros(self.nz + 1)
+        self.L.o1_rho(self.h, _p(out))
+        return out
+
+    def deposit_one(self, z0: float, z1: float, vx: float, vy: float, qw: float):
+        self.L.o1_deposit_one(self.h, z0, z1, vx, vy, qw)
+
+    def particles(self, species: int = 0) -> dict:
+        n = self.L.o1_num_particles(self.h, species)
+        keys = ("z", "ux", "uy", "uz", "w")
+        arrs = {k: np.zeros(n) for k in keys}
+        ids = np.zeros(n, dtype=np.uint32)
+        self.L.o1_get_particles(self.h, species, *(_p(arrs[k]) for k in keys),
+                                ids.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)))
+        arrs["id"] = ids
+        return arrs
+
+    def diag(self) -> dict:
+        o = np.zeros(2)
+        self.L.o1_diag(self.h, _p(o))
+        return {"n_e": o[0], "field_energy": o[1]}

@@ -1,0 +1,154 @@
+"""Pins of the 1D oracle (oracle/pic_oracle1d.c) against closed forms and exact identities.
+
+- vacuum standing modes of Eq. 1db-1de (and of the (E_y, B_x) pair) advance by the root of
+  sin(w dt/2) = (c dt/dz) sin(k dz/2), exact at c dt = dz (App. I);
+- the 1D Esirkepov deposit conserves charge at every node and carries q w v in total;
+- full steps with plasma, ions and the antenna keep Gauss's law (E_z from rho) at round-off, with the
+  current filter on (div E against the filtered rho, PR-8);
+- the linear wake of a Gaussian pulse in a cold plasma: amplitude (sqrt(pi)/4) a0^2 k_p sigma
+  exp(-k_p^2 sigma^2/4) E0 and wavelength 2 pi c/w_p (exact theory in 1D), lab frame and boosted frame.
+"""
+import math
+
+import numpy as np
+import pytest
+
+C = 299792458.0
+QE = 1.602176634e-19
+ME = 9.1093837015e-31
+EPS0 = 8.8541878128e-12
+
+
+def vac1(nz, courant=0.95, **kw):
+    w = {"dim": 1, "nz": nz, "dz_lab": 1e-6, "gamma_boost": 1.0, "courant": courant, "theta": 0.0,
+         "pml_cells": 0, "order": 3}
+    w.update(kw)
+    return w
+
+
+@pytest.mark.parametrize("courant", [0.5, 0.9, 1.0])
+@pytest.mark.parametrize("pol", ["x", "y"])
+def test_1d_vacuum_standing_modes(orc, courant, pol):
+    nz = 64
+    s = orc.Sim1(vac1(nz, courant))
+    dz, dt = s.dz, s.dt
+    k = np.arange(nz + 1)
+    for m in (3, 11, 30):
+        K = math.pi * m / (nz * dz)
+        om = 2.0 / dt * math.asin(C * dt / dz * math.sin(K * dz / 2))
+        B0 = -(dt / dz) * math.sin(K * dz / 2) / math.sin(om * dt / 2)
+        e = np.sin(K * k * dz)
+        b = B0 * np.cos(K * (k + 0.5) * dz) * math.sin(-om * dt / 2)
+        b[-1] = 0.0
+        s2 = orc.Sim1(vac1(nz, courant))
+        # (E_x, B_y): dBy/dt = -dEx/dz; (E_y, B_x): dBx/dt = +dEy/dz, so B_x takes the opposite sign
+        s2.set_field(0 if pol == "x" else 1, e)
+        s2.set_field(4 if pol == "x" else 3, b if pol == "x" else -b)
+        n = 37
+        s2.step(n)
+        got = s2.field(0 if pol == "x" else 1)
+        assert np.abs(got - e * math.cos(om * n * dt)).max() < 1e-11, m
+    if courant == 1.0:
+        # App. I: at c dt = dz the scheme has no dispersion, w = c k
+        assert om == pytest.approx(C * math.pi * 30 / (nz * dz), rel=1e-12)
+
+
+@pytest.mark.parametrize("order", [1, 3])
+def test_1d_esirkepov_continuity_and_total_current(orc, order):
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        s = orc.Sim1(vac1(40, order=order))
+        dz, dt = s.dz, s.dt
+        z0 = rng.uniform(15, 25) * dz
+        z1 = z0 + rng.uniform(-0.9, 0.9) * dz
+        vx, vy, qw = rng.normal(size=3)
+        s.deposit_one(z0, z1, vx, vy, qw)
+        jx, jy, jz = s.field(6), s.field(7), s.field(8)
+        k = np.arange(41)
+        S0 = np.array([orc.shape(order, z0 / dz - kk) for kk in k])
+        S1 = np.array([orc.shape(order, z1 / dz - kk) for kk in k])
+        drho = qw * (S1 - S0) / dz / dt
+        div = (jz - np.concatenate(([0.0], jz[:-1]))) / dz
+        assert np.abs(drho + div).max() < 1e-12 * np.abs(drho).max()
+        assert jz.sum() * dz == pytest.approx(qw * (z1 - z0) / dt, rel=1e-12)
+        assert jx.sum() * dz == pytest.approx(qw * vx, rel=1e-12)
+        assert jy.sum() * dz == pytest.approx(qw * vy, rel=1e-12)
+
+
+def _plasma_laser_1d(gamma, filt):
+    lam = 0.8e-6
+    w = {"dim": 1, "nz": 400, "dz_lab": lam / 24, "gamma_boost": gamma, "courant": 0.9, "theta": 0.1,
+         "pml_cells": 10, "order": 3, "filter_passes": 2 if filt else 0, "filter_compensate": 1 if filt else 0,
+         "filter_J": int(filt), "filter_gather": int(filt),
+         "plasma": {"n0": 1e25, "z_start_lab": 0.0, "ramp_lab": 2e-6, "length_lab": 0.0, "ppc_z": 4, "ions": 1},
+         "laser": {"lambda0": lam, "a0": 0.5, "tau_fwhm": 10e-15, "t_peak": 12e-15, "phase": 0.0,
+                   "z_antenna": 60 * (1 + math.sqrt(1 - 1 / gamma ** 2)) * gamma * lam / 24}}
+    return w
+
+
+@pytest.mark.parametrize("gamma,filt", [(1.0, False), (3.0, True)])
+def test_1d_gauss_law_through_full_steps(orc, gamma, filt):
+    s = orc.Sim1(_plasma_laser_1d(gamma, filt))
+    s.step(300)
+    ez = s.field(2)
+    rho = s.rho()
+    if filt:
+        rho = s.filter_field(6, rho)
+    div = (ez[1:] - ez[:-1]) / s.dz               # at nodes 1..nz-1
+    # the interior: particles that leave through the domain's ends take their charge with them
+    info = s.info()
+    lo, hi = int(info["gz_lo"]) + 6, int(info["gz_hi"]) - 6
+    ref = rho[1:][lo:hi] / EPS0
+    assert np.abs(ref).max() > 0
+    assert np.abs(div[lo:hi] - ref).max() < 1e-9 * np.abs(ref).max()
+    assert s.diag()["n_e"] > 1000
+    assert np.abs(s.field(1)).max() > 1e10           # the laser is in
+
+
+LW_N0, LW_A0, LW_LAM = 2e25, 0.1, 0.8e-6
+
+
+def _linear_wake_1d(gamma, nz, start_cells, ant_cells):
+    wp = math.sqrt(LW_N0 * QE * QE / (EPS0 * ME))
+    kp = wp / C
+    sig = math.sqrt(2.0) / kp
+    tau = 2.0 * math.sqrt(math.log(2.0)) * sig / C
+    dzl = LW_LAM / 24.0
+    beta = math.sqrt(1.0 - 1.0 / gamma ** 2)
+    dzb = (1.0 + beta) * gamma * dzl
+    lab = gamma == 1.0
+    w = {"dim": 1, "nz": nz, "dz_lab": dzl, "gamma_boost": gamma, "courant": 0.95, "theta": 0.0,
+         "pml_cells": 8, "order": 1, "moving_window": int(lab), "window_beta": 1.0 if lab else 0.0,
+         "plasma": {"n0": LW_N0, "z_start_lab": gamma * start_cells * dzb, "ramp_lab": 1e-6, "length_lab": 0.0,
+                    "ppc_z": 2, "ions": 1},
+         "laser": {"lambda0": LW_LAM, "a0": LW_A0, "tau_fwhm": tau,
+                   "t_peak": 3.2 * tau / (2.0 * math.sqrt(math.log(2.0))), "phase": 0.0,
+                   "z_antenna": ant_cells * dzb}}
+    ez_lin = math.sqrt(math.pi) / 4 * LW_A0 ** 2 * kp * sig * math.exp(-(kp * sig) ** 2 / 4) * ME * C * wp / QE
+    return w, ez_lin, 2 * math.pi / kp / dzl, sig / dzl
+
+
+def _wake(s, lp_cells, sig_cells, gamma):
+    ez, ey = s.field(2), s.field(1)
+    kl = int(np.argmax(np.abs(ey)))
+    dzb_over_dzl = s.dz / (LW_LAM / 24.0)
+    lp_b, sig_b = lp_cells / dzb_over_dzl * gamma, sig_cells / dzb_over_dzl * gamma   # boosted-frame lengths
+    a, b = max(kl - int(1.5 * lp_b), 20), kl - int(3 * sig_b)
+    seg = ez[a:b]
+    zc = [a + i + seg[i] / (seg[i] - seg[i + 1]) for i in range(len(seg) - 1) if seg[i] * seg[i + 1] < 0]
+    return np.abs(seg).max(), zc, lp_b
+
+
+def test_1d_linear_wake_lab_and_boosted(orc):
+    w, ez_lin, lp, sg = _linear_wake_1d(1.0, 600, 540, 530)
+    s = orc.Sim1(w)
+    s.step(520)
+    ez, zc, lpb = _wake(s, lp, sg, 1.0)
+    assert ez == pytest.approx(ez_lin, rel=0.03)
+    assert len(zc) >= 2 and np.diff(zc)[-1] == pytest.approx(lpb / 2, rel=0.03)
+    # the same pulse and plasma in a frame boosted at gamma = 2: E_z is invariant under the boost
+    w2, _, _, _ = _linear_wake_1d(2.0, 720, 340, 40)
+    s2 = orc.Sim1(w2)
+    s2.step(600)
+    ez2, _, _ = _wake(s2, lp, sg, 2.0)
+    assert ez2 == pytest.approx(ez_lin, rel=0.04)
