@@ -27,6 +27,14 @@
  *    Ez (i,j,k+1/2), Bx (i,j+1/2,k+1/2), By (i+1/2,j,k+1/2), Bz (i+1/2,j+1/2,k).
  *    3D contexts have no moving window, autotuner or pic_get_rho_noalloc;
  *    the laser antenna is at rest (beta_s = 0).
+ *  - 1D (pic_config.dim = 1; App. I): fields and positions depend on z only,
+ *    arrays are nz+1 values; Ex, Ey, Bz at k, Ez, Bx, By at k+1/2; nx, dx,
+ *    the solver coefficients (the 1D operator is Yee's), ppc_x and the laser's
+ *    w0 and x_center are ignored; the laser is a plane wave from a current
+ *    sheet at rest; weights and the field energy are per unit transverse area;
+ *    pic_get_particles returns the electrons (x = 0; the ions are a column
+ *    current); the moving window runs in the lab frame (gamma_boost = 1);
+ *    no test beam, lab-frame samples, autotuner or pic_get_rho_noalloc.
  */
 #ifndef PIC_H
 #define PIC_H
@@ -69,7 +77,7 @@ typedef void (*pic_free_fn)(void* ptr, size_t bytes, void* stream, void* user);
  * PIC_API_VERSION. */
 typedef struct {
   uint32_t struct_size, version;
-  int32_t dim;            /* 2 (x,z) or 3 (x,y,z) */
+  int32_t dim;            /* 2 (x,z), 3 (x,y,z) or 1 (z) */
   int32_t nx, nz;         /* cells along x and z; the PML occupies pml_cells on each side */
   double dz_lab;          /* lab longitudinal cell [m]; the computational cell is (1+beta) gamma dz_lab (Sec. 5.1.1) */
   double dx;              /* transverse cell [m] */

@@ -1,5 +1,6 @@
-// Internal interface of the 3D path (x, y, z): one object per context created
-// with pic_config.dim == 3. The C entry points of pic_capi.cu forward to it.
+// Internal interface of the 3D path (x, y, z) and of the 1D path (z): one object
+// per context created with pic_config.dim == 3 or 1. The C entry points of
+// pic_capi.cu forward to it.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -34,6 +35,10 @@ struct Sim3Api {
 // Validates the 3D configuration and allocates the fields; on failure returns
 // NULL and sets *status (and *err).
 Sim3Api* make_sim3(const pic_config* cfg, pic_alloc_fn alloc, pic_free_fn free_fn, void* user, cudaStream_t s,
+                   int* status, std::string* err);
+
+// The same for the 1D configuration (pic_config.dim == 1).
+Sim3Api* make_sim1(const pic_config* cfg, pic_alloc_fn alloc, pic_free_fn free_fn, void* user, cudaStream_t s,
                    int* status, std::string* err);
 
 }  // namespace picgb

@@ -64,7 +64,7 @@ struct pic_ctx {
   int status = PIC_OK;
   int64_t launches = 0;
   std::unique_ptr<SimBase> sim;
-  std::unique_ptr<picgb::Sim3Api> s3;   // 3D contexts
+  std::unique_ptr<picgb::Sim3Api> s3;   // 3D and 1D contexts
 
   void* dalloc(size_t bytes) {
     if (bytes == 0) bytes = 16;
@@ -902,7 +902,7 @@ int pic_init(const pic_config* cfg, pic_alloc_fn alloc, pic_free_fn free_fn, voi
   if (!out) return PIC_EINVAL;
   *out = nullptr;
   if (!cfg || cfg->struct_size != sizeof(pic_config) || cfg->version != PIC_API_VERSION) return PIC_EINVAL;
-  if (cfg->dim != 2 && cfg->dim != 3) return PIC_EINVAL;
+  if (cfg->dim != 1 && cfg->dim != 2 && cfg->dim != 3) return PIC_EINVAL;
   if (cfg->gather_scheme != 0 && cfg->gather_scheme != 1) return PIC_EINVAL;
   // the composed filter: at most 16 passes per stride and a halo of at most FILTER_HMAX cells; a stride set
   // is non-negative and 0-terminated
@@ -914,6 +914,23 @@ int pic_init(const pic_config* cfg, pic_alloc_fn alloc, pic_free_fn free_fn, voi
   }
   const int Hf = filter_halo(fs0);
   if (cfg->filter_passes + (cfg->filter_compensate ? 1 : 0) > 16 || Hf > FILTER_HMAX) return PIC_EINVAL;
+  if (cfg->dim == 1) {
+    if (cfg->nz < 16 || !(cfg->dz_lab > 0)) return PIC_EINVAL;
+    if (cfg->shape_order != 1 && cfg->shape_order != 3) return PIC_EINVAL;
+    if (cfg->precision != PIC_FP64 && cfg->precision != PIC_MIXED) return PIC_EINVAL;
+    if (cfg->theta < 0 || cfg->theta > 1) return PIC_EINVAL;
+    if (cfg->filter_passes < 0 || cfg->filter_stride < 1 || cfg->pml_cells < 0) return PIC_EINVAL;
+    std::unique_ptr<pic_ctx> c(new pic_ctx());
+    c->cfg = *cfg;
+    c->stream = (cudaStream_t)cuda_stream;
+    c->alloc = alloc; c->freef = free_fn; c->user = alloc_user;
+    int st = PIC_OK;
+    std::string e;
+    c->s3.reset(picgb::make_sim1(cfg, alloc, free_fn, alloc_user, c->stream, &st, &e));
+    if (!c->s3) return st;
+    *out = c.release();
+    return PIC_OK;
+  }
   if (cfg->dim == 3) {
     if (cfg->nx < 8 || cfg->nz < 8 || !(cfg->dx > 0) || !(cfg->dz_lab > 0)) return PIC_EINVAL;
     if (cfg->shape_order != 1 && cfg->shape_order != 3) return PIC_EINVAL;

@@ -29,10 +29,10 @@ def make_config(w: dict, precision: int, tile=None, sort_every: int = 0) -> capi
     c.struct_size = ctypes.sizeof(capi.PicConfig)
     c.version = capi.API_VERSION
     c.dim = int(w.get("dim", 2))
-    c.nx, c.nz = int(w["nx"]), int(w["nz"])
+    c.nx, c.nz = int(w.get("nx", 0)), int(w["nz"])
     if c.dim == 3:
         c.ny, c.dy = int(w["ny"]), float(w["dy"])
-    c.dz_lab, c.dx = float(w["dz_lab"]), float(w["dx"])
+    c.dz_lab, c.dx = float(w["dz_lab"]), float(w.get("dx", 0.0))
     c.gamma_boost = float(w.get("gamma_boost", 1.0))
     c.courant = float(w.get("courant", 0.9))
     c.dt = float(w.get("dt", 0.0) or 0.0)
@@ -72,7 +72,7 @@ def make_plasma(p: dict | None, beam: dict | None, keep: list) -> capi.PicPlasma
         pl.z_start_lab = float(p.get("z_start_lab", 0.0))
         pl.ramp_lab = float(p.get("ramp_lab", 0.0))
         pl.length_lab = float(p.get("length_lab", 0.0))
-        pl.ppc_x, pl.ppc_z = int(p["ppc_x"]), int(p["ppc_z"])
+        pl.ppc_x, pl.ppc_z = int(p.get("ppc_x", 1)), int(p["ppc_z"])
         pl.ppc_y = int(p.get("ppc_y", 0))
         pl.ions = int(p.get("ions", 1))
     else:
@@ -95,7 +95,7 @@ def make_laser(l: dict, nx: int, dx: float, ny: int = 0, dy: float = 0.0) -> cap
     la = capi.PicLaser()
     la.struct_size = ctypes.sizeof(capi.PicLaser)
     la.version = capi.API_VERSION
-    la.lambda0, la.a0, la.w0 = float(l["lambda0"]), float(l["a0"]), float(l["w0"])
+    la.lambda0, la.a0, la.w0 = float(l["lambda0"]), float(l["a0"]), float(l.get("w0", 0.0))
     la.tau_fwhm, la.t_peak = float(l["tau_fwhm"]), float(l.get("t_peak", 0.0))
     la.x_center = float(l.get("x_center", 0.5 * nx * dx))
     la.phase, la.z_antenna, la.beta_s = float(l.get("phase", 0.0)), float(l["z_antenna"]), float(l.get("beta_s", 0.0))
@@ -157,10 +157,11 @@ class Simulation:
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         prec = precision or w.get("precision", "fp64")
         self.precision = capi.PIC_FP64 if prec == "fp64" else capi.PIC_MIXED
-        self.nx, self.nz = int(w["nx"]), int(w["nz"])
+        self.nx, self.nz = int(w.get("nx", 0)), int(w["nz"])
         self.dim = int(w.get("dim", 2))
         self.ny = int(w["ny"]) if self.dim == 3 else 0
-        self.shape = (self.nx + 1, self.ny + 1, self.nz + 1) if self.dim == 3 else (self.nx + 1, self.nz + 1)
+        self.shape = ((self.nx + 1, self.ny + 1, self.nz + 1) if self.dim == 3 else (self.nz + 1,) if self.dim == 1
+                      else (self.nx + 1, self.nz + 1))
         if tune:
             t = autotune(w, precision=prec, stream=self.stream)
             tile, sort_every = t["tile"], t["sort_every"]
@@ -195,7 +196,7 @@ class Simulation:
         self._check(self.L.pic_load_plasma(self.h, ctypes.byref(pl)), "pic_load_plasma")
 
     def inject_laser(self, l: dict):
-        la = make_laser(l, self.nx, float(self.w["dx"]), self.ny, float(self.w.get("dy", 0.0)))
+        la = make_laser(l, self.nx, float(self.w.get("dx", 0.0)), self.ny, float(self.w.get("dy", 0.0)))
         self._check(self.L.pic_inject_laser(self.h, ctypes.byref(la)), "pic_inject_laser")
 
     def step(self, n: int = 1):

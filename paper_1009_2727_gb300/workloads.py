@@ -292,3 +292,52 @@ def surrogate_runs(n: int, seed: int) -> list:
             "beam": {"x": x, "z": z, "ux": ux, "uy": uy, "uz": uz, "t_lab": 0.0, "z_plane_lab": z_start_lab},
         })
     return runs
+
+
+def parity_1d(gamma_boost: float = 3.0) -> dict:
+    """Plain FP64 parity workload in 1D: 400 cells, dz = lambda0/24 in the lab, Courant 0.9 with Friedman
+    theta = 0.1, 10-cell PML at both ends, 2 passes + compensation on J and on the gathered fields, cubic
+    shapes, n0 = 1e19 cm^-3 behind a 2 um ramp, 4 particles per cell, ions fixed in the lab, a0 = 0.5
+    pulse of 10 fs."""
+    lam = LAMBDA0
+    beta = (1.0 - 1.0 / gamma_boost ** 2) ** 0.5
+    dzb = (1.0 + beta) * gamma_boost * lam / 24.0
+    return {
+        "name": f"parity_1d_400_g{gamma_boost:g}", "dim": 1, "nz": 400, "dz_lab": lam / 24.0,
+        "gamma_boost": gamma_boost, "courant": 0.9, "dt": 0.0, "theta": 0.1,
+        "pml_cells": 10, "pml_sigma_max": 4.0, "pml_delta": 5.0, "pml_power": 2.0, "pml_xi_exp": 1,
+        "filter_passes": 2, "filter_stride": 1, "filter_compensate": 1, "filter_J": 1, "filter_gather": 1,
+        "order": 3, "particle_guard": -1, "moving_window": 0, "window_beta": 0.0, "precision": "fp64",
+        "plasma": {"n0": 1e25, "z_start_lab": gamma_boost * 80 * dzb, "ramp_lab": 2e-6, "length_lab": 0.0,
+                   "ppc_z": 4, "ions": 1},
+        "laser": {"lambda0": lam, "a0": 0.5, "tau_fwhm": 10e-15, "t_peak": 12e-15, "phase": 0.0,
+                  "z_antenna": 60 * dzb},
+        "steps": 400,
+    }
+
+
+def app1_lwfa(filtered: bool = True) -> dict:
+    """The 1D scaled laser-wakefield stage of App. I (Table Tablephyspar): 952 cells of lambda/24 in the lab
+    frame with a moving window at c, c dt = dz (the CFL limit, where the odd-even Nyquist mode of Eq.
+    1db-1de is undamped), cubic shapes, 10 particles per cell, n_e = 1e19 cm^-3 over 1.5 mm behind a 4 um
+    ramp, a0 = 1 at 0.8 um with a 10.08 um (33.6 fs) long pulse; the current filtered by one bilinear pass
+    without compensation, or not at all. The paper's half-sine ramp and sin(pi z/L) pulse envelope are
+    replaced by a linear ramp and a Gaussian of the same FWHM (this path's antenna and plasma profiles);
+    the beam of the table (1e14 cm^-3, a test population) is left out."""
+    lam = LAMBDA0
+    dz = lam / 24.0
+    nz = 952
+    tau = 10.08e-6 / 299792458.0
+    return {
+        "name": "app1_lwfa_952" + ("_filtered" if filtered else "_unfiltered"), "dim": 1, "nz": nz,
+        "dz_lab": dz, "gamma_boost": 1.0, "courant": 1.0, "dt": 0.0, "theta": 0.0,
+        "pml_cells": 16, "pml_sigma_max": 4.0, "pml_delta": 5.0, "pml_power": 2.0, "pml_xi_exp": 1,
+        "filter_passes": 1 if filtered else 0, "filter_stride": 1, "filter_compensate": 0,
+        "filter_J": int(filtered), "filter_gather": 0, "order": 3, "particle_guard": -1,
+        "moving_window": 1, "window_beta": 1.0, "precision": "mixed",
+        "plasma": {"n0": 1e25, "z_start_lab": (nz - 60) * dz, "ramp_lab": 4e-6, "length_lab": 1.5e-3,
+                   "ppc_z": 10, "ions": 1},
+        "laser": {"lambda0": lam, "a0": 1.0, "tau_fwhm": tau, "t_peak": 1.6 * tau, "phase": 0.0,
+                  "z_antenna": (nz - 80) * dz},
+        "steps": 20000,
+    }
