@@ -378,6 +378,115 @@ def run_surrogate(args):
     return 0
 
 
+BYTES_PER_PARTICLE_1D = {"mixed": 44, "fp64": 64}
+
+
+def run_1d(args):
+    """App. I's 1D scaled stage (952 cells of lambda/24, 10 particles per cell, lab frame, window at c,
+    c dt = dz, one bilinear pass on the current): particle-steps/s of the whole step, the push's roofline
+    and the oracle on the same workload"""
+    import torch
+    from paper_1009_2727_gb300 import workloads as W
+    from paper_1009_2727_gb300.pic import Simulation
+    torch.cuda.set_device(0)
+    w = W.app1_lwfa(True)
+    w["precision"] = args.precision
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        wo = dict(w)
+        wo["precision"] = "fp64"
+        o = oracle.Sim1(wo)
+        o.step(200)
+        n = o.diag()["n_e"]
+        t0 = time.perf_counter()
+        k = 0
+        while k < 4000 and time.perf_counter() - t0 < 10.0:
+            o.step(100)
+            k += 100
+        dt = time.perf_counter() - t0
+        cpu = {"value": n * k / dt, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+               "sample": f"{w['name']}: {int(n)} electrons, {k} steps after 200, {dt:.1f} s, single thread"}
+    sim = Simulation(w, precision=args.precision)
+    sim.step(max(args.warmup, 3) + 200)
+    sim.sync()
+    n0 = sim.stats()["n_electrons"]
+    stream = torch.cuda.current_stream()
+    sim.timing(True, 0)
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    torch.cuda.synchronize()
+    l0 = sim.launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    sim.step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    launches = sim.launches() - l0
+    ms = ev0.elapsed_time(ev1)
+    push_ms, push_n = sim.timing(False)
+    n1 = sim.stats()["n_electrons"]
+    n_avg = 0.5 * (n0 + n1)
+    value = n_avg * args.steps / (ms * 1e-3)
+    peaks = measured_peaks()
+    peak = peaks.get("hbm_gbs", 6800.0)
+    bpp = BYTES_PER_PARTICLE_1D[args.precision]
+    push_avg = push_ms / max(push_n, 1)
+    achieved = n_avg * bpp / (push_avg * 1e-3) / 1e9
+    roof = {"kernel": "k1_push (1D gather + Boris + Esirkepov)", "bound": "hbm", "achieved": achieved, "peak": peak,
+            "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+            "note": "9e3 particles and 953 nodes: the 1D step is launch- and latency-bound (about ten launches "
+                    "of a few microseconds); the byte roofline does not bind",
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback",
+            "algorithmic_bytes_per_particle": bpp, "push_ms_per_step": push_avg}
+    sim.close()
+    e2e = None
+    if not args.no_e2e:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s2 = Simulation(w, precision=args.precision)
+        k2 = max(args.steps // 2, 10)
+        for _ in range(k2):
+            s2.step(1)
+            st = s2.stats()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        e2e = {"value": st["n_electrons"] * k2 / wall, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
+               "d2h_bytes_per_step": 160,
+               "note": f"wall clock of pic_init + pic_load_plasma + {k2} x (pic_step + pic_get_stats)"}
+        s2.close()
+    line = {"metric": "particle-steps/s", "value": value, "unit": "particle-steps/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64pos" if args.precision == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": w["name"], "grid": [w["nz"]], "ppc": 10, "gamma_boost": 1.0,
+                       "solver": "Yee (1D)", "c_dt_over_dz": 1.0, "filter": "1 pass, no compensation",
+                       "shape_order": 3, "precision": args.precision, "electrons": int(n_avg),
+                       "moving_window": "lab frame at c", "l2": "fits in L2 (a 1D run is small)",
+                       "parallelism": "1 GPU"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_app1(args):
+    """App. I on the GPU: the Nyquist (odd-even) mode grows without the current filter and is removed by
+    one bilinear pass"""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_1009_2727_gb300 import stability
+    t0 = time.time()
+    runs = stability.app1_runs(20000, every=2000)
+    line = {"metric": "nyquist_share_Ey", "unit": "share of the E_y power at k dz > 3 pi / 4",
+            "higher_is_better": False, "data": "synthetic",
+            "config": {"workload": "app1_lwfa_952", "precision": "mixed", "steps": 20000, "c_dt_over_dz": 1.0},
+            "runs": runs, "wall_s": time.time() - t0}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_dt_scan(args):
     """the time-step scan of the instability (Sec. 5) for the Yee-located and the node-interpolated gather"""
     import torch
@@ -430,8 +539,11 @@ def main():
     ap.add_argument("--tile", default="", help="fixed particle tile x,z (no tuning), e.g. 8,16")
     ap.add_argument("--surrogate", type=int, default=0,
                     help="label N stage runs, train the stage surrogate on them and time its serving")
-    ap.add_argument("--dim", type=int, default=2, choices=[2, 3],
-                    help="3: the 3D stage (1024 x 128 x 128 cells, gamma 30) instead of the 2D one")
+    ap.add_argument("--dim", type=int, default=2, choices=[1, 2, 3],
+                    help="3: the 3D stage (1024 x 128 x 128 cells, gamma 30); 1: App. I's 1D scaled stage")
+    ap.add_argument("--app1", action="store_true",
+                    help="App. I: the 1D scaled stage at c dt = dz over 20000 steps, unfiltered and with one "
+                         "bilinear pass on the current (Nyquist-band share of E_y, wake field)")
     ap.add_argument("--gather", default="energy", choices=["energy", "momentum"],
                     help="momentum: the 'momentum conserving' gather (fields interpolated to the nodes first)")
     ap.add_argument("--dt-scan", action="store_true",
@@ -455,6 +567,10 @@ def main():
         return run_reference(args, w)
     if args.dt_scan:
         return run_dt_scan(args)
+    if args.app1:
+        return run_app1(args)
+    if args.dim == 1 and args.impl != "reference":
+        return run_1d(args)
     if args.ensemble:
         return run_ensemble(args)
     if args.surrogate:

@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -206,67 +207,100 @@ struct Ctrl1 {
   int status;
 };
 
-// one electron: gather -> Boris -> move -> 1D Esirkepov; removal after the deposit when it leaves
-// [z_lo, z_hi + dz)
+// one electron per thread: gather -> Boris -> move -> 1D Esirkepov; removal after the deposit when it
+// leaves [z_lo, z_hi + dz). The particles of a block are consecutive in memory and, injected row by row,
+// close in z: their current is summed in a shared window over the block's cells (one global atomic per
+// window node afterwards), else, for a block spread wider than the window, added to J directly.
+constexpr int PB1 = 128, JW1 = 320;
 template <class T, bool MC>
-__global__ void k1_push(G1 g, const T* fE, const T* fB, T* J, Parts1<T> p, const Ctrl1* ctrl, int order, T kq, T qe,
-                        double zlo, double zhi1) {
+__global__ void __launch_bounds__(PB1) k1_push(G1 g, const T* fE, const T* fB, T* J, Parts1<T> p, const Ctrl1* ctrl,
+                                               int order, T kq, T qe, double zlo, double zhi1) {
+  __shared__ T sJ[3][JW1];
+  __shared__ int s_lo, s_hi;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= ctrl->count) return;
-  const T w = p.w[j];
-  if (!(w > T(0))) return;
   const int n = g.n1p;
-  const double z = p.z[j];
-  const double Z = (z - g.z0) * g.idz;
-  const int f = (int)floor(Z);
-  T EB[6];
+  if (threadIdx.x == 0) { s_lo = INT_MAX; s_hi = INT_MIN; }
+  for (int e = threadIdx.x; e < 3 * JW1; e += blockDim.x) (&sJ[0][0])[e] = T(0);
+  __syncthreads();
+  const bool live = j < ctrl->count && p.w[j] > T(0);
+  double z = 0.0, Z = 0.0;
+  int f = 0;
+  if (live) {
+    z = p.z[j];
+    Z = (z - g.z0) * g.idz;
+    f = (int)floor(Z);
+    atomicMin(&s_lo, f);
+    atomicMax(&s_hi, f);
+  }
+  __syncthreads();
+  // the deposit of a particle in cell f (moving less than a cell) touches nodes f - 4 .. f + 5
+  const int base = s_lo - 5, span = s_hi - s_lo + 12;
+  const bool win = s_hi >= s_lo && span <= JW1;
+  if (live) {
+    const T w = p.w[j];
+    T EB[6];
 #pragma unroll
-  for (int c = 0; c < 6; c++) {
-    const T* F = c < 3 ? fE + c * n : fB + (c - 3) * n;
-    const double st = (!MC && half1(c)) ? 0.5 : 0.0;
-    T acc = T(0);
-    for (int k = f - 3; k <= f + 3; k++) {
+    for (int c = 0; c < 6; c++) {
+      const T* F = c < 3 ? fE + c * n : fB + (c - 3) * n;
+      const double st = (!MC && half1(c)) ? 0.5 : 0.0;
+      T acc = T(0);
+      for (int k = f - 3; k <= f + 3; k++) {
+        if (k < 0 || k > g.nz) continue;
+        const T wz = shp<T>(order, T(Z - (k + st)));
+        if (wz != T(0)) acc += F[k] * wz;
+      }
+      EB[c] = acc;
+    }
+    // relativistic Boris push (textbook)
+    T u0 = p.ux[j], u1 = p.uy[j], u2 = p.uz[j];
+    const T ic2 = T(1.0 / (kC * kC));
+    const T um0 = u0 + kq * EB[0], um1 = u1 + kq * EB[1], um2 = u2 + kq * EB[2];
+    const T gm = sqrt(T(1) + (um0 * um0 + um1 * um1 + um2 * um2) * ic2);
+    const T t0 = kq * EB[3] / gm, t1 = kq * EB[4] / gm, t2 = kq * EB[5] / gm;
+    const T tt = t0 * t0 + t1 * t1 + t2 * t2;
+    const T s0 = T(2) * t0 / (T(1) + tt), s1 = T(2) * t1 / (T(1) + tt), s2 = T(2) * t2 / (T(1) + tt);
+    const T up0 = um0 + (um1 * t2 - um2 * t1), up1 = um1 + (um2 * t0 - um0 * t2), up2 = um2 + (um0 * t1 - um1 * t0);
+    const T pl0 = um0 + (up1 * s2 - up2 * s1), pl1 = um1 + (up2 * s0 - up0 * s2), pl2 = um2 + (up0 * s1 - up1 * s0);
+    u0 = pl0 + kq * EB[0]; u1 = pl1 + kq * EB[1]; u2 = pl2 + kq * EB[2];
+    const T g1 = sqrt(T(1) + (u0 * u0 + u1 * u1 + u2 * u2) * ic2);
+    const double zn = z + g.dt * (double)(u2 / g1);
+    const double Zn = (zn - g.z0) * g.idz;
+    // 1D Esirkepov: Jz(k+1/2) = -(q w/dt) sum_{k' <= k} (S1 - S0)(k'); Jx, Jy = q w v (S0 + S1)/(2 dz)
+    const T qw = qe * w;
+    const T vx = u0 / g1, vy = u1 / g1;
+    const T cz = -qw / T(g.dt), ct = qw * T(0.5) * T(g.idz);
+    const int b = (int)floor(Z < Zn ? Z : Zn) - 3;
+    T run = T(0);
+    for (int a = 0; a < 9; a++) {
+      const int k = b + a;
+      const T S0 = shp<T>(order, T(Z - k)), S1 = shp<T>(order, T(Zn - k));
+      run += S1 - S0;
       if (k < 0 || k > g.nz) continue;
-      const T wz = shp<T>(order, T(Z - (k + st)));
-      if (wz != T(0)) acc += F[k] * wz;
+      const T ss = S0 + S1;
+      const T jz = cz * run, jx = ct * vx * ss, jy = ct * vy * ss;
+      const int l = k - base;
+      if (win && l >= 0 && l < span) {
+        if (jz != T(0)) atomicAdd(&sJ[2][l], jz);
+        if (jx != T(0)) atomicAdd(&sJ[0][l], jx);
+        if (jy != T(0)) atomicAdd(&sJ[1][l], jy);
+      } else {
+        if (jz != T(0)) atomicAdd(J + 2 * n + k, jz);
+        if (jx != T(0)) atomicAdd(J + k, jx);
+        if (jy != T(0)) atomicAdd(J + n + k, jy);
+      }
     }
-    EB[c] = acc;
+    p.z[j] = zn;
+    p.ux[j] = u0; p.uy[j] = u1; p.uz[j] = u2;
+    if (zn < zlo || zn >= zhi1) p.w[j] = T(0);
   }
-  // relativistic Boris push (textbook)
-  T u0 = p.ux[j], u1 = p.uy[j], u2 = p.uz[j];
-  const T ic2 = T(1.0 / (kC * kC));
-  const T um0 = u0 + kq * EB[0], um1 = u1 + kq * EB[1], um2 = u2 + kq * EB[2];
-  const T gm = sqrt(T(1) + (um0 * um0 + um1 * um1 + um2 * um2) * ic2);
-  const T t0 = kq * EB[3] / gm, t1 = kq * EB[4] / gm, t2 = kq * EB[5] / gm;
-  const T tt = t0 * t0 + t1 * t1 + t2 * t2;
-  const T s0 = T(2) * t0 / (T(1) + tt), s1 = T(2) * t1 / (T(1) + tt), s2 = T(2) * t2 / (T(1) + tt);
-  const T up0 = um0 + (um1 * t2 - um2 * t1), up1 = um1 + (um2 * t0 - um0 * t2), up2 = um2 + (um0 * t1 - um1 * t0);
-  const T pl0 = um0 + (up1 * s2 - up2 * s1), pl1 = um1 + (up2 * s0 - up0 * s2), pl2 = um2 + (up0 * s1 - up1 * s0);
-  u0 = pl0 + kq * EB[0]; u1 = pl1 + kq * EB[1]; u2 = pl2 + kq * EB[2];
-  const T g1 = sqrt(T(1) + (u0 * u0 + u1 * u1 + u2 * u2) * ic2);
-  const double zn = z + g.dt * (double)(u2 / g1);
-  const double Zn = (zn - g.z0) * g.idz;
-  // 1D Esirkepov: Jz(k+1/2) = -(q w/dt) sum_{k' <= k} (S1 - S0)(k'); Jx, Jy = q w v (S0 + S1)/(2 dz)
-  const T qw = qe * w;
-  const T vx = u0 / g1, vy = u1 / g1;
-  const T cz = -qw / T(g.dt), ct = qw * T(0.5) * T(g.idz);
-  const int b = (int)floor(Z < Zn ? Z : Zn) - 3;
-  T run = T(0);
-  for (int a = 0; a < 9; a++) {
-    const int k = b + a;
-    const T S0 = shp<T>(order, T(Z - k)), S1 = shp<T>(order, T(Zn - k));
-    run += S1 - S0;
-    if (k < 0 || k > g.nz) continue;
-    if (run != T(0)) atomicAdd(J + 2 * n + k, cz * run);
-    const T ss = S0 + S1;
-    if (ss != T(0)) {
-      if (vx != T(0)) atomicAdd(J + k, ct * vx * ss);
-      if (vy != T(0)) atomicAdd(J + n + k, ct * vy * ss);
+  __syncthreads();
+  if (win) {
+    for (int e = threadIdx.x; e < 3 * span; e += blockDim.x) {
+      const int q = e / span, l = e - q * span, k = base + l;
+      const T v = sJ[q][l];
+      if (v != T(0) && k >= 0 && k <= g.nz) atomicAdd(J + q * n + k, v);
     }
   }
-  p.z[j] = zn;
-  p.ux[j] = u0; p.uy[j] = u1; p.uz[j] = u2;
-  if (zn < zlo || zn >= zhi1) p.w[j] = T(0);
 }
 
 // plasma rows [m0, m0 + nrow): row m at z' = (m + 1/2) h - beta c t, density gamma n0(gamma (m + 1/2) h),
@@ -797,10 +831,10 @@ class Sim1 : public Sim3Api {
     if (loaded && count_ub > 0) {
       const T kq = T(-kQe * g.dt / (2.0 * kMe));
       if (nodal)
-        k1_push<T, true><<<nb1(count_ub, 128), 128, 0, s>>>(g, gE, gB, J, P2[cur], ctrl, cfg.shape_order, kq,
+        k1_push<T, true><<<nb1(count_ub, PB1), PB1, 0, s>>>(g, gE, gB, J, P2[cur], ctrl, cfg.shape_order, kq,
                                                            T(-kQe), z_lo(), z_hi() + g.dz);
       else
-        k1_push<T, false><<<nb1(count_ub, 128), 128, 0, s>>>(g, gE, gB, J, P2[cur], ctrl, cfg.shape_order, kq,
+        k1_push<T, false><<<nb1(count_ub, PB1), PB1, 0, s>>>(g, gE, gB, J, P2[cur], ctrl, cfg.shape_order, kq,
                                                             T(-kQe), z_lo(), z_hi() + g.dz);
       nl++;
     }

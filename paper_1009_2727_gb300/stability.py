@@ -54,3 +54,41 @@ def dt_scan(ratios, schemes=("energy", "momentum"), marks=(1200, 1800, 2400), wo
             s.close()
             out.append(rec)
     return out
+
+
+def nyquist_fraction(f: np.ndarray, margin: int) -> float:
+    """share of the power of a 1D field in its top quarter of wavenumbers (k dz > 3 pi/4), the band of the
+    odd-even mode of App. I, over the grid minus `margin` cells per side"""
+    seg = f[margin:-margin]
+    p = np.abs(np.fft.rfft(seg)) ** 2
+    kdz = np.arange(p.size) * 2 * np.pi / seg.size
+    tot = p.sum()
+    return float(p[kdz > 0.75 * np.pi].sum() / tot) if tot > 0 else 0.0
+
+
+def app1_runs(steps: int = 20000, precision: str = "mixed", every: int = 0) -> list[dict]:
+    """App. I's 1D scaled stage at c dt = dz with and without one bilinear pass on the current: per run
+    the Nyquist-band share of E_y and of E_z at the end (and every `every` steps when > 0), the peak
+    wake field and the electron count."""
+    from .pic import Simulation
+    out = []
+    for filtered in (False, True):
+        w = W.app1_lwfa(filtered)
+        s = Simulation(w, precision=precision)
+        rec = {"filtered": filtered, "steps": steps, "history": []}
+        done = 0
+        chunk = every if every > 0 else steps
+        while done < steps:
+            n = min(chunk, steps - done)
+            s.step(n)
+            done += n
+            ey, ez = s.field(1), s.field(2)
+            m = w["pml_cells"] + 10
+            rec["history"].append({"step": done, "nyq_Ey": nyquist_fraction(ey, m), "nyq_Ez": nyquist_fraction(ez, m),
+                                   "max_Ez": float(np.abs(ez[m:-m]).max()), "max_Ey": float(np.abs(ey[m:-m]).max())})
+        st = s.stats()
+        rec.update(rec["history"][-1])
+        rec["n_electrons"] = st["n_electrons"]
+        s.close()
+        out.append(rec)
+    return out
