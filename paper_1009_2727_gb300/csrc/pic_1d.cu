@@ -529,6 +529,7 @@ class Sim1 : public Sim3Api {
       if (freef) freef(p.first, p.second, (void*)s, user);
       else cudaFree(p.first);
     }
+    for (auto e : tev) cudaEventDestroy(e);
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
   }
@@ -772,17 +773,31 @@ class Sim1 : public Sim3Api {
     return 0.0;
   }
 
+  // event pairs around the timed launches, read when the timing is queried (no wait inside the step)
   void tbeg(int which) {
-    if (timing_on && timing_which == which) cudaEventRecord(ev0, s);
+    if (!(timing_on && timing_which == which)) return;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, s);
+    tev.push_back(a);
+    tev.push_back(b);
   }
   void tend(int which) {
-    if (!(timing_on && timing_which == which)) return;
-    cudaEventRecord(ev1, s);
-    cudaEventSynchronize(ev1);
-    float ms = 0;
-    cudaEventElapsedTime(&ms, ev0, ev1);
-    t_ms += ms;
+    if (!(timing_on && timing_which == which) || tev.empty()) return;
+    cudaEventRecord(tev.back(), s);
     t_n++;
+  }
+  void tcollect() {
+    if (tev.empty()) return;
+    cudaEventSynchronize(tev.back());
+    for (size_t i = 0; i + 1 < tev.size(); i += 2) {
+      float ms = 0;
+      cudaEventElapsedTime(&ms, tev[i], tev[i + 1]);
+      t_ms += ms;
+    }
+    for (auto e : tev) cudaEventDestroy(e);
+    tev.clear();
   }
 
   int one_step() {
@@ -1010,6 +1025,7 @@ class Sim1 : public Sim3Api {
   int kernel_timing(int enable, int which, double* ms_total, int64_t* n) override {
     if (which != 0 && which != 1) return PIC_EINVAL;
     if (!ev0) { cudaEventCreate(&ev0); cudaEventCreate(&ev1); }
+    tcollect();
     if (enable >= 0) {
       timing_on = enable != 0;
       timing_which = which;
@@ -1057,6 +1073,7 @@ class Sim1 : public Sim3Api {
   bool timing_on = false;
   int timing_which = 0;
   double t_ms = 0;
+  std::vector<cudaEvent_t> tev;
   int64_t t_n = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };

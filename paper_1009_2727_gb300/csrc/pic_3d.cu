@@ -1477,6 +1477,7 @@ struct Sim3 : Sim3Api {
   bool timing_on = false;
   int timing_which = 0;   // 0: the push kernel; 1: the field kernels (Faraday, Friedman, filters, Ampere)
   double t_ms = 0;
+  std::vector<cudaEvent_t> tev;
   int64_t t_n = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 
@@ -1486,6 +1487,7 @@ struct Sim3 : Sim3Api {
       if (freef) freef(a.first, a.second, (void*)s, user);
       else cudaFree(a.first);
     }
+    for (auto e : tev) cudaEventDestroy(e);
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
   }
@@ -1888,17 +1890,31 @@ struct Sim3 : Sim3Api {
   }
 
   // CUDA events around the launches of the timed kernel class (host waits for the end event)
+  // event pairs around the timed launches, read when the timing is queried (no wait inside the step)
   void tbeg(int which) {
-    if (timing_on && timing_which == which) cudaEventRecord(ev0, s);
+    if (!(timing_on && timing_which == which)) return;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, s);
+    tev.push_back(a);
+    tev.push_back(b);
   }
   void tend(int which) {
-    if (!(timing_on && timing_which == which)) return;
-    cudaEventRecord(ev1, s);
-    cudaEventSynchronize(ev1);
-    float ms = 0;
-    cudaEventElapsedTime(&ms, ev0, ev1);
-    t_ms += ms;
+    if (!(timing_on && timing_which == which) || tev.empty()) return;
+    cudaEventRecord(tev.back(), s);
     t_n++;
+  }
+  void tcollect() {
+    if (tev.empty()) return;
+    cudaEventSynchronize(tev.back());
+    for (size_t i = 0; i + 1 < tev.size(); i += 2) {
+      float ms = 0;
+      cudaEventElapsedTime(&ms, tev[i], tev[i + 1]);
+      t_ms += ms;
+    }
+    for (auto e : tev) cudaEventDestroy(e);
+    tev.clear();
   }
 
   int one_step() {
@@ -2159,6 +2175,7 @@ struct Sim3 : Sim3Api {
 
   int kernel_timing(int enable, int which, double* ms_total, int64_t* n) override {
     if (which != 0 && which != 1) return PIC_EINVAL;
+    tcollect();
     if (enable >= 0) {
       timing_on = enable != 0;
       timing_which = which;
