@@ -854,8 +854,10 @@ class Sim1 : public Sim3Api {
       nl++;
     }
     tend(0);
-    if (loaded && ions && row_next > mlo) {
-      k1_ion_jz<T><<<nb1(n1, 128), 128, 0, s>>>(g, lat, cfg.shape_order, mlo, row_next, tn, tn1, J + 2 * n);
+    // ions fixed in the lab: no current in the lab frame (beta = 0); 32-thread blocks spread the rows' FP64
+    // sums over more SMs
+    if (loaded && ions && row_next > mlo && beta > 0.0) {
+      k1_ion_jz<T><<<nb1(n1, 32), 32, 0, s>>>(g, lat, cfg.shape_order, mlo, row_next, tn, tn1, J + 2 * n);
       nl++;
     }
     // 4. antenna
