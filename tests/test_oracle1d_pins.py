@@ -152,3 +152,46 @@ def test_1d_linear_wake_lab_and_boosted(orc):
     s2.step(600)
     ez2, _, _ = _wake(s2, lp, sg, 2.0)
     assert ez2 == pytest.approx(ez_lin, rel=0.04)
+
+
+def _g(s, a, k):
+    return a + (1 - a) * np.cos(s * k)
+
+
+@pytest.mark.parametrize("n,stride,comp,strides", [(1, 1, 0, None), (4, 1, 1, None), (2, 3, 1, None),
+                                                   (4, 1, 1, (1, 2, 4))])
+def test_1d_filter_gain_single_mode(orc, n, stride, comp, strides):
+    """Sec. 4.1 in 1D: the filter multiplies an interior mode cos(k z) by the product of the pass gains
+    g(s, 1/2, k)^n g(s, n/2 + 1, k) over its strides"""
+    nz = 200
+    w = vac1(nz, filter_passes=n, filter_stride=stride, filter_compensate=comp)
+    if strides:
+        w["filter_strides"] = list(strides)
+    s = orc.Sim1(w)
+    kk = np.arange(nz + 1)
+    for m in (5, 17, 40):
+        k = 2 * np.pi * m / nz
+        f = np.cos(k * kk + 0.3)
+        got = s.filter_field(1, f)
+        gain = 1.0
+        for st in (strides or (stride,)):
+            gain *= _g(st, 0.5, k) ** n * (_g(st, n / 2 + 1, k) if comp else 1.0)
+        H = (n + comp) * sum(strides or (stride,))
+        sl = slice(H + 2, nz - H - 2)
+        assert np.abs(got[sl] - gain * f[sl]).max() < 1e-12
+
+
+def test_1d_momentum_conserving_gather_node_values(orc):
+    """Sec. 5 in 1D: the node value of a half-staggered gather copy (E_z, B_x, B_y) is the mean of its two
+    neighbours: a quadratic Z^2 at the half positions gains exactly 1/4 at the nodes"""
+    nz = 60
+    s = orc.Sim1(vac1(nz, gather="momentum"))
+    K = np.arange(nz + 1, dtype=float)
+    s.set_field(2, (K + 0.5) ** 2)            # E_z, curl free and static without current
+    s.set_field(3, 2.0 * (K + 0.5) + 1.0)     # B_x: Faraday leaves it (E_y = 0)
+    s.set_field(4, -(K + 0.5) ** 2)           # B_y: E_x = 0
+    s.step(1)
+    sl = slice(2, nz - 2)
+    assert np.abs(s.gather_field(2)[sl] - (K ** 2 + 0.25)[sl]).max() < 1e-12 * (nz ** 2)
+    assert np.abs(s.gather_field(3)[sl] - (2.0 * K + 1.0)[sl]).max() < 1e-12 * nz
+    assert np.abs(s.gather_field(4)[sl] + (K ** 2 + 0.25)[sl]).max() < 1e-12 * (nz ** 2)
