@@ -83,12 +83,18 @@ extern "C" int pic_autotune(const pic_config* cfg, const pic_plasma* plasma, con
   r.struct_size = sizeof(pic_tune_result);
   r.version = PIC_API_VERSION;
   const int warm = 4;
-  // 1. tile shape at the default cadence
+  // one untimed trial first: the GPU reaches its clocks before the candidates are compared
+  trial(cfg, plasma, laser, kTiles[0], kTiles[2], 32, warm, steps, alloc, free_fn, alloc_user, cuda_stream);
+  // 1. tile shape at the default cadence; each tile timed twice, the faster time counts
   double best = -1.0;
   int btx = 0, btz = 0;
   for (int tx : kTiles)
     for (int tz : kTiles) {
-      const double ms = trial(cfg, plasma, laser, tx, tz, 32, warm, steps, alloc, free_fn, alloc_user, cuda_stream);
+      double ms = -1.0;
+      for (int rep = 0; rep < 2; rep++) {
+        const double m = trial(cfg, plasma, laser, tx, tz, 32, warm, steps, alloc, free_fn, alloc_user, cuda_stream);
+        if (m > 0.0 && (ms < 0.0 || m < ms)) ms = m;
+      }
       record(&r, tx, tz, 32, ms);
       if (ms > 0.0 && (best < 0.0 || ms < best)) { best = ms; btx = tx; btz = tz; }
     }
