@@ -69,3 +69,32 @@ def test_ctypes_mirrors_match_c_layout(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(py), cname
         for f in py._fields_:
             assert got[(cname, f[0])] == getattr(py, f[0]).offset, (cname, f[0])
+
+
+def _cfg(**over):
+    from paper_1009_2727_gb300 import workloads as W
+    from paper_1009_2727_gb300.pic import make_config
+    w = W.parity_2d()
+    w.update(over)
+    return make_config(w, capi.PIC_MIXED)
+
+
+def test_init_validates_filter_gather_and_dim_before_gpu_work():
+    """configurations the host rejects before any CUDA call: an unknown dimension or gather scheme, a stride
+    set with a gap or a negative entry, a filter halo wider than 40 cells, more than 16 passes per stride"""
+    L = capi.load()
+    bad = [
+        _cfg(dim=4),
+        _cfg(gather="energy"),
+        _cfg(filter_passes=4, filter_compensate=1, filter_strides=[1, 2, 4, 8]),   # halo 75
+        _cfg(filter_passes=17),
+    ]
+    bad[1].gather_scheme = 2
+    gap = _cfg(filter_passes=1, filter_strides=[1, 0, 2])
+    neg = _cfg(filter_passes=1)
+    neg.filter_stride_set[0] = -1
+    bad += [gap, neg]
+    for c in bad:
+        h = ctypes.c_void_p()
+        r = L.pic_init(ctypes.byref(c), capi.ALLOC_FN(), capi.FREE_FN(), None, None, ctypes.byref(h))
+        assert r == capi.PIC_EINVAL and not h.value
