@@ -195,3 +195,23 @@ def test_1d_momentum_conserving_gather_node_values(orc):
     assert np.abs(s.gather_field(2)[sl] - (K ** 2 + 0.25)[sl]).max() < 1e-12 * (nz ** 2)
     assert np.abs(s.gather_field(3)[sl] - (2.0 * K + 1.0)[sl]).max() < 1e-12 * nz
     assert np.abs(s.gather_field(4)[sl] + (K ** 2 + 0.25)[sl]).max() < 1e-12 * (nz ** 2)
+
+
+@pytest.mark.parametrize("scheme,extra", [("energy", 0.0), ("momentum", 0.25)])
+def test_1d_gather_schemes_on_quadratic_field(orc, scheme, extra):
+    """electrons at rest in a static E_z = Z^2 sampled at the half nodes: one Boris step gives
+    u_z = (q/m) dt (Z^2 + 1/3 [cubic spline variance] + 1/4 [node interpolation, 'momentum conserving'])"""
+    nz = 60
+    w = vac1(nz, gather=scheme)
+    w["plasma"] = {"n0": 1e10, "z_start_lab": 0.0, "ramp_lab": 0.0, "length_lab": 0.0, "ppc_z": 3, "ions": 0}
+    s = orc.Sim1(w)
+    K = np.arange(nz + 1, dtype=float)
+    s.set_field(2, (K + 0.5) ** 2)
+    s.step(1)
+    p = s.particles(0)
+    assert p["z"].size > 20
+    # the position before the step: z moved by dt u_z / gamma
+    g = np.sqrt(1 + (p["uz"] / C) ** 2)
+    Z = (p["z"] - s.dt * p["uz"] / g) / s.dz
+    ez = p["uz"] / (-QE / ME * s.dt)
+    assert np.abs(ez - (Z ** 2 + 1.0 / 3.0 + extra)).max() < 1e-9 * np.abs(Z ** 2).max()

@@ -253,3 +253,26 @@ def test_3d_momentum_conserving_gather_copies_at_the_nodes(orc):
     for c in range(6):
         got = s.gather_field(c)
         assert np.abs(got[sl] - want[c][sl]).max() < 1e-12 * np.abs(want[c][sl]).max(), c
+
+
+@pytest.mark.parametrize("scheme,extra", [("energy", 0.0), ("momentum", 0.25)])
+def test_3d_gather_schemes_on_quadratic_field(orc, scheme, extra):
+    """electrons at rest in a static E_x = X^2 (X = x/dx; uniform in y and z): one Boris step gives
+    u_x = (q/m) dt E_x at the particle. The cubic B-spline adds its variance 1/3 (times f''/2 = 1); the
+    node-interpolated ('momentum conserving') gather adds 1/4 more, from averaging the staggered samples
+    (i + 1/2)^2 to the nodes"""
+    n = (16, 12, 14)
+    w = vacuum3(*n, periodic=False, gather=scheme)
+    w["plasma"] = {"n0": 1e10, "z_start_lab": 0.0, "ramp_lab": 0.0, "length_lab": 0.0, "ppc_x": 2, "ppc_y": 1,
+                   "ppc_z": 1, "ions": 0}
+    s = orc.Sim3(w)
+    I = np.arange(n[0] + 1, dtype=float)[:, None, None] * np.ones((1, n[1] + 1, n[2] + 1))
+    s.set_field(0, (I + 0.5) ** 2)
+    s.step(1)
+    p = s.particles(0)
+    p = {k: v[p["alive"]] for k, v in p.items()}
+    assert p["x"].size > 10
+    X = p["x"] / s.dx
+    qe, me = 1.602176634e-19, 9.1093837015e-31
+    ex = p["ux"] / (-qe / me * s.dt)
+    assert np.abs(ex - (X ** 2 + 1.0 / 3.0 + extra)).max() < 1e-9 * np.abs(X ** 2).max()
