@@ -544,6 +544,9 @@ def main():
     ap.add_argument("--app1", action="store_true",
                     help="App. I: the 1D scaled stage at c dt = dz over 20000 steps, unfiltered and with one "
                          "bilinear pass on the current (Nyquist-band share of E_y, wake field)")
+    ap.add_argument("--solver", default="", help="field-solver preset instead of the workload's (yee, ck, ck2, ...)")
+    ap.add_argument("--theta", type=float, default=-1.0, help="Friedman damping instead of the workload's")
+    ap.add_argument("--no-filter", action="store_true", help="no filter on the current and the gathered fields")
     ap.add_argument("--gather", default="energy", choices=["energy", "momentum"],
                     help="momentum: the 'momentum conserving' gather (fields interpolated to the nodes first)")
     ap.add_argument("--dt-scan", action="store_true",
@@ -561,6 +564,13 @@ def main():
     w["order"] = args.order
     w["precision"] = args.precision
     w["gather"] = args.gather
+    if args.solver:
+        w["solver"] = W.SOLVERS[args.solver]
+    if args.theta >= 0.0:
+        w["theta"] = args.theta
+    if args.no_filter:
+        w["filter_J"] = 0
+        w["filter_gather"] = 0
     if args.filter_strides:
         w = wide_band(w, [int(v) for v in args.filter_strides.split(",")], three)
     if args.impl == "reference":
@@ -632,7 +642,9 @@ def main():
     sim.step(kf)
     field_ms, _ = sim.timing(False)
     sim.sync()
-    n_e1 = sim.stats()["n_electrons"]
+    st1 = sim.stats()
+    n_e1 = st1["n_electrons"]
+    dt_s = st1["dt"]
     n_avg = 0.5 * (n_e + n_e1)
     value, ms_max = job_throughput(n_avg * args.steps, ms, ws)
     # roofline of the dominant kernel
@@ -700,12 +712,12 @@ def main():
             "config": {"workload": w["name"],
                        "grid": [w["nz"], w["ny"], w["nx"]] if three else [w["nz"], w["nx"]],
                        "ppc": 2 if three else 16, "gamma_boost": w["gamma_boost"],
-                       "solver": "CK2" if three else "CK", "theta": w["theta"],
-                       "filter": "4 passes + compensation" + (
+                       "solver": args.solver or ("CK2" if three else "CK"), "theta": w["theta"],
+                       "filter": "none" if args.no_filter else "4 passes + compensation" + (
                            " at each stride of S(" + ":".join(str(v) for v in w["filter_strides"]) + ")"
                            if w.get("filter_strides") else ""),
                        "shape_order": args.order, "precision": args.precision, "electrons": int(n_avg),
-                       "gather": args.gather,
+                       "gather": args.gather, "dt_s": dt_s,
                        "layout": ({"tile_x": tuned["tile"][0], "tile_z": tuned["tile"][1],
                                    "sort_every": tuned["sort_every"],
                                    "source": "--tile" if args.tile else "pic_autotune",

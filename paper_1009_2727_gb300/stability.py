@@ -57,8 +57,8 @@ def dt_scan(ratios, schemes=("energy", "momentum"), marks=(1200, 1800, 2400), wo
 
 
 def nyquist_fraction(f: np.ndarray, margin: int) -> float:
-    """share of the power of a 1D field in its top quarter of wavenumbers (k dz > 3 pi/4), the band of the
-    odd-even mode of App. I, over the grid minus `margin` cells per side"""
+    """share of the one-sided power spectrum of a 1D field in its top quarter of wavenumbers (k dz > 3 pi/4),
+    the band of the odd-even mode of App. I, over the grid minus `margin` cells per side"""
     seg = f[margin:-margin]
     p = np.abs(np.fft.rfft(seg)) ** 2
     kdz = np.arange(p.size) * 2 * np.pi / seg.size
