@@ -75,3 +75,21 @@ def test_reference_arm_other_ranks_do_no_work(monkeypatch, capsys):
     # rank 1 returns at once: no oracle run, nothing printed
     assert bench.run_reference(A, {"nx": 8, "nz": 8, "name": "x"}) == 0
     assert capsys.readouterr().out == ""
+
+
+def test_wide_band_workload_puts_the_antenna_inside_the_wider_domain():
+    """bench --filter-strides: the particle guard grows with the filter halo ((4 + 1) x 7 = 35 cells for
+    S(1:2:4)), and the antenna, which emits only inside the particle domain, moves past it"""
+    import oracle
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    from paper_1009_2727_gb300 import workloads as W
+    w = W.shrink(W.stage_2d(), 128, 320)
+    w["order"] = 3
+    ww = bench.wide_band(w, [1, 2, 4], False)
+    assert ww["filter_strides"] == [1, 2, 4] and w.get("filter_strides") is None
+    o = oracle.Sim(ww)
+    info = o.info()
+    assert info["guard"] == 3 + 35 + 2
+    zlo = info["gz_lo"] * info["dz"]
+    assert ww["laser"]["z_antenna"] >= zlo + 4 * info["dz"] - 1e-12
