@@ -28,6 +28,10 @@ _SRCS = [os.path.join(_HERE, "pic_oracle.c"), os.path.join(_HERE, "pic_oracle3d.
 _lock = threading.Lock()
 _lib = None
 
+C = 299792458.0
+QE = 1.602176634e-19
+EPS0 = 8.8541878128e-12
+
 # component ids used by the oracle: E, B, J
 EX, EY, EZ, BX, BY, BZ, JX, JY, JZ = range(9)
 COMPONENTS = ("Ex", "Ey", "Ez", "Bx", "By", "Bz", "Jx", "Jy", "Jz")
@@ -60,7 +64,7 @@ class _Config(ctypes.Structure):
         ("order", ctypes.c_int), ("particle_guard", ctypes.c_int),
         ("periodic_x", ctypes.c_int), ("periodic_z", ctypes.c_int),
         ("moving_window", ctypes.c_int), ("window_beta", ctypes.c_double),
-        ("filter_strides", ctypes.c_int * 4), ("gather_nodal", ctypes.c_int),
+        ("filter_strides", ctypes.c_int * 4), ("gather_nodal", ctypes.c_int), ("beam_self", ctypes.c_int),
     ]
 
 
@@ -168,6 +172,7 @@ def lib():
             L.orc_filter_field.argtypes = [ctypes.c_void_p, ctypes.c_int, _D]
             L.orc_deposit_one.argtypes = [ctypes.c_void_p, _D, _D, _D] + [ctypes.c_double] * 6
             L.orc_rho_one.argtypes = [ctypes.c_void_p, _D] + [ctypes.c_double] * 3
+            L.orc_beam_weights.argtypes = [ctypes.c_void_p, _D]
             L.orc_shape.restype = ctypes.c_double
             L.orc_shape.argtypes = [ctypes.c_int, ctypes.c_double]
             L.orc_cfl_2d.restype = ctypes.c_double
@@ -276,6 +281,7 @@ def _mk_config(w: dict) -> _Config:
     for q, v in enumerate(list(w.get("filter_strides", []))[:4]):
         c.filter_strides[q] = int(v)
     c.gather_nodal = 1 if w.get("gather", "energy") == "momentum" else 0
+    c.beam_self = int(w.get("beam_self", 0))
     return c
 
 
@@ -310,9 +316,10 @@ class Sim:
 
     # -- state ------------------------------------------------------------
     def info(self) -> dict:
-        o = np.zeros(13)
+        o = np.zeros(14)
         self.L.orc_info(self.h, _p(o))
-        keys = ("dx", "dz", "dt", "gamma", "beta", "z0", "step", "t", "guard", "gx_lo", "gx_hi", "gz_lo", "gz_hi")
+        keys = ("dx", "dz", "dt", "gamma", "beta", "z0", "step", "t", "guard", "gx_lo", "gx_hi", "gz_lo", "gz_hi",
+                "beam_vbar")
         return dict(zip(keys, o.tolist()))
 
     def step(self, n: int = 1):
@@ -383,6 +390,57 @@ class Sim:
     def set_beam(self, x, z, ux, uy, uz, t_lab: float, z_plane: float):
         a = [np.ascontiguousarray(v, dtype=np.float64) for v in (x, z, ux, uy, uz)]
         self.L.orc_set_beam(self.h, a[0].size, *(_p(v) for v in a), float(t_lab), float(z_plane))
+
+    def beam_weights(self, w):
+        """macro-particle weights of the test beam (per unit length along y), in the order it was given"""
+        a = np.ascontiguousarray(w, dtype=np.float64)
+        self._beam_w = a
+        self.L.orc_beam_weights(self.h, _p(a))
+
+    def beam_rho(self, shift: float = 0.0) -> np.ndarray:
+        """charge density of the frozen beam particles, their positions taken `shift` seconds from now"""
+        v = self.info()["beam_vbar"]
+        p = self.particles(2)
+        rho = np.zeros((self.nx + 1) * (self.nz + 1))
+        for j in range(len(p["x"])):
+            if p["alive"][j] and not p["active"][j]:
+                self.L.orc_rho_one(self.h, _p(rho), p["x"][j], p["z"][j] + v * shift, -QE * p["w"][j])
+        return rho.reshape(self.nx + 1, self.nz + 1)
+
+    def beam_self_field(self, shift: float = 0.0) -> dict:
+        """Self-field of the frozen beam (Sec. 3.1.1: the fields at the injection plane must be consistent
+        with the beam): its charge moves rigidly at the mean velocity v along z, so in the computational frame
+        phi solves d2phi/dx2 + d2phi/dz2 / gamma_v^2 = -rho/eps0 (zero on the grid edges, the PEC walls),
+        E_x = -dphi/dx, E_z = -dphi/dz / gamma_v^2, B_y = v E_x / c^2. The discrete operators are those of
+        the Yee mesh (second differences for phi, one-sided differences for E at its half positions), so the
+        discrete Gauss law holds exactly; the DST-I diagonalises them. The beam's positions are taken
+        `shift` seconds from now (frozen particles move at v). Returns Ex, Ez, By on the grid."""
+        from scipy.fft import dstn, idstn
+        v = self.info()["beam_vbar"]
+        gv2 = 1.0 / (1.0 - (v / C) ** 2)
+        rho = self.beam_rho(shift)
+        nx, nz, dx, dz = self.nx, self.nz, self.dx, self.dz
+        lx = -(2.0 - 2.0 * np.cos(np.pi * np.arange(1, nx) / nx)) / dx ** 2
+        lz = -(2.0 - 2.0 * np.cos(np.pi * np.arange(1, nz) / nz)) / dz ** 2
+        rh = dstn(rho[1:nx, 1:nz], type=1)
+        ph = -rh / EPS0 / (lx[:, None] + lz[None, :] / gv2)
+        phi = np.zeros((nx + 1, nz + 1))
+        phi[1:nx, 1:nz] = idstn(ph, type=1)
+        ex = np.zeros_like(phi)
+        ez = np.zeros_like(phi)
+        by = np.zeros_like(phi)
+        ex[:nx, :] = -(phi[1:, :] - phi[:-1, :]) / dx                     # (i + 1/2, k)
+        ez[:, :nz] = -(phi[:, 1:] - phi[:, :-1]) / dz / gv2               # (i, k + 1/2)
+        by[:nx, :nz] = v / C ** 2 * 0.5 * (ex[:nx, :nz] + ex[:nx, 1:])     # (i + 1/2, k + 1/2)
+        return {"Ex": ex, "Ez": ez, "By": by, "vbar": v}
+
+    def add_beam_self_field(self):
+        """add the frozen beam's self-field: E at the current time, B half a step earlier (B^{n-1/2})"""
+        fe = self.beam_self_field(0.0)
+        fb = self.beam_self_field(-0.5 * self.dt)
+        self.set_field(EX, self.field(EX) + fe["Ex"])
+        self.set_field(EZ, self.field(EZ) + fe["Ez"])
+        self.set_field(BY, self.field(BY) + fb["By"])
 
     def diag(self) -> dict:
         o = np.zeros(5)

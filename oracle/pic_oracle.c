@@ -71,6 +71,9 @@ typedef struct {
                                  (n passes + compensation) at each stride, e.g. 1,2,3 for S(1:2:3); else 0 */
   int gather_nodal;           /* 0: 'energy conserving' gather from the Yee locations (Sec. 5);
                                  1: 'momentum conserving': the fields are first interpolated to the nodes */
+  int beam_self;              /* 1: the test beam's frozen and active particles deposit their current
+                                 (Sec. 3.1.1: the charge and current of the frozen particles keep the fields
+                                 at the injection plane consistent); 0: test particles */
 } orc_config;
 
 typedef struct {
@@ -520,6 +523,12 @@ static void deposit_rho(const orc_sim* s, double* rho, double x, double z, doubl
 
 void orc_rho_one(orc_sim* s, double* rho, double x, double z, double qw) { deposit_rho(s, rho, x, z, qw); }
 
+/* weights (macro-particle counts per unit length along y) of the test beam, in the order it was given */
+void orc_beam_weights(orc_sim* s, const double* w) {
+  orc_species* b = &s->sp[2];
+  for (long j = 0; j < b->n; j++) b->w[j] = w[j];
+}
+
 /* ------------------------------------------------------------------ */
 /* species storage */
 static void sp_reserve(orc_species* p, long n) {
@@ -641,6 +650,7 @@ void orc_info(const orc_sim* s, double* out) {
   out[0] = s->dx; out[1] = s->dz; out[2] = s->dt; out[3] = s->gamma; out[4] = s->beta;
   out[5] = s->z0; out[6] = (double)s->step; out[7] = time_of(s, s->step);
   out[8] = s->c.particle_guard; out[9] = s->gx_lo; out[10] = s->gx_hi; out[11] = s->gz_lo; out[12] = s->gz_hi;
+  out[13] = s->beam_vbar;
 }
 
 /* ------------------------------------------------------------------ */
@@ -930,7 +940,12 @@ static void one_step(orc_sim* s) {
           /* a particle whose crossing lies outside the particle domain never enters it (PR-20) */
           if (p->x[q] < xlo || p->x[q] >= xhi || p->z[q] < zlo || p->z[q] >= zhi) { p->alive[q] = 0; continue; }
         } else {
-          p->z[q] = p->zf0[q] + s->beam_vbar * tn1;
+          const double zn = p->zf0[q] + s->beam_vbar * tn1;
+          /* a frozen particle inside the particle domain carries its charge along z at the mean velocity */
+          if (s->c.beam_self && p->x[q] >= xlo && p->x[q] < xhi && p->z[q] >= zlo && p->z[q] < zhi && zn >= zlo &&
+              zn < zhi)
+            esirkepov(s, s->F[OJX], s->F[OJY], s->F[OJZ], p->x[q], p->z[q], p->x[q], zn, 0.0, p->q * p->w[q]);
+          p->z[q] = zn;
           continue;
         }
       }
@@ -949,7 +964,8 @@ static void one_step(orc_sim* s) {
         p->z[q] = p->zl[q] - s->beta * O_C * tn;
         zn = p->zl[q] - s->beta * O_C * tn1;
       }
-      if (j != 2) esirkepov(s, s->F[OJX], s->F[OJY], s->F[OJZ], p->x[q], p->z[q], xn, zn, u[1] / gm, p->q * p->w[q]);
+      if (j != 2 || s->c.beam_self)
+        esirkepov(s, s->F[OJX], s->F[OJY], s->F[OJZ], p->x[q], p->z[q], xn, zn, u[1] / gm, p->q * p->w[q]);
       p->x[q] = xn; p->z[q] = zn; p->ux[q] = u[0]; p->uy[q] = u[1]; p->uz[q] = u[2];
       if (xn < xlo || xn >= xhi || zn < zlo || zn >= zhi) p->alive[q] = 0;
     }
