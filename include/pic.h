@@ -135,7 +135,13 @@ typedef struct {
   double beam_t_lab, beam_z_plane_lab;
   const double* beam_y;   /* 3D: beam y positions (host, beam_n values) */
   int32_t ppc_y;          /* 3D: macro-particles per cell along y (0 = 1) */
-  int32_t reserved[5];
+  int32_t beam_self;      /* 2D: 1 = self-consistent beam (Sec. 3.1.1): its frozen particles inside the
+                             particle domain deposit the current of their move at the mean velocity and
+                             its active particles deposit like the plasma; needs beam_w. The caller sets
+                             the beam's initial self-field (pic_set_field). 0 = test particles */
+  const double* beam_w;   /* beam weights: macro-particle counts per unit length along y (host, beam_n
+                             values; read only with beam_self) */
+  int32_t reserved[2];
 } pic_plasma;
 
 /* Gaussian laser injected through a plane (Sec. 3.1.2). The lab waveform at the

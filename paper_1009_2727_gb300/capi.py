@@ -67,7 +67,8 @@ class PicPlasma(ctypes.Structure):
         ("beam_n", ctypes.c_int64),
         ("beam_x", _D), ("beam_z", _D), ("beam_ux", _D), ("beam_uy", _D), ("beam_uz", _D),
         ("beam_t_lab", ctypes.c_double), ("beam_z_plane_lab", ctypes.c_double),
-        ("beam_y", _D), ("ppc_y", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5),
+        ("beam_y", _D), ("ppc_y", ctypes.c_int32), ("beam_self", ctypes.c_int32), ("beam_w", _D),
+        ("reserved", ctypes.c_int32 * 2),
     ]
 
 

@@ -1800,6 +1800,7 @@ struct Sim3 : Sim3Api {
       cudaStreamSynchronize(s);
     }
     // optional test beam
+    if (p->beam_n > 0 && p->beam_self) return fail(PIC_EINVAL, "3D: the self-consistent beam is 2D only");
     if (p->beam_n > 0) {
       if (!p->beam_x || !p->beam_y || !p->beam_z || !p->beam_ux || !p->beam_uy || !p->beam_uz)
         return fail(PIC_EINVAL, "3D test beam needs x, y, z and the three momenta");

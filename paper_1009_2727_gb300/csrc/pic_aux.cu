@@ -183,6 +183,50 @@ __device__ T gather_global(const T* F, const GridP& g, int order, double X, doub
   return T(acc);
 }
 
+// Esirkepov deposit of one beam particle (charge * weight qw per unit length along y) moving (x0, z0) ->
+// (x1, z1) with out-of-plane velocity vy, into the global current with atomics (a beam has few particles):
+// Jx(i+1/2) - Jx(i-1/2) = -qw/(dz dt) Wx(i), Wx = DSx (S0z + DSz/2); likewise for Jz; Jy = qw vy Wy/(dx dz),
+// Wy = S0x S0z + DSx S0z/2 + S0x DSz/2 + DSx DSz/3 (Esirkepov 2001)
+template <class T>
+__device__ void beam_deposit(const GridP& g, const FieldPtrs<T>& f, int order, double x0, double z0, double x1,
+                             double z1, double vy, double qw) {
+  constexpr int EW = 9;
+  const double X0 = x0 / g.dx, Z0 = (z0 - g.z0) / g.dz, X1 = x1 / g.dx, Z1 = (z1 - g.z0) / g.dz;
+  const int bx = (int)floor(X0 < X1 ? X0 : X1) - 3, bz = (int)floor(Z0 < Z1 ? Z0 : Z1) - 3;
+  double S0x[EW], DSx[EW], S0z[EW], DSz[EW];
+  for (int a = 0; a < EW; a++) {
+    S0x[a] = shape_val(order, X0 - (bx + a));
+    DSx[a] = shape_val(order, X1 - (bx + a)) - S0x[a];
+    S0z[a] = shape_val(order, Z0 - (bz + a));
+    DSz[a] = shape_val(order, Z1 - (bz + a)) - S0z[a];
+  }
+  const double cx = -qw / (g.dz * g.dt), cz = -qw / (g.dx * g.dt), cy = qw * vy / (g.dx * g.dz);
+  for (int b = 0; b < EW; b++) {
+    double acc = 0.0;
+    for (int a = 0; a < EW; a++) {
+      acc += cx * DSx[a] * (S0z[b] + 0.5 * DSz[b]);
+      const int i = bx + a, k = bz + b;
+      if (acc != 0.0 && i >= 0 && i <= g.nx && k >= 0 && k <= g.nz) atomicAdd(f.J[0] + (long)i * g.ld + k, T(acc));
+    }
+  }
+  for (int a = 0; a < EW; a++) {
+    double acc = 0.0;
+    for (int b = 0; b < EW; b++) {
+      acc += cz * DSz[b] * (S0x[a] + 0.5 * DSx[a]);
+      const int i = bx + a, k = bz + b;
+      if (acc != 0.0 && i >= 0 && i <= g.nx && k >= 0 && k <= g.nz) atomicAdd(f.J[2] + (long)i * g.ld + k, T(acc));
+    }
+  }
+  if (vy != 0.0)
+    for (int a = 0; a < EW; a++)
+      for (int b = 0; b < EW; b++) {
+        const double wy = S0x[a] * S0z[b] + 0.5 * DSx[a] * S0z[b] + 0.5 * S0x[a] * DSz[b] + DSx[a] * DSz[b] / 3.0;
+        const int i = bx + a, k = bz + b;
+        if (wy != 0.0 && i >= 0 && i <= g.nx && k >= 0 && k <= g.nz)
+          atomicAdd(f.J[1] + (long)i * g.ld + k, T(cy * wy));
+      }
+}
+
 template <class T>
 __global__ void k_beam_push(GridP g, FieldPtrs<T> f, Beam<T> b, int order, double tn, double tn1, int nodal,
                             const double* acc) {
@@ -202,7 +246,11 @@ __global__ void k_beam_push(GridP g, FieldPtrs<T> f, Beam<T> b, int order, doubl
       b.flag[j] = fl;
       if (!(fl & 1)) return;
     } else {
-      b.z[j] = b.zf0[j] + acc[2] * tn1;
+      const double z0 = b.z[j], z1 = b.zf0[j] + acc[2] * tn1, x0 = b.x[j];
+      // self-consistent beam: a frozen particle inside the particle domain carries its charge along z
+      if (b.self && x0 >= xlo && x0 < xhi && z0 >= zlo && z0 < zhi && z1 >= zlo && z1 < zhi)
+        beam_deposit<T>(g, f, order, x0, z0, x0, z1, 0.0, -kQe * (double)b.w[j]);
+      b.z[j] = z1;
       return;
     }
   }
@@ -233,6 +281,7 @@ __global__ void k_beam_push(GridP g, FieldPtrs<T> f, Beam<T> b, int order, doubl
   const T g1 = sqrt(T(1) + (ux * ux + uy * uy + uz * uz) * ic2);
   const double xn = x + g.dt * (double)(ux / g1);
   const double zn = z + g.dt * (double)(uz / g1);
+  if (b.self) beam_deposit<T>(g, f, order, x, z, xn, zn, (double)(uy / g1), -kQe * (double)b.w[j]);
   b.x[j] = xn; b.z[j] = zn; b.ux[j] = ux; b.uy[j] = uy; b.uz[j] = uz;
   if (xn < xlo || xn >= xhi || zn < zlo || zn >= zhi) b.flag[j] = fl & ~1;
 }

@@ -420,6 +420,17 @@ struct Sim : SimBase {
       beam.x = al<double>(n); beam.z = al<double>(n); beam.ux = al<T>(n); beam.uy = al<T>(n); beam.uz = al<T>(n);
       beam.tc = al<double>(n); beam.zf0 = al<double>(n); beam.uxb = al<T>(n); beam.uyb = al<T>(n); beam.uzb = al<T>(n);
       beam.flag = al<int>(n);
+      if (p->beam_self) {
+        // self-consistent beam: weights (per unit length along y), converted to the path's type
+        if (!p->beam_w) return c->fail(PIC_EINVAL, "beam_self needs beam_w");
+        std::vector<T> wv(n);
+        for (int q = 0; q < n; q++) wv[q] = T(p->beam_w[q]);
+        beam.w = al<T>(n);
+        if (!beam.w) return c->fail(PIC_ENOMEM, "beam allocation failed");
+        cudaMemcpyAsync(beam.w, wv.data(), sizeof(T) * n, cudaMemcpyHostToDevice, c->stream);
+        cudaStreamSynchronize(c->stream);
+        beam.self = 1;
+      }
       beam_scratch = al<double>(4);
       double* lab = al<double>(5 * (size_t)n);
       if (!beam.x || !beam.flag || !lab || !beam_scratch) return c->fail(PIC_ENOMEM, "beam allocation failed");

@@ -295,6 +295,8 @@ struct Beam {
   double* x; double* z; T* ux; T* uy; T* uz;
   double* tc; double* zf0; T* uxb; T* uyb; T* uzb; int* flag;  // bit0 alive, bit1 active
   int n;
+  int self;   // 1: the beam deposits its current (frozen and active particles); weights in w
+  T* w;
 };
 template <class T>
 void launch_beam_init(Beam<T> b, const double* lx, const double* lz, const double* lux, const double* luy,

@@ -88,6 +88,11 @@ def make_plasma(p: dict | None, beam: dict | None, keep: list) -> capi.PicPlasma
             pl.beam_y = _p(ya)
         pl.beam_t_lab = float(beam.get("t_lab", 0.0))
         pl.beam_z_plane_lab = float(beam["z_plane_lab"])
+        if beam.get("self"):
+            wa = np.ascontiguousarray(beam["w"], dtype=np.float64)
+            keep.append(wa)
+            pl.beam_self = 1
+            pl.beam_w = _p(wa)
     return pl
 
 

@@ -224,6 +224,42 @@ def test_test_beam_and_lab_stations_fp64(Sim, orc, gather):
     assert g.stats()["beam_gamma_lab"] == pytest.approx(o.diag()["gamma_lab"], rel=1e-12)
 
 
+def test_self_consistent_beam_fp64(Sim, orc):
+    """self-consistent test beam (Sec. 3.1.1): the frozen beam (2000 particles, gamma 2, 1 uC per metre along
+    y) starts from its self-field (solved by the oracle, the input of both runs) and deposits its current
+    while it moves; 100 FP64 steps against the oracle"""
+    nx, nz = 64, 256
+    w = {"name": "beam_self", "nx": nx, "nz": nz, "dz_lab": 1e-6, "dx": 1e-6, "gamma_boost": 1.0, "courant": 0.95,
+         "dt": 0.0, "solver": W.SOLVERS["yee"], "theta": 0.0, "pml_cells": 0, "order": 3, "filter_passes": 0,
+         "filter_J": 0, "filter_gather": 0, "precision": "fp64", "beam_self": 1}
+    rng = np.random.default_rng(7)
+    n = 2000
+    x = rng.normal(32e-6, 4e-6, n)
+    z = rng.normal(80e-6, 4e-6, n)
+    uz = np.full(n, np.sqrt(3.0) * 299792458.0)
+    zero = np.zeros(n)
+    wts = np.full(n, 1e-6 / (1.602176634e-19 * n))
+    o = orc.Sim(w)
+    o.set_beam(x, z, zero, zero, uz, 0.0, 1.0)
+    o.beam_weights(wts)
+    o.add_beam_self_field()
+    wg = dict(w)
+    wg["beam"] = {"x": x, "z": z, "ux": zero, "uy": zero, "uz": uz, "t_lab": 0.0, "z_plane_lab": 1.0, "self": 1,
+                  "w": wts}
+    g = Sim(wg, precision="fp64")
+    for c in (0, 2, 4):
+        g.set_field(c, o.field(c))
+    e0 = o.diag()["field_energy"]
+    g.step(100)
+    o.step(100)
+    g.sync()
+    check_fields(g, o, TOL64)
+    pg, po = g.particles(2), o.particles(2)
+    for k in ("x", "z", "ux", "uz"):
+        assert rel(pg[k], po[k]) <= TOL64, k
+    assert g.stats()["field_energy"] == pytest.approx(e0, rel=0.05)
+
+
 def test_gauss_law_on_gpu_full_size_mixed(Sim):
     """full stage size (4096 x 256 cells, 16 ppc), mixed precision, in the launch configuration the
     benchmark times: div E - F(rho)/eps0 stays at its initial value (zero) away from the boundaries"""
