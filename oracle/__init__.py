@@ -93,7 +93,7 @@ class _Config3(ctypes.Structure):
         ("filter_J", ctypes.c_int), ("filter_gather", ctypes.c_int),
         ("order", ctypes.c_int), ("particle_guard", ctypes.c_int),
         ("periodic_x", ctypes.c_int), ("periodic_y", ctypes.c_int), ("periodic_z", ctypes.c_int),
-        ("filter_strides", ctypes.c_int * 4), ("gather_nodal", ctypes.c_int),
+        ("filter_strides", ctypes.c_int * 4), ("gather_nodal", ctypes.c_int), ("beam_self", ctypes.c_int),
     ]
 
 
@@ -202,6 +202,8 @@ def lib():
             L.o3_btd_set.argtypes = [vp, ctypes.c_int, _D, _D]
             L.o3_btd_get.argtypes = [vp, _D, ctypes.POINTER(ctypes.c_int)]
             L.o3_deposit_one.argtypes = [vp] + [ctypes.c_double] * 7
+            L.o3_beam_weights.argtypes = [vp, _D]
+            L.o3_rho_one.argtypes = [vp, _D] + [ctypes.c_double] * 4
             L.o1_create.restype = vp
             L.o1_create.argtypes = [ctypes.POINTER(_Config1)]
             L.o1_destroy.argtypes = [vp]
@@ -398,13 +400,18 @@ class Sim:
         self.L.orc_beam_weights(self.h, _p(a))
 
     def beam_rho(self, shift: float = 0.0) -> np.ndarray:
-        """charge density of the frozen beam particles, their positions taken `shift` seconds from now"""
-        v = self.info()["beam_vbar"]
+        """charge density of the frozen beam particles inside the particle domain (the ones that deposit), their
+        positions taken `shift` seconds from now"""
+        info = self.info()
+        v = info["beam_vbar"]
+        xlo, xhi = info["gx_lo"] * self.dx, info["gx_hi"] * self.dx
+        zlo, zhi = info["z0"] + info["gz_lo"] * self.dz, info["z0"] + (info["gz_hi"] + 1) * self.dz
         p = self.particles(2)
         rho = np.zeros((self.nx + 1) * (self.nz + 1))
         for j in range(len(p["x"])):
-            if p["alive"][j] and not p["active"][j]:
-                self.L.orc_rho_one(self.h, _p(rho), p["x"][j], p["z"][j] + v * shift, -QE * p["w"][j])
+            x, z = p["x"][j], p["z"][j] + v * shift
+            if p["alive"][j] and not p["active"][j] and xlo <= x < xhi and zlo <= z < zhi:
+                self.L.orc_rho_one(self.h, _p(rho), x, z, -QE * p["w"][j])
         return rho.reshape(self.nx + 1, self.nz + 1)
 
     def beam_self_field(self, shift: float = 0.0) -> dict:
@@ -501,6 +508,7 @@ def _mk_config3(w: dict) -> _Config3:
     for q, v in enumerate(list(w.get("filter_strides", []))[:4]):
         c.filter_strides[q] = int(v)
     c.gather_nodal = 1 if w.get("gather", "energy") == "momentum" else 0
+    c.beam_self = int(w.get("beam_self", 0))
     return c
 
 
@@ -540,10 +548,10 @@ class Sim3:
             self.h = None
 
     def info(self) -> dict:
-        o = np.zeros(15)
+        o = np.zeros(16)
         self.L.o3_info(self.h, _p(o))
         keys = ("dx", "dy", "dz", "dt", "gamma", "beta", "step", "t", "guard",
-                "gx_lo", "gx_hi", "gy_lo", "gy_hi", "gz_lo", "gz_hi")
+                "gx_lo", "gx_hi", "gy_lo", "gy_hi", "gz_lo", "gz_hi", "beam_vbar")
         return dict(zip(keys, o.tolist()))
 
     def step(self, n: int = 1):
@@ -595,6 +603,62 @@ class Sim3:
         a = [np.ascontiguousarray(v, dtype=np.float64) for v in (x, y, z, ux, uy, uz)]
         self._beam = a
         self.L.o3_set_beam(self.h, a[0].size, *(_p(v) for v in a), float(t_lab), float(z_plane))
+
+    def beam_weights(self, w):
+        a = np.ascontiguousarray(w, dtype=np.float64)
+        self._beam_w = a
+        self.L.o3_beam_weights(self.h, _p(a))
+
+    def beam_rho(self, shift: float = 0.0) -> np.ndarray:
+        """charge density of the frozen beam particles inside the particle domain (the ones that deposit), their
+        positions taken `shift` seconds from now"""
+        info = self.info()
+        v = info["beam_vbar"]
+        d = (self.dx, self.dy, self.dz)
+        lo = [info[k] * d[a] for a, k in enumerate(("gx_lo", "gy_lo", "gz_lo"))]
+        hi = [info[k] * d[a] for a, k in enumerate(("gx_hi", "gy_hi", "gz_hi"))]
+        hi[2] += self.dz
+        p = self.particles(2)
+        rho = np.zeros(int(np.prod(self.shape)))
+        for j in range(len(p["x"])):
+            r = (p["x"][j], p["y"][j], p["z"][j] + v * shift)
+            if p["alive"][j] and not p["active"][j] and all(lo[a] <= r[a] < hi[a] for a in range(3)):
+                self.L.o3_rho_one(self.h, _p(rho), r[0], r[1], r[2], -QE * p["w"][j])
+        return rho.reshape(self.shape)
+
+    def beam_self_field(self, shift: float = 0.0) -> dict:
+        """3D self-field of the frozen beam moving rigidly at v along z (as the 2-1/2D Sim.beam_self_field):
+        d2phi/dx2 + d2phi/dy2 + d2phi/dz2 / gamma_v^2 = -rho/eps0 with phi = 0 on the PEC walls (DST-I of
+        the Yee second differences), E = -grad phi with E_z divided by gamma_v^2, B = v z x E / c^2
+        (B_x = -v E_y / c^2, B_y = v E_x / c^2) at their Yee positions."""
+        from scipy.fft import dstn, idstn
+        v = self.info()["beam_vbar"]
+        gv2 = 1.0 / (1.0 - (v / C) ** 2)
+        rho = self.beam_rho(shift)
+        nx, ny, nz = self.nx, self.ny, self.nz
+        lam = [-(2.0 - 2.0 * np.cos(np.pi * np.arange(1, n) / n)) / d ** 2
+               for n, d in ((nx, self.dx), (ny, self.dy), (nz, self.dz))]
+        den = lam[0][:, None, None] + lam[1][None, :, None] + lam[2][None, None, :] / gv2
+        ph = -dstn(rho[1:nx, 1:ny, 1:nz], type=1) / EPS0 / den
+        phi = np.zeros((nx + 1, ny + 1, nz + 1))
+        phi[1:nx, 1:ny, 1:nz] = idstn(ph, type=1)
+        ex, ey, ez = (np.zeros_like(phi) for _ in range(3))
+        bx, by = np.zeros_like(phi), np.zeros_like(phi)
+        ex[:nx] = -(phi[1:] - phi[:-1]) / self.dx                               # (i + 1/2, j, k)
+        ey[:, :ny] = -(phi[:, 1:] - phi[:, :-1]) / self.dy                      # (i, j + 1/2, k)
+        ez[:, :, :nz] = -(phi[:, :, 1:] - phi[:, :, :-1]) / self.dz / gv2       # (i, j, k + 1/2)
+        bx[:, :ny, :nz] = -v / C ** 2 * 0.5 * (ey[:, :ny, :nz] + ey[:, :ny, 1:])   # (i, j + 1/2, k + 1/2)
+        by[:nx, :, :nz] = v / C ** 2 * 0.5 * (ex[:nx, :, :nz] + ex[:nx, :, 1:])    # (i + 1/2, j, k + 1/2)
+        return {"Ex": ex, "Ey": ey, "Ez": ez, "Bx": bx, "By": by, "vbar": v}
+
+    def add_beam_self_field(self):
+        """add the frozen beam's self-field: E now, B half a step earlier (B^{n-1/2})"""
+        fe = self.beam_self_field(0.0)
+        fb = self.beam_self_field(-0.5 * self.dt)
+        for c, k in ((EX, "Ex"), (EY, "Ey"), (EZ, "Ez")):
+            self.set_field(c, self.field(c) + fe[k])
+        for c, k in ((BX, "Bx"), (BY, "By")):
+            self.set_field(c, self.field(c) + fb[k])
 
     def diag(self) -> dict:
         o = np.zeros(5)

@@ -59,6 +59,7 @@ typedef struct {
   int periodic_x, periodic_y, periodic_z;   /* fields only (test option) */
   int filter_strides[4];      /* > 0: product over these strides of (n passes + compensation), Sec. 4.1 */
   int gather_nodal;           /* 1: 'momentum conserving' gather from node-interpolated fields (Sec. 5) */
+  int beam_self;              /* 1: the test beam's frozen and active particles deposit their current (Sec. 3.1.1) */
 } o3_config;
 
 typedef struct {
@@ -388,6 +389,14 @@ static void esirkepov3(o3_sim* s, const double* p0, const double* p1, double qw)
   }
 }
 
+/* weights of the test beam (macro-particle counts), in the order it was given */
+void o3_beam_weights(o3_sim* s, const double* w) {
+  o3_species* b = &s->sp[2];
+  for (long j = 0; j < b->n; j++) b->w[j] = w[j];
+}
+
+void o3_rho_one(const o3_sim* s, double* rho, double x, double y, double z, double qw);
+
 void o3_deposit_one(o3_sim* s, double x0, double y0, double z0, double x1, double y1, double z1, double qw) {
   double p0[3] = { x0, y0, z0 }, p1[3] = { x1, y1, z1 };
   esirkepov3(s, p0, p1, qw);
@@ -405,6 +414,8 @@ static void deposit_rho(const o3_sim* s, double* rho, double x, double y, double
           rho[I3(s, i, j, k)] += qw * w / (s->dx * s->dy * s->dz);
       }
 }
+
+void o3_rho_one(const o3_sim* s, double* rho, double x, double y, double z, double qw) { deposit_rho(s, rho, x, y, z, qw); }
 
 /* ------------------------------------------------------------------ */
 static void sp_reserve(o3_species* p, long n) {
@@ -519,6 +530,7 @@ void o3_info(const o3_sim* s, double* out) {
   out[0] = s->dx; out[1] = s->dy; out[2] = s->dz; out[3] = s->dt; out[4] = s->gamma; out[5] = s->beta;
   out[6] = (double)s->step; out[7] = time_of(s, s->step); out[8] = s->c.particle_guard;
   for (int a = 0; a < 3; a++) { out[9 + 2 * a] = s->glo[a]; out[10 + 2 * a] = s->ghi[a]; }
+  out[15] = s->beam_vbar;
 }
 
 /* ------------------------------------------------------------------ */
@@ -767,7 +779,14 @@ static void one_step(o3_sim* s) {
           if (p->x[q] < lo[0] || p->x[q] >= hi[0] || p->y[q] < lo[1] || p->y[q] >= hi[1] ||
               p->z[q] < lo[2] || p->z[q] >= hi[2]) { p->alive[q] = 0; continue; }
         } else {
-          p->z[q] = p->zf0[q] + s->beam_vbar * tn1;
+          const double zn = p->zf0[q] + s->beam_vbar * tn1;
+          /* a frozen particle inside the particle domain carries its charge along z at the mean velocity */
+          if (s->c.beam_self && p->x[q] >= lo[0] && p->x[q] < hi[0] && p->y[q] >= lo[1] && p->y[q] < hi[1] &&
+              p->z[q] >= lo[2] && p->z[q] < hi[2] && zn >= lo[2] && zn < hi[2]) {
+            double p0[3] = { p->x[q], p->y[q], p->z[q] }, p1[3] = { p->x[q], p->y[q], zn };
+            esirkepov3(s, p0, p1, p->q * p->w[q]);
+          }
+          p->z[q] = zn;
           continue;
         }
       }
@@ -784,7 +803,7 @@ static void one_step(o3_sim* s) {
         p->z[q] = p->zl[q] - s->beta * O_C * tn;
         pn[2] = p->zl[q] - s->beta * O_C * tn1;
       }
-      if (sp != 2) {
+      if (sp != 2 || s->c.beam_self) {
         double p0[3] = { p->x[q], p->y[q], p->z[q] };
         esirkepov3(s, p0, pn, p->q * p->w[q]);
       }
