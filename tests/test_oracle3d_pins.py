@@ -276,3 +276,95 @@ def test_3d_gather_schemes_on_quadratic_field(orc, scheme, extra):
     qe, me = 1.602176634e-19, 9.1093837015e-31
     ex = p["ux"] / (-qe / me * s.dt)
     assert np.abs(ex - (X ** 2 + 1.0 / 3.0 + extra)).max() < 1e-9 * np.abs(X ** 2).max()
+
+
+# ---------------------------------------------------------------------------
+# App. II in 3D: the split-field PML. The 2-1/2D PML is pinned by its reflection of a Harris pulse;
+# with y periodic (no layer along y) and fields independent of y, the 3D layers on the x and z faces
+# must advance exactly like the 2D ones.
+def _interior_noise(rng, shape, lo, scale):
+    f = np.zeros(shape)
+    sl = tuple(slice(lo, n - lo) for n in shape)
+    f[sl] = rng.standard_normal(tuple(n - 2 * lo for n in shape)) * scale
+    return f
+
+
+def test_3d_pml_reduces_to_2d_when_y_is_periodic(orc):
+    rng = np.random.default_rng(17)
+    nx, nz, pml = 26, 30, 6
+    w2 = {"nx": nx, "nz": nz, "dz_lab": 0.8e-6, "dx": 1.1e-6, "gamma_boost": 1.0, "courant": 0.9,
+          "solver": W.SOLVERS["ck"], "theta": 0.2, "pml_cells": pml, "order": 3,
+          "periodic_x": 0, "periodic_z": 0}
+    s2 = orc.Sim(w2)
+    w3 = vacuum3(nx, 4, nz, "ck", dx=1.1e-6, dy=1.7e-6, dz=0.8e-6, courant=0.9, theta=0.2,
+                 periodic=False, pml_cells=pml, periodic_y=1)
+    w3["dt"] = s2.dt
+    s3 = orc.Sim3(w3)
+    for comp in range(6):
+        f = _interior_noise(rng, (nx + 1, nz + 1), pml + 2, 1.0 if comp < 3 else 1.0 / C)
+        s2.set_field(comp, f)
+        s3.set_field(comp, np.repeat(f[:, None, :], 5, axis=1))
+    # long enough for the noise to cross the layers several times
+    s2.step(60)
+    s3.step(60)
+    inside = 0.0
+    for comp in range(6):
+        a2 = s2.field(comp)
+        a3 = s3.field(comp)[:, :4, :]
+        assert np.abs(a3 - a2[:, None, :]).max() <= 1e-12 * np.abs(a2).max(), comp
+        inside += float(np.sum(a2[:pml, :] ** 2) + np.sum(a2[:, :pml] ** 2)) * (1.0 if comp < 3 else C * C)
+    assert inside > 0.0            # the layers took part
+
+
+# x <-> y mirror symmetry with dx = dy and nx = ny: E is a polar vector, B an axial one, so the
+# mirrored state (E'_x, E'_y, E'_z)(i, j) = (E_y, E_x, E_z)(j, i), B' = -(B_y, B_x, B_z)(j, i), with
+# particles at (y, x, z) and momenta (u_y, u_x, u_z), must stay the mirror of the original under the
+# CK solver, the PML on all six faces, Friedman damping, the filter, the cubic gather, the Boris push and
+# the Esirkepov deposit. Every y-term of the 3D oracle is thereby tied to its x-term.
+def _mirror(comp, a):
+    src = {0: 1, 1: 0, 2: 2, 3: 4, 4: 3, 5: 5}[comp]
+    sign = 1.0 if comp < 3 else -1.0
+    return src, sign
+
+
+def test_3d_mirror_x_y_with_pml_particles_and_filter(orc):
+    rng = np.random.default_rng(23)
+    n, nz, pml = 28, 26, 4
+    w = vacuum3(n, n, nz, "ck", dx=0.9e-6, dy=0.9e-6, dz=0.7e-6, courant=0.9, theta=0.2, periodic=False,
+                pml_cells=pml, filter_passes=2, filter_compensate=1, particle_guard=5)
+    s1, s2 = orc.Sim3(w), orc.Sim3(w)
+    F = [_interior_noise(rng, (n + 1, n + 1, nz + 1), pml + 2, 3e9 if c < 3 else 3e9 / C) for c in range(6)]
+    for comp in range(6):
+        src, sign = _mirror(comp, None)
+        s1.set_field(comp, F[comp])
+        s2.set_field(comp, sign * np.transpose(F[src], (1, 0, 2)))
+    info = s1.info()
+    npart = 40
+    lo, hi = info["gx_lo"] + 1.5, info["gx_hi"] - 1.5
+    x = rng.uniform(lo, hi, npart) * s1.dx
+    y = rng.uniform(lo, hi, npart) * s1.dy
+    z = rng.uniform(info["gz_lo"] + 1.5, info["gz_hi"] - 1.5, npart) * s1.dz
+    u = rng.standard_normal((3, npart)) * 0.3 * C
+    # weights of 1e8 make the deposit's field ~100x the initial noise, and the noise changes the momenta by
+    # about 1% a step; at 1e9 the orbits grow chaotic and round-off differences grow past 1e-12
+    wt = np.full(npart, 1e8)
+    s1.set_particles(0, x, y, z, u[0], u[1], u[2], wt)
+    s2.set_particles(0, y, x, z, u[1], u[0], u[2], wt)
+    s1.step(30)
+    s2.step(30)
+    for comp in range(6):
+        src, sign = _mirror(comp, None)
+        a = s2.field(comp)
+        b = sign * np.transpose(s1.field(src), (1, 0, 2))
+        assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max(), comp
+    assert np.abs(s1.field(1)).max() > 10 * np.abs(F[1]).max()       # the deposit shaped the fields
+    p1, p2 = s1.particles(0), s2.particles(0)
+    assert p1["alive"].sum() > npart // 2
+    o1, o2 = np.argsort(p1["id"]), np.argsort(p2["id"])
+    assert np.array_equal(p1["alive"][o1], p2["alive"][o2])
+    live = p1["alive"][o1]
+    for k1, k2, scale in (("x", "y", s1.dx), ("y", "x", s1.dy), ("z", "z", s1.dz),
+                          ("ux", "uy", C), ("uy", "ux", C), ("uz", "uz", C)):
+        assert np.abs(p2[k1][o2][live] - p1[k2][o1][live]).max() <= 1e-12 * scale, k1
+    du = np.abs(p1["ux"][o1][live] - u[0][np.sort(p1["id"])][live])
+    assert du.max() > 1e-3 * C                                       # the gather and push acted
