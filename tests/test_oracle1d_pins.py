@@ -215,3 +215,38 @@ def test_1d_gather_schemes_on_quadratic_field(orc, scheme, extra):
     Z = (p["z"] - s.dt * p["uz"] / g) / s.dz
     ez = p["uz"] / (-QE / ME * s.dt)
     assert np.abs(ez - (Z ** 2 + 1.0 / 3.0 + extra)).max() < 1e-9 * np.abs(Z ** 2).max()
+
+
+# ---------------------------------------------------------------------------
+# PR-26: the 1D step is the 2-1/2D step with d/dx = 0. With x periodic (no layer along x) and fields
+# independent of x, the 2D CK operator reduces to Yee's (alpha_2 + 2 beta_2 = 1, PR-3) and the split
+# PML's x parts stay zero, so interior noise advanced through Friedman damping and the PML at both ends
+# of z must equal the separately pinned 2D oracle, component by component.
+def test_1d_matches_2d_with_x_independent_fields(orc):
+    from paper_1009_2727_gb300 import workloads as W
+    rng = np.random.default_rng(31)
+    nz, nx, pml = 72, 4, 10
+    w2 = {"nx": nx, "nz": nz, "dz_lab": 0.7e-6, "dx": 1.3e-6, "gamma_boost": 1.0, "courant": 0.9,
+          "solver": W.SOLVERS["ck"], "theta": 0.25, "pml_cells": pml, "order": 3,
+          "periodic_x": 1, "periodic_z": 0}
+    s2 = orc.Sim(w2)
+    s1 = orc.Sim1(vac1(nz, dz_lab=0.7e-6, theta=0.25, pml_cells=pml, dt=s2.dt))
+    assert s1.dt == s2.dt and s1.dz == s2.dz
+    f0 = {}
+    for comp in range(6):
+        f = np.zeros(nz + 1)
+        f[pml + 2:nz - pml - 2] = rng.standard_normal(nz - 2 * pml - 4) * (1.0 if comp < 3 else 1.0 / C)
+        f0[comp] = f
+        s1.set_field(comp, f)
+        s2.set_field(comp, np.repeat(f[None, :], nx + 1, axis=0))
+    s1.step(90)
+    s2.step(90)
+    for comp in range(6):
+        a1 = s1.field(comp)
+        a2 = s2.field(comp)[:nx]
+        assert np.abs(a2 - a1[None, :]).max() <= 1e-12 * max(np.abs(a1).max(), np.abs(f0[comp]).max()), comp
+    # the transverse pairs reached the layers and lost energy there; E_z and B_z do not propagate in 1D
+    for comp in (0, 1, 3, 4):
+        assert np.sum(s1.field(comp) ** 2) < 0.5 * np.sum(f0[comp] ** 2), comp
+    for comp in (2, 5):
+        assert np.array_equal(s1.field(comp), f0[comp]), comp
