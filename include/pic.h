@@ -138,7 +138,8 @@ typedef struct {
   int32_t beam_self;      /* 2D: 1 = self-consistent beam (Sec. 3.1.1): its frozen particles inside the
                              particle domain deposit the current of their move at the mean velocity and
                              its active particles deposit like the plasma; needs beam_w. The caller sets
-                             the beam's initial self-field (pic_set_field). 0 = test particles */
+                             the beam's initial self-field (pic_set_field). 0 = test particles.
+                             PIC_EINVAL when beam_w is NULL, and in 3D (1D takes no test beam at all) */
   const double* beam_w;   /* beam weights: macro-particle counts per unit length along y (host, beam_n
                              values; read only with beam_self) */
   int32_t reserved[2];
