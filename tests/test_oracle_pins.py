@@ -765,3 +765,55 @@ def test_gather_schemes_on_quadratic_field(orc, order):
         qe, me = 1.602176634e-19, 9.1093837015e-31
         ex = p["ux"] / (-qe / me * s.dt)
         assert np.abs(ex - (X ** 2 + var + extra)).max() < 1e-9 * np.abs(X ** 2).max(), scheme
+
+
+# ---------------------------------------------------------------------------
+# x <-> z mirror symmetry of the 2-1/2D step (dx = dz, nx = nz, gamma = 1): E polar, B axial, so the
+# mirrored state (E'_x, E'_y, E'_z)(i, k) = (E_z, E_y, E_x)(k, i), B' = -(B_z, B_y, B_x)(k, i), with
+# particles at (z, x) and momenta (u_z, u_y, u_x), must stay the mirror of the original under CK, the PML
+# on all four sides, Friedman damping, the filter on J and on the gathered fields, the cubic gather,
+# Boris and Esirkepov. Every z-term of the oracle is thereby tied to its x-term. (Only the removal edge
+# differs between the axes: along z at z_hi + dz, one cell above the inflow plane, so the particles stay
+# in the middle of the box here.)
+_MIRROR_XZ = {0: (2, 1.0), 1: (1, 1.0), 2: (0, 1.0), 3: (5, -1.0), 4: (4, -1.0), 5: (3, -1.0)}
+
+
+def test_mirror_x_z_with_pml_particles_and_filter(orc):
+    rng = np.random.default_rng(41)
+    n, pml = 60, 6
+    w = vacuum(n, n, "ck", dx=0.8e-6, dz=0.8e-6, courant=0.9, theta=0.2, periodic=False, pml_cells=pml,
+               filter_passes=2, filter_compensate=1, filter_J=1, filter_gather=1, particle_guard=5)
+    s1, s2, s0 = orc.Sim(w), orc.Sim(w), orc.Sim(w)
+    F = []
+    for c in range(6):
+        f = np.zeros((n + 1, n + 1))
+        f[pml + 2:n - pml - 2, pml + 2:n - pml - 2] = (rng.standard_normal((n - 2 * pml - 4,) * 2)
+                                                       * (3e9 if c < 3 else 3e9 / C))
+        F.append(f)
+    for c in range(6):
+        src, sign = _MIRROR_XZ[c]
+        s1.set_field(c, F[c])
+        s0.set_field(c, F[c])
+        s2.set_field(c, sign * F[src].T)
+    npart = 40
+    x = rng.uniform(25, 35, npart) * s1.dx
+    z = rng.uniform(25, 35, npart) * s1.dz
+    u = rng.standard_normal((3, npart)) * 0.1 * C
+    wt = np.full(npart, 1e12)
+    s1.set_particles(0, x, z, u[0], u[1], u[2], wt)
+    s2.set_particles(0, z, x, u[2], u[1], u[0], wt)
+    for s in (s0, s1, s2):
+        s.step(30)
+    for c in range(6):
+        src, sign = _MIRROR_XZ[c]
+        a = s2.field(c)
+        b = sign * s1.field(src).T
+        assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max(), c
+    # the deposit moved the fields by >10% of their size and the fields moved the momenta by >10% of c
+    assert np.abs(s1.field(1) - s0.field(1)).max() > 0.1 * np.abs(s0.field(1)).max()
+    p1, p2 = s1.particles(0), s2.particles(0)
+    assert p1["alive"].all() and p2["alive"].all()
+    o1, o2 = np.argsort(p1["id"]), np.argsort(p2["id"])
+    assert np.abs(p1["ux"][o1] - u[0]).max() > 0.1 * C
+    for k1, k2, scale in (("x", "z", s1.dx), ("z", "x", s1.dz), ("ux", "uz", C), ("uy", "uy", C), ("uz", "ux", C)):
+        assert np.abs(p2[k1][o2] - p1[k2][o1]).max() <= 1e-12 * scale, k1
