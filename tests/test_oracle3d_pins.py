@@ -368,3 +368,46 @@ def test_3d_mirror_x_y_with_pml_particles_and_filter(orc):
         assert np.abs(p2[k1][o2][live] - p1[k2][o1][live]).max() <= 1e-12 * scale, k1
     du = np.abs(p1["ux"][o1][live] - u[0][np.sort(p1["id"])][live])
     assert du.max() > 1e-3 * C                                       # the gather and push acted
+
+
+# ---------------------------------------------------------------------------
+# Sec. 3.2 in 3D: the lab stations. The 2-1/2D stations are pinned by the lab-frame identity and by a
+# boosted laser seen in the lab with its lab amplitude and period; with fields independent of y the 3D
+# rows (interpolation in z' and t', the transform of E_perp and B_perp to the lab) must equal them at every y.
+def test_3d_lab_stations_reduce_to_2d(orc):
+    rng = np.random.default_rng(29)
+    nx, nz, g = 10, 40, 3.0
+    beta = math.sqrt(1 - 1 / g ** 2)
+    w2 = {"nx": nx, "nz": nz, "dz_lab": 0.3e-6, "dx": 1.2e-6, "gamma_boost": g, "courant": 0.9,
+          "solver": W.SOLVERS["ck"], "theta": 0.1, "pml_cells": 0, "order": 3,
+          "periodic_x": 1, "periodic_z": 1}
+    s2 = orc.Sim(w2)
+    w3 = vacuum3(nx, 4, nz, "ck", dx=1.2e-6, dy=2.0e-6, dz=0.3e-6, courant=0.9, theta=0.1, gamma_boost=g)
+    w3["dz_lab"] = 0.3e-6
+    w3["dt"] = s2.dt
+    s3 = orc.Sim3(w3)
+    assert s3.dz == s2.dz and s3.dt == s2.dt
+    for comp in range(6):
+        f = np.zeros((nx + 1, nz + 1))
+        f[:nx, :nz] = rng.standard_normal((nx, nz)) * (1.0 if comp < 3 else 1.0 / C)
+        s2.set_field(comp, f)
+        s3.set_field(comp, np.repeat(f[:, None, :], 5, axis=1))
+    # rows at boosted (z', t') inside the run, given as lab (z_L, t_L)
+    nst = 12
+    zp = rng.uniform(5, nz - 5, nst) * s2.dz
+    tp = rng.uniform(3, 20, nst) * s2.dt
+    zL = g * (zp + beta * C * tp)
+    tL = g * (tp + beta * zp / C)
+    s2.btd_set(zL, tL)
+    s3.btd_set(zL, tL)
+    s2.step(24)
+    s3.step(24)
+    o2, d2 = s2.btd_get()
+    o3, d3 = s3.btd_get()
+    assert d2.all() and np.array_equal(d2, d3)
+    scale = np.abs(o2[:, :3]).max()
+    for j in range(4):
+        for comp in range(6):
+            sc = scale if comp < 3 else scale / C
+            assert np.abs(o3[:, comp, :nx, j] - o2[:, comp, :nx]).max() <= 1e-12 * sc, (j, comp)
+    assert scale > 0.5                     # rows of the unit-variance noise, not empty rows
