@@ -34,7 +34,7 @@ def vacuum3(nx, ny, nz, solver="yee", dx=1e-6, dy=1e-6, dz=1e-6, courant=0.95, t
 ST = {0: (0.5, 0, 0), 1: (0, 0.5, 0), 2: (0, 0, 0.5), 3: (0, 0.5, 0.5), 4: (0.5, 0, 0.5), 5: (0.5, 0.5, 0)}
 
 
-def _mode3(w, s, m, n, e_dir):
+def _mode3(w, s, m, n, e_dir, om=None):
     a, b, g = w["solver"]
     nn = (w["nx"], w["ny"], w["nz"])
     d = (s.dx, s.dy, s.dz)
@@ -45,7 +45,8 @@ def _mode3(w, s, m, n, e_dir):
           for q in range(3)]
     Ks = np.array([Cq[q] * K[q] for q in range(3)])
     Om = C * math.sqrt(float(np.sum(np.array(Cq) * K * K)))
-    om = 2 * math.asin(Om * s.dt / 2) / s.dt
+    if om is None:
+        om = 2 * math.asin(Om * s.dt / 2) / s.dt
     E = np.array(e_dir, dtype=float)
     E = E - K * (E @ K) / (K @ K)              # discrete transversality E.K = 0
     E /= np.abs(E).max()
@@ -411,3 +412,32 @@ def test_3d_lab_stations_reduce_to_2d(orc):
             sc = scale if comp < 3 else scale / C
             assert np.abs(o3[:, comp, :nx, j] - o2[:, comp, :nx]).max() <= 1e-12 * sc, (j, comp)
     assert scale > 0.5                     # rows of the unit-variance noise, not empty rows
+
+
+# ---------------------------------------------------------------------------
+# Sec. 4.2.1 on cubic cells at each solver's Courant limit: Yee has no numerical dispersion along the
+# 3D diagonal, CK none along the principal axes, CK3 none along the 2D diagonals. There the oracle's
+# vacuum mode must travel at exactly c (omega = c|k|), while Yee along an axis lags.
+@pytest.mark.parametrize("name,m,exact", [("ck", (3, 0, 0), True), ("ck", (0, 0, 4), True),
+                                          ("yee", (3, 3, 3), True), ("ck3", (3, 3, 0), True),
+                                          ("ck3", (0, 2, 2), True), ("yee", (3, 0, 0), False)])
+def test_3d_dispersion_free_directions_at_the_courant_limit(orc, name, m, exact):
+    n = 12
+    w = vacuum3(n, n, n, name, courant=1.0)
+    s = orc.Sim3(w)
+    d = s.dx
+    k = np.array([2 * np.pi * m[q] / (n * d) for q in range(3)])
+    om_c = C * float(np.linalg.norm(k))
+    e_dir = (0.0, 0.0, 1.0) if m[2] == 0 else (1.0, 0.0, 0.0)
+    f0 = _mode3(w, s, m, 0, e_dir)
+    for comp in range(6):
+        s.set_field(comp, f0[comp])
+    N = 40
+    s.step(N)
+    ref = _mode3(w, s, m, N, e_dir, om=om_c)
+    scale = max(np.abs(ref[c]).max() for c in range(3))
+    err = max(np.abs(s.field(c)[:n, :n, :n] - ref[c][:n, :n, :n]).max() for c in range(3)) / scale
+    if exact:
+        assert err < 1e-9
+    else:
+        assert err > 1e-2

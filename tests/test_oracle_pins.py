@@ -112,7 +112,7 @@ def test_stability_boundary(orc, name):
 
 # ---------------------------------------------------------------------------
 # Eq. num_disp: a vacuum Fourier mode advances by exactly the root of the dispersion relation
-def _mode_fields(w, s, mx, mz, n, pol):
+def _mode_fields(w, s, mx, mz, n, pol, om=None):
     a, b, g = w["solver"]
     nx, nz, dx, dz, dt = w["nx"], w["nz"], s.dx, s.dz, s.dt
     kx, kz = 2 * np.pi * mx / (nx * dx), 2 * np.pi * mz / (nz * dz)
@@ -121,7 +121,8 @@ def _mode_fields(w, s, mx, mz, n, pol):
     Cx = a + 2 * b * (1 + cz) + 4 * g * cz       # c_y = 1 (d/dy = 0)
     Cz = a + 2 * b * (cx + 1) + 4 * g * cx
     St = C * dt * math.sqrt(Cx * sx ** 2 / dx ** 2 + Cz * sz ** 2 / dz ** 2)
-    om = 2 * math.asin(St) / dt
+    if om is None:
+        om = 2 * math.asin(St) / dt
     i = np.arange(nx + 1)[:, None]
     k = np.arange(nz + 1)[None, :]
 
@@ -155,6 +156,34 @@ def test_vacuum_mode_follows_dispersion(orc, name, pol, dx, dz):
             got = s.field(comp)[:24, :20]
             scale = np.abs(ref).max()
             assert np.abs(got - ref[:24, :20]).max() <= 1e-10 * scale, (name, pol, mx, mz, comp)
+
+
+# Sec. 4.2.1 in 2D on square cells at the Courant limit: CK (whose limit c dt = dx does not depend on the
+# dimension) has no numerical dispersion along the axes, Yee none along the diagonal; there the oracle's
+# mode travels at exactly c. Yee along an axis lags.
+@pytest.mark.parametrize("name,mx,mz,exact", [("ck", 3, 0, True), ("ck", 0, 4, True), ("yee", 3, 3, True),
+                                              ("yee", 3, 0, False)])
+@pytest.mark.parametrize("pol", ["TE", "TM"])
+def test_dispersion_free_directions_at_the_courant_limit(orc, name, mx, mz, exact, pol):
+    n = 16
+    w = vacuum(n, n, name, courant=1.0)
+    s = orc.Sim(w)
+    if name == "ck":
+        assert s.dt == pytest.approx(s.dx / C, rel=1e-14)
+    kx, kz = 2 * np.pi * mx / (n * s.dx), 2 * np.pi * mz / (n * s.dz)
+    f0 = _mode_fields(w, s, mx, mz, 0, pol)
+    for comp in range(6):
+        s.set_field(comp, f0.get(comp, np.zeros((n + 1, n + 1))))
+    N = 40
+    s.step(N)
+    ref = _mode_fields(w, s, mx, mz, N, pol, om=C * math.hypot(kx, kz))
+    comp = 1 if pol == "TE" else 4
+    scale = np.abs(ref[comp]).max()
+    err = np.abs(s.field(comp)[:n, :n] - ref[comp][:n, :n]).max() / scale
+    if exact:
+        assert err < 1e-9
+    else:
+        assert err > 1e-2
 
 
 # ---------------------------------------------------------------------------
