@@ -192,17 +192,33 @@ def cpu_oracle_sample3(w: dict, seconds: float = 15.0, max_steps: int = 40) -> d
                       f"{dt:.1f} s (setup {setup:.1f} s), single thread"}
 
 
+REF_BUDGET_S = 150.0      # wall-clock bound of the reference arm's steps
+
+
 def run_reference(args, w):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
     import oracle
     from paper_1009_2727_gb300 import workloads as W
-    wsmp = W.shrink(w, w["nx"], 256)
+    # the sample: a 256-cell slice of the box, shortened when one step projects the whole
+    # --steps/--warmup run past REF_BUDGET_S (the oracle's throughput per particle does not depend on it)
+    rows = 256
+    wsmp = W.shrink(w, w["nx"], rows)
     wsmp["precision"] = "fp64"
     s = oracle.Sim(wsmp)
+    t1 = time.perf_counter()
+    s.step(1)
+    t1 = time.perf_counter() - t1
+    projected = t1 * (args.steps + args.warmup)
+    if projected > REF_BUDGET_S:
+        rows = max(32, int(rows * REF_BUDGET_S / projected) // 16 * 16)
+        wsmp = W.shrink(w, w["nx"], rows)
+        wsmp["precision"] = "fp64"
+        s = oracle.Sim(wsmp)
+        s.step(1)
     n = len(s.particles(0)["x"])
-    for _ in range(args.warmup):
+    for _ in range(args.warmup - 1):
         s.step(1)
     t0 = time.perf_counter()
     s.step(args.steps)
@@ -212,7 +228,7 @@ def run_reference(args, w):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": w["name"] + " (bounded sample: 256 x 256 cells)", "grid": [w["nz"], w["nx"]],
+            "config": {"workload": w["name"] + f" (bounded sample: {rows} x {w['nx']} cells)", "grid": [w["nz"], w["nx"]],
                        "ppc": 16, "precision": "fp64 oracle"},
             "cpu_baseline": {"kind": "oracle", "cores": 1, "value": v, "unit": "particle-steps/s",
                              "sample": f"{wsmp['name']}: {n} electrons, {args.steps} steps, {dt:.1f} s"},
