@@ -216,6 +216,7 @@ def lib():
             L.o1_num_particles.restype = ctypes.c_long
             L.o1_num_particles.argtypes = [vp, ctypes.c_int]
             L.o1_get_particles.argtypes = [vp, ctypes.c_int] + [_D] * 5 + [ctypes.POINTER(ctypes.c_uint32)]
+            L.o1_set_particles.argtypes = [vp, ctypes.c_int, ctypes.c_long] + [_D] * 5
             L.o1_rho.argtypes = [vp, _D]
             L.o1_diag.argtypes = [vp, _D]
             L.o1_deposit_one.argtypes = [vp] + [ctypes.c_double] * 5
@@ -785,6 +786,10 @@ class Sim1:
                                 ids.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)))
         arrs["id"] = ids
         return arrs
+
+    def set_particles(self, species: int, z, ux, uy, uz, w):
+        a = [np.ascontiguousarray(v, dtype=np.float64) for v in (z, ux, uy, uz, w)]
+        self.L.o1_set_particles(self.h, species, a[0].size, *(_p(v) for v in a))
 
     def diag(self) -> dict:
         o = np.zeros(2)

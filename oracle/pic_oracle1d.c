@@ -495,6 +495,14 @@ void o1_get_gather_field(const o1_sim* s, int comp, double* out) {
   memcpy(out, comp < 3 ? s->fE[comp] : s->fB[comp - 3], sizeof(double) * s->n1);
 }
 long o1_num_particles(const o1_sim* s, int species) { return s->sp[species].n; }
+
+/* replaces the particles of a species (test input; ids 0..n-1; an ion keeps z as its lab row) */
+void o1_set_particles(o1_sim* s, int species, long n, const double* z, const double* ux, const double* uy,
+                      const double* uz, const double* w) {
+  o1_species* p = &s->sp[species];
+  p->n = 0;
+  for (long j = 0; j < n; j++) sp_push(p, z[j], ux[j], uy[j], uz[j], w[j], (uint32_t)j, z[j]);
+}
 void o1_get_particles(const o1_sim* s, int species, double* z, double* ux, double* uy, double* uz, double* w,
                       uint32_t* id) {
   const o1_species* p = &s->sp[species];

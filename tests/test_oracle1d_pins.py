@@ -250,3 +250,40 @@ def test_1d_matches_2d_with_x_independent_fields(orc):
         assert np.sum(s1.field(comp) ** 2) < 0.5 * np.sum(f0[comp] ** 2), comp
     for comp in (2, 5):
         assert np.array_equal(s1.field(comp), f0[comp]), comp
+
+
+# ---------------------------------------------------------------------------
+# The 1D push through whole steps, in uniform fields far from the walls (weightless particles, so the
+# fields stay uniform where the particle is): the E x B drift state of the relativistic Boris push moves
+# at exactly v_d = E_x/B_y along z, and in a uniform B_z the momentum turns by 2 atan(q B dt/(2 gamma m))
+# per step (an electron turns counter-clockwise about +z) with |u| and z unchanged.
+def test_1d_push_through_full_steps_drift_and_gyration(orc):
+    nz = 400
+    s = orc.Sim1(vac1(nz, courant=0.95))
+    Ex, By = 3e8, 2.0
+    vd = Ex / By
+    gd = 1 / math.sqrt(1 - (vd / C) ** 2)
+    s.set_field(0, np.full(nz + 1, Ex))
+    s.set_field(4, np.full(nz + 1, By))
+    z0 = 200 * s.dz
+    s.set_particles(0, [z0], [0.0], [0.0], [gd * vd], [0.0])
+    N = 60                          # the walls' disturbance travels < 60 cells; the particle stays > 140 away
+    s.step(N)
+    p = s.particles(0)
+    assert p["z"][0] == pytest.approx(z0 + vd * N * s.dt, abs=1e-9 * s.dz)
+    assert abs(p["ux"][0]) < 1e-6 * gd * vd and p["uz"][0] == pytest.approx(gd * vd, rel=1e-9)
+
+    s = orc.Sim1(vac1(nz, courant=0.95))
+    B = 2.0
+    s.set_field(5, np.full(nz + 1, B))
+    u = np.array([0.6 * C, 0.3 * C, 0.0])
+    g = math.sqrt(1 + (u @ u) / C ** 2)
+    s.set_particles(0, [z0], [u[0]], [u[1]], [u[2]], [0.0])
+    N = 300
+    s.step(N)
+    p = s.particles(0)
+    assert p["z"][0] == z0
+    assert math.hypot(p["ux"][0], p["uy"][0]) == pytest.approx(math.hypot(u[0], u[1]), rel=1e-13)
+    turned = math.atan2(p["uy"][0], p["ux"][0]) - math.atan2(u[1], u[0])
+    expect = N * 2 * math.atan(QE * B * s.dt / (2 * g * ME))
+    assert abs((turned - expect + math.pi) % (2 * math.pi) - math.pi) < 1e-9

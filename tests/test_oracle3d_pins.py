@@ -472,3 +472,45 @@ def test_3d_friedman_damping_directions(orc):
     ckf = {m: _mode_energy_after(orc, "ck", m, 0.5) for m in (axis, diag)}
     assert yf[diag] < 0.1 * yf[axis]          # YF: strongest along the 3D diagonal
     assert ckf[axis] < 0.1 * ckf[diag]        # CKF: strongest along the axes
+
+
+# ---------------------------------------------------------------------------
+# The 3D push through whole steps in uniform periodic fields (weightless particles): the E x B drift
+# state moves at exactly v_d = E_x/B_y along z; in a uniform B_y the momentum turns in the (z, x) plane by
+# 2 atan(q B dt/(2 gamma m)) per step, with |u| and y unchanged.
+def test_3d_push_through_full_steps_drift_and_gyration(orc):
+    QEl, MEl = 1.602176634e-19, 9.1093837015e-31
+    n, nz = 16, 40
+    shape = (n + 1, n + 1, nz + 1)
+    w = vacuum3(n, n, nz, "ck", courant=0.95)
+    s = orc.Sim3(w)
+    Ex, By = 6e7, 1.0
+    vd = Ex / By                                   # 0.2 c
+    gd = 1 / math.sqrt(1 - (vd / C) ** 2)
+    s.set_field(0, np.full(shape, Ex))
+    s.set_field(4, np.full(shape, By))
+    x0, y0, z0 = 8.3 * s.dx, 7.6 * s.dy, 12.2 * s.dz
+    s.set_particles(0, [x0], [y0], [z0], [0.0], [0.0], [gd * vd], [0.0])
+    N = 60
+    s.step(N)
+    p = s.particles(0)
+    assert p["alive"][0]
+    assert p["z"][0] == pytest.approx(z0 + vd * N * s.dt, abs=1e-9 * s.dz)
+    assert p["x"][0] == pytest.approx(x0, abs=1e-9 * s.dx) and p["y"][0] == y0
+    assert p["uz"][0] == pytest.approx(gd * vd, rel=1e-9)
+
+    s = orc.Sim3(w)
+    B = 10.0                                       # gyration radius about one cell
+    s.set_field(4, np.full(shape, B))
+    u = np.array([0.005 * C, 0.0, 0.004 * C])
+    g = math.sqrt(1 + (u @ u) / C ** 2)
+    s.set_particles(0, [x0], [y0], [20.0 * s.dz], [u[0]], [u[1]], [u[2]], [0.0])
+    N = 200
+    s.step(N)
+    p = s.particles(0)
+    assert p["alive"][0] and p["y"][0] == y0
+    assert math.hypot(p["ux"][0], p["uz"][0]) == pytest.approx(math.hypot(u[0], u[2]), rel=1e-13)
+    # about +y the positive sense runs from z to x; an electron turns that way
+    turned = math.atan2(p["ux"][0], p["uz"][0]) - math.atan2(u[0], u[2])
+    expect = N * 2 * math.atan(QEl * B * s.dt / (2 * g * MEl))
+    assert abs((turned - expect + math.pi) % (2 * math.pi) - math.pi) < 1e-9
