@@ -846,3 +846,42 @@ def test_mirror_x_z_with_pml_particles_and_filter(orc):
     assert np.abs(p1["ux"][o1] - u[0]).max() > 0.1 * C
     for k1, k2, scale in (("x", "z", s1.dx), ("z", "x", s1.dz), ("ux", "uz", C), ("uy", "uy", C), ("uz", "ux", C)):
         assert np.abs(p2[k1][o2] - p1[k2][o1]).max() <= 1e-12 * scale, k1
+
+
+# ---------------------------------------------------------------------------
+# The 2-1/2D push through whole steps in uniform periodic fields (weightless particles): the E x B drift
+# state moves at exactly v_d = E_x/B_y along z; in a uniform B_z the momentum turns in the (x, y) plane by
+# 2 atan(q B dt/(2 gamma m)) per step (an electron turns counter-clockwise about +z), z unchanged.
+def test_push_through_full_steps_drift_and_gyration(orc):
+    n, nz = 24, 48
+    w = vacuum(n, nz, "ck", courant=0.95)
+    s = orc.Sim(w)
+    Ex, By = 6e7, 1.0
+    vd = Ex / By
+    gd = 1 / math.sqrt(1 - (vd / C) ** 2)
+    s.set_field(0, np.full((n + 1, nz + 1), Ex))
+    s.set_field(4, np.full((n + 1, nz + 1), By))
+    x0, z0 = 11.3 * s.dx, 14.2 * s.dz
+    s.set_particles(0, [x0], [z0], [0.0], [0.0], [gd * vd], [0.0])
+    N = 60
+    s.step(N)
+    p = s.particles(0)
+    assert p["alive"][0]
+    assert p["z"][0] == pytest.approx(z0 + vd * N * s.dt, abs=1e-9 * s.dz)
+    assert p["x"][0] == pytest.approx(x0, abs=1e-9 * s.dx)
+    assert p["uz"][0] == pytest.approx(gd * vd, rel=1e-9)
+
+    s = orc.Sim(w)
+    B = 10.0
+    s.set_field(5, np.full((n + 1, nz + 1), B))
+    u = np.array([0.005 * C, 0.004 * C, 0.0])
+    g = math.sqrt(1 + (u @ u) / C ** 2)
+    s.set_particles(0, [x0], [20.0 * s.dz], [u[0]], [u[1]], [u[2]], [0.0])
+    N = 200
+    s.step(N)
+    p = s.particles(0)
+    assert p["alive"][0] and p["z"][0] == 20.0 * s.dz
+    assert math.hypot(p["ux"][0], p["uy"][0]) == pytest.approx(math.hypot(u[0], u[1]), rel=1e-13)
+    turned = math.atan2(p["uy"][0], p["ux"][0]) - math.atan2(u[1], u[0])
+    expect = N * 2 * math.atan(QE * B * s.dt / (2 * g * ME))
+    assert abs((turned - expect + math.pi) % (2 * math.pi) - math.pi) < 1e-9
