@@ -212,7 +212,8 @@ def run_reference(args, w):
     t1 = time.perf_counter() - t1
     projected = t1 * (args.steps + args.warmup)
     if projected > REF_BUDGET_S:
-        rows = max(32, int(rows * REF_BUDGET_S / projected) // 16 * 16)
+        # at least 96 rows: the first ~60 hold the PML, the guard and the antenna but no plasma
+        rows = max(96, int(rows * REF_BUDGET_S / projected) // 16 * 16)
         wsmp = W.shrink(w, w["nx"], rows)
         wsmp["precision"] = "fp64"
         s = oracle.Sim(wsmp)

@@ -93,3 +93,24 @@ def test_wide_band_workload_puts_the_antenna_inside_the_wider_domain():
     assert info["guard"] == 3 + 35 + 2
     zlo = info["gz_lo"] * info["dz"]
     assert ww["laser"]["z_antenna"] >= zlo + 4 * info["dz"] - 1e-12
+
+
+def test_reference_arm_shortens_its_sample_to_the_wall_clock_bound(monkeypatch, capsys):
+    """when one oracle step projects the run past the bound, the sample drops to fewer rows (>= 96)"""
+    import json
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1009_2727_gb300 import workloads as W
+    for k in ("WORLD_SIZE", "RANK", "LOCAL_RANK"):
+        monkeypatch.delenv(k, raising=False)
+    monkeypatch.setattr(bench, "REF_BUDGET_S", 1e-3)
+    w = W.shrink(W.stage_2d(), 64, 256)
+    w["name"] = "stage_2d_narrow"
+
+    class A:
+        steps, warmup, gpus = 1, 1, 1
+    assert bench.run_reference(A, w) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert "bounded sample: 96 x 64 cells" in line["config"]["workload"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
