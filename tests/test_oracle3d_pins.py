@@ -328,12 +328,12 @@ def _mirror(comp, a):
     return src, sign
 
 
-@pytest.mark.parametrize("gather", ["energy", "momentum"])
-def test_3d_mirror_x_y_with_pml_particles_and_filter(orc, gather):
+@pytest.mark.parametrize("gather,order", [("energy", 3), ("momentum", 3), ("energy", 1)])
+def test_3d_mirror_x_y_with_pml_particles_and_filter(orc, gather, order):
     rng = np.random.default_rng(23)
     n, nz, pml = 28, 26, 4
     w = vacuum3(n, n, nz, "ck", dx=0.9e-6, dy=0.9e-6, dz=0.7e-6, courant=0.9, theta=0.2, periodic=False,
-                pml_cells=pml, filter_passes=2, filter_compensate=1, particle_guard=5, gather=gather)
+                pml_cells=pml, filter_passes=2, filter_compensate=1, particle_guard=5, gather=gather, order=order)
     s1, s2 = orc.Sim3(w), orc.Sim3(w)
     F = [_interior_noise(rng, (n + 1, n + 1, nz + 1), pml + 2, 3e9 if c < 3 else 3e9 / C) for c in range(6)]
     for comp in range(6):

@@ -807,12 +807,13 @@ def test_gather_schemes_on_quadratic_field(orc, order):
 _MIRROR_XZ = {0: (2, 1.0), 1: (1, 1.0), 2: (0, 1.0), 3: (5, -1.0), 4: (4, -1.0), 5: (3, -1.0)}
 
 
-@pytest.mark.parametrize("gather", ["energy", "momentum"])
-def test_mirror_x_z_with_pml_particles_and_filter(orc, gather):
+@pytest.mark.parametrize("gather,order,strides", [("energy", 3, []), ("momentum", 3, []), ("energy", 1, [1, 2])])
+def test_mirror_x_z_with_pml_particles_and_filter(orc, gather, order, strides):
     rng = np.random.default_rng(41)
     n, pml = 60, 6
     w = vacuum(n, n, "ck", dx=0.8e-6, dz=0.8e-6, courant=0.9, theta=0.2, periodic=False, pml_cells=pml,
-               filter_passes=2, filter_compensate=1, filter_J=1, filter_gather=1, particle_guard=5, gather=gather)
+               filter_passes=2, filter_compensate=1, filter_J=1, filter_gather=1, particle_guard=5, gather=gather,
+               order=order, filter_strides=strides)
     s1, s2, s0 = orc.Sim(w), orc.Sim(w), orc.Sim(w)
     F = []
     for c in range(6):
