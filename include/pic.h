@@ -201,26 +201,34 @@ typedef struct {
 
 /* Create a context: validates cfg (coefficient normalisation, shape order,
  * dt against the stability limit -> PIC_ECFL), derives the boosted cell and
- * time step, allocates and zeroes the fields. cuda_stream is a cudaStream_t
+ * time step, allocates and zeroes the fields. The solver coefficients and the
+ * stability limit follow Sec. 4.2.1 (Table CKcoefs, Eq. cfl) and Sec. 4.3 (the
+ * Friedman factor); the boosted cell follows Sec. 5.1.1; the PML App. II. cuda_stream is a cudaStream_t
  * (NULL = the legacy default stream). On error *out is NULL. */
 int pic_init(const pic_config* cfg, pic_alloc_fn alloc, pic_free_fn free_fn, void* alloc_user,
              void* cuda_stream, pic_ctx** out);
 
 /* Load the plasma (rows inside the particle domain at t' = 0) and, optionally,
- * the test beam. May be called once, before the first pic_step. */
+ * the test beam (both as injected through a plane, Sec. 3.1.1). May be called
+ * once, before the first pic_step. */
 int pic_load_plasma(pic_ctx* ctx, const pic_plasma* plasma);
 
-/* Register the laser antenna; its current is deposited inside every pic_step. */
+/* Register the laser antenna (Sec. 3.1.2); its current is deposited inside every pic_step. */
 int pic_inject_laser(pic_ctx* ctx, const pic_laser* laser);
 
-/* Advance nsteps steps (asynchronous on the context stream). Returns a host-side
- * status; device-side errors are reported by pic_sync. */
+/* Advance nsteps steps (asynchronous on the context stream). One step: Faraday
+ * with the tunable operator and Friedman damping (Eq. Faraday, Eq.
+ * Faraday_Friedman) and the PML (App. II); the field gather and Boris push;
+ * Esirkepov deposition (Sec. 4.2.2); the antenna; the filter (Sec. 4.1) of the
+ * current and of the gathered fields; Ampere (Eq. Ampere); inflow, removal and
+ * the moving window (Sec. 3.1.1, Sec. 2). Returns a host-side status;
+ * device-side errors are reported by pic_sync. */
 int pic_step(pic_ctx* ctx, int nsteps);
 
 /* Wait for the stream and return the sticky device status. */
 int pic_sync(pic_ctx* ctx);
 
-/* Lab-frame stations/snapshots. With req != NULL and out == NULL: register the
+/* Lab-frame stations/snapshots (Sec. 3.2). With req != NULL and out == NULL: register the
  * sample rows (replacing any previous request) and zero their buffers; they are
  * filled while stepping. With req == NULL and out != NULL: copy the rows out
  * (synchronises the stream). */
