@@ -523,36 +523,37 @@ def test_3d_push_through_full_steps_drift_and_gyration(orc):
 # (the removal edge along z is one cell above the inflow plane).
 def test_3d_mirror_x_z_with_pml_particles_and_filter(orc):
     rng = np.random.default_rng(37)
-    n, ny, pml = 28, 20, 4
+    n, ny, pml = 28, 28, 4
     w = vacuum3(n, ny, n, "ck", dx=0.8e-6, dy=1.1e-6, dz=0.8e-6, courant=0.9, theta=0.2, periodic=False,
                 pml_cells=pml, filter_passes=2, filter_compensate=1, particle_guard=5)
-    s1, s2 = orc.Sim3(w), orc.Sim3(w)
+    s1, s2, s0 = orc.Sim3(w), orc.Sim3(w), orc.Sim3(w)
     swap = {0: (2, 1.0), 1: (1, 1.0), 2: (0, 1.0), 3: (5, -1.0), 4: (4, -1.0), 5: (3, -1.0)}
     F = [_interior_noise(rng, (n + 1, ny + 1, n + 1), pml + 2, 3e9 if c < 3 else 3e9 / C) for c in range(6)]
     for comp in range(6):
         src, sign = swap[comp]
         s1.set_field(comp, F[comp])
+        s0.set_field(comp, F[comp])
         s2.set_field(comp, sign * np.transpose(F[src], (2, 1, 0)))
     npart = 40
     x = rng.uniform(11.5, 16.5, npart) * s1.dx
-    y = rng.uniform(8.5, 11.5, npart) * s1.dy
+    y = rng.uniform(11.5, 16.5, npart) * s1.dy
     z = rng.uniform(11.5, 16.5, npart) * s1.dz
     u = rng.standard_normal((3, npart)) * 0.05 * C
     wt = np.full(npart, 1e8)
     s1.set_particles(0, x, y, z, u[0], u[1], u[2], wt)
     s2.set_particles(0, z, y, x, u[2], u[1], u[0], wt)
-    s1.step(30)
-    s2.step(30)
+    for s in (s0, s1, s2):
+        s.step(30)
     for comp in range(6):
         src, sign = swap[comp]
         a = s2.field(comp)
         b = sign * np.transpose(s1.field(src), (2, 1, 0))
         assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max(), comp
     p1, p2 = s1.particles(0), s2.particles(0)
-    assert p1["alive"].all() and p2["alive"].all()
+    assert len(p1["id"]) == npart and len(p2["id"]) == npart          # nobody left the particle domain
     o1, o2 = np.argsort(p1["id"]), np.argsort(p2["id"])
     for k1, k2, scale in (("x", "z", s1.dx), ("y", "y", s1.dy), ("z", "x", s1.dz),
                           ("ux", "uz", C), ("uy", "uy", C), ("uz", "ux", C)):
         assert np.abs(p2[k1][o2] - p1[k2][o1]).max() <= 1e-12 * scale, k1
     assert np.abs(p1["ux"][o1] - u[0]).max() > 1e-3 * C                  # the gather and push acted
-    assert np.abs(s1.field(1)).max() > 10 * np.abs(F[1]).max()           # the deposit shaped the fields
+    assert np.abs(s1.field(1) - s0.field(1)).max() > 0.1 * np.abs(s0.field(1)).max()   # the deposit acted
