@@ -270,11 +270,13 @@ const char* pic_last_error(pic_ctx* ctx);
  *    the layout of pic_get_field. It is zeroed and filled on the context's
  *    stream; the call returns without waiting (pic_sync or a stream
  *    synchronisation makes the result visible to the host).
+ *  - 2D contexts only: 1D and 3D contexts return PIC_EINVAL.
  *  - The ion row density is staged in a file-scope static device array of
  *    PIC_NOALLOC_MAX_NZ+1 doubles (128 KiB) that every GPU loading the library
- *    keeps until the process exits. The first call on a device looks up that
- *    array's device address (cudaGetSymbolAddress, with the device current);
- *    make that first call before any stream capture.
+ *    keeps until the process exits. Every call looks up that array's device
+ *    address (cudaGetSymbolAddress, with the caller's device current; the
+ *    lookup allocates nothing). The first call on a device may load the
+ *    library's device code there: make it before any stream capture.
  *  - All calls share the array and it keeps the last call's contents; calls
  *    whose work overlaps on the GPU (several contexts or streams at once) race.
  *  - nz > PIC_NOALLOC_MAX_NZ is rejected with PIC_EINVAL (pic_last_error says

@@ -7,7 +7,6 @@
 //  - the test beam through a plane (Sec. 3.1.1): Lorentz transform and push;
 //  - back-transformed lab-frame samples (Sec. 3.2, PR-16);
 //  - charge density, reductions, moving-window shift, copies.
-#include <mutex>
 
 #include "../../include/pic.h"
 #include "pic_common.cuh"
@@ -555,41 +554,44 @@ __global__ void k_shift_particles(GridP g, Particles<T> p, const Ctrl* ctrl, int
 // ---------------------------------------------------------------------------
 // Charge density without device allocation: the ion row density R(k) goes to
 // this file-scope scratch instead of a context buffer. Its device address is
-// looked up once per device, with that device current.
+// looked up on every call, with the caller's device current: the lookup
+// allocates nothing, and a cached address could go stale if the caller reset
+// the device and the module were loaded again elsewhere.
 static __device__ __align__(256) double g_noalloc_rows[PIC_NOALLOC_MAX_NZ + 1];
-
-static double* noalloc_rows_address(int& err) {
-  static std::mutex mu;
-  static double* addr[256] = {nullptr};
-  int dev = 0;
-  err = (int)cudaGetDevice(&dev);
-  if (err != (int)cudaSuccess || dev < 0 || dev >= 256) return nullptr;
-  std::lock_guard<std::mutex> lock(mu);
-  if (!addr[dev]) {
-    void* p = nullptr;
-    err = (int)cudaGetSymbolAddress(&p, g_noalloc_rows);
-    if (err != (int)cudaSuccess) return nullptr;
-    addr[dev] = (double*)p;
-  }
-  return addr[dev];
-}
 
 template <class T>
 int launch_rho_noalloc(const GridP& g, Particles<T> p, const Ctrl* ctrl, int cap, int order, bool ions,
                        long long mlo, long long mhi, double t, const InjectP& ip, const double* ion_x, double* dst,
-                       cudaStream_t s) {
+                       cudaStream_t s, cudaError_t* why, int* kernels) {
+  *why = cudaSuccess;
+  *kernels = 0;
   if (g.nz > PIC_NOALLOC_MAX_NZ) return 1;
-  int err = 0;
-  double* rows = noalloc_rows_address(err);
-  if (!rows) return 2;
+  // a launch error left on this thread by unrelated work is not this call's failure
+  (void)cudaGetLastError();
+  void* addr = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&addr, g_noalloc_rows);
+  if (e != cudaSuccess || !addr) {
+    *why = e;
+    return 2;
+  }
+  double* rows = static_cast<double*>(addr);
   cudaMemsetAsync(dst, 0, sizeof(double) * (size_t)(g.nx + 1) * (g.nz + 1), s);
-  if (cap > 0) k_rho<T><<<(cap + 255) / 256, 256, 0, s>>>(g, p, ctrl, order, -kQe, dst);
+  if (cap > 0) {
+    k_rho<T><<<(cap + 255) / 256, 256, 0, s>>>(g, p, ctrl, order, -kQe, dst);
+    (*kernels)++;
+  }
   if (ions) {
     // the same row-density kernel as the step, at one time (both outputs alias the scratch)
     k_ion_rows<<<dim3((g.nz + 1 + 7) / 8, 1), 256, 0, s>>>(g, mlo, mhi, t, t, ip, order, rows, rows);
     launch_ion_rho(g, ion_x, rows, kQe / (g.dx * g.dz), dst, s);
+    *kernels += 2;
   }
-  return cudaPeekAtLastError() == cudaSuccess ? 0 : 3;
+  const cudaError_t le = cudaGetLastError();
+  if (le != cudaSuccess) {
+    *why = le;
+    return 3;
+  }
+  return 0;
 }
 
 void launch_ion_column(const GridP& g, long long mlo, long long mhi, double t0, double t1, const InjectP& ip,
@@ -741,7 +743,8 @@ void launch_shift_particles(const GridP& g, Particles<T> p, const Ctrl* ctrl, in
                                        cudaStream_t);                                                             \
   template void launch_shift_particles<T>(const GridP&, Particles<T>, const Ctrl*, int, int, cudaStream_t);                 \
   template int launch_rho_noalloc<T>(const GridP&, Particles<T>, const Ctrl*, int, int, bool, long long,         \
-                                     long long, double, const InjectP&, const double*, double*, cudaStream_t);
+                                     long long, double, const InjectP&, const double*, double*, cudaStream_t,   \
+                                     cudaError_t*, int*);
 INST(float)
 INST(double)
 #undef INST

@@ -755,12 +755,17 @@ struct Sim : SimBase {
       const double t = time_of(step);
       mlo = std::max(row_first, (long long)std::ceil((zlo_prev + c->hg.beta * kC * t) / ip.h - 0.5));
     }
+    cudaError_t why = cudaSuccess;
+    int kernels = 0;
     int r = launch_rho_noalloc<T>(g, P, ctrl, loaded ? cap : 0, c->cfg.shape_order, ions && loaded, mlo, row_next,
-                                  time_of(step), ip, ion_x, dst, c->stream);
+                                  time_of(step), ip, ion_x, dst, c->stream, &why, &kernels);
+    c->launches += kernels;
     if (r == 1) return c->fail(PIC_EINVAL, "pic_get_rho_noalloc: nz exceeds PIC_NOALLOC_MAX_NZ");
-    if (r == 2) return c->fail(PIC_ECUDA, "pic_get_rho_noalloc: cudaGetSymbolAddress of the scratch failed");
-    if (r == 3) return c->fail(PIC_ECUDA, "pic_get_rho_noalloc: kernel launch failed");
-    c->launches += ions && loaded ? 4 : 2;
+    if (r == 2)
+      return c->fail(PIC_ECUDA, std::string("pic_get_rho_noalloc: cudaGetSymbolAddress of the scratch failed: ") +
+                                    cudaGetErrorString(why));
+    if (r == 3)
+      return c->fail(PIC_ECUDA, std::string("pic_get_rho_noalloc: kernel launch failed: ") + cudaGetErrorString(why));
     return PIC_OK;
   }
 

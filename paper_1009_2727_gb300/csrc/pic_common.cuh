@@ -333,10 +333,11 @@ void launch_compact_copy(const GridP& g, Particles<T> p, const Ctrl* ctrl, int c
                          int* nout, cudaStream_t s);
 template <class T>
 void launch_shift_particles(const GridP& g, Particles<T> p, const Ctrl* ctrl, int cap, int sh, cudaStream_t s);
-// returns 0, or 1 (nz above the scratch size), 2 (scratch address lookup failed), 3 (launch error)
+// returns 0, or 1 (nz above the scratch size), 2 (scratch address lookup failed), 3 (launch error); *why is
+// the CUDA error of cases 2 and 3, *kernels the number of kernels enqueued
 template <class T>
 int launch_rho_noalloc(const GridP& g, Particles<T> p, const Ctrl* ctrl, int cap, int order, bool ions,
                        long long mlo, long long mhi, double t, const InjectP& ip, const double* ion_x, double* dst,
-                       cudaStream_t s);
+                       cudaStream_t s, cudaError_t* why, int* kernels);
 
 }  // namespace picgb

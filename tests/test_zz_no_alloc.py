@@ -41,9 +41,16 @@ def test_rho_noalloc_matches_accessor_on_consecutive_calls(precision):
     for call in range(2):
         ref = sim.field(capi.RHO)
         out.fill_(123.0)                      # stale contents must not leak into the result
+        torch.cuda.synchronize()
+        # the library allocates through torch's caching allocator (its allocator callback), and a direct
+        # cudaMalloc would show in the device's free memory: neither may move during the call
+        n_alloc = torch.cuda.memory_stats()["allocation.all.allocated"]
+        free0, _ = torch.cuda.mem_get_info()
         r = L.pic_get_rho_noalloc(sim.h, ptr)
         assert r == capi.PIC_OK, sim.L.pic_last_error(sim.h)
         sim.sync()
+        assert torch.cuda.memory_stats()["allocation.all.allocated"] == n_alloc
+        assert torch.cuda.mem_get_info()[0] == free0
         got = out.cpu().numpy()
         assert np.abs(ref).max() > 0
         err = np.abs(got - ref).max() / scale
