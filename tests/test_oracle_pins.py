@@ -501,6 +501,48 @@ def test_pml_reflection_small(orc, solver):
     assert refl[0] == pytest.approx(refl[1], rel=0.5)     # "both implementations gave nearly identical results"
 
 
+def _pml_round_trip(orc, axis, L, sm, power, xi_exp, dx, dz, N=420):
+    """a smooth plane pulse (Gaussian, 20 cells) sent along one axis (the other periodic) into a weak layer
+    backed by the PEC wall: the amplitude that comes back after the round trip"""
+    w = {"nx": 4 if axis == "z" else N, "nz": N if axis == "z" else 4, "dz_lab": dz, "dx": dx, "gamma_boost": 1.0,
+         "courant": 0.5, "solver": W.SOLVERS["yee"], "theta": 0.0, "order": 3,
+         "periodic_x": int(axis == "z"), "periodic_z": int(axis == "x"),
+         "pml_cells": L, "pml_sigma_max": sm, "pml_delta": 5.0, "pml_power": power, "pml_xi_exp": xi_exp}
+    s = orc.Sim(w)
+    d = dz if axis == "z" else dx
+    j0, wid = 0.6 * N, 20.0
+    j = np.arange(N + 1)
+    ey = np.exp(-((j - j0) / wid) ** 2)
+    # the B partner half a cell up and half a step earlier, so that the pulse runs towards the far wall
+    bp = np.exp(-((j + 0.5 - j0 + 0.5 * C * s.dt / d) / wid) ** 2) / C
+    if axis == "z":
+        s.set_field(1, np.tile(ey, (5, 1)))
+        s.set_field(3, -np.tile(bp, (5, 1)))
+    else:
+        s.set_field(1, np.tile(ey[:, None], (1, 5)))
+        s.set_field(5, np.tile(bp[:, None], (1, 5)))
+    s.step(int(2 * (N - j0) * d / (C * s.dt)))
+    line = s.field(1)[2, :] if axis == "z" else s.field(1)[:, 2]
+    return np.abs(line[int(j0) - 80:int(j0) + 80]).max()
+
+
+@pytest.mark.parametrize("axis", ["z", "x"])
+def test_pml_profile_by_round_trip_attenuation(orc, axis):
+    """App. II's absorption profile sigma = sigma_m (c/delta) (d/Delta)^n (PR-18 units), pinned through what it
+    does: in a continuous layer a plane wave decays as exp(-(1/c) int sigma dz), so the pulse that crosses a
+    weak layer of L cells twice (PEC behind it) returns with amplitude exp(-2 sigma_m L^(n+1)/((n+1) Delta^n)),
+    independent of the cell size. The oracle's layer reproduces it within 1% for the powers 1, 2, 3 and both
+    forms of xi, on cells of different size along x and z (measured 0.03-0.6%); a wrong power, scale,
+    Delta, or the other axis's cell size in sigma would miss it by tens of per cent."""
+    L = 16
+    for power, sm, xi_exp in ((2, 0.0084, 1), (1, 0.0084, 1), (3, 0.004, 1), (2, 0.0084, 0)):
+        got = _pml_round_trip(orc, axis, L, sm, power, xi_exp, dx=2.5e-6, dz=1e-6)
+        want = math.exp(-2.0 * sm * L ** (power + 1) / ((power + 1) * 5.0 ** power))
+        assert got == pytest.approx(want, rel=0.01), (power, sm, xi_exp, got, want)
+    # the same layer with no absorption returns the pulse whole (the PEC reflects it)
+    assert _pml_round_trip(orc, axis, L, 0.0, 2, 1, dx=2.5e-6, dz=1e-6) == pytest.approx(1.0, rel=0.01)
+
+
 # ---------------------------------------------------------------------------
 # Sec. 3.1.1: beam through a plane reproduces the Lorentz transform of the worldlines
 def test_beam_plane_injection_matches_lorentz(orc):
