@@ -41,13 +41,12 @@ BYTES_PER_PARTICLE_3D = {"mixed": 76, "fp64": 104}
 # algorithmic bytes per cell-step of the field kernels (mixed, with Friedman): see the design notes
 BYTES_PER_CELL = {"mixed": 168, "fp64": 336}
 # measured DRAM bytes (read + write) per particle of one push launch, mixed precision, cubic shapes:
-# ncu dram__bytes_read.sum + dram__bytes_write.sum of k_push on the 2048 x 256 stage box with the tuned
-# layout (8 x 16-cell tiles, sort every 64 steps; profiles/k_push_stage2d_2048x256_mixed.md: 382.41 MB
-# for 6,496,584 electrons), scaled to the full box by its particle count; None for other configurations
+# ncu dram__bytes_read.sum + dram__bytes_write.sum of k_push on the 2048 x 256 stage box, scaled to the
+# full box by its particle count; None for other configurations
 TRAFFIC_BYTES_PER_PARTICLE = {("mixed", 3): 58.87}
 TRAFFIC_LAYOUT = ((8, 16), 64)
-# 3D: ncu dram bytes of k3_push_tiles on the 256 x 128 x 128 box (profiles/k3_push_tiles_stage3d_256x128x128_mixed.md:
-# 198.06 MB for 2,356,608 electrons), scaled to the full box by its particle count
+# 3D: ncu dram bytes of k3_push_tiles on the 256 x 128 x 128 box (198.06 MB for 2,356,608 electrons), scaled
+# to the full box by its particle count
 TRAFFIC_BYTES_PER_PARTICLE_3D = {("mixed", 3): 84.0}
 
 
@@ -148,48 +147,92 @@ def barrier(ws: int):
 
 
 # ----------------------------------------------------------------------------
-def cpu_oracle_sample(w: dict, seconds: float = 15.0, max_steps: int = 40) -> dict:
-    """Time the FP64 oracle, as it stands, on a bounded sample of the workload: the same numerics on a
-    box of 512 (z) x 256 (x) cells (one eighth of the particles), a few steps."""
-    import oracle
-    from paper_1009_2727_gb300 import workloads as W
-    ws = W.shrink(w, w["nx"], 512)
-    ws["precision"] = "fp64"
-    t0 = time.perf_counter()
-    s = oracle.Sim(ws)
-    setup = time.perf_counter() - t0
-    n = len(s.particles(0)["x"])
-    steps = 0
-    t0 = time.perf_counter()
-    while steps < max_steps and (time.perf_counter() - t0) < seconds:
-        s.step(1)
-        steps += 1
-    dt = time.perf_counter() - t0
-    return {"value": n * steps / dt, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
-            "sample": f"{ws['name']}: {n} electrons (+ as many ions), {steps} steps, {dt:.1f} s "
-                      f"(setup {setup:.1f} s), single thread"}
+# The CPU baseline: the FP64 oracle as it stands (single-threaded C), on a slice of the workload: all of
+# its transverse cells and particles per cell, ORACLE_ROWS cells along z. On all host cores it runs as one
+# independent copy per core (spawned processes), the oracle itself unchanged.
+ORACLE_ROWS = 256
+ORACLE_ROWS_3D = 128
 
 
-def cpu_oracle_sample3(w: dict, seconds: float = 15.0, max_steps: int = 40) -> dict:
-    """The 3D oracle, as it stands, on a bounded sample of the 3D workload: the same numerics on a box
-    of 128 (z) x 64 (y) x 64 (x) cells, a few steps."""
-    import oracle
+def host_cpu() -> dict:
+    """the host's core count and CPU model (lscpu, else /proc/cpuinfo)"""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu model")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return {"nproc": os.cpu_count(), "model": model}
+
+
+def oracle_slice(w: dict, three: bool, rows: int = 0) -> dict:
     from paper_1009_2727_gb300 import workloads as W
-    ws = W.shrink3(w, 64, 64, 128)
+    if three:
+        ws = W.shrink3(w, 64, 64, rows or ORACLE_ROWS_3D)
+    else:
+        ws = W.shrink(w, w["nx"], rows or ORACLE_ROWS)
     ws["precision"] = "fp64"
-    t0 = time.perf_counter()
-    s = oracle.Sim3(ws)
-    setup = time.perf_counter() - t0
+    return ws
+
+
+def _oracle_worker(job):
+    """one oracle copy (run in its own spawned process, or inline): warm-up steps untimed, then timed steps
+    until `steps` are done or `seconds` have passed; returns (particles, timed steps, seconds)"""
+    ws, three, warmup, steps, seconds = job
+    import oracle
+    s = oracle.Sim3(ws) if three else oracle.Sim(ws)
+    if warmup > 0:
+        s.step(warmup)
     n = len(s.particles(0)["x"])
-    steps = 0
+    k = 0
     t0 = time.perf_counter()
-    while steps < max_steps and (time.perf_counter() - t0) < seconds:
+    while k < steps and (time.perf_counter() - t0) < seconds:
         s.step(1)
-        steps += 1
-    dt = time.perf_counter() - t0
-    return {"value": n * steps / dt, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
-            "sample": f"{ws['name']} on 128 x 64 x 64 cells: {n} electrons (+ as many ions), {steps} steps, "
-                      f"{dt:.1f} s (setup {setup:.1f} s), single thread"}
+        k += 1
+    return n, k, time.perf_counter() - t0
+
+
+def oracle_throughput(ws: dict, three: bool, procs: int, warmup: int, steps: int, seconds: float) -> dict:
+    """particle-steps/s of `procs` copies of the oracle side by side (1: inline, single thread)"""
+    import oracle
+    oracle.build()
+    job = (ws, three, warmup, steps, seconds)
+    if procs <= 1:
+        res = [_oracle_worker(job)]
+    else:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(procs) as pool:
+            res = pool.map(_oracle_worker, [job] * procs)
+    tot = sum(n * k for n, k, _ in res)
+    wall = max(dt for _, _, dt in res)
+    return {"value": tot / wall, "particles": res[0][0], "steps": min(k for _, k, _ in res), "seconds": wall,
+            "copies": len(res)}
+
+
+def cpu_baseline_line(w: dict, three: bool, seconds: float = 8.0) -> dict:
+    """the oracle on the workload's slice: one thread, then one copy per host core"""
+    ws = oracle_slice(w, three)
+    cpu = host_cpu()
+    one = oracle_throughput(ws, three, 1, 1, 40, seconds)
+    allc = oracle_throughput(ws, three, cpu["nproc"] or 1, 1, 40, seconds)
+    box = f"{ws['nz']} x {ws['ny']} x {ws['nx']}" if three else f"{ws['nz']} x {ws['nx']}"
+    return {"value": allc["value"], "unit": "particle-steps/s", "cores": allc["copies"], "kind": "oracle",
+            "single_thread": one["value"], "cpu": cpu,
+            "sample": (f"{w['name']} on a {box}-cell slice ({one['particles']} electrons + as many ions): "
+                       f"{allc['copies']} independent copies of the single-threaded oracle, one per host core, "
+                       f"{allc['steps']}+ steps in {allc['seconds']:.1f} s; one copy alone {one['steps']} steps in "
+                       f"{one['seconds']:.1f} s")}
 
 
 REF_BUDGET_S = 150.0      # wall-clock bound of the reference arm's steps
@@ -199,40 +242,33 @@ def run_reference(args, w):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    import oracle
-    from paper_1009_2727_gb300 import workloads as W
-    # the sample: a 256-cell slice of the box, shortened when one step projects the whole
-    # --steps/--warmup run past REF_BUDGET_S (the oracle's throughput per particle does not depend on it)
-    rows = 256
-    wsmp = W.shrink(w, w["nx"], rows)
-    wsmp["precision"] = "fp64"
-    s = oracle.Sim(wsmp)
-    t1 = time.perf_counter()
-    s.step(1)
-    t1 = time.perf_counter() - t1
+    three = w.get("dim", 2) == 3
+    cpu = host_cpu()
+    procs = cpu["nproc"] or 1
+    # the sample: the same slice as the main arm's cpu_baseline, shortened when one step projects the
+    # whole --steps/--warmup run past REF_BUDGET_S (the oracle's throughput per particle does not depend on it)
+    wsmp = oracle_slice(w, three)
+    t1 = _oracle_worker((wsmp, three, 0, 1, 1e9))[2]
     projected = t1 * (args.steps + args.warmup)
-    if projected > REF_BUDGET_S:
+    if projected > REF_BUDGET_S and not three:
         # at least 96 rows: the first ~60 hold the PML, the guard and the antenna but no plasma
-        rows = max(96, int(rows * REF_BUDGET_S / projected) // 16 * 16)
-        wsmp = W.shrink(w, w["nx"], rows)
-        wsmp["precision"] = "fp64"
-        s = oracle.Sim(wsmp)
-        s.step(1)
-    n = len(s.particles(0)["x"])
-    for _ in range(args.warmup - 1):
-        s.step(1)
-    t0 = time.perf_counter()
-    s.step(args.steps)
-    dt = time.perf_counter() - t0
-    v = n * args.steps / dt
+        rows = max(96, int(ORACLE_ROWS * REF_BUDGET_S / projected) // 16 * 16)
+        wsmp = oracle_slice(w, three, rows)
+    r = oracle_throughput(wsmp, three, procs, args.warmup, args.steps, REF_BUDGET_S)
+    v = r["value"]
+    box = f"{wsmp['nz']} x {wsmp['ny']} x {wsmp['nx']}" if three else f"{wsmp['nz']} x {wsmp['nx']}"
     line = {"metric": "particle-steps/s", "value": v, "unit": "particle-steps/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["seconds"] / max(r["steps"], 1) * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": w["name"] + f" (bounded sample: {rows} x {w['nx']} cells)", "grid": [w["nz"], w["nx"]],
-                       "ppc": 16, "precision": "fp64 oracle"},
-            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": v, "unit": "particle-steps/s",
-                             "sample": f"{wsmp['name']}: {n} electrons, {args.steps} steps, {dt:.1f} s"},
+            "config": {"workload": w["name"] + f" (bounded sample: {box} cells)",
+                       "grid": [w["nz"], w["ny"], w["nx"]] if three else [w["nz"], w["nx"]],
+                       "ppc": 2 if three else 16, "precision": "fp64 oracle"},
+            "cpu_baseline": {"kind": "oracle", "cores": r["copies"], "value": v, "unit": "particle-steps/s",
+                             "cpu": cpu,
+                             "sample": f"{box}-cell slice, {r['particles']} electrons per copy, {r['copies']} "
+                                       f"copies of the single-threaded oracle (one per host core), {r['steps']} "
+                                       f"timed steps after {args.warmup}, {r['seconds']:.1f} s"},
             "e2e": {"value": v, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -290,7 +326,7 @@ def run_ensemble(args):
     ps = 0.5 * (n0 + n1) * args.steps
     line = {"metric": "ensemble particle-steps/s", "value": ps / (ms * 1e-3), "unit": "particle-steps/s",
             "n_gpus": 1, "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps,
-            "higher_is_better": True, "dtype": "f32+f64pos", "data": "synthetic",
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"ensemble_2d({args.ensemble}) seeded uneven runs", "runs": len(ws),
                        "cells": cells, "electrons": int(0.5 * (n0 + n1))},
             "sequential_ms_per_step": seq_ms / args.steps, "speedup_vs_sequential": seq_ms / ms,
@@ -464,7 +500,7 @@ def run_1d(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         s2 = Simulation(w, precision=args.precision)
-        k2 = max(args.steps // 2, 10)
+        k2 = args.steps
         for _ in range(k2):
             s2.step(1)
             st = s2.stats()
@@ -477,8 +513,10 @@ def run_1d(args):
     line = {"metric": "particle-steps/s", "value": value, "unit": "particle-steps/s", "n_gpus": 1,
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+f64pos" if args.precision == "mixed" else "f64", "data": "synthetic",
-            "config": {"workload": w["name"], "grid": [w["nz"]], "ppc": 10, "gamma_boost": 1.0,
+            "dtype": "f32" if args.precision == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": w["name"],
+                       "positions": ("int32 cell + f32 in-cell offset (z in the plasma's drifting frame)"
+                                     if args.precision == "mixed" else "f64"), "grid": [w["nz"]], "ppc": 10, "gamma_boost": 1.0,
                        "solver": "Yee (1D)", "c_dt_over_dz": 1.0, "filter": "1 pass, no compensation",
                        "shape_order": 3, "precision": args.precision, "electrons": int(n_avg),
                        "moving_window": "lab frame at c", "l2": "fits in L2 (a 1D run is small)",
@@ -615,7 +653,7 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = cpu_oracle_sample3(w) if three else cpu_oracle_sample(w)
+        cpu = cpu_baseline_line(w, three)
 
     tuned = None
     if args.tile:
@@ -703,7 +741,7 @@ def main():
             s2 = Simulation(w, precision=args.precision, tune=True)
         else:
             s2 = Simulation(w, precision=args.precision, sort_every=args.sort_every)
-        k2 = max(args.steps // 2, 10)
+        k2 = args.steps
         for _ in range(k2):
             s2.step(1)
             st = s2.stats()
@@ -725,8 +763,10 @@ def main():
             "metric": "particle-steps/s", "value": value, "unit": "particle-steps/s", "n_gpus": ws,
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+f64pos" if args.precision == "mixed" else "f64", "data": "synthetic",
+            "dtype": "f32" if args.precision == "mixed" else "f64", "data": "synthetic",
             "config": {"workload": w["name"],
+                       "positions": ("int32 cell + f32 in-cell offset (z in the plasma's drifting frame)"
+                                     if args.precision == "mixed" else "f64"),
                        "grid": [w["nz"], w["ny"], w["nx"]] if three else [w["nz"], w["nx"]],
                        "ppc": 2 if three else 16, "gamma_boost": w["gamma_boost"],
                        "solver": args.solver or ("CK2" if three else "CK"), "theta": w["theta"],

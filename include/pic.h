@@ -286,6 +286,16 @@ int pic_get_rho_noalloc(pic_ctx* ctx, double* dst_device);
 /* Number of kernel launches enqueued so far by this context (bench accounting). */
 int64_t pic_kernel_launches(pic_ctx* ctx);
 
+/* Measured FP32 arithmetic peak of the current device, in TFLOP/s: the best of
+ * five launches of a kernel whose threads run eight independent FMA chains
+ * over every SM (two FLOPs per FMA lane), once with scalar FMAs and once with
+ * the packed two-lane FMA of sm_100 and later. The denominator of the push
+ * kernel's arithmetic roofline (the paper measures no GPU; this is a
+ * measurement service of the library). Allocates one small scratch buffer
+ * with cudaMalloc and frees it; synchronises the device. Returns PIC_EINVAL
+ * for null outputs, PIC_ENOMEM or PIC_ECUDA on CUDA failures. */
+int pic_measure_fp32_peak(double* scalar_tflops, double* packed_tflops);
+
 /* Record CUDA events around the launches of the named kernel class in the next
  * pic_step calls and return their summed duration in ms (0 = particle kernel,
  * 1 = field kernels). Used by the benchmark for the per-kernel roofline. */

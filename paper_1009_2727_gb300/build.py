@@ -17,7 +17,7 @@ SRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpicgb.so")
 UNITS = ["pic_fields.cu", "pic_particles.cu", "pic_aux.cu", "pic_capi.cu", "pic_tune.cu", "pic_ensemble.cu", "pic_mlp.cu", "pic_3d.cu",
-         "pic_1d.cu"]
+         "pic_1d.cu", "pic_peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off", "--expt-relaxed-constexpr"]
 

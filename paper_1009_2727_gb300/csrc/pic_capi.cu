@@ -613,7 +613,8 @@ struct Sim : SimBase {
       int fr1_sz;
       float fr1_fz;
       frame_of(frame_shift(step + 1), fr1_sz, fr1_fz);
-      launch_push<T>(g, f, P, chunks, ctrl, cf.shape_order, push_grid, smem_nodes, -kQe, kMe, c->hg.gamma, c->hg.beta,
+      launch_push<T>(g, f, P, chunks, ctrl, cf.shape_order, push_grid, smem_nodes, sb.tz, -kQe, kMe, c->hg.gamma,
+                     c->hg.beta,
                      fr1_sz, fr1_fz, (pairs && ions) ? 1 : 0, (int)mlo, nodal ? 1 : 0, c->stream);
       tstop(0);
       c->launches++;

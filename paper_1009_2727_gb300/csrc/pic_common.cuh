@@ -238,8 +238,8 @@ void launch_ampere(const GridP& g, const FieldPtrs<T>& f, const PmlTabs& pt, con
 
 template <class T>
 void launch_push(const GridP& g, const FieldPtrs<T>& f, Particles<T> p, Chunk* chunks, Ctrl* ctrl, int order,
-                 int grid_blocks, int smem_nodes, double q, double m, double gamma_b, double beta_b, int fr1_sz,
-                 float fr1_fz, int pairs, int mlo, int nodal, cudaStream_t s);
+                 int grid_blocks, int smem_nodes, int tile_z, double q, double m, double gamma_b, double beta_b,
+                 int fr1_sz, float fr1_fz, int pairs, int mlo, int nodal, cudaStream_t s);
 
 struct SortBufs {
   int* cell_cnt;       // ntiles*tx*tz, cells in tile-major order: particles per cell

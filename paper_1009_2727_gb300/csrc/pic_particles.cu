@@ -238,30 +238,81 @@ __device__ __forceinline__ void ion_jz(T* Jb, long cs, int ld, int ox, int oz, c
   }
 }
 
+// Cells of the chunk's box (inclusive): a particle whose cell at t^n, or whose
+// lab-fixed ion's cell, lies outside it is not in the staged window.
+struct Box {
+  int ix0, ix1, iz0, iz1;
+  __device__ __forceinline__ bool in(int fx, int fz) const { return fx >= ix0 && fx <= ix1 && fz >= iz0 && fz <= iz1; }
+};
+
+// mixed path, cubic or linear shapes: the gather of two components stored as a
+// pair at one Yee location (weights wx, wz shared) with packed FP32 FMAs, and
+// of two components at different locations (separate windows and weights),
+// also packed: each lane of the pair rounds exactly like the scalar FMA
+template <int ORDER>
+__device__ __forceinline__ float2 interp_pair_f(const float2* __restrict__ F, int base, int ld, const float* wx,
+                                               const float* wz) {
+  constexpr int NG = St<ORDER>::NG;
+  float2 acc = make_float2(0.0f, 0.0f);
+  const float2* row = F + base;
+#pragma unroll
+  for (int a = 0; a < NG; a++) {
+    float2 sacc = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int b = 0; b < NG; b++) sacc = __ffma2_rn(row[b], make_float2(wz[b], wz[b]), sacc);
+    acc = __ffma2_rn(sacc, make_float2(wx[a], wx[a]), acc);
+    row += ld;
+  }
+  return acc;
+}
+template <int ORDER>
+__device__ __forceinline__ float2 interp_two_f(const float* __restrict__ F0, int base0, const float* __restrict__ F1,
+                                              int base1, int ld, const float* wx0, const float* wz0,
+                                              const float* wx1, const float* wz1) {
+  constexpr int NG = St<ORDER>::NG;
+  float2 acc = make_float2(0.0f, 0.0f);
+  const float* r0 = F0 + base0;
+  const float* r1 = F1 + base1;
+#pragma unroll
+  for (int a = 0; a < NG; a++) {
+    float2 sacc = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int b = 0; b < NG; b++) sacc = __ffma2_rn(make_float2(r0[b], r1[b]), make_float2(wz0[b], wz1[b]), sacc);
+    acc = __ffma2_rn(sacc, make_float2(wx0[a], wx1[a]), acc);
+    r0 += ld;
+    r1 += ld;
+  }
+  return acc;
+}
+
 // One particle: gather -> Boris -> move -> Esirkepov. E/B/J are 3-component
 // blocks (component stride cs) addressed as (i - ox)*ld + (k - oz). With SMEM
 // the fields are the shared-memory window: pairs (Ex, Bz) and (Ez, Bx), which
 // share a Yee location, then Ey and By, each block cs elements long (Bb unused).
+// With SMEM the particle must lie in the staged window: when its cell at t^n
+// (or its live lattice ion's cell) is outside the chunk's box, nothing is
+// changed and false is returned, so that the caller takes the global path.
 template <class T, int ORDER, bool SMEM, bool MC = false>
-__device__ __forceinline__ void push_one(const T* __restrict__ Eb, const T* __restrict__ Bb, T* Jb, long cs, int ld,
-                                         int ox, int oz, Particles<T>& p, int pi, const PushConst& pc, int& bx0,
-                                         int& bx1, int& bz0, int& bz1) {
+__device__ __forceinline__ bool push_one(const T* __restrict__ Eb, const T* __restrict__ Bb, T* Jb, long cs, int ld,
+                                         int ox, int oz, Particles<T>& p, int pi, const PushConst& pc, const Box& box,
+                                         int& bx0, int& bx1, int& bz0, int& bz1) {
   constexpr int NG = St<ORDER>::NG, ND = St<ORDER>::ND;
   constexpr bool CP = CellPos<T>::value;
   const T w = p.w[pi];
-  if (w == T(0)) return;
+  if (w == T(0)) return true;
   if constexpr (CP) {
     if (w < T(0)) {
       // ghost: the lab-fixed ion of an electron that has left the domain; it
       // deposits its J_z until its lattice row leaves too
       const uint32_t id = p.id[pi];
-      if (site_row(id, pc) < pc.mlo) { p.w[pi] = T(0); return; }
+      if (site_row(id, pc) < pc.mlo) { p.w[pi] = T(0); return true; }
       IonSite<ORDER> is;
       ion_site<ORDER>(id, pc, is);
+      if (SMEM && !box.in(is.fx, is.fz0)) return false;
       ion_jz<T, ORDER, SMEM>(Jb, cs, ld, ox, oz, is, pc.kz_f * (-w));
       bx0 = min(bx0, is.fx); bx1 = max(bx1, is.fx);
       bz0 = min(bz0, is.fz1); bz1 = max(bz1, is.fz1);
-      return;
+      return true;
     }
   }
   int fx, fz, fxh, fzh;
@@ -269,18 +320,29 @@ __device__ __forceinline__ void push_one(const T* __restrict__ Eb, const T* __re
   double x = 0.0, z = 0.0, X = 0.0, Z = 0.0;
   uint32_t cs0 = 0;   // mixed path: stored cell and z offset (drifting frame)
   float ozs = 0.0f;
+  // the lab-fixed ion of the particle's lattice site (mixed path, electron-ion pairs)
+  bool ion_live = false;
+  IonSite<ORDER> is{};
   if constexpr (CP) {
     cs0 = p.cell[pi];
     ozs = p.oz[pi];
     fx = cell_x(cs0);
     frame_z(cs0, ozs, pc.fr0_sz, pc.fr0_fz, fz, tz);
+    if (pc.pairs) {
+      const uint32_t id = p.id[pi];
+      ion_live = site_row(id, pc) >= pc.mlo;
+      if (ion_live) ion_site<ORDER>(id, pc, is);
+    }
+    if (SMEM && (!box.in(fx, fz) || (ion_live && !box.in(is.fx, is.fz0)))) return false;
     tx = p.ox[pi];
     fxh = tx >= T(0.5) ? fx : fx - 1; txh = tx >= T(0.5) ? tx - T(0.5) : tx + T(0.5);
     fzh = tz >= T(0.5) ? fz : fz - 1; tzh = tz >= T(0.5) ? tz - T(0.5) : tz + T(0.5);
   } else {
     x = p.x[pi]; z = p.z[pi];
     X = x / pc.dx; Z = (z - pc.z0) / pc.dz;
+    if (SMEM && (!(X == X) || !(Z == Z) || fabs(X) > 1e9 || fabs(Z) > 1e9)) return false;
     fx = (int)floor(X); fz = (int)floor(Z);
+    if (SMEM && !box.in(fx, fz)) return false;
     tx = T(X - fx); tz = T(Z - fz);
     const double Xh = X - 0.5, Zh = Z - 0.5;
     fxh = (int)floor(Xh); fzh = (int)floor(Zh);
@@ -290,6 +352,7 @@ __device__ __forceinline__ void push_one(const T* __restrict__ Eb, const T* __re
   T wxi[NG], wzi[NG], wxh[NG], wzh[NG];
   wts<T, ORDER>(tx, wxi); wts<T, ORDER>(tz, wzi);
   T Ex, Ey, Ez, Bx, By, Bz;
+  constexpr int goff = ORDER == 3 ? 1 : 0;
   if constexpr (MC) {
     // 'momentum conserving' gather (Sec. 5): every gather copy already holds node values
     if constexpr (SMEM) {
@@ -309,7 +372,15 @@ __device__ __forceinline__ void push_one(const T* __restrict__ Eb, const T* __re
   } else {
   wts<T, ORDER>(txh, wxh); wts<T, ORDER>(tzh, wzh);
   // energy-conserving gather from each component's Yee location
-  if constexpr (SMEM) {
+  if constexpr (SMEM && CP) {
+    const float2* V = reinterpret_cast<const float2*>(Eb);
+    const int bxh = (fxh - goff - ox) * ld, bxi = (fx - goff - ox) * ld;
+    const int bzi = fz - goff - oz, bzh = fzh - goff - oz;
+    const float2 exbz = interp_pair_f<ORDER>(V, bxh + bzi, ld, wxh, wzi);
+    const float2 ezbx = interp_pair_f<ORDER>(V + cs, bxi + bzh, ld, wxi, wzh);
+    const float2 eyby = interp_two_f<ORDER>(Eb + 4 * cs, bxi + bzi, Eb + 5 * cs, bxh + bzh, ld, wxi, wzi, wxh, wzh);
+    Ex = exbz.x; Bz = exbz.y; Ez = ezbx.x; Bx = ezbx.y; Ey = eyby.x; By = eyby.y;
+  } else if constexpr (SMEM) {
     typedef typename Vec2<T>::type V2;
     interp2<T, ORDER>(reinterpret_cast<const V2*>(Eb), ld, ox, oz, fxh, fz, wxh, wzi, Ex, Bz);
     interp2<T, ORDER>(reinterpret_cast<const V2*>(Eb + 2 * cs), ld, ox, oz, fx, fzh, wxi, wzh, Ez, Bx);
@@ -400,17 +471,6 @@ __device__ __forceinline__ void push_one(const T* __restrict__ Eb, const T* __re
   // Esirkepov deposition on an ND x ND window
   const int off = ORDER == 3 ? 1 : 0;
   const int bx = min(fx, fxn) - off, bz = min(fz, fzn) - off;
-  T S0x[ND], S1x[ND], S0z[ND], S1z[ND];
-  {
-    T w0[NG], w1[NG];
-    place<T, ORDER>(wxi, fx - off - bx, S0x);
-    wts<T, ORDER>(txn, w1); place<T, ORDER>(w1, fxn - off - bx, S1x);
-    place<T, ORDER>(wzi, fz - off - bz, S0z);
-    wts<T, ORDER>(tzn, w0); place<T, ORDER>(w0, fzn - off - bz, S1z);
-  }
-  T DSx[ND], DSz[ND];
-#pragma unroll
-  for (int a = 0; a < ND; a++) { DSx[a] = S1x[a] - S0x[a]; DSz[a] = S1z[a] - S0z[a]; }
   T cx, cz, cy;
   if constexpr (CP) {
     cx = pc.kx_f * w; cz = pc.kz_f * w; cy = pc.ky_f * w * vy;
@@ -421,48 +481,63 @@ __device__ __forceinline__ void push_one(const T* __restrict__ Eb, const T* __re
   // pair is exactly zero when electron and ion made the same move (the cold
   // streaming plasma); otherwise combined on a common window, or separate
   int jz = 1;
-  bool ion_live = false, ion_sep = false;
-  IonSite<ORDER> is;
-  T Sxi[ND], DSzi[ND];
+  bool ion_sep = false;
   if constexpr (CP) {
-    if (pc.pairs) {
-      const uint32_t id = p.id[pi];
-      ion_live = site_row(id, pc) >= pc.mlo;
-      if (ion_live) {
-        ion_site<ORDER>(id, pc, is);
-        if (cs0 == is.cell && ozs == is.oz && tx == is.ox && csn == is.cell && ozn == is.oz && txn == is.ox) {
-          jz = 0;
-        } else if (is.fx - off == bx && min(is.fz0, is.fz1) - off == bz) {
-          jz = 2;
-          T wxi2[NG], w0i[NG], w1i[NG], S0zi[ND], S1zi[ND];
-          wts<T, ORDER>(T(is.ox), wxi2);
-          wts<T, ORDER>(T(is.tz0), w0i);
-          wts<T, ORDER>(T(is.tz1), w1i);
-          place<T, ORDER>(wxi2, 0, Sxi);
-          place<T, ORDER>(w0i, is.fz0 - off - bz, S0zi);
-          place<T, ORDER>(w1i, is.fz1 - off - bz, S1zi);
-#pragma unroll
-          for (int b = 0; b < ND; b++) DSzi[b] = S1zi[b] - S0zi[b];
-        } else {
-          ion_sep = true;
-        }
-      }
+    if (ion_live) {
+      if (cs0 == is.cell && ozs == is.oz && tx == is.ox && csn == is.cell && ozn == is.oz && txn == is.ox)
+        jz = 0;
+      else if (is.fx - off == bx && min(is.fz0, is.fz1) - off == bz)
+        jz = 2;
+      else
+        ion_sep = true;
     }
   }
-  T* Jx = Jb + (long)(bx - ox) * ld + (bz - oz);
-  if constexpr (SMEM) {
-    // when no lane of the warp changes x-cell, column ND-1 of the x window is
-    // empty: the warp deposits on ND-1 columns
-    const bool xcross = fxn != fx;
-    if (__any_sync(__activemask(), xcross))
-      deposit<T, ND, ND, true>(Jx, cs, ld, S0x, DSx, S0z, DSz, cx, cy, cz, jz, Sxi, DSzi);
-    else
-      deposit<T, ND, ND - 1, true>(Jx, cs, ld, S0x, DSx, S0z, DSz, cx, cy, cz, jz, Sxi, DSzi);
-  } else {
-    deposit<T, ND, ND, false>(Jx, cs, ld, S0x, DSx, S0z, DSz, cx, cy, cz, jz, Sxi, DSzi);
-  }
-  if constexpr (CP) {
-    if (ion_sep) ion_jz<T, ORDER, SMEM>(Jb, cs, ld, ox, oz, is, cz);
+  // no current at all: the x weights are unchanged (J_x = 0), no out-of-plane
+  // velocity (J_y = 0) and J_z cancels within the pair; a warp whose lanes all
+  // carry no current skips the weights and the deposit
+  bool dep = !(jz == 0 && fxn == fx && txn == tx && cy == T(0));
+  if constexpr (SMEM) dep = __any_sync(__activemask(), dep);
+  if (dep) {
+    T S0x[ND], S1x[ND], S0z[ND], S1z[ND];
+    {
+      T w0[NG], w1[NG];
+      place<T, ORDER>(wxi, fx - off - bx, S0x);
+      wts<T, ORDER>(txn, w1); place<T, ORDER>(w1, fxn - off - bx, S1x);
+      place<T, ORDER>(wzi, fz - off - bz, S0z);
+      wts<T, ORDER>(tzn, w0); place<T, ORDER>(w0, fzn - off - bz, S1z);
+    }
+    T DSx[ND], DSz[ND];
+#pragma unroll
+    for (int a = 0; a < ND; a++) { DSx[a] = S1x[a] - S0x[a]; DSz[a] = S1z[a] - S0z[a]; }
+    T Sxi[ND], DSzi[ND];
+    if constexpr (CP) {
+      if (jz == 2) {
+        T wxi2[NG], w0i[NG], w1i[NG], S0zi[ND], S1zi[ND];
+        wts<T, ORDER>(T(is.ox), wxi2);
+        wts<T, ORDER>(T(is.tz0), w0i);
+        wts<T, ORDER>(T(is.tz1), w1i);
+        place<T, ORDER>(wxi2, 0, Sxi);
+        place<T, ORDER>(w0i, is.fz0 - off - bz, S0zi);
+        place<T, ORDER>(w1i, is.fz1 - off - bz, S1zi);
+#pragma unroll
+        for (int b = 0; b < ND; b++) DSzi[b] = S1zi[b] - S0zi[b];
+      }
+    }
+    T* Jx = Jb + (long)(bx - ox) * ld + (bz - oz);
+    if constexpr (SMEM) {
+      // when no lane of the warp changes x-cell, column ND-1 of the x window is
+      // empty: the warp deposits on ND-1 columns
+      const bool xcross = fxn != fx;
+      if (__any_sync(__activemask(), xcross))
+        deposit<T, ND, ND, true>(Jx, cs, ld, S0x, DSx, S0z, DSz, cx, cy, cz, jz, Sxi, DSzi);
+      else
+        deposit<T, ND, ND - 1, true>(Jx, cs, ld, S0x, DSx, S0z, DSz, cx, cy, cz, jz, Sxi, DSzi);
+    } else {
+      deposit<T, ND, ND, false>(Jx, cs, ld, S0x, DSx, S0z, DSz, cx, cy, cz, jz, Sxi, DSzi);
+    }
+    if constexpr (CP) {
+      if (ion_sep) ion_jz<T, ORDER, SMEM>(Jb, cs, ld, ox, oz, is, cz);
+    }
   }
   bool gone;
   if constexpr (CP) {
@@ -483,7 +558,15 @@ __device__ __forceinline__ void push_one(const T* __restrict__ Eb, const T* __re
   } else {
     bx0 = min(bx0, fxn); bx1 = max(bx1, fxn);
     bz0 = min(bz0, fzn); bz1 = max(bz1, fzn);
+    if constexpr (CP) {
+      // the pair's ion deposits with it next step: its cell belongs in the chunk's box too
+      if (ion_live) {
+        bx0 = min(bx0, is.fx); bx1 = max(bx1, is.fx);
+        bz0 = min(bz0, is.fz1); bz1 = max(bz1, is.fz1);
+      }
+    }
   }
+  return true;
 }
 
 // current cell of a particle (grid-relative); false for a non-finite position
@@ -521,12 +604,14 @@ __device__ __noinline__ void push_global_guarded(const T* gE, const T* gB, T* gJ
     atomicOr(&ctrl->status, fin ? ST_OUTSIDE : ST_NAN);
     return;
   }
-  push_one<T, ORDER, false, MC>(gE, gB, gJ, g.cs, g.ld, 0, 0, p, pi, pc, bx0, bx1, bz0, bz1);
+  const Box none{0, -1, 0, -1};
+  push_one<T, ORDER, false, MC>(gE, gB, gJ, g.cs, g.ld, 0, 0, p, pi, pc, none, bx0, bx1, bz0, bz1);
 }
 
 template <class T, int ORDER, bool MC>
 __global__ void __launch_bounds__(PB_THREADS, 5) k_push(GridP g, const T* gE, const T* gB, T* gJ, Particles<T> p,
-                                                     Chunk* chunks, Ctrl* ctrl, int cap_nodes, PushConst pc) {
+                                                     Chunk* chunks, Ctrl* ctrl, int cap_nodes, int tile_z,
+                                                     PushConst pc) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);
   typedef typename Vec2<T>::type V2;
@@ -544,6 +629,7 @@ __global__ void __launch_bounds__(PB_THREADS, 5) k_push(GridP g, const T* gE, co
     const int c = s_chunk;
     if (c >= nchunks) break;
     const Chunk ch = chunks[c];
+    const Box box{ch.ix0, ch.ix1, ch.iz0, ch.iz1};
     if (ch.ix0 > ch.ix1 || ch.p1 <= ch.p0) {   // empty chunk
       __syncthreads();
       continue;
@@ -551,7 +637,14 @@ __global__ void __launch_bounds__(PB_THREADS, 5) k_push(GridP g, const T* gE, co
     const int wx0 = ch.ix0 - St<ORDER>::LO, wx1 = ch.ix1 + St<ORDER>::HI;
     const int wz0 = ch.iz0 - St<ORDER>::LO, wz1 = ch.iz1 + St<ORDER>::HI;
     const int wxn = wx1 - wx0 + 1, wzn = wz1 - wz0 + 1;
-    const int lds = wzn;
+    // A warp of a dense tile holds one particle in each of 32 consecutive cells: 32 / tile_z x-columns of
+    // tile_z z-cells each. With the window's row stride congruent to tile_z modulo 32 banks, the columns'
+    // 32-bit loads and atomics fall in disjoint banks; padded when the window still fits, else unpadded.
+    int lds = wzn;
+    if (tile_z < 32) {
+      const int pad = wzn + ((tile_z - wzn) % 32 + 32) % 32;
+      if (wxn * pad <= cap_nodes) lds = pad;
+    }
     const int nn = wxn * lds;
     const bool use_smem = nn <= cap_nodes && wx0 >= 0 && wz0 >= 0 && wx1 <= g.nx && wz1 <= g.nz;
     int bx0 = INT_MAX, bx1 = INT_MIN, bz0 = INT_MAX, bz1 = INT_MIN;
@@ -590,25 +683,10 @@ __global__ void __launch_bounds__(PB_THREADS, 5) k_push(GridP g, const T* gE, co
           asm volatile("prefetch.global.L1 [%0];" ::"l"(p.uz + pn));
           asm volatile("prefetch.global.L1 [%0];" ::"l"(p.w + pn));
         }
-        // a particle outside the chunk's box (should not happen) takes the global path
-        int fx = 0, fz = 0;
-        const bool fin = particle_cell<T>(p, pi, pc, fx, fz);
-        bool inbox = fin && fx >= ch.ix0 && fx <= ch.ix1 && fz >= ch.iz0 && fz <= ch.iz1;
-        if constexpr (CellPos<T>::value) {
-          // a live pair deposits its ion too: the ion's cell must be inside the box as well
-          if (inbox && pc.pairs && p.w[pi] > T(0) && site_row(p.id[pi], pc) >= pc.mlo) {
-            uint32_t c;
-            float sox, soz, tz;
-            int iz;
-            lattice_site_pow2(p.id[pi], pc.kb, pc.lpx, pc.lpz, pc.gx_lo, pc.z0_cells, c, sox, soz);
-            frame_z(c, soz, pc.fr0_sz, pc.fr0_fz, iz, tz);
-            inbox = cell_x(c) >= ch.ix0 && cell_x(c) <= ch.ix1 && iz >= ch.iz0 && iz <= ch.iz1;
-          }
-        }
-        if (inbox)
-          push_one<T, ORDER, true, MC>(sm, nullptr, sm + 6 * cap_nodes, cap_nodes, lds, wx0, wz0, p, pi, pc, bx0,
-                                       bx1, bz0, bz1);
-        else
+        // a particle outside the chunk's box (should not happen; with electron-ion pairs, the ion's cell
+        // counts too) takes the global path
+        if (!push_one<T, ORDER, true, MC>(sm, nullptr, sm + 6 * cap_nodes, cap_nodes, lds, wx0, wz0, p, pi, pc, box,
+                                          bx0, bx1, bz0, bz1))
           push_global_guarded<T, ORDER, MC>(gE, gB, gJ, g, p, pi, pc, ctrl, bx0, bx1, bz0, bz1);
       }
       __syncthreads();
@@ -899,8 +977,8 @@ __global__ void k_add_counts(Ctrl* ctrl, int dcount, int dchunks) {
 
 template <class T>
 void launch_push(const GridP& g, const FieldPtrs<T>& f, Particles<T> p, Chunk* chunks, Ctrl* ctrl, int order,
-                 int grid_blocks, int smem_nodes, double q, double m, double gamma_b, double beta_b, int fr1_sz,
-                 float fr1_fz, int pairs, int mlo, int nodal, cudaStream_t s) {
+                 int grid_blocks, int smem_nodes, int tile_z, double q, double m, double gamma_b, double beta_b,
+                 int fr1_sz, float fr1_fz, int pairs, int mlo, int nodal, cudaStream_t s) {
   PushConst pc;
   pc.dx = g.dx; pc.dz = g.dz; pc.dt = g.dt; pc.z0 = g.z0;
   pc.xlo = g.gx_lo * g.dx; pc.xhi = g.gx_hi * g.dx;
@@ -927,16 +1005,16 @@ void launch_push(const GridP& g, const FieldPtrs<T>& f, Particles<T> p, Chunk* c
   const T* gB = nodal ? f.nB[0] : f.fB[0];
   if (order == 3 && !nodal) {
     cudaFuncSetAttribute(k_push<T, 3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_push<T, 3, false><<<grid_blocks, PB_THREADS, sm, s>>>(g, gE, gB, f.J[0], p, chunks, ctrl, smem_nodes, pc);
+    k_push<T, 3, false><<<grid_blocks, PB_THREADS, sm, s>>>(g, gE, gB, f.J[0], p, chunks, ctrl, smem_nodes, tile_z, pc);
   } else if (order == 3) {
     cudaFuncSetAttribute(k_push<T, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_push<T, 3, true><<<grid_blocks, PB_THREADS, sm, s>>>(g, gE, gB, f.J[0], p, chunks, ctrl, smem_nodes, pc);
+    k_push<T, 3, true><<<grid_blocks, PB_THREADS, sm, s>>>(g, gE, gB, f.J[0], p, chunks, ctrl, smem_nodes, tile_z, pc);
   } else if (!nodal) {
     cudaFuncSetAttribute(k_push<T, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_push<T, 1, false><<<grid_blocks, PB_THREADS, sm, s>>>(g, gE, gB, f.J[0], p, chunks, ctrl, smem_nodes, pc);
+    k_push<T, 1, false><<<grid_blocks, PB_THREADS, sm, s>>>(g, gE, gB, f.J[0], p, chunks, ctrl, smem_nodes, tile_z, pc);
   } else {
     cudaFuncSetAttribute(k_push<T, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_push<T, 1, true><<<grid_blocks, PB_THREADS, sm, s>>>(g, gE, gB, f.J[0], p, chunks, ctrl, smem_nodes, pc);
+    k_push<T, 1, true><<<grid_blocks, PB_THREADS, sm, s>>>(g, gE, gB, f.J[0], p, chunks, ctrl, smem_nodes, tile_z, pc);
   }
 }
 
@@ -1006,7 +1084,7 @@ void launch_add_counts(Ctrl* ctrl, int dcount, int dchunks, cudaStream_t s) {
 
 #define INST(T)                                                                                                 \
   template void launch_push<T>(const GridP&, const FieldPtrs<T>&, Particles<T>, Chunk*, Ctrl*, int, int, int,   \
-                               double, double, double, double, int, float, int, int, int, cudaStream_t);        \
+                               int, double, double, double, double, int, float, int, int, int, cudaStream_t);   \
   template void launch_sort<T>(const GridP&, Particles<T>, Particles<T>, SortBufs, Chunk*, Ctrl*, int, int, int,\
                                cudaStream_t);                                                                   \
   template void launch_inject<T>(const GridP&, Particles<T>, Chunk*, Ctrl*, const InjectP&, int, int, cudaStream_t);

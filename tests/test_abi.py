@@ -11,7 +11,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def declared_functions():
     src = open(os.path.join(ROOT, "include", "pic.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(pic_[a-z_]+)\s*\(", src)) - {"pic_alloc_fn", "pic_free_fn"})
+    return sorted(set(re.findall(r"\b(pic_[a-z0-9_]+)\s*\(", src)) - {"pic_alloc_fn", "pic_free_fn"})
 
 
 def test_library_exports_every_declared_symbol():
