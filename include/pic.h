@@ -256,6 +256,23 @@ int pic_get_stats(pic_ctx* ctx, pic_stats* out);
 int pic_get_particles_y(pic_ctx* ctx, int species, double* y, int64_t* count);
 const char* pic_last_error(pic_ctx* ctx);
 
+/* Self-field of the frozen test beam, solved on the device and added to the
+ * fields (Sec. 3.1.1: the fields at the injection plane must be consistent with
+ * the beam, whose charge the frozen and the active particles deposit; reading
+ * PR-27). The frozen particles inside the particle domain are a charge moving
+ * rigidly at the beam's mean velocity v along z: the potential solves
+ * d2phi/dx2 + d2phi/dz2 / gamma_v^2 = -rho/eps0 with phi = 0 on the PEC walls,
+ * in the Yee mesh's second differences (so that the discrete Gauss law holds
+ * exactly), by sine transforms (DST-I) along both axes; E_x = -dphi/dx and
+ * E_z = -dphi/dz / gamma_v^2 are added to E at the current time, B_y = v E_x / c^2
+ * from the positions half a step earlier to B (B^{n-1/2}). Call it once, after
+ * pic_load_plasma and before the first pic_step, for a beam loaded with
+ * pic_plasma.beam_self = 1. 2D contexts only (PIC_EINVAL otherwise);
+ * PIC_ESTATE without a self-consistent beam. Scratch of two grid-sized FP64
+ * arrays comes from the allocator callback and is released before it returns;
+ * the call synchronises the context's stream. */
+int pic_beam_self_field(pic_ctx* ctx);
+
 /* Largest nz accepted by pic_get_rho_noalloc (size of its static scratch). */
 #define PIC_NOALLOC_MAX_NZ 16384
 

@@ -33,7 +33,7 @@ EXPORTS = ("pic_init", "pic_load_plasma", "pic_inject_laser", "pic_step", "pic_s
            "pic_ensemble_member", "pic_ensemble_free", "pic_ensemble_autotune",
            "pic_mlp_create", "pic_mlp_free", "pic_mlp_param_count", "pic_mlp_get_params", "pic_mlp_set_params",
            "pic_mlp_infer", "pic_mlp_grad", "pic_mlp_train", "pic_mlp_use_tensor_cores", "pic_mlp_status",
-           "pic_measure_fp32_peak")
+           "pic_measure_fp32_peak", "pic_beam_self_field")
 NOALLOC_MAX_NZ = 16384
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -196,5 +196,6 @@ def load(build_if_missing: bool = True):
         L.pic_autotune.argtypes = [ctypes.POINTER(PicConfig), ctypes.POINTER(PicPlasma), ctypes.POINTER(PicLaser),
                                    ctypes.c_int, ALLOC_FN, FREE_FN, vp, vp, ctypes.POINTER(PicTuneResult)]
         L.pic_measure_fp32_peak.argtypes = [_D, _D]
+        L.pic_beam_self_field.argtypes = [vp]
         _lib = L
         return L

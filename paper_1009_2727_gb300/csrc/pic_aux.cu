@@ -594,6 +594,122 @@ int launch_rho_noalloc(const GridP& g, Particles<T> p, const Ctrl* ctrl, int cap
   return 0;
 }
 
+// ---------------------------------------------------------------------------
+// Self-field of the frozen test beam (Sec. 3.1.1: the fields at the injection plane must be consistent with
+// the beam). The frozen charge moves rigidly at the beam's mean velocity v along z, so in the computational
+// frame the potential solves d2phi/dx2 + d2phi/dz2 / gamma_v^2 = -rho/eps0 with phi = 0 on the grid edges
+// (the PEC walls), discretised with the Yee mesh's second differences; E_x = -dphi/dx, E_z = -dphi/dz /
+// gamma_v^2 at their half positions and B_y = v E_x / c^2 (PR-27). The sine transform (DST-I) diagonalises
+// the discrete operator: phi_hat(m, q) = -rho_hat(m, q) / (eps0 (lx(m) + lz(q) / gamma_v^2)) with
+// lx(m) = -(2 - 2 cos(pi m / nx)) / dx^2, lz likewise. The transforms are direct sums over a sine table,
+// FP64 throughout (a one-time set-up: O(nx nz (nx + nz)) multiply-adds).
+
+// charge density (nx+1) x (nz+1) of the frozen beam particles inside the particle domain, their positions
+// taken `shift` seconds from now (frozen particles move at v)
+template <class T>
+__global__ void k_beam_rho(GridP g, Beam<T> b, int order, double shift, const double* acc, double* rho) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= b.n) return;
+  if ((b.flag[j] & 3) != 1) return;   // alive and frozen only
+  const double v = acc[2];
+  const double x = b.x[j], z = b.z[j] + v * shift;
+  const double xlo = g.gx_lo * g.dx, xhi = g.gx_hi * g.dx;
+  const double zlo = g.z0 + g.gz_lo * g.dz, zhi = g.z0 + (g.gz_hi + 1) * g.dz;
+  if (!(x >= xlo && x < xhi && z >= zlo && z < zhi)) return;
+  const double qw = -kQe * (double)b.w[j];
+  const double X = x / g.dx, Z = (z - g.z0) / g.dz;
+  const int fx = (int)floor(X), fz = (int)floor(Z);
+  for (int i = fx - 2; i <= fx + 3; i++)
+    for (int k = fz - 2; k <= fz + 3; k++) {
+      const double sv = shape_val(order, X - i) * shape_val(order, Z - k);
+      if (sv != 0.0 && i >= 0 && i <= g.nx && k >= 0 && k <= g.nz)
+        atomicAdd(&rho[(long)i * (g.nz + 1) + k], qw * sv / (g.dx * g.dz));
+    }
+}
+
+// out(o, m) = 2 sum_{j=1}^{N-1} in(o, j) sin(pi j m / N) for m = 1..N-1 and rows o = 1..n_outer-1, the
+// transform index running with stride si, the rows with stride so; tab[t] = sin(pi t / N), t < 2N. One
+// thread per (o, m); the table index j m mod 2N advances by m per term.
+__global__ void k_dst1(const double* in, double* out, const double* tab, int N, int n_outer, long so, long si) {
+  const long id = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long n_m = N - 1, n_o = n_outer - 1;
+  if (id >= n_m * n_o) return;
+  long o, m;
+  if (si == 1) { o = 1 + id / n_m; m = 1 + id % n_m; }     // transform along the fast axis: threads over m
+  else { m = 1 + id / n_o; o = 1 + id % n_o; }             // along the slow axis: threads over the rows
+  const double* src = in + o * so;
+  const int twoN = 2 * N;
+  int t = 0;
+  double acc = 0.0;
+  for (int jj = 1; jj < N; jj++) {
+    t += (int)m;
+    if (t >= twoN) t -= twoN;
+    acc += src[(long)jj * si] * tab[t];
+  }
+  out[o * so + m * si] = 2.0 * acc;
+}
+
+__global__ void k_poisson_divide(double* a, int nx, int nz, double dx, double dz, double gv2) {
+  const long id = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= (long)(nx - 1) * (nz - 1)) return;
+  const int m = 1 + (int)(id / (nz - 1)), q = 1 + (int)(id % (nz - 1));
+  const double lx = -(2.0 - 2.0 * cospi((double)m / nx)) / (dx * dx);
+  const double lz = -(2.0 - 2.0 * cospi((double)q / nz)) / (dz * dz);
+  // the inverse DST-I of each axis is the forward one over 2N
+  const long p = (long)m * (nz + 1) + q;
+  a[p] = -a[p] / kEps0 / (lx + lz / gv2) / (4.0 * nx * nz);
+}
+
+// E_x, E_z from phi (mode 0) or B_y from phi (mode 1) added to the context's fields
+template <class T>
+__global__ void k_self_field_add(GridP g, FieldPtrs<T> f, const double* phi, double gv2, const double* acc, int mode) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x, i = blockIdx.y;
+  if (k > g.nz) return;
+  const int L = g.nz + 1;
+  const long q = (long)i * g.ld + k;
+  const double* P = phi + (long)i * L;
+  if (mode == 0) {
+    if (i < g.nx) f.E[0][q] += T(-(P[L + k] - P[k]) / g.dx);
+    if (k < g.nz) f.E[2][q] += T(-(P[k + 1] - P[k]) / g.dz / gv2);
+  } else if (i < g.nx && k < g.nz) {
+    const double ex0 = -(P[L + k] - P[k]) / g.dx, ex1 = -(P[L + k + 1] - P[k + 1]) / g.dx;
+    f.B[1][q] += T(acc[2] / (kC * kC) * 0.5 * (ex0 + ex1));
+  }
+}
+
+// phi is zero on the grid's edges (the transforms leave the deposited density there)
+__global__ void k_zero_edges(double* a, int nx, int nz) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int L = nz + 1;
+  if (t <= nz) { a[t] = 0.0; a[(long)nx * L + t] = 0.0; }
+  if (t <= nx) { a[(long)t * L] = 0.0; a[(long)t * L + nz] = 0.0; }
+}
+
+template <class T>
+void launch_beam_self_field(const GridP& g, const FieldPtrs<T>& f, Beam<T> b, int order, const double* acc,
+                            double gv2, double* rho, double* tmp, double* tabx, double* tabz, cudaStream_t s) {
+  const size_t n = (size_t)(g.nx + 1) * (g.nz + 1);
+  const int L = g.nz + 1;
+  for (int mode = 0; mode < 2; mode++) {
+    // E from the positions now, B_y half a step earlier (B^{n-1/2})
+    cudaMemsetAsync(rho, 0, n * sizeof(double), s);
+    cudaMemsetAsync(tmp, 0, n * sizeof(double), s);
+    if (b.n > 0) k_beam_rho<T><<<(b.n + 255) / 256, 256, 0, s>>>(g, b, order, mode == 0 ? 0.0 : -0.5 * g.dt, acc, rho);
+    const long nz_work = (long)(g.nx - 1) * (g.nz - 1);
+    const unsigned blocks = (unsigned)((nz_work + 255) / 256);
+    // forward: along z (rows i), then along x (columns k)
+    k_dst1<<<blocks, 256, 0, s>>>(rho, tmp, tabz, g.nz, g.nx, L, 1);
+    k_dst1<<<blocks, 256, 0, s>>>(tmp, rho, tabx, g.nx, g.nz, 1, L);
+    k_poisson_divide<<<blocks, 256, 0, s>>>(rho, g.nx, g.nz, g.dx, g.dz, gv2);
+    // inverse (the same transforms; the 1/(4 nx nz) is in the division)
+    k_dst1<<<blocks, 256, 0, s>>>(rho, tmp, tabz, g.nz, g.nx, L, 1);
+    k_dst1<<<blocks, 256, 0, s>>>(tmp, rho, tabx, g.nx, g.nz, 1, L);
+    k_zero_edges<<<(max(g.nx, g.nz) + 1 + 255) / 256, 256, 0, s>>>(rho, g.nx, g.nz);
+    dim3 grd((g.nz + 1 + 255) / 256, g.nx + 1);
+    k_self_field_add<T><<<grd, 256, 0, s>>>(g, f, rho, gv2, acc, mode);
+  }
+}
+
 void launch_ion_column(const GridP& g, long long mlo, long long mhi, double t0, double t1, const InjectP& ip,
                        int order, double* C, cudaStream_t s) {
   cudaMemsetAsync(C, 0, sizeof(double) * (size_t)(g.nz + 1), s);
@@ -728,6 +844,8 @@ void launch_shift_particles(const GridP& g, Particles<T> p, const Ctrl* ctrl, in
   template void launch_antenna<T>(const GridP&, T*, const double*, const AntennaStep&, cudaStream_t);           \
   template void launch_beam_init<T>(Beam<T>, const double*, const double*, const double*, const double*,          \
                                     const double*, double, double, double, double, double, double*, cudaStream_t); \
+  template void launch_beam_self_field<T>(const GridP&, const FieldPtrs<T>&, Beam<T>, int, const double*, double, \
+                                          double*, double*, double*, double*, cudaStream_t);                    \
   template void launch_beam_push<T>(const GridP&, const FieldPtrs<T>&, Beam<T>, int, double, double, int,         \
                                     const double*, cudaStream_t);                                                 \
   template void launch_nodal<T>(const GridP&, const FieldPtrs<T>&, cudaStream_t);                                 \

@@ -116,6 +116,7 @@ struct Sim : SimBase {
   // particles
   Particles<T> P{}, P2{};
   Chunk* chunks = nullptr;
+  PushDefer pdef{};          // the push's lists for its global-memory pass
   int cap = 0, chunk_cap = 0, chunk_max = 4096, smem_nodes = 0, push_grid = 0;
   SortBufs sb{};
   int sort_every = 8;
@@ -362,6 +363,11 @@ struct Sim : SimBase {
     chunk_cap = (int)std::max((long long)(2 * ntiles + cap / chunk_max), init_chunks) + inj_chunks * (sort_every + 4) +
                 4096;
     chunks = al<Chunk>(chunk_cap);
+    pdef.ovf_cap = chunk_cap;
+    pdef.defer_cap = std::max(cap / 16, 65536);
+    pdef.ovf = al<int>(pdef.ovf_cap);
+    pdef.defer = al<int2>(pdef.defer_cap);
+    if (!pdef.ovf || !pdef.defer) return c->fail(PIC_ENOMEM, "push list allocation failed");
     if (ntiles > 1024 * 1024) return c->fail(PIC_EINVAL, "too many particle tiles; enlarge tile_x/tile_z");
     const size_t ncells = (size_t)ntiles * sb.tx * sb.tz;
     sb.cell_cnt = al<int>(ncells);
@@ -615,9 +621,9 @@ struct Sim : SimBase {
       frame_of(frame_shift(step + 1), fr1_sz, fr1_fz);
       launch_push<T>(g, f, P, chunks, ctrl, cf.shape_order, push_grid, smem_nodes, sb.tz, -kQe, kMe, c->hg.gamma,
                      c->hg.beta,
-                     fr1_sz, fr1_fz, (pairs && ions) ? 1 : 0, (int)mlo, nodal ? 1 : 0, c->stream);
+                     fr1_sz, fr1_fz, (pairs && ions) ? 1 : 0, (int)mlo, nodal ? 1 : 0, pdef, c->stream);
       tstop(0);
-      c->launches++;
+      c->launches += 2;
     }
     set_frame(step + 1);   // the particles now hold their t^{n+1} positions
     if (beam.n > 0) {
@@ -768,6 +774,32 @@ struct Sim : SimBase {
     if (r == 3)
       return c->fail(PIC_ECUDA, std::string("pic_get_rho_noalloc: kernel launch failed: ") + cudaGetErrorString(why));
     return PIC_OK;
+  }
+
+  // the frozen beam's self-field (Sec. 3.1.1, PR-27), solved on the device and added to E and B_y
+  int beam_self_field() {
+    if (beam.n <= 0 || !beam.self) return c->fail(PIC_ESTATE, "pic_beam_self_field: no self-consistent test beam");
+    const pic_config& cf = c->cfg;
+    if (cf.nx < 2 || cf.nz < 2) return c->fail(PIC_EINVAL, "pic_beam_self_field: grid too small");
+    double* tmp = al<double>(stage_n);
+    double* tabx = al<double>(2 * (size_t)cf.nx);
+    double* tabz = al<double>(2 * (size_t)cf.nz);
+    if (!tmp || !tabx || !tabz) return c->fail(PIC_ENOMEM, "pic_beam_self_field: scratch allocation failed");
+    std::vector<double> tx(2 * (size_t)cf.nx), tz(2 * (size_t)cf.nz);
+    for (int t = 0; t < 2 * cf.nx; t++) tx[t] = std::sin(kPi * t / cf.nx);
+    for (int t = 0; t < 2 * cf.nz; t++) tz[t] = std::sin(kPi * t / cf.nz);
+    cudaMemcpyAsync(tabx, tx.data(), tx.size() * 8, cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(tabz, tz.data(), tz.size() * 8, cudaMemcpyHostToDevice, c->stream);
+    double v = 0.0;
+    cudaMemcpyAsync(&v, beam_scratch + 2, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    cudaStreamSynchronize(c->stream);
+    const double gv2 = 1.0 / (1.0 - (v / kC) * (v / kC));
+    set_ptrs_for_step();
+    launch_beam_self_field<T>(g, f, beam, cf.shape_order, beam_scratch, gv2, stage, tmp, tabx, tabz, c->stream);
+    c->launches += 18;
+    cudaStreamSynchronize(c->stream);
+    free_last(3);
+    return cudaGetLastError() == cudaSuccess ? PIC_OK : c->fail(PIC_ECUDA, "CUDA error in pic_beam_self_field");
   }
 
   int set_field(int comp, const double* src) {
@@ -1088,6 +1120,13 @@ int pic_get_rho_noalloc(pic_ctx* c, double* dst_device) {
   if (c->s3) return c->fail(PIC_EINVAL, "pic_get_rho_noalloc: 2D contexts only");
   if (c->cfg.nz > PIC_NOALLOC_MAX_NZ) return c->fail(PIC_EINVAL, "pic_get_rho_noalloc: nz exceeds PIC_NOALLOC_MAX_NZ");
   return DISPATCH(c, get_rho_noalloc(dst_device));
+}
+
+int pic_beam_self_field(pic_ctx* c) {
+  if (!c) return PIC_EINVAL;
+  if (c->status != PIC_OK) return c->status;
+  if (c->s3) return c->fail(PIC_EINVAL, "pic_beam_self_field: 2D contexts only");
+  return DISPATCH(c, beam_self_field());
 }
 
 int pic_set_field(pic_ctx* c, int comp, const double* src) {

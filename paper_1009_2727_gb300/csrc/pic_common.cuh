@@ -189,7 +189,9 @@ struct Ctrl {
   int next_chunk;     // work counter of the persistent particle kernel
   int status;
   int overflow_chunks;
-  int pad[3];
+  int n_defer;        // particles of this step's push left for the global-memory pass
+  int n_ovf;          // chunks of this step's push left for the global-memory pass (window too large)
+  int pad;
   double red[8];      // reduction scratch
 };
 
@@ -236,10 +238,18 @@ void launch_ampere(const GridP& g, const FieldPtrs<T>& f, const PmlTabs& pt, con
                    const double* ion_x, const double* ion_c, double ion_coef, const TileMaps& tm, Ctrl* ctrl,
                    cudaStream_t s);
 
+// The push runs in two launches: the shared-memory window kernel over every chunk, then a global-memory
+// pass over what it left (particles outside their chunk's box, chunks whose window exceeds the shared
+// memory), recorded in defer (particle, chunk) and ovf (chunk) lists of the given capacities.
+struct PushDefer {
+  int2* defer;
+  int* ovf;
+  int defer_cap, ovf_cap;
+};
 template <class T>
 void launch_push(const GridP& g, const FieldPtrs<T>& f, Particles<T> p, Chunk* chunks, Ctrl* ctrl, int order,
                  int grid_blocks, int smem_nodes, int tile_z, double q, double m, double gamma_b, double beta_b,
-                 int fr1_sz, float fr1_fz, int pairs, int mlo, int nodal, cudaStream_t s);
+                 int fr1_sz, float fr1_fz, int pairs, int mlo, int nodal, const PushDefer& pd, cudaStream_t s);
 
 struct SortBufs {
   int* cell_cnt;       // ntiles*tx*tz, cells in tile-major order: particles per cell
@@ -305,6 +315,11 @@ void launch_beam_init(Beam<T> b, const double* lx, const double* lz, const doubl
 template <class T>
 void launch_beam_push(const GridP& g, const FieldPtrs<T>& f, Beam<T> b, int order, double tn, double tn1, int nodal,
                       const double* scratch, cudaStream_t s);
+// the frozen beam's self-field (Sec. 3.1.1) added to E (now) and B_y (half a step earlier); acc[2] is the
+// beam's mean velocity; rho, tmp: (nx+1)(nz+1) doubles of scratch; tabx, tabz: sin(pi t / N) for t < 2N
+template <class T>
+void launch_beam_self_field(const GridP& g, const FieldPtrs<T>& f, Beam<T> b, int order, const double* acc,
+                            double gv2, double* rho, double* tmp, double* tabx, double* tabz, cudaStream_t s);
 // 'momentum conserving' gather (Sec. 5): f.nE / f.nB = the gather copies interpolated to the nodes
 template <class T>
 void launch_nodal(const GridP& g, const FieldPtrs<T>& f, cudaStream_t s);

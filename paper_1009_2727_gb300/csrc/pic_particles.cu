@@ -161,36 +161,19 @@ __device__ __forceinline__ void deposit(T* Jx, long cs, int ld, const T* S0x, co
   typedef typename std::conditional<SMEM, int, long>::type Idx;
   T* Jy = Jx + cs;
   T* Jz = Jx + 2 * cs;
-  T Px[NDX - 1], Pz[ND - 1], Pzi[ND - 1];
+  // J_x, then J_y, then J_z: each axis's running sums are formed where they are used
   {
-    T ax = T(0), az = T(0), ai = T(0);
+    T Px[NDX - 1];
+    T ax = T(0);
 #pragma unroll
     for (int a = 0; a < NDX - 1; a++) { ax += cx * DSx[a]; Px[a] = ax; }
 #pragma unroll
-    for (int b = 0; b < ND - 1; b++) {
-      az += cz * DSz[b]; Pz[b] = az;
-      if (JZ == 2) { ai += cz * DSzi[b]; Pzi[b] = ai; }
-    }
-  }
+    for (int b = 0; b < ND; b++) {
+      const T fzb = S0z[b] + T(0.5) * DSz[b];
 #pragma unroll
-  for (int b = 0; b < ND; b++) {
-    const T fzb = S0z[b] + T(0.5) * DSz[b];
-#pragma unroll
-    for (int a = 0; a < NDX - 1; a++) {
-      const T v = Px[a] * fzb;
-      if (v != T(0)) atomicAdd(Jx + (Idx)a * ld + b, v);
-    }
-  }
-  if (JZ != 0) {
-#pragma unroll
-    for (int a = 0; a < NDX; a++) {
-      const T fxa = S0x[a] + T(0.5) * DSx[a];
-#pragma unroll
-      for (int b = 0; b < ND - 1; b++) {
-        T v;
-        if (JZ == 2) v = sub_rn(mul_rn(fxa, Pz[b]), mul_rn(Sxi[a], Pzi[b]));
-        else v = fxa * Pz[b];
-        if (v != T(0)) atomicAdd(Jz + (Idx)a * ld + b, v);
+      for (int a = 0; a < NDX - 1; a++) {
+        const T v = Px[a] * fzb;
+        if (v != T(0)) atomicAdd(Jx + (Idx)a * ld + b, v);
       }
     }
   }
@@ -203,6 +186,26 @@ __device__ __forceinline__ void deposit(T* Jx, long cs, int ld, const T* S0x, co
       for (int b = 0; b < ND; b++) {
         const T v = ay * S0z[b] + by * DSz[b];
         if (v != T(0)) atomicAdd(Jy + (Idx)a * ld + b, v);
+      }
+    }
+  }
+  if (JZ != 0) {
+    T Pz[ND - 1], Pzi[ND - 1];
+    T az = T(0), ai = T(0);
+#pragma unroll
+    for (int b = 0; b < ND - 1; b++) {
+      az += cz * DSz[b]; Pz[b] = az;
+      if (JZ == 2) { ai += cz * DSzi[b]; Pzi[b] = ai; }
+    }
+#pragma unroll
+    for (int a = 0; a < NDX; a++) {
+      const T fxa = S0x[a] + T(0.5) * DSx[a];
+#pragma unroll
+      for (int b = 0; b < ND - 1; b++) {
+        T v;
+        if (JZ == 2) v = sub_rn(mul_rn(fxa, Pz[b]), mul_rn(Sxi[a], Pzi[b]));
+        else v = fxa * Pz[b];
+        if (v != T(0)) atomicAdd(Jz + (Idx)a * ld + b, v);
       }
     }
   }
@@ -321,20 +324,29 @@ __device__ __forceinline__ bool push_one(const T* __restrict__ Eb, const T* __re
   uint32_t cs0 = 0;   // mixed path: stored cell and z offset (drifting frame)
   float ozs = 0.0f;
   // the lab-fixed ion of the particle's lattice site (mixed path, electron-ion pairs)
-  bool ion_live = false;
+  bool ion_live = false, at_site = false;
+  uint32_t pid = 0;
   IonSite<ORDER> is{};
   if constexpr (CP) {
     cs0 = p.cell[pi];
     ozs = p.oz[pi];
     fx = cell_x(cs0);
     frame_z(cs0, ozs, pc.fr0_sz, pc.fr0_fz, fz, tz);
-    if (pc.pairs) {
-      const uint32_t id = p.id[pi];
-      ion_live = site_row(id, pc) >= pc.mlo;
-      if (ion_live) ion_site<ORDER>(id, pc, is);
-    }
-    if (SMEM && (!box.in(fx, fz) || (ion_live && !box.in(is.fx, is.fz0)))) return false;
     tx = p.ox[pi];
+    if (pc.pairs) {
+      pid = p.id[pi];
+      ion_live = site_row(pid, pc) >= pc.mlo;
+      if (ion_live) {
+        lattice_site_pow2(pid, pc.kb, pc.lpx, pc.lpz, pc.gx_lo, pc.z0_cells, is.cell, is.ox, is.oz);
+        // an electron still at its lattice site shares its ion's grid position
+        at_site = cs0 == is.cell && ozs == is.oz && tx == is.ox;
+        if (SMEM && !at_site) {
+          frame_z(is.cell, is.oz, pc.fr0_sz, pc.fr0_fz, is.fz0, is.tz0);
+          if (!box.in(cell_x(is.cell), is.fz0)) return false;
+        }
+      }
+    }
+    if (SMEM && !box.in(fx, fz)) return false;
     fxh = tx >= T(0.5) ? fx : fx - 1; txh = tx >= T(0.5) ? tx - T(0.5) : tx + T(0.5);
     fzh = tz >= T(0.5) ? fz : fz - 1; tzh = tz >= T(0.5) ? tz - T(0.5) : tz + T(0.5);
   } else {
@@ -468,59 +480,90 @@ __device__ __forceinline__ bool push_one(const T* __restrict__ Eb, const T* __re
     fxn = (int)floor(Xn); fzn = (int)floor(Zn);
     txn = T(Xn - fxn); tzn = T(Zn - fzn);
   }
-  // Esirkepov deposition on an ND x ND window
+  // the lab-fixed ion of the particle's lattice site (mixed path): J_z of the
+  // pair is exactly zero when electron and ion made the same move (the cold
+  // streaming plasma); otherwise combined on a common window, or separate
   const int off = ORDER == 3 ? 1 : 0;
   const int bx = min(fx, fxn) - off, bz = min(fz, fzn) - off;
+  int jz = 1;
+  bool ion_sep = false;
+  if constexpr (CP) {
+    if (ion_live) {
+      if (at_site && csn == cs0 && ozn == ozs && txn == tx) {
+        // the pair made the same move: the ion is where the electron is
+        jz = 0;
+        is.fx = fxn;
+        is.fz1 = fzn;
+      } else {
+        ion_site<ORDER>(pid, pc, is);
+        if (is.fx - off == bx && min(is.fz0, is.fz1) - off == bz) jz = 2;
+        else ion_sep = true;
+      }
+    }
+  }
   T cx, cz, cy;
   if constexpr (CP) {
     cx = pc.kx_f * w; cz = pc.kz_f * w; cy = pc.ky_f * w * vy;
   } else {
     cx = T(pc.kx) * w; cz = T(pc.kz) * w; cy = T(pc.ky) * w * vy;
   }
-  // the lab-fixed ion of the particle's lattice site (mixed path): J_z of the
-  // pair is exactly zero when electron and ion made the same move (the cold
-  // streaming plasma); otherwise combined on a common window, or separate
-  int jz = 1;
-  bool ion_sep = false;
+  // the new state is stored before the deposit, which reads only registers and
+  // the current window (fewer values live across it)
+  bool gone;
   if constexpr (CP) {
+    p.cell[pi] = csn; p.ox[pi] = txn; p.oz[pi] = ozn;
+    gone = fxn < pc.cx_lo || fxn >= pc.cx_hi || fzn < pc.cz_lo || fzn >= pc.cz_hi;
+  } else {
+    p.x[pi] = xn; p.z[pi] = zn;
+    gone = xn < pc.xlo || xn >= pc.xhi || zn < pc.zlo || zn >= pc.zhi;
+  }
+  p.ux[pi] = ux; p.uy[pi] = uy; p.uz[pi] = uz;
+  if (gone) {
+    // an electron whose ion is still inside leaves a ghost that carries the ion
+    p.w[pi] = ion_live ? -w : T(0);
+  } else {
+    bx0 = min(bx0, fxn); bx1 = max(bx1, fxn);
+    bz0 = min(bz0, fzn); bz1 = max(bz1, fzn);
+  }
+  if constexpr (CP) {
+    // the pair's ion (or the ghost's) deposits next step: its cell belongs in the chunk's box too
     if (ion_live) {
-      if (cs0 == is.cell && ozs == is.oz && tx == is.ox && csn == is.cell && ozn == is.oz && txn == is.ox)
-        jz = 0;
-      else if (is.fx - off == bx && min(is.fz0, is.fz1) - off == bz)
-        jz = 2;
-      else
-        ion_sep = true;
+      bx0 = min(bx0, is.fx); bx1 = max(bx1, is.fx);
+      bz0 = min(bz0, is.fz1); bz1 = max(bz1, is.fz1);
     }
   }
-  // no current at all: the x weights are unchanged (J_x = 0), no out-of-plane
-  // velocity (J_y = 0) and J_z cancels within the pair; a warp whose lanes all
-  // carry no current skips the weights and the deposit
+  // Esirkepov deposition on an ND x ND window. No current at all: the x weights
+  // are unchanged (J_x = 0), no out-of-plane velocity (J_y = 0) and J_z cancels
+  // within the pair; a warp whose lanes all carry no current skips the weights
+  // and the deposit
   bool dep = !(jz == 0 && fxn == fx && txn == tx && cy == T(0));
   if constexpr (SMEM) dep = __any_sync(__activemask(), dep);
   if (dep) {
-    T S0x[ND], S1x[ND], S0z[ND], S1z[ND];
+    T S0x[ND], DSx[ND], S0z[ND], DSz[ND];
     {
-      T w0[NG], w1[NG];
-      place<T, ORDER>(wxi, fx - off - bx, S0x);
-      wts<T, ORDER>(txn, w1); place<T, ORDER>(w1, fxn - off - bx, S1x);
-      place<T, ORDER>(wzi, fz - off - bz, S0z);
-      wts<T, ORDER>(tzn, w0); place<T, ORDER>(w0, fzn - off - bz, S1z);
-    }
-    T DSx[ND], DSz[ND];
+      // the t^n weights again (cheaper than keeping the gather's live through the push)
+      T w1[NG], S1[ND];
+      wts<T, ORDER>(tx, w1); place<T, ORDER>(w1, fx - off - bx, S0x);
+      wts<T, ORDER>(txn, w1); place<T, ORDER>(w1, fxn - off - bx, S1);
 #pragma unroll
-    for (int a = 0; a < ND; a++) { DSx[a] = S1x[a] - S0x[a]; DSz[a] = S1z[a] - S0z[a]; }
+      for (int a = 0; a < ND; a++) DSx[a] = S1[a] - S0x[a];
+      wts<T, ORDER>(tz, w1); place<T, ORDER>(w1, fz - off - bz, S0z);
+      wts<T, ORDER>(tzn, w1); place<T, ORDER>(w1, fzn - off - bz, S1);
+#pragma unroll
+      for (int a = 0; a < ND; a++) DSz[a] = S1[a] - S0z[a];
+    }
     T Sxi[ND], DSzi[ND];
     if constexpr (CP) {
       if (jz == 2) {
-        T wxi2[NG], w0i[NG], w1i[NG], S0zi[ND], S1zi[ND];
-        wts<T, ORDER>(T(is.ox), wxi2);
-        wts<T, ORDER>(T(is.tz0), w0i);
-        wts<T, ORDER>(T(is.tz1), w1i);
-        place<T, ORDER>(wxi2, 0, Sxi);
-        place<T, ORDER>(w0i, is.fz0 - off - bz, S0zi);
-        place<T, ORDER>(w1i, is.fz1 - off - bz, S1zi);
+        T wi[NG], S0i[ND], S1i[ND];
+        wts<T, ORDER>(T(is.ox), wi);
+        place<T, ORDER>(wi, 0, Sxi);
+        wts<T, ORDER>(T(is.tz0), wi);
+        place<T, ORDER>(wi, is.fz0 - off - bz, S0i);
+        wts<T, ORDER>(T(is.tz1), wi);
+        place<T, ORDER>(wi, is.fz1 - off - bz, S1i);
 #pragma unroll
-        for (int b = 0; b < ND; b++) DSzi[b] = S1zi[b] - S0zi[b];
+        for (int b = 0; b < ND; b++) DSzi[b] = S1i[b] - S0i[b];
       }
     }
     T* Jx = Jb + (long)(bx - ox) * ld + (bz - oz);
@@ -537,33 +580,6 @@ __device__ __forceinline__ bool push_one(const T* __restrict__ Eb, const T* __re
     }
     if constexpr (CP) {
       if (ion_sep) ion_jz<T, ORDER, SMEM>(Jb, cs, ld, ox, oz, is, cz);
-    }
-  }
-  bool gone;
-  if constexpr (CP) {
-    p.cell[pi] = csn; p.ox[pi] = txn; p.oz[pi] = ozn;
-    gone = fxn < pc.cx_lo || fxn >= pc.cx_hi || fzn < pc.cz_lo || fzn >= pc.cz_hi;
-  } else {
-    p.x[pi] = xn; p.z[pi] = zn;
-    gone = xn < pc.xlo || xn >= pc.xhi || zn < pc.zlo || zn >= pc.zhi;
-  }
-  p.ux[pi] = ux; p.uy[pi] = uy; p.uz[pi] = uz;
-  if (gone) {
-    // an electron whose ion is still inside leaves a ghost that carries the ion
-    p.w[pi] = ion_live ? -w : T(0);
-    if (ion_live) {
-      bx0 = min(bx0, is.fx); bx1 = max(bx1, is.fx);
-      bz0 = min(bz0, is.fz1); bz1 = max(bz1, is.fz1);
-    }
-  } else {
-    bx0 = min(bx0, fxn); bx1 = max(bx1, fxn);
-    bz0 = min(bz0, fzn); bz1 = max(bz1, fzn);
-    if constexpr (CP) {
-      // the pair's ion deposits with it next step: its cell belongs in the chunk's box too
-      if (ion_live) {
-        bx0 = min(bx0, is.fx); bx1 = max(bx1, is.fx);
-        bz0 = min(bz0, is.fz1); bz1 = max(bz1, is.fz1);
-      }
     }
   }
   return true;
@@ -611,7 +627,7 @@ __device__ __noinline__ void push_global_guarded(const T* gE, const T* gB, T* gJ
 template <class T, int ORDER, bool MC>
 __global__ void __launch_bounds__(PB_THREADS, 5) k_push(GridP g, const T* gE, const T* gB, T* gJ, Particles<T> p,
                                                      Chunk* chunks, Ctrl* ctrl, int cap_nodes, int tile_z,
-                                                     PushConst pc) {
+                                                     PushDefer pd, PushConst pc) {
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);
   typedef typename Vec2<T>::type V2;
@@ -686,8 +702,11 @@ __global__ void __launch_bounds__(PB_THREADS, 5) k_push(GridP g, const T* gE, co
         // a particle outside the chunk's box (should not happen; with electron-ion pairs, the ion's cell
         // counts too) takes the global path
         if (!push_one<T, ORDER, true, MC>(sm, nullptr, sm + 6 * cap_nodes, cap_nodes, lds, wx0, wz0, p, pi, pc, box,
-                                          bx0, bx1, bz0, bz1))
-          push_global_guarded<T, ORDER, MC>(gE, gB, gJ, g, p, pi, pc, ctrl, bx0, bx1, bz0, bz1);
+                                          bx0, bx1, bz0, bz1)) {
+          const int q = atomicAdd(&ctrl->n_defer, 1);
+          if (q < pd.defer_cap) pd.defer[q] = make_int2(pi, c);
+          else atomicOr(&ctrl->status, ST_OVERFLOW);
+        }
       }
       __syncthreads();
       for (int e = threadIdx.x; e < nn; e += blockDim.x) {
@@ -700,10 +719,12 @@ __global__ void __launch_bounds__(PB_THREADS, 5) k_push(GridP g, const T* gE, co
           if (val != T(0)) atomicAdd(gJ + q * g.cs + gp, val);
         }
       }
-    } else {
-      if (threadIdx.x == 0) atomicAdd(&ctrl->overflow_chunks, 1);
-      for (int pi = ch.p0 + threadIdx.x; pi < ch.p1; pi += blockDim.x)
-        push_global_guarded<T, ORDER, MC>(gE, gB, gJ, g, p, pi, pc, ctrl, bx0, bx1, bz0, bz1);
+    } else if (threadIdx.x == 0) {
+      // the whole chunk goes to the global-memory pass; its box is rebuilt there
+      atomicAdd(&ctrl->overflow_chunks, 1);
+      const int q = atomicAdd(&ctrl->n_ovf, 1);
+      if (q < pd.ovf_cap) pd.ovf[q] = c;
+      else atomicOr(&ctrl->status, ST_OVERFLOW);
     }
     // bounding box of the chunk's live particles for the next step
     bx0 = __reduce_min_sync(0xffffffffu, bx0); bx1 = __reduce_max_sync(0xffffffffu, bx1);
@@ -719,6 +740,39 @@ __global__ void __launch_bounds__(PB_THREADS, 5) k_push(GridP g, const T* gE, co
       chunks[c] = o;
     }
     __syncthreads();
+  }
+}
+
+// The global-memory pass after k_push: whole chunks whose window did not fit in shared memory (one block
+// each), then single particles that were outside their chunk's box (one thread each). Both add their
+// current with global atomics and widen their chunk's box atomically (k_push has written the box of the
+// particles it pushed; an overflow chunk's box starts empty).
+template <class T, int ORDER, bool MC>
+__global__ void __launch_bounds__(PB_THREADS) k_push_deferred(GridP g, const T* gE, const T* gB, T* gJ,
+                                                               Particles<T> p, Chunk* chunks, Ctrl* ctrl,
+                                                               PushDefer pd, PushConst pc) {
+  const int novf = min(ctrl->n_ovf, pd.ovf_cap), ndef = min(ctrl->n_defer, pd.defer_cap);
+  for (int j = blockIdx.x; j < novf; j += gridDim.x) {
+    const int c = pd.ovf[j];
+    const Chunk ch = chunks[c];
+    int bx0 = INT_MAX, bx1 = INT_MIN, bz0 = INT_MAX, bz1 = INT_MIN;
+    for (int pi = ch.p0 + threadIdx.x; pi < ch.p1; pi += blockDim.x)
+      push_global_guarded<T, ORDER, MC>(gE, gB, gJ, g, p, pi, pc, ctrl, bx0, bx1, bz0, bz1);
+    bx0 = __reduce_min_sync(0xffffffffu, bx0); bx1 = __reduce_max_sync(0xffffffffu, bx1);
+    bz0 = __reduce_min_sync(0xffffffffu, bz0); bz1 = __reduce_max_sync(0xffffffffu, bz1);
+    if ((threadIdx.x & 31) == 0) {
+      atomicMin(&chunks[c].ix0, bx0); atomicMax(&chunks[c].ix1, bx1);
+      atomicMin(&chunks[c].iz0, bz0); atomicMax(&chunks[c].iz1, bz1);
+    }
+  }
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < ndef; j += gridDim.x * blockDim.x) {
+    const int2 e = pd.defer[j];
+    int bx0 = INT_MAX, bx1 = INT_MIN, bz0 = INT_MAX, bz1 = INT_MIN;
+    push_global_guarded<T, ORDER, MC>(gE, gB, gJ, g, p, e.x, pc, ctrl, bx0, bx1, bz0, bz1);
+    if (bx0 <= bx1) {
+      atomicMin(&chunks[e.y].ix0, bx0); atomicMax(&chunks[e.y].ix1, bx1);
+      atomicMin(&chunks[e.y].iz0, bz0); atomicMax(&chunks[e.y].iz1, bz1);
+    }
   }
 }
 
@@ -978,7 +1032,7 @@ __global__ void k_add_counts(Ctrl* ctrl, int dcount, int dchunks) {
 template <class T>
 void launch_push(const GridP& g, const FieldPtrs<T>& f, Particles<T> p, Chunk* chunks, Ctrl* ctrl, int order,
                  int grid_blocks, int smem_nodes, int tile_z, double q, double m, double gamma_b, double beta_b,
-                 int fr1_sz, float fr1_fz, int pairs, int mlo, int nodal, cudaStream_t s) {
+                 int fr1_sz, float fr1_fz, int pairs, int mlo, int nodal, const PushDefer& pd, cudaStream_t s) {
   PushConst pc;
   pc.dx = g.dx; pc.dz = g.dz; pc.dt = g.dt; pc.z0 = g.z0;
   pc.xlo = g.gx_lo * g.dx; pc.xhi = g.gx_hi * g.dx;
@@ -1000,22 +1054,29 @@ void launch_push(const GridP& g, const FieldPtrs<T>& f, Particles<T> p, Chunk* c
   while ((1 << pc.lpz) < g.il_ppcz) pc.lpz++;
   const size_t sm = (size_t)9 * smem_nodes * sizeof(T);
   cudaMemsetAsync(&ctrl->next_chunk, 0, sizeof(int), s);
+  cudaMemsetAsync(&ctrl->n_defer, 0, 2 * sizeof(int), s);
   // 'momentum conserving' gather: the node-interpolated copies; else the Yee-located gather copies
   const T* gE = nodal ? f.nE[0] : f.fE[0];
   const T* gB = nodal ? f.nB[0] : f.fB[0];
   if (order == 3 && !nodal) {
     cudaFuncSetAttribute(k_push<T, 3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_push<T, 3, false><<<grid_blocks, PB_THREADS, sm, s>>>(g, gE, gB, f.J[0], p, chunks, ctrl, smem_nodes, tile_z, pc);
+    k_push<T, 3, false><<<grid_blocks, PB_THREADS, sm, s>>>(g, gE, gB, f.J[0], p, chunks, ctrl, smem_nodes, tile_z, pd, pc);
   } else if (order == 3) {
     cudaFuncSetAttribute(k_push<T, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_push<T, 3, true><<<grid_blocks, PB_THREADS, sm, s>>>(g, gE, gB, f.J[0], p, chunks, ctrl, smem_nodes, tile_z, pc);
+    k_push<T, 3, true><<<grid_blocks, PB_THREADS, sm, s>>>(g, gE, gB, f.J[0], p, chunks, ctrl, smem_nodes, tile_z, pd, pc);
   } else if (!nodal) {
     cudaFuncSetAttribute(k_push<T, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_push<T, 1, false><<<grid_blocks, PB_THREADS, sm, s>>>(g, gE, gB, f.J[0], p, chunks, ctrl, smem_nodes, tile_z, pc);
+    k_push<T, 1, false><<<grid_blocks, PB_THREADS, sm, s>>>(g, gE, gB, f.J[0], p, chunks, ctrl, smem_nodes, tile_z, pd, pc);
   } else {
     cudaFuncSetAttribute(k_push<T, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_push<T, 1, true><<<grid_blocks, PB_THREADS, sm, s>>>(g, gE, gB, f.J[0], p, chunks, ctrl, smem_nodes, tile_z, pc);
+    k_push<T, 1, true><<<grid_blocks, PB_THREADS, sm, s>>>(g, gE, gB, f.J[0], p, chunks, ctrl, smem_nodes, tile_z, pd, pc);
   }
+  // the global-memory pass over what the window kernel left (usually nothing: the blocks exit at once)
+  const int gb = grid_blocks < 304 ? grid_blocks : 304;
+  if (order == 3 && !nodal) k_push_deferred<T, 3, false><<<gb, PB_THREADS, 0, s>>>(g, gE, gB, f.J[0], p, chunks, ctrl, pd, pc);
+  else if (order == 3) k_push_deferred<T, 3, true><<<gb, PB_THREADS, 0, s>>>(g, gE, gB, f.J[0], p, chunks, ctrl, pd, pc);
+  else if (!nodal) k_push_deferred<T, 1, false><<<gb, PB_THREADS, 0, s>>>(g, gE, gB, f.J[0], p, chunks, ctrl, pd, pc);
+  else k_push_deferred<T, 1, true><<<gb, PB_THREADS, 0, s>>>(g, gE, gB, f.J[0], p, chunks, ctrl, pd, pc);
 }
 
 int push_occupancy(int order, bool dbl, int smem_nodes) {
@@ -1084,7 +1145,8 @@ void launch_add_counts(Ctrl* ctrl, int dcount, int dchunks, cudaStream_t s) {
 
 #define INST(T)                                                                                                 \
   template void launch_push<T>(const GridP&, const FieldPtrs<T>&, Particles<T>, Chunk*, Ctrl*, int, int, int,   \
-                               int, double, double, double, double, int, float, int, int, int, cudaStream_t);   \
+                               int, double, double, double, double, int, float, int, int, int, const PushDefer&, \
+                               cudaStream_t);                                                                   \
   template void launch_sort<T>(const GridP&, Particles<T>, Particles<T>, SortBufs, Chunk*, Ctrl*, int, int, int,\
                                cudaStream_t);                                                                   \
   template void launch_inject<T>(const GridP&, Particles<T>, Chunk*, Ctrl*, const InjectP&, int, int, cudaStream_t);

@@ -225,6 +225,10 @@ class Simulation:
         a = np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
         self._check(self.L.pic_set_field(self.h, comp, _p(a)), "pic_set_field")
 
+    def beam_self_field(self):
+        """add the frozen test beam's self-field, solved on the device (pic_beam_self_field)"""
+        self._check(self.L.pic_beam_self_field(self.h), "pic_beam_self_field")
+
     def particles(self, species: int = capi.ELECTRONS) -> dict:
         n = ctypes.c_int64(0)
         self._check(self.L.pic_get_particles(self.h, species, None, None, None, None, None, None, None, None,
