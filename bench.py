@@ -526,6 +526,114 @@ def run_1d(args):
     return 0
 
 
+def run_stage3d(args):
+    """Config 3 as a whole run: the 3D stage (1024 x 128 x 128 cells, gamma 30, CK2 at c dt = dz/sqrt(2),
+    Friedman 0.1, 16-cell PML, 4 passes + compensation) stepped --stage3d steps with lab-frame snapshots: one
+    lab time per 50 boosted steps (the lab time at which the box centre's boosted time is a multiple of 50
+    steps), each sampled at 16 lab stations across the box. Reports the throughput over the whole run, the
+    field energy every 1000 steps, the lab rows filled and the wall time."""
+    import ctypes
+    import numpy as np
+    import torch
+    from paper_1009_2727_gb300 import capi
+    from paper_1009_2727_gb300 import workloads as W
+    from paper_1009_2727_gb300.pic import Simulation
+    torch.cuda.set_device(0)
+    w = W.stage_3d()
+    w["precision"] = args.precision
+    sim = Simulation(w, precision=args.precision)
+    st = sim.stats()
+    dt, dz, gam, be = st["dt"], st["dz"], st["gamma"], st["beta"]
+    c = 299792458.0
+    every, n_st = 50, 16
+    n_snap = max(args.stage3d // every, 1)
+    zlo, zhi = st["gz_lo"] * dz, st["gz_hi"] * dz
+    zc = 0.5 * (zlo + zhi)
+    zl, tl = [], []
+    for j in range(1, n_snap + 1):
+        tp = j * every * dt
+        t_lab = gam * (tp + be * zc / c)
+        z_c = gam * (zc + be * c * tp)
+        half = 0.5 * (zhi - zlo) / gam
+        for q in range(n_st):
+            zl.append(z_c - half + (q + 0.5) * 2.0 * half / n_st)
+            tl.append(t_lab)
+    sim.btd_set(np.array(zl), np.array(tl))
+    n0 = sim.stats()["n_electrons"]
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    energy = []
+    t_wall = time.perf_counter()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    done = 0
+    while done < args.stage3d:
+        k = min(1000, args.stage3d - done)
+        sim.step(k)
+        done += k
+        sim.sync()
+        fe = sim.stats()["field_energy"]
+        energy.append([done, fe])
+        if not np.isfinite(fe):
+            break
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    n1 = sim.stats()["n_electrons"]
+    o = capi.PicBtdOut()
+    o.struct_size = ctypes.sizeof(capi.PicBtdOut)
+    o.version = capi.API_VERSION
+    o.data = None
+    o.done = None
+    o.on_device = 0
+    sim._check(sim.L.pic_boosted_to_lab_diag(sim.h, None, ctypes.byref(o)), "pic_boosted_to_lab_diag")
+    e = np.array(energy)
+    peak_emit = e[:, 1].max()
+    line = {"metric": "particle-steps/s", "value": 0.5 * (n0 + n1) * done / (ms * 1e-3), "unit": "particle-steps/s",
+            "n_gpus": 1, "steps": done, "ms_per_step": ms / done, "higher_is_better": True,
+            "dtype": "f32" if args.precision == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": w["name"] + " (whole run)", "grid": [w["nz"], w["ny"], w["nx"]], "ppc": 2,
+                       "gamma_boost": w["gamma_boost"], "solver": "CK2", "c_dt_over_dz": 1 / np.sqrt(2.0),
+                       "theta": w["theta"], "filter": "4 passes + compensation", "precision": args.precision,
+                       "electrons": int(0.5 * (n0 + n1)),
+                       "lab_snapshots": {"every_steps": every, "snapshots": n_snap, "stations_each": n_st,
+                                         "rows": len(zl), "rows_filled": int(o.n_rows_filled)}},
+            "field_energy_every_1000_steps": e.tolist(),
+            "finite": bool(np.isfinite(e[:, 1]).all()),
+            "final_over_peak_energy": float(e[-1, 1] / peak_emit) if peak_emit > 0 else None,
+            "wall_s": wall, "clocks": clocks, "gpu_launches": int(sim.launches())}
+    sim.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_layout_sweep(args):
+    """every particle layout the autotuner can return (tiles {8, 16, 32}^2, sort cadences 8, 16, 32, 64) on
+    the given box, a few steps each: run under ncu with the DRAM byte counters to tabulate the push kernel's
+    traffic per particle for each layout (prints one line per layout with its electron count)"""
+    import torch
+    from paper_1009_2727_gb300 import workloads as W
+    from paper_1009_2727_gb300.pic import Simulation
+    torch.cuda.set_device(0)
+    w = W.stage_2d()
+    if args.nz:
+        w = W.shrink(w, w["nx"], args.nz)
+    for tx in (8, 16, 32):
+        for tz in (8, 16, 32):
+            for se in (8, 16, 32, 64):
+                sim = Simulation(w, precision=args.precision, tile=(tx, tz), sort_every=se)
+                sim.step(args.steps)
+                sim.sync()
+                print(json.dumps({"tile": [tx, tz], "sort_every": se, "steps": args.steps,
+                                  "electrons": sim.stats()["n_electrons"]}), flush=True)
+                sim.close()
+    return 0
+
+
 def run_app1(args):
     """App. I on the GPU: the Nyquist (odd-even) mode grows without the current filter and is removed by
     one bilinear pass"""
@@ -606,6 +714,10 @@ def main():
                     help="momentum: the 'momentum conserving' gather (fields interpolated to the nodes first)")
     ap.add_argument("--dt-scan", action="store_true",
                     help="instability level (high-k E_z power at fixed times) against c dt/dz for both gather schemes")
+    ap.add_argument("--layout-sweep", action="store_true",
+                    help="step every layout the autotuner can return, a few steps each (for a DRAM traffic table)")
+    ap.add_argument("--stage3d", type=int, default=0,
+                    help="config 3 as a whole run: N steps of the 3D stage with lab snapshots every 50 steps")
     ap.add_argument("--filter-strides", default="",
                     help="wide-band filter, e.g. 1,2,4: the stage's passes + compensation at each stride "
                          "(the antenna moves past the wider particle guard)")
@@ -636,6 +748,10 @@ def main():
         return run_app1(args)
     if args.dim == 1 and args.impl != "reference":
         return run_1d(args)
+    if args.stage3d:
+        return run_stage3d(args)
+    if args.layout_sweep:
+        return run_layout_sweep(args)
     if args.ensemble:
         return run_ensemble(args)
     if args.surrogate:

@@ -174,7 +174,8 @@ typedef struct {
 typedef struct {
   uint32_t struct_size, version;
   void* data;             /* n_rows * 6 * (nx+1) values of the context precision's real type
-                             (double for PIC_FP64, float for PIC_MIXED), layout [row][component][i] */
+                             (double for PIC_FP64, float for PIC_MIXED), layout [row][component][i]
+                             (3D: [row][component][i][j]); NULL: only the counts are returned */
   int32_t* done;          /* n_rows * 2 flags: E part complete, B part complete (may be NULL) */
   int32_t on_device;      /* 1: data/done are device pointers, 0: host pointers */
   int64_t n_rows_filled;  /* out: rows with both parts complete */

@@ -1101,6 +1101,8 @@ struct Beam3 {
   T *uxb, *uyb, *uzb;
   int* fl;    // bit 0 alive, bit 1 active
   int n;
+  T* w;       // self-consistent beam: macro-particle weights (self = 1)
+  int self;
 };
 
 __global__ void k3_beam_vz(int n, const double* ux, const double* uy, const double* uz, double* acc) {
@@ -1147,6 +1149,52 @@ __global__ void k3_beam_finish(Beam3<T> b, double t_now, double* acc) {
   if (j == 0) acc[2] = vbar;
 }
 
+__device__ __forceinline__ double bshape(int order, double s) {
+  const double a = fabs(s);
+  if (order == 1) return a < 1.0 ? 1.0 - a : 0.0;
+  if (a < 1.0) return 2.0 / 3.0 - a * a + 0.5 * a * a * a;
+  if (a < 2.0) { const double t = 2.0 - a; return t * t * t / 6.0; }
+  return 0.0;
+}
+
+// Esirkepov current of one beam particle (charge * weight qw) moving p0 -> p1, added to J with global
+// atomics (a beam has few particles): along axis q, J_q is the running sum over the q-nodes of
+// -qw d_q / (dx dy dz dt) DS_q times the transverse weight S0u S0v + DSu S0v / 2 + S0u DSv / 2 + DSu DSv / 3
+// (Esirkepov 2001), on a window of 9 nodes per axis starting 3 below the lower of the two cells
+template <class T>
+__device__ void beam_current3(const G3& g, T* const* J, int order, const double* p0, const double* p1, double qw) {
+  constexpr int EW = 9;
+  int base[3];
+  double S0[3][EW], DS[3][EW];
+  for (int a = 0; a < 3; a++) {
+    const double A0 = p0[a] / g.d[a], A1 = p1[a] / g.d[a];
+    base[a] = (int)floor(A0 < A1 ? A0 : A1) - 3;
+    for (int m = 0; m < EW; m++) {
+      S0[a][m] = bshape(order, A0 - (base[a] + m));
+      DS[a][m] = bshape(order, A1 - (base[a] + m)) - S0[a][m];
+    }
+  }
+  for (int q = 0; q < 3; q++) {
+    const int u = (q + 1) % 3, v = (q + 2) % 3;
+    const double cq = -qw * g.d[q] / (g.d[0] * g.d[1] * g.d[2] * g.dt);
+    for (int mu = 0; mu < EW; mu++)
+      for (int mv = 0; mv < EW; mv++) {
+        const double tr = S0[u][mu] * S0[v][mv] + 0.5 * DS[u][mu] * S0[v][mv] + 0.5 * S0[u][mu] * DS[v][mv] +
+                          DS[u][mu] * DS[v][mv] / 3.0;
+        if (tr == 0.0) continue;
+        double acc = 0.0;
+        for (int mq = 0; mq < EW; mq++) {
+          acc += cq * DS[q][mq] * tr;
+          if (acc == 0.0) continue;
+          int idx[3];
+          idx[q] = base[q] + mq; idx[u] = base[u] + mu; idx[v] = base[v] + mv;
+          if (idx[0] < 0 || idx[0] > g.n[0] || idx[1] < 0 || idx[1] > g.n[1] || idx[2] < 0 || idx[2] > g.n[2]) continue;
+          atomicAdd(J[q] + nid(g, idx[0], idx[1], idx[2]), T(acc));
+        }
+      }
+  }
+}
+
 template <class T, int ORD>
 __global__ void k3_beam_push(G3 g, Fld3<T> f, Beam3<T> b, double tn, double tn1, const double* acc, T kq,
                              int nodal) {
@@ -1167,7 +1215,15 @@ __global__ void k3_beam_push(G3 g, Fld3<T> f, Beam3<T> b, double tn, double tn1,
       b.fl[j] = fl;
       if (!(fl & 1)) return;
     } else {
-      b.z[j] = b.zf0[j] + acc[2] * tn1;
+      const double zn = b.zf0[j] + acc[2] * tn1;
+      // self-consistent beam: a frozen particle inside the particle domain carries its charge along z
+      if (b.self) {
+        const double p0[3] = {b.x[j], b.y[j], b.z[j]}, p1[3] = {b.x[j], b.y[j], zn};
+        bool in = zn >= lo[2] && zn < hi[2];
+        for (int a = 0; a < 3; a++) in = in && p0[a] >= lo[a] && p0[a] < hi[a];
+        if (in) beam_current3<T>(g, f.J, ORD, p0, p1, -kQe * (double)b.w[j]);
+      }
+      b.z[j] = zn;
       return;
     }
   }
@@ -1179,11 +1235,120 @@ __global__ void k3_beam_push(G3 g, Fld3<T> f, Beam3<T> b, double tn, double tn1,
   const T gm = sqrt(T(1) + (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]) * T(1.0 / (kC * kC)));
   double pn[3];
   for (int a = 0; a < 3; a++) pn[a] = pos[a] + g.dt * (double)(u[a] / gm);
+  if (b.self) beam_current3<T>(g, f.J, ORD, pos, pn, -kQe * (double)b.w[j]);
   b.x[j] = pn[0]; b.y[j] = pn[1]; b.z[j] = pn[2];
   b.ux[j] = u[0]; b.uy[j] = u[1]; b.uz[j] = u[2];
   for (int a = 0; a < 3; a++)
     if (pn[a] < lo[a] || pn[a] >= hi[a]) fl &= ~1;
   b.fl[j] = fl;
+}
+
+// ---------------------------------------------------------------------------
+// Self-field of the frozen beam in 3D (Sec. 3.1.1, PR-27): d2phi/dx2 + d2phi/dy2 + d2phi/dz2 / gamma_v^2 =
+// -rho/eps0 with phi = 0 on the PEC walls, in the Yee mesh's second differences, solved by sine transforms
+// (DST-I) along the three axes; E = -grad phi with E_z divided by gamma_v^2, B = v z x E / c^2 (B_x = -v E_y
+// / c^2, B_y = v E_x / c^2) at their Yee positions. The solve works on an unpadded (nx+1)(ny+1)(nz+1) array
+// (z fastest), FP64 throughout; a one-time set-up.
+
+// charge density of the frozen beam particles inside the particle domain, positions `shift` seconds on
+template <class T>
+__global__ void k3_beam_rho(G3 g, Beam3<T> b, int order, double shift, const double* acc, double* rho) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= b.n || (b.fl[j] & 3) != 1) return;
+  const double r[3] = {b.x[j], b.y[j], b.z[j] + acc[2] * shift};
+  for (int a = 0; a < 3; a++) {
+    const double lo = g.lo[a] * g.d[a], hi = (g.hi[a] + (a == 2 ? 1 : 0)) * g.d[a];
+    if (!(r[a] >= lo && r[a] < hi)) return;
+  }
+  const double qw = -kQe * (double)b.w[j] / (g.d[0] * g.d[1] * g.d[2]);
+  int f[3];
+  for (int a = 0; a < 3; a++) f[a] = (int)floor(r[a] / g.d[a]);
+  const long L = g.n[2] + 1, PL = (long)(g.n[1] + 1) * L;
+  for (int i = f[0] - 2; i <= f[0] + 3; i++) {
+    const double wx = bshape(order, r[0] / g.d[0] - i);
+    if (wx == 0.0 || i < 0 || i > g.n[0]) continue;
+    for (int jj = f[1] - 2; jj <= f[1] + 3; jj++) {
+      const double wy = bshape(order, r[1] / g.d[1] - jj);
+      if (wy == 0.0 || jj < 0 || jj > g.n[1]) continue;
+      for (int k = f[2] - 2; k <= f[2] + 3; k++) {
+        const double wz = bshape(order, r[2] / g.d[2] - k);
+        if (wz == 0.0 || k < 0 || k > g.n[2]) continue;
+        atomicAdd(rho + i * PL + jj * L + k, qw * wx * wy * wz);
+      }
+    }
+  }
+}
+
+// out(a, b, m) = 2 sum_{j=1}^{N-1} in(a, b, j) sin(pi j m / N), m = 1..N-1, for the interior outer indices
+// a = 1..na-2, b = 1..nb-2 (strides sa, sb; the transform index stride si); tab[t] = sin(pi t / N), t < 2N.
+// Threads run over m when si == 1 (the inputs of a row are shared), else over b (stride 1: coalesced).
+__global__ void k3_dst(const double* in, double* out, const double* tab, int N, int na, int nb, long sa, long sb,
+                       long si) {
+  const long id = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long cm = N - 1, ca = na - 2, cb = nb - 2;
+  if (id >= cm * ca * cb) return;
+  long a, b, m;
+  if (si == 1) { m = 1 + id % cm; const long r = id / cm; b = 1 + r % cb; a = 1 + r / cb; }
+  else { b = 1 + id % cb; const long r = id / cb; a = 1 + r % ca; m = 1 + r / ca; }
+  const double* src = in + a * sa + b * sb;
+  const int twoN = 2 * N;
+  int t = 0;
+  double acc = 0.0;
+  for (int jj = 1; jj < N; jj++) {
+    t += (int)m;
+    if (t >= twoN) t -= twoN;
+    acc += src[(long)jj * si] * tab[t];
+  }
+  out[a * sa + b * sb + m * si] = 2.0 * acc;
+}
+
+__global__ void k3_poisson_divide(double* ph, G3 g, double gv2) {
+  const long L = g.n[2] + 1, PL = (long)(g.n[1] + 1) * L;
+  const long cz = g.n[2] - 1, cy = g.n[1] - 1, cx = g.n[0] - 1;
+  const long id = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= cx * cy * cz) return;
+  const int k = 1 + (int)(id % cz), j = 1 + (int)((id / cz) % cy), i = 1 + (int)(id / (cz * cy));
+  const double lx = -(2.0 - 2.0 * cospi((double)i / g.n[0])) / (g.d[0] * g.d[0]);
+  const double ly = -(2.0 - 2.0 * cospi((double)j / g.n[1])) / (g.d[1] * g.d[1]);
+  const double lz = -(2.0 - 2.0 * cospi((double)k / g.n[2])) / (g.d[2] * g.d[2]);
+  const long p = i * PL + j * L + k;
+  // each inverse DST-I is the forward one over 2N
+  ph[p] = -ph[p] / kEps0 / (lx + ly + lz / gv2) / (8.0 * g.n[0] * g.n[1] * g.n[2]);
+}
+
+// phi = 0 on the six faces of the box (the transforms leave the deposited density there)
+__global__ void k3_zero_faces(double* ph, G3 g) {
+  const long L = g.n[2] + 1, PL = (long)(g.n[1] + 1) * L;
+  const long n = PL * (g.n[0] + 1);
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const int k = (int)(e % L), j = (int)((e / L) % (g.n[1] + 1)), i = (int)(e / PL);
+  if (i == 0 || i == g.n[0] || j == 0 || j == g.n[1] || k == 0 || k == g.n[2]) ph[e] = 0.0;
+}
+
+// mode 0: E_x, E_y, E_z added to E; mode 1: B_x, B_y added to B (from the earlier positions)
+template <class T>
+__global__ void k3_self_field_add(G3 g, T* E, T* B, const double* ph, double gv2, const double* acc, int mode) {
+  const long L = g.n[2] + 1, PL = (long)(g.n[1] + 1) * L;
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= PL * (g.n[0] + 1)) return;
+  const int k = (int)(e % L), j = (int)((e / L) % (g.n[1] + 1)), i = (int)(e / PL);
+  const long q = nid(g, i, j, k);
+  if (mode == 0) {
+    if (i < g.n[0]) E[q] += T(-(ph[e + PL] - ph[e]) / g.d[0]);
+    if (j < g.n[1]) E[g.cs + q] += T(-(ph[e + L] - ph[e]) / g.d[1]);
+    if (k < g.n[2]) E[2 * g.cs + q] += T(-(ph[e + 1] - ph[e]) / g.d[2] / gv2);
+  } else {
+    const double f = acc[2] / (kC * kC);
+    if (j < g.n[1] && k < g.n[2]) {
+      const double ey0 = -(ph[e + L] - ph[e]) / g.d[1], ey1 = -(ph[e + L + 1] - ph[e + 1]) / g.d[1];
+      B[q] += T(-f * 0.5 * (ey0 + ey1));
+    }
+    if (i < g.n[0] && k < g.n[2]) {
+      const double ex0 = -(ph[e + PL] - ph[e]) / g.d[0], ex1 = -(ph[e + PL + 1] - ph[e + 1]) / g.d[0];
+      B[g.cs + q] += T(f * 0.5 * (ex0 + ex1));
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1800,7 +1965,7 @@ struct Sim3 : Sim3Api {
       cudaStreamSynchronize(s);
     }
     // optional test beam
-    if (p->beam_n > 0 && p->beam_self) return fail(PIC_EINVAL, "3D: the self-consistent beam is 2D only");
+    if (p->beam_n > 0 && p->beam_self && !p->beam_w) return fail(PIC_EINVAL, "beam_self needs beam_w");
     if (p->beam_n > 0) {
       if (!p->beam_x || !p->beam_y || !p->beam_z || !p->beam_ux || !p->beam_uy || !p->beam_uz)
         return fail(PIC_EINVAL, "3D test beam needs x, y, z and the three momenta");
@@ -1822,6 +1987,15 @@ struct Sim3 : Sim3Api {
                                                         p->beam_z_plane_lab, gamma, beta, bacc);
       k3_beam_finish<T><<<nblk(n, 256), 256, 0, s>>>(bm, time_of(step), bacc);
       nl += 3;
+      if (p->beam_self) {
+        // self-consistent beam: weights (macro-particle counts) in the path's type
+        std::vector<T> wv(n);
+        for (int q = 0; q < n; q++) wv[q] = T(p->beam_w[q]);
+        bm.w = dal<T>(n);
+        if (!bm.w) return fail(PIC_ENOMEM, "allocation failed");
+        cudaMemcpyAsync(bm.w, wv.data(), sizeof(T) * n, cudaMemcpyHostToDevice, s);
+        bm.self = 1;
+      }
       cudaStreamSynchronize(s);
       dfree(lab);
       has_beam = true;
@@ -2036,7 +2210,8 @@ struct Sim3 : Sim3Api {
   int btd_get(pic_btd_out* o) override {
     if (!rout) return fail(PIC_ESTATE, "no lab-sample request");
     const size_t n = rz.size() * 6 * (size_t)(g.n[0] + 1) * (g.n[1] + 1);
-    cudaMemcpyAsync(o->data, rout, n * sizeof(T), o->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
+    if (o->data)
+      cudaMemcpyAsync(o->data, rout, n * sizeof(T), o->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
     long long filled = 0;
     for (size_t r = 0; r < rz.size(); r++) filled += rdone[2 * r] && rdone[2 * r + 1];
     if (o->done)
@@ -2080,6 +2255,61 @@ struct Sim3 : Sim3Api {
     nl++;
     cudaMemcpyAsync(dst, out_d, sizeof(double) * nn, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s);
     return cudaStreamSynchronize(s) == cudaSuccess ? PIC_OK : fail(PIC_ECUDA, "CUDA error in get_field");
+  }
+
+  // the frozen beam's self-field (Sec. 3.1.1, PR-27) solved on the device: E from the positions now, B_x, B_y
+  // from the positions half a step earlier (B^{n-1/2})
+  int beam_self_field() override {
+    if (!has_beam || !bm.self) return fail(PIC_ESTATE, "pic_beam_self_field: no self-consistent test beam");
+    if (g.n[0] < 2 || g.n[1] < 2 || g.n[2] < 2) return fail(PIC_EINVAL, "pic_beam_self_field: grid too small");
+    const long nn = nodes();
+    const long L = g.n[2] + 1, PL = (long)(g.n[1] + 1) * L;
+    double* a = dal<double>(nn);
+    double* b = dal<double>(nn);
+    double* tab[3];
+    for (int q = 0; q < 3; q++) tab[q] = dal<double>(2 * (size_t)g.n[q]);
+    if (!a || !b || !tab[0] || !tab[1] || !tab[2]) return fail(PIC_ENOMEM, "pic_beam_self_field: allocation failed");
+    for (int q = 0; q < 3; q++) {
+      std::vector<double> t(2 * (size_t)g.n[q]);
+      for (int m = 0; m < 2 * g.n[q]; m++) t[m] = std::sin(kPi * m / g.n[q]);
+      cudaMemcpyAsync(tab[q], t.data(), t.size() * 8, cudaMemcpyHostToDevice, s);
+    }
+    double v = 0.0;
+    cudaMemcpyAsync(&v, bacc + 2, sizeof(double), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    const double gv2 = 1.0 / (1.0 - (v / kC) * (v / kC));
+    auto dst = [&](const double* in, double* out, int axis) {
+      const int nx1 = g.n[0] + 1, ny1 = g.n[1] + 1, nz1 = g.n[2] + 1;
+      long cnt;
+      if (axis == 2) {
+        cnt = (long)(g.n[2] - 1) * (nx1 - 2) * (ny1 - 2);
+        k3_dst<<<nblk(cnt, 256), 256, 0, s>>>(in, out, tab[2], g.n[2], nx1, ny1, PL, L, 1);
+      } else if (axis == 1) {
+        cnt = (long)(g.n[1] - 1) * (nx1 - 2) * (nz1 - 2);
+        k3_dst<<<nblk(cnt, 256), 256, 0, s>>>(in, out, tab[1], g.n[1], nx1, nz1, PL, 1, L);
+      } else {
+        cnt = (long)(g.n[0] - 1) * (ny1 - 2) * (nz1 - 2);
+        k3_dst<<<nblk(cnt, 256), 256, 0, s>>>(in, out, tab[0], g.n[0], ny1, nz1, L, 1, PL);
+      }
+    };
+    const long ni = (long)(g.n[0] - 1) * (g.n[1] - 1) * (g.n[2] - 1);
+    for (int mode = 0; mode < 2; mode++) {
+      cudaMemsetAsync(a, 0, sizeof(double) * nn, s);
+      cudaMemsetAsync(b, 0, sizeof(double) * nn, s);
+      const int ord = cfg.shape_order;
+      k3_beam_rho<T><<<nblk(bm.n, 128), 128, 0, s>>>(g, bm, ord, mode == 0 ? 0.0 : -0.5 * g.dt, bacc, a);
+      dst(a, b, 2); dst(b, a, 1); dst(a, b, 0);
+      k3_poisson_divide<<<nblk(ni, 256), 256, 0, s>>>(b, g, gv2);
+      dst(b, a, 2); dst(a, b, 1); dst(b, a, 0);
+      k3_zero_faces<<<nblk(nn, 256), 256, 0, s>>>(a, g);
+      k3_self_field_add<T><<<nblk(nn, 256), 256, 0, s>>>(g, E, B, a, gv2, bacc, mode);
+      nl += 10;
+    }
+    cudaStreamSynchronize(s);
+    for (int q = 2; q >= 0; q--) dfree(tab[q]);
+    dfree(b);
+    dfree(a);
+    return cudaGetLastError() == cudaSuccess ? PIC_OK : fail(PIC_ECUDA, "CUDA error in pic_beam_self_field");
   }
 
   int set_field(int comp, const double* src) override {

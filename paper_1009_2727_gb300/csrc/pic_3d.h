@@ -28,6 +28,8 @@ struct Sim3Api {
   virtual int stats(pic_stats* o) = 0;
   virtual int64_t launches() const = 0;
   virtual int kernel_timing(int enable, int which, double* ms_total, int64_t* n) = 0;
+  // the frozen test beam's self-field added to the fields (3D only)
+  virtual int beam_self_field() { return PIC_EINVAL; }
   virtual int status() const = 0;
   virtual const std::string& error() const = 0;
 };

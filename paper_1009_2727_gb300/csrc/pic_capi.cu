@@ -1125,7 +1125,12 @@ int pic_get_rho_noalloc(pic_ctx* c, double* dst_device) {
 int pic_beam_self_field(pic_ctx* c) {
   if (!c) return PIC_EINVAL;
   if (c->status != PIC_OK) return c->status;
-  if (c->s3) return c->fail(PIC_EINVAL, "pic_beam_self_field: 2D contexts only");
+  if (c->s3) {
+    const int r = c->s3->beam_self_field();
+    if (r != PIC_OK) return c->fail(r, c->s3->error().empty() ? "pic_beam_self_field: 1D contexts have no test beam"
+                                                              : c->s3->error());
+    return PIC_OK;
+  }
   return DISPATCH(c, beam_self_field());
 }
 
