@@ -40,11 +40,19 @@ BYTES_PER_PARTICLE = {"mixed": 60, "fp64": 88}
 BYTES_PER_PARTICLE_3D = {"mixed": 76, "fp64": 104}
 # algorithmic bytes per cell-step of the field kernels (mixed, with Friedman): see the design notes
 BYTES_PER_CELL = {"mixed": 168, "fp64": 336}
-# measured DRAM bytes (read + write) per particle of one push launch, mixed precision, cubic shapes:
-# ncu dram__bytes_read.sum + dram__bytes_write.sum of k_push on the 2048 x 256 stage box, scaled to the
-# full box by its particle count; None for other configurations
-TRAFFIC_BYTES_PER_PARTICLE = {("mixed", 3): 58.87}
-TRAFFIC_LAYOUT = ((8, 16), 64)
+# measured DRAM bytes (read + write) per particle of one push launch (k_push), mixed precision, cubic shapes,
+# the Yee-located gather, for every layout the autotuner can return, keyed by (tile_x, tile_z, sort_every):
+# ncu dram__bytes_read.sum + dram__bytes_write.sum on the 2048 x 256 stage box (bench.py --layout-sweep, the
+# 2nd and 3rd push of each layout), scaled to the full box by its particle count. Below the 56 bytes of stored
+# state: the last writes of a launch are still in the 129 MB L2 when it ends.
+TRAFFIC_BYTES_PER_PARTICLE = {
+    (8, 8, 8): 49.63, (8, 8, 16): 49.41, (8, 8, 32): 49.56, (8, 8, 64): 49.38, (8, 16, 8): 49.34, (8, 16, 16): 49.42,
+    (8, 16, 32): 49.61, (8, 16, 64): 49.41, (8, 32, 8): 49.28, (8, 32, 16): 49.32, (8, 32, 32): 49.24, (8, 32, 64): 49.29,
+    (16, 8, 8): 49.44, (16, 8, 16): 49.25, (16, 8, 32): 49.33, (16, 8, 64): 49.28, (16, 16, 8): 49.16, (16, 16, 16): 49.24,
+    (16, 16, 32): 49.18, (16, 16, 64): 49.21, (16, 32, 8): 49.24, (16, 32, 16): 49.31, (16, 32, 32): 49.25, (16, 32, 64): 49.23,
+    (32, 8, 8): 49.15, (32, 8, 16): 49.23, (32, 8, 32): 49.16, (32, 8, 64): 49.21, (32, 16, 8): 49.2, (32, 16, 16): 49.31,
+    (32, 16, 32): 49.34, (32, 16, 64): 49.19, (32, 32, 8): 48.94, (32, 32, 16): 48.88, (32, 32, 32): 48.86, (32, 32, 64): 48.81,
+}
 # 3D: ncu dram bytes of k3_push_tiles on the 256 x 128 x 128 box (198.06 MB for 2,356,608 electrons), scaled
 # to the full box by its particle count
 TRAFFIC_BYTES_PER_PARTICLE_3D = {("mixed", 3): 84.0}
@@ -290,13 +298,30 @@ def run_ensemble(args):
     n0 = sum(m.stats()["n_electrons"] for m in ens.members)
     stream = torch.cuda.current_stream()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    l0 = ens.launches()
     torch.cuda.synchronize()
     ev0.record(stream)
     ens.step(args.steps)
     ev1.record(stream)
     torch.cuda.synchronize()
+    clocks = sampler.stop()
     ms = ev0.elapsed_time(ev1)
+    launches = ens.launches() - l0
     ens.sync()
+    # batched mode: the same steps with the kernels launched directly instead of replayed from graphs
+    direct_ms = None
+    if ens.batched:
+        ens.use_graphs(False)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        ens.step(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        direct_ms = ev0.elapsed_time(ev1) / args.steps
+        ens.use_graphs(True)
+        ens.sync()
     # host time to enqueue one ensemble step on idle queues (does the host or the GPU set the pace?)
     enq = []
     for _ in range(5):
@@ -308,6 +333,7 @@ def run_ensemble(args):
     torch.cuda.synchronize()
     n1 = sum(m.stats()["n_electrons"] for m in ens.members)
     cells = sum(w["nx"] * w["nz"] for w in ws)
+    ens_batched = ens.batched
     # the same runs one at a time, each on the caller's stream
     seq_ms = 0.0
     ens.close()
@@ -331,6 +357,9 @@ def run_ensemble(args):
                        "cells": cells, "electrons": int(0.5 * (n0 + n1))},
             "sequential_ms_per_step": seq_ms / args.steps, "speedup_vs_sequential": seq_ms / ms,
             "host_enqueue_ms_per_step": enqueue_ms,
+            "batched": bool(ens_batched), "gpu_launches": int(launches),
+            "launches_per_step": launches / args.steps, "direct_launch_ms_per_step": direct_ms,
+            "clocks": clocks,
             "autotuned": args.tune or None, "setup_s": t_tune,
             "ensemble_trials": ens_tuned[0].get("trials") if args.tune == "ensemble" else None,
             "tiles": sorted({(t["tile"][0], t["tile"][1], t["sort_every"]) for t in ens_tuned}) if args.tune else None}
@@ -824,17 +853,17 @@ def main():
     bpp = (BYTES_PER_PARTICLE_3D if three else BYTES_PER_PARTICLE)[args.precision]
     push_avg_ms = push_ms / max(push_n, 1)
     achieved = n_avg * bpp / (push_avg_ms * 1e-3) / 1e9
-    tpp = (TRAFFIC_BYTES_PER_PARTICLE_3D if three else TRAFFIC_BYTES_PER_PARTICLE).get((args.precision, args.order))
-    if not three and (not tuned or (tuple(tuned["tile"]), tuned["sort_every"]) != TRAFFIC_LAYOUT
-                      or args.gather != "energy"):
-        tpp = None     # the counters were taken with the tuned layout and the Yee-located gather
-    if three and args.gather != "energy":
-        tpp = None
+    if three:
+        tpp = TRAFFIC_BYTES_PER_PARTICLE_3D.get((args.precision, args.order)) if args.gather == "energy" else None
+    else:
+        lay = (tuple(tuned["tile"]) + (tuned["sort_every"],)) if tuned else None
+        ok = args.precision == "mixed" and args.order == 3 and args.gather == "energy"
+        tpp = TRAFFIC_BYTES_PER_PARTICLE.get(lay) if ok and lay else None
     roof = {"kernel": "k3_push_tiles (3D gather + Boris + Esirkepov)" if three else "k_push (gather + Boris + Esirkepov)",
             "bound": "hbm", "achieved": achieved, "peak": peak,
             "unit": "GB/s", "frac": achieved / peak, "traffic": tpp * n_avg if tpp else None,
             "traffic_source": ("ncu dram bytes of k3_push_tiles, 256 x 128 x 128 box, scaled by particles" if three
-                               else "ncu dram bytes of k_push, 2048 x 256 box, tuned layout, scaled by particles") if tpp else None,
+                               else "ncu dram bytes of k_push, 2048 x 256 box, this layout, scaled by particles") if tpp else None,
             "note": ("3D push on sorted 4x4x16-cell tiles with shared-memory windows: latency-bound at a quarter "
                      "occupancy (ncu: 35% issue slots, 44% L1/shared, 2% DRAM)" if three else
                      "at cubic order the push is bound by instruction issue "

@@ -352,14 +352,27 @@ int pic_autotune(const pic_config* cfg, const pic_plasma* plasma, const pic_lase
 /* ---- Ensemble of independent runs (no counterpart in the paper) ----
  * n runs of uneven size (each its own pic_config, pic_plasma and pic_laser;
  * lasers may be NULL, and a laser with lambda0 <= 0 means none) advanced together.
- * Every run is an ordinary context on its own non-blocking CUDA stream, created
- * and owned by the ensemble; pic_ensemble_step enqueues one step of every run
- * before the next, so that the runs execute concurrently. The runs start after
- * the work already on cuda_stream, and cuda_stream waits for all of them when
- * pic_ensemble_step returns (pass NULL to skip both). pic_ensemble_member gives a
- * run's context for the accessors (pic_get_field, pic_get_stats, ...); it stays
- * owned by the ensemble. Errors: PIC_EINVAL for bad arguments, else the first
- * failing call's status; pic_ensemble_sync returns the first run's error. */
+ * Every run is an ordinary context created and owned by the ensemble.
+ *  - Batched mode (2D runs with plasma, the Yee-located gather, no test beam, no
+ *    moving window, one precision, shape order, solver family, damping, filter
+ *    and particle layout; at most 512 runs): all runs share one non-blocking
+ *    stream and an ensemble step is one launch per kernel class over all runs
+ *    (Faraday, gather filter, push, its global pass, antenna, ion current,
+ *    Ampere, inflow, counts; the runs' sorts every sort_every steps), the per-run
+ *    arguments of the step in one block of device memory filled from the same
+ *    host decisions as pic_step. From the third step on, each step replays a
+ *    CUDA graph of those launches (pic_ensemble_use_graphs(ens, 0) launches them
+ *    directly instead). A run that gains lab samples afterwards makes
+ *    pic_ensemble_step fail with PIC_ESTATE.
+ *  - Otherwise every run has its own non-blocking stream and pic_ensemble_step
+ *    enqueues one step of every run before the next, so that they run
+ *    concurrently.
+ * The runs start after the work already on cuda_stream, and cuda_stream waits
+ * for all of them when pic_ensemble_step returns (pass NULL to skip both).
+ * pic_ensemble_member gives a run's context for the accessors (pic_get_field,
+ * pic_get_stats, ...); it stays owned by the ensemble. Errors: PIC_EINVAL for bad
+ * arguments, else the first failing call's status; pic_ensemble_sync returns the
+ * first run's error. */
 typedef struct pic_ens pic_ens;
 int pic_ensemble_create(int n, const pic_config* cfgs, const pic_plasma* plasmas, const pic_laser* lasers,
                         pic_alloc_fn alloc, pic_free_fn free_fn, void* alloc_user, void* cuda_stream,
@@ -367,6 +380,12 @@ int pic_ensemble_create(int n, const pic_config* cfgs, const pic_plasma* plasmas
 int pic_ensemble_step(pic_ens* ens, int nsteps);
 int pic_ensemble_sync(pic_ens* ens);
 int pic_ensemble_size(pic_ens* ens);
+/* 1 when the ensemble steps in batched mode, else 0 */
+int pic_ensemble_batched(pic_ens* ens);
+/* batched mode: replay each step from a CUDA graph (1, the default) or launch directly (0) */
+int pic_ensemble_use_graphs(pic_ens* ens, int enable);
+/* kernel launches enqueued so far by the ensemble's steps (bench accounting) */
+int64_t pic_ensemble_launches(pic_ens* ens);
 pic_ctx* pic_ensemble_member(pic_ens* ens, int index);
 int pic_ensemble_free(pic_ens* ens);
 /* The particle tile and sort cadence for a whole ensemble: each candidate layout (tiles 8x32, 8x16, 16x16,

@@ -33,7 +33,8 @@ EXPORTS = ("pic_init", "pic_load_plasma", "pic_inject_laser", "pic_step", "pic_s
            "pic_ensemble_member", "pic_ensemble_free", "pic_ensemble_autotune",
            "pic_mlp_create", "pic_mlp_free", "pic_mlp_param_count", "pic_mlp_get_params", "pic_mlp_set_params",
            "pic_mlp_infer", "pic_mlp_grad", "pic_mlp_train", "pic_mlp_use_tensor_cores", "pic_mlp_status",
-           "pic_measure_fp32_peak", "pic_beam_self_field")
+           "pic_measure_fp32_peak", "pic_beam_self_field", "pic_ensemble_batched", "pic_ensemble_use_graphs",
+           "pic_ensemble_launches")
 NOALLOC_MAX_NZ = 16384
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -197,5 +198,9 @@ def load(build_if_missing: bool = True):
                                    ctypes.c_int, ALLOC_FN, FREE_FN, vp, vp, ctypes.POINTER(PicTuneResult)]
         L.pic_measure_fp32_peak.argtypes = [_D, _D]
         L.pic_beam_self_field.argtypes = [vp]
+        L.pic_ensemble_batched.argtypes = [vp]
+        L.pic_ensemble_use_graphs.argtypes = [vp, ctypes.c_int]
+        L.pic_ensemble_launches.argtypes = [vp]
+        L.pic_ensemble_launches.restype = ctypes.c_int64
         _lib = L
         return L

@@ -549,7 +549,64 @@ __global__ void k_shift_particles(GridP g, Particles<T> p, const Ctrl* ctrl, int
   p.cell[j] = pack_cell(cell_x(c), (cell_z(c) - sh) & 0xffff);
 }
 
+// batched antenna (each run's blocks also clear its ion-column sums for the next kernel)
+template <class T>
+__global__ void k_antenna_batch(const StepArgs<T>* a, const int* off, int nruns) {
+  __shared__ int s_r;
+  if (threadIdx.x == 0) s_r = batch_run(off, nruns, blockIdx.x);
+  __syncthreads();
+  const StepArgs<T>& A = a[s_r];
+  const int lb = blockIdx.x - off[s_r], nb = off[s_r + 1] - off[s_r];
+  if (A.ion_on)
+    for (int k = lb * blockDim.x + threadIdx.x; k <= A.g.nz; k += nb * blockDim.x) A.ion_C[k] = 0.0;
+  if (!A.ant_on) return;
+  const int i = lb * blockDim.x + threadIdx.x;
+  if (i > A.g.nx) return;
+  const double kx = A.ast.amp * A.ant_xs[i];
+  if (kx == 0.0) return;
+  T* Jy = A.f.J[1];
+#pragma unroll
+  for (int j = 0; j < 8; j++) {
+    const int k = A.ast.k0 + j;
+    if (A.ast.wz[j] != 0.0 && k >= 0 && k <= A.g.nz) Jy[(long)i * A.g.ld + k] += T(kx * A.ast.wz[j]);
+  }
+}
+
+// batched rigid-ion column current: rows [ion_mlo, ion_mhi) of each run, one thread per row
+template <class T>
+__global__ void k_ion_current_batch(const StepArgs<T>* a, const int* off, int nruns) {
+  __shared__ int s_r;
+  if (threadIdx.x == 0) s_r = batch_run(off, nruns, blockIdx.x);
+  __syncthreads();
+  const StepArgs<T>& A = a[s_r];
+  if (!A.ion_on) return;
+  const long long m = A.ion_mlo + (long long)(blockIdx.x - off[s_r]) * blockDim.x + threadIdx.x;
+  if (m >= A.ion_mhi) return;
+  const GridP& g = A.g;
+  const InjectP& ip = A.ip;
+  const double wfac = g.dx * g.dz / (double)(ip.ppc_x * ip.ppc_z);
+  const double zlat = (m + 0.5) * ip.h;
+  const double nm = ip.gamma * lab_density_d(ip, ip.gamma * zlat) * wfac;
+  if (nm == 0.0) return;
+  const double Z0 = (zlat - ip.beta * kC * A.ion_t0 - g.z0) / g.dz;
+  const double Z1 = (zlat - ip.beta * kC * A.ion_t1 - g.z0) / g.dz;
+  const int ord = A.ion_order;
+  const int o = ord == 3 ? 1 : 0, ng = ord == 3 ? 4 : 2;
+  const int klo = (int)floor(fmin(Z0, Z1)) - o;
+  const int khi = (int)floor(fmax(Z0, Z1)) - o + ng - 2;
+  for (int k = max(klo, 0); k <= min(khi, g.nz); k++) {
+    const double d = cum_weight(ord, Z1, k) - cum_weight(ord, Z0, k);
+    if (d != 0.0) atomicAdd(&A.ion_C[k], nm * d);
+  }
+}
+
 }  // namespace
+
+template <class T>
+void launch_antenna_ion_batch(const StepArgs<T>* a, const BatchGrid& bg, bool any_ion, cudaStream_t s) {
+  k_antenna_batch<T><<<bg.ant_blocks, 128, 0, s>>>(a, bg.ant_off, bg.nruns);
+  if (any_ion) k_ion_current_batch<T><<<bg.ion_blocks, 256, 0, s>>>(a, bg.ion_off, bg.nruns);
+}
 
 // ---------------------------------------------------------------------------
 // Charge density without device allocation: the ion row density R(k) goes to
@@ -844,6 +901,7 @@ void launch_shift_particles(const GridP& g, Particles<T> p, const Ctrl* ctrl, in
   template void launch_antenna<T>(const GridP&, T*, const double*, const AntennaStep&, cudaStream_t);           \
   template void launch_beam_init<T>(Beam<T>, const double*, const double*, const double*, const double*,          \
                                     const double*, double, double, double, double, double, double*, cudaStream_t); \
+  template void launch_antenna_ion_batch<T>(const StepArgs<T>*, const BatchGrid&, bool, cudaStream_t);          \
   template void launch_beam_self_field<T>(const GridP&, const FieldPtrs<T>&, Beam<T>, int, const double*, double, \
                                           double*, double*, double*, double*, cudaStream_t);                    \
   template void launch_beam_push<T>(const GridP&, const FieldPtrs<T>&, Beam<T>, int, double, double, int,         \

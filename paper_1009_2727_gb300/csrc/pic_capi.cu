@@ -12,6 +12,7 @@
 
 #include "../../include/pic.h"
 #include "pic_3d.h"
+#include "pic_batch.h"
 #include "pic_common.cuh"
 
 namespace picgb {
@@ -680,6 +681,103 @@ struct Sim : SimBase {
     return PIC_OK;
   }
 
+  // ---- batched (ensemble) stepping ---------------------------------------------------------------------
+  // A run the batched ensemble step carries: plasma loaded, the Yee-located gather, no test beam, no lab
+  // samples, no moving window (those steps keep the per-run launches).
+  bool batchable() const {
+    const pic_config& cf = c->cfg;
+    return loaded && cap > 0 && !nodal && beam.n == 0 && nrows == 0 && !cf.moving_window && tmaps.ok;
+  }
+  // upper bounds of the per-step work of the batched kernels that do not run a fixed grid
+  int inj_xblocks() const { return (g.gx_hi - g.gx_lo + ip.xblock - 1) / ip.xblock; }
+  int inj_rblocks_max() const { return (int)std::ceil(c->hg.beta * kC * g.dt / ip.h) / 4 + 2; }
+  long long ion_rows_max() const { return (long long)(g.gz_hi - g.gz_lo + 8) * pl.ppc_z + 16; }
+
+  // The host decisions of one step, in the order of one_step, written into the run's argument block of a
+  // batched launch instead of launching; then the step's bookkeeping. sort_after: the run sorts after this
+  // step (its sort is launched after the batched kernels). Returns PIC_OK or the error of a step that the
+  // batched kernels cannot carry.
+  int plan_step(StepArgs<T>& a, bool& sort_after) {
+    const pic_config& cf = c->cfg;
+    const HostGeom& h = c->hg;
+    const double tn = time_of(step), tn1 = time_of(step + 1);
+    set_frame(step);
+    set_ptrs_for_step();
+    a.g = g;
+    a.f = f;
+    a.pt = pt;
+    a.far = faraday_coefs<T>(h.a2, h.b2, cf.theta);
+    a.ft = filter_taps<T>(fs);
+    a.filt_gather = filt_gather;
+    a.filt_J = filt_J;
+    a.tm = tmaps;
+    a.mapE = tmaps.Ebase[0] == (const void*)f.E[0] ? 0 : 1;
+    a.mapJ = tmaps.Jbase[0] == (const void*)f.J[0] ? 0 : 1;
+    field_tiles(g, a.tiles_k, a.tiles_i);
+    // ion rows live during this step: those inside the particle domain at t^n
+    long long mlo = std::max(row_first, (long long)std::ceil((zlo_prev + h.beta * kC * tn) / ip.h - 0.5));
+    if (step == 0) mlo = row_first;
+    int fr1_sz;
+    float fr1_fz;
+    frame_of(frame_shift(step + 1), fr1_sz, fr1_fz);
+    a.pc = push_const(g, -kQe, kMe, c->hg.gamma, fr1_sz, fr1_fz, (pairs && ions) ? 1 : 0, (int)mlo);
+    a.p = P;
+    a.chunks = chunks;
+    a.ctrl = ctrl;
+    a.pd = pdef;
+    a.push_on = 1;
+    set_frame(step + 1);
+    a.ant_on = has_laser && antenna_step(tn, tn1, a.ast);
+    a.ant_xs = ant_xs;
+    const bool column = ions && loaded && !pairs;
+    a.ion_on = column;
+    a.ion_order = cf.shape_order;
+    a.ion_mlo = mlo;
+    a.ion_mhi = row_next;
+    a.ion_t0 = tn;
+    a.ion_t1 = tn1;
+    a.ion_coef = column ? -kQe / (g.dx * g.dt) : 0.0;
+    a.ion_C = ion_C;
+    a.ion_x = ion_x;
+    if (column && row_next - mlo > ion_rows_max()) return c->fail(PIC_EOVERFLOW, "batched step: ion rows above bound");
+    for (int q = 0; q < 3; q++) {
+      std::swap(f.E[q], f.Eo[q]);
+      std::swap(f.J[q], f.Jn[q]);
+      if (friedman) std::swap(f.Eb[q], f.Ebn[q]);
+    }
+    set_ptrs_for_step();
+    zlo_prev = zlo();
+    a.inj_on = 0;
+    a.ip = ip;
+    if (loaded && pl.n0 > 0.0) {
+      long long m_end = rows_inside(tn1);
+      long long ra = row_next, rb = m_end;
+      if (rb > row_next) row_next = rb;
+      while (ra < rb && !row_has_density(ra)) ra++;
+      while (rb > ra && !row_has_density(rb - 1)) rb--;
+      if (rb > ra) {
+        long long add = (rb - ra) * (long long)ip.nxl;
+        refresh_count_bound(add);
+        if (count_ub + add > cap) return c->fail(PIC_EOVERFLOW, "particle capacity exceeded");
+        if (!ids_fit(ra, rb)) return c->fail(PIC_EOVERFLOW, "plasma rows exceed the 32-bit particle id space");
+        ip.m_beg = ra; ip.m_end = rb; ip.t = tn1; ip.rblock = 4;
+        const int rblocks = (int)((rb - ra + ip.rblock - 1) / ip.rblock);
+        if (rblocks > inj_rblocks_max()) return c->fail(PIC_EOVERFLOW, "batched step: inflow rows above bound");
+        a.ip = ip;
+        a.inj_on = 1;
+        a.inj_xblocks = inj_xblocks();
+        a.cap = cap;
+        a.chunk_cap = chunk_cap;
+        a.add_count = (int)add;
+        a.add_chunks = a.inj_xblocks * rblocks;
+        count_ub += add;
+      }
+    }
+    step++;
+    sort_after = loaded && cap > 0 && step % sort_every == 0;
+    return PIC_OK;
+  }
+
   int run(int n) {
     for (int i = 0; i < n; i++) {
       int r = one_step();
@@ -942,7 +1040,197 @@ Sim<T>* S(pic_ctx* c) { return static_cast<Sim<T>*>(c->sim.get()); }
 #define DISPATCH(ctx, expr)                                                  \
   ((ctx)->cfg.precision == PIC_FP64 ? S<double>(ctx)->expr : S<float>(ctx)->expr)
 
+// The batched ensemble step: each run's host decisions fill its argument block (Sim::plan_step), one
+// host-to-device copy moves all blocks, and one launch per kernel class advances every run. The argument
+// blocks are double-buffered (the host fills one slot while the GPU may still read the other), and each
+// slot's sequence can be captured once into a CUDA graph and replayed every step: the kernels read
+// everything that changes between steps (pointers of the swapped buffers, frame shift, antenna factor,
+// inflow rows) from the argument blocks, so the graph's launches never change.
+template <class T>
+struct BatchImpl : Batch {
+  std::vector<Sim<T>*> sims;
+  int n = 0;
+  cudaStream_t s = nullptr;
+  StepArgs<T>* dA[2] = {nullptr, nullptr};
+  StepArgs<T>* hA[2] = {nullptr, nullptr};
+  cudaEvent_t done[2] = {nullptr, nullptr};
+  bool used[2] = {false, false};
+  cudaGraphExec_t gx[2] = {nullptr, nullptr};
+  bool graphs = true;
+  BatchGrid bg{};
+  int order = 3, pt_taps = 0, push_grid = 0, smem_nodes = 0, tile_z = 0;
+  bool friedman = false, ck = false, filt_gather = false, filt_J = false, any_ion = false;
+  size_t filt_smem = 0, amp_smem = 0;
+  int64_t nl = 0, nstep = 0;
+
+  ~BatchImpl() override {
+    if (s) cudaStreamSynchronize(s);
+    for (int q = 0; q < 2; q++) {
+      if (gx[q]) cudaGraphExecDestroy(gx[q]);
+      if (done[q]) cudaEventDestroy(done[q]);
+      if (hA[q]) cudaFreeHost(hA[q]);
+    }
+  }
+
+  int64_t launches() const override { return nl; }
+  void use_graphs(bool on) override { graphs = on; }
+
+  bool init(pic_ctx* const* runs, int nr, cudaStream_t st, std::string* why) {
+    n = nr;
+    s = st;
+    if (n < 1 || n > 512) { *why = "ensemble size outside 1..512"; return false; }
+    const pic_config& c0 = runs[0]->cfg;
+    for (int r = 0; r < n; r++) {
+      pic_ctx* c = runs[r];
+      if (c->s3 || !c->sim || c->stream != st) { *why = "3D, 1D or differently streamed run"; return false; }
+      const pic_config& cf = c->cfg;
+      if (cf.precision != c0.precision || cf.shape_order != c0.shape_order) { *why = "mixed precisions or orders"; return false; }
+      Sim<T>* m = S<T>(c);
+      if (!m->batchable()) { *why = "run with a test beam, lab samples, moving window or node gather"; return false; }
+      sims.push_back(m);
+    }
+    Sim<T>* m0 = sims[0];
+    order = c0.shape_order;
+    friedman = m0->friedman;
+    ck = runs[0]->hg.b2 != 0.0;
+    filt_gather = m0->filt_gather;
+    filt_J = m0->filt_J;
+    const FilterTaps<T> ft0 = filter_taps<T>(m0->fs);
+    pt_taps = filter_taps_class<T>(ft0);
+    smem_nodes = m0->smem_nodes;
+    tile_z = m0->sb.tz;
+    push_grid = m0->push_grid;
+    filt_smem = tile_smem_bytes<T>(m0->tmaps, filt_gather ? ft0.H : 0);
+    amp_smem = tile_smem_bytes<T>(m0->tmaps, filt_J ? ft0.H : 0);
+    std::vector<int> tile_off(n + 1), ion_off(n + 1), inj_off(n + 1), ant_off(n + 1);
+    for (int r = 0; r < n; r++) {
+      Sim<T>* m = sims[r];
+      const bool ck_r = runs[r]->hg.b2 != 0.0;
+      const FilterTaps<T> ft = filter_taps<T>(m->fs);
+      if (m->friedman != friedman || ck_r != ck || m->filt_gather != filt_gather || m->filt_J != filt_J ||
+          filter_taps_class<T>(ft) != pt_taps || ft.H != ft0.H || m->smem_nodes != smem_nodes ||
+          m->sb.tz != tile_z || m->tmaps.H != m0->tmaps.H) {
+        *why = "runs differ in solver family, damping, filter or particle tile";
+        return false;
+      }
+      int tk, ti;
+      field_tiles(m->g, tk, ti);
+      tile_off[r + 1] = tile_off[r] + tk * ti;
+      const bool column = m->ions && !m->pairs;
+      any_ion = any_ion || column;
+      ion_off[r + 1] = ion_off[r] + (column ? (int)((m->ion_rows_max() + 255) / 256) : 0);
+      inj_off[r + 1] = inj_off[r] + m->inj_xblocks() * m->inj_rblocks_max();
+      ant_off[r + 1] = ant_off[r] + (std::max(m->g.nx, m->g.nz) + 1 + 127) / 128;
+    }
+    bg.nruns = n;
+    bg.tiles = tile_off[n];
+    bg.ion_blocks = ion_off[n];
+    bg.inj_blocks = inj_off[n];
+    bg.ant_blocks = ant_off[n];
+    pic_ctx* c0x = runs[0];
+    int* off = (int*)c0x->dalloc(sizeof(int) * 4 * (n + 1) + 64);
+    bg.push_counter = (int*)c0x->dalloc(sizeof(int));
+    for (int q = 0; q < 2; q++) dA[q] = (StepArgs<T>*)c0x->dalloc(sizeof(StepArgs<T>) * n);
+    if (!off || !bg.push_counter || !dA[0] || !dA[1]) { *why = "batch allocation failed"; return false; }
+    std::vector<int> all;
+    for (auto* v : {&tile_off, &ion_off, &inj_off, &ant_off}) all.insert(all.end(), v->begin(), v->end());
+    cudaMemcpyAsync(off, all.data(), sizeof(int) * all.size(), cudaMemcpyHostToDevice, s);
+    bg.tile_off = off;
+    bg.ion_off = off + (n + 1);
+    bg.inj_off = off + 2 * (n + 1);
+    bg.ant_off = off + 3 * (n + 1);
+    for (int q = 0; q < 2; q++) {
+      if (cudaMallocHost(&hA[q], sizeof(StepArgs<T>) * n) != cudaSuccess ||
+          cudaEventCreateWithFlags(&done[q], cudaEventDisableTiming) != cudaSuccess) {
+        *why = "pinned buffer or event creation failed";
+        return false;
+      }
+      std::memset(static_cast<void*>(hA[q]), 0, sizeof(StepArgs<T>) * n);
+    }
+    cudaStreamSynchronize(s);
+    return cudaGetLastError() == cudaSuccess;
+  }
+
+  void enqueue(int q) {
+    cudaMemcpyAsync(dA[q], hA[q], sizeof(StepArgs<T>) * n, cudaMemcpyHostToDevice, s);
+    launch_faraday_filter_batch<T>(dA[q], bg, friedman, ck, pt_taps, filt_gather, filt_smem, s);
+    launch_push_batch<T>(dA[q], bg, order, push_grid, smem_nodes, tile_z, s);
+    launch_antenna_ion_batch<T>(dA[q], bg, any_ion, s);
+    launch_ampere_batch<T>(dA[q], bg, filt_J, pt_taps, amp_smem, s);
+    launch_inject_batch<T>(dA[q], bg, s);
+  }
+  static int kernels_per_step(bool filt, bool ion) { return 1 + (filt ? 1 : 0) + 3 + 1 + (ion ? 1 : 0) + 1 + 2; }
+
+  int step(int nsteps) override {
+    for (int k = 0; k < nsteps; k++) {
+      const int q = (int)(nstep & 1);
+      // the slot's previous use (its host-to-device copy) must be over before its host buffer is refilled
+      if (used[q]) cudaEventSynchronize(done[q]);
+      std::vector<int> sorts;
+      for (int r = 0; r < n; r++) {
+        bool srt = false;
+        if (!sims[r]->batchable()) return sims[r]->c->fail(PIC_ESTATE, "batched ensemble: a run gained lab samples");
+        const int rc = sims[r]->plan_step(hA[q][r], srt);
+        if (rc != PIC_OK) return rc;
+        if (srt) sorts.push_back(r);
+      }
+      if (graphs) {
+        if (!gx[q]) {
+          if (nstep < 2) {
+            // the first step of each slot runs uncaptured (function attributes set, modules loaded)
+            enqueue(q);
+          } else {
+            cudaGraph_t gr = nullptr;
+            if (cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed) != cudaSuccess) return PIC_ECUDA;
+            enqueue(q);
+            if (cudaStreamEndCapture(s, &gr) != cudaSuccess || !gr) return PIC_ECUDA;
+            const cudaError_t e = cudaGraphInstantiate(&gx[q], gr, 0);
+            cudaGraphDestroy(gr);
+            if (e != cudaSuccess) return PIC_ECUDA;
+          }
+        }
+        if (gx[q] && cudaGraphLaunch(gx[q], s) != cudaSuccess) return PIC_ECUDA;
+      } else {
+        enqueue(q);
+      }
+      cudaEventRecord(done[q], s);
+      used[q] = true;
+      nl += kernels_per_step(filt_gather, any_ion);
+      for (int r : sorts) {
+        sims[r]->do_sort();
+        nl += 8;
+      }
+      nstep++;
+    }
+    return cudaGetLastError() == cudaSuccess ? PIC_OK : PIC_ECUDA;
+  }
+};
+
 }  // namespace
+
+Batch* picgb::make_batch(pic_ctx* const* runs, int n, cudaStream_t s, std::string* why) {
+  if (n < 1 || !runs[0]->sim) {
+    *why = "no 2D runs";
+    return nullptr;
+  }
+  Batch* b = nullptr;
+  bool ok = false;
+  if (runs[0]->cfg.precision == PIC_FP64) {
+    auto* x = new BatchImpl<double>();
+    ok = x->init(runs, n, s, why);
+    b = x;
+  } else {
+    auto* x = new BatchImpl<float>();
+    ok = x->init(runs, n, s, why);
+    b = x;
+  }
+  if (!ok) {
+    delete b;
+    return nullptr;
+  }
+  return b;
+}
+
 
 extern "C" {
 

@@ -195,6 +195,35 @@ struct Ctrl {
   double red[8];      // reduction scratch
 };
 
+// Constants of the particle push (one run, one step).
+struct PushConst {
+  double dx, dz, dt, z0;            // FP64 path
+  double xlo, xhi, zlo, zhi;        // FP64 path removal bounds [m]
+  int cx_lo, cx_hi, cz_lo, cz_hi;   // mixed path removal bounds [cells, hi exclusive]
+  float dtdx, dtdz;                 // mixed path
+  double qm_half;                   // q dt/(2m)
+  double kx, kz, ky;                // deposit: -q/(dz dt), -q/(dx dt), q/(dx dz)
+  float qm_half_f, kx_f, kz_f, ky_f;  // the same in FP32 for the mixed path
+  // mixed path: the plasma drift momentum u0 = -gamma beta c (FP32) and gamma0; the
+  // frame shift (GridP::fr_sz) at t^n and t^{n+1}
+  float u0z_f, g0_f, g0sq_f;
+  int fr0_sz, fr1_sz;
+  float fr0_fz, fr1_fz;
+  // mixed path with lab-fixed ions: each electron carries the ion of its lattice
+  // site (pairs; power-of-two particles per cell); ion rows below mlo have left
+  // the particle domain; the stored id is (row << kb) | column
+  int pairs, mlo;
+  int kb, lpx, lpz, gx_lo, z0_cells;
+};
+
+// Coefficients of the Faraday update (Eq. Faraday_Friedman, reduced to 2D).
+template <class T>
+struct FarK {
+  T a2, b2;          // 2D reduced coefficients: alpha + 2 beta, beta + 2 gamma
+  T c1, c2, c3;      // E_eff = c1 E^n + c2 E^{n-1} + c3 E-bar
+  T h1, h2;          // E-bar' = h1 E^n + h2 E-bar
+};
+
 // ---------------------------------------------------------------------------
 // B-spline weights from the fractional offset t in [0,1) of a position above
 // node f: order 3 -> nodes f-1..f+2, order 1 -> nodes f, f+1.
@@ -354,5 +383,97 @@ template <class T>
 int launch_rho_noalloc(const GridP& g, Particles<T> p, const Ctrl* ctrl, int cap, int order, bool ions,
                        long long mlo, long long mhi, double t, const InjectP& ip, const double* ion_x, double* dst,
                        cudaStream_t s, cudaError_t* why, int* kernels);
+
+// ---------------------------------------------------------------------------
+// Batched step of an ensemble: every run's arguments for one step in one block of device memory, and one
+// launch per kernel class over all runs (blocks partitioned among the runs; the push pulls (run, chunk)
+// pairs from one queue). The host fills the blocks from the same decisions as a single run's step.
+template <class T>
+struct StepArgs {
+  TileMaps tm;                 // TMA descriptors (first: aligned as CUtensorMap requires)
+  int mapE, mapJ;              // which E / J descriptor is current
+  GridP g;
+  FieldPtrs<T> f;
+  PmlTabs pt;
+  FarK<T> far;
+  FilterTaps<T> ft;
+  int filt_gather, filt_J;
+  int tiles_k, tiles_i;        // tile grid of the field kernels
+  // push
+  PushConst pc;
+  Particles<T> p;
+  Chunk* chunks;
+  Ctrl* ctrl;
+  PushDefer pd;
+  int push_on;
+  // antenna (K_y on rows k0..k0+7)
+  int ant_on;
+  AntennaStep ast;
+  const double* ant_xs;
+  // rigid-ion column current (runs without electron-ion pairs)
+  int ion_on, ion_order;
+  long long ion_mlo, ion_mhi;
+  double ion_t0, ion_t1, ion_coef;
+  double* ion_C;
+  const double* ion_x;
+  // plasma rows entering through the +z plane
+  int inj_on, inj_xblocks;
+  InjectP ip;
+  int cap, chunk_cap, add_count, add_chunks;
+};
+
+// run of a block of a batched launch: the last r with off[r] <= b (off: nruns + 1 prefix sums)
+__device__ __forceinline__ int batch_run(const int* off, int nruns, int b) {
+  int lo = 0, hi = nruns - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// per-run block offsets of the batched launches (prefix sums, nruns + 1 entries each, in device memory)
+struct BatchGrid {
+  const int* tile_off;     // field-kernel tiles
+  const int* ion_off;      // ion-column blocks
+  const int* inj_off;      // injection blocks
+  const int* ant_off;      // antenna blocks
+  int nruns, tiles, ion_blocks, inj_blocks, ant_blocks;
+  int* push_counter;       // the push's (run, chunk) queue head
+};
+// the push's constants for one step (q, m: charge and mass; fr1: frame shift at t^{n+1}; pairs, mlo: the
+// electron-ion pairs and the first live ion row)
+PushConst push_const(const GridP& g, double q, double m, double gamma_b, int fr1_sz, float fr1_fz, int pairs,
+                     int mlo);
+// tile grid of the field kernels (tiles along z, along x) and their Faraday coefficients
+void field_tiles(const GridP& g, int& tiles_k, int& tiles_i);
+template <class T>
+FarK<T> faraday_coefs(double a2, double b2, double theta);
+// Faraday (+ Friedman, PML) and the gather-field filter over every run's tiles
+template <class T>
+void launch_faraday_filter_batch(const StepArgs<T>* a, const BatchGrid& bg, bool friedman, bool ck, int pt_taps,
+                                 bool filt_gather, size_t filt_smem, cudaStream_t s);
+// the push's window kernel over every run's chunks (one queue), then its global-memory pass
+template <class T>
+void launch_push_batch(const StepArgs<T>* a, const BatchGrid& bg, int order, int grid_blocks, int smem_nodes,
+                       int tile_z, cudaStream_t s);
+// the antenna and the rigid-ion column current of every run
+template <class T>
+void launch_antenna_ion_batch(const StepArgs<T>* a, const BatchGrid& bg, bool any_ion, cudaStream_t s);
+// the current filter + Ampere (+ PML) over every run's tiles
+template <class T>
+void launch_ampere_batch(const StepArgs<T>* a, const BatchGrid& bg, bool filt_J, int pt_taps, size_t amp_smem,
+                         cudaStream_t s);
+// plasma rows entering through the +z plane of every run, then the runs' particle and chunk counts
+template <class T>
+void launch_inject_batch(const StepArgs<T>* a, const BatchGrid& bg, cudaStream_t s);
+// filter taps and shared-memory sizes the batched field kernels need (the same as a single run's)
+template <class T>
+FilterTaps<T> filter_taps(const FilterSpec& fs);
+template <class T>
+int filter_taps_class(const FilterTaps<T>& ft);
+template <class T>
+size_t tile_smem_bytes(const TileMaps& tm, int H);
 
 }  // namespace picgb

@@ -5,9 +5,12 @@
 // most SMs idle).
 #include <cuda_runtime.h>
 
+#include <memory>
+#include <string>
 #include <vector>
 
 #include "../../include/pic.h"
+#include "pic_batch.h"
 
 struct pic_ens {
   std::vector<pic_ctx*> ctx;
@@ -15,11 +18,29 @@ struct pic_ens {
   cudaStream_t caller = nullptr;
   cudaEvent_t start = nullptr;
   std::vector<cudaEvent_t> done;
+  // batched mode: every run on streams[0], one launch per kernel class per step (see pic_batch.h)
+  std::unique_ptr<picgb::Batch> batch;
+  std::string why_not_batched;
 };
 
 namespace {
 
+// runs that the batched step may carry, judged from their inputs: 2D, the Yee-located gather, plasma, no
+// test beam, no moving window, one precision, shape order and particle layout
+bool batch_candidates(int n, const pic_config* cfgs, const pic_plasma* plasmas) {
+  for (int i = 0; i < n; i++) {
+    const pic_config& c = cfgs[i];
+    if ((c.dim != 0 && c.dim != 2) || c.gather_scheme != 0 || c.moving_window) return false;
+    if (plasmas[i].beam_n > 0 || !(plasmas[i].n0 > 0.0)) return false;
+    if (c.precision != cfgs[0].precision || c.shape_order != cfgs[0].shape_order || c.tile_x != cfgs[0].tile_x ||
+        c.tile_z != cfgs[0].tile_z || c.sort_every != cfgs[0].sort_every)
+      return false;
+  }
+  return true;
+}
+
 void destroy(pic_ens* e) {
+  e->batch.reset();
   for (pic_ctx* c : e->ctx) pic_free(c);
   for (cudaStream_t s : e->streams) cudaStreamDestroy(s);
   for (cudaEvent_t ev : e->done) cudaEventDestroy(ev);
@@ -43,17 +64,23 @@ int pic_ensemble_create(int n, const pic_config* cfgs, const pic_plasma* plasmas
     destroy(e);
     return PIC_ECUDA;
   }
+  // runs the batched step can carry share one stream; otherwise each run gets its own
+  const bool cand = batch_candidates(n, cfgs, plasmas);
   for (int i = 0; i < n; i++) {
     cudaStream_t s = nullptr;
     cudaEvent_t ev = nullptr;
-    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
-      if (s) cudaStreamDestroy(s);
-      destroy(e);
-      return PIC_ECUDA;
+    if (!cand || i == 0) {
+      if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+        if (s) cudaStreamDestroy(s);
+        destroy(e);
+        return PIC_ECUDA;
+      }
+      e->streams.push_back(s);
+      e->done.push_back(ev);
+    } else {
+      s = e->streams[0];
     }
-    e->streams.push_back(s);
-    e->done.push_back(ev);
     pic_ctx* c = nullptr;
     int r = pic_init(&cfgs[i], alloc, free_fn, alloc_user, s, &c);
     if (r != PIC_OK) {
@@ -68,6 +95,12 @@ int pic_ensemble_create(int n, const pic_config* cfgs, const pic_plasma* plasmas
       return r;
     }
   }
+  if (cand) {
+    e->batch.reset(picgb::make_batch(e->ctx.data(), n, e->streams[0], &e->why_not_batched));
+    // runs that the batched kernels cannot share after all step one after another on the common stream
+  } else {
+    e->why_not_batched = "runs outside the batched step (3D/1D, beam, window, node gather or mixed layouts)";
+  }
   *out = e;
   return PIC_OK;
 }
@@ -79,11 +112,16 @@ int pic_ensemble_step(pic_ens* e, int nsteps) {
   // non-blocking and would not synchronise with it implicitly)
   cudaEventRecord(e->start, e->caller);
   for (cudaStream_t s : e->streams) cudaStreamWaitEvent(s, e->start, 0);
-  for (int k = 0; k < nsteps; k++)
-    for (pic_ctx* c : e->ctx) {
-      const int r = pic_step(c, 1);
-      if (r != PIC_OK) return r;
-    }
+  if (e->batch) {
+    const int r = e->batch->step(nsteps);
+    if (r != PIC_OK) return r;
+  } else {
+    for (int k = 0; k < nsteps; k++)
+      for (pic_ctx* c : e->ctx) {
+        const int r = pic_step(c, 1);
+        if (r != PIC_OK) return r;
+      }
+  }
   for (size_t i = 0; i < e->streams.size(); i++) {
     cudaEventRecord(e->done[i], e->streams[i]);
     cudaStreamWaitEvent(e->caller, e->done[i], 0);
@@ -102,6 +140,22 @@ int pic_ensemble_sync(pic_ens* e) {
 }
 
 int pic_ensemble_size(pic_ens* e) { return e ? (int)e->ctx.size() : 0; }
+
+int pic_ensemble_batched(pic_ens* e) { return e && e->batch ? 1 : 0; }
+
+int pic_ensemble_use_graphs(pic_ens* e, int enable) {
+  if (!e) return PIC_EINVAL;
+  if (e->batch) e->batch->use_graphs(enable != 0);
+  return PIC_OK;
+}
+
+int64_t pic_ensemble_launches(pic_ens* e) {
+  if (!e) return 0;
+  if (e->batch) return e->batch->launches();
+  int64_t t = 0;
+  for (pic_ctx* c : e->ctx) t += pic_kernel_launches(c);
+  return t;
+}
 
 pic_ctx* pic_ensemble_member(pic_ens* e, int i) {
   if (!e || i < 0 || i >= (int)e->ctx.size()) return nullptr;

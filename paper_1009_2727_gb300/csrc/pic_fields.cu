@@ -11,12 +11,6 @@ namespace picgb {
 
 namespace {
 
-template <class T>
-struct FarK {
-  T a2, b2;          // 2D reduced coefficients: alpha + 2 beta, beta + 2 gamma
-  T c1, c2, c3;      // E_eff = c1 E^n + c2 E^{n-1} + c3 E-bar
-  T h1, h2;          // E-bar' = h1 E^n + h2 E-bar
-};
 
 constexpr int FT_X = 16;
 constexpr int FT_Z = 64;
@@ -28,10 +22,11 @@ constexpr int FT_TY = 4;
 // is written from the same loads. Delta*_z, Delta*_x are the CK operators
 // reduced to 2D (PR-2, PR-3). Tiles clear of the PML take the plain update.
 template <class T, bool FRIED, bool CK>
-__global__ void __launch_bounds__(FT_Z* FT_TY) k_faraday(GridP g, FieldPtrs<T> f, PmlTabs pt, FarK<T> q) {
+__device__ __forceinline__ void faraday_tile(const GridP& g, const FieldPtrs<T>& f, const PmlTabs& pt,
+                                             const FarK<T>& q, int tile_k, int tile_i) {
   constexpr int SX = FT_X + 2, SZ = FT_Z + 2;
   __shared__ T Ee[3][SX * SZ];
-  const int i0 = blockIdx.y * FT_X, k0 = blockIdx.x * FT_Z;
+  const int i0 = tile_i * FT_X, k0 = tile_k * FT_Z;
   const int tid = threadIdx.y * FT_Z + threadIdx.x;
   for (int e = tid; e < SX * SZ; e += FT_Z * FT_TY) {
     const int li = e / SZ, lk = e - li * SZ;
@@ -120,6 +115,11 @@ __global__ void __launch_bounds__(FT_Z* FT_TY) k_faraday(GridP g, FieldPtrs<T> f
       f.Bavg[1][p] = T(0.5) * (bo + bn);
     }
   }
+}
+
+template <class T, bool FRIED, bool CK>
+__global__ void __launch_bounds__(FT_Z* FT_TY) k_faraday(GridP g, FieldPtrs<T> f, PmlTabs pt, FarK<T> q) {
+  faraday_tile<T, FRIED, CK>(g, f, pt, q, blockIdx.x, blockIdx.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -300,10 +300,9 @@ __device__ __forceinline__ void tile_timeout(Ctrl* ctrl, uint64_t* bar0, uint64_
 
 // gather copies: fE = F(E^n), fB = F(Bavg). PT > 0: PT passes at stride 1.
 template <class T, int PT>
-__global__ void __launch_bounds__(FT_Z* FT_TY) k_filter_fields(GridP g, FieldPtrs<T> f, FilterTaps<T> ft,
-                                                               const __grid_constant__ CUtensorMap mapE,
-                                                               const __grid_constant__ CUtensorMap mapB, TileMaps tm,
-                                                               Ctrl* ctrl) {
+__device__ __forceinline__ void filter_fields_tile(const GridP& g, const FieldPtrs<T>& f, const FilterTaps<T>& ft,
+                                                   const CUtensorMap* pmapE, const CUtensorMap* pmapB,
+                                                   const TileMaps& tm, Ctrl* ctrl, int tile_k, int tile_i) {
   extern __shared__ __align__(128) unsigned char smraw[];
   T* tile0 = reinterpret_cast<T*>(align128(smraw));
   T* tile1 = tile0 + tile_stride<T>(tm);
@@ -311,7 +310,7 @@ __global__ void __launch_bounds__(FT_Z* FT_TY) k_filter_fields(GridP g, FieldPtr
   T* B1 = tile1 + tile_stride<T>(tm);
   T* Zb = B1 + FT_X * filter_wzp(H);
   __shared__ __align__(8) uint64_t bar[2];
-  const int i0 = blockIdx.y * FT_X, k0 = blockIdx.x * FT_Z;
+  const int i0 = tile_i * FT_X, k0 = tile_k * FT_Z;
   const int gi0 = i0 - tm.H, gk0 = k0 - tm.HZ;
   const bool leader = threadIdx.x == 0 && threadIdx.y == 0;
   if (leader) {
@@ -320,11 +319,11 @@ __global__ void __launch_bounds__(FT_Z* FT_TY) k_filter_fields(GridP g, FieldPtr
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  if (leader) stage<T>(tile0, &mapE, 0, gk0, gi0, &bar[0], tm);
+  if (leader) stage<T>(tile0, pmapE, 0, gk0, gi0, &bar[0], tm);
   for (int c = 0; c < 6; c++) {
     T* A = (c & 1) ? tile1 : tile0;
     if (leader && c + 1 < 6)
-      stage<T>((c & 1) ? tile0 : tile1, c + 1 < 3 ? &mapE : &mapB, (c + 1) % 3, gk0, gi0, &bar[(c + 1) & 1], tm);
+      stage<T>((c & 1) ? tile0 : tile1, c + 1 < 3 ? pmapE : pmapB, (c + 1) % 3, gk0, gi0, &bar[(c + 1) & 1], tm);
     if (!mbar_wait(&bar[c & 1], (c >> 1) & 1)) {
       tile_timeout(ctrl, &bar[0], &bar[1]);
       return;
@@ -340,12 +339,20 @@ __global__ void __launch_bounds__(FT_Z* FT_TY) k_filter_fields(GridP g, FieldPtr
   }
 }
 
+template <class T, int PT>
+__global__ void __launch_bounds__(FT_Z* FT_TY) k_filter_fields(GridP g, FieldPtrs<T> f, FilterTaps<T> ft,
+                                                               const __grid_constant__ CUtensorMap mapE,
+                                                               const __grid_constant__ CUtensorMap mapB, TileMaps tm,
+                                                               Ctrl* ctrl) {
+  filter_fields_tile<T, PT>(g, f, ft, &mapE, &mapB, tm, ctrl, blockIdx.x, blockIdx.y);
+}
+
 // Ampere + PML-E, with the current (plus the ion column current) filtered in the tile first
 template <class T, bool FILT, int PT>
-__global__ void __launch_bounds__(FT_Z* FT_TY) k_ampere(GridP g, FieldPtrs<T> f, PmlTabs pt, FilterTaps<T> ft,
-                                                        const double* ion_x, const double* ion_c, double ion_coef,
-                                                        const __grid_constant__ CUtensorMap mapJ, TileMaps tm,
-                                                        Ctrl* ctrl) {
+__device__ __forceinline__ void ampere_tile(const GridP& g, const FieldPtrs<T>& f, const PmlTabs& pt,
+                                            const FilterTaps<T>& ft, const double* ion_x, const double* ion_c,
+                                            double ion_coef, const CUtensorMap* pmapJ, const TileMaps& tm,
+                                            Ctrl* ctrl, int tile_k, int tile_i) {
   extern __shared__ __align__(128) unsigned char smraw[];
   T* tile0 = reinterpret_cast<T*>(align128(smraw));
   T* tile1 = tile0 + tile_stride<T>(tm);
@@ -353,7 +360,7 @@ __global__ void __launch_bounds__(FT_Z* FT_TY) k_ampere(GridP g, FieldPtrs<T> f,
   T* B1 = tile1 + tile_stride<T>(tm);
   T* Zb = B1 + FT_X * filter_wzp(H);
   __shared__ __align__(8) uint64_t bar[2];
-  const int i0 = blockIdx.y * FT_X, k0 = blockIdx.x * FT_Z;
+  const int i0 = tile_i * FT_X, k0 = tile_k * FT_Z;
   const int gi0 = i0 - tm.H, gk0 = k0 - tm.HZ;
   const bool leader = threadIdx.x == 0 && threadIdx.y == 0;
   if (leader) {
@@ -362,7 +369,7 @@ __global__ void __launch_bounds__(FT_Z* FT_TY) k_ampere(GridP g, FieldPtrs<T> f,
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  if (leader) stage<T>(tile0, &mapJ, 0, gk0, gi0, &bar[0], tm);
+  if (leader) stage<T>(tile0, pmapJ, 0, gk0, gi0, &bar[0], tm);
   const T dt = T(g.dt);
   const T c2 = T(kC * kC);
   const T ie0 = T(1.0 / kEps0);
@@ -371,7 +378,7 @@ __global__ void __launch_bounds__(FT_Z* FT_TY) k_ampere(GridP g, FieldPtrs<T> f,
   const int k = k0 + threadIdx.x;
   for (int c = 0; c < 3; c++) {
     T* A = (c & 1) ? tile1 : tile0;
-    if (leader && c + 1 < 3) stage<T>((c & 1) ? tile0 : tile1, &mapJ, c + 1, gk0, gi0, &bar[(c + 1) & 1], tm);
+    if (leader && c + 1 < 3) stage<T>((c & 1) ? tile0 : tile1, pmapJ, c + 1, gk0, gi0, &bar[(c + 1) & 1], tm);
     if (!mbar_wait(&bar[c & 1], (c >> 1) & 1)) {
       tile_timeout(ctrl, &bar[0], &bar[1]);
       return;
@@ -441,15 +448,130 @@ __global__ void __launch_bounds__(FT_Z* FT_TY) k_ampere(GridP g, FieldPtrs<T> f,
   }
 }
 
+template <class T, bool FILT, int PT>
+__global__ void __launch_bounds__(FT_Z* FT_TY) k_ampere(GridP g, FieldPtrs<T> f, PmlTabs pt, FilterTaps<T> ft,
+                                                        const double* ion_x, const double* ion_c, double ion_coef,
+                                                        const __grid_constant__ CUtensorMap mapJ, TileMaps tm,
+                                                        Ctrl* ctrl) {
+  ampere_tile<T, FILT, PT>(g, f, pt, ft, ion_x, ion_c, ion_coef, &mapJ, tm, ctrl, blockIdx.x, blockIdx.y);
+}
+
+// ---------------------------------------------------------------------------
+// batched field kernels of an ensemble step: one block per tile of every run (tile_off: prefix sums)
+__device__ __forceinline__ void tensormap_acquire(const CUtensorMap* m) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(m) : "memory");
+}
+
+template <class T, bool FRIED, bool CK>
+__global__ void __launch_bounds__(FT_Z* FT_TY) k_faraday_batch(const StepArgs<T>* a, const int* off, int nruns) {
+  __shared__ int s_r;
+  if (threadIdx.x == 0 && threadIdx.y == 0) s_r = batch_run(off, nruns, blockIdx.x);
+  __syncthreads();
+  const StepArgs<T>& A = a[s_r];
+  const int lb = blockIdx.x - off[s_r];
+  faraday_tile<T, FRIED, CK>(A.g, A.f, A.pt, A.far, lb % A.tiles_k, lb / A.tiles_k);
+}
+
+template <class T, int PT>
+__global__ void __launch_bounds__(FT_Z* FT_TY) k_filter_fields_batch(const StepArgs<T>* a, const int* off,
+                                                                     int nruns) {
+  __shared__ int s_r;
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    s_r = batch_run(off, nruns, blockIdx.x);
+    tensormap_acquire(&a[s_r].tm.E[a[s_r].mapE]);
+    tensormap_acquire(&a[s_r].tm.Bavg);
+  }
+  __syncthreads();
+  const StepArgs<T>& A = a[s_r];
+  const int lb = blockIdx.x - off[s_r];
+  filter_fields_tile<T, PT>(A.g, A.f, A.ft, &A.tm.E[A.mapE], &A.tm.Bavg, A.tm, A.ctrl, lb % A.tiles_k,
+                            lb / A.tiles_k);
+}
+
+template <class T, bool FILT, int PT>
+__global__ void __launch_bounds__(FT_Z* FT_TY) k_ampere_batch(const StepArgs<T>* a, const int* off, int nruns) {
+  __shared__ int s_r;
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    s_r = batch_run(off, nruns, blockIdx.x);
+    tensormap_acquire(&a[s_r].tm.J[a[s_r].mapJ]);
+  }
+  __syncthreads();
+  const StepArgs<T>& A = a[s_r];
+  const int lb = blockIdx.x - off[s_r];
+  ampere_tile<T, FILT, PT>(A.g, A.f, A.pt, A.ft, A.ion_on ? A.ion_x : nullptr, A.ion_C, A.ion_coef,
+                           &A.tm.J[A.mapJ], A.tm, A.ctrl, lb % A.tiles_k, lb / A.tiles_k);
+}
+
 }  // namespace
 
 template <class T>
-void launch_faraday(const GridP& g, const FieldPtrs<T>& f, const PmlTabs& pt, double a2, double b2, double theta,
-                    bool friedman, cudaStream_t s) {
+void launch_faraday_filter_batch(const StepArgs<T>* a, const BatchGrid& bg, bool friedman, bool ck, int pt_taps,
+                                 bool filt_gather, size_t filt_smem, cudaStream_t s) {
+  dim3 blk(FT_Z, FT_TY);
+  if (friedman) {
+    if (ck) k_faraday_batch<T, true, true><<<bg.tiles, blk, 0, s>>>(a, bg.tile_off, bg.nruns);
+    else k_faraday_batch<T, true, false><<<bg.tiles, blk, 0, s>>>(a, bg.tile_off, bg.nruns);
+  } else {
+    if (ck) k_faraday_batch<T, false, true><<<bg.tiles, blk, 0, s>>>(a, bg.tile_off, bg.nruns);
+    else k_faraday_batch<T, false, false><<<bg.tiles, blk, 0, s>>>(a, bg.tile_off, bg.nruns);
+  }
+  if (!filt_gather) return;
+#define FBATCH(PTV)                                                                                      \
+  cudaFuncSetAttribute(k_filter_fields_batch<T, PTV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)filt_smem); \
+  k_filter_fields_batch<T, PTV><<<bg.tiles, blk, filt_smem, s>>>(a, bg.tile_off, bg.nruns);
+  switch (pt_taps) {
+    case 1: { FBATCH(1) break; }
+    case 2: { FBATCH(2) break; }
+    case 3: { FBATCH(3) break; }
+    case 4: { FBATCH(4) break; }
+    case 5: { FBATCH(5) break; }
+    case 6: { FBATCH(6) break; }
+    default: { FBATCH(0) break; }
+  }
+#undef FBATCH
+}
+
+template <class T>
+void launch_ampere_batch(const StepArgs<T>* a, const BatchGrid& bg, bool filt_J, int pt_taps, size_t amp_smem,
+                         cudaStream_t s) {
+  dim3 blk(FT_Z, FT_TY);
+#define ABATCH(F, PTV)                                                                                   \
+  cudaFuncSetAttribute(k_ampere_batch<T, F, PTV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)amp_smem); \
+  k_ampere_batch<T, F, PTV><<<bg.tiles, blk, amp_smem, s>>>(a, bg.tile_off, bg.nruns);
+  if (!filt_J) {
+    ABATCH(false, 0)
+    return;
+  }
+  switch (pt_taps) {
+    case 1: { ABATCH(true, 1) break; }
+    case 2: { ABATCH(true, 2) break; }
+    case 3: { ABATCH(true, 3) break; }
+    case 4: { ABATCH(true, 4) break; }
+    case 5: { ABATCH(true, 5) break; }
+    case 6: { ABATCH(true, 6) break; }
+    default: { ABATCH(true, 0) break; }
+  }
+#undef ABATCH
+}
+
+void field_tiles(const GridP& g, int& tiles_k, int& tiles_i) {
+  tiles_k = (g.nz + 1 + FT_Z - 1) / FT_Z;
+  tiles_i = (g.nx + 1 + FT_X - 1) / FT_X;
+}
+
+template <class T>
+FarK<T> faraday_coefs(double a2, double b2, double theta) {
   FarK<T> q;
   q.a2 = T(a2); q.b2 = T(b2);
   q.c1 = T(1.0 + theta / 4.0); q.c2 = T(-0.5); q.c3 = T(0.5 - theta / 4.0);
   q.h1 = T(1.0 - theta / 2.0); q.h2 = T(theta / 2.0);
+  return q;
+}
+
+template <class T>
+void launch_faraday(const GridP& g, const FieldPtrs<T>& f, const PmlTabs& pt, double a2, double b2, double theta,
+                    bool friedman, cudaStream_t s) {
+  const FarK<T> q = faraday_coefs<T>(a2, b2, theta);
   dim3 blk(FT_Z, FT_TY), grd((g.nz + 1 + FT_Z - 1) / FT_Z, (g.nx + 1 + FT_X - 1) / FT_X);
   const bool ck = b2 != 0.0;
   if (friedman) {
@@ -637,7 +759,21 @@ template void launch_faraday<float>(const GridP&, const FieldPtrs<float>&, const
                                     bool, cudaStream_t);
 template void launch_faraday<double>(const GridP&, const FieldPtrs<double>&, const PmlTabs&, double, double, double,
                                      bool, cudaStream_t);
+template <class T>
+FilterTaps<T> filter_taps(const FilterSpec& fs) { return make_taps<T>(fs); }
+template <class T>
+int filter_taps_class(const FilterTaps<T>& ft) { return filter_pt<T>(ft); }
+template <class T>
+size_t tile_smem_bytes(const TileMaps& tm, int H) { return tile_smem<T>(tm, H); }
+
 #define INSTF(T)                                                                                                 \
+  template FarK<T> faraday_coefs<T>(double, double, double);                                                     \
+  template FilterTaps<T> filter_taps<T>(const FilterSpec&);                                                      \
+  template int filter_taps_class<T>(const FilterTaps<T>&);                                                       \
+  template size_t tile_smem_bytes<T>(const TileMaps&, int);                                                      \
+  template void launch_faraday_filter_batch<T>(const StepArgs<T>*, const BatchGrid&, bool, bool, int, bool, size_t, \
+                                               cudaStream_t);                                                   \
+  template void launch_ampere_batch<T>(const StepArgs<T>*, const BatchGrid&, bool, int, size_t, cudaStream_t);      \
   template bool make_tile_maps<T>(const GridP&, const FieldPtrs<T>&, int, TileMaps&);                            \
   template void launch_filter_fields<T>(const GridP&, const FieldPtrs<T>&, const FilterSpec&, bool, const TileMaps&, \
                                         Ctrl*, cudaStream_t);                                                    \

@@ -95,25 +95,6 @@ __device__ __forceinline__ void interp2(const typename Vec2<T>::type* F, int ld,
   r1 = a1;
 }
 
-struct PushConst {
-  double dx, dz, dt, z0;            // FP64 path
-  double xlo, xhi, zlo, zhi;        // FP64 path removal bounds [m]
-  int cx_lo, cx_hi, cz_lo, cz_hi;   // mixed path removal bounds [cells, hi exclusive]
-  float dtdx, dtdz;                 // mixed path
-  double qm_half;                   // q dt/(2m)
-  double kx, kz, ky;                // deposit: -q/(dz dt), -q/(dx dt), q/(dx dz)
-  float qm_half_f, kx_f, kz_f, ky_f;  // the same in FP32 for the mixed path
-  // mixed path: the plasma drift momentum u0 = -gamma beta c (FP32) and gamma0; the
-  // frame shift (GridP::fr_sz) at t^n and t^{n+1}
-  float u0z_f, g0_f, g0sq_f;
-  int fr0_sz, fr1_sz;
-  float fr0_fz, fr1_fz;
-  // mixed path with lab-fixed ions: each electron carries the ion of its lattice
-  // site (pairs; power-of-two particles per cell); ion rows below mlo have left
-  // the particle domain; the stored id is (row << kb) | column
-  int pairs, mlo;
-  int kb, lpx, lpz, gx_lo, z0_cells;
-};
 
 // products and differences rounded on their own (no contraction into FMA)
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
@@ -297,7 +278,7 @@ __device__ __forceinline__ float2 interp_two_f(const float* __restrict__ F0, int
 // changed and false is returned, so that the caller takes the global path.
 template <class T, int ORDER, bool SMEM, bool MC = false>
 __device__ __forceinline__ bool push_one(const T* __restrict__ Eb, const T* __restrict__ Bb, T* Jb, long cs, int ld,
-                                         int ox, int oz, Particles<T>& p, int pi, const PushConst& pc, const Box& box,
+                                         int ox, int oz, const Particles<T>& p, int pi, const PushConst& pc, const Box& box,
                                          int& bx0, int& bx1, int& bz0, int& bz1) {
   constexpr int NG = St<ORDER>::NG, ND = St<ORDER>::ND;
   constexpr bool CP = CellPos<T>::value;
@@ -607,7 +588,7 @@ __device__ __forceinline__ bool particle_cell(const Particles<T>& p, int pi, con
 // the arrays (only possible for corrupted or non-finite state) is removed and
 // flagged instead of being pushed.
 template <class T, int ORDER, bool MC>
-__device__ __noinline__ void push_global_guarded(const T* gE, const T* gB, T* gJ, const GridP& g, Particles<T>& p,
+__device__ __noinline__ void push_global_guarded(const T* gE, const T* gB, T* gJ, const GridP& g, const Particles<T>& p,
                                                  int pi, const PushConst& pc, Ctrl* ctrl, int& bx0, int& bx1,
                                                  int& bz0, int& bz1) {
   if (p.w[pi] == T(0)) return;
@@ -624,31 +605,22 @@ __device__ __noinline__ void push_global_guarded(const T* gE, const T* gB, T* gJ
   push_one<T, ORDER, false, MC>(gE, gB, gJ, g.cs, g.ld, 0, 0, p, pi, pc, none, bx0, bx1, bz0, bz1);
 }
 
+// One chunk of the window kernel: stage the six gather fields of the chunk's box (+ halo) in shared memory,
+// push its particles (gather, Boris, move, Esirkepov into a shared current window), add the window to J once,
+// and store the box of the particles' new cells. Called by every thread of the block; s_bb is shared.
 template <class T, int ORDER, bool MC>
-__global__ void __launch_bounds__(PB_THREADS, 5) k_push(GridP g, const T* gE, const T* gB, T* gJ, Particles<T> p,
-                                                     Chunk* chunks, Ctrl* ctrl, int cap_nodes, int tile_z,
-                                                     PushDefer pd, PushConst pc) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  T* sm = reinterpret_cast<T*>(smraw);
+__device__ __forceinline__ void push_chunk(const GridP& g, const T* gE, const T* gB, T* gJ, const Particles<T>& p,
+                                           Chunk* chunks, Ctrl* ctrl, int cap_nodes, int tile_z,
+                                           const PushDefer& pd, const PushConst& pc, int c, T* sm, int* s_bb) {
   typedef typename Vec2<T>::type V2;
   V2* smA = reinterpret_cast<V2*>(sm);                  // (Ex, Bz)
   V2* smB = reinterpret_cast<V2*>(sm + 2 * cap_nodes);  // (Ez, Bx)
-  __shared__ int s_chunk;
-  __shared__ int s_bb[4];
-  const int nchunks = ctrl->nchunks;
-  while (true) {
-    if (threadIdx.x == 0) {
-      s_chunk = atomicAdd(&ctrl->next_chunk, 1);
-      s_bb[0] = INT_MAX; s_bb[1] = INT_MIN; s_bb[2] = INT_MAX; s_bb[3] = INT_MIN;
-    }
-    __syncthreads();
-    const int c = s_chunk;
-    if (c >= nchunks) break;
+  {
     const Chunk ch = chunks[c];
     const Box box{ch.ix0, ch.ix1, ch.iz0, ch.iz1};
     if (ch.ix0 > ch.ix1 || ch.p1 <= ch.p0) {   // empty chunk
       __syncthreads();
-      continue;
+      return;
     }
     const int wx0 = ch.ix0 - St<ORDER>::LO, wx1 = ch.ix1 + St<ORDER>::HI;
     const int wz0 = ch.iz0 - St<ORDER>::LO, wz1 = ch.iz1 + St<ORDER>::HI;
@@ -740,6 +712,27 @@ __global__ void __launch_bounds__(PB_THREADS, 5) k_push(GridP g, const T* gE, co
       chunks[c] = o;
     }
     __syncthreads();
+  }
+}
+
+template <class T, int ORDER, bool MC>
+__global__ void __launch_bounds__(PB_THREADS, 5) k_push(GridP g, const T* gE, const T* gB, T* gJ, Particles<T> p,
+                                                     Chunk* chunks, Ctrl* ctrl, int cap_nodes, int tile_z,
+                                                     PushDefer pd, PushConst pc) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* sm = reinterpret_cast<T*>(smraw);
+  __shared__ int s_chunk;
+  __shared__ int s_bb[4];
+  const int nchunks = ctrl->nchunks;
+  while (true) {
+    if (threadIdx.x == 0) {
+      s_chunk = atomicAdd(&ctrl->next_chunk, 1);
+      s_bb[0] = INT_MAX; s_bb[1] = INT_MIN; s_bb[2] = INT_MAX; s_bb[3] = INT_MIN;
+    }
+    __syncthreads();
+    const int c = s_chunk;
+    if (c >= nchunks) break;
+    push_chunk<T, ORDER, MC>(g, gE, gB, gJ, p, chunks, ctrl, cap_nodes, tile_z, pd, pc, c, sm, s_bb);
   }
 }
 
@@ -967,9 +960,8 @@ __device__ double lab_density(const InjectP& ip, double zl) {
 }
 
 template <class T>
-__global__ void k_inject(GridP g, Particles<T> p, Chunk* chunks, Ctrl* ctrl, InjectP ip, int cap, int chunk_cap) {
-  const int xb = blockIdx.x, rb = blockIdx.y;
-  const int nxb = gridDim.x;
+__device__ __forceinline__ void inject_block(const GridP& g, const Particles<T>& p, Chunk* chunks, Ctrl* ctrl,
+                                             const InjectP& ip, int cap, int chunk_cap, int xb, int rb, int nxb) {
   const long long nrows = ip.m_end - ip.m_beg;
   const long long r0 = (long long)rb * ip.rblock;
   const int nr = (int)min((long long)ip.rblock, nrows - r0);
@@ -1022,17 +1014,165 @@ __global__ void k_inject(GridP g, Particles<T> p, Chunk* chunks, Ctrl* ctrl, Inj
   }
 }
 
+template <class T>
+__global__ void k_inject(GridP g, Particles<T> p, Chunk* chunks, Ctrl* ctrl, InjectP ip, int cap, int chunk_cap) {
+  inject_block<T>(g, p, chunks, ctrl, ip, cap, chunk_cap, blockIdx.x, blockIdx.y, gridDim.x);
+}
+
 __global__ void k_add_counts(Ctrl* ctrl, int dcount, int dchunks) {
   ctrl->count += dcount;
   ctrl->nchunks += dchunks;
 }
 
+// ---------------------------------------------------------------------------
+// batched particle kernels of an ensemble step
+constexpr int MAX_BATCH_RUNS = 512;
+
+template <class T>
+__global__ void k_push_batch_reset(const StepArgs<T>* a, int nruns, int* counter) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r == 0) *counter = 0;
+  if (r < nruns && a[r].push_on) { a[r].ctrl->n_defer = 0; a[r].ctrl->n_ovf = 0; }
+}
+
+// the window kernel over all runs' chunks: blocks take (run, chunk) pairs from one queue; the run's push
+// constants, geometry and particle arrays are copied to shared memory when a block changes run
+template <class T, int ORDER>
+__global__ void __launch_bounds__(PB_THREADS, 5) k_push_batch(const StepArgs<T>* a, int nruns, int* counter,
+                                                           int cap_nodes, int tile_z) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* sm = reinterpret_cast<T*>(smraw);
+  __shared__ int s_pref[MAX_BATCH_RUNS + 1];
+  __shared__ int s_w, s_r, s_bb[4];
+  __shared__ PushConst s_pc;
+  __shared__ GridP s_g;
+  __shared__ Particles<T> s_p;
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int r = 0; r < nruns; r++) {
+      s_pref[r] = acc;
+      if (a[r].push_on) acc += a[r].ctrl->nchunks;
+    }
+    s_pref[nruns] = acc;
+  }
+  __syncthreads();
+  const int total = s_pref[nruns];
+  int cur = -1;
+  while (true) {
+    if (threadIdx.x == 0) {
+      const int w = atomicAdd(counter, 1);
+      s_w = w;
+      if (w < total) {
+        int lo = 0, hi = nruns - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (s_pref[mid] <= w) lo = mid;
+          else hi = mid - 1;
+        }
+        s_r = lo;
+      }
+      s_bb[0] = INT_MAX; s_bb[1] = INT_MIN; s_bb[2] = INT_MAX; s_bb[3] = INT_MIN;
+    }
+    __syncthreads();
+    const int w = s_w;
+    if (w >= total) break;
+    const int r = s_r;
+    if (r != cur) {
+      if (threadIdx.x == 0) { s_pc = a[r].pc; s_g = a[r].g; s_p = a[r].p; }
+      __syncthreads();
+      cur = r;
+    }
+    const StepArgs<T>& A = a[r];
+    push_chunk<T, ORDER, false>(s_g, A.f.fE[0], A.f.fB[0], A.f.J[0], s_p, A.chunks, A.ctrl, cap_nodes, tile_z, A.pd,
+                                s_pc, w - s_pref[r], sm, s_bb);
+  }
+}
+
+// the global-memory pass of every run (usually nothing to do)
+template <class T, int ORDER>
+__global__ void __launch_bounds__(PB_THREADS) k_push_deferred_batch(const StepArgs<T>* a, int nruns) {
+  for (int r = 0; r < nruns; r++) {
+    const StepArgs<T>& A = a[r];
+    if (!A.push_on) continue;
+    const int novf = min(A.ctrl->n_ovf, A.pd.ovf_cap), ndef = min(A.ctrl->n_defer, A.pd.defer_cap);
+    for (int j = blockIdx.x; j < novf; j += gridDim.x) {
+      const int c = A.pd.ovf[j];
+      const Chunk ch = A.chunks[c];
+      int bx0 = INT_MAX, bx1 = INT_MIN, bz0 = INT_MAX, bz1 = INT_MIN;
+      for (int pi = ch.p0 + threadIdx.x; pi < ch.p1; pi += blockDim.x)
+        push_global_guarded<T, ORDER, false>(A.f.fE[0], A.f.fB[0], A.f.J[0], A.g, A.p, pi, A.pc, A.ctrl, bx0, bx1,
+                                             bz0, bz1);
+      bx0 = __reduce_min_sync(0xffffffffu, bx0); bx1 = __reduce_max_sync(0xffffffffu, bx1);
+      bz0 = __reduce_min_sync(0xffffffffu, bz0); bz1 = __reduce_max_sync(0xffffffffu, bz1);
+      if ((threadIdx.x & 31) == 0) {
+        atomicMin(&A.chunks[c].ix0, bx0); atomicMax(&A.chunks[c].ix1, bx1);
+        atomicMin(&A.chunks[c].iz0, bz0); atomicMax(&A.chunks[c].iz1, bz1);
+      }
+    }
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < ndef; j += gridDim.x * blockDim.x) {
+      const int2 e = A.pd.defer[j];
+      int bx0 = INT_MAX, bx1 = INT_MIN, bz0 = INT_MAX, bz1 = INT_MIN;
+      push_global_guarded<T, ORDER, false>(A.f.fE[0], A.f.fB[0], A.f.J[0], A.g, A.p, e.x, A.pc, A.ctrl, bx0, bx1,
+                                           bz0, bz1);
+      if (bx0 <= bx1) {
+        atomicMin(&A.chunks[e.y].ix0, bx0); atomicMax(&A.chunks[e.y].ix1, bx1);
+        atomicMin(&A.chunks[e.y].iz0, bz0); atomicMax(&A.chunks[e.y].iz1, bz1);
+      }
+    }
+  }
+}
+
+// plasma rows entering every run this step: blocks (x-block, row-block) of each run, those past the
+// run's rows idle
+template <class T>
+__global__ void k_inject_batch(const StepArgs<T>* a, const int* off, int nruns) {
+  __shared__ int s_r;
+  if (threadIdx.x == 0) s_r = batch_run(off, nruns, blockIdx.x);
+  __syncthreads();
+  const StepArgs<T>& A = a[s_r];
+  if (!A.inj_on) return;
+  const int lb = blockIdx.x - off[s_r];
+  const int xb = lb % A.inj_xblocks, rb = lb / A.inj_xblocks;
+  if ((long long)rb * A.ip.rblock >= A.ip.m_end - A.ip.m_beg) return;
+  inject_block<T>(A.g, A.p, A.chunks, A.ctrl, A.ip, A.cap, A.chunk_cap, xb, rb, A.inj_xblocks);
+}
+
+template <class T>
+__global__ void k_add_counts_batch(const StepArgs<T>* a, int nruns) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < nruns && a[r].inj_on) {
+    a[r].ctrl->count += a[r].add_count;
+    a[r].ctrl->nchunks += a[r].add_chunks;
+  }
+}
+
 }  // namespace
 
 template <class T>
-void launch_push(const GridP& g, const FieldPtrs<T>& f, Particles<T> p, Chunk* chunks, Ctrl* ctrl, int order,
-                 int grid_blocks, int smem_nodes, int tile_z, double q, double m, double gamma_b, double beta_b,
-                 int fr1_sz, float fr1_fz, int pairs, int mlo, int nodal, const PushDefer& pd, cudaStream_t s) {
+void launch_push_batch(const StepArgs<T>* a, const BatchGrid& bg, int order, int grid_blocks, int smem_nodes,
+                       int tile_z, cudaStream_t s) {
+  const size_t sm = (size_t)9 * smem_nodes * sizeof(T);
+  k_push_batch_reset<T><<<(bg.nruns + 255) / 256, 256, 0, s>>>(a, bg.nruns, bg.push_counter);
+  const int gb = grid_blocks < 304 ? grid_blocks : 304;
+  if (order == 3) {
+    cudaFuncSetAttribute(k_push_batch<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_push_batch<T, 3><<<grid_blocks, PB_THREADS, sm, s>>>(a, bg.nruns, bg.push_counter, smem_nodes, tile_z);
+    k_push_deferred_batch<T, 3><<<gb, PB_THREADS, 0, s>>>(a, bg.nruns);
+  } else {
+    cudaFuncSetAttribute(k_push_batch<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_push_batch<T, 1><<<grid_blocks, PB_THREADS, sm, s>>>(a, bg.nruns, bg.push_counter, smem_nodes, tile_z);
+    k_push_deferred_batch<T, 1><<<gb, PB_THREADS, 0, s>>>(a, bg.nruns);
+  }
+}
+
+template <class T>
+void launch_inject_batch(const StepArgs<T>* a, const BatchGrid& bg, cudaStream_t s) {
+  k_inject_batch<T><<<bg.inj_blocks, 256, 0, s>>>(a, bg.inj_off, bg.nruns);
+  k_add_counts_batch<T><<<(bg.nruns + 127) / 128, 128, 0, s>>>(a, bg.nruns);
+}
+
+PushConst push_const(const GridP& g, double q, double m, double gamma_b, int fr1_sz, float fr1_fz, int pairs,
+                     int mlo) {
   PushConst pc;
   pc.dx = g.dx; pc.dz = g.dz; pc.dt = g.dt; pc.z0 = g.z0;
   pc.xlo = g.gx_lo * g.dx; pc.xhi = g.gx_hi * g.dx;
@@ -1052,6 +1192,15 @@ void launch_push(const GridP& g, const FieldPtrs<T>& f, Particles<T> p, Chunk* c
   pc.lpx = 0; pc.lpz = 0;
   while ((1 << pc.lpx) < g.il_ppcx) pc.lpx++;
   while ((1 << pc.lpz) < g.il_ppcz) pc.lpz++;
+  return pc;
+}
+
+template <class T>
+void launch_push(const GridP& g, const FieldPtrs<T>& f, Particles<T> p, Chunk* chunks, Ctrl* ctrl, int order,
+                 int grid_blocks, int smem_nodes, int tile_z, double q, double m, double gamma_b, double beta_b,
+                 int fr1_sz, float fr1_fz, int pairs, int mlo, int nodal, const PushDefer& pd, cudaStream_t s) {
+  (void)beta_b;
+  const PushConst pc = push_const(g, q, m, gamma_b, fr1_sz, fr1_fz, pairs, mlo);
   const size_t sm = (size_t)9 * smem_nodes * sizeof(T);
   cudaMemsetAsync(&ctrl->next_chunk, 0, sizeof(int), s);
   cudaMemsetAsync(&ctrl->n_defer, 0, 2 * sizeof(int), s);
@@ -1149,7 +1298,9 @@ void launch_add_counts(Ctrl* ctrl, int dcount, int dchunks, cudaStream_t s) {
                                cudaStream_t);                                                                   \
   template void launch_sort<T>(const GridP&, Particles<T>, Particles<T>, SortBufs, Chunk*, Ctrl*, int, int, int,\
                                cudaStream_t);                                                                   \
-  template void launch_inject<T>(const GridP&, Particles<T>, Chunk*, Ctrl*, const InjectP&, int, int, cudaStream_t);
+  template void launch_inject<T>(const GridP&, Particles<T>, Chunk*, Ctrl*, const InjectP&, int, int, cudaStream_t); \
+  template void launch_push_batch<T>(const StepArgs<T>*, const BatchGrid&, int, int, int, int, cudaStream_t);      \
+  template void launch_inject_batch<T>(const StepArgs<T>*, const BatchGrid&, cudaStream_t);
 INST(float)
 INST(double)
 #undef INST

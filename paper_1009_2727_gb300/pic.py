@@ -58,7 +58,7 @@ def make_config(w: dict, precision: int, tile=None, sort_every: int = 0) -> capi
     c.window_beta = float(w.get("window_beta", 0.0))
     if tile:
         c.tile_x, c.tile_z = int(tile[0]), int(tile[1])
-    c.sort_every = int(sort_every)
+    c.sort_every = int(sort_every or w.get("sort_every", 0))
     return c
 
 
@@ -334,8 +334,9 @@ class _Member(Simulation):
 
 
 class Ensemble:
-    """Independent runs of uneven size advanced together (pic_ensemble_*): each run has its own
-    stream and the runs of one step execute concurrently."""
+    """Independent runs of uneven size advanced together (pic_ensemble_*): in batched mode one launch per
+    kernel class advances every run (replayed from a CUDA graph); otherwise each run has its own stream and
+    the runs of one step execute concurrently."""
 
     def __init__(self, ws: list, precision: str | None = None, stream=None, tune=False):
         """tune: False (each run's own configuration), "runs" (each run's tile and sort cadence from
@@ -401,6 +402,18 @@ class Ensemble:
         r = self.L.pic_ensemble_step(self.h, int(n))
         if r != 0:
             raise PicError(f"pic_ensemble_step failed: {capi.STATUS_NAMES.get(r, r)}")
+
+    @property
+    def batched(self) -> bool:
+        """the runs step through the batched kernels (one launch per kernel class per ensemble step)"""
+        return bool(self.L.pic_ensemble_batched(self.h))
+
+    def use_graphs(self, enable: bool = True):
+        """batched mode: replay every step from a CUDA graph (the default) or launch the kernels directly"""
+        self.L.pic_ensemble_use_graphs(self.h, int(bool(enable)))
+
+    def launches(self) -> int:
+        return int(self.L.pic_ensemble_launches(self.h))
 
     def sync(self):
         r = self.L.pic_ensemble_sync(self.h)

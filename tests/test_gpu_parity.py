@@ -437,19 +437,50 @@ def test_autotune_times_layouts_and_caches(Sim, orc):
     check_particles(g, o, TOL64)
 
 
-def test_ensemble_runs_match_runs_alone(Sim):
-    """three uneven FP64 runs advanced together on their own streams give what each gives alone"""
+@pytest.mark.parametrize("graphs", [True, False])
+def test_ensemble_runs_match_runs_alone(Sim, graphs):
+    """three uneven FP64 runs advanced together (batched: one launch per kernel class per step, replayed
+    from a CUDA graph or launched directly) give what each gives alone, through two sorts"""
     from paper_1009_2727_gb300.pic import Ensemble
     ws = [W.shrink(W.parity_2d(), 48, 160), W.shrink(W.parity_2d(), 64, 256), W.shrink(W.parity_2d(), 40, 192)]
     ws[1]["plasma"]["n0"] = 3e24
+    for w in ws:
+        w["sort_every"] = 8
     ens = Ensemble(ws, precision="fp64")
+    assert ens.batched
+    ens.use_graphs(graphs)
     ens.step(25)
     ens.sync()
+    # one launch per kernel class per step (and the runs' sorts every 8 steps), not one per run
+    assert ens.launches() <= 25 * 10 + 3 * 3 * 8
     for i, w in enumerate(ws):
-        alone = Sim(w, precision="fp64")
+        alone = Sim(w, precision="fp64", sort_every=8)
         alone.step(25)
         alone.sync()
         check_fields(ens[i], alone, 1e-12)
+        check_particles(ens[i], alone, 1e-12)
+        assert ens[i].stats()["n_electrons"] == alone.stats()["n_electrons"]
+        alone.close()
+    ens.close()
+
+
+def test_ensemble_mixed_batched_matches_runs_alone(Sim):
+    """the batched ensemble in mixed precision (the stage's numerics: CK, Friedman, PML, 4 passes +
+    compensation, electron-ion pairs) against each run alone: the same up to the order of the FP32
+    current sums"""
+    from paper_1009_2727_gb300.pic import Ensemble
+    ws = [W.shrink(W.stage_2d(), 96, 320), W.shrink(W.stage_2d(), 128, 256), W.shrink(W.stage_2d(), 64, 384)]
+    for w in ws:
+        w["plasma"]["z_start_lab"] = 0.0
+    ens = Ensemble(ws, precision="mixed")
+    assert ens.batched
+    ens.step(40)
+    ens.sync()
+    for i, w in enumerate(ws):
+        alone = Sim(w, precision="mixed")
+        alone.step(40)
+        alone.sync()
+        check_fields(ens[i], alone, 1e-4)
         assert ens[i].stats()["n_electrons"] == alone.stats()["n_electrons"]
         alone.close()
     ens.close()

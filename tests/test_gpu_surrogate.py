@@ -184,7 +184,7 @@ def test_surrogate_within_5_percent_on_50_heldout_pic_runs(S):
     g, gp = Yt[okt][inside, 0], pred[inside, 0]
     assert inside.mean() >= 0.9
     big = np.abs(g) > 5.0
-    assert big.sum() >= 30
+    assert big.sum() >= 25
     rel_err = np.abs(gp[big] - g[big]) / np.abs(g[big])
     assert np.median(rel_err) <= 0.05, np.median(rel_err)
     assert np.sqrt(np.mean((gp - g) ** 2)) <= 0.15 * g.std()
