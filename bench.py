@@ -53,6 +53,12 @@ TRAFFIC_BYTES_PER_PARTICLE = {
     (32, 8, 8): 49.15, (32, 8, 16): 49.23, (32, 8, 32): 49.16, (32, 8, 64): 49.21, (32, 16, 8): 49.2, (32, 16, 16): 49.31,
     (32, 16, 32): 49.34, (32, 16, 64): 49.19, (32, 32, 8): 48.94, (32, 32, 16): 48.88, (32, 32, 32): 48.86, (32, 32, 64): 48.81,
 }
+# the push's instruction and FP32 arithmetic counts per particle (mixed, cubic, Yee-located gather; ncu
+# smsp__inst_executed.sum and smsp__sass_thread_inst_executed_op_{fadd,fmul,ffma}_pred_on.sum of three pushes
+# at steps 5-7 of the 2048 x 256 stage box, 8 x 16-cell tiles, sort every 64): warp instructions, and FLOPs
+# counted as FADD + FMUL + 2 FFMA (the packed two-lane FMAs of the gather are not in these counters)
+PUSH_WARP_INST_PER_PARTICLE = 20.7
+PUSH_FLOPS_PER_PARTICLE = 174.0
 # 3D: ncu dram bytes of k3_push_tiles on the 256 x 128 x 128 box (198.06 MB for 2,356,608 electrons), scaled
 # to the full box by its particle count
 TRAFFIC_BYTES_PER_PARTICLE_3D = {("mixed", 3): 84.0}
@@ -866,12 +872,34 @@ def main():
                                else "ncu dram bytes of k_push, 2048 x 256 box, this layout, scaled by particles") if tpp else None,
             "note": ("3D push on sorted 4x4x16-cell tiles with shared-memory windows: latency-bound at a quarter "
                      "occupancy (ncu: 35% issue slots, 44% L1/shared, 2% DRAM)" if three else
-                     "at cubic order the push is bound by instruction issue "
-                     "(ncu: 65% issue slots, 59% L1/shared, 19% DRAM), not by HBM"),
+                     "at cubic order the push is bound by instruction issue and the L1/shared pipe "
+                     "(ncu: 64-65% issue slots, 69% L1/TEX, 17% DRAM), not by HBM; see issue and alu"),
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback",
             "algorithmic_bytes_per_particle": bpp, "push_ms_per_step": push_avg_ms,
             "field_kernels_ms_per_step": field_ms / kf,
             "share_of_step": push_avg_ms / (ms / args.steps)}
+    if not three and args.precision == "mixed" and args.order == 3 and args.gather == "energy":
+        # the push's instruction-issue and FP32 rooflines: instruction and FLOP counts per particle from ncu,
+        # time from the CUDA events above; issue peak = 4 warp-instructions per SM per cycle at the median SM
+        # clock sampled during the timed steps; FP32 peak measured by the library's FMA microbenchmark
+        nsm = torch.cuda.get_device_properties(0).multi_processor_count
+        mhz = clocks.get("sm_mhz") or 2070.0
+        issue_peak = 4.0 * nsm * mhz * 1e6
+        issue_ach = PUSH_WARP_INST_PER_PARTICLE * n_avg / (push_avg_ms * 1e-3)
+        import ctypes
+        from paper_1009_2727_gb300 import capi
+        sc, pk = ctypes.c_double(0.0), ctypes.c_double(0.0)
+        fp32_peak = None
+        if capi.load().pic_measure_fp32_peak(ctypes.byref(sc), ctypes.byref(pk)) == 0:
+            fp32_peak = max(sc.value, pk.value)
+        alu_ach = PUSH_FLOPS_PER_PARTICLE * n_avg / (push_avg_ms * 1e-3) / 1e12
+        roof["issue"] = {"achieved": issue_ach, "peak": issue_peak, "unit": "warp-instructions/s",
+                         "frac": issue_ach / issue_peak, "warp_instructions_per_particle": PUSH_WARP_INST_PER_PARTICLE,
+                         "peak_source": f"4 per SM per cycle x {nsm} SMs x {mhz:g} MHz (sampled)"}
+        roof["alu"] = {"achieved": alu_ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                       "frac": alu_ach / fp32_peak if fp32_peak else None,
+                       "flops_per_particle": PUSH_FLOPS_PER_PARTICLE,
+                       "peak_source": "pic_measure_fp32_peak (FMA microbenchmark, measured in this run)"}
     sim.close()
     del sim
 
