@@ -669,6 +669,57 @@ def run_layout_sweep(args):
     return 0
 
 
+def run_solver_accuracy(args):
+    """Sec. 5.1.2's comparison of damping and smoothing against the frame: the scaled stage (n_e = 1e19 cm^-3,
+    workloads.scaled_stage) in frames boosted by gamma = 2, 5, 10, 13 (gamma_w = 13.2), each with the CK solver
+    undamped (the reference), the Yee-Friedman solver at theta = 1, and the Yee solver with the wide-band
+    filter S(1:2:4); the test beam's energy gain at the end of the stage (the same physical time in every
+    run of a frame), its deviation from the reference, and the GPU time of each run"""
+    import numpy as np
+    import torch
+    from paper_1009_2727_gb300 import workloads as W
+    from paper_1009_2727_gb300.pic import Simulation
+    torch.cuda.set_device(0)
+    me_mev = 0.51099895000
+    cases = (("ck", "ck", 0.0, None), ("yee_friedman_1", "yee", 1.0, None), ("yee_S124", "yee", 0.0, (1, 2, 4)))
+    out = []
+    for g in (2.0, 5.0, 10.0, 13.0):
+        row = {"gamma_boost": g}
+        for name, solver, theta, strides in cases:
+            w = W.scaled_stage(g, solver, theta, strides)
+            w["precision"] = args.precision
+            dt_ref = W.scaled_stage(g)["dt"]
+            sim = Simulation(w, precision=args.precision)
+            st = sim.stats()
+            steps = int(np.ceil(w["steps"] * dt_ref / st["dt"]))
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            stream = torch.cuda.current_stream()
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            sim.step(steps)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            sim.sync()
+            st = sim.stats()
+            gain = (st["beam_gamma_lab"] - w["gamma_w"]) * me_mev if st["n_beam_active"] > 0 else None
+            row[name] = {"gain_mev": gain, "steps": steps, "dt_s": st["dt"], "gpu_ms": ev0.elapsed_time(ev1),
+                         "beam_active": int(st["n_beam_active"]), "field_energy": st["field_energy"]}
+            sim.close()
+        ref = row["ck"]["gain_mev"]
+        for name, _, _, _ in cases[1:]:
+            gn = row[name]["gain_mev"]
+            row[name]["rel_dev_from_ck"] = abs(gn - ref) / abs(ref) if (gn is not None and ref) else None
+        out.append(row)
+        print(json.dumps(row), flush=True)
+    line = {"metric": "beam energy gain deviation from the undamped run", "unit": "relative",
+            "higher_is_better": False, "data": "synthetic",
+            "config": {"workload": "scaled_stage (n_e 1e19 cm^-3, a0 1.5, w0 12 um, tau 30 fs, L 0.4 mm)",
+                       "precision": args.precision, "gamma_w": W.scaled_stage(13.0)["gamma_w"]},
+            "rows": out}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_app1(args):
     """App. I on the GPU: the Nyquist (odd-even) mode grows without the current filter and is removed by
     one bilinear pass"""
@@ -749,6 +800,8 @@ def main():
                     help="momentum: the 'momentum conserving' gather (fields interpolated to the nodes first)")
     ap.add_argument("--dt-scan", action="store_true",
                     help="instability level (high-k E_z power at fixed times) against c dt/dz for both gather schemes")
+    ap.add_argument("--solver-accuracy", action="store_true",
+                    help="Sec. 5.1.2: beam gain of the scaled stage at gamma 2-13 with CK, Yee-Friedman and Yee + S(1:2:4)")
     ap.add_argument("--layout-sweep", action="store_true",
                     help="step every layout the autotuner can return, a few steps each (for a DRAM traffic table)")
     ap.add_argument("--stage3d", type=int, default=0,
@@ -787,6 +840,8 @@ def main():
         return run_stage3d(args)
     if args.layout_sweep:
         return run_layout_sweep(args)
+    if args.solver_accuracy:
+        return run_solver_accuracy(args)
     if args.ensemble:
         return run_ensemble(args)
     if args.surrogate:
@@ -878,6 +933,17 @@ def main():
             "algorithmic_bytes_per_particle": bpp, "push_ms_per_step": push_avg_ms,
             "field_kernels_ms_per_step": field_ms / kf,
             "share_of_step": push_avg_ms / (ms / args.steps)}
+    # the field kernels' roofline (Faraday + Friedman + PML, gather filter, current filter + Ampere): SURVEY's
+    # algorithmic bytes per cell-step (all six E/B components and the current, fused) over their measured time
+    cells = w["nx"] * w.get("ny", 1) * w["nz"]
+    bpc = BYTES_PER_CELL[args.precision]
+    field_avg_ms = field_ms / kf
+    field_ach = cells * bpc / (field_avg_ms * 1e-3) / 1e9 if field_avg_ms > 0 else None
+    roof["field_kernels"] = {"kernels": "k3_faraday_tile, k3_friedman, k3_filter_*, k3_ampere" if three else
+                             "k_faraday, k_filter_fields, k_ampere", "bound": "hbm", "achieved": field_ach,
+                             "peak": peak, "unit": "GB/s", "frac": field_ach / peak if field_ach else None,
+                             "algorithmic_bytes_per_cell": bpc, "ms_per_step": field_avg_ms,
+                             "cell_steps_per_s": cells / (field_avg_ms * 1e-3) if field_avg_ms > 0 else None}
     if not three and args.precision == "mixed" and args.order == 3 and args.gather == "energy":
         # the push's instruction-issue and FP32 rooflines: instruction and FLOP counts per particle from ncu,
         # time from the CUDA events above; issue peak = 4 warp-instructions per SM per cycle at the median SM

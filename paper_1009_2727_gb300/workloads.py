@@ -244,8 +244,6 @@ def surrogate_runs(n: int, seed: int) -> list:
     "inputs", its step count under "steps" (the laser's tail has then left the plasma's end) and under
     "emit_steps" the step at which the antenna has finished emitting."""
     rng = np.random.default_rng(seed)
-    c = 299792458.0
-    qe, me, eps0 = 1.602176634e-19, 9.1093837015e-31, 8.8541878128e-12
     runs = []
     for i in range(n):
         ln0 = float(rng.uniform(23.5, 25.0))
@@ -254,44 +252,83 @@ def surrogate_runs(n: int, seed: int) -> list:
         tau = float(rng.uniform(20e-15, 40e-15))
         L = float(rng.uniform(0.2e-3, 0.8e-3))
         g = float(rng.uniform(4.0, 6.0))
-        n0 = 10.0 ** ln0
-        beta = np.sqrt(1.0 - 1.0 / g ** 2)
-        dz_lab = LAMBDA0 / 16.0
-        dz_b = (1.0 + beta) * g * dz_lab
-        nx, nz, dx = 96, 1600, 1.5e-6
-        dt = dz_b / (np.sqrt(2.0) * c)
-        t_peak = 1.6 * tau
-        wp = np.sqrt(n0 * qe * qe / (eps0 * me))
-        lam_p = 2 * np.pi * c / wp
-        gw = (2 * np.pi * c / LAMBDA0) / wp
-        z_ant = (48 + np.ceil(g * beta * (0.5 * lam_p + 4e-6) / dz_b)) * dz_b
-        # the antenna at rest emits for (1 + beta) gamma 2 t_peak; the plasma closes in at beta c
-        t_emit = (1.0 + beta) * g * 2.0 * t_peak
-        gap = (np.ceil(beta * c * t_emit / dz_b) + 24) * dz_b
-        z_start_lab = g * (z_ant + gap)
-        # laser peak in the lab at t = 0 (emitted at t' = (1+beta) gamma t_peak by the antenna at rest)
-        z_peak0 = z_ant / ((1.0 + beta) * g) - c * t_peak
-        x, z, ux, uy, uz = lab_beam(256, seed=seed * 100003 + i, gamma_b=gw, R_b=1e-6, L_b=0.5e-6,
-                                    z_c=z_peak0 - 0.5 * lam_p, x_c=0.5 * nx * dx)
-        # the pulse's tail leaves the antenna at t_emit; the plasma's end (gap + ramp + L/gamma beyond the
-        # antenna at t = 0, moving at -beta c) then meets it after the closing distance / (1 + beta) c
-        z_end = gap + (20e-6 + L) / g
-        steps = int((t_emit + (z_end - beta * c * t_emit) / ((1.0 + beta) * c)) / dt) + 50
-        runs.append({
-            "name": f"surrogate_{seed}_{i}", "inputs": [ln0, a0, w0 * 1e6, tau * 1e15, L * 1e3, g],
-            "steps": steps, "emit_steps": int(t_emit / dt) + 1, "lambda_p": lam_p, "gamma_w": gw,
-            "nx": nx, "nz": nz, "dz_lab": dz_lab, "dx": dx, "gamma_boost": g, "courant": 0.99, "dt": dt,
-            "solver": SOLVERS["ck"], "theta": 0.1,
-            "pml_cells": 16, "pml_sigma_max": 4.0, "pml_delta": 5.0, "pml_power": 2.0, "pml_xi_exp": 1,
-            "filter_passes": 4, "filter_stride": 1, "filter_compensate": 1, "filter_J": 1, "filter_gather": 1,
-            "order": 3, "particle_guard": -1, "moving_window": 0, "window_beta": 0.0, "precision": "mixed",
-            "plasma": {"n0": n0, "z_start_lab": z_start_lab, "ramp_lab": 20e-6, "length_lab": L,
-                       "ppc_x": 2, "ppc_z": 2, "ions": 1},
-            "laser": {"lambda0": LAMBDA0, "a0": a0, "w0": w0, "tau_fwhm": tau, "t_peak": t_peak,
-                      "x_center": 0.5 * nx * dx, "phase": 0.0, "z_antenna": z_ant, "beta_s": 0.0},
-            "beam": {"x": x, "z": z, "ux": ux, "uy": uy, "uz": uz, "t_lab": 0.0, "z_plane_lab": z_start_lab},
-        })
+        runs.append(stage_run(ln0, a0, w0, tau, L, g, beam_seed=seed * 100003 + i, name=f"surrogate_{seed}_{i}"))
     return runs
+
+
+def stage_run(ln0: float, a0: float, w0: float, tau: float, L: float, g: float, beam_seed: int, name: str,
+              nz: int = 1600) -> dict:
+    """One stage run of the surrogate_runs recipe for the given inputs (log10 n0 [m^-3], a0, w0 [m], tau [s],
+    stage length L [m], gamma_boost): 1600 (z) x 96 (x) cells of lambda/16 (lab) by 1.5 um, 2 x 2 particles per
+    cell with rigid ions, CK at c dt = dz/sqrt(2), theta = 0.1, 4 passes + compensation, cubic shapes, a
+    256-particle lab test beam at gamma_w half a plasma wavelength behind the laser peak."""
+    c = 299792458.0
+    qe, me, eps0 = 1.602176634e-19, 9.1093837015e-31, 8.8541878128e-12
+    n0 = 10.0 ** ln0
+    beta = np.sqrt(1.0 - 1.0 / g ** 2)
+    dz_lab = LAMBDA0 / 16.0
+    dz_b = (1.0 + beta) * g * dz_lab
+    nx, dx = 96, 1.5e-6
+    dt = dz_b / (np.sqrt(2.0) * c)
+    t_peak = 1.6 * tau
+    wp = np.sqrt(n0 * qe * qe / (eps0 * me))
+    lam_p = 2 * np.pi * c / wp
+    gw = (2 * np.pi * c / LAMBDA0) / wp
+    z_ant = (48 + np.ceil(g * beta * (0.5 * lam_p + 4e-6) / dz_b)) * dz_b
+    # the antenna at rest emits for (1 + beta) gamma 2 t_peak; the plasma closes in at beta c
+    t_emit = (1.0 + beta) * g * 2.0 * t_peak
+    gap = (np.ceil(beta * c * t_emit / dz_b) + 24) * dz_b
+    z_start_lab = g * (z_ant + gap)
+    # laser peak in the lab at t = 0 (emitted at t' = (1+beta) gamma t_peak by the antenna at rest)
+    z_peak0 = z_ant / ((1.0 + beta) * g) - c * t_peak
+    x, z, ux, uy, uz = lab_beam(256, seed=beam_seed, gamma_b=gw, R_b=1e-6, L_b=0.5e-6,
+                                z_c=z_peak0 - 0.5 * lam_p, x_c=0.5 * nx * dx)
+    # the pulse's tail leaves the antenna at t_emit; the plasma's end (gap + ramp + L/gamma beyond the
+    # antenna at t = 0, moving at -beta c) then meets it after the closing distance / (1 + beta) c
+    z_end = gap + (20e-6 + L) / g
+    steps = int((t_emit + (z_end - beta * c * t_emit) / ((1.0 + beta) * c)) / dt) + 50
+    return {
+        "name": name, "inputs": [ln0, a0, w0 * 1e6, tau * 1e15, L * 1e3, g],
+        "steps": steps, "emit_steps": int(t_emit / dt) + 1, "lambda_p": lam_p, "gamma_w": gw,
+        "nx": nx, "nz": nz, "dz_lab": dz_lab, "dx": dx, "gamma_boost": g, "courant": 0.99, "dt": dt,
+        "solver": SOLVERS["ck"], "theta": 0.1,
+        "pml_cells": 16, "pml_sigma_max": 4.0, "pml_delta": 5.0, "pml_power": 2.0, "pml_xi_exp": 1,
+        "filter_passes": 4, "filter_stride": 1, "filter_compensate": 1, "filter_J": 1, "filter_gather": 1,
+        "order": 3, "particle_guard": -1, "moving_window": 0, "window_beta": 0.0, "precision": "mixed",
+        "plasma": {"n0": n0, "z_start_lab": z_start_lab, "ramp_lab": 20e-6, "length_lab": L,
+                   "ppc_x": 2, "ppc_z": 2, "ions": 1},
+        "laser": {"lambda0": LAMBDA0, "a0": a0, "w0": w0, "tau_fwhm": tau, "t_peak": t_peak,
+                  "x_center": 0.5 * nx * dx, "phase": 0.0, "z_antenna": z_ant, "beta_s": 0.0},
+        "beam": {"x": x, "z": z, "ux": ux, "uy": uy, "uz": uz, "t_lab": 0.0, "z_plane_lab": z_start_lab},
+    }
+
+
+def scaled_stage(gamma_boost: float, solver: str = "ck", theta: float = 0.0, filter_strides=None) -> dict:
+    """The scaled 0.1 GeV-class stage of Sec. 5.1 (n_e = 1e19 cm^-3) in the frame boosted by gamma_boost, for the
+    comparison of solvers, damping and smoothing against the frame (Sec. 5.1.2): the stage_run recipe with
+    a0 = 1.5, w0 = 12 um, tau = 30 fs and a 0.4 mm plasma; the given solver and Friedman theta (the time step
+    0.99 of that solver's limit with the damping's factor, or the singular step c dt = dz/sqrt(2) when that is
+    smaller), the stage's 4 passes + compensation, or a wide-band filter S(...) of one pass + compensation per
+    stride. The box grows along z with 1/gamma so that the slower frames keep the pulse and the beam inside;
+    every variant has the particle domain of the widest filter."""
+    g = float(gamma_boost)
+    nz = 1600 if g >= 4.0 else int(1600 * 4.0 / g) // 64 * 64
+    r = stage_run(25.0, 1.5, 12e-6, 30e-15, 0.4e-3, g, beam_seed=7, name=f"scaled_stage_g{g:g}_{solver}_th{theta:g}",
+                  nz=nz)
+    r["solver"] = SOLVERS[solver]
+    r["theta"] = float(theta)
+    # one particle domain for every variant: the guard of the widest filter, S(1:2:4) with one pass +
+    # compensation per stride (shape reach 3 + halo 14 + 2)
+    r["particle_guard"] = 19
+    if solver != "ck" or theta != 0.0:
+        r["dt"] = 0.0        # the library's step: courant x the solver's limit (Friedman factor included)
+        r["courant"] = 0.99
+    if filter_strides:
+        r["filter_strides"] = list(filter_strides)
+        r["filter_passes"] = 1
+        r["filter_compensate"] = 1
+        r["name"] += "_S(" + ":".join(str(v) for v in filter_strides) + ")"
+    return r
 
 
 def parity_1d(gamma_boost: float = 3.0) -> dict:
