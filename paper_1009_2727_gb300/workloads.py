@@ -304,25 +304,65 @@ def stage_run(ln0: float, a0: float, w0: float, tau: float, L: float, g: float, 
 
 
 def scaled_stage(gamma_boost: float, solver: str = "ck", theta: float = 0.0, filter_strides=None) -> dict:
-    """The scaled 0.1 GeV-class stage of Sec. 5.1 (n_e = 1e19 cm^-3) in the frame boosted by gamma_boost, for the
-    comparison of solvers, damping and smoothing against the frame (Sec. 5.1.2): the stage_run recipe with
-    a0 = 1.5, w0 = 12 um, tau = 30 fs and a 0.4 mm plasma; the given solver and Friedman theta (the time step
-    0.99 of that solver's limit with the damping's factor, or the singular step c dt = dz/sqrt(2) when that is
-    smaller), the stage's 4 passes + compensation, or a wide-band filter S(...) of one pass + compensation per
-    stride. The box grows along z with 1/gamma so that the slower frames keep the pulse and the beam inside;
-    every variant has the particle domain of the widest filter."""
+    """The scaled 0.1 GeV-class stage of Sec. 5.1 (n_e = 1e19 cm^-3, gamma_w = 13.2) in the frame boosted by
+    gamma_boost, for the comparison of solvers, damping and smoothing against the frame (Sec. 5.1.2): a0 = 1.5,
+    w0 = 12 um, tau = 30 fs, a 0.4 mm plasma behind a 20 um ramp, lambda/16 in the lab by 1.5 um cells, 2 x 2
+    particles per cell with rigid ions, cubic shapes, the given solver and Friedman theta (the time step 0.99 of
+    that solver's limit with the damping's factor, or the singular step c dt = dz/sqrt(2) for undamped CK),
+    the stage's 4 passes + compensation, or a wide-band filter S(...) of one pass + compensation per stride;
+    every variant has the particle domain of the widest filter. A 256-particle lab test beam at gamma_w rides
+    half a plasma wavelength behind the laser peak. The geometry follows the frame: the antenna sits far enough
+    up the box that the beam, which the boost holds nearly at rest when gamma_boost approaches gamma_w, starts
+    inside it; the plasma starts beyond the emitted pulse; the run ends when the plasma's end has passed the
+    beam and the laser's tail has left the plasma (the box grows along z to hold all of it)."""
+    c = 299792458.0
+    qe, me, eps0 = 1.602176634e-19, 9.1093837015e-31, 8.8541878128e-12
     g = float(gamma_boost)
-    nz = 1600 if g >= 4.0 else int(1600 * 4.0 / g) // 64 * 64
-    r = stage_run(25.0, 1.5, 12e-6, 30e-15, 0.4e-3, g, beam_seed=7, name=f"scaled_stage_g{g:g}_{solver}_th{theta:g}",
-                  nz=nz)
-    r["solver"] = SOLVERS[solver]
-    r["theta"] = float(theta)
-    # one particle domain for every variant: the guard of the widest filter, S(1:2:4) with one pass +
-    # compensation per stride (shape reach 3 + halo 14 + 2)
-    r["particle_guard"] = 19
+    n0, a0, w0, tau, L, ramp = 1e25, 1.5, 12e-6, 30e-15, 0.4e-3, 20e-6
+    beta = np.sqrt(1.0 - 1.0 / g ** 2)
+    dz_lab = LAMBDA0 / 16.0
+    dz_b = (1.0 + beta) * g * dz_lab
+    nx, dx = 96, 1.5e-6
+    dt = dz_b / (np.sqrt(2.0) * c)
+    t_peak = 1.6 * tau
+    wp = np.sqrt(n0 * qe * qe / (eps0 * me))
+    lam_p = 2 * np.pi * c / wp
+    gw = (2 * np.pi * c / LAMBDA0) / wp
+    guard = 19
+    # the beam starts (t = 0, lab) half a plasma wavelength behind the laser peak, which is still c t_peak
+    # behind the antenna's lab position: the antenna sits that far (boosted) above the particle domain's edge
+    z_ant = (16 + guard + 8 + np.ceil((1.0 + beta) * g * (c * t_peak + 0.5 * lam_p + 2e-6) / dz_b)) * dz_b
+    t_emit = (1.0 + beta) * g * 2.0 * t_peak
+    gap = (np.ceil(beta * c * t_emit / dz_b) + 24) * dz_b
+    z_start_lab = g * (z_ant + gap)
+    z_peak0 = z_ant / ((1.0 + beta) * g) - c * t_peak
+    z_beam0 = z_peak0 - 0.5 * lam_p
+    x, z, ux, uy, uz = lab_beam(256, seed=7, gamma_b=gw, R_b=1e-6, L_b=0.5e-6, z_c=z_beam0, x_c=0.5 * nx * dx)
+    # end: the laser's tail leaves the plasma's end, and the plasma's end passes the beam (lab worldlines
+    # transformed: the beam crosses the lab plane z_start_lab + ramp + L at t = (plane - z_beam0) / v_b)
+    vb = c * np.sqrt(1.0 - 1.0 / gw ** 2)
+    z_end = gap + (ramp + L) / g
+    t_laser = t_emit + (z_end - beta * c * t_emit) / ((1.0 + beta) * c)
+    z_pl_end = z_start_lab + ramp + L
+    t_beam = g * ((z_pl_end - z_beam0) / vb - beta * z_pl_end / c)
+    steps = int(max(t_laser, t_beam) / dt) + 50
+    nz = int(np.ceil((z_ant + gap + (ramp + L) / g) / dz_b + 16 + guard + 40) / 64.0) * 64
+    r = {
+        "name": f"scaled_stage_g{g:g}_{solver}_th{theta:g}", "inputs": [np.log10(n0), a0, w0 * 1e6, tau * 1e15, L * 1e3, g],
+        "steps": steps, "emit_steps": int(t_emit / dt) + 1, "lambda_p": lam_p, "gamma_w": gw,
+        "nx": nx, "nz": max(nz, 640), "dz_lab": dz_lab, "dx": dx, "gamma_boost": g, "courant": 0.99, "dt": dt,
+        "solver": SOLVERS[solver], "theta": float(theta),
+        "pml_cells": 16, "pml_sigma_max": 4.0, "pml_delta": 5.0, "pml_power": 2.0, "pml_xi_exp": 1,
+        "filter_passes": 4, "filter_stride": 1, "filter_compensate": 1, "filter_J": 1, "filter_gather": 1,
+        "order": 3, "particle_guard": guard, "moving_window": 0, "window_beta": 0.0, "precision": "mixed",
+        "plasma": {"n0": n0, "z_start_lab": z_start_lab, "ramp_lab": ramp, "length_lab": L,
+                   "ppc_x": 2, "ppc_z": 2, "ions": 1},
+        "laser": {"lambda0": LAMBDA0, "a0": a0, "w0": w0, "tau_fwhm": tau, "t_peak": t_peak,
+                  "x_center": 0.5 * nx * dx, "phase": 0.0, "z_antenna": z_ant, "beta_s": 0.0},
+        "beam": {"x": x, "z": z, "ux": ux, "uy": uy, "uz": uz, "t_lab": 0.0, "z_plane_lab": z_start_lab},
+    }
     if solver != "ck" or theta != 0.0:
         r["dt"] = 0.0        # the library's step: courant x the solver's limit (Friedman factor included)
-        r["courant"] = 0.99
     if filter_strides:
         r["filter_strides"] = list(filter_strides)
         r["filter_passes"] = 1
