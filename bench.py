@@ -561,7 +561,7 @@ def run_1d(args):
     return 0
 
 
-def run_stage3d(args):
+def run_stage3d(args):  # noqa: C901
     """Config 3 as a whole run: the 3D stage (1024 x 128 x 128 cells, gamma 30, CK2 at c dt = dz/sqrt(2),
     Friedman 0.1, 16-cell PML, 4 passes + compensation) stepped --stage3d steps with lab-frame snapshots: one
     lab time per 50 boosted steps (the lab time at which the box centre's boosted time is a multiple of 50
@@ -576,6 +576,8 @@ def run_stage3d(args):
     torch.cuda.set_device(0)
     w = W.stage_3d()
     w["precision"] = args.precision
+    if args.theta >= 0.0:
+        w["theta"] = args.theta
     sim = Simulation(w, precision=args.precision)
     st = sim.stats()
     dt, dz, gam, be = st["dt"], st["dz"], st["gamma"], st["beta"]
@@ -681,7 +683,8 @@ def run_solver_accuracy(args):
     from paper_1009_2727_gb300.pic import Simulation
     torch.cuda.set_device(0)
     me_mev = 0.51099895000
-    cases = (("ck", "ck", 0.0, None), ("yee_friedman_1", "yee", 1.0, None), ("yee_S124", "yee", 0.0, (1, 2, 4)))
+    cases = (("ck", "ck", 0.0, None), ("ck_friedman_0.1", "ck", 0.1, None), ("yee_friedman_1", "yee", 1.0, None),
+             ("yee_S124", "yee", 0.0, (1, 2, 4)))
     out = []
     for g in (2.0, 3.0, 5.0, 8.0, 13.0):
         row = {"gamma_boost": g}
