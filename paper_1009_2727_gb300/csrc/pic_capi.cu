@@ -603,11 +603,15 @@ struct Sim : SimBase {
         timed_launches++;
       }
     };
-    // 1. Faraday + Friedman + PML-B (B^{n-1/2} -> B^{n+1/2}, Bavg)
+    // 1. Faraday + Friedman + PML-B (B^{n-1/2} -> B^{n+1/2}, Bavg), fused with the gather filter of E^n
+    //    where the filter allows
     tstart(1);
-    launch_faraday<T>(g, f, pt, h.a2, h.b2, cf.theta, friedman, c->stream);
-    // 2. gather copies (interpolated to the nodes for the 'momentum conserving' gather)
-    launch_filter_fields<T>(g, f, fs, filt_gather, tmaps, ctrl, c->stream);
+    const bool fused = launch_faraday_fused<T>(g, f, pt, h.a2, h.b2, cf.theta, friedman, fs, filt_gather, tmaps,
+                                               ctrl, c->stream);
+    if (!fused) launch_faraday<T>(g, f, pt, h.a2, h.b2, cf.theta, friedman, c->stream);
+    // 2. gather copies (interpolated to the nodes for the 'momentum conserving' gather): B_avg, and E^n
+    //    unless the fused kernel filtered it
+    launch_filter_fields<T>(g, f, fs, filt_gather, tmaps, ctrl, c->stream, fused ? 3 : 0);
     if (nodal) launch_nodal<T>(g, f, c->stream);
     tstop(1);
     c->launches += 1 + (filt_gather ? 1 : 0) + (nodal ? 1 : 0);

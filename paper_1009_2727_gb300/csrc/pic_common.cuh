@@ -252,16 +252,25 @@ struct TileMaps {
   CUtensorMap E[2];     // the two E buffers
   CUtensorMap J[2];     // the two current buffers
   CUtensorMap Bavg;
+  CUtensorMap Er[2];    // the two E buffers in small boxes (tile + one node, z aligned), when r_ok
+  CUtensorMap Eb[2];    // the two Friedman E-bar buffers in the same small boxes, when r_ok
   const void* Ebase[2];
   const void* Jbase[2];
+  const void* Ebbase[2];
   int H, HZ, BX, BZ;    // halo (cells), aligned z halo, box extents
-  bool ok;
+  bool ok, r_ok;
 };
 template <class T>
 bool make_tile_maps(const GridP& g, const FieldPtrs<T>& f, int H, TileMaps& tm);
+// the gather filter of components c_first..5 (E^n: 0..2, B_avg: 3..5)
 template <class T>
 void launch_filter_fields(const GridP& g, const FieldPtrs<T>& f, const FilterSpec& fs, bool enabled,
-                          const TileMaps& tm, Ctrl* ctrl, cudaStream_t s);
+                          const TileMaps& tm, Ctrl* ctrl, cudaStream_t s, int c_first = 0);
+// Faraday fused with the gather filter of E^n (false: not applicable, nothing launched)
+template <class T>
+bool launch_faraday_fused(const GridP& g, const FieldPtrs<T>& f, const PmlTabs& pt, double a2, double b2,
+                          double theta, bool friedman, const FilterSpec& fs, bool filt_gather, const TileMaps& tm,
+                          Ctrl* ctrl, cudaStream_t s);
 template <class T>
 void launch_ampere(const GridP& g, const FieldPtrs<T>& f, const PmlTabs& pt, const FilterSpec& fs, bool filter_on,
                    const double* ion_x, const double* ion_c, double ion_coef, const TileMaps& tm, Ctrl* ctrl,

@@ -16,6 +16,94 @@ constexpr int FT_X = 16;
 constexpr int FT_Z = 64;
 constexpr int FT_TY = 4;
 
+// B update of one tile from E_eff staged in shared memory: Ee[c] holds the tile and a one-node halo, row
+// stride SZ, node (i0 - 1 + li, k0 - 1 + lk) at li * SZ + lk (zero outside the grid)
+template <class T, bool CK>
+__device__ __forceinline__ void faraday_update(const GridP& g, const FieldPtrs<T>& f, const PmlTabs& pt,
+                                               const FarK<T>& q, const T* const* Ee, const int SZ, int i0,
+                                               int k0) {
+  const bool interior = i0 >= pt.iin0 && i0 + FT_X - 1 <= pt.iin1 && k0 >= pt.kin0 && k0 + FT_Z - 1 <= pt.kin1;
+  const T dt = T(g.dt), idx = T(1.0 / g.dx), idz = T(1.0 / g.dz);
+  const int k = k0 + threadIdx.x;
+  // the thread's B^{n-1/2} values of all its rows are loaded first, so that their latencies overlap (the
+  // stores of one row could otherwise alias the loads of the next)
+  constexpr int NR = FT_X / FT_TY;
+  T bx0[NR], by0[NR], bz0[NR];
+#pragma unroll
+  for (int r = 0; r < NR; r++) {
+    const int i = i0 + threadIdx.y + r * FT_TY;
+    const long p = (long)i * g.ld + k;
+    const bool in = i <= g.nx && k <= g.nz;
+    bx0[r] = (in && k <= g.nz - 1) ? f.B[0][p] : T(0);
+    bz0[r] = (in && i <= g.nx - 1) ? f.B[2][p] : T(0);
+    by0[r] = (in && i <= g.nx - 1 && k <= g.nz - 1) ? f.B[1][p] : T(0);
+  }
+#pragma unroll
+  for (int r = 0; r < NR; r++) {
+    const int ti = threadIdx.y + r * FT_TY;
+    const int i = i0 + ti;
+    if (i > g.nx || k > g.nz) continue;
+    const long p = (long)i * g.ld + k;
+    const int s0 = (ti + 1) * SZ + threadIdx.x + 1;   // node (i, k) in the staged tile
+    // Delta*_z at (i, k+1/2) and Delta*_x at (i+1/2, k) of component c
+    auto dsz = [&](int c) {
+      const T* E = Ee[c];
+      const T d0 = E[s0 + 1] - E[s0];
+      if (!CK) return d0 * idz;
+      const T dp = E[s0 + SZ + 1] - E[s0 + SZ];
+      const T dm = E[s0 - SZ + 1] - E[s0 - SZ];
+      return (q.a2 * d0 + q.b2 * (dp + dm)) * idz;
+    };
+    auto dsx = [&](int c) {
+      const T* E = Ee[c];
+      const T d0 = E[s0 + SZ] - E[s0];
+      if (!CK) return d0 * idx;
+      const T dp = E[s0 + SZ + 1] - E[s0 + 1];
+      const T dm = E[s0 + SZ - 1] - E[s0 - 1];
+      return (q.a2 * d0 + q.b2 * (dp + dm)) * idx;
+    };
+    // Bx at (i, k+1/2): dBx/dt = Delta*_z Ey
+    if (k <= g.nz - 1) {
+      const T d = dsz(EY);
+      const T bo = bx0[r];
+      T bn;
+      if (!interior && pt.sz_h[k] > 0.0) bn = T(pt.xz_h[k] * (double)bo + pt.cz_h[k] * (double)d);
+      else bn = bo + dt * d;
+      f.B[0][p] = bn;
+      f.Bavg[0][p] = T(0.5) * (bo + bn);
+    }
+    // Bz at (i+1/2, k): dBz/dt = -Delta*_x Ey
+    if (i <= g.nx - 1) {
+      const T d = dsx(EY);
+      const T bo = bz0[r];
+      T bn;
+      if (!interior && pt.sx_h[i] > 0.0) bn = T(pt.xx_h[i] * (double)bo - pt.cx_h[i] * (double)d);
+      else bn = bo - dt * d;
+      f.B[2][p] = bn;
+      f.Bavg[2][p] = T(0.5) * (bo + bn);
+    }
+    // By at (i+1/2, k+1/2): dBy/dt = -Delta*_z Ex + Delta*_x Ez; split in the PML
+    if (i <= g.nx - 1 && k <= g.nz - 1) {
+      const T a = dsz(EX);
+      const T b = dsx(EZ);
+      const T bo = by0[r];
+      T bn;
+      if (!interior && (pt.sx_h[i] > 0.0 || pt.sz_h[k] > 0.0)) {
+        double yz = pt.xz_h[k] * (double)f.Byz[p] - pt.cz_h[k] * (double)a;
+        double yx = pt.xx_h[i] * (double)f.Byx[p] + pt.cx_h[i] * (double)b;
+        f.Byz[p] = T(yz);
+        f.Byx[p] = T(yx);
+        bn = T(yx) + T(yz);
+      } else {
+        bn = bo - dt * (a - b);
+      }
+      f.B[1][p] = bn;
+      f.Bavg[1][p] = T(0.5) * (bo + bn);
+    }
+  }
+}
+
+
 // Faraday + PML-B over a tile of FT_X x FT_Z nodes (threads FT_Z x FT_TY). The
 // Friedman field E_eff (Eq. 7) of the tile's nodes and a one-node halo is built
 // once in shared memory (zero outside the grid); the Friedman average update
@@ -51,70 +139,8 @@ __device__ __forceinline__ void faraday_tile(const GridP& g, const FieldPtrs<T>&
     }
   }
   __syncthreads();
-  const bool interior = i0 >= pt.iin0 && i0 + FT_X - 1 <= pt.iin1 && k0 >= pt.kin0 && k0 + FT_Z - 1 <= pt.kin1;
-  const T dt = T(g.dt), idx = T(1.0 / g.dx), idz = T(1.0 / g.dz);
-  const int k = k0 + threadIdx.x;
-  for (int ti = threadIdx.y; ti < FT_X; ti += FT_TY) {
-    const int i = i0 + ti;
-    if (i > g.nx || k > g.nz) continue;
-    const long p = (long)i * g.ld + k;
-    const int s0 = (ti + 1) * SZ + threadIdx.x + 1;   // node (i, k) in the staged tile
-    // Delta*_z at (i, k+1/2) and Delta*_x at (i+1/2, k) of component c
-    auto dsz = [&](int c) {
-      const T* E = Ee[c];
-      const T d0 = E[s0 + 1] - E[s0];
-      if (!CK) return d0 * idz;
-      const T dp = E[s0 + SZ + 1] - E[s0 + SZ];
-      const T dm = E[s0 - SZ + 1] - E[s0 - SZ];
-      return (q.a2 * d0 + q.b2 * (dp + dm)) * idz;
-    };
-    auto dsx = [&](int c) {
-      const T* E = Ee[c];
-      const T d0 = E[s0 + SZ] - E[s0];
-      if (!CK) return d0 * idx;
-      const T dp = E[s0 + SZ + 1] - E[s0 + 1];
-      const T dm = E[s0 + SZ - 1] - E[s0 - 1];
-      return (q.a2 * d0 + q.b2 * (dp + dm)) * idx;
-    };
-    // Bx at (i, k+1/2): dBx/dt = Delta*_z Ey
-    if (k <= g.nz - 1) {
-      const T d = dsz(EY);
-      const T bo = f.B[0][p];
-      T bn;
-      if (!interior && pt.sz_h[k] > 0.0) bn = T(pt.xz_h[k] * (double)bo + pt.cz_h[k] * (double)d);
-      else bn = bo + dt * d;
-      f.B[0][p] = bn;
-      f.Bavg[0][p] = T(0.5) * (bo + bn);
-    }
-    // Bz at (i+1/2, k): dBz/dt = -Delta*_x Ey
-    if (i <= g.nx - 1) {
-      const T d = dsx(EY);
-      const T bo = f.B[2][p];
-      T bn;
-      if (!interior && pt.sx_h[i] > 0.0) bn = T(pt.xx_h[i] * (double)bo - pt.cx_h[i] * (double)d);
-      else bn = bo - dt * d;
-      f.B[2][p] = bn;
-      f.Bavg[2][p] = T(0.5) * (bo + bn);
-    }
-    // By at (i+1/2, k+1/2): dBy/dt = -Delta*_z Ex + Delta*_x Ez; split in the PML
-    if (i <= g.nx - 1 && k <= g.nz - 1) {
-      const T a = dsz(EX);
-      const T b = dsx(EZ);
-      const T bo = f.B[1][p];
-      T bn;
-      if (!interior && (pt.sx_h[i] > 0.0 || pt.sz_h[k] > 0.0)) {
-        double yz = pt.xz_h[k] * (double)f.Byz[p] - pt.cz_h[k] * (double)a;
-        double yx = pt.xx_h[i] * (double)f.Byx[p] + pt.cx_h[i] * (double)b;
-        f.Byz[p] = T(yz);
-        f.Byx[p] = T(yx);
-        bn = T(yx) + T(yz);
-      } else {
-        bn = bo - dt * (a - b);
-      }
-      f.B[1][p] = bn;
-      f.Bavg[1][p] = T(0.5) * (bo + bn);
-    }
-  }
+  const T* Eep[3] = {Ee[0], Ee[1], Ee[2]};
+  faraday_update<T, CK>(g, f, pt, q, Eep, SZ, i0, k0);
 }
 
 template <class T, bool FRIED, bool CK>
@@ -156,6 +182,15 @@ __device__ __forceinline__ void tma_load_box(void* dst, const CUtensorMap* map, 
       : "memory");
 }
 
+// a box copy counted by an expect_tx issued beforehand
+__device__ __forceinline__ void tma_copy_box(void* dst, const CUtensorMap* map, int z, int x, int c, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+          "r"(smem_u32(dst)),
+      "l"((unsigned long long)map), "r"(z), "r"(x), "r"(c), "r"(smem_u32(bar))
+      : "memory");
+}
+
 // bounded wait for the phase with the given parity; false on timeout
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   const uint32_t a = smem_u32(bar);
@@ -178,6 +213,12 @@ template <class T>
 __host__ __device__ __forceinline__ int tile_stride(const TileMaps& tm) {
   const int line = 128 / (int)sizeof(T);
   return (tm.BX * tm.BZ + line - 1) / line * line;
+}
+
+// the fused Faraday kernel's boxes of E^{n-1} and E-bar: FT_X + 2 rows by FT_Z + 8 columns, whole lines
+template <class T>
+__host__ __device__ constexpr int ring_stride() {
+  return ((FT_X + 2) * (FT_Z + 8) + 128 / (int)sizeof(T) - 1) / (128 / (int)sizeof(T)) * (128 / (int)sizeof(T));
 }
 
 __device__ __forceinline__ unsigned char* align128(unsigned char* p) {
@@ -232,6 +273,58 @@ struct Vec16<float> { typedef float4 type; static constexpr int n = 4; };
 template <>
 struct Vec16<double> { typedef double2 type; static constexpr int n = 2; };
 
+// FP32: the x-pass works on pairs of columns with packed FMAs (one 8-byte load and one FFMA2 serve two
+// columns). A pair must start at an even element both in the staged box and in B1; where the box's
+// first filter column is odd ((HZ - H) odd, HZ = H rounded up to 4), B1 carries one leading pad column
+// and the z-pass reads its window one element early.
+template <int P>
+__device__ __forceinline__ void filter_tile_fixed_f32(const float* A, int BZ, float* B1, float* Zb,
+                                                      const FilterTaps<float>& ft) {
+  constexpr int NT = 2 * P + 1, NW = 4 + 2 * P;
+  constexpr int WZ = FT_Z + 2 * P, WZP = filter_wzp(P);
+  constexpr int HZ = (P + 3) & ~3, PAD = (HZ - P) & 1;
+  constexpr int NPAIR = (WZ + PAD + 1) / 2;
+  static_assert(2 * NPAIR <= WZP, "B1 row holds the pad and every pair");
+  const int tid = threadIdx.y * FT_Z + threadIdx.x;
+  for (int task = tid; task < (FT_X / 4) * NPAIR; task += FT_Z * FT_TY) {
+    const int rq = task / NPAIR, cpair = task - rq * NPAIR;
+    const int r0 = 4 * rq, b = 2 * cpair;   // B1 column b <-> filter column b - PAD
+    const float* col = A + r0 * BZ + b - PAD;
+    float2 v[NW];
+#pragma unroll
+    for (int j = 0; j < NW; j++) v[j] = *reinterpret_cast<const float2*>(col + j * BZ);
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int j = 0; j < NT; j++) acc = __ffma2_rn(make_float2(ft.c[j], ft.c[j]), v[q + j], acc);
+      *reinterpret_cast<float2*>(B1 + (r0 + q) * WZP + b) = acc;
+    }
+  }
+  __syncthreads();
+  {
+    constexpr int NV = (NW + PAD + 3) / 4;   // float4 vectors covering the pad and the window
+    const int ti = tid >> 4, g4 = (tid & 15) * 4;
+    float v[NV * 4];
+    const float4* row = reinterpret_cast<const float4*>(B1 + ti * WZP + g4);
+#pragma unroll
+    for (int u = 0; u < NV; u++) {
+      const float4 x = row[u];
+      v[4 * u] = x.x; v[4 * u + 1] = x.y; v[4 * u + 2] = x.z; v[4 * u + 3] = x.w;
+    }
+    float o[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      float acc = 0.f;
+#pragma unroll
+      for (int j = 0; j < NT; j++) acc = fmaf(ft.c[j], v[PAD + q + j], acc);
+      o[q] = acc;
+    }
+    *reinterpret_cast<float4*>(Zb + ti * FT_Z + g4) = make_float4(o[0], o[1], o[2], o[3]);
+  }
+  __syncthreads();
+}
+
 template <class T, int P>
 __device__ __forceinline__ void filter_tile_fixed(const T* A, int BZ, T* B1, T* Zb, const FilterTaps<T>& ft) {
   constexpr int NT = 2 * P + 1, NW = 4 + 2 * P;
@@ -285,7 +378,8 @@ __device__ __forceinline__ void filter_tile_fixed(const T* A, int BZ, T* B1, T* 
 
 template <class T, int PT>
 __device__ __forceinline__ void filter_tile(const T* A, int BZ, T* B1, T* Zb, const FilterTaps<T>& ft) {
-  if constexpr (PT > 0) filter_tile_fixed<T, PT>(A, BZ, B1, Zb, ft);
+  if constexpr (PT > 0 && sizeof(T) == 4) filter_tile_fixed_f32<PT>(A, BZ, B1, Zb, ft);
+  else if constexpr (PT > 0) filter_tile_fixed<T, PT>(A, BZ, B1, Zb, ft);
   else filter_tile_any<T>(A, BZ, B1, Zb, ft);
 }
 
@@ -302,7 +396,8 @@ __device__ __forceinline__ void tile_timeout(Ctrl* ctrl, uint64_t* bar0, uint64_
 template <class T, int PT>
 __device__ __forceinline__ void filter_fields_tile(const GridP& g, const FieldPtrs<T>& f, const FilterTaps<T>& ft,
                                                    const CUtensorMap* pmapE, const CUtensorMap* pmapB,
-                                                   const TileMaps& tm, Ctrl* ctrl, int tile_k, int tile_i) {
+                                                   const TileMaps& tm, Ctrl* ctrl, int tile_k, int tile_i,
+                                                   int c_first = 0) {
   extern __shared__ __align__(128) unsigned char smraw[];
   T* tile0 = reinterpret_cast<T*>(align128(smraw));
   T* tile1 = tile0 + tile_stride<T>(tm);
@@ -319,12 +414,13 @@ __device__ __forceinline__ void filter_fields_tile(const GridP& g, const FieldPt
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  if (leader) stage<T>(tile0, pmapE, 0, gk0, gi0, &bar[0], tm);
-  for (int c = 0; c < 6; c++) {
-    T* A = (c & 1) ? tile1 : tile0;
+  if (leader) stage<T>(tile0, c_first < 3 ? pmapE : pmapB, c_first % 3, gk0, gi0, &bar[0], tm);
+  for (int c = c_first; c < 6; c++) {
+    const int u = c - c_first;   // staging slot and phase follow the components handled
+    T* A = (u & 1) ? tile1 : tile0;
     if (leader && c + 1 < 6)
-      stage<T>((c & 1) ? tile0 : tile1, c + 1 < 3 ? pmapE : pmapB, (c + 1) % 3, gk0, gi0, &bar[(c + 1) & 1], tm);
-    if (!mbar_wait(&bar[c & 1], (c >> 1) & 1)) {
+      stage<T>((u & 1) ? tile0 : tile1, c + 1 < 3 ? pmapE : pmapB, (c + 1) % 3, gk0, gi0, &bar[(u + 1) & 1], tm);
+    if (__syncthreads_or(!mbar_wait(&bar[u & 1], (u >> 1) & 1))) {   // block-uniform outcome
       tile_timeout(ctrl, &bar[0], &bar[1]);
       return;
     }
@@ -343,8 +439,99 @@ template <class T, int PT>
 __global__ void __launch_bounds__(FT_Z* FT_TY) k_filter_fields(GridP g, FieldPtrs<T> f, FilterTaps<T> ft,
                                                                const __grid_constant__ CUtensorMap mapE,
                                                                const __grid_constant__ CUtensorMap mapB, TileMaps tm,
-                                                               Ctrl* ctrl) {
-  filter_fields_tile<T, PT>(g, f, ft, &mapE, &mapB, tm, ctrl, blockIdx.x, blockIdx.y);
+                                                               Ctrl* ctrl, int c_first) {
+  filter_fields_tile<T, PT>(g, f, ft, &mapE, &mapB, tm, ctrl, blockIdx.x, blockIdx.y, c_first);
+}
+
+// Faraday with its E tiles staged by TMA, fused with the gather filter of E^n. One round of bulk tensor
+// copies brings the tile's E^n with the filter's halo (serving both the Friedman field and the filter)
+// and, under Friedman damping, E^{n-1} and E-bar on the tile and a one-node halo (boxes of FT_X + 2 rows
+// by FT_Z + 8 columns, starting 16-byte aligned at k0 - 4). E_eff (Eq. 7) is formed in place of the
+// staged E^{n-1}; B, B_avg and E-bar are updated as in k_faraday, then F(E^n) is written for the gather
+// (k_filter_fields then filters B_avg only).
+template <class T, bool FRIED, bool CK, int PT>
+__global__ void __launch_bounds__(FT_Z* FT_TY, 3) k_faraday_fused(GridP g, FieldPtrs<T> f, PmlTabs pt, FarK<T> q,
+                                                               FilterTaps<T> ft,
+                                                               const __grid_constant__ CUtensorMap mapE,
+                                                               const __grid_constant__ CUtensorMap mapEo,
+                                                               const __grid_constant__ CUtensorMap mapEb,
+                                                               TileMaps tm, Ctrl* ctrl) {
+  constexpr int SX = FT_X + 2, SZ = FT_Z + 2, RZ = FT_Z + 8;
+  extern __shared__ __align__(128) unsigned char smraw[];
+  const int stride = tile_stride<T>(tm);
+  const int rstride = ring_stride<T>();
+  T* A = reinterpret_cast<T*>(align128(smraw));   // E^n, three boxes with the filter halo
+  T* R = A + 3 * stride;                          // E^{n-1} then E-bar, three components each (FRIED)
+  const int H = ft.H;
+  T* B1 = R + (FRIED ? 6 * rstride : 0);
+  T* Zb = B1 + FT_X * filter_wzp(H);
+  __shared__ __align__(8) uint64_t bar[1];
+  const int i0 = blockIdx.y * FT_X, k0 = blockIdx.x * FT_Z;
+  const int gi0 = i0 - tm.H, gk0 = k0 - tm.HZ;
+  const bool leader = threadIdx.x == 0 && threadIdx.y == 0;
+  const int tid = threadIdx.y * FT_Z + threadIdx.x;
+  if (leader) {
+    mbar_init(&bar[0]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (leader) {
+    const uint32_t box = (uint32_t)(tm.BX * tm.BZ * sizeof(T)), rbox = (uint32_t)(SX * RZ * sizeof(T));
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&bar[0])),
+                 "r"(3 * box + (FRIED ? 6 * rbox : 0u))
+                 : "memory");
+    for (int c = 0; c < 3; c++) tma_copy_box(A + c * stride, &mapE, gk0, gi0, c, &bar[0]);
+    if (FRIED)
+      for (int c = 0; c < 3; c++) {
+        tma_copy_box(R + c * rstride, &mapEo, k0 - 4, i0 - 1, c, &bar[0]);
+        tma_copy_box(R + (3 + c) * rstride, &mapEb, k0 - 4, i0 - 1, c, &bar[0]);
+      }
+  }
+  // the wait's outcome is made block-uniform, so that no thread is left at a later barrier
+  if (__syncthreads_or(!mbar_wait(&bar[0], 0))) {
+    tile_timeout(ctrl, &bar[0], &bar[0]);
+    return;
+  }
+  const T* Eep[3];
+  int esz;
+  if (FRIED) {
+    // E_eff = c1 E^n + c2 E^{n-1} + c3 E-bar on the tile and its halo, in place of E^{n-1}; E-bar's update
+    // for the tile's own nodes
+    const int off = (tm.H - 1) * tm.BZ + (tm.HZ - 1);   // box element of node (i0 - 1, k0 - 1)
+    for (int c = 0; c < 3; c++) {
+      const T* Ac = A + c * stride;
+      T* Ro = R + c * rstride;
+      const T* Rb = R + (3 + c) * rstride;
+      for (int e = tid; e < SX * SZ; e += FT_Z * FT_TY) {
+        const int li = e / SZ, lk = e - li * SZ;
+        const int r = li * RZ + lk + 3;
+        const T en = Ac[off + li * tm.BZ + lk], eb = Rb[r];
+        Ro[r] = q.c1 * en + q.c2 * Ro[r] + q.c3 * eb;
+        const int i = i0 - 1 + li, k = k0 - 1 + lk;
+        if (li >= 1 && li <= FT_X && lk >= 1 && lk <= FT_Z && i <= g.nx && k <= g.nz)
+          f.Ebn[c][(long)i * g.ld + k] = q.h1 * en + q.h2 * eb;
+      }
+    }
+    Eep[0] = R + 3;
+    Eep[1] = R + rstride + 3;
+    Eep[2] = R + 2 * rstride + 3;
+    esz = RZ;
+    __syncthreads();
+  } else {
+    for (int c = 0; c < 3; c++) Eep[c] = A + c * stride + (tm.H - 1) * tm.BZ + (tm.HZ - 1);
+    esz = tm.BZ;
+  }
+  faraday_update<T, CK>(g, f, pt, q, Eep, esz, i0, k0);
+  // the gather copies of E^n: the filter of the staged boxes (filter halo H == tm.H)
+  const int gk = k0 + threadIdx.x;
+  for (int c = 0; c < 3; c++) {
+    filter_tile<T, PT>(A + c * stride + (tm.H - H) * tm.BZ + (tm.HZ - H), tm.BZ, B1, Zb, ft);
+    for (int ti = threadIdx.y; ti < FT_X; ti += FT_TY) {
+      const int gi = i0 + ti;
+      if (gi <= g.nx && gk <= g.nz) f.fE[c][(long)gi * g.ld + gk] = Zb[ti * FT_Z + threadIdx.x];
+    }
+  }
 }
 
 // Ampere + PML-E, with the current (plus the ion column current) filtered in the tile first
@@ -379,7 +566,7 @@ __device__ __forceinline__ void ampere_tile(const GridP& g, const FieldPtrs<T>& 
   for (int c = 0; c < 3; c++) {
     T* A = (c & 1) ? tile1 : tile0;
     if (leader && c + 1 < 3) stage<T>((c & 1) ? tile0 : tile1, pmapJ, c + 1, gk0, gi0, &bar[(c + 1) & 1], tm);
-    if (!mbar_wait(&bar[c & 1], (c >> 1) & 1)) {
+    if (__syncthreads_or(!mbar_wait(&bar[c & 1], (c >> 1) & 1))) {   // block-uniform outcome
       tile_timeout(ctrl, &bar[0], &bar[1]);
       return;
     }
@@ -406,9 +593,32 @@ __device__ __forceinline__ void ampere_tile(const GridP& g, const FieldPtrs<T>& 
     }
     int vi0, vi1, vk0, vk1;
     valid_range(c, g.nx, g.nz, vi0, vi1, vk0, vk1);
+    // E^n and the B^{n+1/2} values of the curl for the thread's rows, loaded before the filter so that
+    // their latency overlaps it
+    constexpr int NR = FT_X / FT_TY;
+    T e0[NR], ba[NR], bb[NR], bc[NR], bd[NR];
+#pragma unroll
+    for (int r = 0; r < NR; r++) {
+      const int i = i0 + threadIdx.y + r * FT_TY;
+      const long p = (long)i * g.ld + k;
+      const bool v = i <= g.nx && k <= g.nz && i >= vi0 && i <= vi1 && k >= vk0 && k <= vk1;
+      e0[r] = ba[r] = bb[r] = bc[r] = bd[r] = T(0);
+      if (v) {
+        e0[r] = f.E[c][p];
+        if (c == 0) {
+          ba[r] = f.B[1][p]; bb[r] = f.B[1][p - 1];
+        } else if (c == 2) {
+          ba[r] = f.B[1][p]; bb[r] = f.B[1][p - g.ld];
+        } else {
+          ba[r] = f.B[0][p]; bb[r] = f.B[0][p - 1]; bc[r] = f.B[2][p]; bd[r] = f.B[2][p - g.ld];
+        }
+      }
+    }
     if (FILT) filter_tile<T, PT>(A + (tm.H - H) * tm.BZ + (tm.HZ - H), tm.BZ, B1, Zb, ft);
     const bool interior = i0 >= pt.iin0 && i0 + FT_X - 1 <= pt.iin1 && k0 >= pt.kin0 && k0 + FT_Z - 1 <= pt.kin1;
-    for (int ti = threadIdx.y; ti < FT_X; ti += FT_TY) {
+#pragma unroll
+    for (int r = 0; r < NR; r++) {
+      const int ti = threadIdx.y + r * FT_TY;
       const int i = i0 + ti;
       if (i > g.nx || k > g.nz) continue;
       const long p = (long)i * g.ld + k;
@@ -419,19 +629,19 @@ __device__ __forceinline__ void ampere_tile(const GridP& g, const FieldPtrs<T>& 
         continue;
       }
       const T jv = FILT ? Zb[ti * FT_Z + threadIdx.x] : A[(ti + tm.H) * tm.BZ + threadIdx.x + tm.HZ];
-      const T eo = f.E[c][p];
+      const T eo = e0[r];
       T en;
       if (c == 0) {
-        T d = (f.B[1][p] - f.B[1][p - 1]) * idz;
+        T d = (ba[r] - bb[r]) * idz;
         if (!interior && pt.sz_i[k] > 0.0) en = T(pt.xz_i[k] * (double)eo - c2d * pt.cz_i[k] * (double)d);
         else en = eo - dt * (c2 * d + jv * ie0);
       } else if (c == 2) {
-        T d = (f.B[1][p] - f.B[1][p - g.ld]) * idx;
+        T d = (ba[r] - bb[r]) * idx;
         if (!interior && pt.sx_i[i] > 0.0) en = T(pt.xx_i[i] * (double)eo + c2d * pt.cx_i[i] * (double)d);
         else en = eo + dt * (c2 * d - jv * ie0);
       } else {
-        T dbx = (f.B[0][p] - f.B[0][p - 1]) * idz;
-        T dbz = (f.B[2][p] - f.B[2][p - g.ld]) * idx;
+        T dbx = (ba[r] - bb[r]) * idz;
+        T dbz = (bc[r] - bd[r]) * idx;
         if (!interior && (pt.sx_i[i] > 0.0 || pt.sz_i[k] > 0.0)) {
           double yz = pt.xz_i[k] * (double)f.Eyz[p] + c2d * pt.cz_i[k] * (double)dbx;
           double yx = pt.xx_i[i] * (double)f.Eyx[p] - c2d * pt.cx_i[i] * (double)dbz;
@@ -449,7 +659,7 @@ __device__ __forceinline__ void ampere_tile(const GridP& g, const FieldPtrs<T>& 
 }
 
 template <class T, bool FILT, int PT>
-__global__ void __launch_bounds__(FT_Z* FT_TY) k_ampere(GridP g, FieldPtrs<T> f, PmlTabs pt, FilterTaps<T> ft,
+__global__ void __launch_bounds__(FT_Z* FT_TY, sizeof(T) == 4 ? 4 : 2) k_ampere(GridP g, FieldPtrs<T> f, PmlTabs pt, FilterTaps<T> ft,
                                                         const double* ion_x, const double* ion_c, double ion_coef,
                                                         const __grid_constant__ CUtensorMap mapJ, TileMaps tm,
                                                         Ctrl* ctrl) {
@@ -489,7 +699,7 @@ __global__ void __launch_bounds__(FT_Z* FT_TY) k_filter_fields_batch(const StepA
 }
 
 template <class T, bool FILT, int PT>
-__global__ void __launch_bounds__(FT_Z* FT_TY) k_ampere_batch(const StepArgs<T>* a, const int* off, int nruns) {
+__global__ void __launch_bounds__(FT_Z* FT_TY, sizeof(T) == 4 ? 4 : 2) k_ampere_batch(const StepArgs<T>* a, const int* off, int nruns) {
   __shared__ int s_r;
   if (threadIdx.x == 0 && threadIdx.y == 0) {
     s_r = batch_run(off, nruns, blockIdx.x);
@@ -658,14 +868,16 @@ static EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// 3D tensor over a 3-component block: (nz+1) x (nx+1) x 3, rows ld elements apart, components cs apart
+// 3D tensor over a 3-component block: (nz+1) x (nx+1) x 3, rows ld elements apart, components cs apart;
+// boxes of bx rows by bz columns (the tile maps' BX x BZ by default)
 template <class T>
-static bool encode_block(CUtensorMap* m, const void* base, const GridP& g, const TileMaps& tm) {
+static bool encode_block(CUtensorMap* m, const void* base, const GridP& g, const TileMaps& tm, int bx = 0,
+                         int bz = 0) {
   EncodeTiledFn fn = encode_fn();
   if (!fn || !base) return false;
   const cuuint64_t dims[3] = {(cuuint64_t)(g.nz + 1), (cuuint64_t)(g.nx + 1), 3};
   const cuuint64_t strides[2] = {(cuuint64_t)g.ld * sizeof(T), (cuuint64_t)g.cs * sizeof(T)};
-  const cuuint32_t box[3] = {(cuuint32_t)tm.BZ, (cuuint32_t)tm.BX, 1};
+  const cuuint32_t box[3] = {(cuuint32_t)(bz ? bz : tm.BZ), (cuuint32_t)(bx ? bx : tm.BX), 1};
   const cuuint32_t es[3] = {1, 1, 1};
   const CUtensorMapDataType dt = sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   return fn(m, dt, 3, const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -680,7 +892,7 @@ bool make_tile_maps(const GridP& g, const FieldPtrs<T>& f, int H, TileMaps& tm) 
   tm.HZ = (H + 3) & ~3;
   tm.BX = FT_X + 2 * H;
   tm.BZ = FT_Z + 2 * tm.HZ;
-  tm.ok = false;
+  tm.ok = tm.r_ok = false;
   if (tm.BX > 256 || tm.BZ > 256) return false;
   if (tile_smem<T>(tm, H) > 227 * 1024) return false;
   tm.Ebase[0] = f.E[0];
@@ -691,6 +903,13 @@ bool make_tile_maps(const GridP& g, const FieldPtrs<T>& f, int H, TileMaps& tm) 
                   encode_block<T>(&tm.J[0], f.J[0], g, tm) && encode_block<T>(&tm.J[1], f.Jn[0], g, tm) &&
                   encode_block<T>(&tm.Bavg, f.Bavg[0], g, tm);
   tm.ok = ok;
+  // the fused Faraday kernel's small boxes of E^{n-1} and of Friedman's E-bar (FT_X + 2 by FT_Z + 8)
+  tm.Ebbase[0] = f.Eb[0];
+  tm.Ebbase[1] = f.Ebn[0];
+  tm.r_ok = f.Eb[0] && f.Ebn[0] && encode_block<T>(&tm.Er[0], f.E[0], g, tm, FT_X + 2, FT_Z + 8) &&
+            encode_block<T>(&tm.Er[1], f.Eo[0], g, tm, FT_X + 2, FT_Z + 8) &&
+            encode_block<T>(&tm.Eb[0], f.Eb[0], g, tm, FT_X + 2, FT_Z + 8) &&
+            encode_block<T>(&tm.Eb[1], f.Ebn[0], g, tm, FT_X + 2, FT_Z + 8);
   return ok;
 }
 
@@ -700,28 +919,85 @@ static int filter_pt(const FilterTaps<T>& ft) { return (ft.s == 1 && ft.P >= 1 &
 
 template <class T, int PT>
 static void run_filter_fields(dim3 grd, dim3 blk, size_t sm, cudaStream_t s, const GridP& g, const FieldPtrs<T>& f,
-                              const FilterTaps<T>& ft, const CUtensorMap& mE, const TileMaps& tm, Ctrl* ctrl) {
+                              const FilterTaps<T>& ft, const CUtensorMap& mE, const TileMaps& tm, Ctrl* ctrl,
+                              int c_first) {
   cudaFuncSetAttribute(k_filter_fields<T, PT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_filter_fields<T, PT><<<grd, blk, sm, s>>>(g, f, ft, mE, tm.Bavg, tm, ctrl);
+  k_filter_fields<T, PT><<<grd, blk, sm, s>>>(g, f, ft, mE, tm.Bavg, tm, ctrl, c_first);
 }
 
 template <class T>
 void launch_filter_fields(const GridP& g, const FieldPtrs<T>& f, const FilterSpec& fs, bool enabled,
-                          const TileMaps& tm, Ctrl* ctrl, cudaStream_t s) {
+                          const TileMaps& tm, Ctrl* ctrl, cudaStream_t s, int c_first) {
   if (!enabled) return;
   const FilterTaps<T> ft = make_taps<T>(fs);
   dim3 grd((g.nz + 1 + FT_Z - 1) / FT_Z, (g.nx + 1 + FT_X - 1) / FT_X), blk(FT_Z, FT_TY);
   const size_t sm = tile_smem<T>(tm, ft.H);
   const CUtensorMap& mE = tm.Ebase[0] == (const void*)f.E[0] ? tm.E[0] : tm.E[1];
   switch (filter_pt(ft)) {
-    case 1: run_filter_fields<T, 1>(grd, blk, sm, s, g, f, ft, mE, tm, ctrl); break;
-    case 2: run_filter_fields<T, 2>(grd, blk, sm, s, g, f, ft, mE, tm, ctrl); break;
-    case 3: run_filter_fields<T, 3>(grd, blk, sm, s, g, f, ft, mE, tm, ctrl); break;
-    case 4: run_filter_fields<T, 4>(grd, blk, sm, s, g, f, ft, mE, tm, ctrl); break;
-    case 5: run_filter_fields<T, 5>(grd, blk, sm, s, g, f, ft, mE, tm, ctrl); break;
-    case 6: run_filter_fields<T, 6>(grd, blk, sm, s, g, f, ft, mE, tm, ctrl); break;
-    default: run_filter_fields<T, 0>(grd, blk, sm, s, g, f, ft, mE, tm, ctrl); break;
+    case 1: run_filter_fields<T, 1>(grd, blk, sm, s, g, f, ft, mE, tm, ctrl, c_first); break;
+    case 2: run_filter_fields<T, 2>(grd, blk, sm, s, g, f, ft, mE, tm, ctrl, c_first); break;
+    case 3: run_filter_fields<T, 3>(grd, blk, sm, s, g, f, ft, mE, tm, ctrl, c_first); break;
+    case 4: run_filter_fields<T, 4>(grd, blk, sm, s, g, f, ft, mE, tm, ctrl, c_first); break;
+    case 5: run_filter_fields<T, 5>(grd, blk, sm, s, g, f, ft, mE, tm, ctrl, c_first); break;
+    case 6: run_filter_fields<T, 6>(grd, blk, sm, s, g, f, ft, mE, tm, ctrl, c_first); break;
+    default: run_filter_fields<T, 0>(grd, blk, sm, s, g, f, ft, mE, tm, ctrl, c_first); break;
   }
+}
+
+// shared memory of the fused Faraday kernel: four staged boxes, E_eff, the filter's scratch
+template <class T>
+static size_t fused_smem(const TileMaps& tm, int H, bool fried) {
+  return (3 * (size_t)tile_stride<T>(tm) + (fried ? 6 * (size_t)ring_stride<T>() : 0) +
+          (size_t)FT_X * filter_wzp(H) + (size_t)FT_X * FT_Z) * sizeof(T) + 128;
+}
+
+template <class T, bool FRIED, bool CK, int PT>
+static bool run_faraday_fused(dim3 grd, dim3 blk, cudaStream_t s, const GridP& g, const FieldPtrs<T>& f,
+                              const PmlTabs& pt, const FarK<T>& q, const FilterTaps<T>& ft, const TileMaps& tm,
+                              Ctrl* ctrl) {
+  const size_t sm = fused_smem<T>(tm, ft.H, FRIED);
+  if (sm > 227 * 1024) return false;
+  const bool cur0 = tm.Ebase[0] == (const void*)f.E[0];
+  const CUtensorMap& mE = cur0 ? tm.E[0] : tm.E[1];
+  const CUtensorMap& mEo = cur0 ? tm.Er[1] : tm.Er[0];
+  const CUtensorMap& mEb = tm.Ebbase[0] == (const void*)f.Eb[0] ? tm.Eb[0] : tm.Eb[1];
+  cudaFuncSetAttribute(k_faraday_fused<T, FRIED, CK, PT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_faraday_fused<T, FRIED, CK, PT><<<grd, blk, sm, s>>>(g, f, pt, q, ft, mE, mEo, mEb, tm, ctrl);
+  return true;
+}
+
+// Faraday fused with the gather filter of E (TMA-staged E tiles). False when the fused kernel does not
+// apply (no gather filter, a strided filter, other than one or five passes, E-bar descriptors missing):
+// the caller then runs launch_faraday and launch_filter_fields over all six components.
+template <class T>
+bool launch_faraday_fused(const GridP& g, const FieldPtrs<T>& f, const PmlTabs& pt, double a2, double b2,
+                          double theta, bool friedman, const FilterSpec& fs, bool filt_gather, const TileMaps& tm,
+                          Ctrl* ctrl, cudaStream_t s) {
+  if (!filt_gather || !tm.ok || (friedman && !tm.r_ok)) return false;
+  const FilterTaps<T> ft = make_taps<T>(fs);
+  const int ptc = filter_pt(ft);
+  if (ft.H != tm.H) return false;
+  const FarK<T> q = faraday_coefs<T>(a2, b2, theta);
+  dim3 blk(FT_Z, FT_TY), grd((g.nz + 1 + FT_Z - 1) / FT_Z, (g.nx + 1 + FT_X - 1) / FT_X);
+  const bool ck = b2 != 0.0;
+  // one pass (the single binomial pass) and five (four passes and the compensation)
+  if (ptc == 5) {
+    if (friedman) {
+      if (ck) return run_faraday_fused<T, true, true, 5>(grd, blk, s, g, f, pt, q, ft, tm, ctrl);
+      return run_faraday_fused<T, true, false, 5>(grd, blk, s, g, f, pt, q, ft, tm, ctrl);
+    }
+    if (ck) return run_faraday_fused<T, false, true, 5>(grd, blk, s, g, f, pt, q, ft, tm, ctrl);
+    return run_faraday_fused<T, false, false, 5>(grd, blk, s, g, f, pt, q, ft, tm, ctrl);
+  }
+  if (ptc == 1) {
+    if (friedman) {
+      if (ck) return run_faraday_fused<T, true, true, 1>(grd, blk, s, g, f, pt, q, ft, tm, ctrl);
+      return run_faraday_fused<T, true, false, 1>(grd, blk, s, g, f, pt, q, ft, tm, ctrl);
+    }
+    if (ck) return run_faraday_fused<T, false, true, 1>(grd, blk, s, g, f, pt, q, ft, tm, ctrl);
+    return run_faraday_fused<T, false, false, 1>(grd, blk, s, g, f, pt, q, ft, tm, ctrl);
+  }
+  return false;
 }
 
 template <class T, bool FILT, int PT>
@@ -776,7 +1052,9 @@ size_t tile_smem_bytes(const TileMaps& tm, int H) { return tile_smem<T>(tm, H); 
   template void launch_ampere_batch<T>(const StepArgs<T>*, const BatchGrid&, bool, int, size_t, cudaStream_t);      \
   template bool make_tile_maps<T>(const GridP&, const FieldPtrs<T>&, int, TileMaps&);                            \
   template void launch_filter_fields<T>(const GridP&, const FieldPtrs<T>&, const FilterSpec&, bool, const TileMaps&, \
-                                        Ctrl*, cudaStream_t);                                                    \
+                                        Ctrl*, cudaStream_t, int);                                               \
+  template bool launch_faraday_fused<T>(const GridP&, const FieldPtrs<T>&, const PmlTabs&, double, double, double,  \
+                                        bool, const FilterSpec&, bool, const TileMaps&, Ctrl*, cudaStream_t);   \
   template void launch_ampere<T>(const GridP&, const FieldPtrs<T>&, const PmlTabs&, const FilterSpec&, bool,       \
                                  const double*, const double*, double, const TileMaps&, Ctrl*, cudaStream_t);
 INSTF(float)

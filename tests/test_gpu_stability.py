@@ -1,7 +1,8 @@
 """Sec. 5, scan of the time step: on the 2D stage workload the gather from the Yee locations keeps the
 high-k E_z power low up to the singular step c dt = dz/sqrt(2) and far lower than at 0.8, while the
 node-interpolated ('momentum conserving') gather lets the instability grow by orders of magnitude more at
-the same step (the paper: high at every step). Mixed path, one GB300."""
+the same step (the paper: high at every step). Mixed path, one GB300. And the need for damping or
+smoothing at high boosts (Sec. 5.1.2)."""
 import numpy as np
 import pytest
 
@@ -20,3 +21,31 @@ def test_dt_scan_energy_vs_momentum_conserving_gather():
     # measured: 2.7e22 at dz/sqrt(2) and 3.4e23 at 0.8 (energy conserving), 3.9e29 (momentum conserving)
     assert ec[0.8] > 3.0 * ec[0.7071]
     assert mc > 1e3 * ec[0.7071]
+
+
+def test_scaled_stage_high_gamma_needs_damping_or_smoothing():
+    """Sec. 5.1.2 on the scaled stage (n_e = 1e19 cm^-3) boosted by gamma = 13, to the same physical time:
+    the undamped CK run at its singular step grows without bound and loses the test beam, while Yee with
+    Friedman theta = 1 and Yee with the wide-band filter S(1:2:4) stay at the laser's energy and keep the beam"""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1009_2727_gb300 import workloads as W
+    from paper_1009_2727_gb300.pic import Simulation
+    g = 13.0
+    t_end = W.scaled_stage(g)["steps"] * W.scaled_stage(g)["dt"]
+    out = {}
+    for name, solver, theta, strides in (("ck", "ck", 0.0, None), ("yee_f1", "yee", 1.0, None),
+                                         ("yee_S124", "yee", 0.0, (1, 2, 4))):
+        w = W.scaled_stage(g, solver, theta, strides)
+        sim = Simulation(w, precision="mixed")
+        sim.step(int(np.ceil(t_end / sim.stats()["dt"])))
+        sim.sync()
+        out[name] = sim.stats()
+        sim.close()
+    # measured on GB300: field energy 1.0e5 (CK) against 45 and 70; beam particles active 0, 255, 256 of 256
+    for name in ("yee_f1", "yee_S124"):
+        assert np.isfinite(out[name]["field_energy"])
+        assert out[name]["n_beam_active"] >= 240, (name, out[name]["n_beam_active"])
+        assert out["ck"]["field_energy"] > 100.0 * out[name]["field_energy"]
+    assert out["ck"]["n_beam_active"] < 128
