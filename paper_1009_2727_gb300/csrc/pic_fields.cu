@@ -277,9 +277,12 @@ struct Vec16<double> { typedef double2 type; static constexpr int n = 2; };
 // columns). A pair must start at an even element both in the staged box and in B1; where the box's
 // first filter column is odd ((HZ - H) odd, HZ = H rounded up to 4), B1 carries one leading pad column
 // and the z-pass reads its window one element early.
-template <int P>
+// With STORE the z-pass writes its four outputs straight to dst (row i0 + ti, columns k0 + g4 ...; a
+// 16-byte store where all four lie inside the grid) instead of to Zb.
+template <int P, bool STORE = false>
 __device__ __forceinline__ void filter_tile_fixed_f32(const float* A, int BZ, float* B1, float* Zb,
-                                                      const FilterTaps<float>& ft) {
+                                                      const FilterTaps<float>& ft, float* dst = nullptr,
+                                                      const GridP* g = nullptr, int i0 = 0, int k0 = 0) {
   constexpr int NT = 2 * P + 1, NW = 4 + 2 * P;
   constexpr int WZ = FT_Z + 2 * P, WZP = filter_wzp(P);
   constexpr int HZ = (P + 3) & ~3, PAD = (HZ - P) & 1;
@@ -320,7 +323,21 @@ __device__ __forceinline__ void filter_tile_fixed_f32(const float* A, int BZ, fl
       for (int j = 0; j < NT; j++) acc = fmaf(ft.c[j], v[PAD + q + j], acc);
       o[q] = acc;
     }
-    *reinterpret_cast<float4*>(Zb + ti * FT_Z + g4) = make_float4(o[0], o[1], o[2], o[3]);
+    if constexpr (STORE) {
+      const int gi = i0 + ti, gk = k0 + g4;
+      if (gi <= g->nx) {
+        float* d = dst + (long)gi * g->ld + gk;
+        if (gk + 3 <= g->nz) {
+          *reinterpret_cast<float4*>(d) = make_float4(o[0], o[1], o[2], o[3]);
+        } else {
+#pragma unroll
+          for (int q = 0; q < 4; q++)
+            if (gk + q <= g->nz) d[q] = o[q];
+        }
+      }
+    } else {
+      *reinterpret_cast<float4*>(Zb + ti * FT_Z + g4) = make_float4(o[0], o[1], o[2], o[3]);
+    }
   }
   __syncthreads();
 }
@@ -383,6 +400,22 @@ __device__ __forceinline__ void filter_tile(const T* A, int BZ, T* B1, T* Zb, co
   else filter_tile_any<T>(A, BZ, B1, Zb, ft);
 }
 
+// the filtered tile written to dst (the tile's nodes inside the grid)
+template <class T, int PT>
+__device__ __forceinline__ void filter_tile_to(const T* A, int BZ, T* B1, T* Zb, const FilterTaps<T>& ft, T* dst,
+                                               const GridP& g, int i0, int k0) {
+  if constexpr (PT > 0 && sizeof(T) == 4) {
+    filter_tile_fixed_f32<PT, true>(A, BZ, B1, Zb, ft, dst, &g, i0, k0);
+  } else {
+    filter_tile<T, PT>(A, BZ, B1, Zb, ft);
+    const int gk = k0 + threadIdx.x;
+    for (int ti = threadIdx.y; ti < FT_X; ti += FT_TY) {
+      const int gi = i0 + ti;
+      if (gi <= g.nx && gk <= g.nz) dst[(long)gi * g.ld + gk] = Zb[ti * FT_Z + threadIdx.x];
+    }
+  }
+}
+
 __device__ __forceinline__ void tile_timeout(Ctrl* ctrl, uint64_t* bar0, uint64_t* bar1) {
   if (threadIdx.x == 0 && threadIdx.y == 0) {
     atomicOr(&ctrl->status, ST_TIMEOUT);
@@ -425,12 +458,7 @@ __device__ __forceinline__ void filter_fields_tile(const GridP& g, const FieldPt
       return;
     }
     T* dst = c < 3 ? f.fE[c] : f.fB[c - 3];
-    filter_tile<T, PT>(A + (tm.H - H) * tm.BZ + (tm.HZ - H), tm.BZ, B1, Zb, ft);
-    const int gk = k0 + threadIdx.x;
-    for (int ti = threadIdx.y; ti < FT_X; ti += FT_TY) {
-      const int gi = i0 + ti;
-      if (gi <= g.nx && gk <= g.nz) dst[(long)gi * g.ld + gk] = Zb[ti * FT_Z + threadIdx.x];
-    }
+    filter_tile_to<T, PT>(A + (tm.H - H) * tm.BZ + (tm.HZ - H), tm.BZ, B1, Zb, ft, dst, g, i0, k0);
     // Zb and the other staging buffer are rewritten only after the next filter_tile's first barrier
   }
 }
@@ -469,7 +497,6 @@ __global__ void __launch_bounds__(FT_Z* FT_TY, 3) k_faraday_fused(GridP g, Field
   const int i0 = blockIdx.y * FT_X, k0 = blockIdx.x * FT_Z;
   const int gi0 = i0 - tm.H, gk0 = k0 - tm.HZ;
   const bool leader = threadIdx.x == 0 && threadIdx.y == 0;
-  const int tid = threadIdx.y * FT_Z + threadIdx.x;
   if (leader) {
     mbar_init(&bar[0]);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -499,19 +526,29 @@ __global__ void __launch_bounds__(FT_Z* FT_TY, 3) k_faraday_fused(GridP g, Field
     // E_eff = c1 E^n + c2 E^{n-1} + c3 E-bar on the tile and its halo, in place of E^{n-1}; E-bar's update
     // for the tile's own nodes
     const int off = (tm.H - 1) * tm.BZ + (tm.HZ - 1);   // box element of node (i0 - 1, k0 - 1)
+    // E-bar's update of the tile's own nodes first (read before E_eff overwrites nothing it needs: E_eff
+    // replaces E^{n-1}, E-bar's box is only read)
+    const int k = k0 + threadIdx.x;
+#pragma unroll
     for (int c = 0; c < 3; c++) {
-      const T* Ac = A + c * stride;
-      T* Ro = R + c * rstride;
-      const T* Rb = R + (3 + c) * rstride;
-      for (int e = tid; e < SX * SZ; e += FT_Z * FT_TY) {
-        const int li = e / SZ, lk = e - li * SZ;
-        const int r = li * RZ + lk + 3;
-        const T en = Ac[off + li * tm.BZ + lk], eb = Rb[r];
-        Ro[r] = q.c1 * en + q.c2 * Ro[r] + q.c3 * eb;
-        const int i = i0 - 1 + li, k = k0 - 1 + lk;
-        if (li >= 1 && li <= FT_X && lk >= 1 && lk <= FT_Z && i <= g.nx && k <= g.nz)
-          f.Ebn[c][(long)i * g.ld + k] = q.h1 * en + q.h2 * eb;
+      const T* Ac = A + c * stride + off + tm.BZ + 1;
+      const T* Rb = R + (3 + c) * rstride + RZ + 4;
+#pragma unroll
+      for (int r = 0; r < FT_X / FT_TY; r++) {
+        const int ti = threadIdx.y + r * FT_TY, i = i0 + ti;
+        if (i <= g.nx && k <= g.nz)
+          f.Ebn[c][(long)i * g.ld + k] = q.h1 * Ac[ti * tm.BZ + threadIdx.x] + q.h2 * Rb[ti * RZ + threadIdx.x];
       }
+    }
+    for (int c = 0; c < 3; c++) {
+      const T* Ac = A + c * stride + off;
+      T* Ro = R + c * rstride + 3;
+      const T* Rb = R + (3 + c) * rstride + 3;
+      for (int li = threadIdx.y; li < SX; li += FT_TY)
+        for (int lk = threadIdx.x; lk < SZ; lk += FT_Z) {
+          const int r = li * RZ + lk;
+          Ro[r] = q.c1 * Ac[li * tm.BZ + lk] + q.c2 * Ro[r] + q.c3 * Rb[r];
+        }
     }
     Eep[0] = R + 3;
     Eep[1] = R + rstride + 3;
@@ -524,14 +561,8 @@ __global__ void __launch_bounds__(FT_Z* FT_TY, 3) k_faraday_fused(GridP g, Field
   }
   faraday_update<T, CK>(g, f, pt, q, Eep, esz, i0, k0);
   // the gather copies of E^n: the filter of the staged boxes (filter halo H == tm.H)
-  const int gk = k0 + threadIdx.x;
-  for (int c = 0; c < 3; c++) {
-    filter_tile<T, PT>(A + c * stride + (tm.H - H) * tm.BZ + (tm.HZ - H), tm.BZ, B1, Zb, ft);
-    for (int ti = threadIdx.y; ti < FT_X; ti += FT_TY) {
-      const int gi = i0 + ti;
-      if (gi <= g.nx && gk <= g.nz) f.fE[c][(long)gi * g.ld + gk] = Zb[ti * FT_Z + threadIdx.x];
-    }
-  }
+  for (int c = 0; c < 3; c++)
+    filter_tile_to<T, PT>(A + c * stride + (tm.H - H) * tm.BZ + (tm.HZ - H), tm.BZ, B1, Zb, ft, f.fE[c], g, i0, k0);
 }
 
 // Ampere + PML-E, with the current (plus the ion column current) filtered in the tile first
