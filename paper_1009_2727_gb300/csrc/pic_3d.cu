@@ -669,11 +669,34 @@ __global__ void __launch_bounds__(256) k3_push_tiles(G3 g, Fld3<T> f, Parts3<T> 
   const int tz = tile % t.nt[2], r = tile / t.nt[2];
   const int ty = r % t.nt[1], tx = r / t.nt[1];
   const int c0[3] = {tx * TX, ty * TY, tz * TZ};          // the tile's first cell; the window starts WM before
-  for (int e = threadIdx.x; e < 6 * WN; e += blockDim.x) {
-    const int c = e / WN, n = e - c * WN;
-    const int a = n / (WY * WZ), rr = n - a * (WY * WZ), b = rr / WZ, k = rr - b * WZ;
-    const T* F = c < 3 ? f.fE[c] : f.fB[c - 3];
-    sF[e] = rd3(g, F, c0[0] - WM + a, c0[1] - WM + b, c0[2] - WM + k);
+  // the window line by line: a warp per (component, x, y) line, a lane per z node (WZ <= 32), so that the
+  // index arithmetic is paid once per line; a window clear of the grid's faces skips the bounds checks
+  static_assert(WZ <= 32, "one lane per z node of a window line");
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const bool clear = c0[0] - WM >= 0 && c0[1] - WM >= 0 && c0[2] - WM >= 0 && c0[0] - WM + WX - 1 <= g.n[0] &&
+                     c0[1] - WM + WY - 1 <= g.n[1] && c0[2] - WM + WZ - 1 <= g.n[2];
+  const long line_stride = (long)(g.n[1] + 1) * g.ldz;   // nid step along x
+  // each warp takes SU consecutive lines at a time and issues their loads together (one round trip to
+  // L2 or HBM per SU lines instead of one per line)
+  constexpr int NL = 6 * WX * WY, SU = 8;
+  for (int l0 = warp * SU; l0 < NL; l0 += nwarps * SU) {
+    T v[SU];
+#pragma unroll
+    for (int u = 0; u < SU; u++) {
+      const int line = l0 + u;
+      v[u] = T(0);
+      if (line < NL && lane < WZ) {
+        const int c = line / (WX * WY), ab = line - c * (WX * WY);
+        const int a = ab / WY, b = ab - a * WY;
+        const T* F =
+            c == 0 ? f.fE[0] : c == 1 ? f.fE[1] : c == 2 ? f.fE[2] : c == 3 ? f.fB[0] : c == 4 ? f.fB[1] : f.fB[2];
+        const int i = c0[0] - WM + a, jj = c0[1] - WM + b, k = c0[2] - WM + lane;
+        v[u] = clear ? F[(long)i * line_stride + (long)jj * g.ldz + k] : rd3(g, F, i, jj, k);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < SU; u++)
+      if (l0 + u < NL && lane < WZ) sF[(l0 + u) * WZ + lane] = v[u];
   }
   for (int e = threadIdx.x; e < 3 * WN; e += blockDim.x) sJ[e] = T(0);
   __syncthreads();
@@ -729,20 +752,25 @@ __global__ void __launch_bounds__(256) k3_push_tiles(G3 g, Fld3<T> f, Parts3<T> 
     T EB[6];
 #pragma unroll
     for (int c = 0; c < 6; c++) {
-      // Yee locations; every component at the nodes for the 'momentum conserving' gather (MC)
+      // Yee locations; every component at the nodes for the 'momentum conserving' gather (MC). The
+      // tensor-product sum taken axis by axis: z within each (x, y) row, then y, then x
       const int hx = MC ? 0 : c < 3 ? (c == 0) : (c != 3), hy = MC ? 0 : c < 3 ? (c == 1) : (c != 4),
                 hz = MC ? 0 : c < 3 ? (c == 2) : (c != 5);
-      const T* F = sF + c * WN;
+      const T* F = sF + c * WN + (bl[0][hx] * WY + bl[1][hy]) * WZ + bl[2][hz];
       T acc = T(0);
 #pragma unroll
-      for (int l0 = 0; l0 < NS; l0++)
+      for (int l0 = 0; l0 < NS; l0++) {
+        T accy = T(0);
 #pragma unroll
         for (int l1 = 0; l1 < NS; l1++) {
-          const T w01 = wg[0][hx][l0] * wg[1][hy][l1];
-          const T* row = F + ((bl[0][hx] + l0) * WY + (bl[1][hy] + l1)) * WZ + bl[2][hz];
+          const T* row = F + (l0 * WY + l1) * WZ;
+          T accz = T(0);
 #pragma unroll
-          for (int l2 = 0; l2 < NS; l2++) acc += row[l2] * (w01 * wg[2][hz][l2]);
+          for (int l2 = 0; l2 < NS; l2++) accz += row[l2] * wg[2][hz][l2];
+          accy += wg[1][hy][l1] * accz;
         }
+        acc += wg[0][hx][l0] * accy;
+      }
       EB[c] = acc;
     }
     T u[3] = {p.ux[j], p.uy[j], p.uz[j]};
@@ -835,14 +863,17 @@ __global__ void __launch_bounds__(256) k3_push_tiles(G3 g, Fld3<T> f, Parts3<T> 
     if (out) p.fl[j] = 0;
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < 3 * WN; e += blockDim.x) {
-    const T v = sJ[e];
+  // the window's current added to J line by line, as it was staged
+  for (int line = warp; line < 3 * WX * WY; line += nwarps) {
+    if (lane >= WZ) continue;
+    const T v = sJ[line * WZ + lane];
     if (v == T(0)) continue;
-    const int c = e / WN, n = e - c * WN;
-    const int a = n / (WY * WZ), rr = n - a * (WY * WZ), b = rr / WZ, k = rr - b * WZ;
-    const int i = c0[0] - WM + a, jj = c0[1] - WM + b, kk = c0[2] - WM + k;
-    if (i < 0 || i > g.n[0] || jj < 0 || jj > g.n[1] || kk < 0 || kk > g.n[2]) continue;
-    atomicAdd(f.J[c] + nid(g, i, jj, kk), v);
+    const int c = line / (WX * WY), ab = line - c * (WX * WY);
+    const int a = ab / WY, b = ab - a * WY;
+    const int i = c0[0] - WM + a, jj = c0[1] - WM + b, kk = c0[2] - WM + lane;
+    if (!clear && (i < 0 || i > g.n[0] || jj < 0 || jj > g.n[1] || kk < 0 || kk > g.n[2])) continue;
+    T* J = c == 0 ? f.J[0] : c == 1 ? f.J[1] : f.J[2];
+    atomicAdd(J + (long)i * line_stride + (long)jj * g.ldz + kk, v);
   }
 }
 
