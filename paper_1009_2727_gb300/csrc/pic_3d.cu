@@ -537,9 +537,11 @@ __device__ __forceinline__ void boris3(T* u, const T* E, const T* B, T k) {
   const T ic2 = T(1.0 / (kC * kC));
   const T um0 = u[0] + k * E[0], um1 = u[1] + k * E[1], um2 = u[2] + k * E[2];
   const T gm = sqrt(T(1) + (um0 * um0 + um1 * um1 + um2 * um2) * ic2);
-  const T t0 = k * B[0] / gm, t1 = k * B[1] / gm, t2 = k * B[2] / gm;
+  const T kg = k / gm;   // one division each for k/gamma and 2/(1 + t^2)
+  const T t0 = kg * B[0], t1 = kg * B[1], t2 = kg * B[2];
   const T tt = t0 * t0 + t1 * t1 + t2 * t2;
-  const T s0 = T(2) * t0 / (T(1) + tt), s1 = T(2) * t1 / (T(1) + tt), s2 = T(2) * t2 / (T(1) + tt);
+  const T sf = T(2) / (T(1) + tt);
+  const T s0 = sf * t0, s1 = sf * t1, s2 = sf * t2;
   const T up0 = um0 + (um1 * t2 - um2 * t1), up1 = um1 + (um2 * t0 - um0 * t2), up2 = um2 + (um0 * t1 - um1 * t0);
   const T pl0 = um0 + (up1 * s2 - up2 * s1), pl1 = um1 + (up2 * s0 - up0 * s2), pl2 = um2 + (up0 * s1 - up1 * s0);
   u[0] = pl0 + k * E[0];
@@ -565,6 +567,8 @@ constexpr int TX = 4, TY = 4, TZ = 16;
 constexpr int WM = 3;
 constexpr int WX = TX + 2 * WM + 1, WY = TY + 2 * WM + 1, WZ = TZ + 2 * WM + 1;
 constexpr int WN = WX * WY * WZ;
+// window element stride along axis a
+__host__ __device__ constexpr int wstride(int a) { return a == 0 ? WY * WZ : a == 1 ? WZ : 1; }
 
 struct Tiles3 {
   int nt[3];
@@ -777,9 +781,10 @@ __global__ void __launch_bounds__(256) k3_push_tiles(G3 g, Fld3<T> f, Parts3<T> 
     boris3<T>(u, EB, EB + 3, kq);
     const T gm = sqrt(T(1) + (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]) * T(1.0 / (kC * kC)));
     T X1[3], Dm[3];
+    const T ig = T(1) / gm;
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-      Dm[a] = dtT * (u[a] / gm);          // displacement [m]
+      Dm[a] = dtT * (u[a] * ig);          // displacement [m]
       X1[a] = X[a] + Dm[a] * invT[a];
     }
     // Esirkepov into the shared window
@@ -805,17 +810,22 @@ __global__ void __launch_bounds__(256) k3_push_tiles(G3 g, Fld3<T> f, Parts3<T> 
     }
     // the prefix along q of W_q = DS_q tr(u, v) factorises: J_q(m_q, m_u, m_v) = cq tr(m_u, m_v) C_q(m_q),
     // C_q the running sum of DS_q; all loops unrolled so that the stencils stay in registers
-    T Cm[3][W];
+    // C_q at the W - 1 edges between the stencil's nodes (its value past the last node is the total change
+    // of the shape, zero)
+    T Cm[3][W - 1];
 #pragma unroll
     for (int a = 0; a < 3; a++) {
       T run = T(0);
 #pragma unroll
-      for (int m = 0; m < W; m++) {
+      for (int m = 0; m < W - 1; m++) {
         run += DS[a][m];
         Cm[a][m] = run;
       }
     }
     const T wj = p.w[j];
+    // the window offset of the stencil's first node; every term's offset from it is a compile-time
+    // constant once the loops are unrolled
+    const int off0 = (base[0] * WY + base[1]) * WZ + base[2];
 #pragma unroll
     for (int q = 0; q < 3; q++) {
       const int u1 = (q + 1) % 3, v1 = (q + 2) % 3;
@@ -824,22 +834,26 @@ __global__ void __launch_bounds__(256) k3_push_tiles(G3 g, Fld3<T> f, Parts3<T> 
       for (int m = 0; m < W; m++) moved |= DS[q][m] != T(0);
       if (!moved) continue;
       const T cq = cqw[q] * wj;
-      T* Jq = sJ + q * WN;
+      T* Jq = sJ + q * WN + off0;
+      // tr(u, v) = S0_u S0_v + DS_u S0_v / 2 + S0_u DS_v / 2 + DS_u DS_v / 3
+      //          = S0_u (S0_v + DS_v / 2) + DS_u (S0_v / 2 + DS_v / 3), times cq
+      T Av[W], Bv[W];
+#pragma unroll
+      for (int mv = 0; mv < W; mv++) {
+        Av[mv] = cq * (S0[v1][mv] + T(0.5) * DS[v1][mv]);
+        Bv[mv] = cq * (T(0.5) * S0[v1][mv] + DS[v1][mv] * T(1.0 / 3.0));
+      }
 #pragma unroll
       for (int mu = 0; mu < W; mu++)
 #pragma unroll
         for (int mv = 0; mv < W; mv++) {
-          const T tr = S0[u1][mu] * S0[v1][mv] + T(0.5) * DS[u1][mu] * S0[v1][mv] +
-                       T(0.5) * S0[u1][mu] * DS[v1][mv] + DS[u1][mu] * DS[v1][mv] / T(3);
-          if (tr == T(0)) continue;
-          const T ct = cq * tr;
+          const T ct = S0[u1][mu] * Av[mv] + DS[u1][mu] * Bv[mv];
+          if (ct == T(0)) continue;
 #pragma unroll
-          for (int mq = 0; mq < W; mq++) {
+          for (int mq = 0; mq < W - 1; mq++) {
             const T v = ct * Cm[q][mq];
             if (v == T(0)) continue;
-            int id3[3];
-            id3[q] = base[q] + mq; id3[u1] = base[u1] + mu; id3[v1] = base[v1] + mv;
-            atomicAdd(Jq + (id3[0] * WY + id3[1]) * WZ + id3[2], v);
+            atomicAdd(Jq + mq * wstride(q) + mu * wstride(u1) + mv * wstride(v1), v);
           }
         }
     }
