@@ -86,6 +86,20 @@ def test_vacuum_ck_friedman_pml_filter_fp64(Sim, orc):
     check_fields(g, o, TOL64)
 
 
+@pytest.mark.parametrize("solver,theta", [("ck", 0.0), ("yee", 1.0)])
+def test_vacuum_faraday_variants_with_stage_filter_fp64(Sim, orc, solver, theta):
+    """the fused Faraday + gather-filter kernel without Friedman damping (CK) and with Yee's operator under
+    full damping, with the stage's 4 passes + compensation, against the oracle"""
+    w = W.shrink(W.stage_2d(), 96, 400)
+    w["plasma"] = None
+    w["precision"] = "fp64"
+    w["solver"] = W.SOLVERS[solver]
+    w["theta"] = theta
+    w["dt"] = 0.0
+    g, o = run_pair(Sim, orc, w, 80)
+    check_fields(g, o, TOL64)
+
+
 @pytest.mark.parametrize("order", [3, 1])
 def test_parity_2d_small_fp64(Sim, orc, order):
     w = W.shrink(W.parity_2d(), 48, 160, order=order)
