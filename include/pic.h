@@ -328,7 +328,7 @@ int pic_kernel_timing(pic_ctx* ctx, int enable, int which, double* ms_total, int
  * laser (laser may be NULL) through
  * pic_init/pic_load_plasma/pic_inject_laser with the given allocator and stream.
  * The result is cached per (nx, nz, ppc_x, ppc_z, shape order, precision,
- * gamma_boost) for the life of the process; a cached answer comes back without
+ * gamma_boost, warm-up and timed steps) for the life of the process; a cached answer comes back without
  * timing and with cached = 1. out->struct_size must be set by the caller.
  * Returns PIC_EINVAL for bad arguments, PIC_ECUDA when no trial ran. */
 #define PIC_TUNE_MAX_TRIALS 16
@@ -348,6 +348,13 @@ typedef struct pic_tune_result {
 int pic_autotune(const pic_config* cfg, const pic_plasma* plasma, const pic_laser* laser, int steps,
                  pic_alloc_fn alloc, pic_free_fn free_fn, void* alloc_user, void* cuda_stream,
                  pic_tune_result* out);
+/* The same with the window of the run that the trials time: `warm` untimed steps (instead of 4), then
+ * `steps` timed steps; a layout that is best while the plasma is still cold need not be best once the
+ * laser has reached it, so a caller that times a later window tunes on that window. The cache key
+ * includes warm and steps. Errors as pic_autotune (warm < 0: PIC_EINVAL). */
+int pic_autotune_window(const pic_config* cfg, const pic_plasma* plasma, const pic_laser* laser, int warm,
+                        int steps, pic_alloc_fn alloc, pic_free_fn free_fn, void* alloc_user, void* cuda_stream,
+                        pic_tune_result* out);
 
 /* ---- Ensemble of independent runs (no counterpart in the paper) ----
  * n runs of uneven size (each its own pic_config, pic_plasma and pic_laser;
@@ -428,6 +435,13 @@ int pic_mlp_grad(pic_mlp* mlp, const float* x_device, const float* t_device, int
                  float* grad_host);
 int pic_mlp_train(pic_mlp* mlp, const float* x_device, const float* t_device, int n, int epochs, int batch,
                   float lr, float weight_decay, uint64_t seed, float* loss_curve_host);
+/* pic_mlp_train with epochs > 1 captures one epoch's launches (gather, forward, backward, AdamW per
+ * minibatch; the epoch index and AdamW's bias corrections read on the device from a table the host fills
+ * as the per-step launches would) in a CUDA graph on a private stream ordered after the MLP's stream,
+ * and replays it once per epoch after uploading that epoch's order; the parameters come out bitwise the
+ * same as from the direct launches. pic_mlp_use_graphs(mlp, 0) selects the direct launches on the MLP's
+ * stream, as does a stream that is itself being captured. Errors: PIC_EINVAL (mlp NULL). */
+int pic_mlp_use_graphs(pic_mlp* mlp, int enable);
 
 #ifdef __cplusplus
 }

@@ -29,10 +29,12 @@ EXPORTS = ("pic_init", "pic_load_plasma", "pic_inject_laser", "pic_step", "pic_s
            "pic_free", "pic_get_field", "pic_set_field", "pic_get_particles", "pic_get_stats",
            "pic_get_particles_y", "pic_last_error",
            "pic_kernel_launches", "pic_kernel_timing", "pic_get_rho_noalloc", "pic_autotune",
+           "pic_autotune_window",
            "pic_ensemble_create", "pic_ensemble_step", "pic_ensemble_sync", "pic_ensemble_size",
            "pic_ensemble_member", "pic_ensemble_free", "pic_ensemble_autotune",
            "pic_mlp_create", "pic_mlp_free", "pic_mlp_param_count", "pic_mlp_get_params", "pic_mlp_set_params",
-           "pic_mlp_infer", "pic_mlp_grad", "pic_mlp_train", "pic_mlp_use_tensor_cores", "pic_mlp_status",
+           "pic_mlp_infer", "pic_mlp_grad", "pic_mlp_train", "pic_mlp_use_tensor_cores", "pic_mlp_use_graphs",
+           "pic_mlp_status",
            "pic_measure_fp32_peak", "pic_beam_self_field", "pic_ensemble_batched", "pic_ensemble_use_graphs",
            "pic_ensemble_launches")
 NOALLOC_MAX_NZ = 16384
@@ -190,12 +192,16 @@ def load(build_if_missing: bool = True):
         L.pic_mlp_set_params.argtypes = [vp, _F]
         L.pic_mlp_infer.argtypes = [vp, vp, ctypes.c_int64, vp]
         L.pic_mlp_use_tensor_cores.argtypes = [vp, ctypes.c_int]
+        L.pic_mlp_use_graphs.argtypes = [vp, ctypes.c_int]
         L.pic_mlp_status.argtypes = [vp]
         L.pic_mlp_grad.argtypes = [vp, vp, vp, ctypes.c_int, _F, _F]
         L.pic_mlp_train.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_float,
                                     ctypes.c_float, ctypes.c_uint64, _F]
         L.pic_autotune.argtypes = [ctypes.POINTER(PicConfig), ctypes.POINTER(PicPlasma), ctypes.POINTER(PicLaser),
                                    ctypes.c_int, ALLOC_FN, FREE_FN, vp, vp, ctypes.POINTER(PicTuneResult)]
+        L.pic_autotune_window.argtypes = [ctypes.POINTER(PicConfig), ctypes.POINTER(PicPlasma),
+                                          ctypes.POINTER(PicLaser), ctypes.c_int, ctypes.c_int, ALLOC_FN, FREE_FN,
+                                          vp, vp, ctypes.POINTER(PicTuneResult)]
         L.pic_measure_fp32_peak.argtypes = [_D, _D]
         L.pic_beam_self_field.argtypes = [vp]
         L.pic_ensemble_batched.argtypes = [vp]

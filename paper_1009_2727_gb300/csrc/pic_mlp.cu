@@ -92,7 +92,8 @@ __global__ void k_colsum(int n, int cols, const float* dZ, float* db) {
 }
 
 // mean squared error over n x d outputs; dY = 2 (Y - T) / (n d); loss summed into *loss
-__global__ void k_mse(long nd, const float* Y, const float* T, float* dY, float* loss) {
+// loss: the sum is added to loss[*eidx] when eidx is given (the epoch's slot of a training run), else to *loss
+__global__ void k_mse(long nd, const float* Y, const float* T, float* dY, float* loss, const int* eidx) {
   __shared__ float red[256];
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   float l = 0.0f;
@@ -107,7 +108,7 @@ __global__ void k_mse(long nd, const float* Y, const float* T, float* dY, float*
     if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x == 0) atomicAdd(loss, red[0]);
+  if (threadIdx.x == 0) atomicAdd(eidx ? loss + *eidx : loss, red[0]);
 }
 
 __global__ void k_to_bf16(long n, const float* src, __nv_bfloat16* dst) {
@@ -115,11 +116,19 @@ __global__ void k_to_bf16(long n, const float* src, __nv_bfloat16* dst) {
   if (i < n) dst[i] = __float2bfloat16(src[i]);
 }
 
-// AdamW (decoupled weight decay) on the FP32 master parameters, then their BF16 copies
+// AdamW (decoupled weight decay) on the FP32 master parameters, then their BF16 copies. The bias corrections
+// c1 = 1 - b1^t, c2 = 1 - b2^t come as arguments, or (ctab given) from a host-computed table at step
+// (*eidx) * nbat + kk: the form a captured epoch replays
 __global__ void k_adamw(long n, float* p, const float* g, float* m, float* v, __nv_bfloat16* pb, float lr, float b1,
-                        float b2, float eps, float wd, float c1, float c2) {
+                        float b2, float eps, float wd, float c1, float c2, const float2* ctab, const int* eidx,
+                        int nbat, int kk) {
   const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  if (ctab) {
+    const float2 c = ctab[(long)(*eidx) * nbat + kk];
+    c1 = c.x;
+    c2 = c.y;
+  }
   const float gi = g[i];
   const float mi = b1 * m[i] + (1.0f - b1) * gi;
   const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
@@ -169,6 +178,8 @@ __host__ __device__ inline int pad16(int v) { return (v + 15) & ~15; }
 __host__ __device__ inline uint32_t canon_off(int r, int k, int Kp) {
   return (uint32_t)((r >> 3) * (Kp * 16) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
 }
+
+__global__ void k_next_epoch(int* eidx) { *eidx += 1; }
 
 __global__ void k_pack_weights(const __nv_bfloat16* W, int N, int K, int Np, int Kp, __nv_bfloat16* img) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -366,6 +377,10 @@ struct pic_mlp {
   int perm_cap = 0;
   float* curve = nullptr;               // per-epoch loss sums (training)
   int curve_cap = 0;
+  float2* ctab = nullptr;               // AdamW bias corrections per step of a training call
+  long ctab_cap = 0;
+  int* eidx = nullptr;                  // epoch index of a training call, advanced on the device
+  bool use_graphs = true;               // training replays a captured epoch
   float* xb = nullptr;
   float* tb = nullptr;
   // tensor-core inference: packed weight images per layer, rebuilt when the BF16 weights change
@@ -449,10 +464,10 @@ void forward(pic_mlp* m, const float* X, int n) {
 }
 
 // gradient of the mean squared error of m->out against T (n x wL) into m->g; the loss is added to *loss
-void backward(pic_mlp* m, const float* T, int n, float* loss) {
+void backward(pic_mlp* m, const float* T, int n, float* loss, const int* eidx = nullptr) {
   const int wl = m->w[m->L];
   const long nd = (long)n * wl;
-  k_mse<<<(unsigned)((nd + 255) / 256), 256, 0, m->s>>>(nd, m->out, T, m->dA, loss);
+  k_mse<<<(unsigned)((nd + 255) / 256), 256, 0, m->s>>>(nd, m->out, T, m->dA, loss, eidx);
   float* dZ = m->dA;   // gradient w.r.t. the current layer's output (pre-activation for the last)
   float* dH = m->dB;
   for (int l = m->L; l >= 1; l--) {
@@ -612,6 +627,12 @@ int pic_mlp_use_tensor_cores(pic_mlp* m, int enable) {
   return PIC_OK;
 }
 
+int pic_mlp_use_graphs(pic_mlp* m, int enable) {
+  if (!m) return PIC_EINVAL;
+  m->use_graphs = enable != 0;
+  return PIC_OK;
+}
+
 int pic_mlp_status(pic_mlp* m) {
   if (!m) return PIC_EINVAL;
   if (cudaStreamSynchronize(m->s) != cudaSuccess) return PIC_ECUDA;
@@ -653,6 +674,70 @@ int pic_mlp_train(pic_mlp* m, const float* x, const float* t, int n, int epochs,
   uint64_t st = seed;
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
   const int nbat = n / batch;
+  // AdamW's bias corrections of every step of this call, computed on the host as the per-step launches did
+  const long nsteps = (long)epochs * nbat;
+  std::vector<float2> ctab((size_t)(nsteps > 0 ? nsteps : 1));
+  for (long q = 0; q < nsteps; q++) {
+    const float tq = (float)(m->adam_t + q + 1);
+    ctab[q] = make_float2(1.0f - std::pow(b1, tq), 1.0f - std::pow(b2, tq));
+  }
+  if (nsteps > m->ctab_cap) {
+    m->ctab = mlp_al<float2>(m, (size_t)nsteps);
+    if (!m->ctab) return PIC_ENOMEM;
+    m->ctab_cap = nsteps;
+  }
+  if (!m->eidx) {
+    m->eidx = mlp_al<int>(m, 1);
+    if (!m->eidx) return PIC_ENOMEM;
+  }
+  if (nsteps > 0)
+    cudaMemcpyAsync(m->ctab, ctab.data(), (size_t)nsteps * sizeof(float2), cudaMemcpyHostToDevice, m->s);
+  cudaMemsetAsync(m->eidx, 0, sizeof(int), m->s);
+  // one epoch's launches (nbat batches of gather, forward, backward, AdamW, then the epoch counter), with
+  // the epoch index and the step's bias corrections read on the device
+  auto epoch_launches = [&](cudaStream_t s) {
+    cudaStream_t keep = m->s;
+    m->s = s;
+    for (int k = 0; k < nbat; k++) {
+      k_gather_rows<<<batch, 64, 0, s>>>(batch, m->perm + (long)k * batch, x, m->w[0], t, m->w[m->L], m->xb, m->tb);
+      forward(m, m->xb, batch);
+      backward(m, m->tb, batch, m->curve, m->eidx);
+      k_adamw<<<(unsigned)((m->np + 255) / 256), 256, 0, s>>>(m->np, m->p, m->g, m->m, m->v, m->pb, lr, b1, b2, eps,
+                                                              weight_decay, 0.f, 0.f, m->ctab, m->eidx, nbat, k);
+    }
+    k_next_epoch<<<1, 1, 0, s>>>(m->eidx);
+    m->s = keep;
+  };
+  // The epoch is captured once in a CUDA graph on a private stream and replayed (about 20 launches per
+  // batch otherwise: at batch 64 the step is launch-bound). Where capture is not possible, the same
+  // launches run directly on the caller's stream.
+  cudaStream_t ts = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  cudaStreamCaptureStatus cap_st = cudaStreamCaptureStatusNone;
+  if (m->use_graphs && epochs > 1 && nbat > 0 && cudaStreamIsCapturing(m->s, &cap_st) == cudaSuccess &&
+      cap_st == cudaStreamCaptureStatusNone && cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking) == cudaSuccess) {
+    cudaGraph_t gr = nullptr;
+    if (cudaStreamBeginCapture(ts, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      epoch_launches(ts);
+      if (cudaStreamEndCapture(ts, &gr) == cudaSuccess && gr) {
+        if (cudaGraphInstantiate(&ge, gr, 0) != cudaSuccess) ge = nullptr;
+        cudaGraphDestroy(gr);
+      }
+    }
+    cudaGetLastError();   // a refused capture leaves no sticky error; the direct path follows
+    if (!ge) {
+      cudaStreamDestroy(ts);
+      ts = nullptr;
+    }
+  }
+  cudaEvent_t ready = nullptr;
+  if (ge) {
+    // the private stream starts after everything queued on the caller's stream
+    cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
+    cudaEventRecord(ready, m->s);
+    cudaStreamWaitEvent(ts, ready, 0);
+  }
+  cudaStream_t run_s = ge ? ts : m->s;
   for (int e = 0; e < epochs; e++) {
     for (int i = 0; i < n; i++) perm[i] = i;
     for (int i = n - 1; i > 0; i--) {   // Fisher-Yates with a counter-based generator
@@ -660,22 +745,25 @@ int pic_mlp_train(pic_mlp* m, const float* x, const float* t, int n, int epochs,
       const int tmp = perm[i]; perm[i] = perm[j]; perm[j] = tmp;
     }
     // pageable source: the copy has been staged when the call returns, so perm may be refilled
-    cudaMemcpyAsync(m->perm, perm.data(), (size_t)n * sizeof(int), cudaMemcpyHostToDevice, m->s);
-    for (int k = 0; k < nbat; k++) {
-      k_gather_rows<<<batch, 64, 0, m->s>>>(batch, m->perm + (long)k * batch, x, m->w[0], t, m->w[m->L], m->xb,
-                                            m->tb);
-      forward(m, m->xb, batch);
-      backward(m, m->tb, batch, m->curve + e);
-      m->adam_t++;
-      const float c1 = 1.0f - std::pow(b1, (float)m->adam_t), c2 = 1.0f - std::pow(b2, (float)m->adam_t);
-      k_adamw<<<(unsigned)((m->np + 255) / 256), 256, 0, m->s>>>(m->np, m->p, m->g, m->m, m->v, m->pb, lr, b1, b2,
-                                                                 eps, weight_decay, c1, c2);
-    }
+    cudaMemcpyAsync(m->perm, perm.data(), (size_t)n * sizeof(int), cudaMemcpyHostToDevice, run_s);
+    if (ge) cudaGraphLaunch(ge, ts);
+    else epoch_launches(m->s);
+  }
+  m->adam_t += nsteps;
+  if (ge) {
+    cudaEventRecord(ready, ts);
+    cudaStreamWaitEvent(m->s, ready, 0);
   }
   if (loss_curve && epochs > 0) {
     cudaMemcpyAsync(loss_curve, m->curve, (size_t)epochs * sizeof(float), cudaMemcpyDeviceToHost, m->s);
   }
-  if (cudaStreamSynchronize(m->s) != cudaSuccess) return PIC_ECUDA;
+  const bool ok = cudaStreamSynchronize(m->s) == cudaSuccess;
+  if (ge) {
+    cudaGraphExecDestroy(ge);
+    cudaStreamDestroy(ts);
+    cudaEventDestroy(ready);
+  }
+  if (!ok) return PIC_ECUDA;
   if (loss_curve)
     for (int e = 0; e < epochs; e++) loss_curve[e] /= (float)(nbat > 0 ? nbat : 1);
   return PIC_OK;

@@ -1,6 +1,6 @@
 // Autotuner of the particle layout: the tile shape of the particle sort and the
-// sort cadence, timed on the first steps of the run itself and cached per run
-// shape. Every trial is an ordinary context built through the public ABI, so a
+// sort cadence, timed on a window of steps of the run itself (by default its first
+// steps) and cached per run shape and window. Every trial is an ordinary context built through the public ABI, so a
 // tuned configuration is exactly what the caller then runs.
 #include <cuda_runtime.h>
 
@@ -16,13 +16,15 @@ namespace {
 constexpr int kTiles[3] = {8, 16, 32};
 constexpr int kCadences[4] = {8, 16, 32, 64};
 
-typedef std::tuple<int, int, int, int, int, int, long long> Key;   // nx, nz, ppc_x, ppc_z, order, precision, gamma*1e6
+// nx, nz, ppc_x, ppc_z, order, precision, gamma*1e6, warm-up steps, timed steps
+typedef std::tuple<int, int, int, int, int, int, long long, int, int> Key;
 
 std::mutex g_mu;
 std::map<Key, pic_tune_result> g_cache;
 
-Key key_of(const pic_config* c, const pic_plasma* p) {
-  return Key(c->nx, c->nz, p->ppc_x, p->ppc_z, c->shape_order, c->precision, (long long)(c->gamma_boost * 1e6));
+Key key_of(const pic_config* c, const pic_plasma* p, int warm, int steps) {
+  return Key(c->nx, c->nz, p->ppc_x, p->ppc_z, c->shape_order, c->precision, (long long)(c->gamma_boost * 1e6), warm,
+             steps);
 }
 
 // one trial: a context with this layout, warm-up steps, then timed steps (ms per step; < 0 on failure)
@@ -64,12 +66,12 @@ void record(pic_tune_result* o, int tx, int tz, int se, double ms) {
 
 }  // namespace
 
-extern "C" int pic_autotune(const pic_config* cfg, const pic_plasma* plasma, const pic_laser* laser, int steps,
-                            pic_alloc_fn alloc, pic_free_fn free_fn, void* alloc_user, void* cuda_stream,
-                            pic_tune_result* out) {
+extern "C" int pic_autotune_window(const pic_config* cfg, const pic_plasma* plasma, const pic_laser* laser,
+                                   int warm, int steps, pic_alloc_fn alloc, pic_free_fn free_fn, void* alloc_user,
+                                   void* cuda_stream, pic_tune_result* out) {
   if (!cfg || !plasma || !out || out->struct_size != sizeof(pic_tune_result)) return PIC_EINVAL;
-  if (steps < 1 || cfg->dim != 2) return PIC_EINVAL;
-  const Key key = key_of(cfg, plasma);
+  if (steps < 1 || warm < 0 || cfg->dim != 2) return PIC_EINVAL;
+  const Key key = key_of(cfg, plasma, warm, steps);
   {
     std::lock_guard<std::mutex> lk(g_mu);
     auto it = g_cache.find(key);
@@ -82,7 +84,6 @@ extern "C" int pic_autotune(const pic_config* cfg, const pic_plasma* plasma, con
   pic_tune_result r{};
   r.struct_size = sizeof(pic_tune_result);
   r.version = PIC_API_VERSION;
-  const int warm = 4;
   // one untimed trial first: the GPU reaches its clocks before the candidates are compared
   trial(cfg, plasma, laser, kTiles[0], kTiles[2], 32, warm, steps, alloc, free_fn, alloc_user, cuda_stream);
   // 1. tile shape at the default cadence; each tile timed twice, the faster time counts
@@ -123,4 +124,10 @@ extern "C" int pic_autotune(const pic_config* cfg, const pic_plasma* plasma, con
   }
   *out = r;
   return PIC_OK;
+}
+
+extern "C" int pic_autotune(const pic_config* cfg, const pic_plasma* plasma, const pic_laser* laser, int steps,
+                            pic_alloc_fn alloc, pic_free_fn free_fn, void* alloc_user, void* cuda_stream,
+                            pic_tune_result* out) {
+  return pic_autotune_window(cfg, plasma, laser, 4, steps, alloc, free_fn, alloc_user, cuda_stream, out);
 }

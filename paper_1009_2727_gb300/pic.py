@@ -124,9 +124,9 @@ def torch_allocator(device_index: int):
     return capi.ALLOC_FN(_alloc), capi.FREE_FN(_free)
 
 
-def autotune(w: dict, steps: int = 16, precision: str | None = None, stream=None) -> dict:
-    """Tile shape and sort cadence for this workload, timed on its first steps (pic_autotune; the
-    result is cached per run shape inside the library)."""
+def autotune(w: dict, steps: int = 16, precision: str | None = None, stream=None, warm: int = 4) -> dict:
+    """Tile shape and sort cadence for this workload, timed on `steps` steps after `warm` untimed ones
+    (pic_autotune_window; the result is cached per run shape and window inside the library)."""
     import torch
     L = capi.load()
     prec = precision or w.get("precision", "fp64")
@@ -138,8 +138,9 @@ def autotune(w: dict, steps: int = 16, precision: str | None = None, stream=None
     acb, fcb = torch_allocator(torch.cuda.current_device())
     out = capi.PicTuneResult()
     out.struct_size = ctypes.sizeof(capi.PicTuneResult)
-    r = L.pic_autotune(ctypes.byref(c), ctypes.byref(pl), ctypes.byref(la) if la is not None else None, int(steps),
-                       acb, fcb, None, ctypes.c_void_p(st.cuda_stream), ctypes.byref(out))
+    r = L.pic_autotune_window(ctypes.byref(c), ctypes.byref(pl), ctypes.byref(la) if la is not None else None,
+                              int(warm), int(steps), acb, fcb, None, ctypes.c_void_p(st.cuda_stream),
+                              ctypes.byref(out))
     if r != 0:
         raise PicError(f"pic_autotune failed: {capi.STATUS_NAMES.get(r, r)}")
     n = out.n_trials
@@ -151,7 +152,7 @@ def autotune(w: dict, steps: int = 16, precision: str | None = None, stream=None
 
 class Simulation:
     def __init__(self, w: dict, precision: str | None = None, stream=None, tile=None, sort_every: int = 0,
-                 use_torch_allocator: bool = True, tune: bool = False):
+                 use_torch_allocator: bool = True, tune: bool = False, tune_window: tuple = (4, 16)):
         import torch
         if not torch.cuda.is_available():
             raise PicError("a CUDA device is required (the library has no CPU path)")
@@ -168,7 +169,8 @@ class Simulation:
         self.shape = ((self.nx + 1, self.ny + 1, self.nz + 1) if self.dim == 3 else (self.nz + 1,) if self.dim == 1
                       else (self.nx + 1, self.nz + 1))
         if tune:
-            t = autotune(w, precision=prec, stream=self.stream)
+            # the layout tuned on `tune_window` = (untimed, timed) steps of this run
+            t = autotune(w, precision=prec, stream=self.stream, warm=int(tune_window[0]), steps=int(tune_window[1]))
             tile, sort_every = t["tile"], t["sort_every"]
             self.tuned = t
         c = make_config(w, self.precision, tile, sort_every)

@@ -62,6 +62,10 @@ class MLP:
         """serve with the fused tcgen05 kernel (default when every padded width <= 256) or the CUDA-core GEMMs"""
         self._check(self.L.pic_mlp_use_tensor_cores(self.h, int(bool(enable))))
 
+    def use_graphs(self, enable: bool = True):
+        """train by replaying one captured epoch (default) or by direct launches"""
+        self._check(self.L.pic_mlp_use_graphs(self.h, int(bool(enable))))
+
     def forward(self, x) -> np.ndarray:
         xd, xp = self._dev(x)
         y = self.torch.empty((xd.shape[0], self.widths[-1]), dtype=self.torch.float32, device="cuda")

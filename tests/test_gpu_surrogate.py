@@ -139,6 +139,22 @@ def test_mlp_training_fits_and_is_deterministic(S):
     assert np.array_equal(params[0], params[1])
 
 
+def test_mlp_training_graph_matches_direct_launches(S):
+    """an epoch captured once and replayed gives bitwise the parameters and loss curve of the direct launches"""
+    rng = np.random.default_rng(11)
+    x = rng.uniform(-1.5, 1.5, (640, 6))
+    t = smooth_target(x)
+    out = []
+    for graphs in (True, False):
+        net = S.MLP([6, 96, 96, 4], seed=3)
+        net.use_graphs(graphs)
+        c = net.train(x, t, epochs=7, batch=64, lr=2e-3, weight_decay=1e-4, seed=4)
+        out.append((net.get_params(), c))
+        net.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.allclose(out[0][1], out[1][1], rtol=1e-5, atol=0.0)
+
+
 def test_stage_surrogate_end_to_end(S):
     """a handful of stage runs through the ensemble: finite, plausible labels; the fitted surrogate
     reproduces its training set and flags a query outside the sampled box"""
