@@ -99,6 +99,13 @@ struct Cq3 {
   T v[3];
 };
 
+struct Ctrl3 {
+  int count;
+  int status;
+  int pad[2];
+  double red[8];
+};
+
 template <class T>
 struct Taps3 {
   T c[2 * FILTER_HMAX + 1];
@@ -394,6 +401,176 @@ __global__ void __launch_bounds__(128) k3_filter_zs(G3 g, const T* __restrict__ 
   }
 }
 
+// x and y axes of the composed filter (stride 1, PT taps each side) in one pass. A CTA stages, by one bulk
+// tensor copy, a box of the source (XYT + 2 PT nodes along x and along y, ZB along z; off-grid nodes arrive
+// as zero), filters it along x into a scratch box that keeps the y halo, then along y, and writes the
+// XYT x XYT x ZB outputs: one read and one write of the component instead of two of each. Each thread
+// slides a register window along its line, summing the taps in the same order as k3_filter_axis, and the
+// outputs of either pass at invalid nodes of the component are zero, as in the separate sweeps.
+constexpr int XYT = 16, ZB = 16;
+constexpr long kWait3 = 1L << 24;
+
+template <class T, int PT>
+__global__ void __launch_bounds__(256) k3_filter_xy(G3 g, const __grid_constant__ CUtensorMap map, int slot,
+                                                    T* __restrict__ dst, int comp, Taps3<T> t, Ctrl3* ctrl) {
+  constexpr int W = 2 * PT + 1, XW = XYT + 2 * PT;
+  extern __shared__ __align__(128) unsigned char raw3[];
+  T* S = reinterpret_cast<T*>(raw3 + ((128u - ((uint32_t)__cvta_generic_to_shared(raw3) & 127u)) & 127u));
+  T* X1 = S + XW * XW * ZB;    // after the x pass: [x 0..XYT) [y 0..XW) [z 0..ZB)
+  __shared__ __align__(8) uint64_t bar;
+  const int k0 = blockIdx.x * ZB, j0 = blockIdx.y * XYT, i0 = blockIdx.z * XYT;
+  const int tid = threadIdx.x;
+  const uint32_t sbar = (uint32_t)__cvta_generic_to_shared(&bar);
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sbar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (tid == 0) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sbar),
+                 "r"((uint32_t)(XW * XW * ZB * sizeof(T)))
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"((uint32_t)__cvta_generic_to_shared(S)),
+        "l"((unsigned long long)&map), "r"(k0), "r"(j0 - PT), "r"(i0 - PT), "r"(slot), "r"(sbar)
+        : "memory");
+  }
+  bool done = false;
+  for (long it = 0; it < kWait3 && !done; it++) {
+    uint32_t d;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(d)
+        : "r"(sbar)
+        : "memory");
+    done = d != 0;
+  }
+  // the outcome is made block-uniform; a timed-out block records it and leaves once its copy has landed
+  if (__syncthreads_or(!done)) {
+    if (tid == 0) {
+      atomicOr(&ctrl->status, (int)ST_TIMEOUT);
+      for (long it = 0; it < kWait3; it++) {
+        uint32_t d;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(d)
+            : "r"(sbar)
+            : "memory");
+        if (d) break;
+      }
+    }
+    return;
+  }
+  int lo0, hi0, lo1, hi1, lo2, hi2;
+  vr(comp, 0, g, lo0, hi0);
+  vr(comp, 1, g, lo1, hi1);
+  vr(comp, 2, g, lo2, hi2);
+  T c[W];
+#pragma unroll
+  for (int m = 0; m < W; m++) c[m] = t.c[m];
+  // x pass: one (y, z) line of the box per task, XYT outputs
+  for (int task = tid; task < XW * ZB; task += 256) {
+    const int yi = task / ZB, zi = task - yi * ZB;
+    const int gj = j0 - PT + yi, gk = k0 + zi;
+    const bool other = gj >= lo1 && gj <= hi1 && gk >= lo2 && gk <= hi2;
+    const T* col = S + yi * ZB + zi;
+    T w[W];
+#pragma unroll
+    for (int m = 0; m < W; m++) w[m] = col[m * XW * ZB];
+#pragma unroll
+    for (int xo = 0; xo < XYT; xo++) {
+      T acc = T(0);
+#pragma unroll
+      for (int m = 0; m < W; m++) acc += c[m] * w[m];
+      const int gi = i0 + xo;
+      X1[(xo * XW + yi) * ZB + zi] = (other && gi >= lo0 && gi <= hi0) ? acc : T(0);
+      if (xo + 1 < XYT) {
+#pragma unroll
+        for (int m = 0; m < W - 1; m++) w[m] = w[m + 1];
+        w[W - 1] = col[(xo + W) * XW * ZB];
+      }
+    }
+  }
+  __syncthreads();
+  // y pass: one (x, z) line per thread, XYT outputs written to dst
+  {
+    const int xo = tid / ZB, zi = tid - xo * ZB;
+    const int gi = i0 + xo, gk = k0 + zi;
+    const bool other = gi >= lo0 && gi <= hi0 && gk >= lo2 && gk <= hi2;
+    const bool in = gi <= g.n[0] && gk <= g.n[2];
+    const T* row = X1 + xo * XW * ZB + zi;
+    T w[W];
+#pragma unroll
+    for (int m = 0; m < W; m++) w[m] = row[m * ZB];
+#pragma unroll
+    for (int yo = 0; yo < XYT; yo++) {
+      T acc = T(0);
+#pragma unroll
+      for (int m = 0; m < W; m++) acc += c[m] * w[m];
+      const int gj = j0 + yo;
+      if (in && gj <= g.n[1]) dst[nid(g, gi, gj, gk)] = (other && gj >= lo1 && gj <= hi1) ? acc : T(0);
+      if (yo + 1 < XYT) {
+#pragma unroll
+        for (int m = 0; m < W - 1; m++) w[m] = w[m + 1];
+        w[W - 1] = row[(yo + W) * ZB];
+      }
+    }
+  }
+}
+static_assert(XYT * ZB == 256, "one y-pass line per thread");
+
+template <class T, int PT>
+constexpr size_t filter_xy_smem() {
+  return (size_t)((XYT + 2 * PT) * (XYT + 2 * PT) * ZB + XYT * (XYT + 2 * PT) * ZB) * sizeof(T) + 128;
+}
+
+typedef CUresult (*Encode3Fn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// 4D tensor over a 3-component block (z, y, x, component), boxes of ZB x (XYT + 2 halo)^2 x 1 nodes, zero
+// fill off the grid; false when the driver entry point is missing or the encoding is refused
+template <class T>
+bool encode_xy_map(CUtensorMap* m, const T* base, const G3& g, int halo) {
+  static Encode3Fn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (Encode3Fn)p;
+  }
+  if (!fn || !base) return false;
+  const cuuint64_t dims[4] = {(cuuint64_t)(g.n[2] + 1), (cuuint64_t)(g.n[1] + 1), (cuuint64_t)(g.n[0] + 1), 3};
+  const cuuint64_t strides[3] = {(cuuint64_t)g.ldz * sizeof(T), (cuuint64_t)(g.n[1] + 1) * g.ldz * sizeof(T),
+                                 (cuuint64_t)g.cs * sizeof(T)};
+  const cuuint32_t box[4] = {(cuuint32_t)ZB, (cuuint32_t)(XYT + 2 * halo), (cuuint32_t)(XYT + 2 * halo), 1};
+  const cuuint32_t es[4] = {1, 1, 1, 1};
+  const CUtensorMapDataType dt = sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  return fn(m, dt, 4, const_cast<T*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
+template <class T, int PT>
+void launch_filter_xy(const G3& g, const CUtensorMap& map, int slot, T* dst, int comp, const Taps3<T>& t,
+                      Ctrl3* ctrl, cudaStream_t s) {
+  const dim3 grid(nblk(g.n[2] + 1, ZB), nblk(g.n[1] + 1, XYT), nblk(g.n[0] + 1, XYT));
+  k3_filter_xy<T, PT><<<grid, 256, filter_xy_smem<T, PT>(), s>>>(g, map, slot, dst, comp, t, ctrl);
+}
+
+template <class T>
+void set_filter_xy_smem() {
+  cudaFuncSetAttribute(k3_filter_xy<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)filter_xy_smem<T, 1>());
+  cudaFuncSetAttribute(k3_filter_xy<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)filter_xy_smem<T, 2>());
+  cudaFuncSetAttribute(k3_filter_xy<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)filter_xy_smem<T, 3>());
+  cudaFuncSetAttribute(k3_filter_xy<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)filter_xy_smem<T, 4>());
+  cudaFuncSetAttribute(k3_filter_xy<T, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)filter_xy_smem<T, 5>());
+}
+
 template <class T, int PT>
 void launch_filter_fast(const G3& g, const T* src, T* dst, int comp, int axis, const Taps3<T>& t, cudaStream_t s) {
   if (axis == 2) {
@@ -481,12 +658,6 @@ struct Parts3 {
   int* fl;          // bit 0: alive
 };
 
-struct Ctrl3 {
-  int count;
-  int status;
-  int pad[2];
-  double red[8];
-};
 
 template <class T, int ORD>
 __device__ __forceinline__ void shape_w(T t, T* w) {
@@ -1646,6 +1817,10 @@ struct Sim3 : Sim3Api {
   double* out_d = nullptr;            // copy-out scratch
   Pml3<T> pm;
   Taps3<T> taps;
+  // the fused x-y filter: tensor maps of the blocks it reads (gather copies and current), when it applies
+  bool xy_ok = false;
+  CUtensorMap xy_map[3];
+  const T* xy_base[3] = {nullptr, nullptr, nullptr};
   Cq3<T> cq_e;
   bool nodal = false;     // 'momentum conserving' gather (pic_config.gather_scheme = 1)
   T* nF = nullptr;        // its node values: Ex, Ey, Ez, Bx, By, Bz
@@ -1823,6 +1998,13 @@ struct Sim3 : Sim3Api {
     for (int m = 0; m < 2 * FILTER_HMAX + 1; m++) taps.c[m] = m <= 2 * R ? T(t[m]) : T(0);
     taps.P = R;
     taps.s = wide ? 1 : c->filter_stride;
+    // stride-1 filters of up to five taps a side take the fused x-y pass (one TMA-staged box per CTA)
+    if (taps.s == 1 && taps.P >= 1 && taps.P <= 5) {
+      xy_base[0] = fE; xy_base[1] = fB; xy_base[2] = J;
+      xy_ok = true;
+      for (int q = 0; q < 3; q++) xy_ok = xy_ok && encode_xy_map<T>(&xy_map[q], xy_base[q], g, taps.P);
+      if (xy_ok) set_filter_xy_smem<T>();
+    }
     tl.nt[0] = (g.n[0] + TX - 1) / TX;
     tl.nt[1] = (g.n[1] + TY - 1) / TY;
     tl.nt[2] = (g.n[2] + TZ - 1) / TZ;
@@ -2102,6 +2284,22 @@ struct Sim3 : Sim3Api {
   dim3 grid3() const { return dim3(nblk(g.n[2] + 1, 128 * KPT), g.n[1] + 1, g.n[0] + 1); }
 
   void filter3(T* F, int comp) {
+    // F inside one of the mapped blocks: x and y in one TMA-staged pass F -> tmp, then z: tmp -> F
+    for (int q = 0; xy_ok && q < 3; q++) {
+      const long d = F - xy_base[q];
+      if (d < 0 || d >= 3 * g.cs || d % g.cs != 0) continue;
+      const int slot = (int)(d / g.cs);
+      switch (taps.P) {
+        case 1: launch_filter_xy<T, 1>(g, xy_map[q], slot, tmp, comp, taps, ctrl, s); break;
+        case 2: launch_filter_xy<T, 2>(g, xy_map[q], slot, tmp, comp, taps, ctrl, s); break;
+        case 3: launch_filter_xy<T, 3>(g, xy_map[q], slot, tmp, comp, taps, ctrl, s); break;
+        case 4: launch_filter_xy<T, 4>(g, xy_map[q], slot, tmp, comp, taps, ctrl, s); break;
+        default: launch_filter_xy<T, 5>(g, xy_map[q], slot, tmp, comp, taps, ctrl, s); break;
+      }
+      launch_filter_axis<T>(g, grid3(), tmp, F, comp, 2, taps, s);
+      nl += 2;
+      return;
+    }
     // x: F -> tmp, y: tmp -> tmp2, z: tmp2 -> F
     launch_filter_axis<T>(g, grid3(), F, tmp, comp, 0, taps, s);
     launch_filter_axis<T>(g, grid3(), tmp, tmp2, comp, 1, taps, s);
@@ -2238,6 +2436,7 @@ struct Sim3 : Sim3Api {
     int dst = 0;
     cudaMemcpy(&dst, &ctrl->status, sizeof(int), cudaMemcpyDeviceToHost);
     if (dst & ST_OUTSIDE) return fail(PIC_EOVERFLOW, "a particle left its tile's window (not pushed)");
+    if (dst & ST_TIMEOUT) return fail(PIC_ETIMEOUT, "a bounded wait for a staged filter box gave up");
     return st;
   }
 
