@@ -144,8 +144,9 @@ __device__ __forceinline__ T dstar_s(const T* S, int a, int c0, T ca, T cb, T cg
 
 template <class T>
 __global__ void __launch_bounds__(256) k3_faraday_tile(G3 g, Pml3<T> pm, const T* __restrict__ E,
-                                                       const T* __restrict__ Ep, const T* __restrict__ Eb, T* B, T* Bs,
-                                                       T* fB, T c1, T c2, T c3, T ca, T cb, T cg, T dtT) {
+                                                       const T* __restrict__ Ep, const T* __restrict__ Eb,
+                                                       T* __restrict__ B, T* __restrict__ Bs, T* __restrict__ fB, T c1,
+                                                       T c2, T c3, T ca, T cb, T cg, T dtT) {
   constexpr int SX = FX + 2, SY = FY + 2, SZ = FZ + 2, SN = SX * SY * SZ;
   __shared__ T se[3][SN];   // index (x * SY + y) * SZ + z, tile origin at (1, 1, 1)
   const int i0 = blockIdx.z * FX, j0 = blockIdx.y * FY, k0 = blockIdx.x * FZ;
@@ -213,8 +214,9 @@ __global__ void k3_friedman(long n, const T* E, T* Ep, T* Eb, T* fE, T a, T b) {
 }
 
 template <class T>
-__device__ __forceinline__ void ampere_node(const G3& g, const Pml3<T>& pm, T* E, T* Es, const T* B, const T* J, T dtc2,
-                                            T dte, int i, int j, int k) {
+__device__ __forceinline__ void ampere_node(const G3& g, const Pml3<T>& pm, T* __restrict__ E, T* __restrict__ Es,
+                                            const T* __restrict__ B, const T* __restrict__ J, T dtc2, T dte, int i,
+                                            int j, int k) {
   const long p = nid(g, i, j, k);
   const int idx[3] = {i, j, k};
   const T c2 = T(kC * kC);
@@ -253,7 +255,8 @@ __device__ __forceinline__ void ampere_node(const G3& g, const Pml3<T>& pm, T* E
 }
 
 template <class T>
-__global__ void __launch_bounds__(128) k3_ampere(G3 g, Pml3<T> pm, T* E, T* Es, const T* B, const T* J, T dtc2, T dte) {
+__global__ void __launch_bounds__(128) k3_ampere(G3 g, Pml3<T> pm, T* __restrict__ E, T* __restrict__ Es,
+                                                 const T* __restrict__ B, const T* __restrict__ J, T dtc2, T dte) {
   const int k0 = blockIdx.x * blockDim.x * KPT + threadIdx.x, j = blockIdx.y, i = blockIdx.z;
 #pragma unroll
   for (int kk = 0; kk < KPT; kk++) {
@@ -366,19 +369,50 @@ __device__ __forceinline__ void ld16(const double* p, double* v) {
 // z axis of the composed filter (stride 1): each block stages a row segment of 128 * ZR nodes and an
 // 8-node halo in shared memory; each thread reads its ZR + 16 staged values with 16-byte loads and sums
 // the taps of ZR consecutive outputs in the same order as k3_filter_axis.
-constexpr int ZR = 4, ZHA = 8;
+// A row's last block also takes a remainder of up to ZTAIL nodes past its segment (a row of 2^m + 1 nodes
+// would otherwise need a block for its last node); longer remainders get a block of their own.
+constexpr int ZR = 8, ZHA = 8, ZTAIL = 32;
 template <class T, int PT>
 __global__ void __launch_bounds__(128) k3_filter_zs(G3 g, const T* __restrict__ src, T* __restrict__ dst, int comp,
                                                     Taps3<T> t) {
   static_assert(PT <= ZHA, "filter halo above the staged halo");
   constexpr int SEG = 128 * ZR, NV = ZR + 2 * ZHA, VL = 16 / (int)sizeof(T);
-  __shared__ __align__(16) T row[SEG + 2 * ZHA];
+  constexpr int ROW = SEG + 2 * ZHA + ZTAIL, NVEC = ROW / VL, UV = (NVEC + 127) / 128;
+  static_assert(ROW % VL == 0 && ZHA % VL == 0, "16-byte vectors tile the staged row");
+  typedef typename std::conditional<sizeof(T) == 4, float4, double2>::type V;
+  __shared__ __align__(16) T row[ROW];
   const int kb = blockIdx.x * SEG, j = blockIdx.y, i = blockIdx.z;
   const int n = g.n[2];
-  const long base = nid(g, i, j, 0);
-  for (int e = threadIdx.x; e < SEG + 2 * ZHA; e += 128) {
-    const int q = kb - ZHA + e;
-    row[e] = (q >= 0 && q <= n) ? src[base + q] : T(0);
+  // nodes past this segment that this block also filters (the row's last block only)
+  const int tail = blockIdx.x + 1 == gridDim.x ? min(max(n + 1 - (kb + SEG), 0), ZTAIL) : 0;
+  const long base = nid(g, i, j, 0);   // 16-byte aligned: ldz is padded to 128 bytes
+  // the staged row in 16-byte vectors, every thread's loads issued before any is stored (an element
+  // q of the row is node kb - ZHA + q; off the row: zero)
+  V vv[UV];
+#pragma unroll
+  for (int u = 0; u < UV; u++) {
+    const int e = (threadIdx.x + u * 128) * VL, q0 = kb - ZHA + e;
+    T x[VL];
+#pragma unroll
+    for (int l = 0; l < VL; l++) x[l] = T(0);
+    if (e < SEG + 2 * ZHA + tail) {
+      if (q0 >= 0 && q0 + VL - 1 <= n) {
+        const V w = *reinterpret_cast<const V*>(src + base + q0);
+        if constexpr (VL == 4) { x[0] = w.x; x[1] = w.y; x[2] = w.z; x[3] = w.w; }
+        else { x[0] = w.x; x[1] = w.y; }
+      } else {
+#pragma unroll
+        for (int l = 0; l < VL; l++)
+          if (q0 + l >= 0 && q0 + l <= n) x[l] = src[base + q0 + l];
+      }
+    }
+    if constexpr (VL == 4) vv[u] = make_float4(x[0], x[1], x[2], x[3]);
+    else vv[u] = make_double2(x[0], x[1]);
+  }
+#pragma unroll
+  for (int u = 0; u < UV; u++) {
+    const int vi = threadIdx.x + u * 128;
+    if (vi < NVEC) reinterpret_cast<V*>(row)[vi] = vv[u];
   }
   __syncthreads();
   int lo0, hi0, lo1, hi1, lo2, hi2;
@@ -390,15 +424,43 @@ __global__ void __launch_bounds__(128) k3_filter_zs(G3 g, const T* __restrict__ 
   T v[NV];
 #pragma unroll
   for (int q = 0; q < NV / VL; q++) ld16(row + l0 + q * VL, v + q * VL);
+  T o[ZR];
 #pragma unroll
   for (int r = 0; r < ZR; r++) {
     const int k = kb + l0 + r;
-    if (k > n) break;
     T acc = T(0);
 #pragma unroll
     for (int m = 0; m <= 2 * PT; m++) acc += t.c[m] * v[r + ZHA - PT + m];
+    o[r] = (other && k >= lo2 && k <= hi2) ? acc : T(0);
+  }
+  if (kb + l0 + ZR - 1 <= n) {
+#pragma unroll
+    for (int r = 0; r < ZR; r += VL) {
+      V w;
+      if constexpr (VL == 4) w = make_float4(o[r], o[r + 1], o[r + 2], o[r + 3]);
+      else w = make_double2(o[r], o[r + 1]);
+      *reinterpret_cast<V*>(dst + base + kb + l0 + r) = w;
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < ZR; r++)
+      if (kb + l0 + r <= n) dst[base + kb + l0 + r] = o[r];
+  }
+  if ((int)threadIdx.x < tail) {
+    const int e = SEG + threadIdx.x, k = kb + e;   // k <= n by the choice of tail
+    T acc = T(0);
+#pragma unroll
+    for (int m = 0; m <= 2 * PT; m++) acc += t.c[m] * row[e + ZHA - PT + m];
     dst[base + k] = (other && k >= lo2 && k <= hi2) ? acc : T(0);
   }
+}
+
+// blocks along a row of n + 1 nodes for k3_filter_zs: a remainder of up to ZTAIL nodes rides with the last
+// segment
+inline unsigned zs_blocks(int n) {
+  constexpr int SEG = 128 * ZR;
+  const int full = (n + 1) / SEG, rem = n + 1 - full * SEG;
+  return (unsigned)(full == 0 ? 1 : full + (rem > ZTAIL ? 1 : 0));
 }
 
 // x and y axes of the composed filter (stride 1, PT taps each side) in one pass. A CTA stages, by one bulk
@@ -574,7 +636,7 @@ void set_filter_xy_smem() {
 template <class T, int PT>
 void launch_filter_fast(const G3& g, const T* src, T* dst, int comp, int axis, const Taps3<T>& t, cudaStream_t s) {
   if (axis == 2) {
-    k3_filter_zs<T, PT><<<dim3(nblk(g.n[2] + 1, 128 * ZR), g.n[1] + 1, g.n[0] + 1), 128, 0, s>>>(g, src, dst, comp, t);
+    k3_filter_zs<T, PT><<<dim3(zs_blocks(g.n[2]), g.n[1] + 1, g.n[0] + 1), 128, 0, s>>>(g, src, dst, comp, t);
   } else {
     // segments of about 32 nodes along the axis: enough lines in flight to cover the load latency
     const int n1 = (axis == 0 ? g.n[0] : g.n[1]) + 1;
