@@ -478,7 +478,10 @@ __global__ void __launch_bounds__(256) k3_filter_xy(G3 g, const __grid_constant_
   constexpr int W = 2 * PT + 1, XW = XYT + 2 * PT;
   extern __shared__ __align__(128) unsigned char raw3[];
   T* S = reinterpret_cast<T*>(raw3 + ((128u - ((uint32_t)__cvta_generic_to_shared(raw3) & 127u)) & 127u));
-  T* X1 = S + XW * XW * ZB;    // after the x pass: [x 0..XYT) [y 0..XW) [z 0..ZB)
+  // after the x pass: [x 0..XYT) [y 0..XW) [z 0..ZB), x planes XP apart (padded by 16 elements, so that the
+  // two x planes a warp of the y pass reads fall in different banks)
+  constexpr int XP = XW * ZB + 16;
+  T* X1 = S + XW * XW * ZB;
   __shared__ __align__(8) uint64_t bar;
   const int k0 = blockIdx.x * ZB, j0 = blockIdx.y * XYT, i0 = blockIdx.z * XYT;
   const int tid = threadIdx.x;
@@ -547,7 +550,7 @@ __global__ void __launch_bounds__(256) k3_filter_xy(G3 g, const __grid_constant_
 #pragma unroll
       for (int m = 0; m < W; m++) acc += c[m] * w[m];
       const int gi = i0 + xo;
-      X1[(xo * XW + yi) * ZB + zi] = (other && gi >= lo0 && gi <= hi0) ? acc : T(0);
+      X1[xo * XP + yi * ZB + zi] = (other && gi >= lo0 && gi <= hi0) ? acc : T(0);
       if (xo + 1 < XYT) {
 #pragma unroll
         for (int m = 0; m < W - 1; m++) w[m] = w[m + 1];
@@ -562,7 +565,7 @@ __global__ void __launch_bounds__(256) k3_filter_xy(G3 g, const __grid_constant_
     const int gi = i0 + xo, gk = k0 + zi;
     const bool other = gi >= lo0 && gi <= hi0 && gk >= lo2 && gk <= hi2;
     const bool in = gi <= g.n[0] && gk <= g.n[2];
-    const T* row = X1 + xo * XW * ZB + zi;
+    const T* row = X1 + xo * XP + zi;
     T w[W];
 #pragma unroll
     for (int m = 0; m < W; m++) w[m] = row[m * ZB];
@@ -585,7 +588,7 @@ static_assert(XYT * ZB == 256, "one y-pass line per thread");
 
 template <class T, int PT>
 constexpr size_t filter_xy_smem() {
-  return (size_t)((XYT + 2 * PT) * (XYT + 2 * PT) * ZB + XYT * (XYT + 2 * PT) * ZB) * sizeof(T) + 128;
+  return (size_t)((XYT + 2 * PT) * (XYT + 2 * PT) * ZB + XYT * ((XYT + 2 * PT) * ZB + 16)) * sizeof(T) + 128;
 }
 
 typedef CUresult (*Encode3Fn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -1188,10 +1191,12 @@ __device__ __forceinline__ double cum_shape(int order, double u) {
   return acc;
 }
 
-// Z(k) = sum over the live ion rows of w_m (C(Z1 - k) - C(Z0 - k)): the z-prefix of the rows' shape change
+// Z(k) = sum over the live ion rows of w_m (C(Z1 - k) - C(Z0 - k)): the z-prefix of the rows' shape change.
+// One warp per z node, its lanes over the rows near the node (strided), then a warp sum: the FP64 shape
+// sums are latency-bound, so they are spread over many warps instead of run one node per thread.
 __global__ void k3_ion_z(G3 g, Lat3 L, int order, long long mlo, long long mhi, double t0, double t1, double* Zs) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k > g.n[2]) return;
+  const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (k > g.n[2]) return;   // warp-uniform
   const double dz = g.d[2], idz = g.id[2];
   const double vsh = L.beta * kC;
   long long m0 = (long long)floor(((k - 4) * dz + vsh * t0) / L.h - 0.5);
@@ -1199,7 +1204,7 @@ __global__ void k3_ion_z(G3 g, Lat3 L, int order, long long mlo, long long mhi, 
   if (m0 < mlo) m0 = mlo;
   if (m1 > mhi - 1) m1 = mhi - 1;
   double acc = 0.0;
-  for (long long m = m0; m <= m1; m++) {
+  for (long long m = m0 + lane; m <= m1; m += 32) {
     const double zl = (m + 0.5) * L.h;
     const double n = L.gamma * lab_density3(L, L.gamma * zl);
     if (n <= 0.0) continue;
@@ -1207,7 +1212,9 @@ __global__ void k3_ion_z(G3 g, Lat3 L, int order, long long mlo, long long mhi, 
     const double Z0 = (zl - vsh * t0) * idz, Z1 = (zl - vsh * t1) * idz;
     acc += w * (cum_shape(order, Z1 - k) - cum_shape(order, Z0 - k));
   }
-  Zs[k] = acc;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if (lane == 0) Zs[k] = acc;
 }
 
 // J_z += coef Tx(i) Ty(j) Z(k), coef = -q_ion/(dx dy dt), on the nodes where T_x T_y is non-zero
@@ -1219,12 +1226,21 @@ __global__ void __launch_bounds__(128) k3_ion_jz(G3 g, const double* Tx, const d
   const double f = coef * Tx[i] * Ty[j];
   if (f == 0.0) return;
   const int kb = blockIdx.x * 128 * KPT + threadIdx.x;
+  // every load of the thread's KPT nodes issued before any store
+  T jv[KPT];
+  double zv[KPT];
+#pragma unroll
+  for (int kk = 0; kk < KPT; kk++) {
+    const int k = min(kb + kk * 128, g.n[2]);
+    zv[kk] = Zs[k];
+    jv[kk] = Jz[nid(g, i, j, k)];
+  }
 #pragma unroll
   for (int kk = 0; kk < KPT; kk++) {
     const int k = kb + kk * 128;
     if (k > g.n[2]) break;
-    const double v = f * Zs[k];
-    if (v != 0.0) Jz[nid(g, i, j, k)] += T(v);
+    const double v = f * zv[kk];
+    if (v != 0.0) Jz[nid(g, i, j, k)] = jv[kk] + T(v);
   }
 }
 
@@ -2441,7 +2457,7 @@ struct Sim3 : Sim3Api {
     }
     const double tn = time_of(step), tn1 = time_of(step + 1);
     if (loaded && ions && row_next > mlo) {
-      k3_ion_z<<<nblk(g.n[2] + 1, 32), 32, 0, s>>>(g, lat, cfg.shape_order, mlo, row_next, tn, tn1, Zs);
+      k3_ion_z<<<nblk(g.n[2] + 1, 4), 128, 0, s>>>(g, lat, cfg.shape_order, mlo, row_next, tn, tn1, Zs);
       k3_ion_jz<T><<<dim3(nblk(g.n[2] + 1, 128 * KPT), ion_j1 - ion_j0 + 1, ion_i1 - ion_i0 + 1), 128, 0, s>>>(
           g, Tx, Ty, Zs, -kQe / (g.d[0] * g.d[1] * g.dt), ion_i0, ion_j0, J + 2 * g.cs);
       nl += 2;
