@@ -227,10 +227,8 @@ __device__ void beam_deposit(const GridP& g, const FieldPtrs<T>& f, int order, d
 }
 
 template <class T>
-__global__ void k_beam_push(GridP g, FieldPtrs<T> f, Beam<T> b, int order, double tn, double tn1, int nodal,
-                            const double* acc) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= b.n) return;
+__device__ __forceinline__ void beam_push_one(const GridP& g, const FieldPtrs<T>& f, const Beam<T>& b, int order,
+                                              double tn, double tn1, int nodal, const double* acc, int j) {
   int fl = b.flag[j];
   if (!(fl & 1)) return;
   const double xlo = g.gx_lo * g.dx, xhi = g.gx_hi * g.dx;
@@ -283,6 +281,25 @@ __global__ void k_beam_push(GridP g, FieldPtrs<T> f, Beam<T> b, int order, doubl
   if (b.self) beam_deposit<T>(g, f, order, x, z, xn, zn, (double)(uy / g1), -kQe * (double)b.w[j]);
   b.x[j] = xn; b.z[j] = zn; b.ux[j] = ux; b.uy[j] = uy; b.uz[j] = uz;
   if (xn < xlo || xn >= xhi || zn < zlo || zn >= zhi) b.flag[j] = fl & ~1;
+}
+
+template <class T>
+__global__ void k_beam_push(GridP g, FieldPtrs<T> f, Beam<T> b, int order, double tn, double tn1, int nodal,
+                            const double* acc) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= b.n) return;
+  beam_push_one<T>(g, f, b, order, tn, tn1, nodal, acc, j);
+}
+
+// the batched step's test beams: run blockIdx.y, its particles from blockIdx.x * 128 (the Yee-located
+// gather; the batched step carries no node-interpolated runs)
+template <class T>
+__global__ void k_beam_push_batch(const StepArgs<T>* a) {
+  const StepArgs<T>& A = a[blockIdx.y];
+  if (!A.beam_on) return;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= A.beam.n) return;
+  beam_push_one<T>(A.g, A.f, A.beam, A.beam_order, A.beam_tn, A.beam_tn1, 0, A.beam_acc, j);
 }
 
 // ---------------------------------------------------------------------------
@@ -796,6 +813,11 @@ void launch_beam_init(Beam<T> b, const double* lx, const double* lz, const doubl
 }
 
 template <class T>
+void launch_beam_push_batch(const StepArgs<T>* a, int nruns, int beam_blocks, cudaStream_t s) {
+  if (beam_blocks > 0) k_beam_push_batch<T><<<dim3(beam_blocks, nruns), 128, 0, s>>>(a);
+}
+
+template <class T>
 void launch_beam_push(const GridP& g, const FieldPtrs<T>& f, Beam<T> b, int order, double tn, double tn1, int nodal,
                       const double* scratch, cudaStream_t s) {
   if (b.n <= 0) return;
@@ -904,6 +926,7 @@ void launch_shift_particles(const GridP& g, Particles<T> p, const Ctrl* ctrl, in
   template void launch_antenna_ion_batch<T>(const StepArgs<T>*, const BatchGrid&, bool, cudaStream_t);          \
   template void launch_beam_self_field<T>(const GridP&, const FieldPtrs<T>&, Beam<T>, int, const double*, double, \
                                           double*, double*, double*, double*, cudaStream_t);                    \
+  template void launch_beam_push_batch<T>(const StepArgs<T>*, int, int, cudaStream_t);                              \
   template void launch_beam_push<T>(const GridP&, const FieldPtrs<T>&, Beam<T>, int, double, double, int,         \
                                     const double*, cudaStream_t);                                                 \
   template void launch_nodal<T>(const GridP&, const FieldPtrs<T>&, cudaStream_t);                                 \

@@ -686,11 +686,11 @@ struct Sim : SimBase {
   }
 
   // ---- batched (ensemble) stepping ---------------------------------------------------------------------
-  // A run the batched ensemble step carries: plasma loaded, the Yee-located gather, no test beam, no lab
-  // samples, no moving window (those steps keep the per-run launches).
+  // A run the batched ensemble step carries: plasma loaded, the Yee-located gather, no lab samples, no
+  // moving window (those steps keep the per-run launches); a test beam rides along.
   bool batchable() const {
     const pic_config& cf = c->cfg;
-    return loaded && cap > 0 && !nodal && beam.n == 0 && nrows == 0 && !cf.moving_window && tmaps.ok;
+    return loaded && cap > 0 && !nodal && nrows == 0 && !cf.moving_window && tmaps.ok;
   }
   // upper bounds of the per-step work of the batched kernels that do not run a fixed grid
   int inj_xblocks() const { return (g.gx_hi - g.gx_lo + ip.xblock - 1) / ip.xblock; }
@@ -731,6 +731,13 @@ struct Sim : SimBase {
     a.pd = pdef;
     a.push_on = 1;
     set_frame(step + 1);
+    // the test beam, pushed with the same fields after the plasma
+    a.beam_on = beam.n > 0;
+    a.beam = beam;
+    a.beam_order = cf.shape_order;
+    a.beam_tn = tn;
+    a.beam_tn1 = tn1;
+    a.beam_acc = beam_scratch;
     a.ant_on = has_laser && antenna_step(tn, tn1, a.ast);
     a.ant_xs = ant_xs;
     const bool column = ions && loaded && !pairs;
@@ -1064,6 +1071,7 @@ struct BatchImpl : Batch {
   BatchGrid bg{};
   int order = 3, pt_taps = 0, push_grid = 0, smem_nodes = 0, tile_z = 0;
   bool friedman = false, ck = false, filt_gather = false, filt_J = false, any_ion = false;
+  int beam_blocks = 0;   // blocks of 128 particles of the largest test beam (0: no run has one)
   size_t filt_smem = 0, amp_smem = 0;
   int64_t nl = 0, nstep = 0;
 
@@ -1090,7 +1098,7 @@ struct BatchImpl : Batch {
       const pic_config& cf = c->cfg;
       if (cf.precision != c0.precision || cf.shape_order != c0.shape_order) { *why = "mixed precisions or orders"; return false; }
       Sim<T>* m = S<T>(c);
-      if (!m->batchable()) { *why = "run with a test beam, lab samples, moving window or node gather"; return false; }
+      if (!m->batchable()) { *why = "run with lab samples, moving window or node gather"; return false; }
       sims.push_back(m);
     }
     Sim<T>* m0 = sims[0];
@@ -1125,6 +1133,7 @@ struct BatchImpl : Batch {
       ion_off[r + 1] = ion_off[r] + (column ? (int)((m->ion_rows_max() + 255) / 256) : 0);
       inj_off[r + 1] = inj_off[r] + m->inj_xblocks() * m->inj_rblocks_max();
       ant_off[r + 1] = ant_off[r] + (std::max(m->g.nx, m->g.nz) + 1 + 127) / 128;
+      beam_blocks = std::max(beam_blocks, (m->beam.n + 127) / 128);
     }
     bg.nruns = n;
     bg.tiles = tile_off[n];
@@ -1159,11 +1168,14 @@ struct BatchImpl : Batch {
     cudaMemcpyAsync(dA[q], hA[q], sizeof(StepArgs<T>) * n, cudaMemcpyHostToDevice, s);
     launch_faraday_filter_batch<T>(dA[q], bg, friedman, ck, pt_taps, filt_gather, filt_smem, s);
     launch_push_batch<T>(dA[q], bg, order, push_grid, smem_nodes, tile_z, s);
+    launch_beam_push_batch<T>(dA[q], n, beam_blocks, s);
     launch_antenna_ion_batch<T>(dA[q], bg, any_ion, s);
     launch_ampere_batch<T>(dA[q], bg, filt_J, pt_taps, amp_smem, s);
     launch_inject_batch<T>(dA[q], bg, s);
   }
-  static int kernels_per_step(bool filt, bool ion) { return 1 + (filt ? 1 : 0) + 3 + 1 + (ion ? 1 : 0) + 1 + 2; }
+  static int kernels_per_step(bool filt, bool ion, bool beam) {
+    return 1 + (filt ? 1 : 0) + 3 + (beam ? 1 : 0) + 1 + (ion ? 1 : 0) + 1 + 2;
+  }
 
   int step(int nsteps) override {
     for (int k = 0; k < nsteps; k++) {
@@ -1199,7 +1211,7 @@ struct BatchImpl : Batch {
       }
       cudaEventRecord(done[q], s);
       used[q] = true;
-      nl += kernels_per_step(filt_gather, any_ion);
+      nl += kernels_per_step(filt_gather, any_ion, beam_blocks > 0);
       for (int r : sorts) {
         sims[r]->do_sort();
         nl += 8;

@@ -429,6 +429,11 @@ struct StepArgs {
   int inj_on, inj_xblocks;
   InjectP ip;
   int cap, chunk_cap, add_count, add_chunks;
+  // test beam (pushed after the plasma, before the antenna)
+  int beam_on, beam_order;
+  Beam<T> beam;
+  double beam_tn, beam_tn1;
+  const double* beam_acc;
 };
 
 // run of a block of a batched launch: the last r with off[r] <= b (off: nruns + 1 prefix sums)
@@ -477,6 +482,9 @@ void launch_ampere_batch(const StepArgs<T>* a, const BatchGrid& bg, bool filt_J,
 // plasma rows entering through the +z plane of every run, then the runs' particle and chunk counts
 template <class T>
 void launch_inject_batch(const StepArgs<T>* a, const BatchGrid& bg, cudaStream_t s);
+// the test beams of every run with one (blockIdx.y: run; beam_blocks: blocks of 128 particles of the largest)
+template <class T>
+void launch_beam_push_batch(const StepArgs<T>* a, int nruns, int beam_blocks, cudaStream_t s);
 // filter taps and shared-memory sizes the batched field kernels need (the same as a single run's)
 template <class T>
 FilterTaps<T> filter_taps(const FilterSpec& fs);

@@ -26,12 +26,12 @@ struct pic_ens {
 namespace {
 
 // runs that the batched step may carry, judged from their inputs: 2D, the Yee-located gather, plasma, no
-// test beam, no moving window, one precision, shape order and particle layout
+// moving window, one precision, shape order and particle layout (a test beam rides along)
 bool batch_candidates(int n, const pic_config* cfgs, const pic_plasma* plasmas) {
   for (int i = 0; i < n; i++) {
     const pic_config& c = cfgs[i];
     if ((c.dim != 0 && c.dim != 2) || c.gather_scheme != 0 || c.moving_window) return false;
-    if (plasmas[i].beam_n > 0 || !(plasmas[i].n0 > 0.0)) return false;
+    if (!(plasmas[i].n0 > 0.0)) return false;
     if (c.precision != cfgs[0].precision || c.shape_order != cfgs[0].shape_order || c.tile_x != cfgs[0].tile_x ||
         c.tile_z != cfgs[0].tile_z || c.sort_every != cfgs[0].sort_every)
       return false;

@@ -478,6 +478,38 @@ def test_ensemble_runs_match_runs_alone(Sim, graphs):
     ens.close()
 
 
+def test_ensemble_with_test_beams_batched_matches_runs_alone(Sim):
+    """runs carrying a test beam (the surrogate's labelling runs) ride the batched step: each run's fields
+    and beam at the end of the shortest run, its beam inside the plasma, are those of the run alone (FP64;
+    over about a thousand steps the shared-memory current sums, whose order differs between the batched
+    and the single-run kernels, leave differences of a few 1e-12 that grow slowly, hence 1e-9)"""
+    from paper_1009_2727_gb300.pic import Ensemble
+    ws = W.surrogate_runs(3, seed=21)
+    for w in ws:
+        w["precision"] = "fp64"
+        w["sort_every"] = 16
+    steps = min(int(w["steps"]) for w in ws)   # to the end of the shortest run: its beam has crossed
+    ens = Ensemble(ws, precision="fp64")
+    assert ens.batched
+    ens.step(steps)
+    ens.sync()
+    active = []
+    for i, w in enumerate(ws):
+        alone = Sim(w, precision="fp64", sort_every=16)
+        alone.step(steps)
+        alone.sync()
+        check_fields(ens[i], alone, 1e-9)
+        pe, pa = ens[i].particles(2), alone.particles(2)
+        assert np.array_equal(pe["active"], pa["active"]) and np.array_equal(pe["alive"], pa["alive"])
+        for k in ("x", "z", "ux", "uy", "uz"):
+            assert rel(pe[k], pa[k]) <= 1e-9, k
+        assert ens[i].stats()["beam_gamma_lab"] == pytest.approx(alone.stats()["beam_gamma_lab"], rel=1e-9)
+        active.append(int(ens[i].stats()["n_beam_active"]))
+        alone.close()
+    ens.close()
+    assert max(active) > 0, active
+
+
 def test_ensemble_mixed_batched_matches_runs_alone(Sim):
     """the batched ensemble in mixed precision (the stage's numerics: CK, Friedman, PML, 4 passes +
     compensation, electron-ion pairs) against each run alone: the same up to the order of the FP32
