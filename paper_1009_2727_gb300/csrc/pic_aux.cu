@@ -402,18 +402,34 @@ __global__ void __launch_bounds__(256) k_stats(GridP g, FieldPtrs<T> f, Particle
     float wtf = 0.f;
     const long n = ctrl->count;
     if (trap > 0.0) {
-      // every load of an iteration issued at once (no branch before them), four iterations in flight
-#pragma unroll 4
-      for (long j = tid; j < n; j += nthr) {
-        const float w = float(p.w[j]);
+      // four consecutive particles per iteration from 16-byte loads of each array (the arrays are 16-byte
+      // aligned), every load of an iteration issued at once, two iterations in flight; the last n % 4
+      // particles one by one
+      auto one = [&](float w, float ux, float uy, float uzs) {
         // boosted-frame momentum (the mixed path stores u_z - u0) -> lab-frame gamma
-        const float ux = float(p.ux[j]), uy = float(p.uy[j]);
-        const float uz = CellPos<T>::value ? g.fr_u0 + float(p.uz[j]) : float(p.uz[j]);
+        const float uz = CellPos<T>::value ? g.fr_u0 + uzs : uzs;
         const bool live = w > 0.f;
         nef += live ? 1 : 0;
         const float gp = sqrtf(1.f + (ux * ux + uy * uy + uz * uz) * ic2);
         if (live && gamf * (gp + bef * uz * ic) > trapf) wtf += w;
+      };
+      // (arrays from an allocator that does not align to 16 bytes take the one-by-one loop throughout)
+      const bool al16 = ((reinterpret_cast<uintptr_t>(p.w) | reinterpret_cast<uintptr_t>(p.ux) |
+                          reinterpret_cast<uintptr_t>(p.uy) | reinterpret_cast<uintptr_t>(p.uz)) & 15) == 0;
+      const long n4 = al16 ? n / 4 : 0;
+      const float4* w4 = reinterpret_cast<const float4*>(p.w);
+      const float4* x4 = reinterpret_cast<const float4*>(p.ux);
+      const float4* y4 = reinterpret_cast<const float4*>(p.uy);
+      const float4* z4 = reinterpret_cast<const float4*>(p.uz);
+#pragma unroll 2
+      for (long j = tid; j < n4; j += nthr) {
+        const float4 w = w4[j], ux = x4[j], uy = y4[j], uz = z4[j];
+        one(w.x, ux.x, uy.x, uz.x);
+        one(w.y, ux.y, uy.y, uz.y);
+        one(w.z, ux.z, uy.z, uz.z);
+        one(w.w, ux.w, uy.w, uz.w);
       }
+      for (long j = 4 * n4 + tid; j < n; j += nthr) one(float(p.w[j]), float(p.ux[j]), float(p.uy[j]), float(p.uz[j]));
     } else {
 #pragma unroll 4
       for (long j = tid; j < n; j += nthr) nef += float(p.w[j]) > 0.f ? 1 : 0;

@@ -387,6 +387,34 @@ def test_gauss_law_on_gpu_full_size_mixed(Sim):
     assert np.abs(G[i0:i1, k0:k1]).max() <= 1e-4 * scale
 
 
+def test_stats_mixed_match_host_recount(Sim):
+    """the diagnostics' particle pass on the mixed path (16-byte loads of w and u, four particles per
+    iteration, the remainder one by one) against a recount of the particles read back: the live-electron
+    count exactly, the trapped charge above a threshold set in a gap of the lab gamma (FP32 on the device)"""
+    w = W.shrink(W.stage_2d(), 96, 322)   # a particle count that is no multiple of four, most likely
+    w["plasma"]["z_start_lab"] = 0.0
+    g = Sim(w)
+    g.step(120)
+    g.sync()
+    po = g.particles(0)
+    live = po["alive"] & (po["w"] > 0)
+    c = 299792458.0
+    gb = float(w["gamma_boost"])
+    bb = np.sqrt(1.0 - 1.0 / gb ** 2)
+    gp = np.sqrt(1.0 + (po["ux"] ** 2 + po["uy"] ** 2 + po["uz"] ** 2) / c ** 2)
+    glab = (gb * (gp + bb * po["uz"] / c))[live]
+    st = g.stats()
+    assert st["n_electrons"] == int(live.sum())
+    s_ = np.sort(glab[glab > 1.0 + 1e-4])
+    assert s_.size > 100
+    i = s_.size // 2 + int(np.argmax(np.diff(s_[s_.size // 2:]) > 1e-4 * s_[s_.size // 2:-1]))
+    thr = 0.5 * (s_[i] + s_[i + 1])
+    assert s_[i + 1] - s_[i] > 1e-4 * thr   # far above FP32 rounding of the device's lab gamma
+    ref = 1.602176634e-19 * po["w"][live][glab > thr].sum()
+    assert ref > 0
+    assert g.stats(trap_gamma_lab=thr)["trapped_charge"] == pytest.approx(ref, rel=1e-5)
+
+
 def test_mixed_vs_fp64_full_stage(Sim):
     """The mixed path against the FP64 GPU path (itself pinned to the oracle at 1e-10) on the full
     4096 x 256 stage, both stepped 300 steps from the same inputs. The laser field agrees to FP32
