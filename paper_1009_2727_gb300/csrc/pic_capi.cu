@@ -113,6 +113,7 @@ struct Sim : SimBase {
   T* tmp = nullptr;
   Ctrl* ctrl = nullptr;
   Ctrl* hmirror = nullptr;     // pinned
+  double* hstats = nullptr;    // pinned: the diagnostics' sums and a copy of the control block
   TileMaps tmaps{};
   // particles
   Particles<T> P{}, P2{};
@@ -163,6 +164,7 @@ struct Sim : SimBase {
   ~Sim() override {
     for (auto e : ev) cudaEventDestroy(e);
     if (hmirror) cudaFreeHost(hmirror);
+    if (hstats) cudaFreeHost(hstats);
   }
 
   template <class U>
@@ -259,6 +261,7 @@ struct Sim : SimBase {
     stage = al<double>(stage_n);
     if (!ctrl || !stats_buf || !stage) return c->fail(PIC_ENOMEM, "allocation failed");
     if (cudaMallocHost(&hmirror, sizeof(Ctrl)) != cudaSuccess) hmirror = nullptr;
+    if (cudaMallocHost(&hstats, 8 * sizeof(double) + sizeof(Ctrl)) != cudaSuccess) hstats = nullptr;
     // particle tiles
     // default tile: 8 (x) by 32 (z) cells, so that a warp spans 32 consecutive z-cells
     int tx = cf.tile_x > 0 ? cf.tile_x : 8, tz = cf.tile_z > 0 ? cf.tile_z : 32;
@@ -991,9 +994,18 @@ struct Sim : SimBase {
     launch_stats<T>(g, f, P, ctrl, cap, beam, c->hg.gamma, c->hg.beta, trap, stats_buf, c->stream);
     double h[8];
     Ctrl hc;
-    cudaStreamSynchronize(c->stream);
-    cudaMemcpy(h, stats_buf, sizeof(h), cudaMemcpyDeviceToHost);
-    cudaMemcpy(&hc, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost);
+    if (hstats) {
+      // both reads queued behind the reduction into pinned memory, one wait
+      cudaMemcpyAsync(hstats, stats_buf, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+      cudaMemcpyAsync(hstats + 8, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, c->stream);
+      cudaStreamSynchronize(c->stream);
+      std::memcpy(h, hstats, sizeof(h));
+      std::memcpy(&hc, hstats + 8, sizeof(Ctrl));
+    } else {
+      cudaStreamSynchronize(c->stream);
+      cudaMemcpy(h, stats_buf, sizeof(h), cudaMemcpyDeviceToHost);
+      cudaMemcpy(&hc, ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost);
+    }
     o->step = step; o->t = time_of(step);
     o->dt = g.dt; o->dx = g.dx; o->dz = g.dz; o->gamma = c->hg.gamma; o->beta = c->hg.beta;
     o->n_electrons = (int64_t)h[0];

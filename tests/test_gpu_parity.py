@@ -390,7 +390,8 @@ def test_gauss_law_on_gpu_full_size_mixed(Sim):
 def test_stats_mixed_match_host_recount(Sim):
     """the diagnostics' particle pass on the mixed path (16-byte loads of w and u, four particles per
     iteration, the remainder one by one) against a recount of the particles read back: the live-electron
-    count exactly, the trapped charge above a threshold set in a gap of the lab gamma (FP32 on the device)"""
+    count exactly; the trapped charge between the recounts above thr + d and above thr - d, d covering the
+    device's FP32 lab gamma (gamma_b (gamma' + beta u'_z / c) cancels to about 1e-5 absolute at gamma_b = 13)"""
     w = W.shrink(W.stage_2d(), 96, 322)   # a particle count that is no multiple of four, most likely
     w["plasma"]["z_start_lab"] = 0.0
     g = Sim(w)
@@ -405,14 +406,15 @@ def test_stats_mixed_match_host_recount(Sim):
     glab = (gb * (gp + bb * po["uz"] / c))[live]
     st = g.stats()
     assert st["n_electrons"] == int(live.sum())
-    s_ = np.sort(glab[glab > 1.0 + 1e-4])
-    assert s_.size > 100
-    i = s_.size // 2 + int(np.argmax(np.diff(s_[s_.size // 2:]) > 1e-4 * s_[s_.size // 2:-1]))
-    thr = 0.5 * (s_[i] + s_[i + 1])
-    assert s_[i + 1] - s_[i] > 1e-4 * thr   # far above FP32 rounding of the device's lab gamma
-    ref = 1.602176634e-19 * po["w"][live][glab > thr].sum()
-    assert ref > 0
-    assert g.stats(trap_gamma_lab=thr)["trapped_charge"] == pytest.approx(ref, rel=1e-5)
+    assert (glab > 1.0 + 1e-3).sum() > 100
+    thr = 0.5 * (1.0 + float(glab.max()))   # between the cold plasma and the most disturbed electron
+    d = 2e-4
+    wl = po["w"][live]
+    q_lo = 1.602176634e-19 * wl[glab > thr + d].sum()
+    q_hi = 1.602176634e-19 * wl[glab > thr - d].sum()
+    assert q_lo > 0
+    q = g.stats(trap_gamma_lab=thr)["trapped_charge"]
+    assert q_lo * (1 - 1e-5) <= q <= q_hi * (1 + 1e-5), (q_lo, q, q_hi)
 
 
 def test_mixed_vs_fp64_full_stage(Sim):
