@@ -253,7 +253,6 @@ struct Sim : SimBase {
     ctrl = al<Ctrl>(1);
     stats_buf = al<double>(8);
     {
-      const int P = cf.filter_passes + (cf.filter_compensate ? 1 : 0);
       const int H = (filt_gather || filt_J) ? filter_halo(fs) : 0;
       if (!make_tile_maps<T>(g, f, H, tmaps)) return c->fail(PIC_ECUDA, "TMA descriptor encoding failed");
     }

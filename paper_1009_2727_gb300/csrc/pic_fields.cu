@@ -265,11 +265,10 @@ __device__ __forceinline__ void filter_tile_any(const T* A, int BZ, T* B1, T* Zb
 
 // P passes at stride 1 with the taps unrolled: each thread filters four
 // consecutive values from a register window of 4 + 2P inputs (x-pass: four rows
-// of one column; z-pass: four columns of one row, read as 16-byte vectors)
+// of one column; z-pass: four columns of one row, read as 16-byte vectors). The
+// FP32 path takes filter_tile_fixed_f32 (below); this form serves FP64.
 template <class T>
 struct Vec16;
-template <>
-struct Vec16<float> { typedef float4 type; static constexpr int n = 4; };
 template <>
 struct Vec16<double> { typedef double2 type; static constexpr int n = 2; };
 
