@@ -502,7 +502,8 @@ __global__ void __launch_bounds__(256) k3_filter_xy(G3 g, const __grid_constant_
         "l"((unsigned long long)&map), "r"(k0), "r"(j0 - PT), "r"(i0 - PT), "r"(slot), "r"(sbar)
         : "memory");
   }
-  bool done = false;
+  // one warp polls the mbarrier; the others wait at the barrier below, taking no issue slots
+  bool done = tid >= 32;
   for (long it = 0; it < kWait3 && !done; it++) {
     uint32_t d;
     asm volatile(

@@ -415,6 +415,15 @@ __device__ __forceinline__ void filter_tile_to(const T* A, int BZ, T* B1, T* Zb,
   }
 }
 
+// Block-wide wait for a staged copy: one warp polls the mbarrier (the other warps wait at the barrier
+// instruction, which takes no issue slots from the SM's other blocks); the bar.sync that follows orders
+// the copy's arrival before every thread's reads. Returns false, block-uniformly, on timeout.
+__device__ __forceinline__ bool block_wait(uint64_t* bar, uint32_t parity) {
+  bool ok = true;
+  if (threadIdx.y == 0 && threadIdx.x < 32) ok = mbar_wait(bar, parity);
+  return __syncthreads_or(!ok) == 0;
+}
+
 __device__ __forceinline__ void tile_timeout(Ctrl* ctrl, uint64_t* bar0, uint64_t* bar1) {
   if (threadIdx.x == 0 && threadIdx.y == 0) {
     atomicOr(&ctrl->status, ST_TIMEOUT);
@@ -452,7 +461,7 @@ __device__ __forceinline__ void filter_fields_tile(const GridP& g, const FieldPt
     T* A = (u & 1) ? tile1 : tile0;
     if (leader && c + 1 < 6)
       stage<T>((u & 1) ? tile0 : tile1, c + 1 < 3 ? pmapE : pmapB, (c + 1) % 3, gk0, gi0, &bar[(u + 1) & 1], tm);
-    if (__syncthreads_or(!mbar_wait(&bar[u & 1], (u >> 1) & 1))) {   // block-uniform outcome
+    if (!block_wait(&bar[u & 1], (u >> 1) & 1)) {
       tile_timeout(ctrl, &bar[0], &bar[1]);
       return;
     }
@@ -515,7 +524,7 @@ __global__ void __launch_bounds__(FT_Z* FT_TY, 3) k_faraday_fused(GridP g, Field
       }
   }
   // the wait's outcome is made block-uniform, so that no thread is left at a later barrier
-  if (__syncthreads_or(!mbar_wait(&bar[0], 0))) {
+  if (!block_wait(&bar[0], 0)) {
     tile_timeout(ctrl, &bar[0], &bar[0]);
     return;
   }
@@ -596,7 +605,7 @@ __device__ __forceinline__ void ampere_tile(const GridP& g, const FieldPtrs<T>& 
   for (int c = 0; c < 3; c++) {
     T* A = (c & 1) ? tile1 : tile0;
     if (leader && c + 1 < 3) stage<T>((c & 1) ? tile0 : tile1, pmapJ, c + 1, gk0, gi0, &bar[(c + 1) & 1], tm);
-    if (__syncthreads_or(!mbar_wait(&bar[c & 1], (c >> 1) & 1))) {   // block-uniform outcome
+    if (!block_wait(&bar[c & 1], (c >> 1) & 1)) {
       tile_timeout(ctrl, &bar[0], &bar[1]);
       return;
     }
