@@ -175,6 +175,8 @@ struct Sim : SimBase {
     const HostGeom& h = c->hg;
     g.nx = cf.nx; g.nz = cf.nz; g.ld = h.ld;
     g.dx = h.dx; g.dz = h.dz; g.dt = h.dt; g.z0 = 0.0;
+    g.idx = 1.0 / h.dx; g.idz = 1.0 / h.dz;
+    g.dtf = (float)h.dt; g.idxf = (float)g.idx; g.idzf = (float)g.idz;
     g.gx_lo = h.gx_lo; g.gx_hi = h.gx_hi; g.gz_lo = h.gz_lo; g.gz_hi = h.gz_hi;
     g.pml = cf.pml_cells;
     g.fr_sz = 0; g.fr_fz = 0.0f;

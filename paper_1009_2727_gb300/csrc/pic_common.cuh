@@ -25,6 +25,8 @@ struct GridP {
   int nx, nz, ld;            // cells; row stride (elements) of every grid array
   long cs;                   // stride between the components of a 3-component block
   double dx, dz, dt;
+  double idx, idz;           // 1/dx, 1/dz from the host
+  float dtf, idxf, idzf;     // dt, 1/dx, 1/dz in FP32 (the field kernels of the mixed path run no FP64)
   double z0;                 // grid origin along z (moving window)
   int gx_lo, gx_hi, gz_lo, gz_hi;  // particle domain (cells)
   int pml;                   // PML cells (0 = none)
@@ -42,6 +44,21 @@ struct GridP {
   int il_nxl, il_ppcx, il_ppcz, il_kb;
   int z0_cells;
 };
+
+// dt, 1/dx, 1/dz in the path's type (host-computed: on this GPU an FP64 divide or conversion per thread
+// would run on its narrow FP64 pipe)
+template <class T>
+__host__ __device__ __forceinline__ T grid_dt(const GridP& g) {
+  if constexpr (sizeof(T) == 4) return g.dtf; else return g.dt;
+}
+template <class T>
+__host__ __device__ __forceinline__ T grid_idx(const GridP& g) {
+  if constexpr (sizeof(T) == 4) return g.idxf; else return g.idx;
+}
+template <class T>
+__host__ __device__ __forceinline__ T grid_idz(const GridP& g) {
+  if constexpr (sizeof(T) == 4) return g.idzf; else return g.idz;
+}
 
 // Valid index range of each E/B component (PEC walls); J uses the E ranges.
 __host__ __device__ inline void valid_range(int comp, int nx, int nz, int& i0, int& i1, int& k0, int& k1) {

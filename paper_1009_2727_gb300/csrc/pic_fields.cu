@@ -5,6 +5,8 @@
 //    the fields used by the gather, tile by tile in shared memory;
 //  - Ampere with the Yee operator and the split-field PML for E, fused with the
 //    filter of the deposited current and the rigid ion-column current.
+#include <type_traits>
+
 #include "pic_common.cuh"
 
 namespace picgb {
@@ -16,28 +18,43 @@ constexpr int FT_X = 16;
 constexpr int FT_Z = 64;
 constexpr int FT_TY = 4;
 
-// B update of one tile from E_eff staged in shared memory: Ee[c] holds the tile and a one-node halo, row
-// stride SZ, node (i0 - 1 + li, k0 - 1 + lk) at li * SZ + lk (zero outside the grid)
-template <class T, bool CK>
-__device__ __forceinline__ void faraday_update(const GridP& g, const FieldPtrs<T>& f, const PmlTabs& pt,
-                                               const FarK<T>& q, const T* const* Ee, const int SZ, int i0,
-                                               int k0) {
-  const bool interior = i0 >= pt.iin0 && i0 + FT_X - 1 <= pt.iin1 && k0 >= pt.kin0 && k0 + FT_Z - 1 <= pt.kin1;
-  const T dt = T(g.dt), idx = T(1.0 / g.dx), idz = T(1.0 / g.dz);
+// B^{n-1/2} of the thread's rows of a tile (rows ty, ty + FT_TY, ...; column k0 + tx), loaded together so
+// that their latencies overlap (and, in the fused kernel, overlap the tile's bulk copies)
+template <class T>
+struct TileB {
+  static constexpr int NR = FT_X / FT_TY;
+  T x[NR], y[NR], z[NR];
+};
+
+template <class T>
+__device__ __forceinline__ void load_tile_b(const GridP& g, const FieldPtrs<T>& f, int i0, int k0, TileB<T>& b) {
   const int k = k0 + threadIdx.x;
-  // the thread's B^{n-1/2} values of all its rows are loaded first, so that their latencies overlap (the
-  // stores of one row could otherwise alias the loads of the next)
-  constexpr int NR = FT_X / FT_TY;
-  T bx0[NR], by0[NR], bz0[NR];
 #pragma unroll
-  for (int r = 0; r < NR; r++) {
+  for (int r = 0; r < TileB<T>::NR; r++) {
     const int i = i0 + threadIdx.y + r * FT_TY;
     const long p = (long)i * g.ld + k;
     const bool in = i <= g.nx && k <= g.nz;
-    bx0[r] = (in && k <= g.nz - 1) ? f.B[0][p] : T(0);
-    bz0[r] = (in && i <= g.nx - 1) ? f.B[2][p] : T(0);
-    by0[r] = (in && i <= g.nx - 1 && k <= g.nz - 1) ? f.B[1][p] : T(0);
+    b.x[r] = (in && k <= g.nz - 1) ? f.B[0][p] : T(0);
+    b.z[r] = (in && i <= g.nx - 1) ? f.B[2][p] : T(0);
+    b.y[r] = (in && i <= g.nx - 1 && k <= g.nz - 1) ? f.B[1][p] : T(0);
   }
+}
+
+// B update of one tile from E_eff staged in shared memory: Ee[c] holds the tile and a one-node halo, row
+// stride SZ, node (i0 - 1 + li, k0 - 1 + lk) at li * SZ + lk (zero outside the grid); b: the tile's
+// B^{n-1/2} (load_tile_b). PML = false: a tile clear of the PML (no table reads, no FP64 in the
+// instruction stream)
+template <class T, bool CK, bool PML>
+__device__ __forceinline__ void faraday_update_t(const GridP& g, const FieldPtrs<T>& f, const PmlTabs& pt,
+                                                 const FarK<T>& q, const T* const* Ee, const int SZ, int i0,
+                                                 int k0, const TileB<T>& b) {
+  constexpr bool interior = !PML;
+  const T dt = grid_dt<T>(g), idx = grid_idx<T>(g), idz = grid_idz<T>(g);
+  const int k = k0 + threadIdx.x;
+  constexpr int NR = TileB<T>::NR;
+  const T* bx0 = b.x;
+  const T* by0 = b.y;
+  const T* bz0 = b.z;
 #pragma unroll
   for (int r = 0; r < NR; r++) {
     const int ti = threadIdx.y + r * FT_TY;
@@ -104,6 +121,16 @@ __device__ __forceinline__ void faraday_update(const GridP& g, const FieldPtrs<T
 }
 
 
+template <class T, bool CK>
+__device__ __forceinline__ void faraday_update(const GridP& g, const FieldPtrs<T>& f, const PmlTabs& pt,
+                                               const FarK<T>& q, const T* const* Ee, const int SZ, int i0,
+                                               int k0, const TileB<T>& b) {
+  // block-uniform: the tiles clear of the PML take the instantiation without its branches
+  const bool interior = i0 >= pt.iin0 && i0 + FT_X - 1 <= pt.iin1 && k0 >= pt.kin0 && k0 + FT_Z - 1 <= pt.kin1;
+  if (interior) faraday_update_t<T, CK, false>(g, f, pt, q, Ee, SZ, i0, k0, b);
+  else faraday_update_t<T, CK, true>(g, f, pt, q, Ee, SZ, i0, k0, b);
+}
+
 // Faraday + PML-B over a tile of FT_X x FT_Z nodes (threads FT_Z x FT_TY). The
 // Friedman field E_eff (Eq. 7) of the tile's nodes and a one-node halo is built
 // once in shared memory (zero outside the grid); the Friedman average update
@@ -115,6 +142,8 @@ __device__ __forceinline__ void faraday_tile(const GridP& g, const FieldPtrs<T>&
   constexpr int SX = FT_X + 2, SZ = FT_Z + 2;
   __shared__ T Ee[3][SX * SZ];
   const int i0 = tile_i * FT_X, k0 = tile_k * FT_Z;
+  TileB<T> bold;
+  load_tile_b<T>(g, f, i0, k0, bold);
   const int tid = threadIdx.y * FT_Z + threadIdx.x;
   for (int e = tid; e < SX * SZ; e += FT_Z * FT_TY) {
     const int li = e / SZ, lk = e - li * SZ;
@@ -140,7 +169,7 @@ __device__ __forceinline__ void faraday_tile(const GridP& g, const FieldPtrs<T>&
   }
   __syncthreads();
   const T* Eep[3] = {Ee[0], Ee[1], Ee[2]};
-  faraday_update<T, CK>(g, f, pt, q, Eep, SZ, i0, k0);
+  faraday_update<T, CK>(g, f, pt, q, Eep, SZ, i0, k0, bold);
 }
 
 template <class T, bool FRIED, bool CK>
@@ -287,14 +316,18 @@ __device__ __forceinline__ void filter_tile_fixed_f32(const float* A, int BZ, fl
   constexpr int HZ = (P + 3) & ~3, PAD = (HZ - P) & 1;
   constexpr int NPAIR = (WZ + PAD + 1) / 2;
   static_assert(2 * NPAIR <= WZP, "B1 row holds the pad and every pair");
+  // the staged box's row stride as a constant (a stride-1 filter of P passes has halo P, and the tile maps'
+  // boxes are FT_Z + 2 HZ wide): every load below addresses with an immediate offset
+  constexpr int BZC = FT_Z + 2 * HZ;
+  (void)BZ;
   const int tid = threadIdx.y * FT_Z + threadIdx.x;
   for (int task = tid; task < (FT_X / 4) * NPAIR; task += FT_Z * FT_TY) {
     const int rq = task / NPAIR, cpair = task - rq * NPAIR;
     const int r0 = 4 * rq, b = 2 * cpair;   // B1 column b <-> filter column b - PAD
-    const float* col = A + r0 * BZ + b - PAD;
+    const float* col = A + r0 * BZC + b - PAD;
     float2 v[NW];
 #pragma unroll
-    for (int j = 0; j < NW; j++) v[j] = *reinterpret_cast<const float2*>(col + j * BZ);
+    for (int j = 0; j < NW; j++) v[j] = *reinterpret_cast<const float2*>(col + j * BZC);
 #pragma unroll
     for (int q = 0; q < 4; q++) {
       float2 acc = make_float2(0.f, 0.f);
@@ -493,17 +526,19 @@ __global__ void __launch_bounds__(FT_Z* FT_TY, 3) k_faraday_fused(GridP g, Field
                                                                const __grid_constant__ CUtensorMap mapEb,
                                                                TileMaps tm, Ctrl* ctrl) {
   constexpr int SX = FT_X + 2, SZ = FT_Z + 2, RZ = FT_Z + 8;
+  // the staged boxes' geometry as constants: a stride-1 filter of PT passes has halo H = PT (the host
+  // checks that the tile maps were built for it), the boxes are FT_X + 2 H rows of FT_Z + 2 HZ
+  constexpr int H = PT, HZ = (PT + 3) & ~3, BX = FT_X + 2 * H, BZ = FT_Z + 2 * HZ;
+  constexpr int LINE = 128 / (int)sizeof(T), stride = (BX * BZ + LINE - 1) / LINE * LINE;
   extern __shared__ __align__(128) unsigned char smraw[];
-  const int stride = tile_stride<T>(tm);
   const int rstride = ring_stride<T>();
   T* A = reinterpret_cast<T*>(align128(smraw));   // E^n, three boxes with the filter halo
   T* R = A + 3 * stride;                          // E^{n-1} then E-bar, three components each (FRIED)
-  const int H = ft.H;
   T* B1 = R + (FRIED ? 6 * rstride : 0);
   T* Zb = B1 + FT_X * filter_wzp(H);
   __shared__ __align__(8) uint64_t bar[1];
   const int i0 = blockIdx.y * FT_X, k0 = blockIdx.x * FT_Z;
-  const int gi0 = i0 - tm.H, gk0 = k0 - tm.HZ;
+  const int gi0 = i0 - H, gk0 = k0 - HZ;
   const bool leader = threadIdx.x == 0 && threadIdx.y == 0;
   if (leader) {
     mbar_init(&bar[0]);
@@ -511,7 +546,7 @@ __global__ void __launch_bounds__(FT_Z* FT_TY, 3) k_faraday_fused(GridP g, Field
   }
   __syncthreads();
   if (leader) {
-    const uint32_t box = (uint32_t)(tm.BX * tm.BZ * sizeof(T)), rbox = (uint32_t)(SX * RZ * sizeof(T));
+    const uint32_t box = (uint32_t)(BX * BZ * sizeof(T)), rbox = (uint32_t)(SX * RZ * sizeof(T));
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&bar[0])),
                  "r"(3 * box + (FRIED ? 6 * rbox : 0u))
@@ -523,6 +558,9 @@ __global__ void __launch_bounds__(FT_Z* FT_TY, 3) k_faraday_fused(GridP g, Field
         tma_copy_box(R + (3 + c) * rstride, &mapEb, k0 - 4, i0 - 1, c, &bar[0]);
       }
   }
+  // the tile's B^{n-1/2} in flight while the copies land
+  TileB<T> bold;
+  load_tile_b<T>(g, f, i0, k0, bold);
   // the wait's outcome is made block-uniform, so that no thread is left at a later barrier
   if (!block_wait(&bar[0], 0)) {
     tile_timeout(ctrl, &bar[0], &bar[0]);
@@ -533,30 +571,37 @@ __global__ void __launch_bounds__(FT_Z* FT_TY, 3) k_faraday_fused(GridP g, Field
   if (FRIED) {
     // E_eff = c1 E^n + c2 E^{n-1} + c3 E-bar on the tile and its halo, in place of E^{n-1}; E-bar's update
     // for the tile's own nodes
-    const int off = (tm.H - 1) * tm.BZ + (tm.HZ - 1);   // box element of node (i0 - 1, k0 - 1)
+    constexpr int off = (H - 1) * BZ + (HZ - 1);   // box element of node (i0 - 1, k0 - 1)
     // E-bar's update of the tile's own nodes first (read before E_eff overwrites nothing it needs: E_eff
     // replaces E^{n-1}, E-bar's box is only read)
     const int k = k0 + threadIdx.x;
 #pragma unroll
     for (int c = 0; c < 3; c++) {
-      const T* Ac = A + c * stride + off + tm.BZ + 1;
+      const T* Ac = A + c * stride + off + BZ + 1;
       const T* Rb = R + (3 + c) * rstride + RZ + 4;
 #pragma unroll
       for (int r = 0; r < FT_X / FT_TY; r++) {
         const int ti = threadIdx.y + r * FT_TY, i = i0 + ti;
         if (i <= g.nx && k <= g.nz)
-          f.Ebn[c][(long)i * g.ld + k] = q.h1 * Ac[ti * tm.BZ + threadIdx.x] + q.h2 * Rb[ti * RZ + threadIdx.x];
+          f.Ebn[c][(long)i * g.ld + k] = q.h1 * Ac[ti * BZ + threadIdx.x] + q.h2 * Rb[ti * RZ + threadIdx.x];
       }
     }
+    // rows ty, ty + 4, ... of the tile + halo, columns tx and (two threads) tx + FT_Z: unrolled with
+    // constant strides
+#pragma unroll
     for (int c = 0; c < 3; c++) {
-      const T* Ac = A + c * stride + off;
-      T* Ro = R + c * rstride + 3;
-      const T* Rb = R + (3 + c) * rstride + 3;
-      for (int li = threadIdx.y; li < SX; li += FT_TY)
-        for (int lk = threadIdx.x; lk < SZ; lk += FT_Z) {
-          const int r = li * RZ + lk;
-          Ro[r] = q.c1 * Ac[li * tm.BZ + lk] + q.c2 * Ro[r] + q.c3 * Rb[r];
+      const T* Ac = A + c * stride + off + threadIdx.y * BZ + threadIdx.x;
+      T* Ro = R + c * rstride + 3 + threadIdx.y * RZ + threadIdx.x;
+      const T* Rb = R + (3 + c) * rstride + 3 + threadIdx.y * RZ + threadIdx.x;
+#pragma unroll
+      for (int m = 0; m < (SX + FT_TY - 1) / FT_TY; m++) {
+        if (threadIdx.y + m * FT_TY < SX) {
+          Ro[m * FT_TY * RZ] = q.c1 * Ac[m * FT_TY * BZ] + q.c2 * Ro[m * FT_TY * RZ] + q.c3 * Rb[m * FT_TY * RZ];
+          if (threadIdx.x < SZ - FT_Z)
+            Ro[m * FT_TY * RZ + FT_Z] =
+                q.c1 * Ac[m * FT_TY * BZ + FT_Z] + q.c2 * Ro[m * FT_TY * RZ + FT_Z] + q.c3 * Rb[m * FT_TY * RZ + FT_Z];
         }
+      }
     }
     Eep[0] = R + 3;
     Eep[1] = R + rstride + 3;
@@ -564,13 +609,13 @@ __global__ void __launch_bounds__(FT_Z* FT_TY, 3) k_faraday_fused(GridP g, Field
     esz = RZ;
     __syncthreads();
   } else {
-    for (int c = 0; c < 3; c++) Eep[c] = A + c * stride + (tm.H - 1) * tm.BZ + (tm.HZ - 1);
-    esz = tm.BZ;
+    for (int c = 0; c < 3; c++) Eep[c] = A + c * stride + (H - 1) * BZ + (HZ - 1);
+    esz = BZ;
   }
-  faraday_update<T, CK>(g, f, pt, q, Eep, esz, i0, k0);
-  // the gather copies of E^n: the filter of the staged boxes (filter halo H == tm.H)
+  faraday_update<T, CK>(g, f, pt, q, Eep, esz, i0, k0, bold);
+  // the gather copies of E^n: the filter of the staged boxes
   for (int c = 0; c < 3; c++)
-    filter_tile_to<T, PT>(A + c * stride + (tm.H - H) * tm.BZ + (tm.HZ - H), tm.BZ, B1, Zb, ft, f.fE[c], g, i0, k0);
+    filter_tile_to<T, PT>(A + c * stride + (HZ - H), BZ, B1, Zb, ft, f.fE[c], g, i0, k0);
 }
 
 // Ampere + PML-E, with the current (plus the ion column current) filtered in the tile first
@@ -596,15 +641,38 @@ __device__ __forceinline__ void ampere_tile(const GridP& g, const FieldPtrs<T>& 
   }
   __syncthreads();
   if (leader) stage<T>(tile0, pmapJ, 0, gk0, gi0, &bar[0], tm);
-  const T dt = T(g.dt);
+  const T dt = grid_dt<T>(g);
   const T c2 = T(kC * kC);
   const T ie0 = T(1.0 / kEps0);
-  const T idx = T(1.0 / g.dx), idz = T(1.0 / g.dz);
+  const T idx = grid_idx<T>(g), idz = grid_idz<T>(g);
   const double c2d = kC * kC;
   const int k = k0 + threadIdx.x;
   for (int c = 0; c < 3; c++) {
     T* A = (c & 1) ? tile1 : tile0;
     if (leader && c + 1 < 3) stage<T>((c & 1) ? tile0 : tile1, pmapJ, c + 1, gk0, gi0, &bar[(c + 1) & 1], tm);
+    int vi0, vi1, vk0, vk1;
+    valid_range(c, g.nx, g.nz, vi0, vi1, vk0, vk1);
+    // E^n and the B^{n+1/2} values of the curl for the thread's rows, loaded before the wait for the
+    // staged current and the filter, so that their latency overlaps both
+    constexpr int NR = FT_X / FT_TY;
+    T e0[NR], ba[NR], bb[NR], bc[NR], bd[NR];
+#pragma unroll
+    for (int r = 0; r < NR; r++) {
+      const int i = i0 + threadIdx.y + r * FT_TY;
+      const long p = (long)i * g.ld + k;
+      const bool v = i <= g.nx && k <= g.nz && i >= vi0 && i <= vi1 && k >= vk0 && k <= vk1;
+      e0[r] = ba[r] = bb[r] = bc[r] = bd[r] = T(0);
+      if (v) {
+        e0[r] = f.E[c][p];
+        if (c == 0) {
+          ba[r] = f.B[1][p]; bb[r] = f.B[1][p - 1];
+        } else if (c == 2) {
+          ba[r] = f.B[1][p]; bb[r] = f.B[1][p - g.ld];
+        } else {
+          ba[r] = f.B[0][p]; bb[r] = f.B[0][p - 1]; bc[r] = f.B[2][p]; bd[r] = f.B[2][p - g.ld];
+        }
+      }
+    }
     if (!block_wait(&bar[c & 1], (c >> 1) & 1)) {
       tile_timeout(ctrl, &bar[0], &bar[1]);
       return;
@@ -630,31 +698,11 @@ __device__ __forceinline__ void ampere_tile(const GridP& g, const FieldPtrs<T>& 
       }
       __syncthreads();
     }
-    int vi0, vi1, vk0, vk1;
-    valid_range(c, g.nx, g.nz, vi0, vi1, vk0, vk1);
-    // E^n and the B^{n+1/2} values of the curl for the thread's rows, loaded before the filter so that
-    // their latency overlaps it
-    constexpr int NR = FT_X / FT_TY;
-    T e0[NR], ba[NR], bb[NR], bc[NR], bd[NR];
-#pragma unroll
-    for (int r = 0; r < NR; r++) {
-      const int i = i0 + threadIdx.y + r * FT_TY;
-      const long p = (long)i * g.ld + k;
-      const bool v = i <= g.nx && k <= g.nz && i >= vi0 && i <= vi1 && k >= vk0 && k <= vk1;
-      e0[r] = ba[r] = bb[r] = bc[r] = bd[r] = T(0);
-      if (v) {
-        e0[r] = f.E[c][p];
-        if (c == 0) {
-          ba[r] = f.B[1][p]; bb[r] = f.B[1][p - 1];
-        } else if (c == 2) {
-          ba[r] = f.B[1][p]; bb[r] = f.B[1][p - g.ld];
-        } else {
-          ba[r] = f.B[0][p]; bb[r] = f.B[0][p - 1]; bc[r] = f.B[2][p]; bd[r] = f.B[2][p - g.ld];
-        }
-      }
-    }
     if (FILT) filter_tile<T, PT>(A + (tm.H - H) * tm.BZ + (tm.HZ - H), tm.BZ, B1, Zb, ft);
-    const bool interior = i0 >= pt.iin0 && i0 + FT_X - 1 <= pt.iin1 && k0 >= pt.kin0 && k0 + FT_Z - 1 <= pt.kin1;
+    // block-uniform: the tiles clear of the PML run the rows without its branches (no FP64 table reads)
+    const bool clear = i0 >= pt.iin0 && i0 + FT_X - 1 <= pt.iin1 && k0 >= pt.kin0 && k0 + FT_Z - 1 <= pt.kin1;
+    auto rows = [&](auto pml) {
+      constexpr bool interior = !decltype(pml)::value;
 #pragma unroll
     for (int r = 0; r < NR; r++) {
       const int ti = threadIdx.y + r * FT_TY;
@@ -693,6 +741,9 @@ __device__ __forceinline__ void ampere_tile(const GridP& g, const FieldPtrs<T>& 
       }
       f.Eo[c][p] = en;
     }
+    };
+    if (clear) rows(std::false_type{});
+    else rows(std::true_type{});
     __syncthreads();
   }
 }
