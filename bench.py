@@ -52,6 +52,8 @@ TRAFFIC_BYTES_PER_PARTICLE = {
     (16, 16, 32): 49.18, (16, 16, 64): 49.21, (16, 32, 8): 49.24, (16, 32, 16): 49.31, (16, 32, 32): 49.25, (16, 32, 64): 49.23,
     (32, 8, 8): 49.15, (32, 8, 16): 49.23, (32, 8, 32): 49.16, (32, 8, 64): 49.21, (32, 16, 8): 49.2, (32, 16, 16): 49.31,
     (32, 16, 32): 49.34, (32, 16, 64): 49.19, (32, 32, 8): 48.94, (32, 32, 16): 48.88, (32, 32, 32): 48.86, (32, 32, 64): 48.81,
+    (8, 8, 128): 49.62, (8, 16, 128): 49.49, (8, 32, 128): 49.26, (16, 8, 128): 49.45, (16, 16, 128): 49.22,
+    (16, 32, 128): 49.23, (32, 8, 128): 49.22, (32, 16, 128): 49.22, (32, 32, 128): 48.91,
 }
 # the push's instruction and FP32 arithmetic counts per particle (mixed, cubic, Yee-located gather; ncu
 # smsp__inst_executed.sum and smsp__sass_thread_inst_executed_op_{fadd,fmul,ffma}_pred_on.sum of three pushes
@@ -649,9 +651,10 @@ def run_stage3d(args):  # noqa: C901
 
 
 def run_layout_sweep(args):
-    """every particle layout the autotuner can return (tiles {8, 16, 32}^2, sort cadences 8, 16, 32, 64) on
-    the given box, a few steps each: run under ncu with the DRAM byte counters to tabulate the push kernel's
-    traffic per particle for each layout (prints one line per layout with its electron count)"""
+    """every particle layout the autotuner can return (tiles {8, 16, 32}^2, sort cadences 8, 16, 32, 64, 128;
+    --sweep-cadences restricts the cadences) on the given box, a few steps each: run under ncu with the DRAM
+    byte counters to tabulate the push kernel's traffic per particle for each layout (prints one line per
+    layout with its electron count)"""
     import torch
     from paper_1009_2727_gb300 import workloads as W
     from paper_1009_2727_gb300.pic import Simulation
@@ -661,7 +664,7 @@ def run_layout_sweep(args):
         w = W.shrink(w, w["nx"], args.nz)
     for tx in (8, 16, 32):
         for tz in (8, 16, 32):
-            for se in (8, 16, 32, 64):
+            for se in (int(v) for v in args.sweep_cadences.split(",")):
                 sim = Simulation(w, precision=args.precision, tile=(tx, tz), sort_every=se)
                 sim.step(args.steps)
                 sim.sync()
@@ -779,6 +782,8 @@ def main():
     ap.add_argument("--order", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--sweep-cadences", default="8,16,32,64,128",
+                    help="sort cadences of --layout-sweep (comma-separated)")
     ap.add_argument("--nz", type=int, default=0, help="smaller box for profiling captures (default: the full 4096)")
     ap.add_argument("--sort-every", type=int, default=0, help="steps between particle sorts (0: the library default)")
     ap.add_argument("--ensemble", type=int, default=0,

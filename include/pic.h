@@ -321,7 +321,7 @@ int pic_kernel_timing(pic_ctx* ctx, int enable, int which, double* ms_total, int
 
 /* ---- Autotuner of the particle layout (no counterpart in the paper) ----
  * Picks the particle tile (tile_x, tile_z) from {8, 16, 32}^2 at a cadence of 32,
- * then the sort cadence from {8, 16, 32, 64} for that tile, by timing `steps`
+ * then the sort cadence from {8, 16, 32, 64, 128} for that tile, by timing `steps`
  * steps (after 4 warm-up steps; a cadence trial runs at least two sort periods;
  * each tile is timed twice and the faster time is recorded, after one untimed
  * trial that brings the GPU to its clocks) of contexts built from cfg, plasma and

@@ -14,7 +14,7 @@ namespace {
 
 // trial sets: tiles of 8/16/32 cells on each axis, then cadences around the default
 constexpr int kTiles[3] = {8, 16, 32};
-constexpr int kCadences[4] = {8, 16, 32, 64};
+constexpr int kCadences[5] = {8, 16, 32, 64, 128};
 
 // nx, nz, ppc_x, ppc_z, order, precision, gamma*1e6, warm-up steps, timed steps
 typedef std::tuple<int, int, int, int, int, int, long long, int, int> Key;
