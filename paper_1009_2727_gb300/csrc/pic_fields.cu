@@ -519,7 +519,7 @@ __global__ void __launch_bounds__(FT_Z* FT_TY) k_filter_fields(GridP g, FieldPtr
 // staged E^{n-1}; B, B_avg and E-bar are updated as in k_faraday, then F(E^n) is written for the gather
 // (k_filter_fields then filters B_avg only).
 template <class T, bool FRIED, bool CK, int PT>
-__global__ void __launch_bounds__(FT_Z* FT_TY, 3) k_faraday_fused(GridP g, FieldPtrs<T> f, PmlTabs pt, FarK<T> q,
+__global__ void __launch_bounds__(FT_Z* FT_TY, 4) k_faraday_fused(GridP g, FieldPtrs<T> f, PmlTabs pt, FarK<T> q,
                                                                FilterTaps<T> ft,
                                                                const __grid_constant__ CUtensorMap mapE,
                                                                const __grid_constant__ CUtensorMap mapEo,
@@ -534,7 +534,8 @@ __global__ void __launch_bounds__(FT_Z* FT_TY, 3) k_faraday_fused(GridP g, Field
   const int rstride = ring_stride<T>();
   T* A = reinterpret_cast<T*>(align128(smraw));   // E^n, three boxes with the filter halo
   T* R = A + 3 * stride;                          // E^{n-1} then E-bar, three components each (FRIED)
-  T* B1 = R + (FRIED ? 6 * rstride : 0);
+  // the filter's scratch reuses R once the B update has read E_eff (four CTAs fit on an SM)
+  T* B1 = R;
   T* Zb = B1 + FT_X * filter_wzp(H);
   __shared__ __align__(8) uint64_t bar[1];
   const int i0 = blockIdx.y * FT_X, k0 = blockIdx.x * FT_Z;
@@ -613,7 +614,9 @@ __global__ void __launch_bounds__(FT_Z* FT_TY, 3) k_faraday_fused(GridP g, Field
     esz = BZ;
   }
   faraday_update<T, CK>(g, f, pt, q, Eep, esz, i0, k0, bold);
-  // the gather copies of E^n: the filter of the staged boxes
+  // the gather copies of E^n: the filter of the staged boxes (its scratch overwrites E_eff: every thread's
+  // B update has read it first)
+  __syncthreads();
   for (int c = 0; c < 3; c++)
     filter_tile_to<T, PT>(A + c * stride + (HZ - H), BZ, B1, Zb, ft, f.fE[c], g, i0, k0);
 }
@@ -1037,8 +1040,10 @@ void launch_filter_fields(const GridP& g, const FieldPtrs<T>& f, const FilterSpe
 // shared memory of the fused Faraday kernel: four staged boxes, E_eff, the filter's scratch
 template <class T>
 static size_t fused_smem(const TileMaps& tm, int H, bool fried) {
-  return (3 * (size_t)tile_stride<T>(tm) + (fried ? 6 * (size_t)ring_stride<T>() : 0) +
-          (size_t)FT_X * filter_wzp(H) + (size_t)FT_X * FT_Z) * sizeof(T) + 128;
+  // three E^n boxes, then the E^{n-1}/E-bar boxes, whose space the filter's scratch reuses
+  const size_t scratch = (size_t)FT_X * filter_wzp(H) + (size_t)FT_X * FT_Z;
+  const size_t rest = fried ? std::max(6 * (size_t)ring_stride<T>(), scratch) : scratch;
+  return (3 * (size_t)tile_stride<T>(tm) + rest) * sizeof(T) + 128;
 }
 
 template <class T, bool FRIED, bool CK, int PT>

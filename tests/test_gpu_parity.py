@@ -108,6 +108,15 @@ def test_parity_2d_small_fp64(Sim, orc, order):
     check_particles(g, o, TOL64)
 
 
+def test_grid_smaller_than_one_field_tile_fp64(Sim, orc):
+    """a grid below one 16 x 64-node field tile along z and of two along x (every field kernel runs on ragged
+    tiles only; TMA boxes reach past the grid on every side), with plasma and laser, against the oracle"""
+    w = W.shrink(W.parity_2d(), 32, 56)
+    g, o = run_pair(Sim, orc, w, 40)
+    check_fields(g, o, TOL64)
+    check_particles(g, o, TOL64)
+
+
 def test_parity_2d_config_fp64_100_steps(Sim, orc):
     """the plain-FP64 parity workload (256 x 64 cells, 4 ppc) over 100 steps"""
     w = W.parity_2d()
