@@ -806,6 +806,16 @@ constexpr int WX = TX + 2 * WM + 1, WY = TY + 2 * WM + 1, WZ = TZ + 2 * WM + 1;
 constexpr int WN = WX * WY * WZ;
 // window element stride along axis a
 __host__ __device__ constexpr int wstride(int a) { return a == 0 ? WY * WZ : a == 1 ? WZ : 1; }
+// The gathered fields need less: a cubic stencil of a particle within half a cell of its tile reaches
+// nodes -2 .. T+2 (integer and half positions alike), so their window starts WGM = 2 before the tile
+// and is T + 5 nodes long on each axis (the current window above keeps WM = 3 for the move). The
+// smaller field window is what lets three CTAs share an SM.
+constexpr int WGM = 2;
+constexpr int WGX = TX + 2 * WGM + 1, WGY = TY + 2 * WGM + 1, WGZ = TZ + 2 * WGM + 1;
+constexpr int WGN = WGX * WGY * WGZ;
+// shared memory of the 3D push: the six gathered fields on the field window, the current on its window
+template <class T>
+constexpr int push3_smem() { return (int)((6 * WGN + 3 * WN) * sizeof(T)); }
 
 struct Tiles3 {
   int nt[3];
@@ -899,11 +909,11 @@ __global__ void k3_tile_scatter(Parts3<T> src, Parts3<T> dst, Tiles3 t, int n_ol
 }
 
 template <class T, int ORD, bool MC>
-__global__ void __launch_bounds__(256) k3_push_tiles(G3 g, Fld3<T> f, Parts3<T> p, Tiles3 t, Ctrl3* ctrl, T kq,
+__global__ void __launch_bounds__(256, 3) k3_push_tiles(G3 g, Fld3<T> f, Parts3<T> p, Tiles3 t, Ctrl3* ctrl, T kq,
                                                      Cq3<T> cq) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  T* sF = reinterpret_cast<T*>(smraw);        // 6 x WN gather fields
-  T* sJ = sF + 6 * WN;                        // 3 x WN current
+  T* sF = reinterpret_cast<T*>(smraw);        // 6 x WGN gather fields
+  T* sJ = sF + 6 * WGN;                       // 3 x WN current
   const int tile = blockIdx.x;
   const int p0 = t.start[tile], p1 = t.start[tile + 1];
   if (p1 <= p0) return;
@@ -916,28 +926,32 @@ __global__ void __launch_bounds__(256) k3_push_tiles(G3 g, Fld3<T> f, Parts3<T> 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const bool clear = c0[0] - WM >= 0 && c0[1] - WM >= 0 && c0[2] - WM >= 0 && c0[0] - WM + WX - 1 <= g.n[0] &&
                      c0[1] - WM + WY - 1 <= g.n[1] && c0[2] - WM + WZ - 1 <= g.n[2];
+  const bool clear_g = c0[0] - WGM >= 0 && c0[1] - WGM >= 0 && c0[2] - WGM >= 0 &&
+                       c0[0] - WGM + WGX - 1 <= g.n[0] && c0[1] - WGM + WGY - 1 <= g.n[1] &&
+                       c0[2] - WGM + WGZ - 1 <= g.n[2];
   const long line_stride = (long)(g.n[1] + 1) * g.ldz;   // nid step along x
   // each warp takes SU consecutive lines at a time and issues their loads together (one round trip to
   // L2 or HBM per SU lines instead of one per line)
-  constexpr int NL = 6 * WX * WY, SU = 8;
+  static_assert(WGZ <= 32, "one lane per z node of a field-window line");
+  constexpr int NL = 6 * WGX * WGY, SU = 8;
   for (int l0 = warp * SU; l0 < NL; l0 += nwarps * SU) {
     T v[SU];
 #pragma unroll
     for (int u = 0; u < SU; u++) {
       const int line = l0 + u;
       v[u] = T(0);
-      if (line < NL && lane < WZ) {
-        const int c = line / (WX * WY), ab = line - c * (WX * WY);
-        const int a = ab / WY, b = ab - a * WY;
+      if (line < NL && lane < WGZ) {
+        const int c = line / (WGX * WGY), ab = line - c * (WGX * WGY);
+        const int a = ab / WGY, b = ab - a * WGY;
         const T* F =
             c == 0 ? f.fE[0] : c == 1 ? f.fE[1] : c == 2 ? f.fE[2] : c == 3 ? f.fB[0] : c == 4 ? f.fB[1] : f.fB[2];
-        const int i = c0[0] - WM + a, jj = c0[1] - WM + b, k = c0[2] - WM + lane;
-        v[u] = clear ? F[(long)i * line_stride + (long)jj * g.ldz + k] : rd3(g, F, i, jj, k);
+        const int i = c0[0] - WGM + a, jj = c0[1] - WGM + b, k = c0[2] - WGM + lane;
+        v[u] = clear_g ? F[(long)i * line_stride + (long)jj * g.ldz + k] : rd3(g, F, i, jj, k);
       }
     }
 #pragma unroll
     for (int u = 0; u < SU; u++)
-      if (l0 + u < NL && lane < WZ) sF[(l0 + u) * WZ + lane] = v[u];
+      if (l0 + u < NL && lane < WGZ) sF[(l0 + u) * WGZ + lane] = v[u];
   }
   for (int e = threadIdx.x; e < 3 * WN; e += blockDim.x) sJ[e] = T(0);
   __syncthreads();
@@ -978,7 +992,7 @@ __global__ void __launch_bounds__(256) k3_push_tiles(G3 g, Fld3<T> f, Parts3<T> 
       atomicOr(&ctrl->status, (int)ST_OUTSIDE);
       continue;
     }
-    // gather from the staged window (window index = local cell + WM)
+    // gather from the staged window (field-window index = local cell + WGM)
     T wg[3][2][NS];
     int bl[3][2];
 #pragma unroll
@@ -988,7 +1002,7 @@ __global__ void __launch_bounds__(256) k3_push_tiles(G3 g, Fld3<T> f, Parts3<T> 
         const T Xs = X[a] - T(0.5) * T(h);
         const T fl = floor(Xs);
         shape_w<T, ORD>(Xs - fl, wg[a][h]);
-        bl[a][h] = (int)fl - SH + WM;
+        bl[a][h] = (int)fl - SH + WGM;
       }
     T EB[6];
 #pragma unroll
@@ -997,14 +1011,14 @@ __global__ void __launch_bounds__(256) k3_push_tiles(G3 g, Fld3<T> f, Parts3<T> 
       // tensor-product sum taken axis by axis: z within each (x, y) row, then y, then x
       const int hx = MC ? 0 : c < 3 ? (c == 0) : (c != 3), hy = MC ? 0 : c < 3 ? (c == 1) : (c != 4),
                 hz = MC ? 0 : c < 3 ? (c == 2) : (c != 5);
-      const T* F = sF + c * WN + (bl[0][hx] * WY + bl[1][hy]) * WZ + bl[2][hz];
+      const T* F = sF + c * WGN + (bl[0][hx] * WGY + bl[1][hy]) * WGZ + bl[2][hz];
       T acc = T(0);
 #pragma unroll
       for (int l0 = 0; l0 < NS; l0++) {
         T accy = T(0);
 #pragma unroll
         for (int l1 = 0; l1 < NS; l1++) {
-          const T* row = F + (l0 * WY + l1) * WZ;
+          const T* row = F + (l0 * WGY + l1) * WGZ;
           T accz = T(0);
 #pragma unroll
           for (int l2 = 0; l2 < NS; l2++) accz += row[l2] * wg[2][hz][l2];
@@ -2091,7 +2105,7 @@ struct Sim3 : Sim3Api {
     tl.cnt = dal<int>(ntiles + 1);
     tl.start = dal<int>(ntiles + 1);
     if (!tl.cnt || !tl.start) return fail(PIC_ENOMEM, "allocation failed");
-    const int smem = (int)(9 * WN * sizeof(T));
+    const int smem = push3_smem<T>();
     cudaFuncSetAttribute(k3_push_tiles<T, 3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     cudaFuncSetAttribute(k3_push_tiles<T, 1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     cudaFuncSetAttribute(k3_push_tiles<T, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -2443,7 +2457,7 @@ struct Sim3 : Sim3Api {
     const T kq = T(-kQe * g.dt / (2.0 * kMe));
     if (loaded && count_ub > 0) {
       sort_tiles();
-      const int smem = (int)(9 * WN * sizeof(T));
+      const int smem = push3_smem<T>();
       tbeg(0);
       if (cfg.shape_order == 3 && !nodal)
         k3_push_tiles<T, 3, false><<<ntiles, 256, smem, s>>>(g, f, P2[cur], tl, ctrl, kq, cq_e);
