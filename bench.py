@@ -61,9 +61,9 @@ TRAFFIC_BYTES_PER_PARTICLE = {
 # counted as FADD + FMUL + 2 FFMA (the packed two-lane FMAs of the gather are not in these counters)
 PUSH_WARP_INST_PER_PARTICLE = 20.7
 PUSH_FLOPS_PER_PARTICLE = 174.0
-# 3D: ncu dram bytes of k3_push_tiles on the 256 x 128 x 128 box (192.8 MB for 2,356,608 electrons), scaled
+# 3D: ncu dram bytes of k3_push_tiles on the 256 x 128 x 128 box (189.5 MB for 2,356,608 electrons), scaled
 # to the full box by its particle count
-TRAFFIC_BYTES_PER_PARTICLE_3D = {("mixed", 3): 81.8}
+TRAFFIC_BYTES_PER_PARTICLE_3D = {("mixed", 3): 80.4}
 
 
 def measured_peaks() -> dict:
@@ -934,9 +934,9 @@ def main():
             "unit": "GB/s", "frac": achieved / peak, "traffic": tpp * n_avg if tpp else None,
             "traffic_source": ("ncu dram bytes of k3_push_tiles, 256 x 128 x 128 box, scaled by particles" if three
                                else "ncu dram bytes of k_push, 2048 x 256 box, this layout, scaled by particles") if tpp else None,
-            "note": ("3D push on sorted 4x4x16-cell tiles with shared-memory windows: issue- and latency-bound at a "
-                     "quarter occupancy (ncu: 38% issue slots, 25% warps active, 5.2k thread-instructions per "
-                     "particle, 3% DRAM)" if three else
+            "note": ("3D push on sorted 4x4x16-cell tiles with shared-memory windows: issue- and latency-bound at "
+                     "three CTAs per SM (ncu: 44% issue slots, 37% warps active, 4.5k thread-instructions per "
+                     "particle, 4% DRAM)" if three else
                      "at cubic order the push is bound by instruction issue and the L1/shared pipe "
                      "(ncu: 64-65% issue slots, 69% L1/TEX, 17% DRAM), not by HBM; see issue and alu"),
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback",
