@@ -360,12 +360,13 @@ int pic_autotune_window(const pic_config* cfg, const pic_plasma* plasma, const p
  * n runs of uneven size (each its own pic_config, pic_plasma and pic_laser;
  * lasers may be NULL, and a laser with lambda0 <= 0 means none) advanced together.
  * Every run is an ordinary context created and owned by the ensemble.
- *  - Batched mode (2D runs with plasma, the Yee-located gather, no test beam, no
- *    moving window, one precision, shape order, solver family, damping, filter
- *    and particle layout; at most 512 runs): all runs share one non-blocking
- *    stream and an ensemble step is one launch per kernel class over all runs
- *    (Faraday, gather filter, push, its global pass, antenna, ion current,
- *    Ampere, inflow, counts; the runs' sorts every sort_every steps), the per-run
+ *  - Batched mode (2D runs with plasma, the Yee-located gather, no lab samples,
+ *    no moving window, one precision, shape order, solver family, damping, filter
+ *    and particle layout; at most 512 runs; a test beam rides along): all runs
+ *    share one non-blocking stream and an ensemble step is one launch per kernel
+ *    class over all runs (Faraday, gather filter, push, its global pass, test
+ *    beams, antenna, ion current, Ampere, inflow, counts; the runs' sorts every
+ *    sort_every steps), the per-run
  *    arguments of the step in one block of device memory filled from the same
  *    host decisions as pic_step. From the third step on, each step replays a
  *    CUDA graph of those launches (pic_ensemble_use_graphs(ens, 0) launches them
