@@ -721,6 +721,7 @@ struct Sim : SimBase {
     a.tm = tmaps;
     a.mapE = tmaps.Ebase[0] == (const void*)f.E[0] ? 0 : 1;
     a.mapJ = tmaps.Jbase[0] == (const void*)f.J[0] ? 0 : 1;
+    a.mapEb = tmaps.Ebbase[0] == (const void*)f.Eb[0] ? 0 : 1;
     field_tiles(g, a.tiles_k, a.tiles_i);
     // ion rows live during this step: those inside the particle domain at t^n
     long long mlo = std::max(row_first, (long long)std::ceil((zlo_prev + h.beta * kC * tn) / ip.h - 0.5));
@@ -1086,6 +1087,7 @@ struct BatchImpl : Batch {
   bool friedman = false, ck = false, filt_gather = false, filt_J = false, any_ion = false;
   int beam_blocks = 0;   // blocks of 128 particles of the largest test beam (0: no run has one)
   size_t filt_smem = 0, amp_smem = 0;
+  size_t fused_smem = 0;   // > 0: the fused Faraday + E filter kernel serves every run
   int64_t nl = 0, nstep = 0;
 
   ~BatchImpl() override {
@@ -1126,6 +1128,7 @@ struct BatchImpl : Batch {
     tile_z = m0->sb.tz;
     push_grid = m0->push_grid;
     filt_smem = tile_smem_bytes<T>(m0->tmaps, filt_gather ? ft0.H : 0);
+    fused_smem = filt_gather ? faraday_fused_smem<T>(m0->tmaps, ft0.H, pt_taps, friedman) : 0;
     amp_smem = tile_smem_bytes<T>(m0->tmaps, filt_J ? ft0.H : 0);
     std::vector<int> tile_off(n + 1), ion_off(n + 1), inj_off(n + 1), ant_off(n + 1);
     for (int r = 0; r < n; r++) {
@@ -1138,6 +1141,7 @@ struct BatchImpl : Batch {
         *why = "runs differ in solver family, damping, filter or particle tile";
         return false;
       }
+      if (fused_smem > 0 && faraday_fused_smem<T>(m->tmaps, ft.H, pt_taps, friedman) == 0) fused_smem = 0;
       int tk, ti;
       field_tiles(m->g, tk, ti);
       tile_off[r + 1] = tile_off[r] + tk * ti;
@@ -1179,7 +1183,7 @@ struct BatchImpl : Batch {
 
   void enqueue(int q) {
     cudaMemcpyAsync(dA[q], hA[q], sizeof(StepArgs<T>) * n, cudaMemcpyHostToDevice, s);
-    launch_faraday_filter_batch<T>(dA[q], bg, friedman, ck, pt_taps, filt_gather, filt_smem, s);
+    launch_faraday_filter_batch<T>(dA[q], bg, friedman, ck, pt_taps, filt_gather, filt_smem, fused_smem, s);
     launch_push_batch<T>(dA[q], bg, order, push_grid, smem_nodes, tile_z, s);
     launch_beam_push_batch<T>(dA[q], n, beam_blocks, s);
     launch_antenna_ion_batch<T>(dA[q], bg, any_ion, s);

@@ -417,7 +417,7 @@ int launch_rho_noalloc(const GridP& g, Particles<T> p, const Ctrl* ctrl, int cap
 template <class T>
 struct StepArgs {
   TileMaps tm;                 // TMA descriptors (first: aligned as CUtensorMap requires)
-  int mapE, mapJ;              // which E / J descriptor is current
+  int mapE, mapJ, mapEb;       // which E / J / E-bar descriptor is current
   GridP g;
   FieldPtrs<T> f;
   PmlTabs pt;
@@ -482,9 +482,14 @@ void field_tiles(const GridP& g, int& tiles_k, int& tiles_i);
 template <class T>
 FarK<T> faraday_coefs(double a2, double b2, double theta);
 // Faraday (+ Friedman, PML) and the gather-field filter over every run's tiles
+// fused_smem > 0: Faraday fused with the E filter (every run's descriptors allow it), then the filter of
+// B_avg only
 template <class T>
 void launch_faraday_filter_batch(const StepArgs<T>* a, const BatchGrid& bg, bool friedman, bool ck, int pt_taps,
-                                 bool filt_gather, size_t filt_smem, cudaStream_t s);
+                                 bool filt_gather, size_t filt_smem, size_t fused_smem, cudaStream_t s);
+// shared memory of the fused Faraday kernel for these tile maps and filter halo, 0 when it does not apply
+template <class T>
+size_t faraday_fused_smem(const TileMaps& tm, int H, int pt_taps, bool friedman);
 // the push's window kernel over every run's chunks (one queue), then its global-memory pass
 template <class T>
 void launch_push_batch(const StepArgs<T>* a, const BatchGrid& bg, int order, int grid_blocks, int smem_nodes,

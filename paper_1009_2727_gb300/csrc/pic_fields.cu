@@ -519,12 +519,10 @@ __global__ void __launch_bounds__(FT_Z* FT_TY) k_filter_fields(GridP g, FieldPtr
 // staged E^{n-1}; B, B_avg and E-bar are updated as in k_faraday, then F(E^n) is written for the gather
 // (k_filter_fields then filters B_avg only).
 template <class T, bool FRIED, bool CK, int PT>
-__global__ void __launch_bounds__(FT_Z* FT_TY, 4) k_faraday_fused(GridP g, FieldPtrs<T> f, PmlTabs pt, FarK<T> q,
-                                                               FilterTaps<T> ft,
-                                                               const __grid_constant__ CUtensorMap mapE,
-                                                               const __grid_constant__ CUtensorMap mapEo,
-                                                               const __grid_constant__ CUtensorMap mapEb,
-                                                               TileMaps tm, Ctrl* ctrl) {
+__device__ __forceinline__ void faraday_fused_tile(const GridP& g, const FieldPtrs<T>& f, const PmlTabs& pt,
+                                                   const FarK<T>& q, const FilterTaps<T>& ft,
+                                                   const CUtensorMap* mapE, const CUtensorMap* mapEo,
+                                                   const CUtensorMap* mapEb, Ctrl* ctrl, int tile_k, int tile_i) {
   constexpr int SX = FT_X + 2, SZ = FT_Z + 2, RZ = FT_Z + 8;
   // the staged boxes' geometry as constants: a stride-1 filter of PT passes has halo H = PT (the host
   // checks that the tile maps were built for it), the boxes are FT_X + 2 H rows of FT_Z + 2 HZ
@@ -538,7 +536,7 @@ __global__ void __launch_bounds__(FT_Z* FT_TY, 4) k_faraday_fused(GridP g, Field
   T* B1 = R;
   T* Zb = B1 + FT_X * filter_wzp(H);
   __shared__ __align__(8) uint64_t bar[1];
-  const int i0 = blockIdx.y * FT_X, k0 = blockIdx.x * FT_Z;
+  const int i0 = tile_i * FT_X, k0 = tile_k * FT_Z;
   const int gi0 = i0 - H, gk0 = k0 - HZ;
   const bool leader = threadIdx.x == 0 && threadIdx.y == 0;
   if (leader) {
@@ -552,11 +550,11 @@ __global__ void __launch_bounds__(FT_Z* FT_TY, 4) k_faraday_fused(GridP g, Field
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&bar[0])),
                  "r"(3 * box + (FRIED ? 6 * rbox : 0u))
                  : "memory");
-    for (int c = 0; c < 3; c++) tma_copy_box(A + c * stride, &mapE, gk0, gi0, c, &bar[0]);
+    for (int c = 0; c < 3; c++) tma_copy_box(A + c * stride, mapE, gk0, gi0, c, &bar[0]);
     if (FRIED)
       for (int c = 0; c < 3; c++) {
-        tma_copy_box(R + c * rstride, &mapEo, k0 - 4, i0 - 1, c, &bar[0]);
-        tma_copy_box(R + (3 + c) * rstride, &mapEb, k0 - 4, i0 - 1, c, &bar[0]);
+        tma_copy_box(R + c * rstride, mapEo, k0 - 4, i0 - 1, c, &bar[0]);
+        tma_copy_box(R + (3 + c) * rstride, mapEb, k0 - 4, i0 - 1, c, &bar[0]);
       }
   }
   // the tile's B^{n-1/2} in flight while the copies land
@@ -619,6 +617,16 @@ __global__ void __launch_bounds__(FT_Z* FT_TY, 4) k_faraday_fused(GridP g, Field
   __syncthreads();
   for (int c = 0; c < 3; c++)
     filter_tile_to<T, PT>(A + c * stride + (HZ - H), BZ, B1, Zb, ft, f.fE[c], g, i0, k0);
+}
+
+template <class T, bool FRIED, bool CK, int PT>
+__global__ void __launch_bounds__(FT_Z* FT_TY, 4) k_faraday_fused(GridP g, FieldPtrs<T> f, PmlTabs pt, FarK<T> q,
+                                                               FilterTaps<T> ft,
+                                                               const __grid_constant__ CUtensorMap mapE,
+                                                               const __grid_constant__ CUtensorMap mapEo,
+                                                               const __grid_constant__ CUtensorMap mapEb,
+                                                               Ctrl* ctrl) {
+  faraday_fused_tile<T, FRIED, CK, PT>(g, f, pt, q, ft, &mapE, &mapEo, &mapEb, ctrl, blockIdx.x, blockIdx.y);
 }
 
 // Ampere + PML-E, with the current (plus the ion column current) filtered in the tile first
@@ -775,9 +783,30 @@ __global__ void __launch_bounds__(FT_Z* FT_TY) k_faraday_batch(const StepArgs<T>
   faraday_tile<T, FRIED, CK>(A.g, A.f, A.pt, A.far, lb % A.tiles_k, lb / A.tiles_k);
 }
 
+// the fused Faraday + E filter over every run's tiles (the run's descriptors in device memory)
+template <class T, bool FRIED, bool CK, int PT>
+__global__ void __launch_bounds__(FT_Z* FT_TY, 4) k_faraday_fused_batch(const StepArgs<T>* a, const int* off,
+                                                                     int nruns) {
+  __shared__ int s_r;
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    s_r = batch_run(off, nruns, blockIdx.x);
+    const StepArgs<T>& A0 = a[s_r];
+    tensormap_acquire(&A0.tm.E[A0.mapE]);
+    if (FRIED) {
+      tensormap_acquire(&A0.tm.Er[1 - A0.mapE]);
+      tensormap_acquire(&A0.tm.Eb[A0.mapEb]);
+    }
+  }
+  __syncthreads();
+  const StepArgs<T>& A = a[s_r];
+  const int lb = blockIdx.x - off[s_r];
+  faraday_fused_tile<T, FRIED, CK, PT>(A.g, A.f, A.pt, A.far, A.ft, &A.tm.E[A.mapE], &A.tm.Er[1 - A.mapE],
+                                       &A.tm.Eb[A.mapEb], A.ctrl, lb % A.tiles_k, lb / A.tiles_k);
+}
+
 template <class T, int PT>
 __global__ void __launch_bounds__(FT_Z* FT_TY) k_filter_fields_batch(const StepArgs<T>* a, const int* off,
-                                                                     int nruns) {
+                                                                     int nruns, int c_first) {
   __shared__ int s_r;
   if (threadIdx.x == 0 && threadIdx.y == 0) {
     s_r = batch_run(off, nruns, blockIdx.x);
@@ -788,7 +817,7 @@ __global__ void __launch_bounds__(FT_Z* FT_TY) k_filter_fields_batch(const StepA
   const StepArgs<T>& A = a[s_r];
   const int lb = blockIdx.x - off[s_r];
   filter_fields_tile<T, PT>(A.g, A.f, A.ft, &A.tm.E[A.mapE], &A.tm.Bavg, A.tm, A.ctrl, lb % A.tiles_k,
-                            lb / A.tiles_k);
+                            lb / A.tiles_k, c_first);
 }
 
 template <class T, bool FILT, int PT>
@@ -809,8 +838,31 @@ __global__ void __launch_bounds__(FT_Z* FT_TY, sizeof(T) == 4 ? 4 : 2) k_ampere_
 
 template <class T>
 void launch_faraday_filter_batch(const StepArgs<T>* a, const BatchGrid& bg, bool friedman, bool ck, int pt_taps,
-                                 bool filt_gather, size_t filt_smem, cudaStream_t s) {
+                                 bool filt_gather, size_t filt_smem, size_t fused_smem, cudaStream_t s) {
   dim3 blk(FT_Z, FT_TY);
+  if (fused_smem > 0 && filt_gather && (pt_taps == 1 || pt_taps == 5)) {
+#define FUSEDB(FR, C, PTV)                                                                                    \
+  cudaFuncSetAttribute(k_faraday_fused_batch<T, FR, C, PTV>, cudaFuncAttributeMaxDynamicSharedMemorySize,       \
+                       (int)fused_smem);                                                                      \
+  k_faraday_fused_batch<T, FR, C, PTV><<<bg.tiles, blk, fused_smem, s>>>(a, bg.tile_off, bg.nruns);
+    if (pt_taps == 5) {
+      if (friedman) { if (ck) { FUSEDB(true, true, 5) } else { FUSEDB(true, false, 5) } }
+      else { if (ck) { FUSEDB(false, true, 5) } else { FUSEDB(false, false, 5) } }
+    } else {
+      if (friedman) { if (ck) { FUSEDB(true, true, 1) } else { FUSEDB(true, false, 1) } }
+      else { if (ck) { FUSEDB(false, true, 1) } else { FUSEDB(false, false, 1) } }
+    }
+#undef FUSEDB
+    // B_avg's gather copies
+    if (pt_taps == 5) {
+      cudaFuncSetAttribute(k_filter_fields_batch<T, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)filt_smem);
+      k_filter_fields_batch<T, 5><<<bg.tiles, blk, filt_smem, s>>>(a, bg.tile_off, bg.nruns, 3);
+    } else {
+      cudaFuncSetAttribute(k_filter_fields_batch<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)filt_smem);
+      k_filter_fields_batch<T, 1><<<bg.tiles, blk, filt_smem, s>>>(a, bg.tile_off, bg.nruns, 3);
+    }
+    return;
+  }
   if (friedman) {
     if (ck) k_faraday_batch<T, true, true><<<bg.tiles, blk, 0, s>>>(a, bg.tile_off, bg.nruns);
     else k_faraday_batch<T, true, false><<<bg.tiles, blk, 0, s>>>(a, bg.tile_off, bg.nruns);
@@ -821,7 +873,7 @@ void launch_faraday_filter_batch(const StepArgs<T>* a, const BatchGrid& bg, bool
   if (!filt_gather) return;
 #define FBATCH(PTV)                                                                                      \
   cudaFuncSetAttribute(k_filter_fields_batch<T, PTV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)filt_smem); \
-  k_filter_fields_batch<T, PTV><<<bg.tiles, blk, filt_smem, s>>>(a, bg.tile_off, bg.nruns);
+  k_filter_fields_batch<T, PTV><<<bg.tiles, blk, filt_smem, s>>>(a, bg.tile_off, bg.nruns, 0);
   switch (pt_taps) {
     case 1: { FBATCH(1) break; }
     case 2: { FBATCH(2) break; }
@@ -1046,6 +1098,13 @@ static size_t fused_smem(const TileMaps& tm, int H, bool fried) {
   return (3 * (size_t)tile_stride<T>(tm) + rest) * sizeof(T) + 128;
 }
 
+template <class T>
+size_t faraday_fused_smem(const TileMaps& tm, int H, int pt_taps, bool friedman) {
+  if (!tm.ok || (friedman && !tm.r_ok) || H != tm.H || (pt_taps != 1 && pt_taps != 5)) return 0;
+  const size_t sm = fused_smem<T>(tm, H, friedman);
+  return sm <= 227 * 1024 ? sm : 0;
+}
+
 template <class T, bool FRIED, bool CK, int PT>
 static bool run_faraday_fused(dim3 grd, dim3 blk, cudaStream_t s, const GridP& g, const FieldPtrs<T>& f,
                               const PmlTabs& pt, const FarK<T>& q, const FilterTaps<T>& ft, const TileMaps& tm,
@@ -1057,7 +1116,7 @@ static bool run_faraday_fused(dim3 grd, dim3 blk, cudaStream_t s, const GridP& g
   const CUtensorMap& mEo = cur0 ? tm.Er[1] : tm.Er[0];
   const CUtensorMap& mEb = tm.Ebbase[0] == (const void*)f.Eb[0] ? tm.Eb[0] : tm.Eb[1];
   cudaFuncSetAttribute(k_faraday_fused<T, FRIED, CK, PT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_faraday_fused<T, FRIED, CK, PT><<<grd, blk, sm, s>>>(g, f, pt, q, ft, mE, mEo, mEb, tm, ctrl);
+  k_faraday_fused<T, FRIED, CK, PT><<<grd, blk, sm, s>>>(g, f, pt, q, ft, mE, mEo, mEb, ctrl);
   return true;
 }
 
@@ -1143,11 +1202,12 @@ size_t tile_smem_bytes(const TileMaps& tm, int H) { return tile_smem<T>(tm, H); 
   template int filter_taps_class<T>(const FilterTaps<T>&);                                                       \
   template size_t tile_smem_bytes<T>(const TileMaps&, int);                                                      \
   template void launch_faraday_filter_batch<T>(const StepArgs<T>*, const BatchGrid&, bool, bool, int, bool, size_t, \
-                                               cudaStream_t);                                                   \
+                                               size_t, cudaStream_t);                                           \
   template void launch_ampere_batch<T>(const StepArgs<T>*, const BatchGrid&, bool, int, size_t, cudaStream_t);      \
   template bool make_tile_maps<T>(const GridP&, const FieldPtrs<T>&, int, TileMaps&);                            \
   template void launch_filter_fields<T>(const GridP&, const FieldPtrs<T>&, const FilterSpec&, bool, const TileMaps&, \
                                         Ctrl*, cudaStream_t, int);                                               \
+  template size_t faraday_fused_smem<T>(const TileMaps&, int, int, bool);                                          \
   template bool launch_faraday_fused<T>(const GridP&, const FieldPtrs<T>&, const PmlTabs&, double, double, double,  \
                                         bool, const FilterSpec&, bool, const TileMaps&, Ctrl*, cudaStream_t);   \
   template void launch_ampere<T>(const GridP&, const FieldPtrs<T>&, const PmlTabs&, const FilterSpec&, bool,       \
