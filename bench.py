@@ -950,7 +950,7 @@ def main():
     field_avg_ms = field_ms / kf
     field_ach = cells * bpc / (field_avg_ms * 1e-3) / 1e9 if field_avg_ms > 0 else None
     roof["field_kernels"] = {"kernels": "k3_faraday_tile, k3_friedman, k3_filter_*, k3_ampere" if three else
-                             "k_faraday, k_filter_fields, k_ampere", "bound": "hbm", "achieved": field_ach,
+                             "k_faraday_fused (k_faraday where it does not apply), k_filter_fields, k_ampere", "bound": "hbm", "achieved": field_ach,
                              "peak": peak, "unit": "GB/s", "frac": field_ach / peak if field_ach else None,
                              "algorithmic_bytes_per_cell": bpc, "ms_per_step": field_avg_ms,
                              "cell_steps_per_s": cells / (field_avg_ms * 1e-3) if field_avg_ms > 0 else None}
