@@ -276,10 +276,35 @@ __device__ __forceinline__ float2 interp_two_f(const float* __restrict__ F0, int
 // With SMEM the particle must lie in the staged window: when its cell at t^n
 // (or its live lattice ion's cell) is outside the chunk's box, nothing is
 // changed and false is returned, so that the caller takes the global path.
-template <class T, int ORDER, bool SMEM, bool MC = false>
+// Bounding box of the cells a thread's particles occupy, accumulated over its particles of a chunk.
+struct BoxI {
+  int x0 = INT_MAX, x1 = INT_MIN, z0 = INT_MAX, z1 = INT_MIN;
+  __device__ __forceinline__ void add(int x, int z) {
+    x0 = min(x0, x); x1 = max(x1, x); z0 = min(z0, z); z1 = max(z1, z);
+  }
+  __device__ __forceinline__ BoxI unpack() const { return *this; }
+};
+// The same in two registers, (x, z) as unsigned 16-bit halves: mixed-path cells are 16-bit and the
+// window path only adds cells of its own non-negative window
+struct BoxP {
+  uint32_t lo = 0xffffffffu, hi = 0u;
+  __device__ __forceinline__ void add(int x, int z) {
+    const uint32_t v = ((uint32_t)x << 16) | ((uint32_t)z & 0xffffu);
+    lo = __vminu2(lo, v); hi = __vmaxu2(hi, v);
+  }
+  __device__ __forceinline__ BoxI unpack() const {
+    BoxI b;
+    if ((lo >> 16) <= (hi >> 16)) {   // something was added
+      b.x0 = (int)(lo >> 16); b.x1 = (int)(hi >> 16); b.z0 = (int)(lo & 0xffffu); b.z1 = (int)(hi & 0xffffu);
+    }
+    return b;
+  }
+};
+
+template <class T, int ORDER, bool SMEM, bool MC = false, class ACC = BoxI>
 __device__ __forceinline__ bool push_one(const T* __restrict__ Eb, const T* __restrict__ Bb, T* Jb, long cs, int ld,
                                          int ox, int oz, const Particles<T>& p, int pi, const PushConst& pc, const Box& box,
-                                         int& bx0, int& bx1, int& bz0, int& bz1) {
+                                         ACC& acc) {
   constexpr int NG = St<ORDER>::NG, ND = St<ORDER>::ND;
   constexpr bool CP = CellPos<T>::value;
   const T w = p.w[pi];
@@ -294,8 +319,7 @@ __device__ __forceinline__ bool push_one(const T* __restrict__ Eb, const T* __re
       ion_site<ORDER>(id, pc, is);
       if (SMEM && !box.in(is.fx, is.fz0)) return false;
       ion_jz<T, ORDER, SMEM>(Jb, cs, ld, ox, oz, is, pc.kz_f * (-w));
-      bx0 = min(bx0, is.fx); bx1 = max(bx1, is.fx);
-      bz0 = min(bz0, is.fz1); bz1 = max(bz1, is.fz1);
+      acc.add(is.fx, is.fz1);
       return true;
     }
   }
@@ -503,14 +527,12 @@ __device__ __forceinline__ bool push_one(const T* __restrict__ Eb, const T* __re
     // an electron whose ion is still inside leaves a ghost that carries the ion
     p.w[pi] = ion_live ? -w : T(0);
   } else {
-    bx0 = min(bx0, fxn); bx1 = max(bx1, fxn);
-    bz0 = min(bz0, fzn); bz1 = max(bz1, fzn);
+    acc.add(fxn, fzn);
   }
   if constexpr (CP) {
     // the pair's ion (or the ghost's) deposits next step: its cell belongs in the chunk's box too
     if (ion_live) {
-      bx0 = min(bx0, is.fx); bx1 = max(bx1, is.fx);
-      bz0 = min(bz0, is.fz1); bz1 = max(bz1, is.fz1);
+      acc.add(is.fx, is.fz1);
     }
   }
   // Esirkepov deposition on an ND x ND window. No current at all: the x weights
@@ -589,8 +611,7 @@ __device__ __forceinline__ bool particle_cell(const Particles<T>& p, int pi, con
 // flagged instead of being pushed.
 template <class T, int ORDER, bool MC>
 __device__ __noinline__ void push_global_guarded(const T* gE, const T* gB, T* gJ, const GridP& g, const Particles<T>& p,
-                                                 int pi, const PushConst& pc, Ctrl* ctrl, int& bx0, int& bx1,
-                                                 int& bz0, int& bz1) {
+                                                 int pi, const PushConst& pc, Ctrl* ctrl, BoxI& acc) {
   if (p.w[pi] == T(0)) return;
   int fx, fz;
   const bool fin = particle_cell<T>(p, pi, pc, fx, fz);
@@ -602,7 +623,7 @@ __device__ __noinline__ void push_global_guarded(const T* gE, const T* gB, T* gJ
     return;
   }
   const Box none{0, -1, 0, -1};
-  push_one<T, ORDER, false, MC>(gE, gB, gJ, g.cs, g.ld, 0, 0, p, pi, pc, none, bx0, bx1, bz0, bz1);
+  push_one<T, ORDER, false, MC>(gE, gB, gJ, g.cs, g.ld, 0, 0, p, pi, pc, none, acc);
 }
 
 // One chunk of the window kernel: stage the six gather fields of the chunk's box (+ halo) in shared memory,
@@ -635,7 +656,7 @@ __device__ __forceinline__ void push_chunk(const GridP& g, const T* gE, const T*
     }
     const int nn = wxn * lds;
     const bool use_smem = nn <= cap_nodes && wx0 >= 0 && wz0 >= 0 && wx1 <= g.nx && wz1 <= g.nz;
-    int bx0 = INT_MAX, bx1 = INT_MIN, bz0 = INT_MAX, bz1 = INT_MIN;
+    typename std::conditional<CellPos<T>::value, BoxP, BoxI>::type acc;
     if (use_smem) {
       for (int e = threadIdx.x; e < nn; e += blockDim.x) {
         const int li = e / lds, lk = e - li * lds;
@@ -674,7 +695,7 @@ __device__ __forceinline__ void push_chunk(const GridP& g, const T* gE, const T*
         // a particle outside the chunk's box (should not happen; with electron-ion pairs, the ion's cell
         // counts too) takes the global path
         if (!push_one<T, ORDER, true, MC>(sm, nullptr, sm + 6 * cap_nodes, cap_nodes, lds, wx0, wz0, p, pi, pc, box,
-                                          bx0, bx1, bz0, bz1)) {
+                                          acc)) {
           const int q = atomicAdd(&ctrl->n_defer, 1);
           if (q < pd.defer_cap) pd.defer[q] = make_int2(pi, c);
           else atomicOr(&ctrl->status, ST_OVERFLOW);
@@ -699,6 +720,8 @@ __device__ __forceinline__ void push_chunk(const GridP& g, const T* gE, const T*
       else atomicOr(&ctrl->status, ST_OVERFLOW);
     }
     // bounding box of the chunk's live particles for the next step
+    const BoxI bb = acc.unpack();
+    int bx0 = bb.x0, bx1 = bb.x1, bz0 = bb.z0, bz1 = bb.z1;
     bx0 = __reduce_min_sync(0xffffffffu, bx0); bx1 = __reduce_max_sync(0xffffffffu, bx1);
     bz0 = __reduce_min_sync(0xffffffffu, bz0); bz1 = __reduce_max_sync(0xffffffffu, bz1);
     if ((threadIdx.x & 31) == 0) {
@@ -748,9 +771,10 @@ __global__ void __launch_bounds__(PB_THREADS) k_push_deferred(GridP g, const T* 
   for (int j = blockIdx.x; j < novf; j += gridDim.x) {
     const int c = pd.ovf[j];
     const Chunk ch = chunks[c];
-    int bx0 = INT_MAX, bx1 = INT_MIN, bz0 = INT_MAX, bz1 = INT_MIN;
+    BoxI acc;
     for (int pi = ch.p0 + threadIdx.x; pi < ch.p1; pi += blockDim.x)
-      push_global_guarded<T, ORDER, MC>(gE, gB, gJ, g, p, pi, pc, ctrl, bx0, bx1, bz0, bz1);
+      push_global_guarded<T, ORDER, MC>(gE, gB, gJ, g, p, pi, pc, ctrl, acc);
+    int bx0 = acc.x0, bx1 = acc.x1, bz0 = acc.z0, bz1 = acc.z1;
     bx0 = __reduce_min_sync(0xffffffffu, bx0); bx1 = __reduce_max_sync(0xffffffffu, bx1);
     bz0 = __reduce_min_sync(0xffffffffu, bz0); bz1 = __reduce_max_sync(0xffffffffu, bz1);
     if ((threadIdx.x & 31) == 0) {
@@ -760,8 +784,9 @@ __global__ void __launch_bounds__(PB_THREADS) k_push_deferred(GridP g, const T* 
   }
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < ndef; j += gridDim.x * blockDim.x) {
     const int2 e = pd.defer[j];
-    int bx0 = INT_MAX, bx1 = INT_MIN, bz0 = INT_MAX, bz1 = INT_MIN;
-    push_global_guarded<T, ORDER, MC>(gE, gB, gJ, g, p, e.x, pc, ctrl, bx0, bx1, bz0, bz1);
+    BoxI acc;
+    push_global_guarded<T, ORDER, MC>(gE, gB, gJ, g, p, e.x, pc, ctrl, acc);
+    const int bx0 = acc.x0, bx1 = acc.x1, bz0 = acc.z0, bz1 = acc.z1;
     if (bx0 <= bx1) {
       atomicMin(&chunks[e.y].ix0, bx0); atomicMax(&chunks[e.y].ix1, bx1);
       atomicMin(&chunks[e.y].iz0, bz0); atomicMax(&chunks[e.y].iz1, bz1);
@@ -1098,10 +1123,10 @@ __global__ void __launch_bounds__(PB_THREADS) k_push_deferred_batch(const StepAr
     for (int j = blockIdx.x; j < novf; j += gridDim.x) {
       const int c = A.pd.ovf[j];
       const Chunk ch = A.chunks[c];
-      int bx0 = INT_MAX, bx1 = INT_MIN, bz0 = INT_MAX, bz1 = INT_MIN;
+      BoxI acc;
       for (int pi = ch.p0 + threadIdx.x; pi < ch.p1; pi += blockDim.x)
-        push_global_guarded<T, ORDER, false>(A.f.fE[0], A.f.fB[0], A.f.J[0], A.g, A.p, pi, A.pc, A.ctrl, bx0, bx1,
-                                             bz0, bz1);
+        push_global_guarded<T, ORDER, false>(A.f.fE[0], A.f.fB[0], A.f.J[0], A.g, A.p, pi, A.pc, A.ctrl, acc);
+      int bx0 = acc.x0, bx1 = acc.x1, bz0 = acc.z0, bz1 = acc.z1;
       bx0 = __reduce_min_sync(0xffffffffu, bx0); bx1 = __reduce_max_sync(0xffffffffu, bx1);
       bz0 = __reduce_min_sync(0xffffffffu, bz0); bz1 = __reduce_max_sync(0xffffffffu, bz1);
       if ((threadIdx.x & 31) == 0) {
@@ -1111,9 +1136,9 @@ __global__ void __launch_bounds__(PB_THREADS) k_push_deferred_batch(const StepAr
     }
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < ndef; j += gridDim.x * blockDim.x) {
       const int2 e = A.pd.defer[j];
-      int bx0 = INT_MAX, bx1 = INT_MIN, bz0 = INT_MAX, bz1 = INT_MIN;
-      push_global_guarded<T, ORDER, false>(A.f.fE[0], A.f.fB[0], A.f.J[0], A.g, A.p, e.x, A.pc, A.ctrl, bx0, bx1,
-                                           bz0, bz1);
+      BoxI acc;
+      push_global_guarded<T, ORDER, false>(A.f.fE[0], A.f.fB[0], A.f.J[0], A.g, A.p, e.x, A.pc, A.ctrl, acc);
+      const int bx0 = acc.x0, bx1 = acc.x1, bz0 = acc.z0, bz1 = acc.z1;
       if (bx0 <= bx1) {
         atomicMin(&A.chunks[e.y].ix0, bx0); atomicMax(&A.chunks[e.y].ix1, bx1);
         atomicMin(&A.chunks[e.y].iz0, bz0); atomicMax(&A.chunks[e.y].iz1, bz1);
