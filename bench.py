@@ -46,14 +46,15 @@ BYTES_PER_CELL = {"mixed": 168, "fp64": 336}
 # 2nd and 3rd push of each layout), scaled to the full box by its particle count. Below the 56 bytes of stored
 # state: the last writes of a launch are still in the 129 MB L2 when it ends.
 TRAFFIC_BYTES_PER_PARTICLE = {
-    (8, 8, 8): 49.63, (8, 8, 16): 49.41, (8, 8, 32): 49.56, (8, 8, 64): 49.38, (8, 16, 8): 49.34, (8, 16, 16): 49.42,
-    (8, 16, 32): 49.61, (8, 16, 64): 49.41, (8, 32, 8): 49.28, (8, 32, 16): 49.32, (8, 32, 32): 49.24, (8, 32, 64): 49.29,
-    (16, 8, 8): 49.44, (16, 8, 16): 49.25, (16, 8, 32): 49.33, (16, 8, 64): 49.28, (16, 16, 8): 49.16, (16, 16, 16): 49.24,
-    (16, 16, 32): 49.18, (16, 16, 64): 49.21, (16, 32, 8): 49.24, (16, 32, 16): 49.31, (16, 32, 32): 49.25, (16, 32, 64): 49.23,
-    (32, 8, 8): 49.15, (32, 8, 16): 49.23, (32, 8, 32): 49.16, (32, 8, 64): 49.21, (32, 16, 8): 49.2, (32, 16, 16): 49.31,
-    (32, 16, 32): 49.34, (32, 16, 64): 49.19, (32, 32, 8): 48.94, (32, 32, 16): 48.88, (32, 32, 32): 48.86, (32, 32, 64): 48.81,
-    (8, 8, 128): 49.62, (8, 16, 128): 49.49, (8, 32, 128): 49.26, (16, 8, 128): 49.45, (16, 16, 128): 49.22,
-    (16, 32, 128): 49.23, (32, 8, 128): 49.22, (32, 16, 128): 49.22, (32, 32, 128): 48.91,
+    (8, 8, 8): 49.14, (8, 8, 16): 49.09, (8, 8, 32): 49.33, (8, 8, 64): 49.19, (8, 8, 128): 49.01, (8, 16, 8): 49.05,
+    (8, 16, 16): 49.08, (8, 16, 32): 49.16, (8, 16, 64): 49.09, (8, 16, 128): 49.15, (8, 32, 8): 48.91,
+    (8, 32, 16): 49.01, (8, 32, 32): 48.93, (8, 32, 64): 48.99, (8, 32, 128): 48.91, (16, 8, 8): 48.95,
+    (16, 8, 16): 48.99, (16, 8, 32): 49.2, (16, 8, 64): 48.96, (16, 8, 128): 49.06, (16, 16, 8): 48.99,
+    (16, 16, 16): 49.0, (16, 16, 32): 48.94, (16, 16, 64): 48.96, (16, 16, 128): 48.96, (16, 32, 8): 48.89,
+    (16, 32, 16): 48.98, (16, 32, 32): 48.92, (16, 32, 64): 49.04, (16, 32, 128): 48.97, (32, 8, 8): 48.84,
+    (32, 8, 16): 48.97, (32, 8, 32): 48.89, (32, 8, 64): 48.99, (32, 8, 128): 48.9, (32, 16, 8): 48.99,
+    (32, 16, 16): 48.93, (32, 16, 32): 48.99, (32, 16, 64): 49.03, (32, 16, 128): 48.83, (32, 32, 8): 48.76,
+    (32, 32, 16): 48.78, (32, 32, 32): 48.74, (32, 32, 64): 48.86, (32, 32, 128): 48.69,
 }
 # the push's instruction and FP32 arithmetic counts per particle (mixed, cubic, Yee-located gather; ncu
 # smsp__inst_executed.sum and smsp__sass_thread_inst_executed_op_{fadd,fmul,ffma}_pred_on.sum of three pushes
