@@ -10,6 +10,7 @@
 //    particles of different cells and their shared atomics do not collide);
 //  - plasma rows entering through the +z plane (Sec. 3.1.1, PR-12).
 #include <climits>
+#include <cstring>
 #include <type_traits>
 
 #include "pic_common.cuh"
@@ -276,6 +277,45 @@ __device__ __forceinline__ float2 interp_two_f(const float* __restrict__ F0, int
 // With SMEM the particle must lie in the staged window: when its cell at t^n
 // (or its live lattice ion's cell) is outside the chunk's box, nothing is
 // changed and false is returned, so that the caller takes the global path.
+// Mixed path: the state of a thread's next particle is copied into shared memory by per-thread
+// asynchronous copies while the thread pushes the current one (each thread reads only what it copied
+// itself: no block barrier). Word k of a thread's record sits at rec[k * PB_THREADS] (a warp's reads fall
+// in consecutive banks); the record is read into registers before the next copy overwrites it.
+enum { RW_W, RW_CELL, RW_OX, RW_OZ, RW_UX, RW_UY, RW_UZ, RW_ID, RW_N };
+struct PRec { uint32_t v[RW_N]; };
+
+template <class T>
+constexpr size_t push_stage_bytes() { return CellPos<T>::value ? (size_t)RW_N * PB_THREADS * 4 : 0; }
+
+__device__ __forceinline__ void cp_async4(uint32_t* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+
+__device__ __forceinline__ void stage_particle(const Particles<float>& p, int pi, uint32_t* rec) {
+  cp_async4(rec + RW_W * PB_THREADS, p.w + pi);
+  cp_async4(rec + RW_CELL * PB_THREADS, p.cell + pi);
+  cp_async4(rec + RW_OX * PB_THREADS, p.ox + pi);
+  cp_async4(rec + RW_OZ * PB_THREADS, p.oz + pi);
+  cp_async4(rec + RW_UX * PB_THREADS, p.ux + pi);
+  cp_async4(rec + RW_UY * PB_THREADS, p.uy + pi);
+  cp_async4(rec + RW_UZ * PB_THREADS, p.uz + pi);
+  cp_async4(rec + RW_ID * PB_THREADS, p.id + pi);
+}
+
+// a particle's word from its record (ST) or from global memory
+template <bool ST, class X>
+__device__ __forceinline__ X pword(const X* g, int pi, const PRec* r, int k) {
+  if constexpr (ST) {
+    static_assert(sizeof(X) == 4, "records hold 32-bit words");
+    X x;
+    memcpy(&x, &r->v[k], 4);
+    return x;
+  } else {
+    return g[pi];
+  }
+}
+
 // Bounding box of the cells a thread's particles occupy, accumulated over its particles of a chunk.
 struct BoxI {
   int x0 = INT_MAX, x1 = INT_MIN, z0 = INT_MAX, z1 = INT_MIN;
@@ -301,19 +341,20 @@ struct BoxP {
   }
 };
 
-template <class T, int ORDER, bool SMEM, bool MC = false, class ACC = BoxI>
+template <class T, int ORDER, bool SMEM, bool MC = false, class ACC = BoxI, bool ST = false>
 __device__ __forceinline__ bool push_one(const T* __restrict__ Eb, const T* __restrict__ Bb, T* Jb, long cs, int ld,
                                          int ox, int oz, const Particles<T>& p, int pi, const PushConst& pc, const Box& box,
-                                         ACC& acc) {
+                                         ACC& acc,
+                                         const PRec* rec = nullptr) {
   constexpr int NG = St<ORDER>::NG, ND = St<ORDER>::ND;
   constexpr bool CP = CellPos<T>::value;
-  const T w = p.w[pi];
+  const T w = pword<ST>(p.w, pi, rec, RW_W);
   if (w == T(0)) return true;
   if constexpr (CP) {
     if (w < T(0)) {
       // ghost: the lab-fixed ion of an electron that has left the domain; it
       // deposits its J_z until its lattice row leaves too
-      const uint32_t id = p.id[pi];
+      const uint32_t id = pword<ST>(p.id, pi, rec, RW_ID);
       if (site_row(id, pc) < pc.mlo) { p.w[pi] = T(0); return true; }
       IonSite<ORDER> is;
       ion_site<ORDER>(id, pc, is);
@@ -333,13 +374,13 @@ __device__ __forceinline__ bool push_one(const T* __restrict__ Eb, const T* __re
   uint32_t pid = 0;
   IonSite<ORDER> is{};
   if constexpr (CP) {
-    cs0 = p.cell[pi];
-    ozs = p.oz[pi];
+    cs0 = pword<ST>(p.cell, pi, rec, RW_CELL);
+    ozs = pword<ST>(p.oz, pi, rec, RW_OZ);
     fx = cell_x(cs0);
     frame_z(cs0, ozs, pc.fr0_sz, pc.fr0_fz, fz, tz);
-    tx = p.ox[pi];
+    tx = pword<ST>(p.ox, pi, rec, RW_OX);
     if (pc.pairs) {
-      pid = p.id[pi];
+      pid = pword<ST>(p.id, pi, rec, RW_ID);
       ion_live = site_row(pid, pc) >= pc.mlo;
       if (ion_live) {
         lattice_site_pow2(pid, pc.kb, pc.lpx, pc.lpz, pc.gx_lo, pc.z0_cells, is.cell, is.ox, is.oz);
@@ -365,7 +406,7 @@ __device__ __forceinline__ bool push_one(const T* __restrict__ Eb, const T* __re
     fxh = (int)floor(Xh); fzh = (int)floor(Zh);
     txh = T(Xh - fxh); tzh = T(Zh - fzh);
   }
-  T ux = p.ux[pi], uy = p.uy[pi], uz = p.uz[pi];
+  T ux = pword<ST>(p.ux, pi, rec, RW_UX), uy = pword<ST>(p.uy, pi, rec, RW_UY), uz = pword<ST>(p.uz, pi, rec, RW_UZ);
   T wxi[NG], wzi[NG], wxh[NG], wzh[NG];
   wts<T, ORDER>(tx, wxi); wts<T, ORDER>(tz, wzi);
   T Ex, Ey, Ez, Bx, By, Bz;
@@ -657,7 +698,13 @@ __device__ __forceinline__ void push_chunk(const GridP& g, const T* gE, const T*
     const int nn = wxn * lds;
     const bool use_smem = nn <= cap_nodes && wx0 >= 0 && wz0 >= 0 && wx1 <= g.nx && wz1 <= g.nz;
     typename std::conditional<CellPos<T>::value, BoxP, BoxI>::type acc;
+    uint32_t* rec = reinterpret_cast<uint32_t*>(sm + 9 * cap_nodes) + threadIdx.x;   // mixed path
     if (use_smem) {
+      if constexpr (CellPos<T>::value) {
+        // the thread's first particle is copied while the window is staged
+        if (ch.p0 + (int)threadIdx.x < ch.p1) stage_particle(p, ch.p0 + threadIdx.x, rec);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+      }
       for (int e = threadIdx.x; e < nn; e += blockDim.x) {
         const int li = e / lds, lk = e - li * lds;
         const long gp = (long)(wx0 + li) * g.ld + (wz0 + lk);
@@ -679,28 +726,48 @@ __device__ __forceinline__ void push_chunk(const GridP& g, const T* gE, const T*
       }
       __syncthreads();
       for (int pi = ch.p0 + threadIdx.x; pi < ch.p1; pi += blockDim.x) {
-        // prefetch the next particle of this thread into L1
         const int pn = pi + blockDim.x;
-        if (pn < ch.p1) {
-          if constexpr (CellPos<T>::value) {
-            asm volatile("prefetch.global.L1 [%0];" ::"l"(p.cell + pn));
-            asm volatile("prefetch.global.L1 [%0];" ::"l"(p.ox + pn));
-            asm volatile("prefetch.global.L1 [%0];" ::"l"(p.oz + pn));
+        bool in_box;
+        if constexpr (CellPos<T>::value) {
+          // this particle's record has landed: read it, then copy the next particle into it; the xor chain
+          // reads every word, so the copy is issued only once the reads have returned
+          asm volatile("cp.async.wait_group 0;" ::: "memory");
+          PRec r;
+#pragma unroll
+          for (int k = 0; k < RW_N; k++) r.v[k] = rec[k * PB_THREADS];
+          uint32_t dep;
+          asm volatile(
+              "xor.b32 %0, %1, %2;\n\txor.b32 %0, %0, %3;\n\txor.b32 %0, %0, %4;\n\txor.b32 %0, %0, %5;\n\t"
+              "xor.b32 %0, %0, %6;\n\txor.b32 %0, %0, %7;\n\txor.b32 %0, %0, %8;"
+              : "=r"(dep)
+              : "r"(r.v[0]), "r"(r.v[1]), "r"(r.v[2]), "r"(r.v[3]), "r"(r.v[4]), "r"(r.v[5]), "r"(r.v[6]),
+                "r"(r.v[7])
+              : "memory");
+          (void)dep;
+          if (pn < ch.p1) stage_particle(p, pn, rec);
+          asm volatile("cp.async.commit_group;" ::: "memory");
+          // a particle outside the chunk's box (should not happen; with electron-ion pairs, the ion's cell
+          // counts too) takes the global path
+          in_box = push_one<T, ORDER, true, MC, decltype(acc), true>(sm, nullptr, sm + 6 * cap_nodes, cap_nodes, lds,
+                                                                     wx0, wz0, p, pi, pc, box, acc, &r);
+        } else {
+          // prefetch the next particle of this thread into L1
+          if (pn < ch.p1) {
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(p.ux + pn));
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(p.uy + pn));
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(p.uz + pn));
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(p.w + pn));
           }
-          asm volatile("prefetch.global.L1 [%0];" ::"l"(p.ux + pn));
-          asm volatile("prefetch.global.L1 [%0];" ::"l"(p.uy + pn));
-          asm volatile("prefetch.global.L1 [%0];" ::"l"(p.uz + pn));
-          asm volatile("prefetch.global.L1 [%0];" ::"l"(p.w + pn));
+          in_box = push_one<T, ORDER, true, MC>(sm, nullptr, sm + 6 * cap_nodes, cap_nodes, lds, wx0, wz0, p, pi, pc,
+                                                box, acc);
         }
-        // a particle outside the chunk's box (should not happen; with electron-ion pairs, the ion's cell
-        // counts too) takes the global path
-        if (!push_one<T, ORDER, true, MC>(sm, nullptr, sm + 6 * cap_nodes, cap_nodes, lds, wx0, wz0, p, pi, pc, box,
-                                          acc)) {
+        if (!in_box) {
           const int q = atomicAdd(&ctrl->n_defer, 1);
           if (q < pd.defer_cap) pd.defer[q] = make_int2(pi, c);
           else atomicOr(&ctrl->status, ST_OVERFLOW);
         }
       }
+      if constexpr (CellPos<T>::value) asm volatile("cp.async.wait_all;" ::: "memory");
       __syncthreads();
       for (int e = threadIdx.x; e < nn; e += blockDim.x) {
         const int li = e / lds, lk = e - li * lds;
@@ -1176,7 +1243,7 @@ __global__ void k_add_counts_batch(const StepArgs<T>* a, int nruns) {
 template <class T>
 void launch_push_batch(const StepArgs<T>* a, const BatchGrid& bg, int order, int grid_blocks, int smem_nodes,
                        int tile_z, cudaStream_t s) {
-  const size_t sm = (size_t)9 * smem_nodes * sizeof(T);
+  const size_t sm = (size_t)9 * smem_nodes * sizeof(T) + push_stage_bytes<T>();
   k_push_batch_reset<T><<<(bg.nruns + 255) / 256, 256, 0, s>>>(a, bg.nruns, bg.push_counter);
   const int gb = grid_blocks < 304 ? grid_blocks : 304;
   if (order == 3) {
@@ -1226,7 +1293,7 @@ void launch_push(const GridP& g, const FieldPtrs<T>& f, Particles<T> p, Chunk* c
                  int fr1_sz, float fr1_fz, int pairs, int mlo, int nodal, const PushDefer& pd, cudaStream_t s) {
   (void)beta_b;
   const PushConst pc = push_const(g, q, m, gamma_b, fr1_sz, fr1_fz, pairs, mlo);
-  const size_t sm = (size_t)9 * smem_nodes * sizeof(T);
+  const size_t sm = (size_t)9 * smem_nodes * sizeof(T) + push_stage_bytes<T>();
   cudaMemsetAsync(&ctrl->next_chunk, 0, sizeof(int), s);
   cudaMemsetAsync(&ctrl->n_defer, 0, 2 * sizeof(int), s);
   // 'momentum conserving' gather: the node-interpolated copies; else the Yee-located gather copies
@@ -1265,7 +1332,7 @@ int push_occupancy(int order, bool dbl, int smem_nodes) {
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_push<double, 1, false>, PB_THREADS, sm);
     }
   } else {
-    size_t sm = (size_t)9 * smem_nodes * sizeof(float);
+    size_t sm = (size_t)9 * smem_nodes * sizeof(float) + push_stage_bytes<float>();
     if (order == 3) {
       cudaFuncSetAttribute(k_push<float, 3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_push<float, 3, false>, PB_THREADS, sm);
