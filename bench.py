@@ -46,15 +46,15 @@ BYTES_PER_CELL = {"mixed": 168, "fp64": 336}
 # 2nd and 3rd push of each layout), scaled to the full box by its particle count. Below the 56 bytes of stored
 # state: the last writes of a launch are still in the 129 MB L2 when it ends.
 TRAFFIC_BYTES_PER_PARTICLE = {
-    (8, 8, 8): 49.65, (8, 8, 16): 49.6, (8, 8, 32): 49.65, (8, 8, 64): 49.7, (8, 8, 128): 49.59, (8, 16, 8): 49.68,
-    (8, 16, 16): 49.65, (8, 16, 32): 49.8, (8, 16, 64): 49.72, (8, 16, 128): 49.66, (8, 32, 8): 49.52,
-    (8, 32, 16): 49.57, (8, 32, 32): 49.58, (8, 32, 64): 49.58, (8, 32, 128): 49.4, (16, 8, 8): 49.47,
-    (16, 8, 16): 49.55, (16, 8, 32): 49.65, (16, 8, 64): 49.54, (16, 8, 128): 49.69, (16, 16, 8): 49.68,
-    (16, 16, 16): 49.67, (16, 16, 32): 49.65, (16, 16, 64): 49.67, (16, 16, 128): 49.63, (16, 32, 8): 49.15,
-    (16, 32, 16): 49.2, (16, 32, 32): 49.17, (16, 32, 64): 49.13, (16, 32, 128): 49.06, (32, 8, 8): 49.45,
-    (32, 8, 16): 49.44, (32, 8, 32): 49.4, (32, 8, 64): 49.41, (32, 8, 128): 49.57, (32, 16, 8): 49.16,
-    (32, 16, 16): 49.36, (32, 16, 32): 49.09, (32, 16, 64): 49.21, (32, 16, 128): 49.14, (32, 32, 8): 48.9,
-    (32, 32, 16): 48.84, (32, 32, 32): 48.87, (32, 32, 64): 48.81, (32, 32, 128): 48.87,
+    (8, 8, 8): 49.71, (8, 8, 16): 49.61, (8, 8, 32): 49.58, (8, 8, 64): 49.49, (8, 8, 128): 49.62, (8, 16, 8): 49.58,
+    (8, 16, 16): 49.63, (8, 16, 32): 49.61, (8, 16, 64): 49.49, (8, 16, 128): 49.63, (8, 32, 8): 49.83,
+    (8, 32, 16): 49.81, (8, 32, 32): 49.78, (8, 32, 64): 49.71, (8, 32, 128): 49.74, (16, 8, 8): 49.64,
+    (16, 8, 16): 49.6, (16, 8, 32): 49.74, (16, 8, 64): 49.58, (16, 8, 128): 49.72, (16, 16, 8): 49.79,
+    (16, 16, 16): 49.73, (16, 16, 32): 49.78, (16, 16, 64): 49.69, (16, 16, 128): 49.68, (16, 32, 8): 49.07,
+    (16, 32, 16): 49.13, (16, 32, 32): 49.08, (16, 32, 64): 48.96, (16, 32, 128): 49.09, (32, 8, 8): 49.53,
+    (32, 8, 16): 49.53, (32, 8, 32): 49.54, (32, 8, 64): 49.52, (32, 8, 128): 49.47, (32, 16, 8): 49.05,
+    (32, 16, 16): 49.3, (32, 16, 32): 49.07, (32, 16, 64): 49.05, (32, 16, 128): 49.2, (32, 32, 8): 48.87,
+    (32, 32, 16): 48.85, (32, 32, 32): 48.84, (32, 32, 64): 48.94, (32, 32, 128): 48.95,
 }
 # the push's instruction and FP32 arithmetic counts per particle (mixed, cubic, Yee-located gather; ncu
 # smsp__inst_executed.sum and smsp__sass_thread_inst_executed_op_{fadd,fmul,ffma}_pred_on.sum of three pushes
