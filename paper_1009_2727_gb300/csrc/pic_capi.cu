@@ -273,11 +273,12 @@ struct Sim : SimBase {
     // the boosted-frame drift is uniform, so the cell order decays slowly
     sort_every = cf.sort_every > 0 ? cf.sort_every : 32;
     // the push's shared-memory window of a chunk: its tile plus the stencil's reach (5 cells at cubic
-    // order, 3 at linear) and room for the particles to spread; no more than the padded row stride of
-    // the push (tile_z + 32 nodes: congruent to tile_z modulo 32 banks) times one cell of growth along x,
-    // so that the window and the particle records leave the L1 its share of the SM's 256 KB
+    // order, 3 at linear) and room for the particles to spread; no more than one cell of growth along x
+    // times the row stride: padded for tile_z < 32 (tile_z + 32 nodes, congruent to tile_z modulo 32
+    // banks), else unpadded with 16 cells of room. The window and the particle records then leave the L1
+    // its share of the SM's 256 KB
     const int margin = 10, reach = cf.shape_order == 3 ? 5 : 3;
-    smem_nodes = std::min((tx + 6 + margin) * (tz + 6 + margin), (tx + reach + 1) * (tz + 32));
+    smem_nodes = std::min((tx + 6 + margin) * (tz + 6 + margin), (tx + reach + 1) * (tz + (tz < 32 ? 32 : 16)));
     int dev = 0, nsm = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
