@@ -270,13 +270,6 @@ __device__ __forceinline__ float2 interp_two_f(const float* __restrict__ F0, int
   return acc;
 }
 
-// One particle: gather -> Boris -> move -> Esirkepov. E/B/J are 3-component
-// blocks (component stride cs) addressed as (i - ox)*ld + (k - oz). With SMEM
-// the fields are the shared-memory window: pairs (Ex, Bz) and (Ez, Bx), which
-// share a Yee location, then Ey and By, each block cs elements long (Bb unused).
-// With SMEM the particle must lie in the staged window: when its cell at t^n
-// (or its live lattice ion's cell) is outside the chunk's box, nothing is
-// changed and false is returned, so that the caller takes the global path.
 // Mixed path: the state of a thread's next particle is copied into shared memory by per-thread
 // asynchronous copies while the thread pushes the current one (each thread reads only what it copied
 // itself: no block barrier). Word k of a thread's record sits at rec[k * PB_THREADS] (a warp's reads fall
@@ -341,6 +334,15 @@ struct BoxP {
   }
 };
 
+// One particle: gather -> Boris -> move -> Esirkepov. E/B/J are 3-component
+// blocks (component stride cs) addressed as (i - ox)*ld + (k - oz). With SMEM
+// the fields are the shared-memory window: pairs (Ex, Bz) and (Ez, Bx), which
+// share a Yee location, then Ey and By, each block cs elements long (Bb unused).
+// With SMEM the particle must lie in the staged window: when its cell at t^n
+// (or its live lattice ion's cell) is outside the chunk's box, nothing is
+// changed and false is returned, so that the caller takes the global path.
+// The cells of the particle's new position (and of its ion) are added to acc; with ST the particle's
+// state comes from its record rec instead of the arrays of p.
 template <class T, int ORDER, bool SMEM, bool MC = false, class ACC = BoxI, bool ST = false>
 __device__ __forceinline__ bool push_one(const T* __restrict__ Eb, const T* __restrict__ Bb, T* Jb, long cs, int ld,
                                          int ox, int oz, const Particles<T>& p, int pi, const PushConst& pc, const Box& box,
